@@ -1,0 +1,179 @@
+"""FP64 CPU oracle for the points-as-tori SDF -- TEST INFRASTRUCTURE ONLY.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  The CUDA library never calls it and it
+never calls the CUDA library: the two share no code.
+
+The arithmetic lives in ``oracle.c`` (plain C, double precision, POSIX threads
+over queries); this module is a ctypes wrapper with numpy arrays.  Functions:
+
+  Cloud(points, normals, params)        fit every torus (Sec. 4.1, App. C)
+  Cloud.phi(x, C=64, ...)               shifted blend, Eqs. BasicFormulaShifted
+                                        and RelationshipBetweenLambdaAndRadius
+  Cloud.grad_x(x, ...)                  d phi / d x (forward-mode duals; App. D
+                                        plus the x-dependence of lambda_x)
+  Cloud.grad_params(x, G, ...)          d (sum_q G_q phi_q) / d a_i
+  Cloud.g(i, x)                         g_i(x) = sign(T_i) phi_T(x), Eq. SingleTorusSDF
+  Cloud.trace(org, dir, ...)            sphere tracing (Sec. 6)
+  fit_record(p, n, a)                   the fitted torus of one point
+  torus_sdf(c, u, R, r, x)              literal Eq. SingleTorusSDF for an explicit torus
+  frame(n)                              the (s, t) frame convention
+
+Parity status: every function is pinned by tests/test_oracle_pins.py except
+the blend on noisy clouds with per-query lambda, which has no independent
+closed form ("parity unpinned" beyond the properties listed there).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SO = os.path.join(_HERE, "liboracle.so")
+_SRC = os.path.join(_HERE, "oracle.c")
+
+GLOBAL, FIXED = 0, 1
+SHIFT_SIGMA, SHIFT_DMIN = 0, 1
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c into liboracle.so with gcc (-O2, IEEE double; no
+    fast-math so the oracle keeps correctly rounded libm semantics)."""
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+        cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", _SO, _SRC, "-lm", "-lpthread"]
+        subprocess.run(cmd, check=True)
+    return _SO
+
+
+_lib = None
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        _lib = ctypes.CDLL(build())
+        P = ctypes.c_void_p
+        i64, i32, f64 = ctypes.c_int64, ctypes.c_int, ctypes.c_double
+        _lib.or_build.restype = P
+        _lib.or_build.argtypes = [P, P, P, i64]
+        _lib.or_free.argtypes = [P]
+        _lib.or_phi.argtypes = [P, i32, f64, f64, i32, P, i64, P, P, i32]
+        _lib.or_grad_x.argtypes = [P, i32, f64, f64, P, i64, P, P, i32]
+        _lib.or_grad_params.argtypes = [P, i32, f64, f64, P, i64, P, P, i32]
+        _lib.or_g.argtypes = [P, i64, P, i64, P]
+        _lib.or_trace.argtypes = [P, i32, f64, f64, P, P, i64, i32, f64, f64, f64, P, P, i32]
+        _lib.or_fit_record.argtypes = [P, P, P, P]
+        _lib.or_torus_sdf.argtypes = [P, P, f64, f64, P, i64, P]
+        _lib.or_frame.argtypes = [P, P, P]
+    return _lib
+
+
+def _f64(a, cols=None):
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+    if cols is not None:
+        a = a.reshape(-1, cols)
+    return a
+
+
+def _ptr(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def default_threads() -> int:
+    return len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+
+
+class Cloud:
+    """A fitted cloud held by the oracle."""
+
+    def __init__(self, points, normals, params):
+        lib = _load()
+        self._p = _f64(points, 3)
+        self._n = _f64(normals, 3)
+        self._a = _f64(params, 6)
+        n = self._p.shape[0]
+        if self._n.shape[0] != n or self._a.shape[0] != n:
+            raise ValueError("points, normals and params must have the same length")
+        self._h = lib.or_build(_ptr(self._p), _ptr(self._n), _ptr(self._a), n)
+        if not self._h:
+            raise ValueError("oracle build rejected the cloud (empty, or a zero / non-finite normal)")
+        self.n = n
+
+    def __del__(self):
+        if getattr(self, "_h", None):
+            _load().or_free(self._h)
+            self._h = None
+
+    def phi(self, x, C: float = 64.0, mode: int = GLOBAL, lam: float = 0.0,
+            shift: int = SHIFT_SIGMA, threads: int | None = None, stats: bool = False):
+        x = _f64(x, 3)
+        m = x.shape[0]
+        out = np.empty(m)
+        st = np.empty((m, 5)) if stats else None
+        _load().or_phi(self._h, mode, C, lam, shift, _ptr(x), m, _ptr(out),
+                       _ptr(st) if stats else None, threads or default_threads())
+        return (out, st) if stats else out
+
+    def grad_x(self, x, C: float = 64.0, mode: int = GLOBAL, lam: float = 0.0,
+               threads: int | None = None):
+        x = _f64(x, 3)
+        m = x.shape[0]
+        phi = np.empty(m)
+        g = np.empty((m, 3))
+        _load().or_grad_x(self._h, mode, C, lam, _ptr(x), m, _ptr(phi), _ptr(g), threads or default_threads())
+        return phi, g
+
+    def grad_params(self, x, G, C: float = 64.0, mode: int = GLOBAL, lam: float = 0.0,
+                    threads: int | None = None):
+        x = _f64(x, 3)
+        G = _f64(G).ravel()
+        out = np.empty((self.n, 6))
+        _load().or_grad_params(self._h, mode, C, lam, _ptr(x), x.shape[0], _ptr(G), _ptr(out),
+                               threads or default_threads())
+        return out
+
+    def g(self, i: int, x):
+        x = _f64(x, 3)
+        out = np.empty(x.shape[0])
+        _load().or_g(self._h, int(i), _ptr(x), x.shape[0], _ptr(out))
+        return out
+
+    def trace(self, org, dirs, max_steps: int = 48, eps: float = 1e-4, t_max: float = 6.0,
+              offset: float = 0.0, C: float = 64.0, mode: int = GLOBAL, lam: float = 0.0,
+              threads: int | None = None):
+        org, dirs = _f64(org, 3), _f64(dirs, 3)
+        m = org.shape[0]
+        th = np.empty(m)
+        steps = np.empty(m, dtype=np.int32)
+        _load().or_trace(self._h, mode, C, lam, _ptr(org), _ptr(dirs), m, max_steps, eps, t_max, offset,
+                         _ptr(th), _ptr(steps), threads or default_threads())
+        return th, steps
+
+
+FIT_FIELDS = {"q": slice(0, 3), "nstar": slice(3, 6), "vmin": slice(6, 9), "u": slice(9, 12),
+              "c": slice(12, 15), "R": 15, "r": 16, "kmin": 17, "kmax": 18, "kplus": 19,
+              "kminus": 20, "H": 21, "K": 22, "sign": 23, "flat": 24, "plane": 25}
+
+
+def fit_record(p, n, a) -> dict:
+    p, n, a = _f64(p).ravel(), _f64(n).ravel(), _f64(a).ravel()
+    out = np.zeros(32)
+    _load().or_fit_record(_ptr(p), _ptr(n), _ptr(a), _ptr(out))
+    return {k: (out[v].copy() if isinstance(v, slice) else float(out[v])) for k, v in FIT_FIELDS.items()}
+
+
+def torus_sdf(c, u, R: float, r: float, x):
+    c, u, x = _f64(c).ravel(), _f64(u).ravel(), _f64(x, 3)
+    out = np.empty(x.shape[0])
+    _load().or_torus_sdf(_ptr(c), _ptr(u), float(R), float(r), _ptr(x), x.shape[0], _ptr(out))
+    return out
+
+
+def frame(n):
+    n = _f64(n).ravel()
+    s, t = np.empty(3), np.empty(3)
+    _load().or_frame(_ptr(n), _ptr(s), _ptr(t))
+    return s, t

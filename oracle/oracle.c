@@ -1,0 +1,605 @@
+/*
+ * FP64 CPU oracle for the points-as-tori signed distance ("Points as Tori:
+ * Fast Pointwise Signed Distance for Point Clouds").
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the slow, literal statement of what
+ * the CUDA path computes.  Only the tests, the smoke check and the benchmark's
+ * CPU-baseline leg load it.  It shares no code, header, table or helper with
+ * the CUDA library, and it includes nothing from it.
+ *
+ * What it computes, in the paper's order and notation:
+ *   - the local frame (s_i, t_i) of a normal n_i            (Sec. 4.1; frame
+ *     convention: Duff et al. 2017, "Building an Orthonormal Basis, Revisited")
+ *   - the torus fit from the six coefficients a00..a20       (Sec. 4.1, Eqs.
+ *     MeanAndGaussCurvatures, PrincipalDirections, TorusSigns; App. C)
+ *   - the torus SDF  phi_T = ||(||(x-c) x u|| - R, <x-c,u>)|| - r
+ *     and g_i = sign(T_i) phi_T                              (Eq. SingleTorusSDF)
+ *   - the shifted self-normalised blend with per-query screening
+ *     lambda_x = C / sigma_x, sigma_x = max_i ||x-p_i|| / 2 (Eqs.
+ *     BasicFormulaShifted, RelationshipBetweenLambdaAndRadius)
+ *   - gradients by forward-mode dual numbers through the literal definition
+ *     (App. D states the x-gradient; the dual numbers also carry the
+ *     dependence of lambda_x on x, and d/d(a00..a20) through the fit)
+ *   - a sphere tracer stepping by phi (Sec. 6, "Direct visualization").
+ *
+ * Readings taken where the paper is silent or garbled (each is listed in the
+ * design notes with its evidence):
+ *   X1  torus centre c = Q*(0,0) + n* / kappa_min with SIGNED kappa_min.  The
+ *       printed c = Q* - sign(T)/|kappa_min| n* agrees whenever the two
+ *       curvatures share a sign and puts the centre on the wrong side for
+ *       saddles; the signed form keeps the intent that the torus osculates.
+ *   X2  the sign table of Eq. TorusSigns is kept as printed, with "< 0" read
+ *       as "<= 0" (X5); it equals -sgn(kappa_max).
+ *   X4  principal direction: both rows of (II - kappa I) w = 0 give a
+ *       candidate; the longer one is used; an umbilic takes w = (1, 0).
+ *   X5  kappa_min == 0 (planes, cylinders): R is infinite; the torus is
+ *       replaced by its limit (cylinder about the v_min axis, or the plane).
+ *       "Zero" means |kappa| <= 1e-8 (coordinates are O(1)): below that the
+ *       literal form loses ~eps/|kappa| to cancellation while the limit
+ *       form is off by ~|kappa| |x-q|^2 / 2, both under 1e-7.  A zero
+ *       curvature counts as convex (sgn 0 := -1).
+ *   X6  |kappa_+| == |kappa_-|: kappa_min := kappa_-, kappa_max := kappa_+.
+ *   X8  unit vectors of zero-length vectors are taken as zero (derivatives
+ *       of a norm at 0 are 0).
+ *   X9  d_max == 0 (one point at the query): lambda := 0.
+ */
+#include <math.h>
+#include <pthread.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ------------------------------------------------------------------------ */
+/* Forward-mode dual numbers: a value and up to six partial derivatives.     */
+/* ------------------------------------------------------------------------ */
+#define ND 6
+#define FLAT_EPS 1e-8   /* |kappa| at or below this is a zero curvature (X5) */
+typedef struct { double v; double d[ND]; } dual;
+
+static dual dconst(double v) { dual r; r.v = v; for (int k = 0; k < ND; ++k) r.d[k] = 0.0; return r; }
+static dual dvar(double v, int k) { dual r = dconst(v); r.d[k] = 1.0; return r; }
+static dual dadd(dual a, dual b) { dual r; r.v = a.v + b.v; for (int k = 0; k < ND; ++k) r.d[k] = a.d[k] + b.d[k]; return r; }
+static dual dsub(dual a, dual b) { dual r; r.v = a.v - b.v; for (int k = 0; k < ND; ++k) r.d[k] = a.d[k] - b.d[k]; return r; }
+static dual dmul(dual a, dual b) { dual r; r.v = a.v * b.v; for (int k = 0; k < ND; ++k) r.d[k] = a.d[k] * b.v + a.v * b.d[k]; return r; }
+static dual dscale(dual a, double s) { dual r; r.v = a.v * s; for (int k = 0; k < ND; ++k) r.d[k] = a.d[k] * s; return r; }
+static dual dneg(dual a) { return dscale(a, -1.0); }
+static dual ddiv(dual a, dual b) {
+    dual r; r.v = a.v / b.v;
+    for (int k = 0; k < ND; ++k) r.d[k] = (a.d[k] * b.v - a.v * b.d[k]) / (b.v * b.v);
+    return r;
+}
+static dual dsqrt(dual a) {
+    dual r; r.v = sqrt(a.v > 0.0 ? a.v : 0.0);
+    for (int k = 0; k < ND; ++k) r.d[k] = (r.v > 0.0) ? 0.5 * a.d[k] / r.v : 0.0; /* X8 */
+    return r;
+}
+static dual dabs(dual a) { return a.v < 0.0 ? dneg(a) : a; }
+static dual dexp(dual a) { dual r; r.v = exp(a.v); for (int k = 0; k < ND; ++k) r.d[k] = a.d[k] * r.v; return r; }
+
+typedef struct { dual x, y, z; } dvec;
+static dvec dv_const(const double* p) { dvec r = {dconst(p[0]), dconst(p[1]), dconst(p[2])}; return r; }
+static dvec dv_add(dvec a, dvec b) { dvec r = {dadd(a.x, b.x), dadd(a.y, b.y), dadd(a.z, b.z)}; return r; }
+static dvec dv_sub(dvec a, dvec b) { dvec r = {dsub(a.x, b.x), dsub(a.y, b.y), dsub(a.z, b.z)}; return r; }
+static dvec dv_scale(dvec a, dual s) { dvec r = {dmul(a.x, s), dmul(a.y, s), dmul(a.z, s)}; return r; }
+static dual dv_dot(dvec a, dvec b) { return dadd(dadd(dmul(a.x, b.x), dmul(a.y, b.y)), dmul(a.z, b.z)); }
+static dvec dv_cross(dvec a, dvec b) {
+    dvec r = {dsub(dmul(a.y, b.z), dmul(a.z, b.y)),
+              dsub(dmul(a.z, b.x), dmul(a.x, b.z)),
+              dsub(dmul(a.x, b.y), dmul(a.y, b.x))};
+    return r;
+}
+static dual dv_norm(dvec a) { return dsqrt(dv_dot(a, a)); }
+
+/* ------------------------------------------------------------------------ */
+/* Local frame of a unit normal (Duff et al. 2017, branchless basis).       */
+/* ------------------------------------------------------------------------ */
+void or_frame(const double n[3], double s[3], double t[3]) {
+    double sg = (n[2] >= 0.0) ? 1.0 : -1.0;
+    double a = -1.0 / (sg + n[2]);
+    double b = n[0] * n[1] * a;
+    s[0] = 1.0 + sg * n[0] * n[0] * a; s[1] = sg * b; s[2] = -sg * n[0];
+    t[0] = b; t[1] = sg + n[1] * n[1] * a; t[2] = -n[1];
+}
+
+/* ------------------------------------------------------------------------ */
+/* Torus fit (Sec. 4.1, App. C).  Everything is carried as duals so the same */
+/* code yields d/d(a00..a20) when the coefficients are seeded as variables. */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    dual kplus, kminus, H, K, kmin, kmax;   /* curvatures */
+    dvec nstar, q, vmin, u, c;              /* unit normal n*(0,0), Q*(0,0), directions, centre */
+    dual R, r;                              /* radii (R unused when flat) */
+    int sign;                               /* sign(T_i) */
+    int flat;                               /* kappa_min == 0: limit forms (X5) */
+    int plane;                              /* kappa_max == 0 too */
+} dtorus;
+
+/* a[] = {a00, a01, a10, a11, a02, a20}; n must be unit. */
+static void fit_dual(const double p[3], const double n[3], const dual a[6], dtorus* T) {
+    const dual a00 = a[0], a01 = a[1], a10 = a[2], a11 = a[3], a02 = a[4], a20 = a[5];
+    double s[3], t[3];
+    or_frame(n, s, t);
+    const dual one = dconst(1.0);
+
+    /* A = sqrt(1 + a01^2 + a10^2) */
+    dual A = dsqrt(dadd(one, dadd(dmul(a01, a01), dmul(a10, a10))));
+    dual A2 = dmul(A, A), A3 = dmul(A2, A), A4 = dmul(A2, A2);
+    dual E = dadd(one, dmul(a10, a10));        /* 1 + a10^2 */
+    dual G = dadd(one, dmul(a01, a01));        /* 1 + a01^2 */
+    dual F = dmul(a10, a01);
+    /* Eq. MeanAndGaussCurvatures */
+    T->H = ddiv(dsub(dadd(dmul(a02, E), dmul(a20, G)), dmul(a11, F)), A3);
+    T->K = ddiv(dsub(dscale(dmul(a02, a20), 4.0), dmul(a11, a11)), A4);
+    dual disc = dsub(dmul(T->H, T->H), T->K);
+    if (disc.v < 0.0) disc = dconst(0.0);     /* rounding of an exact umbilic */
+    dual root = dsqrt(disc);
+    T->kplus = dadd(T->H, root);
+    T->kminus = dsub(T->H, root);
+
+    /* kappa_min / kappa_max by magnitude; the tie goes to kappa_- (X6) */
+    int min_is_plus = fabs(T->kplus.v) < fabs(T->kminus.v);
+    T->kmin = min_is_plus ? T->kplus : T->kminus;
+    T->kmax = min_is_plus ? T->kminus : T->kplus;
+
+    /* Eq. PrincipalDirections for kappa_min: the printed w (first row of
+     * (II - kappa I) w = 0) and the second row's candidate (X4). */
+    dual km = T->kmin;
+    dual kA = dmul(km, A);
+    dual w1x = dsub(dmul(kA, F), a11);
+    dual w1y = dsub(dscale(a20, 2.0), dmul(kA, E));
+    dual w2x = dsub(dscale(a02, 2.0), dmul(kA, G));
+    dual w2y = dsub(dmul(kA, F), a11);
+    double l1 = w1x.v * w1x.v + w1y.v * w1y.v;
+    double l2 = w2x.v * w2x.v + w2y.v * w2y.v;
+    double scale = fabs(a20.v) + fabs(a02.v) + fabs(a11.v) + fabs(kA.v) * (E.v + G.v) + 1e-300;
+    dual wx, wy;
+    if (l1 >= l2) { wx = w1x; wy = w1y; } else { wx = w2x; wy = w2y; }
+    if (sqrt(l1 > l2 ? l1 : l2) <= 1e-12 * scale) { wx = dconst(1.0); wy = dconst(0.0); } /* umbilic */
+    dvec sv = dv_const(s), tv = dv_const(t), nv = dv_const(n);
+    /* v = w_x (s + a10 n) + w_y (t + a01 n) */
+    dvec Qs = dv_add(sv, dv_scale(nv, a10));
+    dvec Qt = dv_add(tv, dv_scale(nv, a01));
+    dvec v = dv_add(dv_scale(Qs, wx), dv_scale(Qt, wy));
+    T->vmin = dv_scale(v, ddiv(one, dv_norm(v)));
+
+    /* n*(0,0) = (n - a10 s - a01 t) / A */
+    T->nstar = dv_scale(dv_sub(dv_sub(nv, dv_scale(sv, a10)), dv_scale(tv, a01)), ddiv(one, A));
+    /* Q*(0,0) = p + a00 n */
+    T->q = dv_add(dv_const(p), dv_scale(nv, a00));
+    /* u = n* x v_min */
+    T->u = dv_cross(T->nstar, T->vmin);
+
+    /* Eq. TorusSigns with zero read as negative (X2, X5) */
+    int kmax_nonpos = T->kmax.v <= FLAT_EPS, kmin_nonpos = T->kmin.v <= FLAT_EPS;
+    T->sign = ((kmax_nonpos && kmin_nonpos) || (kmax_nonpos && !kmin_nonpos)) ? 1 : -1;
+
+    T->plane = fabs(T->kmax.v) <= FLAT_EPS;
+    T->flat = fabs(T->kmin.v) <= FLAT_EPS;
+    /* r = 1/|kappa_max| */
+    T->r = T->plane ? dconst(INFINITY) : ddiv(one, dabs(T->kmax));
+    if (!T->flat) {
+        /* R = 1/|kappa_min| - sign(kappa_+ kappa_-) r */
+        double sgp = (T->kplus.v * T->kminus.v > 0.0) ? 1.0 : -1.0;
+        T->R = dsub(ddiv(one, dabs(T->kmin)), dscale(T->r, sgp));
+        /* c = Q* + n* / kappa_min (X1, signed kappa_min) */
+        T->c = dv_add(T->q, dv_scale(T->nstar, ddiv(one, T->kmin)));
+    } else {
+        T->R = dconst(INFINITY);
+        T->c = T->q;
+    }
+}
+
+/* g_i(x) = sign(T_i) phi_T(x), Eq. SingleTorusSDF, as a dual in x and/or the
+ * torus.  Limit forms for kappa_min == 0 (X5):
+ *   plane    : phi = <x - q, n*>, sign +1
+ *   cylinder : axis through q + n* / kappa_max along v_min, radius r,
+ *              phi_T = dist(x, axis) - r. */
+static dual g_dual(const dtorus* T, dvec x) {
+    if (T->plane) {
+        return dv_dot(dv_sub(x, T->q), T->nstar);
+    }
+    dual phiT;
+    if (T->flat) {
+        dvec axis_pt = dv_add(T->q, dv_scale(T->nstar, ddiv(dconst(1.0), T->kmax)));
+        dvec w = dv_sub(x, axis_pt);
+        dual along = dv_dot(w, T->vmin);
+        dvec perp = dv_sub(w, dv_scale(T->vmin, along));
+        phiT = dsub(dv_norm(perp), T->r);
+    } else {
+        dvec v = dv_sub(x, T->c);
+        dual rho = dv_norm(dv_cross(v, T->u));       /* ||(x - c) x u|| */
+        dual h = dv_dot(v, T->u);                    /* <x - c, u> */
+        dual e = dsub(rho, T->R);
+        phiT = dsub(dsqrt(dadd(dmul(e, e), dmul(h, h))), T->r);
+    }
+    return dscale(phiT, (double)T->sign);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Plain FP64 torus record and g (used by the fast blend loop).              */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    double p[3];
+    double q[3], nstar[3], vmin[3], u[3], c[3];
+    double R, r, kmin, kmax;
+    int sign, flat, plane;
+} torus_t;
+
+static void torus_from_dual(const double p[3], const dtorus* D, torus_t* T) {
+    memcpy(T->p, p, sizeof(T->p));
+    T->q[0] = D->q.x.v; T->q[1] = D->q.y.v; T->q[2] = D->q.z.v;
+    T->nstar[0] = D->nstar.x.v; T->nstar[1] = D->nstar.y.v; T->nstar[2] = D->nstar.z.v;
+    T->vmin[0] = D->vmin.x.v; T->vmin[1] = D->vmin.y.v; T->vmin[2] = D->vmin.z.v;
+    T->u[0] = D->u.x.v; T->u[1] = D->u.y.v; T->u[2] = D->u.z.v;
+    T->c[0] = D->c.x.v; T->c[1] = D->c.y.v; T->c[2] = D->c.z.v;
+    T->R = D->R.v; T->r = D->r.v; T->kmin = D->kmin.v; T->kmax = D->kmax.v;
+    T->sign = D->sign; T->flat = D->flat; T->plane = D->plane;
+}
+
+static double dot3(const double* a, const double* b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+
+static double g_plain(const torus_t* T, const double x[3]) {
+    if (T->plane) {
+        double w[3] = {x[0] - T->q[0], x[1] - T->q[1], x[2] - T->q[2]};
+        return dot3(w, T->nstar);
+    }
+    double phiT;
+    if (T->flat) {
+        double ap[3], w[3];
+        for (int k = 0; k < 3; ++k) ap[k] = T->q[k] + T->nstar[k] / T->kmax;
+        for (int k = 0; k < 3; ++k) w[k] = x[k] - ap[k];
+        double along = dot3(w, T->vmin);
+        double pp[3] = {w[0] - along * T->vmin[0], w[1] - along * T->vmin[1], w[2] - along * T->vmin[2]};
+        phiT = sqrt(dot3(pp, pp)) - T->r;
+    } else {
+        double v[3] = {x[0] - T->c[0], x[1] - T->c[1], x[2] - T->c[2]};
+        double cr[3] = {v[1] * T->u[2] - v[2] * T->u[1],
+                        v[2] * T->u[0] - v[0] * T->u[2],
+                        v[0] * T->u[1] - v[1] * T->u[0]};
+        double rho = sqrt(dot3(cr, cr));
+        double h = dot3(v, T->u);
+        double e = rho - T->R;
+        phiT = sqrt(e * e + h * h) - T->r;
+    }
+    return T->sign * phiT;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Cloud                                                                    */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    int64_t n;
+    torus_t* tori;
+    double (*a)[6];          /* coefficients, kept for the parameter gradient */
+    double (*nrm)[3];        /* unit input normals */
+} or_cloud;
+
+/* Builds the cloud: normalises each normal and fits its torus.  Returns NULL
+ * for n <= 0 or a zero / non-finite normal. */
+or_cloud* or_build(const double* points, const double* normals, const double* params, int64_t n) {
+    if (n <= 0) return NULL;
+    or_cloud* C = (or_cloud*)calloc(1, sizeof(or_cloud));
+    C->n = n;
+    C->tori = (torus_t*)calloc((size_t)n, sizeof(torus_t));
+    C->a = calloc((size_t)n, sizeof(*C->a));
+    C->nrm = calloc((size_t)n, sizeof(*C->nrm));
+    for (int64_t i = 0; i < n; ++i) {
+        double nn[3] = {normals[3 * i], normals[3 * i + 1], normals[3 * i + 2]};
+        double len = sqrt(dot3(nn, nn));
+        if (!(len > 0.0) || !isfinite(len)) { free(C->tori); free(C->a); free(C->nrm); free(C); return NULL; }
+        for (int k = 0; k < 3; ++k) nn[k] /= len;
+        memcpy(C->nrm[i], nn, sizeof(nn));
+        dual a[6];
+        for (int k = 0; k < 6; ++k) { C->a[i][k] = params[6 * i + k]; a[k] = dconst(params[6 * i + k]); }
+        dtorus D;
+        fit_dual(points + 3 * i, nn, a, &D);
+        torus_from_dual(points + 3 * i, &D, &C->tori[i]);
+    }
+    return C;
+}
+
+void or_free(or_cloud* C) {
+    if (!C) return;
+    free(C->tori); free(C->a); free(C->nrm); free(C);
+}
+
+int64_t or_size(const or_cloud* C) { return C->n; }
+
+/* Per-point fit record, for tests.  out[32] =
+ * {q(3), nstar(3), vmin(3), u(3), c(3), R, r, kmin, kmax, kplus, kminus, H, K,
+ *  sign, flat, plane, 0...} */
+void or_fit_record(const double p[3], const double n_in[3], const double a_in[6], double out[32]) {
+    double n[3] = {n_in[0], n_in[1], n_in[2]};
+    double len = sqrt(dot3(n, n));
+    for (int k = 0; k < 3; ++k) n[k] /= len;
+    dual a[6];
+    for (int k = 0; k < 6; ++k) a[k] = dconst(a_in[k]);
+    dtorus D;
+    fit_dual(p, n, a, &D);
+    torus_t T;
+    torus_from_dual(p, &D, &T);
+    memset(out, 0, 32 * sizeof(double));
+    memcpy(out + 0, T.q, 3 * sizeof(double));
+    memcpy(out + 3, T.nstar, 3 * sizeof(double));
+    memcpy(out + 6, T.vmin, 3 * sizeof(double));
+    memcpy(out + 9, T.u, 3 * sizeof(double));
+    memcpy(out + 12, T.c, 3 * sizeof(double));
+    out[15] = T.R; out[16] = T.r; out[17] = T.kmin; out[18] = T.kmax;
+    out[19] = D.kplus.v; out[20] = D.kminus.v; out[21] = D.H.v; out[22] = D.K.v;
+    out[23] = T.sign; out[24] = T.flat; out[25] = T.plane;
+}
+
+/* g_i at m query points, for tests. */
+void or_g(const or_cloud* C, int64_t i, const double* x, int64_t m, double* out) {
+    for (int64_t j = 0; j < m; ++j) out[j] = g_plain(&C->tori[i], x + 3 * j);
+}
+
+/* Literal torus SDF for an explicit torus (c, u, R, r), Eq. SingleTorusSDF. */
+void or_torus_sdf(const double c[3], const double u[3], double R, double r,
+                  const double* x, int64_t m, double* out) {
+    for (int64_t j = 0; j < m; ++j) {
+        const double* xj = x + 3 * j;
+        double v[3] = {xj[0] - c[0], xj[1] - c[1], xj[2] - c[2]};
+        double cr[3] = {v[1] * u[2] - v[2] * u[1], v[2] * u[0] - v[0] * u[2], v[0] * u[1] - v[1] * u[0]};
+        double rho = sqrt(dot3(cr, cr));
+        double h = dot3(v, u);
+        out[j] = sqrt((rho - R) * (rho - R) + h * h) - r;
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* The blend (Eqs. BasicFormulaShifted, RelationshipBetweenLambdaAndRadius) */
+/* ------------------------------------------------------------------------ */
+enum { OR_GLOBAL = 0, OR_FIXED = 1 };
+enum { OR_SHIFT_SIGMA = 0, OR_SHIFT_DMIN = 1 };
+
+typedef struct {
+    int mode;          /* OR_GLOBAL: lambda_x = C / sigma_x;  OR_FIXED: lambda given */
+    double C;          /* screening constant (64 in the paper) */
+    double lambda;     /* fixed lambda */
+    int shift;         /* exponent shift: sigma_x (paper) or d_min */
+} or_opts;
+
+/* One query.  Outputs phi and, when non-NULL, the statistics {lambda, dmax,
+ * dmin, W (with the sigma_x shift), argmax index}. */
+static double phi_one(const or_cloud* C, const or_opts* o, const double x[3], double* stats) {
+    const int64_t n = C->n;
+    double dmax = -1.0, dmin = INFINITY;
+    int64_t imax = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        const double* p = C->tori[i].p;
+        double w[3] = {x[0] - p[0], x[1] - p[1], x[2] - p[2]};
+        double d = sqrt(dot3(w, w));
+        if (d > dmax) { dmax = d; imax = i; }
+        if (d < dmin) dmin = d;
+    }
+    double sigma = 0.5 * dmax;
+    double lambda;
+    if (o->mode == OR_GLOBAL) lambda = (dmax > 0.0) ? o->C / sigma : 0.0;   /* X9 */
+    else lambda = o->lambda;
+    double shift = (o->shift == OR_SHIFT_SIGMA && o->mode == OR_GLOBAL) ? sigma : dmin;
+    double W = 0.0, S = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        const double* p = C->tori[i].p;
+        double w3[3] = {x[0] - p[0], x[1] - p[1], x[2] - p[2]};
+        double d = sqrt(dot3(w3, w3));
+        double w = exp(-lambda * (d - shift));
+        W += w;
+        S += w * g_plain(&C->tori[i], x);
+    }
+    if (stats) {
+        stats[0] = lambda; stats[1] = dmax; stats[2] = dmin; stats[3] = W; stats[4] = (double)imax;
+    }
+    return S / W;
+}
+
+typedef struct {
+    const or_cloud* C; const or_opts* o; const double* x; double* phi; double* stats;
+    int64_t q0, q1;
+} phi_job;
+
+static void* phi_worker(void* arg) {
+    phi_job* J = (phi_job*)arg;
+    for (int64_t j = J->q0; j < J->q1; ++j)
+        J->phi[j] = phi_one(J->C, J->o, J->x + 3 * j, J->stats ? J->stats + 5 * j : NULL);
+    return NULL;
+}
+
+static int clamp_threads(int threads, int64_t m) {
+    if (threads < 1) threads = 1;
+    if (threads > 256) threads = 256;
+    if ((int64_t)threads > m) threads = (int)(m > 0 ? m : 1);
+    return threads;
+}
+
+/* phi at m queries with `threads` POSIX threads (queries split in blocks). */
+void or_phi(const or_cloud* C, int mode, double Cconst, double lambda, int shift,
+            const double* x, int64_t m, double* phi, double* stats, int threads) {
+    or_opts o = {mode, Cconst, lambda, shift};
+    threads = clamp_threads(threads, m);
+    pthread_t th[256];
+    phi_job jobs[256];
+    int64_t per = (m + threads - 1) / threads;
+    for (int k = 0; k < threads; ++k) {
+        int64_t q0 = k * per, q1 = q0 + per < m ? q0 + per : m;
+        jobs[k] = (phi_job){C, &o, x, phi, stats, q0, q1 > q0 ? q1 : q0};
+        pthread_create(&th[k], NULL, phi_worker, &jobs[k]);
+    }
+    for (int k = 0; k < threads; ++k) pthread_join(th[k], NULL);
+}
+
+/* ------------------------------------------------------------------------ */
+/* d phi / d x: forward-mode duals through the whole definition, including  */
+/* the dependence of lambda_x on x through the farthest point (App. D gives */
+/* the constant-lambda part; the farthest-point tie goes to the lowest      */
+/* index).                                                                  */
+/* ------------------------------------------------------------------------ */
+static void dtorus_const(const torus_t* T, dtorus* D) {
+    D->q = dv_const(T->q); D->nstar = dv_const(T->nstar); D->vmin = dv_const(T->vmin);
+    D->u = dv_const(T->u); D->c = dv_const(T->c);
+    D->R = dconst(T->R); D->r = dconst(T->r); D->kmin = dconst(T->kmin); D->kmax = dconst(T->kmax);
+    D->sign = T->sign; D->flat = T->flat; D->plane = T->plane;
+}
+
+static double grad_one(const or_cloud* C, const or_opts* o, const double x[3], double g3[3]) {
+    const int64_t n = C->n;
+    dvec X = {dvar(x[0], 0), dvar(x[1], 1), dvar(x[2], 2)};
+    dual dmax = dconst(-1.0);
+    double dmin = INFINITY;
+    for (int64_t i = 0; i < n; ++i) {
+        dual d = dv_norm(dv_sub(X, dv_const(C->tori[i].p)));
+        if (d.v > dmax.v) dmax = d;
+        if (d.v < dmin) dmin = d.v;
+    }
+    dual sigma = dscale(dmax, 0.5);
+    dual lambda;
+    if (o->mode == OR_GLOBAL) lambda = (dmax.v > 0.0) ? ddiv(dconst(o->C), sigma) : dconst(0.0);
+    else lambda = dconst(o->lambda);
+    dual shift = (o->mode == OR_GLOBAL) ? sigma : dconst(dmin);
+    dual W = dconst(0.0), S = dconst(0.0);
+    for (int64_t i = 0; i < n; ++i) {
+        dual d = dv_norm(dv_sub(X, dv_const(C->tori[i].p)));
+        dual w = dexp(dneg(dmul(lambda, dsub(d, shift))));
+        dtorus D;
+        dtorus_const(&C->tori[i], &D);
+        W = dadd(W, w);
+        S = dadd(S, dmul(w, g_dual(&D, X)));
+    }
+    dual phi = ddiv(S, W);
+    g3[0] = phi.d[0]; g3[1] = phi.d[1]; g3[2] = phi.d[2];
+    return phi.v;
+}
+
+typedef struct { const or_cloud* C; const or_opts* o; const double* x; double* phi; double* grad; int64_t q0, q1; } grad_job;
+static void* grad_worker(void* arg) {
+    grad_job* J = (grad_job*)arg;
+    for (int64_t j = J->q0; j < J->q1; ++j) J->phi[j] = grad_one(J->C, J->o, J->x + 3 * j, J->grad + 3 * j);
+    return NULL;
+}
+
+void or_grad_x(const or_cloud* C, int mode, double Cconst, double lambda,
+               const double* x, int64_t m, double* phi, double* grad, int threads) {
+    or_opts o = {mode, Cconst, lambda, OR_SHIFT_SIGMA};
+    threads = clamp_threads(threads, m);
+    pthread_t th[256];
+    grad_job jobs[256];
+    int64_t per = (m + threads - 1) / threads;
+    for (int k = 0; k < threads; ++k) {
+        int64_t q0 = k * per, q1 = q0 + per < m ? q0 + per : m;
+        jobs[k] = (grad_job){C, &o, x, phi, grad, q0, q1 > q0 ? q1 : q0};
+        pthread_create(&th[k], NULL, grad_worker, &jobs[k]);
+    }
+    for (int k = 0; k < threads; ++k) pthread_join(th[k], NULL);
+}
+
+/* ------------------------------------------------------------------------ */
+/* d L / d a_i for L = sum_q G_q phi(x_q).  The weights do not depend on the */
+/* coefficients, so d phi_q / d a_i = (w_qi / W_q) d g_i(x_q) / d a_i; the  */
+/* last factor is a forward-mode dual through the fit and the torus SDF.    */
+/* Parallel over points.                                                    */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    const or_cloud* C; const or_opts* o; const double* x; int64_t m;
+    const double* G; const double* lam; const double* shift; const double* W;
+    double* grad; int64_t i0, i1;
+} pgrad_job;
+
+static void* pgrad_worker(void* arg) {
+    pgrad_job* J = (pgrad_job*)arg;
+    const or_cloud* C = J->C;
+    for (int64_t i = J->i0; i < J->i1; ++i) {
+        dual a[6];
+        for (int k = 0; k < 6; ++k) a[k] = dvar(C->a[i][k], k);
+        dtorus D;
+        fit_dual(C->tori[i].p, C->nrm[i], a, &D);
+        double acc[6] = {0, 0, 0, 0, 0, 0};
+        const double* p = C->tori[i].p;
+        for (int64_t j = 0; j < J->m; ++j) {
+            const double* xj = J->x + 3 * j;
+            double w3[3] = {xj[0] - p[0], xj[1] - p[1], xj[2] - p[2]};
+            double d = sqrt(dot3(w3, w3));
+            double w = exp(-J->lam[j] * (d - J->shift[j]));
+            double coef = J->G[j] * w / J->W[j];
+            if (coef == 0.0) continue;
+            dual g = g_dual(&D, dv_const(xj));
+            for (int k = 0; k < 6; ++k) acc[k] += coef * g.d[k];
+        }
+        for (int k = 0; k < 6; ++k) J->grad[6 * i + k] = acc[k];
+    }
+    return NULL;
+}
+
+void or_grad_params(const or_cloud* C, int mode, double Cconst, double lambda,
+                    const double* x, int64_t m, const double* G, double* grad, int threads) {
+    or_opts o = {mode, Cconst, lambda, OR_SHIFT_SIGMA};
+    double* stats = (double*)malloc((size_t)(m > 0 ? m : 1) * 5 * sizeof(double));
+    double* phi = (double*)malloc((size_t)(m > 0 ? m : 1) * sizeof(double));
+    double* lam = (double*)malloc((size_t)(m > 0 ? m : 1) * sizeof(double));
+    double* sh = (double*)malloc((size_t)(m > 0 ? m : 1) * sizeof(double));
+    double* W = (double*)malloc((size_t)(m > 0 ? m : 1) * sizeof(double));
+    or_phi(C, mode, Cconst, lambda, OR_SHIFT_SIGMA, x, m, phi, stats, threads);
+    for (int64_t j = 0; j < m; ++j) {
+        lam[j] = stats[5 * j];
+        sh[j] = (mode == OR_GLOBAL) ? 0.5 * stats[5 * j + 1] : stats[5 * j + 2];
+        W[j] = stats[5 * j + 3];
+    }
+    threads = clamp_threads(threads, C->n);
+    pthread_t th[256];
+    pgrad_job jobs[256];
+    int64_t per = (C->n + threads - 1) / threads;
+    for (int k = 0; k < threads; ++k) {
+        int64_t i0 = k * per, i1 = i0 + per < C->n ? i0 + per : C->n;
+        jobs[k] = (pgrad_job){C, &o, x, m, G, lam, sh, W, grad, i0, i1 > i0 ? i1 : i0};
+        pthread_create(&th[k], NULL, pgrad_worker, &jobs[k]);
+    }
+    for (int k = 0; k < threads; ++k) pthread_join(th[k], NULL);
+    free(stats); free(phi); free(lam); free(sh); free(W);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Sphere tracing (Sec. 6): from t = 0 evaluate f = phi(o + t dir) - offset; */
+/* a ray hits when f < eps (t_hit = t, steps = evaluations so far), else    */
+/* t += f; it misses when t > t_max or after max_steps evaluations          */
+/* (t_hit = -1).                                                            */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    const or_cloud* C; const or_opts* o; const double* org; const double* dir;
+    int max_steps; double eps, t_max, offset; double* t_hit; int32_t* steps; int64_t r0, r1;
+} trace_job;
+
+static void* trace_worker(void* arg) {
+    trace_job* J = (trace_job*)arg;
+    for (int64_t j = J->r0; j < J->r1; ++j) {
+        const double* o3 = J->org + 3 * j;
+        const double* d3 = J->dir + 3 * j;
+        double t = 0.0, th = -1.0;
+        int k = 0;
+        while (k < J->max_steps) {
+            double x[3] = {o3[0] + t * d3[0], o3[1] + t * d3[1], o3[2] + t * d3[2]};
+            double f = phi_one(J->C, J->o, x, NULL) - J->offset;
+            ++k;
+            if (f < J->eps) { th = t; break; }
+            t += f;
+            if (t > J->t_max) break;
+        }
+        J->t_hit[j] = th;
+        J->steps[j] = k;
+    }
+    return NULL;
+}
+
+void or_trace(const or_cloud* C, int mode, double Cconst, double lambda,
+              const double* org, const double* dir, int64_t nrays, int max_steps, double eps,
+              double t_max, double offset, double* t_hit, int32_t* steps, int threads) {
+    or_opts o = {mode, Cconst, lambda, OR_SHIFT_SIGMA};
+    threads = clamp_threads(threads, nrays);
+    pthread_t th[256];
+    trace_job jobs[256];
+    int64_t per = (nrays + threads - 1) / threads;
+    for (int k = 0; k < threads; ++k) {
+        int64_t r0 = k * per, r1 = r0 + per < nrays ? r0 + per : nrays;
+        jobs[k] = (trace_job){C, &o, org, dir, max_steps, eps, t_max, offset, t_hit, steps, r0, r1 > r0 ? r1 : r0};
+        pthread_create(&th[k], NULL, trace_worker, &jobs[k]);
+    }
+    for (int k = 0; k < threads; ++k) pthread_join(th[k], NULL);
+}
