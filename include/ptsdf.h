@@ -1,0 +1,169 @@
+/*
+ * ptsdf.h -- C ABI of the points-as-tori signed-distance library (libptsdf.so).
+ *
+ * The library evaluates the signed distance of "Points as Tori: Fast Pointwise
+ * Signed Distance for Point Clouds" on one NVIDIA B300 (sm_103a):
+ *
+ *   phi(x) = sum_i g_i(x) w_i(x) / sum_i w_i(x),
+ *   w_i(x) = exp(-lambda_x (||x - p_i|| - sigma_x)),
+ *   sigma_x = max_i ||x - p_i|| / 2,   lambda_x = C / sigma_x,   C = 64,
+ *
+ * (Sec. 4.2, Eqs. BasicFormulaShifted and RelationshipBetweenLambdaAndRadius;
+ * Algorithm 1, "Inference"), where g_i is the signed distance of a torus fitted
+ * at p_i from six coefficients (Sec. 4.1, Eq. SingleTorusSDF).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - Pointers named d_* are DEVICE pointers on the current CUDA device; h_*
+ *    pointers are HOST pointers (pageable or pinned).  float arrays are
+ *    contiguous, row-major, 4-byte aligned; "Q x 3" means x0 y0 z0 x1 y1 z1 ...
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Calls on device pointers are stream-ordered and return once
+ *    the work is enqueued; results are valid after the stream synchronises.
+ *  - The caller owns every input and output buffer.  A cloud owns its packed
+ *    torus records (device memory) until sdf_destroy.
+ *  - Every call returns an sdf_status.  Nothing aborts or exits.  On failure
+ *    sdf_last_error() returns a thread-local message.  Kernels that detect a
+ *    fault (a bounded wait that ran out) set a per-cloud device status word
+ *    instead of trapping; sdf_device_status() reads and clears it.
+ *  - Work is not thread-safe per cloud for concurrent *builds*; queries on
+ *    one cloud from several host threads/streams are safe (read-only).
+ */
+#ifndef PTSDF_H
+#define PTSDF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define PTSDF_API __attribute__((visibility("default")))
+#else
+#define PTSDF_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sdf_cloud_s* sdf_cloud;
+
+typedef enum {
+    SDF_OK = 0,
+    SDF_EINVAL = 1,    /* bad argument (null pointer, negative size, bad option, bad input) */
+    SDF_ENOMEM = 2,    /* device or host allocation failed */
+    SDF_ECUDA = 3,     /* a CUDA runtime call failed (message has the CUDA error string) */
+    SDF_EBUSY = 4,     /* resource in use (serving: no slot / admission refused) */
+    SDF_ETIMEOUT = 5,  /* a host-side wait ran out */
+    SDF_EDEVICE = 6    /* a kernel reported a fault through the device status word */
+} sdf_status;
+
+typedef enum { SDF_F32 = 0, SDF_F16X2 = 1, SDF_BF16X2 = 2 } sdf_precision;
+
+typedef enum {
+    SDF_LAMBDA_GLOBAL = 0,  /* lambda_x = C / sigma_x, sigma_x = max_i ||x - p_i|| / 2 (the paper's rule) */
+    SDF_LAMBDA_FIXED = 1    /* lambda_x = fixed_lambda for every query (Sec. 4.2, "Acceleration and
+                               adaptive lambda", without the radius cut-off) */
+} sdf_lambda_mode;
+
+typedef struct {
+    int32_t lambda_mode;   /* sdf_lambda_mode */
+    int32_t precision;     /* sdf_precision (SDF_F32 is the reference path) */
+    float C;               /* screening constant C of Eq. RelationshipBetweenLambdaAndRadius (64) */
+    float fixed_lambda;    /* lambda for SDF_LAMBDA_FIXED, >= 0 */
+    float offset;          /* returned value is phi(x) - offset (offset surfaces, Sec. 6) */
+    int32_t split_n;       /* number of point chunks per query block; 0 = automatic.  The
+                              automatic choice depends only on (Q, N, SM count), so a query's
+                              result does not depend on what else runs. */
+} sdf_query_opts;
+
+/* Fills *opts with the paper's defaults: GLOBAL lambda, C = 64, F32, offset 0,
+ * automatic split.  Returns SDF_EINVAL for NULL. */
+PTSDF_API sdf_status sdf_opts_default(sdf_query_opts* opts);
+
+/* ---------------------------------------------------------------------------
+ * sdf_build -- fit one torus per point and pack the cloud for querying.
+ *   Sec. 4.1 (Eqs. BivariatePolynomial, MeanAndGaussCurvatures,
+ *   PrincipalDirections, TorusSigns; App. C); Algorithm 1, "Precomputation"
+ *   with the per-point coefficients given as input.
+ *
+ *   d_points   N x 3 float, point positions p_i.
+ *   d_normals  N x 3 float, oriented normals n_i (normalised here; need not
+ *              be unit).  The local frame (s_i, t_i) of n_i is the branchless
+ *              orthonormal basis of Duff et al. 2017.
+ *   d_params   N x 6 float per point: a00, a01, a10, a11, a02, a20 of
+ *              Q(s,t) = a00 + a10 s + a01 t + a11 s t + a20 s^2 + a02 t^2.
+ *   n          number of points, 1 <= n <= 2^31 - 1.
+ *   out        receives the new cloud handle.
+ *   The fit runs in double precision on the device; the cloud copies what it
+ *   needs (inputs may be freed after the stream synchronises).  The call
+ *   synchronises `stream` once (to size the packed layout).
+ *   Errors: SDF_EINVAL for n < 1, NULL pointers, or a zero / non-finite
+ *   normal or non-finite input (detected on the device, reported here);
+ *   SDF_ENOMEM; SDF_ECUDA.
+ * ------------------------------------------------------------------------- */
+PTSDF_API sdf_status sdf_build(const float* d_points, const float* d_normals, const float* d_params,
+                     int64_t n, void* stream, sdf_cloud* out);
+
+/* Releases a cloud (synchronises the device first).  NULL is a no-op. */
+PTSDF_API sdf_status sdf_destroy(sdf_cloud cloud);
+
+/* Cloud facts: number of points, the diagonal of the points' axis-aligned
+ * bounding box (the error scale of the FP32 tolerance), and how many points
+ * use the direct (radius) torus form vs the curvature (kappa) form. */
+PTSDF_API sdf_status sdf_cloud_info(sdf_cloud cloud, int64_t* n, float* aabb_diag, int64_t* n_direct,
+                          int64_t* n_kappa);
+
+/* ---------------------------------------------------------------------------
+ * sdf_query -- phi at Q query points (Algorithm 1, "Inference"; Eqs.
+ *   BasicFormulaShifted, RelationshipBetweenLambdaAndRadius, SingleTorusSDF).
+ *
+ *   d_x     Q x 3 float query positions.
+ *   q       number of queries, >= 0 (0 is a no-op).
+ *   d_phi   Q float, receives phi(x) - opts->offset.
+ *   opts    NULL = sdf_opts_default.
+ *   Every (query, point) pair is evaluated (no cut-off).  Scratch memory is
+ *   taken from the stream-ordered allocator and returned on the stream.
+ *   Errors: SDF_EINVAL (NULL pointers with q > 0, bad opts); SDF_ENOMEM;
+ *   SDF_ECUDA.  Kernel faults show up in sdf_device_status.
+ * ------------------------------------------------------------------------- */
+PTSDF_API sdf_status sdf_query(sdf_cloud cloud, const float* d_x, int64_t q, float* d_phi,
+                     const sdf_query_opts* opts, void* stream);
+
+/* As sdf_query with HOST buffers: copies h_x to the device, evaluates, copies
+ * phi back into h_phi, and synchronises `stream` before returning (so h_phi
+ * is valid on return).  Large batches are cut into chunks whose copies
+ * overlap the evaluation of the previous chunk.  Pinned host memory gives
+ * the fastest copies; pageable memory works. */
+PTSDF_API sdf_status sdf_query_host(sdf_cloud cloud, const float* h_x, int64_t q, float* h_phi,
+                          const sdf_query_opts* opts, void* stream);
+
+/* Reads and clears the cloud's device status word (synchronises `stream`).
+ * *code = 0 when no kernel reported a fault; otherwise a bit set of
+ * SDF_DEV_* codes.  Returns SDF_EDEVICE when *code != 0. */
+enum { SDF_DEV_WAIT_TIMEOUT = 1, SDF_DEV_BAD_INPUT = 2 };
+PTSDF_API sdf_status sdf_device_status(sdf_cloud cloud, void* stream, int32_t* code);
+
+/* ---------------------------------------------------------------------------
+ * Kernel timing (a tracing aid, not part of the method).  While enabled,
+ * every kernel the library launches is bracketed by two CUDA events recorded
+ * on the stream it is launched on.  sdf_profile_read waits for the recorded
+ * events and returns, for one kernel family, the number of launches and
+ * their total device time in milliseconds since the last enable.  Enabling
+ * clears earlier records; disabling stops recording and keeps them.
+ * ------------------------------------------------------------------------- */
+enum { SDF_K_PREPASS = 0, SDF_K_FWD = 1, SDF_K_MERGE = 2, SDF_K_BUILD = 3, SDF_K_COUNT_ = 4 };
+PTSDF_API sdf_status sdf_profile_enable(int32_t on);
+PTSDF_API sdf_status sdf_profile_read(int32_t kernel, int64_t* launches, double* total_ms);
+/* Name of a kernel family (NULL for an id out of range). */
+PTSDF_API const char* sdf_kernel_name(int32_t kernel);
+
+/* Thread-local description of the last failure on this thread ("" if none). */
+PTSDF_API const char* sdf_last_error(void);
+
+/* Library version string. */
+PTSDF_API const char* sdf_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PTSDF_H */

@@ -1,0 +1,385 @@
+// sdf_build: one torus per point from six coefficients (Sec. 4.1, App. C),
+// packed into the two record forms of the query kernels.
+//
+//   1. k_aabb       one CTA: axis-aligned bounding box of the points.
+//   2. k_fit        one thread per point, double precision: frame, fundamental
+//                   forms, curvatures, principal direction, n*, Q*(0,0), axis,
+//                   sign, and the record in the direct or the kappa form.
+//   3. k_partition  one CTA: stable partition of the records into the two
+//                   segments, each padded to whole tiles; the prepass array
+//                   and the slot -> point permutation.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "device_common.cuh"
+#include "internal.h"
+
+namespace ptsdf {
+
+namespace {
+
+constexpr int kAabbThreads = 1024;
+constexpr int kPartThreads = 1024;
+// |kappa| at or below this (coordinates are O(1)) is a zero curvature.
+constexpr double kFlatKappa = 1e-8;
+
+__global__ void k_aabb(const float* __restrict__ pts, int64_t n, float* __restrict__ box) {
+    __shared__ float red[6][kAabbThreads / 32];
+    float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+        for (int k = 0; k < 3; ++k) {
+            const float v = pts[3 * i + k];
+            lo[k] = fminf(lo[k], v);
+            hi[k] = fmaxf(hi[k], v);
+        }
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+        for (int k = 0; k < 3; ++k) {
+            lo[k] = fminf(lo[k], __shfl_xor_sync(0xffffffffu, lo[k], off));
+            hi[k] = fmaxf(hi[k], __shfl_xor_sync(0xffffffffu, hi[k], off));
+        }
+    }
+    const int w = threadIdx.x / 32, lane = threadIdx.x % 32;
+    if (lane == 0) {
+        for (int k = 0; k < 3; ++k) {
+            red[k][w] = lo[k];
+            red[3 + k][w] = hi[k];
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < 3; ++k) {
+            float a = INFINITY, b = -INFINITY;
+            for (int j = 0; j < (int)(blockDim.x / 32); ++j) {
+                a = fminf(a, red[k][j]);
+                b = fmaxf(b, red[3 + k][j]);
+            }
+            box[k] = a;
+            box[3 + k] = b;
+        }
+    }
+}
+
+__device__ __forceinline__ double sgn_convex(double v) { return v > 0.0 ? 1.0 : -1.0; }
+
+// One point: returns the record (16 floats) and its kind (0 direct, 1 kappa);
+// sets *bad for a zero / non-finite normal or non-finite input.
+__global__ void k_fit(const float* __restrict__ P, const float* __restrict__ Nrm, const float* __restrict__ A6,
+                      int64_t n, double thr, float* __restrict__ rec_tmp, int8_t* __restrict__ kind,
+                      int32_t* __restrict__ status) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double p[3], nv[3], a[6];
+    bool finite = true;
+    for (int k = 0; k < 3; ++k) {
+        p[k] = P[3 * i + k];
+        nv[k] = Nrm[3 * i + k];
+        finite = finite && isfinite(p[k]) && isfinite(nv[k]);
+    }
+    for (int k = 0; k < 6; ++k) {
+        a[k] = A6[6 * i + k];
+        finite = finite && isfinite(a[k]);
+    }
+    const double len = sqrt(nv[0] * nv[0] + nv[1] * nv[1] + nv[2] * nv[2]);
+    float* out = rec_tmp + (size_t)i * kRecFloats;
+    if (!finite || !(len > 0.0) || !isfinite(len)) {
+        atomicOr(status, (int32_t)SDF_DEV_BAD_INPUT);
+        for (int k = 0; k < kRecFloats; ++k) out[k] = 0.f;
+        kind[i] = 0;
+        return;
+    }
+    for (int k = 0; k < 3; ++k) nv[k] /= len;
+    const double a00 = a[0], a01 = a[1], a10 = a[2], a11 = a[3], a02 = a[4], a20 = a[5];
+
+    // branchless orthonormal frame of n (Duff et al. 2017)
+    const double sg = nv[2] >= 0.0 ? 1.0 : -1.0;
+    const double fa = -1.0 / (sg + nv[2]);
+    const double fb = nv[0] * nv[1] * fa;
+    const double s[3] = {1.0 + sg * nv[0] * nv[0] * fa, sg * fb, -sg * nv[0]};
+    const double t[3] = {fb, sg + nv[1] * nv[1] * fa, -nv[1]};
+
+    // fundamental forms at (0,0): I = [[E, F], [F, G]], II = [[2a20, a11], [a11, 2a02]] / A
+    const double E = 1.0 + a10 * a10, G = 1.0 + a01 * a01, F = a10 * a01;
+    const double A2 = 1.0 + a01 * a01 + a10 * a10;
+    const double A = sqrt(A2);
+    // mean and Gauss curvature (Eq. MeanAndGaussCurvatures)
+    const double H = (a02 * E + a20 * G - a11 * F) / (A2 * A);
+    const double K = (4.0 * a02 * a20 - a11 * a11) / (A2 * A2);
+    const double root = sqrt(fmax(H * H - K, 0.0));
+    const double kp = H + root, km = H - root;
+    // kappa_min has the smaller magnitude; a tie keeps kappa_- as kappa_min
+    double kmin = (fabs(kp) < fabs(km)) ? kp : km;
+    double kmax = (fabs(kp) < fabs(km)) ? km : kp;
+    if (fabs(kmin) <= kFlatKappa) kmin = 0.0;
+    if (fabs(kmax) <= kFlatKappa) kmax = 0.0;
+
+    // principal direction of kappa_min: (II - kappa I) w = 0 (Eq. PrincipalDirections).
+    // Each row of the 2x2 system gives a candidate; the longer is kept (the
+    // printed one vanishes when a11 = 0 and kappa = 2 a20).  Umbilic: w = (1, 0).
+    const double kA = kmin * A;
+    double w1x = kA * F - a11, w1y = 2.0 * a20 - kA * E;
+    double w2x = 2.0 * a02 - kA * G, w2y = kA * F - a11;
+    const double l1 = w1x * w1x + w1y * w1y, l2 = w2x * w2x + w2y * w2y;
+    double wx = l1 >= l2 ? w1x : w2x, wy = l1 >= l2 ? w1y : w2y;
+    const double scale = fabs(a20) + fabs(a02) + fabs(a11) + fabs(kA) * (E + G) + 1e-300;
+    if (sqrt(fmax(l1, l2)) <= 1e-12 * scale) {
+        wx = 1.0;
+        wy = 0.0;
+    }
+    double v[3], nstar[3], q[3], u[3];
+    for (int k = 0; k < 3; ++k) v[k] = wx * (s[k] + a10 * nv[k]) + wy * (t[k] + a01 * nv[k]);
+    const double vl = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+    for (int k = 0; k < 3; ++k) v[k] /= vl;
+    // unit normal of the patch at (0,0), and the shifted point Q*(0,0)
+    for (int k = 0; k < 3; ++k) {
+        nstar[k] = (nv[k] - a10 * s[k] - a01 * t[k]) / A;
+        q[k] = p[k] + a00 * nv[k];
+    }
+    // axis of revolution u = n* x v_min
+    u[0] = nstar[1] * v[2] - nstar[2] * v[1];
+    u[1] = nstar[2] * v[0] - nstar[0] * v[2];
+    u[2] = nstar[0] * v[1] - nstar[1] * v[0];
+
+    const double sT = -sgn_convex(kmax);          // Eq. TorusSigns
+    const bool direct = (kmin != 0.0) && (1.0 / fabs(kmin) <= thr) && (1.0 / fabs(kmax) <= thr);
+    if (direct) {
+        const double r = 1.0 / fabs(kmax);
+        const double R = 1.0 / fabs(kmin) - sgn_convex(kmin) * sgn_convex(kmax) * r;
+        double c[3];
+        for (int k = 0; k < 3; ++k) c[k] = q[k] + nstar[k] / kmin;   // signed kappa_min
+        out[0] = (float)p[0]; out[1] = (float)p[1]; out[2] = (float)p[2]; out[3] = (float)sT;
+        out[4] = (float)c[0]; out[5] = (float)c[1]; out[6] = (float)c[2]; out[7] = (float)R;
+        out[8] = (float)u[0]; out[9] = (float)u[1]; out[10] = (float)u[2]; out[11] = (float)(-sT * r);
+        out[12] = 0.f; out[13] = 0.f; out[14] = 0.f; out[15] = 0.f;
+        kind[i] = 0;
+    } else {
+        const double zeta = -sgn_convex(kmin);
+        out[0] = (float)p[0]; out[1] = (float)p[1]; out[2] = (float)p[2]; out[3] = (float)(2.0 * zeta);
+        out[4] = (float)q[0]; out[5] = (float)q[1]; out[6] = (float)q[2]; out[7] = (float)fabs(kmin);
+        out[8] = (float)u[0]; out[9] = (float)u[1]; out[10] = (float)u[2]; out[11] = (float)(-kmax);
+        out[12] = (float)(2.0 * zeta * nstar[0]); out[13] = (float)(2.0 * zeta * nstar[1]);
+        out[14] = (float)(2.0 * zeta * nstar[2]); out[15] = 0.f;
+        kind[i] = 1;
+    }
+}
+
+// Block-wide exclusive scan of one int per thread; returns the prefix and
+// writes the block total to *total.
+__device__ int block_exclusive_scan(int v, int* warp_sums, int* total) {
+    const int lane = threadIdx.x % 32, w = threadIdx.x / 32, nw = blockDim.x / 32;
+    int x = v;
+    for (int off = 1; off < 32; off <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, off);
+        if (lane >= off) x += y;
+    }
+    if (lane == 31) warp_sums[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        int s = lane < nw ? warp_sums[lane] : 0;
+        for (int off = 1; off < 32; off <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, s, off);
+            if (lane >= off) s += y;
+        }
+        if (lane < nw) warp_sums[lane] = s;   // inclusive over warps
+    }
+    __syncthreads();
+    const int base = w > 0 ? warp_sums[w - 1] : 0;
+    *total = warp_sums[nw - 1];
+    __syncthreads();
+    return base + x - v;
+}
+
+__global__ void k_count(const int8_t* __restrict__ kind, int64_t n, int64_t* __restrict__ counts) {
+    __shared__ int ws[32];
+    int64_t nk = 0;
+    for (int64_t base = 0; base < n; base += blockDim.x) {
+        const int64_t i = base + threadIdx.x;
+        int tot;
+        block_exclusive_scan((i < n && kind[i]) ? 1 : 0, ws, &tot);
+        nk += tot;
+    }
+    if (threadIdx.x == 0) {
+        counts[0] = n - nk;
+        counts[1] = nk;
+    }
+}
+
+__global__ void k_partition(const float4* __restrict__ rec_tmp, const int8_t* __restrict__ kind,
+                            const float* __restrict__ P, int64_t n, int64_t n_direct, int64_t tiles_direct,
+                            float cx, float cy, float cz, float4* __restrict__ rec, float4* __restrict__ pre,
+                            int32_t* __restrict__ perm) {
+    __shared__ int ws[32];
+    int64_t pos_d = 0, pos_k = 0;
+    for (int64_t base = 0; base < n; base += blockDim.x) {
+        const int64_t i = base + threadIdx.x;
+        const bool valid = i < n;
+        const int isk = valid ? (int)kind[i] : 0;
+        int tot_k, tot_d;
+        const int ek = block_exclusive_scan(valid && isk ? 1 : 0, ws, &tot_k);
+        const int ed = block_exclusive_scan(valid && !isk ? 1 : 0, ws, &tot_d);
+        if (valid) {
+            const int64_t slot = isk ? tiles_direct * kTileRecs + pos_k + ek : pos_d + ed;
+            const int64_t cpos = isk ? n_direct + pos_k + ek : pos_d + ed;
+            for (int k = 0; k < 4; ++k) rec[slot * 4 + k] = rec_tmp[i * 4 + k];
+            perm[slot] = (int32_t)i;
+            const float px = P[3 * i] - cx, py = P[3 * i + 1] - cy, pz = P[3 * i + 2] - cz;
+            pre[cpos] = make_float4(-2.f * px, -2.f * py, -2.f * pz, px * px + py * py + pz * pz);
+        }
+        pos_d += tot_d;
+        pos_k += tot_k;
+    }
+}
+
+__global__ void k_fill_perm(int32_t* perm, int64_t m) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < m) perm[i] = -1;
+}
+
+}  // namespace
+
+}  // namespace ptsdf
+
+using namespace ptsdf;
+
+namespace {
+
+void free_cloud(Cloud* c) {
+    if (!c) return;
+    cudaFree(c->rec);
+    cudaFree(c->pre);
+    cudaFree(c->perm);
+    cudaFree(c->src_points);
+    cudaFree(c->src_normals);
+    cudaFree(c->src_params);
+    cudaFree(c->status);
+    delete c;
+}
+
+}  // namespace
+
+extern "C" sdf_status sdf_build(const float* d_points, const float* d_normals, const float* d_params, int64_t n,
+                                void* stream, sdf_cloud* out) {
+    if (!out) return set_error(SDF_EINVAL, "sdf_build: out is NULL");
+    *out = nullptr;
+    if (n < 1 || n > 0x7fffffffLL) return set_error(SDF_EINVAL, "sdf_build: n must be in [1, 2^31-1]");
+    if (!d_points || !d_normals || !d_params) return set_error(SDF_EINVAL, "sdf_build: NULL input pointer");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    Cloud* c = new Cloud();
+    c->n = n;
+    cudaError_t e = cudaGetDevice(&c->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
+    if (e != cudaSuccess) {
+        delete c;
+        return cuda_error(e, "sdf_build: device query");
+    }
+    float* box = nullptr;
+    float* rec_tmp = nullptr;
+    int8_t* kind = nullptr;
+    int64_t* counts = nullptr;
+    auto fail = [&](cudaError_t err, const char* what) {
+        cudaStreamSynchronize(st);
+        cudaFree(box);
+        cudaFree(rec_tmp);
+        cudaFree(kind);
+        cudaFree(counts);
+        free_cloud(c);
+        return err == cudaErrorMemoryAllocation ? set_error(SDF_ENOMEM, what) : cuda_error(err, what);
+    };
+#define PTSDF_TRY(call, what)                  \
+    do {                                       \
+        cudaError_t _e = (call);               \
+        if (_e != cudaSuccess) return fail(_e, what); \
+    } while (0)
+    PTSDF_TRY(cudaMalloc(&c->status, sizeof(int32_t)), "sdf_build: status alloc");
+    PTSDF_TRY(cudaMemsetAsync(c->status, 0, sizeof(int32_t), st), "sdf_build: status init");
+    PTSDF_TRY(cudaMalloc(&box, 6 * sizeof(float)), "sdf_build: box alloc");
+    PTSDF_TRY(cudaMalloc(&rec_tmp, (size_t)n * kRecFloats * sizeof(float)), "sdf_build: temp alloc");
+    PTSDF_TRY(cudaMalloc(&kind, (size_t)n), "sdf_build: temp alloc");
+    PTSDF_TRY(cudaMalloc(&counts, 2 * sizeof(int64_t)), "sdf_build: temp alloc");
+    PTSDF_TRY(cudaMalloc(&c->src_points, (size_t)n * 3 * sizeof(float)), "sdf_build: copy alloc");
+    PTSDF_TRY(cudaMalloc(&c->src_normals, (size_t)n * 3 * sizeof(float)), "sdf_build: copy alloc");
+    PTSDF_TRY(cudaMalloc(&c->src_params, (size_t)n * 6 * sizeof(float)), "sdf_build: copy alloc");
+    PTSDF_TRY(cudaMemcpyAsync(c->src_points, d_points, (size_t)n * 3 * sizeof(float), cudaMemcpyDeviceToDevice, st),
+              "sdf_build: copy points");
+    PTSDF_TRY(cudaMemcpyAsync(c->src_normals, d_normals, (size_t)n * 3 * sizeof(float), cudaMemcpyDeviceToDevice, st),
+              "sdf_build: copy normals");
+    PTSDF_TRY(cudaMemcpyAsync(c->src_params, d_params, (size_t)n * 6 * sizeof(float), cudaMemcpyDeviceToDevice, st),
+              "sdf_build: copy params");
+
+    k_aabb<<<1, kAabbThreads, 0, st>>>(c->src_points, n, box);
+    PTSDF_TRY(cudaGetLastError(), "sdf_build: k_aabb launch");
+    PTSDF_TRY(cudaMemcpyAsync(c->aabb, box, 6 * sizeof(float), cudaMemcpyDeviceToHost, st), "sdf_build: box copy");
+    PTSDF_TRY(cudaStreamSynchronize(st), "sdf_build: sync");
+    const double dx = c->aabb[3] - c->aabb[0], dy = c->aabb[4] - c->aabb[1], dz = c->aabb[5] - c->aabb[2];
+    c->aabb_diag = (float)std::sqrt(dx * dx + dy * dy + dz * dz);
+    // radii up to 8 AABB diagonals keep the direct form's FP32 cancellation
+    // (about 3 ulp of the radius) below 1e-5 of the diagonal; larger ones, and
+    // zero curvatures, use the kappa form
+    const double thr = 8.0 * std::fmax((double)c->aabb_diag, 1e-6);
+
+    const int fit_threads = 128;
+    k_fit<<<(unsigned)((n + fit_threads - 1) / fit_threads), fit_threads, 0, st>>>(
+        c->src_points, c->src_normals, c->src_params, n, thr, rec_tmp, kind, c->status);
+    PTSDF_TRY(cudaGetLastError(), "sdf_build: k_fit launch");
+    k_count<<<1, kPartThreads, 0, st>>>(kind, n, counts);
+    PTSDF_TRY(cudaGetLastError(), "sdf_build: k_count launch");
+    int64_t hcounts[2];
+    int32_t hstatus = 0;
+    PTSDF_TRY(cudaMemcpyAsync(hcounts, counts, sizeof(hcounts), cudaMemcpyDeviceToHost, st), "sdf_build: counts");
+    PTSDF_TRY(cudaMemcpyAsync(&hstatus, c->status, sizeof(int32_t), cudaMemcpyDeviceToHost, st), "sdf_build: status");
+    PTSDF_TRY(cudaStreamSynchronize(st), "sdf_build: sync");
+    if (hstatus & SDF_DEV_BAD_INPUT) {
+        fail(cudaSuccess, "");
+        return set_error(SDF_EINVAL, "sdf_build: zero or non-finite normal, or non-finite point / coefficient");
+    }
+    c->n_direct = hcounts[0];
+    c->n_kappa = hcounts[1];
+    c->tiles_direct = (c->n_direct + kTileRecs - 1) / kTileRecs;
+    c->tiles_kappa = (c->n_kappa + kTileRecs - 1) / kTileRecs;
+    c->pre_tiles = (n + kPreTile - 1) / kPreTile;
+    const int64_t slots = (c->tiles_direct + c->tiles_kappa) * kTileRecs;
+    PTSDF_TRY(cudaMalloc(&c->rec, (size_t)slots * 4 * sizeof(float4)), "sdf_build: record alloc");
+    PTSDF_TRY(cudaMemsetAsync(c->rec, 0, (size_t)slots * 4 * sizeof(float4), st), "sdf_build: record init");
+    PTSDF_TRY(cudaMalloc(&c->pre, (size_t)c->pre_tiles * kPreTile * sizeof(float4)), "sdf_build: prepass alloc");
+    PTSDF_TRY(cudaMemsetAsync(c->pre, 0, (size_t)c->pre_tiles * kPreTile * sizeof(float4), st),
+              "sdf_build: prepass init");
+    PTSDF_TRY(cudaMalloc(&c->perm, (size_t)slots * sizeof(int32_t)), "sdf_build: perm alloc");
+    k_fill_perm<<<(unsigned)((slots + 255) / 256), 256, 0, st>>>(c->perm, slots);
+    PTSDF_TRY(cudaGetLastError(), "sdf_build: k_fill_perm launch");
+    k_partition<<<1, kPartThreads, 0, st>>>(reinterpret_cast<const float4*>(rec_tmp), kind, c->src_points, n,
+                                            c->n_direct, c->tiles_direct, 0.5f * (c->aabb[0] + c->aabb[3]),
+                                            0.5f * (c->aabb[1] + c->aabb[4]), 0.5f * (c->aabb[2] + c->aabb[5]),
+                                            c->rec, c->pre, c->perm);
+    PTSDF_TRY(cudaGetLastError(), "sdf_build: k_partition launch");
+    PTSDF_TRY(cudaStreamSynchronize(st), "sdf_build: sync");
+#undef PTSDF_TRY
+    cudaFree(box);
+    cudaFree(rec_tmp);
+    cudaFree(kind);
+    cudaFree(counts);
+    *out = reinterpret_cast<sdf_cloud>(c);
+    return SDF_OK;
+}
+
+extern "C" sdf_status sdf_destroy(sdf_cloud cloud) {
+    if (!cloud) return SDF_OK;
+    Cloud* c = reinterpret_cast<Cloud*>(cloud);
+    cudaDeviceSynchronize();
+    free_cloud(c);
+    return SDF_OK;
+}
+
+extern "C" sdf_status sdf_cloud_info(sdf_cloud cloud, int64_t* n, float* aabb_diag, int64_t* n_direct,
+                                     int64_t* n_kappa) {
+    if (!cloud) return set_error(SDF_EINVAL, "sdf_cloud_info: cloud is NULL");
+    const Cloud* c = reinterpret_cast<const Cloud*>(cloud);
+    if (n) *n = c->n;
+    if (aabb_diag) *aabb_diag = c->aabb_diag;
+    if (n_direct) *n_direct = c->n_direct;
+    if (n_kappa) *n_kappa = c->n_kappa;
+    return SDF_OK;
+}

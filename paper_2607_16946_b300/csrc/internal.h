@@ -1,0 +1,97 @@
+// Internal declarations shared by the translation units of libptsdf.so.
+// Not part of the public ABI (that is include/ptsdf.h).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+
+#include "ptsdf.h"
+
+namespace ptsdf {
+
+// ---------------------------------------------------------------------------
+// Packed cloud layout in HBM
+// ---------------------------------------------------------------------------
+// Every point becomes one 64-byte record (4 x float4) in one of two forms.
+// Records are partitioned: all direct-form records first, padded to a whole
+// tile, then all kappa-form records, padded to a whole tile.  A tile is
+// kTileRecs records = kTileRecs * 64 bytes, the unit of one bulk (TMA) copy.
+//
+//  direct (radius) form, Eq. SingleTorusSDF with its centre and radii:
+//    r0 = (p.x, p.y, p.z, sT)      sT = sign(T_i) = -sgn(kappa_max)
+//    r1 = (c.x, c.y, c.z, R)
+//    r2 = (u.x, u.y, u.z, -sT r)
+//    r3 = 0
+//  curvature (kappa) form, the same SDF rewritten around Q*(0,0) so that it
+//  stays accurate when R or r is huge (near-flat points):
+//    r0 = (p.x, p.y, p.z, 2 zeta)  zeta = -sgn(kappa_min)
+//    r1 = (q.x, q.y, q.z, k)       q = Q*(0,0), k = |kappa_min|
+//    r2 = (u.x, u.y, u.z, -kappa_max)
+//    r3 = (2 zeta n*.x, 2 zeta n*.y, 2 zeta n*.z, 0)
+// with sgn(0) := -1 (a zero curvature counts as convex).
+//
+// A second array holds, per point in the same partitioned order (compact,
+// padded to kPreTile), float4(-2 p', |p'|^2) with p' = p - (bounding-box
+// centre), for the d_max / d_min prepass.
+constexpr int kTileRecs = 32;        // records per main-loop tile (2 KB)
+constexpr int kRecFloats = 16;
+constexpr int kPreTile = 256;        // points per prepass tile (4 KB)
+
+struct Cloud {
+    int device = 0;
+    int64_t n = 0;                   // points
+    int64_t n_direct = 0, n_kappa = 0;
+    int64_t tiles_direct = 0, tiles_kappa = 0;
+    int64_t pre_tiles = 0;
+    float aabb_diag = 0.f;
+    float aabb[6] = {0, 0, 0, 0, 0, 0};
+    float4* rec = nullptr;           // (tiles_direct + tiles_kappa) * kTileRecs * 4 float4
+    float4* pre = nullptr;           // pre_tiles * kPreTile float4
+    int32_t* perm = nullptr;         // record slot -> original point index (-1 for padding)
+    float* src_points = nullptr;     // copies of the inputs (N x 3, N x 3, N x 6), kept for
+    float* src_normals = nullptr;    // the parameter gradient's chain through the fit
+    float* src_params = nullptr;
+    int32_t* status = nullptr;       // device status word (SDF_DEV_* bits)
+    int num_sms = 148;
+};
+
+// thread-local error message
+sdf_status set_error(sdf_status st, const std::string& msg);
+sdf_status cuda_error(cudaError_t e, const char* what);
+
+// launch planning shared by the query kernels
+struct Plan {
+    int64_t q = 0;
+    int64_t qblocks = 0;             // query blocks of kQueriesPerCta
+    int split = 1;                   // point chunks
+    int64_t tiles_per_chunk = 0;     // main-loop tiles per chunk
+    int64_t pre_tiles_per_chunk = 0; // prepass tiles per chunk
+};
+
+constexpr int kConsumerWarps = 8;
+constexpr int kQueriesPerThread = 2;
+constexpr int kQueriesPerCta = kConsumerWarps * 32 * kQueriesPerThread;   // 512
+constexpr int kStages = 4;
+
+Plan make_plan(const Cloud& c, int64_t q, int split_override);
+
+// Brackets one kernel launch with CUDA events while sdf_profile is enabled.
+class ProfRange {
+  public:
+    ProfRange(int kernel, cudaStream_t st);
+    ~ProfRange();
+    ProfRange(const ProfRange&) = delete;
+    ProfRange& operator=(const ProfRange&) = delete;
+
+  private:
+    cudaStream_t st_;
+    int idx_;
+};
+
+// kernels' host launchers (query.cu)
+sdf_status launch_query(const Cloud& c, const float* d_x, int64_t q, float* d_phi,
+                        const sdf_query_opts& o, cudaStream_t st);
+
+}  // namespace ptsdf

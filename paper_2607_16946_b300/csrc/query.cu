@@ -1,0 +1,378 @@
+// Query kernels: phi(x) for every query against every point (Sec. 4.2,
+// Eqs. BasicFormulaShifted and RelationshipBetweenLambdaAndRadius; torus SDF
+// of Eq. SingleTorusSDF).
+//
+//   k_prepass  per query, over a chunk of points: max_i and min_i of
+//              |x - p_i|^2 (d_max gives lambda_x, d_min the exponent shift).
+//   k_fwd      per query, over a chunk of tiles: W = sum_i w_i,
+//              S = sum_i w_i g_i.  Writes phi = S / W - offset when the
+//              points are not split, else the (W, S) partials.
+//   k_merge    sums the partials of every chunk in chunk order.
+//
+// Geometry of both pair kernels: a CTA holds kQueriesPerCta = 512 queries in
+// registers (8 consumer warps x 32 lanes x 2 queries) and streams the point
+// data through a 4-stage shared-memory ring filled by bulk (TMA) copies from
+// a 9th, producer warp.  All lanes of a warp read the same record (a
+// shared-memory broadcast), so per point every lane does 2 independent pair
+// evaluations.
+//
+// Exponent shift: the ratio S / W does not depend on the shift.  The paper
+// shifts by sigma_x = d_max / 2, which bounds the smallest weight by e^-C but
+// lets near points weigh up to e^C: for C near 87 a few such terms overflow an
+// FP32 sum.  The kernels shift by d_min instead, w_i = exp2(-L (d_i - d_min)),
+// L = lambda_x log2 e, so every weight is at most 1 (the nearest point's is 1),
+// W >= 1 and nothing overflows for any C; weights far below the nearest one
+// underflow to 0 without changing phi at FP32 precision.  All chunks of a
+// split query share the same d_min, so their partial sums add directly.
+//
+// The prepass works in coordinates centred on the cloud's bounding box, so
+// |x - p|^2 = |x'|^2 + |p'|^2 - 2 <x', p'> keeps its relative accuracy for
+// clouds away from the origin.
+#include <cuda_runtime.h>
+
+#include <cmath>
+
+#include "device_common.cuh"
+#include "internal.h"
+
+namespace ptsdf {
+
+namespace {
+
+constexpr int kThreads = (kConsumerWarps + 1) * 32;   // + producer warp
+constexpr float kLog2e = 1.4426950408889634f;
+constexpr uint32_t kTileBytes = kTileRecs * kRecFloats * sizeof(float);
+constexpr uint32_t kPreBytes = kPreTile * sizeof(float4);
+
+struct QueryArgs {
+    const float* x;          // Q x 3
+    int64_t q;
+    float* phi;              // Q (split == 1)
+    float2* part;            // split x Q (W, S) partials (split > 1)
+    float2* d2;              // split x Q prepass partials (max, min of |x - p|^2)
+    float cx, cy, cz;        // cloud bounding-box centre (prepass coordinates)
+    int split;
+    int mode;                // sdf_lambda_mode
+    float C;
+    float lam;               // fixed lambda
+    float offset;
+};
+
+// --------------------------------------------------------------------------
+// Prepass
+// --------------------------------------------------------------------------
+template <int MODE>
+__global__ void __launch_bounds__(kThreads) k_prepass(const float4* __restrict__ pre, int64_t n, int64_t pre_tiles,
+                                                      int64_t tiles_per_chunk, QueryArgs a, int32_t* status) {
+    extern __shared__ __align__(128) char smem[];
+    __shared__ TileRing<kStages> ring;
+    char* buf = smem;
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int chunk = blockIdx.y;
+    const int64_t t0 = (int64_t)chunk * tiles_per_chunk;
+    const int64_t t1 = t0 + tiles_per_chunk < pre_tiles ? t0 + tiles_per_chunk : pre_tiles;
+    const int64_t nt = t1 > t0 ? t1 - t0 : 0;
+    if (threadIdx.x == 0) ring.init(kConsumerWarps);
+    __syncthreads();
+    if (warp == kConsumerWarps) {
+        if (lane == 0) ring.produce(buf, reinterpret_cast<const char*>(pre + t0 * kPreTile), nt, kPreBytes, status);
+        return;
+    }
+    float xs[kQueriesPerThread][3], hi[kQueriesPerThread], lo[kQueriesPerThread], xx[kQueriesPerThread];
+    int64_t qi[kQueriesPerThread];
+#pragma unroll
+    for (int k = 0; k < kQueriesPerThread; ++k) {
+        qi[k] = (int64_t)blockIdx.x * kQueriesPerCta + k * (kConsumerWarps * 32) + threadIdx.x;
+        const int64_t qq = qi[k] < a.q ? qi[k] : a.q - 1;
+        xs[k][0] = a.x[3 * qq] - a.cx;
+        xs[k][1] = a.x[3 * qq + 1] - a.cy;
+        xs[k][2] = a.x[3 * qq + 2] - a.cz;
+        xx[k] = xs[k][0] * xs[k][0] + xs[k][1] * xs[k][1] + xs[k][2] * xs[k][2];
+        hi[k] = -INFINITY;
+        lo[k] = INFINITY;
+    }
+    for (int64_t t = 0; t < nt; ++t) {
+        if (!ring.wait_full(t, status)) return;
+        const float4* tile = reinterpret_cast<const float4*>(buf + (size_t)(t % kStages) * kPreBytes);
+        const int64_t first = (t0 + t) * kPreTile;
+        const int cnt = (int)(n - first < kPreTile ? n - first : kPreTile);
+        if (MODE == SDF_LAMBDA_GLOBAL) {
+            // |x'-p'|^2 - |x'|^2 = |p'|^2 - 2 <x', p'>: three FMAs per pair.  Its
+            // cancellation near d = 0 only perturbs the shift d_min (harmless
+            // for lambda_x = 2 C / d_max); d_max keeps full relative accuracy.
+#pragma unroll 4
+            for (int j = 0; j < cnt; ++j) {
+                const float4 r = tile[j];
+#pragma unroll
+                for (int k = 0; k < kQueriesPerThread; ++k) {
+                    const float v = fmaf(xs[k][0], r.x, fmaf(xs[k][1], r.y, fmaf(xs[k][2], r.z, r.w)));
+                    hi[k] = fmaxf(hi[k], v);
+                    lo[k] = fminf(lo[k], v);
+                }
+            }
+        } else {
+            // FIXED lambda may be large, so the shift d_min is computed from
+            // the difference vector (no cancellation)
+#pragma unroll 4
+            for (int j = 0; j < cnt; ++j) {
+                const float4 r = tile[j];
+#pragma unroll
+                for (int k = 0; k < kQueriesPerThread; ++k) {
+                    const float dx = fmaf(0.5f, r.x, xs[k][0]), dy = fmaf(0.5f, r.y, xs[k][1]),
+                                dz = fmaf(0.5f, r.z, xs[k][2]);
+                    lo[k] = fminf(lo[k], fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+                }
+            }
+        }
+        ring.release(t, lane);
+    }
+#pragma unroll
+    for (int k = 0; k < kQueriesPerThread; ++k) {
+        if (qi[k] < a.q) {
+            const float2 v = MODE == SDF_LAMBDA_GLOBAL ? make_float2(hi[k] + xx[k], lo[k] + xx[k])
+                                                       : make_float2(-INFINITY, lo[k]);
+            a.d2[(size_t)chunk * a.q + qi[k]] = v;
+        }
+    }
+}
+
+// --------------------------------------------------------------------------
+// Pair terms
+// --------------------------------------------------------------------------
+// Direct form: v = x - c, h = <v, u>, rho = |v - h u| (the distance to the
+// axis, computed from the perpendicular component so it stays accurate near
+// the axis), g = sT (||(rho - R, h)|| - r).
+__device__ __forceinline__ float g_direct(float x, float y, float z, const float4& r1, const float4& r2, float sT) {
+    const float vx = x - r1.x, vy = y - r1.y, vz = z - r1.z;
+    const float h = fmaf(vx, r2.x, fmaf(vy, r2.y, vz * r2.z));
+    const float wx = fmaf(-h, r2.x, vx), wy = fmaf(-h, r2.y, vy), wz = fmaf(-h, r2.z, vz);
+    const float rho = sqrt_mufu(fmaf(wx, wx, fmaf(wy, wy, wz * wz)));
+    const float e = rho - r1.w;
+    const float D = sqrt_mufu(fmaf(e, e, h * h));
+    return fmaf(sT, D, r2.w);
+}
+
+// Curvature form around q = Q*(0,0), exact rewrite of the same torus SDF:
+// with y = x - q, h = <y, u>, t^2 = |y|^2 - h^2, k = |kappa_min|,
+//   m  = k t^2 + 2 zeta <y, n*>,    a' = m / (1 + sqrt(1 + k m))   (= rho - 1/k)
+//   N' = -kappa_max (a'^2 + h^2) + 2 zeta a'
+//   g  = N' / (1 + sqrt(1 + (-kappa_max) N'))
+// which has no 1/k or 1/|kappa_max| and so no cancellation of large radii.
+__device__ __forceinline__ float g_kappa(float x, float y, float z, const float4& r0, const float4& r1,
+                                         const float4& r2, const float4& r3) {
+    const float yx = x - r1.x, yy = y - r1.y, yz = z - r1.z;
+    const float h = fmaf(yx, r2.x, fmaf(yy, r2.y, yz * r2.z));
+    const float hh = h * h;
+    const float t2 = fmaf(yx, yx, fmaf(yy, yy, yz * yz)) - hh;
+    const float m = fmaf(r1.w, t2, fmaf(yx, r3.x, fmaf(yy, r3.y, yz * r3.z)));
+    const float s1 = sqrt_mufu(fmaxf(fmaf(r1.w, m, 1.f), 0.f));
+    const float ap = m * rcp_mufu(1.f + s1);
+    const float Np = fmaf(r2.w, fmaf(ap, ap, hh), r0.w * ap);
+    const float s2 = sqrt_mufu(fmaxf(fmaf(r2.w, Np, 1.f), 0.f));
+    return Np * rcp_mufu(1.f + s2);
+}
+
+struct QState {
+    float x, y, z;     // query
+    float L, A0;       // exponent = A0 - L d
+    float W, S;        // totals
+    float w, s;        // tile partials
+};
+
+template <bool KAPPA>
+__device__ __forceinline__ void pair_tile(const float4* __restrict__ tile, int cnt, QState (&qs)[kQueriesPerThread]) {
+#pragma unroll 2
+    for (int j = 0; j < cnt; ++j) {
+        const float4 r0 = tile[4 * j], r1 = tile[4 * j + 1], r2 = tile[4 * j + 2];
+        float4 r3;
+        if (KAPPA) r3 = tile[4 * j + 3];
+#pragma unroll
+        for (int k = 0; k < kQueriesPerThread; ++k) {
+            const float dx = qs[k].x - r0.x, dy = qs[k].y - r0.y, dz = qs[k].z - r0.z;
+            const float d = sqrt_mufu(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+            const float g = KAPPA ? g_kappa(qs[k].x, qs[k].y, qs[k].z, r0, r1, r2, r3)
+                                  : g_direct(qs[k].x, qs[k].y, qs[k].z, r1, r2, r0.w);
+            const float w = ex2_mufu(fmaf(-qs[k].L, d, qs[k].A0));
+            qs[k].w += w;
+            qs[k].s = fmaf(w, g, qs[k].s);
+        }
+    }
+}
+
+// --------------------------------------------------------------------------
+// Forward pass
+// --------------------------------------------------------------------------
+__global__ void __launch_bounds__(kThreads) k_fwd(const float4* __restrict__ rec, int64_t n_direct, int64_t n_kappa,
+                                                  int64_t tiles_direct, int64_t tiles_total, int64_t tiles_per_chunk,
+                                                  QueryArgs a, int32_t* status) {
+    extern __shared__ __align__(128) char smem[];
+    __shared__ TileRing<kStages> ring;
+    char* buf = smem;
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int chunk = blockIdx.y;
+    const int64_t t0 = (int64_t)chunk * tiles_per_chunk;
+    const int64_t t1 = t0 + tiles_per_chunk < tiles_total ? t0 + tiles_per_chunk : tiles_total;
+    const int64_t nt = t1 > t0 ? t1 - t0 : 0;
+    if (threadIdx.x == 0) ring.init(kConsumerWarps);
+    __syncthreads();
+    if (warp == kConsumerWarps) {
+        if (lane == 0)
+            ring.produce(buf, reinterpret_cast<const char*>(rec + t0 * kTileRecs * 4), nt, kTileBytes, status);
+        return;
+    }
+    QState qs[kQueriesPerThread];
+    int64_t qi[kQueriesPerThread];
+#pragma unroll
+    for (int k = 0; k < kQueriesPerThread; ++k) {
+        qi[k] = (int64_t)blockIdx.x * kQueriesPerCta + k * (kConsumerWarps * 32) + threadIdx.x;
+        const int64_t qq = qi[k] < a.q ? qi[k] : a.q - 1;
+        qs[k].x = a.x[3 * qq];
+        qs[k].y = a.x[3 * qq + 1];
+        qs[k].z = a.x[3 * qq + 2];
+        float2 d2 = a.d2[qq];
+        for (int c = 1; c < a.split; ++c) {
+            const float2 v = a.d2[(size_t)c * a.q + qq];
+            d2.x = fmaxf(d2.x, v.x);
+            d2.y = fminf(d2.y, v.y);
+        }
+        const float dmin = sqrtf(fmaxf(d2.y, 0.f));
+        float lam = a.lam;
+        if (a.mode == SDF_LAMBDA_GLOBAL) {
+            // lambda_x = C / sigma_x = 2 C / d_max (Eq. RelationshipBetweenLambdaAndRadius);
+            // d_max = 0 (one point, at the query) takes lambda = 0
+            const float dmax = sqrtf(fmaxf(d2.x, 0.f));
+            lam = dmax > 0.f ? 2.f * a.C / dmax : 0.f;
+        }
+        qs[k].L = lam * kLog2e;
+        qs[k].A0 = qs[k].L * dmin;   // exponent -L (d - d_min)
+        qs[k].W = qs[k].S = 0.f;
+    }
+    for (int64_t t = 0; t < nt; ++t) {
+        if (!ring.wait_full(t, status)) return;
+        const float4* tile = reinterpret_cast<const float4*>(buf + (size_t)(t % kStages) * kTileBytes);
+        const int64_t gt = t0 + t;
+        const bool kappa = gt >= tiles_direct;
+        const int64_t first = (kappa ? gt - tiles_direct : gt) * kTileRecs;
+        const int64_t seg = kappa ? n_kappa : n_direct;
+        const int cnt = (int)(seg - first < kTileRecs ? seg - first : kTileRecs);
+#pragma unroll
+        for (int k = 0; k < kQueriesPerThread; ++k) qs[k].w = qs[k].s = 0.f;
+        if (kappa)
+            pair_tile<true>(tile, cnt, qs);
+        else
+            pair_tile<false>(tile, cnt, qs);
+        // blocked summation: tile partials are added to the totals once per
+        // tile, which keeps the FP32 rounding of long sums small
+#pragma unroll
+        for (int k = 0; k < kQueriesPerThread; ++k) {
+            qs[k].W += qs[k].w;
+            qs[k].S += qs[k].s;
+        }
+        ring.release(t, lane);
+    }
+#pragma unroll
+    for (int k = 0; k < kQueriesPerThread; ++k) {
+        if (qi[k] >= a.q) continue;
+        if (a.split == 1)
+            a.phi[qi[k]] = __fdiv_rn(qs[k].S, qs[k].W) - a.offset;
+        else
+            a.part[(size_t)chunk * a.q + qi[k]] = make_float2(qs[k].W, qs[k].S);
+    }
+}
+
+__global__ void k_merge(QueryArgs a) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.q) return;
+    float W = 0.f, S = 0.f;
+    for (int c = 0; c < a.split; ++c) {
+        const float2 v = a.part[(size_t)c * a.q + i];
+        W += v.x;
+        S += v.y;
+    }
+    a.phi[i] = __fdiv_rn(S, W) - a.offset;
+}
+
+}  // namespace
+
+Plan make_plan(const Cloud& c, int64_t q, int split_override) {
+    Plan p;
+    p.q = q;
+    p.qblocks = (q + kQueriesPerCta - 1) / kQueriesPerCta;
+    const int64_t tiles = c.tiles_direct + c.tiles_kappa;
+    int64_t split = 1;
+    if (split_override > 0) {
+        split = split_override;
+    } else {
+        // aim for at least two waves of 3 resident CTAs per SM
+        const int64_t target = 2LL * 3 * c.num_sms;
+        if (p.qblocks < target) split = (target + p.qblocks - 1) / p.qblocks;
+        const int64_t max_split = tiles / 4 > 0 ? tiles / 4 : 1;   // >= 4 tiles per chunk
+        if (split > max_split) split = max_split;
+        if (split > 64) split = 64;
+    }
+    if (split > tiles) split = tiles;
+    if (split < 1) split = 1;
+    p.tiles_per_chunk = (tiles + split - 1) / split;
+    split = (tiles + p.tiles_per_chunk - 1) / p.tiles_per_chunk;
+    p.split = (int)split;
+    p.pre_tiles_per_chunk = (c.pre_tiles + split - 1) / split;
+    return p;
+}
+
+sdf_status launch_query(const Cloud& c, const float* d_x, int64_t q, float* d_phi, const sdf_query_opts& o,
+                        cudaStream_t st) {
+    const Plan p = make_plan(c, q, o.split_n);
+    QueryArgs a;
+    a.x = d_x;
+    a.q = q;
+    a.phi = d_phi;
+    a.split = p.split;
+    a.mode = o.lambda_mode;
+    a.C = o.C;
+    a.lam = o.fixed_lambda;
+    a.offset = o.offset;
+    a.part = nullptr;
+    a.d2 = nullptr;
+    a.cx = 0.5f * (c.aabb[0] + c.aabb[3]);
+    a.cy = 0.5f * (c.aabb[1] + c.aabb[4]);
+    a.cz = 0.5f * (c.aabb[2] + c.aabb[5]);
+    cudaError_t e = cudaMallocAsync(&a.d2, (size_t)p.split * q * sizeof(float2), st);
+    if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? set_error(SDF_ENOMEM, "sdf_query: scratch")
+                                                                : cuda_error(e, "sdf_query: scratch");
+    if (p.split > 1) {
+        e = cudaMallocAsync(&a.part, (size_t)p.split * q * sizeof(float2), st);
+        if (e != cudaSuccess) {
+            cudaFreeAsync(a.d2, st);
+            return e == cudaErrorMemoryAllocation ? set_error(SDF_ENOMEM, "sdf_query: scratch")
+                                                  : cuda_error(e, "sdf_query: scratch");
+        }
+    }
+    const dim3 grid((unsigned)p.qblocks, (unsigned)p.split);
+    {
+        ProfRange pr(SDF_K_PREPASS, st);
+        if (o.lambda_mode == SDF_LAMBDA_GLOBAL)
+            k_prepass<SDF_LAMBDA_GLOBAL><<<grid, kThreads, kStages * kPreBytes, st>>>(
+                c.pre, c.n, c.pre_tiles, p.pre_tiles_per_chunk, a, c.status);
+        else
+            k_prepass<SDF_LAMBDA_FIXED><<<grid, kThreads, kStages * kPreBytes, st>>>(
+                c.pre, c.n, c.pre_tiles, p.pre_tiles_per_chunk, a, c.status);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) {
+        ProfRange pr(SDF_K_FWD, st);
+        k_fwd<<<grid, kThreads, kStages * kTileBytes, st>>>(c.rec, c.n_direct, c.n_kappa, c.tiles_direct,
+                                                           c.tiles_direct + c.tiles_kappa, p.tiles_per_chunk, a,
+                                                           c.status);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess && p.split > 1) {
+        ProfRange pr(SDF_K_MERGE, st);
+        k_merge<<<(unsigned)((q + 255) / 256), 256, 0, st>>>(a);
+        e = cudaGetLastError();
+    }
+    cudaFreeAsync(a.d2, st);
+    if (a.part) cudaFreeAsync(a.part, st);
+    return e == cudaSuccess ? SDF_OK : cuda_error(e, "sdf_query: launch");
+}
+
+}  // namespace ptsdf

@@ -1,0 +1,60 @@
+"""A reduced case of the dense-grid workload for profiler captures.
+
+    python -m paper_2607_16946_b300.profile_case [--queries Q] [--launches K] [--warmup W]
+
+Builds the dense-grid cloud (ring torus, N = 100,000) and evaluates an evenly
+strided subset of Q nodes of the 256^3 grid with sdf_query, W times untimed
+and then K times, printing the device time of each call.  Used to give ncu a
+short, self-terminating run of the same kernels the benchmark times.
+"""
+from __future__ import annotations
+
+import argparse
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--queries", type=int, default=1 << 20)
+    ap.add_argument("--launches", type=int, default=1)
+    ap.add_argument("--warmup", type=int, default=1)
+    ap.add_argument("--points", type=int, default=100_000)
+    args = ap.parse_args()
+
+    import torch
+
+    import paper_2607_16946_b300 as ptsdf
+    import synth
+
+    p, n, a = synth.ring_torus(args.points, 1002, R=1.0, r=0.35, noise=0.005, jitter_deg=2.0)
+    cloud = ptsdf.Cloud(p, n, a)
+    res = 256
+    g = torch.linspace(-1.6, 1.6, res, device="cuda", dtype=torch.float64)
+    zz, yy, xx = torch.meshgrid(g, g, g, indexing="ij")
+    x = torch.stack([xx.reshape(-1), yy.reshape(-1), zz.reshape(-1)], 1).to(torch.float32)
+    stride = max(1, x.shape[0] // args.queries)
+    x = x[::stride][: args.queries].contiguous()
+    phi = torch.empty(x.shape[0], device="cuda")
+    for _ in range(args.warmup):
+        cloud.query(x, out=phi)
+    torch.cuda.synchronize()
+    for i in range(args.launches):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        cloud.query(x, out=phi)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        print(f"call {i}: Q={x.shape[0]} N={args.points} {ms:.3f} ms "
+              f"{x.shape[0] * args.points / ms / 1e6:.1f} Gpairs/s", flush=True)
+    assert cloud.device_status() == 0
+    assert bool(torch.isfinite(phi).all())
+
+
+if __name__ == "__main__":
+    main()

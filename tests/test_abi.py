@@ -1,0 +1,66 @@
+"""The C ABI without a GPU: the library loads, exports every entry point that
+include/ptsdf.h declares, the Python binding names the same calls, and the
+host-side argument checks reject bad input before touching the device."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "ptsdf.h")
+
+
+@pytest.fixture(scope="module")
+def abi():
+    from paper_2607_16946_b300 import build
+    build.build()
+    from paper_2607_16946_b300 import _abi
+    return _abi
+
+
+def declared_functions():
+    txt = open(HEADER).read()
+    return sorted(set(re.findall(r"PTSDF_API\s+[\w\s\*]+?\b(sdf_\w+)\s*\(", txt)))
+
+
+def test_header_declares_calls():
+    names = declared_functions()
+    for required in ("sdf_build", "sdf_query", "sdf_query_host", "sdf_destroy", "sdf_last_error"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(abi):
+    L = ctypes.CDLL(abi.LIB_PATH)
+    for name in declared_functions():
+        assert hasattr(L, name), name
+
+
+def test_binding_covers_header(abi):
+    assert set(declared_functions()) == set(abi.SIGNATURES)
+
+
+def test_host_side_validation(abi):
+    L = abi.lib()
+    o = abi.sdf_query_opts()
+    assert L.sdf_opts_default(ctypes.byref(o)) == abi.SDF_OK
+    assert o.C == 64.0 and o.lambda_mode == abi.SDF_LAMBDA_GLOBAL and o.split_n == 0
+    assert L.sdf_opts_default(None) == abi.SDF_EINVAL
+    h = ctypes.c_void_p()
+    assert L.sdf_build(None, None, None, 0, None, ctypes.byref(h)) == abi.SDF_EINVAL
+    assert b"n must be" in L.sdf_last_error()
+    assert L.sdf_build(None, None, None, 10, None, ctypes.byref(h)) == abi.SDF_EINVAL
+    assert L.sdf_build(None, None, None, 10, None, None) == abi.SDF_EINVAL
+    assert L.sdf_query(None, None, 0, None, None, None) == abi.SDF_EINVAL
+    assert L.sdf_query_host(None, None, 5, None, None, None) == abi.SDF_EINVAL
+    assert L.sdf_destroy(None) == abi.SDF_OK
+    code = ctypes.c_int32()
+    assert L.sdf_device_status(None, None, ctypes.byref(code)) == abi.SDF_EINVAL
+    assert L.sdf_version().startswith(b"ptsdf")
+
+
+def test_missing_library_fails_loudly(abi, monkeypatch, tmp_path):
+    monkeypatch.setattr(abi, "LIB_PATH", str(tmp_path / "nope.so"))
+    monkeypatch.setattr(abi, "_lib", None)
+    with pytest.raises(FileNotFoundError):
+        abi.lib()
