@@ -144,6 +144,68 @@ enum { SDF_DEV_WAIT_TIMEOUT = 1, SDF_DEV_BAD_INPUT = 2 };
 PTSDF_API sdf_status sdf_device_status(sdf_cloud cloud, void* stream, int32_t* code);
 
 /* ---------------------------------------------------------------------------
+ * sdf_query_grad -- phi and d phi / d x (App. D, "Gradient expressions",
+ *   plus the x-dependence of lambda_x through the farthest point).
+ *
+ *   d_phi      Q float (phi - offset).
+ *   d_grad     Q x 3 float, d phi / d x.
+ *   d_saved    Q x 8 float or NULL: per-query statistics for
+ *              sdf_backward_params {x, y, z, L, A0, W, phi, 0} where the
+ *              weights are w_i = 2^(A0 - L |x - p_i|) (L = lambda_x log2 e,
+ *              A0 = L d_min), W = sum_i w_i and phi excludes the offset.
+ *   Where two points tie for the farthest, lambda_x has a kink; the
+ *   gradient then uses one of them.
+ *   Errors as sdf_query.
+ * ------------------------------------------------------------------------- */
+PTSDF_API sdf_status sdf_query_grad(sdf_cloud cloud, const float* d_x, int64_t q, float* d_phi,
+                          float* d_grad, float* d_saved, const sdf_query_opts* opts, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * sdf_backward_params -- d L / d(a00..a20) for L = sum_q G_q phi(x_q): the
+ *   weights do not depend on the coefficients, so
+ *   dL/da_i = sum_q G_q (w_qi / W_q) d g_i(x_q) / d a_i, chained through the
+ *   fit of Sec. 4.1.
+ *
+ *   d_saved        Q x 8 float written by sdf_query_grad for the same d_x.
+ *   d_grad_phi     Q float, G_q.
+ *   d_grad_params  N x 6 float in the ORIGINAL point order; overwritten
+ *                  (zeros when q == 0).
+ *   opts           must equal the options of the sdf_query_grad call.
+ *   The chain through the fit runs in double precision.  At a zero
+ *   curvature the derivative is that of the curvature form's smooth
+ *   continuation through zero.
+ *   Errors as sdf_query.
+ * ------------------------------------------------------------------------- */
+PTSDF_API sdf_status sdf_backward_params(sdf_cloud cloud, const float* d_x, int64_t q, const float* d_saved,
+                               const float* d_grad_phi, float* d_grad_params,
+                               const sdf_query_opts* opts, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * sdf_trace -- sphere tracing of the level set phi = offset (Sec. 6, "Direct
+ *   visualization of point cloud surfaces").  From t = 0 each step evaluates
+ *   f = phi(o + t d) - offset; a ray hits when f < eps (t_hit = t), else
+ *   t += f; it misses when t > t_max or after max_steps evaluations
+ *   (t_hit = -1).  Each step is one query batch over the rays still live.
+ *
+ *   d_origins, d_dirs  R x 3 float (dirs unit length).
+ *   d_t_hit            R float; d_steps R int32 (evaluations used).
+ *   d_normals          R x 3 float or NULL: unit grad phi at hits (0 at misses).
+ *   The call synchronises `stream` once per step (the live-ray count sizes
+ *   the next batch) and returns when the results are written.
+ *   Errors as sdf_query; SDF_EINVAL for nrays < 0, max_steps < 1, eps <= 0 or
+ *   t_max <= 0.
+ * ------------------------------------------------------------------------- */
+PTSDF_API sdf_status sdf_trace(sdf_cloud cloud, const float* d_origins, const float* d_dirs, int64_t nrays,
+                     int32_t max_steps, float eps, float t_max, float* d_t_hit, int32_t* d_steps,
+                     float* d_normals, const sdf_query_opts* opts, void* stream);
+
+/* Booleans of two phi arrays (Sec. 6, "Offset surfaces and Booleans"):
+ * union min(a, b), intersection max(a, b), difference max(a, -b). */
+typedef enum { SDF_UNION = 0, SDF_INTERSECT = 1, SDF_DIFFERENCE = 2 } sdf_bool_op;
+PTSDF_API sdf_status sdf_combine(int32_t op, const float* d_a, const float* d_b, int64_t q, float* d_out,
+                       void* stream);
+
+/* ---------------------------------------------------------------------------
  * Kernel timing (a tracing aid, not part of the method).  While enabled,
  * every kernel the library launches is bracketed by two CUDA events recorded
  * on the stream it is launched on.  sdf_profile_read waits for the recorded
@@ -151,7 +213,8 @@ PTSDF_API sdf_status sdf_device_status(sdf_cloud cloud, void* stream, int32_t* c
  * their total device time in milliseconds since the last enable.  Enabling
  * clears earlier records; disabling stops recording and keeps them.
  * ------------------------------------------------------------------------- */
-enum { SDF_K_PREPASS = 0, SDF_K_FWD = 1, SDF_K_MERGE = 2, SDF_K_BUILD = 3, SDF_K_COUNT_ = 4 };
+enum { SDF_K_PREPASS = 0, SDF_K_FWD = 1, SDF_K_MERGE = 2, SDF_K_BUILD = 3, SDF_K_FWD_GRAD = 4, SDF_K_BWD = 5,
+       SDF_K_COUNT_ = 6 };
 PTSDF_API sdf_status sdf_profile_enable(int32_t on);
 PTSDF_API sdf_status sdf_profile_read(int32_t kernel, int64_t* launches, double* total_ms);
 /* Name of a kernel family (NULL for an id out of range). */

@@ -8,6 +8,7 @@ supplies device memory and the current CUDA stream.
     cloud = Cloud(points, normals, params)        # N x 3, N x 3, N x 6
     phi = cloud.query(x)                           # x: Q x 3 (CUDA tensor) -> Q
     phi = cloud.query_host(x_numpy)                # host arrays in and out
+    phi = sdf(x, cloud, params)                    # differentiable in x and params
 """
 from __future__ import annotations
 
@@ -18,7 +19,7 @@ import numpy as np
 from . import _abi
 from ._abi import (SDF_LAMBDA_FIXED, SDF_LAMBDA_GLOBAL, SdfError, check, lib, make_opts)
 
-__all__ = ["Cloud", "SdfError", "SDF_LAMBDA_GLOBAL", "SDF_LAMBDA_FIXED", "make_opts", "lib"]
+__all__ = ["Cloud", "SdfError", "SDF_LAMBDA_GLOBAL", "SDF_LAMBDA_FIXED", "make_opts", "lib", "sdf"]
 
 
 def _torch():
@@ -91,6 +92,34 @@ class Cloud:
                               ctypes.byref(o), _stream_ptr(stream)), "sdf_query")
         return out
 
+    def query_grad(self, x, stream=None, saved=True, **opts):
+        """(phi, d phi / d x, saved statistics or None) at the rows of x."""
+        torch = _torch()
+        x = _dev_f32(x, 3)
+        q = x.shape[0]
+        phi = torch.empty(q, device=x.device, dtype=torch.float32)
+        grad = torch.empty((q, 3), device=x.device, dtype=torch.float32)
+        sv = torch.empty((q, 8), device=x.device, dtype=torch.float32) if saved else None
+        o = make_opts(**opts)
+        check(lib().sdf_query_grad(self._h, ctypes.c_void_p(x.data_ptr()), q, ctypes.c_void_p(phi.data_ptr()),
+                                   ctypes.c_void_p(grad.data_ptr()),
+                                   ctypes.c_void_p(sv.data_ptr()) if saved else None,
+                                   ctypes.byref(o), _stream_ptr(stream)), "sdf_query_grad")
+        return phi, grad, sv
+
+    def backward_params(self, x, saved, grad_phi, stream=None, **opts):
+        """d(sum_q grad_phi[q] phi(x_q)) / d params, N x 6 in the input point order."""
+        torch = _torch()
+        x = _dev_f32(x, 3)
+        gphi = _dev_f32(grad_phi).reshape(-1)
+        out = torch.empty((self.n, 6), device=x.device, dtype=torch.float32)
+        o = make_opts(**opts)
+        check(lib().sdf_backward_params(self._h, ctypes.c_void_p(x.data_ptr()), x.shape[0],
+                                        ctypes.c_void_p(saved.data_ptr()), ctypes.c_void_p(gphi.data_ptr()),
+                                        ctypes.c_void_p(out.data_ptr()), ctypes.byref(o), _stream_ptr(stream)),
+              "sdf_backward_params")
+        return out
+
     def query_host(self, x, out=None, stream=None, **opts):
         """phi with host (numpy) buffers; copies happen inside the library."""
         x = np.ascontiguousarray(x, dtype=np.float32).reshape(-1, 3)
@@ -109,3 +138,47 @@ class Cloud:
         if st not in (_abi.SDF_OK, _abi.SDF_EDEVICE):
             check(st, "sdf_device_status")
         return code.value
+
+
+def _autograd_function():
+    torch = _torch()
+
+    class SDFQuery(torch.autograd.Function):
+        """phi(x) with hand-written backward kernels: d phi / d x from
+        sdf_query_grad (computed in the forward, recomputing no pair terms
+        later) and d phi / d params from sdf_backward_params."""
+
+        @staticmethod
+        def forward(ctx, x, params, cloud, opts):
+            phi, grad, saved = cloud.query_grad(x.detach(), **opts)
+            ctx.cloud, ctx.opts = cloud, opts
+            ctx.save_for_backward(x.detach(), grad, saved)
+            return phi
+
+        @staticmethod
+        def backward(ctx, gphi):
+            x, grad, saved = ctx.saved_tensors
+            gphi = gphi.contiguous().to(torch.float32)
+            gx = gparams = None
+            if ctx.needs_input_grad[0]:
+                gx = (gphi[:, None] * grad).to(x.dtype)
+            if ctx.needs_input_grad[1]:
+                gparams = ctx.cloud.backward_params(x, saved, gphi, **ctx.opts)
+            return gx, gparams, None, None
+
+    return SDFQuery
+
+
+_SDFQuery = None
+
+
+def sdf(x, cloud: Cloud, params=None, **opts):
+    """Differentiable phi(x).  `params` is the N x 6 coefficient tensor the
+    cloud was built from (pass it to receive d phi / d params)."""
+    global _SDFQuery
+    torch = _torch()
+    if _SDFQuery is None:
+        _SDFQuery = _autograd_function()
+    if params is None:
+        params = torch.zeros(0, device=x.device)
+    return _SDFQuery.apply(x, params, cloud, opts)

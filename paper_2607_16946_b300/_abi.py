@@ -16,8 +16,9 @@ SDF_OK, SDF_EINVAL, SDF_ENOMEM, SDF_ECUDA, SDF_EBUSY, SDF_ETIMEOUT, SDF_EDEVICE 
 SDF_F32, SDF_F16X2, SDF_BF16X2 = 0, 1, 2
 SDF_LAMBDA_GLOBAL, SDF_LAMBDA_FIXED = 0, 1
 SDF_DEV_WAIT_TIMEOUT, SDF_DEV_BAD_INPUT = 1, 2
-SDF_K_PREPASS, SDF_K_FWD, SDF_K_MERGE, SDF_K_BUILD = 0, 1, 2, 3
-KERNEL_IDS = {"prepass": 0, "fwd": 1, "merge": 2, "build": 3}
+SDF_K_PREPASS, SDF_K_FWD, SDF_K_MERGE, SDF_K_BUILD, SDF_K_FWD_GRAD, SDF_K_BWD = 0, 1, 2, 3, 4, 5
+SDF_UNION, SDF_INTERSECT, SDF_DIFFERENCE = 0, 1, 2
+KERNEL_IDS = {"prepass": 0, "fwd": 1, "merge": 2, "build": 3, "fwd_grad": 4, "bwd_params": 5}
 
 STATUS_NAMES = {0: "SDF_OK", 1: "SDF_EINVAL", 2: "SDF_ENOMEM", 3: "SDF_ECUDA", 4: "SDF_EBUSY",
                 5: "SDF_ETIMEOUT", 6: "SDF_EDEVICE"}
@@ -44,6 +45,10 @@ SIGNATURES = {
                                       ctypes.POINTER(_I64)]),
     "sdf_query": (ctypes.c_int, [_P, _P, _I64, _P, ctypes.POINTER(sdf_query_opts), _P]),
     "sdf_query_host": (ctypes.c_int, [_P, _P, _I64, _P, ctypes.POINTER(sdf_query_opts), _P]),
+    "sdf_query_grad": (ctypes.c_int, [_P, _P, _I64, _P, _P, _P, ctypes.POINTER(sdf_query_opts), _P]),
+    "sdf_backward_params": (ctypes.c_int, [_P, _P, _I64, _P, _P, _P, ctypes.POINTER(sdf_query_opts), _P]),
+    "sdf_trace": (ctypes.c_int, [_P, _P, _P, _I64, _I32, _F, _F, _P, _P, _P, ctypes.POINTER(sdf_query_opts), _P]),
+    "sdf_combine": (ctypes.c_int, [_I32, _P, _P, _I64, _P, _P]),
     "sdf_device_status": (ctypes.c_int, [_P, _P, ctypes.POINTER(_I32)]),
     "sdf_profile_enable": (ctypes.c_int, [_I32]),
     "sdf_profile_read": (ctypes.c_int, [_I32, ctypes.POINTER(_I64), ctypes.POINTER(ctypes.c_double)]),

@@ -36,6 +36,15 @@ sdf_status check_opts(const sdf_query_opts& o, const char* fn) {
     return SDF_OK;
 }
 
+// Booleans of two phi arrays (Sec. 6): union min, intersection max, difference max(a, -b)
+__global__ void k_combine(int op, const float* __restrict__ a, const float* __restrict__ b, int64_t q,
+                          float* __restrict__ out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= q) return;
+    const float x = a[i], y = b[i];
+    out[i] = op == SDF_UNION ? fminf(x, y) : op == SDF_INTERSECT ? fmaxf(x, y) : fmaxf(x, -y);
+}
+
 sdf_query_opts resolve_opts(const sdf_query_opts* o) {
     sdf_query_opts r;
     sdf_opts_default(&r);
@@ -68,6 +77,66 @@ extern "C" sdf_status sdf_query(sdf_cloud cloud, const float* d_x, int64_t q, fl
     if (!d_x || !d_phi) return set_error(SDF_EINVAL, "sdf_query: NULL buffer");
     return launch_query(*reinterpret_cast<const Cloud*>(cloud), d_x, q, d_phi, o,
                         static_cast<cudaStream_t>(stream));
+}
+
+extern "C" sdf_status sdf_query_grad(sdf_cloud cloud, const float* d_x, int64_t q, float* d_phi, float* d_grad,
+                                     float* d_saved, const sdf_query_opts* opts, void* stream) {
+    if (!cloud) return set_error(SDF_EINVAL, "sdf_query_grad: cloud is NULL");
+    if (q < 0) return set_error(SDF_EINVAL, "sdf_query_grad: q < 0");
+    const sdf_query_opts o = resolve_opts(opts);
+    const sdf_status s = check_opts(o, "sdf_query_grad");
+    if (s != SDF_OK) return s;
+    if (q == 0) return SDF_OK;
+    if (!d_x || !d_phi || !d_grad) return set_error(SDF_EINVAL, "sdf_query_grad: NULL buffer");
+    return launch_query_grad(*reinterpret_cast<const Cloud*>(cloud), d_x, q, d_phi, d_grad, d_saved, o,
+                             static_cast<cudaStream_t>(stream));
+}
+
+extern "C" sdf_status sdf_backward_params(sdf_cloud cloud, const float* d_x, int64_t q, const float* d_saved,
+                                          const float* d_grad_phi, float* d_grad_params,
+                                          const sdf_query_opts* opts, void* stream) {
+    if (!cloud) return set_error(SDF_EINVAL, "sdf_backward_params: cloud is NULL");
+    if (q < 0) return set_error(SDF_EINVAL, "sdf_backward_params: q < 0");
+    if (!d_grad_params) return set_error(SDF_EINVAL, "sdf_backward_params: NULL output");
+    const sdf_query_opts o = resolve_opts(opts);
+    const sdf_status s = check_opts(o, "sdf_backward_params");
+    if (s != SDF_OK) return s;
+    const Cloud& c = *reinterpret_cast<const Cloud*>(cloud);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (q == 0) {
+        const cudaError_t e = cudaMemsetAsync(d_grad_params, 0, (size_t)c.n * 6 * sizeof(float), st);
+        return e == cudaSuccess ? SDF_OK : cuda_error(e, "sdf_backward_params: clear");
+    }
+    if (!d_x || !d_saved || !d_grad_phi) return set_error(SDF_EINVAL, "sdf_backward_params: NULL buffer");
+    return launch_backward_params(c, q, d_saved, d_grad_phi, d_grad_params, o, st);
+}
+
+extern "C" sdf_status sdf_trace(sdf_cloud cloud, const float* d_origins, const float* d_dirs, int64_t nrays,
+                                int32_t max_steps, float eps, float t_max, float* d_t_hit, int32_t* d_steps,
+                                float* d_normals, const sdf_query_opts* opts, void* stream) {
+    if (!cloud) return set_error(SDF_EINVAL, "sdf_trace: cloud is NULL");
+    if (nrays < 0 || nrays > 0x7fffffffLL) return set_error(SDF_EINVAL, "sdf_trace: nrays out of range");
+    if (max_steps < 1 || !(eps > 0.f) || !(t_max > 0.f) || !std::isfinite(t_max))
+        return set_error(SDF_EINVAL, "sdf_trace: need max_steps >= 1, eps > 0, finite t_max > 0");
+    const sdf_query_opts o = resolve_opts(opts);
+    const sdf_status s = check_opts(o, "sdf_trace");
+    if (s != SDF_OK) return s;
+    if (nrays == 0) return SDF_OK;
+    if (!d_origins || !d_dirs || !d_t_hit || !d_steps) return set_error(SDF_EINVAL, "sdf_trace: NULL buffer");
+    return launch_trace(*reinterpret_cast<const Cloud*>(cloud), d_origins, d_dirs, nrays, max_steps, eps, t_max,
+                        d_t_hit, d_steps, d_normals, o, static_cast<cudaStream_t>(stream));
+}
+
+extern "C" sdf_status sdf_combine(int32_t op, const float* d_a, const float* d_b, int64_t q, float* d_out,
+                                  void* stream) {
+    if (op != SDF_UNION && op != SDF_INTERSECT && op != SDF_DIFFERENCE)
+        return set_error(SDF_EINVAL, "sdf_combine: unknown op");
+    if (q < 0) return set_error(SDF_EINVAL, "sdf_combine: q < 0");
+    if (q == 0) return SDF_OK;
+    if (!d_a || !d_b || !d_out) return set_error(SDF_EINVAL, "sdf_combine: NULL buffer");
+    ptsdf::k_combine<<<(unsigned)((q + 255) / 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(op, d_a, d_b, q, d_out);
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? SDF_OK : cuda_error(e, "sdf_combine");
 }
 
 extern "C" sdf_status sdf_query_host(sdf_cloud cloud, const float* h_x, int64_t q, float* h_phi,

@@ -16,6 +16,7 @@
 #include <string>
 
 #include "device_common.cuh"
+#include "fit_math.cuh"
 #include "internal.h"
 
 namespace ptsdf {
@@ -24,8 +25,6 @@ namespace {
 
 constexpr int kAabbThreads = 1024;
 constexpr int kPartThreads = 1024;
-// |kappa| at or below this (coordinates are O(1)) is a zero curvature.
-constexpr double kFlatKappa = 1e-8;
 
 __global__ void k_aabb(const float* __restrict__ pts, int64_t n, float* __restrict__ box) {
     __shared__ float red[6][kAabbThreads / 32];
@@ -64,8 +63,6 @@ __global__ void k_aabb(const float* __restrict__ pts, int64_t n, float* __restri
     }
 }
 
-__device__ __forceinline__ double sgn_convex(double v) { return v > 0.0 ? 1.0 : -1.0; }
-
 // One point: returns the record (16 floats) and its kind (0 direct, 1 kappa);
 // sets *bad for a zero / non-finite normal or non-finite input.
 __global__ void k_fit(const float* __restrict__ P, const float* __restrict__ Nrm, const float* __restrict__ A6,
@@ -93,56 +90,12 @@ __global__ void k_fit(const float* __restrict__ P, const float* __restrict__ Nrm
         return;
     }
     for (int k = 0; k < 3; ++k) nv[k] /= len;
-    const double a00 = a[0], a01 = a[1], a10 = a[2], a11 = a[3], a02 = a[4], a20 = a[5];
-
-    // branchless orthonormal frame of n (Duff et al. 2017)
-    const double sg = nv[2] >= 0.0 ? 1.0 : -1.0;
-    const double fa = -1.0 / (sg + nv[2]);
-    const double fb = nv[0] * nv[1] * fa;
-    const double s[3] = {1.0 + sg * nv[0] * nv[0] * fa, sg * fb, -sg * nv[0]};
-    const double t[3] = {fb, sg + nv[1] * nv[1] * fa, -nv[1]};
-
-    // fundamental forms at (0,0): I = [[E, F], [F, G]], II = [[2a20, a11], [a11, 2a02]] / A
-    const double E = 1.0 + a10 * a10, G = 1.0 + a01 * a01, F = a10 * a01;
-    const double A2 = 1.0 + a01 * a01 + a10 * a10;
-    const double A = sqrt(A2);
-    // mean and Gauss curvature (Eq. MeanAndGaussCurvatures)
-    const double H = (a02 * E + a20 * G - a11 * F) / (A2 * A);
-    const double K = (4.0 * a02 * a20 - a11 * a11) / (A2 * A2);
-    const double root = sqrt(fmax(H * H - K, 0.0));
-    const double kp = H + root, km = H - root;
-    // kappa_min has the smaller magnitude; a tie keeps kappa_- as kappa_min
-    double kmin = (fabs(kp) < fabs(km)) ? kp : km;
-    double kmax = (fabs(kp) < fabs(km)) ? km : kp;
-    if (fabs(kmin) <= kFlatKappa) kmin = 0.0;
-    if (fabs(kmax) <= kFlatKappa) kmax = 0.0;
-
-    // principal direction of kappa_min: (II - kappa I) w = 0 (Eq. PrincipalDirections).
-    // Each row of the 2x2 system gives a candidate; the longer is kept (the
-    // printed one vanishes when a11 = 0 and kappa = 2 a20).  Umbilic: w = (1, 0).
-    const double kA = kmin * A;
-    double w1x = kA * F - a11, w1y = 2.0 * a20 - kA * E;
-    double w2x = 2.0 * a02 - kA * G, w2y = kA * F - a11;
-    const double l1 = w1x * w1x + w1y * w1y, l2 = w2x * w2x + w2y * w2y;
-    double wx = l1 >= l2 ? w1x : w2x, wy = l1 >= l2 ? w1y : w2y;
-    const double scale = fabs(a20) + fabs(a02) + fabs(a11) + fabs(kA) * (E + G) + 1e-300;
-    if (sqrt(fmax(l1, l2)) <= 1e-12 * scale) {
-        wx = 1.0;
-        wy = 0.0;
-    }
-    double v[3], nstar[3], q[3], u[3];
-    for (int k = 0; k < 3; ++k) v[k] = wx * (s[k] + a10 * nv[k]) + wy * (t[k] + a01 * nv[k]);
-    const double vl = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
-    for (int k = 0; k < 3; ++k) v[k] /= vl;
-    // unit normal of the patch at (0,0), and the shifted point Q*(0,0)
-    for (int k = 0; k < 3; ++k) {
-        nstar[k] = (nv[k] - a10 * s[k] - a01 * t[k]) / A;
-        q[k] = p[k] + a00 * nv[k];
-    }
-    // axis of revolution u = n* x v_min
-    u[0] = nstar[1] * v[2] - nstar[2] * v[1];
-    u[1] = nstar[2] * v[0] - nstar[0] * v[2];
-    u[2] = nstar[0] * v[1] - nstar[1] * v[0];
+    FitPoint<double> f;
+    fit_point<double>(p, nv, a, f);
+    const double kmin = f.kmin, kmax = f.kmax;
+    const double* q = f.q;
+    const double* nstar = f.nstar;
+    const double* u = f.u;
 
     const double sT = -sgn_convex(kmax);          // Eq. TorusSigns
     const bool direct = (kmin != 0.0) && (1.0 / fabs(kmin) <= thr) && (1.0 / fabs(kmax) <= thr);

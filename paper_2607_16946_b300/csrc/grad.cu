@@ -1,0 +1,323 @@
+// sdf_query_grad: phi and its gradient in x (App. D, "Gradient expressions"),
+// including the dependence of lambda_x = 2 C / d_max(x) on x.
+//
+// With w_i = exp(-lambda (d_i - d_min)), n_i = (x - p_i) / d_i and phi = S / W:
+//
+//   grad phi = [ sum w_i grad g_i
+//                - lambda ( sum w_i g_i n_i - phi sum w_i n_i )
+//                - grad lambda ( sum w_i g_i d_i - phi sum w_i d_i ) ] / W,
+//   grad lambda = -(lambda / d_max^2) (x - p_far)       (GLOBAL lambda; 0 if FIXED)
+//
+// (the first two terms are App. D's A + phi B for a constant lambda; the last
+// is the derivative of lambda_x through the farthest point p_far).  The pair
+// loop accumulates the 13 sums W, S, sum w grad g (3), sum w n (3),
+// sum w g n (3), sum w d, sum w g d per query; nothing per pair is stored.
+#include <cuda_runtime.h>
+
+#include <cmath>
+
+#include "query_common.cuh"
+
+namespace ptsdf {
+
+using namespace qk;
+
+namespace {
+
+constexpr int kGradQPerCta = kConsumerWarps * 32;   // one query per consumer thread
+constexpr int kAcc = 13;
+constexpr float kTiny = 1e-30f;                      // zero-length vectors get a zero unit vector
+
+enum { A_W, A_S, A_GX, A_GY, A_GZ, A_NX, A_NY, A_NZ, A_HX, A_HY, A_HZ, A_D, A_GD };
+
+struct GradArgs {
+    QueryArgs a;
+    const float4* pre;       // prepass array (farthest point position)
+    float* grad;             // Q x 3
+    float* saved;            // Q x 8 or null
+    float* part;             // split x Q x kAcc partials (split > 1)
+};
+
+// Accumulates one tile of pairs for one query into acc[].
+template <bool KAPPA>
+__device__ __forceinline__ void grad_tile(const float4* __restrict__ tile, int cnt, float x, float y, float z,
+                                          float L, float A0, float (&acc)[kAcc]) {
+#pragma unroll 1
+    for (int j = 0; j < cnt; ++j) {
+        const float4 r0 = tile[4 * j], r1 = tile[4 * j + 1], r2 = tile[4 * j + 2];
+        const float dx = x - r0.x, dy = y - r0.y, dz = z - r0.z;
+        const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        const float rd = rsqrt_mufu(fmaxf(d2, kTiny));
+        const float d = d2 * rd;
+        float g, gx, gy, gz;
+        if (!KAPPA) {
+            // direct form: g = sT (||(rho - R, h)|| - r), grad g = alpha v_perp + beta u
+            const float vx = x - r1.x, vy = y - r1.y, vz = z - r1.z;
+            const float h = fmaf(vx, r2.x, fmaf(vy, r2.y, vz * r2.z));
+            const float px = fmaf(-h, r2.x, vx), py = fmaf(-h, r2.y, vy), pz = fmaf(-h, r2.z, vz);
+            const float rho2 = fmaf(px, px, fmaf(py, py, pz * pz));
+            const float rr = rsqrt_mufu(fmaxf(rho2, kTiny));
+            const float e = fmaf(rho2, rr, -r1.w);
+            const float Dt2 = fmaf(e, e, h * h);
+            const float rD = rsqrt_mufu(fmaxf(Dt2, kTiny));
+            g = fmaf(r0.w, Dt2 * rD, r2.w);
+            const float sr = r0.w * rD;
+            const float alpha = e * rr * sr, beta = h * sr;
+            gx = fmaf(alpha, px, beta * r2.x);
+            gy = fmaf(alpha, py, beta * r2.y);
+            gz = fmaf(alpha, pz, beta * r2.z);
+        } else {
+            // kappa form (see g_kappa): with s1 = sqrt(1 + k m), s2 = sqrt(1 + K N'),
+            // K = -kappa_max, grad m = 2 k y_perp + m*, d a'/dm = 1/(2 s1),
+            // dg/dN' = 1/(2 s2), dN'/da' = 2 K a' + 2 zeta, dN'/dh = 2 K h:
+            //   grad g = c1 (2 k y_perp + m*) + (K h / s2) u,
+            //   c1 = (2 K a' + 2 zeta) / (4 s1 s2)
+            const float4 r3 = tile[4 * j + 3];
+            const float yx = x - r1.x, yy = y - r1.y, yz = z - r1.z;
+            const float h = fmaf(yx, r2.x, fmaf(yy, r2.y, yz * r2.z));
+            const float hh = h * h;
+            const float t2 = fmaf(yx, yx, fmaf(yy, yy, yz * yz)) - hh;
+            const float m = fmaf(r1.w, t2, fmaf(yx, r3.x, fmaf(yy, r3.y, yz * r3.z)));
+            const float z1 = fmaxf(fmaf(r1.w, m, 1.f), 0.f);
+            const float rs1 = rsqrt_mufu(fmaxf(z1, kTiny));
+            const float ap = m * rcp_mufu(1.f + z1 * rs1);
+            const float Np = fmaf(r2.w, fmaf(ap, ap, hh), r0.w * ap);
+            const float z2 = fmaxf(fmaf(r2.w, Np, 1.f), 0.f);
+            const float rs2 = rsqrt_mufu(fmaxf(z2, kTiny));
+            g = Np * rcp_mufu(1.f + z2 * rs2);
+            const float c1 = 0.25f * rs1 * rs2 * fmaf(2.f * r2.w, ap, r0.w);
+            const float ay = 2.f * c1 * r1.w;             // coefficient of y_perp
+            const float bu = h * fmaf(rs2, r2.w, -ay);    // u coefficient after y_perp = y - h u
+            gx = fmaf(ay, yx, fmaf(c1, r3.x, bu * r2.x));
+            gy = fmaf(ay, yy, fmaf(c1, r3.y, bu * r2.y));
+            gz = fmaf(ay, yz, fmaf(c1, r3.z, bu * r2.z));
+        }
+        const float w = ex2_mufu(fmaf(-L, d, A0));
+        const float wg = w * g;
+        const float wn = w * rd, wgn = wg * rd;
+        acc[A_W] += w;
+        acc[A_S] += wg;
+        acc[A_GX] = fmaf(w, gx, acc[A_GX]);
+        acc[A_GY] = fmaf(w, gy, acc[A_GY]);
+        acc[A_GZ] = fmaf(w, gz, acc[A_GZ]);
+        acc[A_NX] = fmaf(wn, dx, acc[A_NX]);
+        acc[A_NY] = fmaf(wn, dy, acc[A_NY]);
+        acc[A_NZ] = fmaf(wn, dz, acc[A_NZ]);
+        acc[A_HX] = fmaf(wgn, dx, acc[A_HX]);
+        acc[A_HY] = fmaf(wgn, dy, acc[A_HY]);
+        acc[A_HZ] = fmaf(wgn, dz, acc[A_HZ]);
+        acc[A_D] = fmaf(w, d, acc[A_D]);
+        acc[A_GD] = fmaf(wg, d, acc[A_GD]);
+    }
+}
+
+// Per-query lambda and shift from the prepass partials; p_far for GLOBAL.
+struct QueryLam {
+    float L, A0, lam, dmax;
+    float fx, fy, fz;
+};
+
+__device__ __forceinline__ QueryLam query_lambda(const QueryArgs& a, const float4* __restrict__ pre, int64_t qq) {
+    QueryLam r;
+    float2 d2 = a.d2[qq];
+    int32_t far = a.far ? a.far[qq] : 0;
+    for (int c = 1; c < a.split; ++c) {
+        const float2 v = a.d2[(size_t)c * a.q + qq];
+        if (v.x > d2.x) {
+            d2.x = v.x;
+            if (a.far) far = a.far[(size_t)c * a.q + qq];
+        }
+        d2.y = fminf(d2.y, v.y);
+    }
+    const float dmin = sqrtf(fmaxf(d2.y, 0.f));
+    r.dmax = sqrtf(fmaxf(d2.x, 0.f));
+    r.lam = a.lam;
+    r.fx = r.fy = r.fz = 0.f;
+    if (a.mode == SDF_LAMBDA_GLOBAL) {
+        r.lam = r.dmax > 0.f ? 2.f * a.C / r.dmax : 0.f;
+        const float4 pf = pre[far];   // (-2 p', |p'|^2), p' = p - centre
+        r.fx = fmaf(-0.5f, pf.x, a.cx);
+        r.fy = fmaf(-0.5f, pf.y, a.cy);
+        r.fz = fmaf(-0.5f, pf.z, a.cz);
+    }
+    r.L = r.lam * kLog2e;
+    r.A0 = r.L * dmin;
+    return r;
+}
+
+__device__ __forceinline__ void finalize(const GradArgs& ga, int64_t qi, float x, float y, float z,
+                                         const QueryLam& ql, const float (&acc)[kAcc]) {
+    const QueryArgs& a = ga.a;
+    const float invW = 1.f / acc[A_W];
+    const float phi = acc[A_S] * invW;
+    float glx = 0.f, gly = 0.f, glz = 0.f;
+    if (a.mode == SDF_LAMBDA_GLOBAL && ql.dmax > 0.f) {
+        const float s = -ql.lam / (ql.dmax * ql.dmax);
+        glx = s * (x - ql.fx);
+        gly = s * (y - ql.fy);
+        glz = s * (z - ql.fz);
+    }
+    const float cd = fmaf(-phi, acc[A_D], acc[A_GD]);   // sum w g d - phi sum w d
+    const float gx = (acc[A_GX] - ql.lam * fmaf(-phi, acc[A_NX], acc[A_HX]) - glx * cd) * invW;
+    const float gy = (acc[A_GY] - ql.lam * fmaf(-phi, acc[A_NY], acc[A_HY]) - gly * cd) * invW;
+    const float gz = (acc[A_GZ] - ql.lam * fmaf(-phi, acc[A_NZ], acc[A_HZ]) - glz * cd) * invW;
+    a.phi[qi] = phi - a.offset;
+    ga.grad[3 * qi] = gx;
+    ga.grad[3 * qi + 1] = gy;
+    ga.grad[3 * qi + 2] = gz;
+    if (ga.saved) {
+        float* s = ga.saved + 8 * qi;
+        s[0] = x;
+        s[1] = y;
+        s[2] = z;
+        s[3] = ql.L;
+        s[4] = ql.A0;
+        s[5] = acc[A_W];
+        s[6] = phi;
+        s[7] = 0.f;
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) k_fwd_grad(const float4* __restrict__ rec, int64_t n_direct,
+                                                       int64_t n_kappa, int64_t tiles_direct, int64_t tiles_total,
+                                                       int64_t tiles_per_chunk, GradArgs ga, int32_t* status) {
+    extern __shared__ __align__(128) char smem[];
+    __shared__ TileRing<kStages> ring;
+    char* buf = smem;
+    const QueryArgs& a = ga.a;
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int chunk = blockIdx.y;
+    const int64_t t0 = (int64_t)chunk * tiles_per_chunk;
+    const int64_t t1 = t0 + tiles_per_chunk < tiles_total ? t0 + tiles_per_chunk : tiles_total;
+    const int64_t nt = t1 > t0 ? t1 - t0 : 0;
+    if (threadIdx.x == 0) ring.init(kConsumerWarps);
+    __syncthreads();
+    if (warp == kConsumerWarps) {
+        if (lane == 0)
+            ring.produce(buf, reinterpret_cast<const char*>(rec + t0 * kTileRecs * 4), nt, kTileBytes, status);
+        return;
+    }
+    const int64_t qi = (int64_t)blockIdx.x * kGradQPerCta + threadIdx.x;
+    const int64_t qq = qi < a.q ? qi : a.q - 1;
+    const float x = a.x[3 * qq], y = a.x[3 * qq + 1], z = a.x[3 * qq + 2];
+    const QueryLam ql = query_lambda(a, ga.pre, qq);
+    float acc[kAcc], tacc[kAcc];
+#pragma unroll
+    for (int k = 0; k < kAcc; ++k) acc[k] = 0.f;
+    for (int64_t t = 0; t < nt; ++t) {
+        if (!ring.wait_full(t, status)) return;
+        const float4* tile = reinterpret_cast<const float4*>(buf + (size_t)(t % kStages) * kTileBytes);
+        const int64_t gt = t0 + t;
+        const bool kappa = gt >= tiles_direct;
+        const int64_t first = (kappa ? gt - tiles_direct : gt) * kTileRecs;
+        const int64_t seg = kappa ? n_kappa : n_direct;
+        const int cnt = (int)(seg - first < kTileRecs ? seg - first : kTileRecs);
+#pragma unroll
+        for (int k = 0; k < kAcc; ++k) tacc[k] = 0.f;
+        if (kappa)
+            grad_tile<true>(tile, cnt, x, y, z, ql.L, ql.A0, tacc);
+        else
+            grad_tile<false>(tile, cnt, x, y, z, ql.L, ql.A0, tacc);
+#pragma unroll
+        for (int k = 0; k < kAcc; ++k) acc[k] += tacc[k];
+        ring.release(t, lane);
+    }
+    if (qi >= a.q) return;
+    if (a.split == 1) {
+        finalize(ga, qi, x, y, z, ql, acc);
+    } else {
+        float* dst = ga.part + ((size_t)chunk * a.q + qi) * kAcc;
+#pragma unroll
+        for (int k = 0; k < kAcc; ++k) dst[k] = acc[k];
+    }
+}
+
+__global__ void k_merge_grad(GradArgs ga) {
+    const QueryArgs& a = ga.a;
+    const int64_t qi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (qi >= a.q) return;
+    float acc[kAcc];
+#pragma unroll
+    for (int k = 0; k < kAcc; ++k) acc[k] = 0.f;
+    for (int c = 0; c < a.split; ++c) {
+        const float* src = ga.part + ((size_t)c * a.q + qi) * kAcc;
+#pragma unroll
+        for (int k = 0; k < kAcc; ++k) acc[k] += src[k];
+    }
+    const QueryLam ql = query_lambda(a, ga.pre, qi);
+    finalize(ga, qi, a.x[3 * qi], a.x[3 * qi + 1], a.x[3 * qi + 2], ql, acc);
+}
+
+}  // namespace
+
+sdf_status launch_query_grad(const Cloud& c, const float* d_x, int64_t q, float* d_phi, float* d_grad,
+                             float* d_saved, const sdf_query_opts& o, cudaStream_t st) {
+    const Plan p = make_plan(c, q, o.split_n, kGradQPerCta);
+    GradArgs ga;
+    QueryArgs& a = ga.a;
+    a.x = d_x;
+    a.q = q;
+    a.phi = d_phi;
+    a.split = p.split;
+    a.mode = o.lambda_mode;
+    a.C = o.C;
+    a.lam = o.fixed_lambda;
+    a.offset = o.offset;
+    a.part = nullptr;
+    a.d2 = nullptr;
+    a.far = nullptr;
+    a.cx = 0.5f * (c.aabb[0] + c.aabb[3]);
+    a.cy = 0.5f * (c.aabb[1] + c.aabb[4]);
+    a.cz = 0.5f * (c.aabb[2] + c.aabb[5]);
+    ga.pre = c.pre;
+    ga.grad = d_grad;
+    ga.saved = d_saved;
+    ga.part = nullptr;
+    auto oom = [&](cudaError_t e) {
+        if (a.d2) cudaFreeAsync(a.d2, st);
+        if (a.far) cudaFreeAsync(a.far, st);
+        if (ga.part) cudaFreeAsync(ga.part, st);
+        return e == cudaErrorMemoryAllocation ? set_error(SDF_ENOMEM, "sdf_query_grad: scratch")
+                                              : cuda_error(e, "sdf_query_grad: scratch");
+    };
+    cudaError_t e = cudaMallocAsync(&a.d2, (size_t)p.split * q * sizeof(float2), st);
+    if (e != cudaSuccess) return oom(e);
+    if (o.lambda_mode == SDF_LAMBDA_GLOBAL) {
+        e = cudaMallocAsync(&a.far, (size_t)p.split * q * sizeof(int32_t), st);
+        if (e != cudaSuccess) return oom(e);
+    }
+    if (p.split > 1) {
+        e = cudaMallocAsync(&ga.part, (size_t)p.split * q * kAcc * sizeof(float), st);
+        if (e != cudaSuccess) return oom(e);
+    }
+    const dim3 grid((unsigned)p.qblocks, (unsigned)p.split);
+    const dim3 pre_grid((unsigned)p.pre_qblocks, (unsigned)p.split);
+    {
+        ProfRange pr(SDF_K_PREPASS, st);
+        if (o.lambda_mode == SDF_LAMBDA_GLOBAL)
+            k_prepass<SDF_LAMBDA_GLOBAL, true><<<pre_grid, kThreads, kStages * kPreBytes, st>>>(
+                c.pre, c.n, c.pre_tiles, p.pre_tiles_per_chunk, a, c.status);
+        else
+            k_prepass<SDF_LAMBDA_FIXED, false><<<pre_grid, kThreads, kStages * kPreBytes, st>>>(
+                c.pre, c.n, c.pre_tiles, p.pre_tiles_per_chunk, a, c.status);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) {
+        ProfRange pr(SDF_K_FWD_GRAD, st);
+        k_fwd_grad<<<grid, kThreads, kStages * kTileBytes, st>>>(c.rec, c.n_direct, c.n_kappa, c.tiles_direct,
+                                                                c.tiles_direct + c.tiles_kappa, p.tiles_per_chunk,
+                                                                ga, c.status);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess && p.split > 1) {
+        ProfRange pr(SDF_K_MERGE, st);
+        k_merge_grad<<<(unsigned)((q + 255) / 256), 256, 0, st>>>(ga);
+        e = cudaGetLastError();
+    }
+    cudaFreeAsync(a.d2, st);
+    if (a.far) cudaFreeAsync(a.far, st);
+    if (ga.part) cudaFreeAsync(ga.part, st);
+    return e == cudaSuccess ? SDF_OK : cuda_error(e, "sdf_query_grad: launch");
+}
+
+}  // namespace ptsdf

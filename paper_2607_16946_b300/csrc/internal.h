@@ -64,7 +64,8 @@ sdf_status cuda_error(cudaError_t e, const char* what);
 // launch planning shared by the query kernels
 struct Plan {
     int64_t q = 0;
-    int64_t qblocks = 0;             // query blocks of kQueriesPerCta
+    int64_t qblocks = 0;             // query blocks of the main kernel
+    int64_t pre_qblocks = 0;         // query blocks of the prepass (kQueriesPerCta)
     int split = 1;                   // point chunks
     int64_t tiles_per_chunk = 0;     // main-loop tiles per chunk
     int64_t pre_tiles_per_chunk = 0; // prepass tiles per chunk
@@ -75,7 +76,9 @@ constexpr int kQueriesPerThread = 2;
 constexpr int kQueriesPerCta = kConsumerWarps * 32 * kQueriesPerThread;   // 512
 constexpr int kStages = 4;
 
-Plan make_plan(const Cloud& c, int64_t q, int split_override);
+// queries_per_cta: queries one CTA of the main kernel holds (the prepass
+// always uses kQueriesPerCta).
+Plan make_plan(const Cloud& c, int64_t q, int split_override, int queries_per_cta = kQueriesPerCta);
 
 // Brackets one kernel launch with CUDA events while sdf_profile is enabled.
 class ProfRange {
@@ -93,5 +96,15 @@ class ProfRange {
 // kernels' host launchers (query.cu)
 sdf_status launch_query(const Cloud& c, const float* d_x, int64_t q, float* d_phi,
                         const sdf_query_opts& o, cudaStream_t st);
+// trace.cu
+sdf_status launch_trace(const Cloud& c, const float* d_org, const float* d_dir, int64_t nrays, int32_t max_steps,
+                        float eps, float t_max, float* d_t_hit, int32_t* d_steps, float* d_normals,
+                        const sdf_query_opts& o, cudaStream_t st);
+// backward.cu
+sdf_status launch_backward_params(const Cloud& c, int64_t q, const float* d_saved, const float* d_grad_phi,
+                                  float* d_grad_params, const sdf_query_opts& o, cudaStream_t st);
+// grad.cu
+sdf_status launch_query_grad(const Cloud& c, const float* d_x, int64_t q, float* d_phi, float* d_grad,
+                             float* d_saved, const sdf_query_opts& o, cudaStream_t st);
 
 }  // namespace ptsdf

@@ -1,0 +1,164 @@
+// Shared by the query kernels (query.cu, grad.cu): launch constants, the
+// argument block, the d_max / d_min prepass and the two forms of the torus
+// SDF pair term.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cmath>
+
+#include "device_common.cuh"
+#include "internal.h"
+
+namespace ptsdf {
+namespace qk {
+namespace {
+
+constexpr int kThreads = (kConsumerWarps + 1) * 32;   // + producer warp
+constexpr float kLog2e = 1.4426950408889634f;
+constexpr uint32_t kTileBytes = kTileRecs * kRecFloats * sizeof(float);
+constexpr uint32_t kPreBytes = kPreTile * sizeof(float4);
+
+struct QueryArgs {
+    const float* x;          // Q x 3
+    int64_t q;
+    float* phi;              // Q (split == 1)
+    float2* part;            // split x Q (W, S) partials (split > 1)
+    float2* d2;              // split x Q prepass partials (max, min of |x - p|^2)
+    int32_t* far;            // split x Q index of the farthest point (prepass order), or null
+    float cx, cy, cz;        // cloud bounding-box centre (prepass coordinates)
+    int split;
+    int mode;                // sdf_lambda_mode
+    float C;
+    float lam;               // fixed lambda
+    float offset;
+};
+
+// --------------------------------------------------------------------------
+// Prepass
+// --------------------------------------------------------------------------
+template <int MODE, bool ARGMAX = false>
+__global__ void __launch_bounds__(kThreads) k_prepass(const float4* __restrict__ pre, int64_t n, int64_t pre_tiles,
+                                                      int64_t tiles_per_chunk, QueryArgs a, int32_t* status) {
+    extern __shared__ __align__(128) char smem[];
+    __shared__ TileRing<kStages> ring;
+    char* buf = smem;
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int chunk = blockIdx.y;
+    const int64_t t0 = (int64_t)chunk * tiles_per_chunk;
+    const int64_t t1 = t0 + tiles_per_chunk < pre_tiles ? t0 + tiles_per_chunk : pre_tiles;
+    const int64_t nt = t1 > t0 ? t1 - t0 : 0;
+    if (threadIdx.x == 0) ring.init(kConsumerWarps);
+    __syncthreads();
+    if (warp == kConsumerWarps) {
+        if (lane == 0) ring.produce(buf, reinterpret_cast<const char*>(pre + t0 * kPreTile), nt, kPreBytes, status);
+        return;
+    }
+    float xs[kQueriesPerThread][3], hi[kQueriesPerThread], lo[kQueriesPerThread], xx[kQueriesPerThread];
+    int64_t qi[kQueriesPerThread];
+    int32_t far[kQueriesPerThread];
+#pragma unroll
+    for (int k = 0; k < kQueriesPerThread; ++k) {
+        qi[k] = (int64_t)blockIdx.x * kQueriesPerCta + k * (kConsumerWarps * 32) + threadIdx.x;
+        const int64_t qq = qi[k] < a.q ? qi[k] : a.q - 1;
+        xs[k][0] = a.x[3 * qq] - a.cx;
+        xs[k][1] = a.x[3 * qq + 1] - a.cy;
+        xs[k][2] = a.x[3 * qq + 2] - a.cz;
+        xx[k] = xs[k][0] * xs[k][0] + xs[k][1] * xs[k][1] + xs[k][2] * xs[k][2];
+        hi[k] = -INFINITY;
+        lo[k] = INFINITY;
+        far[k] = 0;
+    }
+    for (int64_t t = 0; t < nt; ++t) {
+        if (!ring.wait_full(t, status)) return;
+        const float4* tile = reinterpret_cast<const float4*>(buf + (size_t)(t % kStages) * kPreBytes);
+        const int64_t first = (t0 + t) * kPreTile;
+        const int cnt = (int)(n - first < kPreTile ? n - first : kPreTile);
+        if (MODE == SDF_LAMBDA_GLOBAL) {
+            // |x'-p'|^2 - |x'|^2 = |p'|^2 - 2 <x', p'>: three FMAs per pair.  Its
+            // cancellation near d = 0 only perturbs the shift d_min (harmless
+            // for lambda_x = 2 C / d_max); d_max keeps full relative accuracy.
+#pragma unroll 4
+            for (int j = 0; j < cnt; ++j) {
+                const float4 r = tile[j];
+#pragma unroll
+                for (int k = 0; k < kQueriesPerThread; ++k) {
+                    const float v = fmaf(xs[k][0], r.x, fmaf(xs[k][1], r.y, fmaf(xs[k][2], r.z, r.w)));
+                    if (ARGMAX) {
+                        // first (lowest prepass index) of equal maxima
+                        if (v > hi[k]) {
+                            hi[k] = v;
+                            far[k] = (int32_t)(first + j);
+                        }
+                    } else {
+                        hi[k] = fmaxf(hi[k], v);
+                    }
+                    lo[k] = fminf(lo[k], v);
+                }
+            }
+        } else {
+            // FIXED lambda may be large, so the shift d_min is computed from
+            // the difference vector (no cancellation)
+#pragma unroll 4
+            for (int j = 0; j < cnt; ++j) {
+                const float4 r = tile[j];
+#pragma unroll
+                for (int k = 0; k < kQueriesPerThread; ++k) {
+                    const float dx = fmaf(0.5f, r.x, xs[k][0]), dy = fmaf(0.5f, r.y, xs[k][1]),
+                                dz = fmaf(0.5f, r.z, xs[k][2]);
+                    lo[k] = fminf(lo[k], fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+                }
+            }
+        }
+        ring.release(t, lane);
+    }
+#pragma unroll
+    for (int k = 0; k < kQueriesPerThread; ++k) {
+        if (qi[k] < a.q) {
+            const float2 v = MODE == SDF_LAMBDA_GLOBAL ? make_float2(hi[k] + xx[k], lo[k] + xx[k])
+                                                       : make_float2(-INFINITY, lo[k]);
+            a.d2[(size_t)chunk * a.q + qi[k]] = v;
+            if (ARGMAX) a.far[(size_t)chunk * a.q + qi[k]] = far[k];
+        }
+    }
+}
+
+// --------------------------------------------------------------------------
+// Pair terms
+// --------------------------------------------------------------------------
+// Direct form: v = x - c, h = <v, u>, rho = |v - h u| (the distance to the
+// axis, computed from the perpendicular component so it stays accurate near
+// the axis), g = sT (||(rho - R, h)|| - r).
+__device__ __forceinline__ float g_direct(float x, float y, float z, const float4& r1, const float4& r2, float sT) {
+    const float vx = x - r1.x, vy = y - r1.y, vz = z - r1.z;
+    const float h = fmaf(vx, r2.x, fmaf(vy, r2.y, vz * r2.z));
+    const float wx = fmaf(-h, r2.x, vx), wy = fmaf(-h, r2.y, vy), wz = fmaf(-h, r2.z, vz);
+    const float rho = sqrt_mufu(fmaf(wx, wx, fmaf(wy, wy, wz * wz)));
+    const float e = rho - r1.w;
+    const float D = sqrt_mufu(fmaf(e, e, h * h));
+    return fmaf(sT, D, r2.w);
+}
+
+// Curvature form around q = Q*(0,0), exact rewrite of the same torus SDF:
+// with y = x - q, h = <y, u>, t^2 = |y|^2 - h^2, k = |kappa_min|,
+//   m  = k t^2 + 2 zeta <y, n*>,    a' = m / (1 + sqrt(1 + k m))   (= rho - 1/k)
+//   N' = -kappa_max (a'^2 + h^2) + 2 zeta a'
+//   g  = N' / (1 + sqrt(1 + (-kappa_max) N'))
+// which has no 1/k or 1/|kappa_max| and so no cancellation of large radii.
+__device__ __forceinline__ float g_kappa(float x, float y, float z, const float4& r0, const float4& r1,
+                                         const float4& r2, const float4& r3) {
+    const float yx = x - r1.x, yy = y - r1.y, yz = z - r1.z;
+    const float h = fmaf(yx, r2.x, fmaf(yy, r2.y, yz * r2.z));
+    const float hh = h * h;
+    const float t2 = fmaf(yx, yx, fmaf(yy, yy, yz * yz)) - hh;
+    const float m = fmaf(r1.w, t2, fmaf(yx, r3.x, fmaf(yy, r3.y, yz * r3.z)));
+    const float s1 = sqrt_mufu(fmaxf(fmaf(r1.w, m, 1.f), 0.f));
+    const float ap = m * rcp_mufu(1.f + s1);
+    const float Np = fmaf(r2.w, fmaf(ap, ap, hh), r0.w * ap);
+    const float s2 = sqrt_mufu(fmaxf(fmaf(r2.w, Np, 1.f), 0.f));
+    return Np * rcp_mufu(1.f + s2);
+}
+
+}  // namespace
+}  // namespace qk
+}  // namespace ptsdf

@@ -1,0 +1,156 @@
+"""GPU parity of the gradient paths against the FP64 oracle.
+
+  sdf_query_grad       d phi / d x (App. D plus the lambda_x(x) term) vs the
+                       oracle's forward-mode duals, and vs central finite
+                       differences of the oracle (h = 1e-3, Richardson).
+  sdf_backward_params  d(sum G phi) / d a vs the oracle's duals through the fit.
+  autograd             the torch.autograd.Function routes both.
+Tolerance: 1e-3 relative to max(1, |reference|) per entry (FP32 path).
+Queries whose two farthest points lie within 1e-3 of each other are left
+out: lambda_x has a kink there and the two sides may pick different points.
+"""
+import numpy as np
+import pytest
+
+import synth
+from workloads import f32, mixed_cloud
+
+pytestmark = pytest.mark.gpu
+GTOL = 1e-3
+
+
+@pytest.fixture(scope="module")
+def ptsdf():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2607_16946_b300 import build
+    build.build()
+    import paper_2607_16946_b300 as m
+    return m
+
+
+def far_gap(p, x):
+    d = np.sort(np.linalg.norm(x[:, None, :] - p[None], axis=2), axis=1)
+    return d[:, -1] - d[:, -2]
+
+
+def config4(n=65536, q=1_000_000):
+    p, nn, a = synth.ellipsoid(n, 1004, axes=(1.0, 0.6, 0.4), perturb=0.05)
+    x = synth.uniform_queries(q, 1004, -1.5, 1.5)
+    return f32(p, nn, a, x)
+
+
+def gpu_grad(cl, x, **kw):
+    import torch
+    phi, g, saved = cl.query_grad(torch.as_tensor(x, dtype=torch.float32, device="cuda"), **kw)
+    torch.cuda.synchronize()
+    assert cl.device_status() == 0
+    return phi.cpu().numpy().astype(np.float64), g.cpu().numpy().astype(np.float64), saved
+
+
+def check_close(got, ref, tol=GTOL):
+    err = np.abs(got - ref) / np.maximum(1.0, np.abs(ref))
+    assert err.max() <= tol, (err.max(), np.unravel_index(err.argmax(), err.shape))
+
+
+def test_grad_config4_subset(ptsdf, oracle_mod):
+    """Differentiation config (N = 65,536 perturbed ellipsoid), 768 sampled
+    queries of the 1e6: phi and d phi / d x against the oracle's duals."""
+    p, n, a, x = config4(q=4096)
+    x = x[far_gap(p, x) > 1e-3][:768]
+    cl = ptsdf.Cloud(p, n, a)
+    phi, g, _ = gpu_grad(cl, x)
+    ophi, og = oracle_mod.Cloud(p, n, a).grad_x(x)
+    assert np.abs(phi - ophi).max() <= 1e-4 * np.linalg.norm(p.max(0) - p.min(0))
+    check_close(g, og)
+
+
+@pytest.mark.parametrize("split", [0, 1, 4])
+@pytest.mark.parametrize("q", [1, 255, 257, 700])
+def test_grad_mixed_ragged(ptsdf, oracle_mod, q, split):
+    """Both torus record forms, ragged query counts around the 256-query
+    block, explicit splits (the 13-sum merge)."""
+    p, n, a = mixed_cloud(21)
+    x = f32(synth.uniform_queries(3 * q + 10, 600 + q, -1.5, 1.5))
+    x = x[far_gap(p, x) > 1e-3][:q]
+    cl = ptsdf.Cloud(p, n, a)
+    phi, g, _ = gpu_grad(cl, x, split_n=split)
+    ophi, og = oracle_mod.Cloud(p, n, a).grad_x(x)
+    assert np.abs(phi - ophi).max() <= 1e-4 * np.linalg.norm(p.max(0) - p.min(0))
+    check_close(g, og)
+
+
+def test_grad_fixed_lambda(ptsdf, oracle_mod):
+    p, n, a = f32(*synth.ring_torus(3000, 31, noise=0.005, jitter_deg=2.0))
+    x = f32(synth.uniform_queries(500, 32, -1.6, 1.6))
+    cl = ptsdf.Cloud(p, n, a)
+    _, g, _ = gpu_grad(cl, x, lambda_mode=ptsdf.SDF_LAMBDA_FIXED, fixed_lambda=150.0)
+    _, og = oracle_mod.Cloud(p, n, a).grad_x(x, mode=oracle_mod.FIXED, lam=150.0)
+    check_close(g, og)
+
+
+def test_grad_vs_finite_differences(ptsdf, oracle_mod):
+    """1,024 sampled entries of d phi / d x (config 4 cloud, N reduced to
+    8,192): GPU analytic vs central differences of the FP64 oracle with
+    h = 1e-3 and h / 2, Richardson-extrapolated."""
+    p, n, a, x = config4(n=8192, q=4000)
+    x = x[far_gap(p, x) > 4e-3]
+    rng = np.random.Generator(np.random.PCG64(5))
+    rows = rng.choice(x.shape[0], size=1024, replace=False)
+    comp = rng.integers(0, 3, size=1024)
+    xs = x[rows]
+    cl = ptsdf.Cloud(p, n, a)
+    _, g, _ = gpu_grad(cl, xs)
+    oc = oracle_mod.Cloud(p, n, a)
+    e = np.zeros((1024, 3))
+    e[np.arange(1024), comp] = 1.0
+    fd = []
+    for h in (1e-3, 5e-4):
+        fd.append((oc.phi(xs + h * e) - oc.phi(xs - h * e)) / (2 * h))
+    rich = (4 * fd[1] - fd[0]) / 3
+    got = g[np.arange(1024), comp]
+    check_close(got, rich, tol=2e-3)
+
+
+def test_backward_params(ptsdf, oracle_mod):
+    """d(sum_q G_q phi_q)/d a: ellipsoid (direct records) and the mixed
+    cloud without zero curvatures (kappa records), against the oracle."""
+    import torch
+    for p, n, a in (f32(*synth.ellipsoid(1500, 41, perturb=0.05)),
+                    mixed_cloud(22)):
+        keep = np.ones(p.shape[0], bool)
+        if p.shape[0] == 1000:      # mixed cloud: drop plane / cylinder points (zero curvature)
+            fit = [oracle_mod.fit_record(p[i], n[i], a[i]) for i in range(p.shape[0])]
+            keep = np.array([abs(f["kmin"]) > 1e-6 for f in fit])
+            p, n, a = p[keep], n[keep], a[keep]
+        x = f32(synth.uniform_queries(400, 42, -1.5, 1.5))
+        x = x[far_gap(p, x) > 1e-3][:300]
+        G = f32(np.random.Generator(np.random.PCG64(43)).normal(size=x.shape[0]))
+        cl = ptsdf.Cloud(p, n, a)
+        info = cl.info()
+        xt = torch.as_tensor(x, dtype=torch.float32, device="cuda")
+        _, _, saved = cl.query_grad(xt)
+        gp = cl.backward_params(xt, saved, torch.as_tensor(G, dtype=torch.float32, device="cuda"))
+        torch.cuda.synchronize()
+        assert cl.device_status() == 0
+        gp = gp.cpu().numpy().astype(np.float64)
+        ref = oracle_mod.Cloud(p, n, a).grad_params(x, G)
+        scale = np.abs(ref).max()
+        assert np.abs(gp - ref).max() <= 2e-3 * scale, (info, np.abs(gp - ref).max(), scale)
+
+
+def test_autograd_function(ptsdf):
+    import torch
+    p, n, a = f32(*synth.ellipsoid(2000, 51, perturb=0.05))
+    params = torch.as_tensor(a, dtype=torch.float32, device="cuda").requires_grad_(True)
+    cl = ptsdf.Cloud(p, n, a)
+    x = torch.as_tensor(f32(synth.uniform_queries(300, 52)), dtype=torch.float32, device="cuda")
+    x.requires_grad_(True)
+    phi = ptsdf.sdf(x, cl, params)
+    w = torch.linspace(-1, 1, 300, device="cuda")
+    (phi * w).sum().backward()
+    _, g, saved = cl.query_grad(x.detach())
+    torch.testing.assert_close(x.grad, w[:, None] * g)
+    gp = cl.backward_params(x.detach(), saved, w)
+    torch.testing.assert_close(params.grad, gp)
