@@ -17,9 +17,11 @@ import ctypes
 import numpy as np
 
 from . import _abi
-from ._abi import (SDF_LAMBDA_FIXED, SDF_LAMBDA_GLOBAL, SdfError, check, lib, make_opts)
+from ._abi import (SDF_DIFFERENCE, SDF_INTERSECT, SDF_LAMBDA_FIXED, SDF_LAMBDA_GLOBAL, SDF_UNION, SdfError,
+                   check, lib, make_opts)
 
-__all__ = ["Cloud", "SdfError", "SDF_LAMBDA_GLOBAL", "SDF_LAMBDA_FIXED", "make_opts", "lib", "sdf"]
+__all__ = ["Cloud", "SdfError", "SDF_LAMBDA_GLOBAL", "SDF_LAMBDA_FIXED", "SDF_UNION", "SDF_INTERSECT",
+           "SDF_DIFFERENCE", "make_opts", "lib", "sdf", "combine"]
 
 
 def _torch():
@@ -120,6 +122,23 @@ class Cloud:
               "sdf_backward_params")
         return out
 
+    def trace(self, origins, dirs, max_steps: int = 48, eps: float = 1e-4, t_max: float = 6.0,
+              normals: bool = True, stream=None, **opts):
+        """Sphere tracing of phi = offset: (t_hit, steps, normals or None); t_hit = -1 for misses."""
+        torch = _torch()
+        org, d = _dev_f32(origins, 3), _dev_f32(dirs, 3)
+        r = org.shape[0]
+        t_hit = torch.empty(r, device=org.device, dtype=torch.float32)
+        steps = torch.empty(r, device=org.device, dtype=torch.int32)
+        nrm = torch.empty((r, 3), device=org.device, dtype=torch.float32) if normals else None
+        o = make_opts(**opts)
+        check(lib().sdf_trace(self._h, ctypes.c_void_p(org.data_ptr()), ctypes.c_void_p(d.data_ptr()), r,
+                              int(max_steps), float(eps), float(t_max), ctypes.c_void_p(t_hit.data_ptr()),
+                              ctypes.c_void_p(steps.data_ptr()),
+                              ctypes.c_void_p(nrm.data_ptr()) if normals else None,
+                              ctypes.byref(o), _stream_ptr(stream)), "sdf_trace")
+        return t_hit, steps, nrm
+
     def query_host(self, x, out=None, stream=None, **opts):
         """phi with host (numpy) buffers; copies happen inside the library."""
         x = np.ascontiguousarray(x, dtype=np.float32).reshape(-1, 3)
@@ -170,6 +189,17 @@ def _autograd_function():
 
 
 _SDFQuery = None
+
+
+def combine(op: int, a, b, out=None, stream=None):
+    """Booleans of two phi arrays (CUDA tensors): SDF_UNION, SDF_INTERSECT, SDF_DIFFERENCE."""
+    torch = _torch()
+    a, b = _dev_f32(a).reshape(-1), _dev_f32(b).reshape(-1)
+    if out is None:
+        out = torch.empty_like(a)
+    check(lib().sdf_combine(int(op), ctypes.c_void_p(a.data_ptr()), ctypes.c_void_p(b.data_ptr()), a.shape[0],
+                            ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)), "sdf_combine")
+    return out
 
 
 def sdf(x, cloud: Cloud, params=None, **opts):

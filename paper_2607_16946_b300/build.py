@@ -29,23 +29,25 @@ def _headers():
         glob.glob(os.path.join(ROOT, "include", "*.h"))
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, defines=(), lib_path: str = LIB, build_dir: str = BUILD) -> str:
+    """Compiles and links libptsdf.so.  `defines` (e.g. ["PTSDF_QPT=4"]) and a
+    separate lib_path / build_dir build a tuning variant next to the default."""
+    os.makedirs(build_dir, exist_ok=True)
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")) + glob.glob(os.path.join(CSRC, "*.cpp")))
     hdr_time = max([os.path.getmtime(h) for h in _headers()] + [0.0])
     objs = []
     for s in srcs:
-        o = os.path.join(BUILD, os.path.basename(s) + ".o")
+        o = os.path.join(build_dir, os.path.basename(s) + ".o")
         objs.append(o)
         if not force and os.path.exists(o) and os.path.getmtime(o) >= max(os.path.getmtime(s), hdr_time):
             continue
-        cmd = [NVCC, *ARCH, *FLAGS, "-c", s, "-o", o]
+        cmd = [NVCC, *ARCH, *FLAGS, *[f"-D{d}" for d in defines], "-c", s, "-o", o]
         if verbose:
             cmd.insert(1, "-Xptxas=-v")
         subprocess.run(cmd, check=True)
-    if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < max(os.path.getmtime(o) for o in objs):
-        subprocess.run([NVCC, *ARCH, "-shared", "-o", LIB, *objs, "-lpthread"], check=True)
-    return LIB
+    if force or not os.path.exists(lib_path) or os.path.getmtime(lib_path) < max(os.path.getmtime(o) for o in objs):
+        subprocess.run([NVCC, *ARCH, "-shared", "-o", lib_path, *objs, "-lpthread"], check=True)
+    return lib_path
 
 
 if __name__ == "__main__":

@@ -35,7 +35,18 @@ namespace ptsdf {
 // A second array holds, per point in the same partitioned order (compact,
 // padded to kPreTile), float4(-2 p', |p'|^2) with p' = p - (bounding-box
 // centre), for the d_max / d_min prepass.
-constexpr int kTileRecs = 32;        // records per main-loop tile (2 KB)
+// Tuning constants can be overridden at compile time (-DPTSDF_TILE_RECS=...,
+// -DPTSDF_QPT=..., -DPTSDF_STAGES=...) to build variants for a sweep.
+#ifndef PTSDF_TILE_RECS
+#define PTSDF_TILE_RECS 32
+#endif
+#ifndef PTSDF_QPT
+#define PTSDF_QPT 2
+#endif
+#ifndef PTSDF_STAGES
+#define PTSDF_STAGES 4
+#endif
+constexpr int kTileRecs = PTSDF_TILE_RECS;   // records per main-loop tile (32 x 64 B = 2 KB)
 constexpr int kRecFloats = 16;
 constexpr int kPreTile = 256;        // points per prepass tile (4 KB)
 
@@ -72,9 +83,9 @@ struct Plan {
 };
 
 constexpr int kConsumerWarps = 8;
-constexpr int kQueriesPerThread = 2;
+constexpr int kQueriesPerThread = PTSDF_QPT;
 constexpr int kQueriesPerCta = kConsumerWarps * 32 * kQueriesPerThread;   // 512
-constexpr int kStages = 4;
+constexpr int kStages = PTSDF_STAGES;
 
 // queries_per_cta: queries one CTA of the main kernel holds (the prepass
 // always uses kQueriesPerCta).
