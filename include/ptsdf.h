@@ -206,6 +206,34 @@ PTSDF_API sdf_status sdf_combine(int32_t op, const float* d_a, const float* d_b,
                        void* stream);
 
 /* ---------------------------------------------------------------------------
+ * sdf_query_noalloc -- sdf_query that allocates nothing.  The paper has no
+ *   counterpart; this is a service of this library.
+ *
+ *   For callers that must not touch the CUDA allocator once they are running:
+ *   latency-bound loops (a renderer asking for phi every frame, a controller
+ *   checking clearance every cycle), where cudaMalloc / cudaMallocAsync can
+ *   block, synchronise or fail at the worst moment, and services that reserve
+ *   all of their device memory at start-up and treat any later allocation as
+ *   an error.
+ *
+ *   Same arguments, results and errors as sdf_query, but the scratch lives in
+ *   one fixed 8 MiB array compiled into the library.  Every GPU that loads the
+ *   library holds that array until the process exits.
+ *   - Limit: q <= 1,048,576 queries per call; larger q returns SDF_EINVAL with
+ *     a message (split the batch).  For small batches the number of point
+ *     chunks is reduced until the chunk partials fit.
+ *   - The first call on each device looks up the array's device address
+ *     (with that device current); make that first call before any stream
+ *     capture.
+ *   - Every call on a device shares the one array and it keeps the last
+ *     call's contents (every entry is written before it is read, so nothing
+ *     needs clearing).  Calls whose kernels overlap on the GPU (different
+ *     streams, or several host threads) race on it: serialise them.
+ * ------------------------------------------------------------------------- */
+PTSDF_API sdf_status sdf_query_noalloc(sdf_cloud cloud, const float* d_x, int64_t q, float* d_phi,
+                                       const sdf_query_opts* opts, void* stream);
+
+/* ---------------------------------------------------------------------------
  * Kernel timing (a tracing aid, not part of the method).  While enabled,
  * every kernel the library launches is bracketed by two CUDA events recorded
  * on the stream it is launched on.  sdf_profile_read waits for the recorded

@@ -45,6 +45,7 @@ SIGNATURES = {
                                       ctypes.POINTER(_I64)]),
     "sdf_query": (ctypes.c_int, [_P, _P, _I64, _P, ctypes.POINTER(sdf_query_opts), _P]),
     "sdf_query_host": (ctypes.c_int, [_P, _P, _I64, _P, ctypes.POINTER(sdf_query_opts), _P]),
+    "sdf_query_noalloc": (ctypes.c_int, [_P, _P, _I64, _P, ctypes.POINTER(sdf_query_opts), _P]),
     "sdf_query_grad": (ctypes.c_int, [_P, _P, _I64, _P, _P, _P, ctypes.POINTER(sdf_query_opts), _P]),
     "sdf_backward_params": (ctypes.c_int, [_P, _P, _I64, _P, _P, _P, ctypes.POINTER(sdf_query_opts), _P]),
     "sdf_trace": (ctypes.c_int, [_P, _P, _P, _I64, _I32, _F, _F, _P, _P, _P, ctypes.POINTER(sdf_query_opts), _P]),

@@ -31,6 +31,8 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <mutex>
+#include <string>
 
 #include "query_common.cuh"
 
@@ -247,3 +249,126 @@ sdf_status launch_query(const Cloud& c, const float* d_x, int64_t q, float* d_ph
 }
 
 }  // namespace ptsdf
+
+// ---------------------------------------------------------------------------
+// sdf_query_noalloc: sdf_query for callers that must not allocate device
+// memory while they run.  Its scratch (the prepass partials and, for split
+// point chunks, the (W, S) partials) lives in one fixed file-scope device
+// array instead of the stream-ordered allocator.
+// ---------------------------------------------------------------------------
+namespace ptsdf {
+
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = 8u << 20;   // 8 MiB per device, held until the process exits
+
+// The scratch array.  Host code must not use this symbol as a pointer (it is a
+// host-side stand-in); the device address comes from cudaGetSymbolAddress.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[kMaxDevices] = {};
+
+// Device address of the scratch array on the current device, looked up once
+// per device (the first call on a device does this lookup).
+sdf_status noalloc_scratch(void** out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_error(e, "sdf_query_noalloc: cudaGetDevice");
+    if (dev < 0 || dev >= kMaxDevices) return set_error(SDF_EINVAL, "sdf_query_noalloc: device id out of range");
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return cuda_error(e, "sdf_query_noalloc: cudaGetSymbolAddress");
+        g_noalloc_ptr[dev] = p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return SDF_OK;
+}
+
+size_t round256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+}  // namespace
+
+}  // namespace ptsdf
+
+extern "C" sdf_status sdf_query_noalloc(sdf_cloud cloud, const float* d_x, int64_t q, float* d_phi,
+                                        const sdf_query_opts* opts, void* stream) {
+    using namespace ptsdf;
+    if (!cloud) return set_error(SDF_EINVAL, "sdf_query_noalloc: cloud is NULL");
+    if (q < 0) return set_error(SDF_EINVAL, "sdf_query_noalloc: q < 0");
+    sdf_query_opts o;
+    sdf_opts_default(&o);
+    if (opts) o = *opts;
+    if (o.lambda_mode != SDF_LAMBDA_GLOBAL && o.lambda_mode != SDF_LAMBDA_FIXED)
+        return set_error(SDF_EINVAL, "sdf_query_noalloc: unknown lambda_mode");
+    if (o.precision != SDF_F32) return set_error(SDF_EINVAL, "sdf_query_noalloc: unsupported precision");
+    if (!(o.C > 0.f) || !std::isfinite(o.C)) return set_error(SDF_EINVAL, "sdf_query_noalloc: C must be > 0");
+    if (o.lambda_mode == SDF_LAMBDA_FIXED && (!(o.fixed_lambda >= 0.f) || !std::isfinite(o.fixed_lambda)))
+        return set_error(SDF_EINVAL, "sdf_query_noalloc: fixed_lambda must be >= 0");
+    if (!std::isfinite(o.offset) || o.split_n < 0) return set_error(SDF_EINVAL, "sdf_query_noalloc: bad options");
+    if (q == 0) return SDF_OK;
+    if (!d_x || !d_phi) return set_error(SDF_EINVAL, "sdf_query_noalloc: NULL buffer");
+    // one float2 per query for the prepass is the least this path needs
+    if ((size_t)q * sizeof(float2) > kNoAllocScratchBytes)
+        return set_error(SDF_EINVAL, "sdf_query_noalloc: q = " + std::to_string(q) + " exceeds the maximum of " +
+                                         std::to_string(kNoAllocScratchBytes / sizeof(float2)) +
+                                         " queries per call (8 MiB of fixed scratch); split the batch");
+    const Cloud& c = *reinterpret_cast<const Cloud*>(cloud);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    void* scratch = nullptr;
+    sdf_status s = noalloc_scratch(&scratch);
+    if (s != SDF_OK) return s;
+    Plan p = make_plan(c, q, o.split_n);
+    // the split partials must fit too: d2 (split x q float2) + (W, S) (split x q float2)
+    const int64_t tiles = c.tiles_direct + c.tiles_kappa;
+    int64_t split = p.split;
+    while (split > 1 && round256((size_t)split * q * sizeof(float2)) + (size_t)split * q * sizeof(float2) >
+                            kNoAllocScratchBytes)
+        --split;
+    if (split != p.split) {
+        p.tiles_per_chunk = (tiles + split - 1) / split;
+        split = (tiles + p.tiles_per_chunk - 1) / p.tiles_per_chunk;
+        p.split = (int)split;
+        p.pre_tiles_per_chunk = (c.pre_tiles + split - 1) / split;
+    }
+    QueryArgs a;
+    a.x = d_x;
+    a.q = q;
+    a.phi = d_phi;
+    a.split = p.split;
+    a.mode = o.lambda_mode;
+    a.C = o.C;
+    a.lam = o.fixed_lambda;
+    a.offset = o.offset;
+    a.far = nullptr;
+    a.cx = 0.5f * (c.aabb[0] + c.aabb[3]);
+    a.cy = 0.5f * (c.aabb[1] + c.aabb[4]);
+    a.cz = 0.5f * (c.aabb[2] + c.aabb[5]);
+    // every scratch entry is written before it is read, so nothing is cleared
+    char* base = static_cast<char*>(scratch);
+    a.d2 = reinterpret_cast<float2*>(base);
+    a.part = p.split > 1 ? reinterpret_cast<float2*>(base + round256((size_t)p.split * q * sizeof(float2))) : nullptr;
+    const dim3 grid((unsigned)p.qblocks, (unsigned)p.split);
+    const dim3 pre_grid((unsigned)p.pre_qblocks, (unsigned)p.split);
+    if (o.lambda_mode == SDF_LAMBDA_GLOBAL)
+        k_prepass<SDF_LAMBDA_GLOBAL><<<pre_grid, kThreads, kStages * kPreBytes, st>>>(
+            c.pre, c.n, c.pre_tiles, p.pre_tiles_per_chunk, a, c.status);
+    else
+        k_prepass<SDF_LAMBDA_FIXED><<<pre_grid, kThreads, kStages * kPreBytes, st>>>(
+            c.pre, c.n, c.pre_tiles, p.pre_tiles_per_chunk, a, c.status);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) {
+        k_fwd<<<grid, kThreads, kStages * kTileBytes, st>>>(c.rec, c.n_direct, c.n_kappa, c.tiles_direct,
+                                                           c.tiles_direct + c.tiles_kappa, p.tiles_per_chunk, a,
+                                                           c.status);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess && p.split > 1) {
+        k_merge<<<(unsigned)((q + 255) / 256), 256, 0, st>>>(a);
+        e = cudaGetLastError();
+    }
+    return e == cudaSuccess ? SDF_OK : cuda_error(e, "sdf_query_noalloc: launch");
+}
