@@ -175,6 +175,230 @@ def cpu_baseline(points, normals, params, target_s: float = 12.0):
                       f"{threads} threads, {dt:.1f} s"}
 
 
+SERVE_SEED = 1005
+
+
+def make_serving_clouds(n_clouds: int, seed: int):
+    """Serving configuration: clouds with N log-uniform in [2,048, 500,000] drawn
+    from the sphere / ring torus / superquadric / ellipsoid generators."""
+    import synth
+    rng = np.random.Generator(np.random.PCG64(seed))
+    gens = [lambda n, s: synth.sphere_fibonacci(n, s),
+            lambda n, s: synth.ring_torus(n, s),
+            lambda n, s: synth.superquadric(n, s, grid=256),
+            lambda n, s: synth.ellipsoid(n, s)]
+    out = []
+    for i in range(n_clouds):
+        n = int(np.exp(rng.uniform(np.log(2048), np.log(500_000))))
+        out.append(gens[int(rng.integers(0, 4))](n, seed + 1 + i))
+    return out
+
+
+def run_served(args, dev, pair_rate_gps: float):
+    """Continuous-batching run: Poisson arrivals at `load` x the measured pair
+    rate, requests of Q log-uniform in [1,024, 4,194,304] against random
+    resident clouds; kinds QUERY 70%, OFFSET 10%, UNION / DIFFERENCE 10%,
+    TRACE_STEP 10%.  Returns the latency / throughput summary."""
+    import torch
+
+    import paper_2607_16946_b300 as ptsdf
+    from paper_2607_16946_b300 import serve as S
+
+    clouds_np = make_serving_clouds(args.serve_clouds, SERVE_SEED)
+    clouds = [ptsdf.Cloud(*c) for c in clouds_np]
+    ns = [c.n for c in clouds]
+    rng = np.random.Generator(np.random.PCG64(SERVE_SEED))
+    qmax = 4_194_304
+    pool = torch.rand((qmax, 3), device=dev, generator=torch.Generator(device=dev).manual_seed(SERVE_SEED)) * 3.0 - 1.5
+    dpool = torch.nn.functional.normalize(torch.randn((qmax, 3), device=dev), dim=1).contiguous()
+    tpool = (torch.rand(qmax, device=dev) * 0.5).contiguous()
+    reqs = []
+    for _ in range(args.serve_requests):
+        u = rng.random()
+        kind = (S.SDF_REQ_QUERY if u < 0.8 else
+                (S.SDF_REQ_UNION if u < 0.85 else S.SDF_REQ_DIFFERENCE) if u < 0.9 else S.SDF_REQ_TRACE_STEP)
+        q = int(np.exp(rng.uniform(np.log(1024), np.log(qmax))))
+        ca, cb = int(rng.integers(0, len(clouds))), int(rng.integers(0, len(clouds)))
+        off = int(rng.integers(0, qmax - q + 1))
+        pairs = q * ns[ca] + (q * ns[cb] if kind in (S.SDF_REQ_UNION, S.SDF_REQ_DIFFERENCE) else 0)
+        reqs.append(dict(kind=kind, q=q, ca=ca, cb=cb, off=off, pairs=pairs, offset=0.05 if 0.7 <= u < 0.8 else 0.0))
+    mean_pairs = float(np.mean([r["pairs"] for r in reqs]))
+    rate = args.serve_load * pair_rate_gps * 1e9 / mean_pairs          # requests per second
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=len(reqs)))
+    srv = S.Server(mem_budget_bytes=16 << 30, max_inflight=8, n_streams=4)
+    ids = [srv.register(c) for c in clouds]
+    outs = [torch.empty(r["q"], device=dev) for r in reqs]
+    torch.cuda.synchronize(dev)
+    tickets = [None] * len(reqs)
+    t0 = time.perf_counter()
+
+    def submitter():
+        for i, r in enumerate(reqs):
+            dt = arrivals[i] - (time.perf_counter() - t0)
+            if dt > 0:
+                time.sleep(dt)
+            x = pool[r["off"]:r["off"] + r["q"]]
+            kw = {}
+            if r["kind"] == S.SDF_REQ_TRACE_STEP:
+                kw = dict(dirs=dpool[r["off"]:r["off"] + r["q"]], t=tpool[r["off"]:r["off"] + r["q"]])
+            tickets[i] = srv.submit(r["kind"], ids[r["ca"]], x, outs[i], cloud_id_b=ids[r["cb"]],
+                                    offset=r["offset"], **kw)
+
+    th = threading.Thread(target=submitter)
+    th.start()
+    stats = []
+    for i in range(len(reqs)):
+        while tickets[i] is None:
+            time.sleep(0.0005)
+        stats.append(srv.poll(tickets[i]))
+    th.join()
+    srv.shutdown()
+    lat = np.array([(s["done_ns"] - s["arrive_ns"]) / 1e6 for s in stats])
+    queue = np.array([(s["admit_ns"] - s["arrive_ns"]) / 1e6 for s in stats])
+    service = np.array([(s["done_ns"] - s["admit_ns"]) / 1e6 for s in stats])
+    span_s = (max(s["done_ns"] for s in stats) - min(s["arrive_ns"] for s in stats)) / 1e9
+    total_pairs = float(sum(r["pairs"] for r in reqs))
+    finite = all(bool(torch.isfinite(o).all()) for o in outs)
+    return {"value": total_pairs / span_s / 1e9, "unit": UNIT, "requests": len(reqs),
+            "queries_per_s": float(sum(r["q"] for r in reqs)) / span_s,
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "queue_p50_ms": float(np.percentile(queue, 50)), "queue_p99_ms": float(np.percentile(queue, 99)),
+            "service_p50_ms": float(np.percentile(service, 50)), "service_p99_ms": float(np.percentile(service, 99)),
+            "offered_load": args.serve_load, "arrival_rate_per_s": rate, "mean_pairs_per_request": mean_pairs,
+            "clouds": len(clouds), "points_total": int(sum(ns)), "outputs_finite": finite,
+            "server": {"max_inflight": 8, "n_streams": 4, "mem_budget_bytes": 16 << 30},
+            "workload": f"{len(clouds)} resident clouds N~logU[2048,500000] (sphere/torus/superquadric/ellipsoid), "
+                        f"{len(reqs)} requests Q~logU[1024,4194304], Poisson arrivals at "
+                        f"{args.serve_load} x measured capacity; FP32"}
+
+
+# Algorithmic issue slots per pair of the other pair loops (direct torus form,
+# counted from their arithmetic): the gradient term is 54 FP32 (distance,
+# torus, grad g, weight, 13 accumulations) + 4 MUFU; the parameter-backward
+# term is 47 FP32 (distance, weight, torus, 8 record derivatives) + 4 MUFU.
+GRAD_INSTR_PER_PAIR = 58
+BWD_INSTR_PER_PAIR = 51
+
+
+def _profile_window(L, abi):
+    out = {}
+    for name, kid in abi.KERNEL_IDS.items():
+        cnt, ms = ctypes.c_int64(), ctypes.c_double()
+        abi.check(L.sdf_profile_read(kid, ctypes.byref(cnt), ctypes.byref(ms)))
+        if cnt.value:
+            out[name] = {"launches": cnt.value, "ms": ms.value}
+    return out
+
+
+def run_grad_leg(dev, peak_instr_rate, steps: int = 3):
+    """Differentiation configuration: N = 65,536 perturbed ellipsoid, Q = 1e6
+    uniform queries; forward + d phi / dx (sdf_query_grad) and the parameter
+    backward (sdf_backward_params), each timed on the device."""
+    import torch
+
+    import paper_2607_16946_b300 as ptsdf
+    from paper_2607_16946_b300 import _abi
+    import synth
+    L = _abi.lib()
+    p, n, a = synth.ellipsoid(65536, 1004, axes=(1.0, 0.6, 0.4), perturb=0.05)
+    cl = ptsdf.Cloud(p, n, a)
+    x = torch.as_tensor(synth.uniform_queries(1_000_000, 1004, -1.5, 1.5), dtype=torch.float32, device=dev)
+    G = torch.ones(x.shape[0], device=dev)
+    for _ in range(2):
+        _, _, saved = cl.query_grad(x)
+        cl.backward_params(x, saved, G)
+    torch.cuda.synchronize(dev)
+    L.sdf_profile_enable(1)
+    for _ in range(steps):
+        _, _, saved = cl.query_grad(x)
+        cl.backward_params(x, saved, G)
+    torch.cuda.synchronize(dev)
+    L.sdf_profile_enable(0)
+    prof = _profile_window(L, _abi)
+    pairs = x.shape[0] * 65536
+    fg = prof["fwd_grad"]["ms"] / prof["fwd_grad"]["launches"] / 1e3
+    bw = prof["bwd_params"]["ms"] / prof["bwd_params"]["launches"] / 1e3
+    pre = prof.get("prepass", {"ms": 0.0, "launches": 1})
+    return {"workload": "differentiation: ellipsoid N=65536 (axes 1/0.6/0.4, curvatures x(1+0.05N(0,1))), "
+                        "Q=1e6 uniform in [-1.5,1.5]^3; FP32",
+            "fwd_grad_gpairs_s": pairs / fg / 1e9, "bwd_params_gpairs_s": pairs / bw / 1e9,
+            "step_ms": (fg + bw) * 1e3 + pre["ms"] / pre["launches"],
+            "kernels": prof,
+            "roofline_fwd_grad": {"bound": "alu", "achieved": pairs / fg / 1e9,
+                                  "peak": peak_instr_rate / GRAD_INSTR_PER_PAIR, "unit": UNIT,
+                                  "frac": pairs / fg / 1e9 / (peak_instr_rate / GRAD_INSTR_PER_PAIR)},
+            "roofline_bwd_params": {"bound": "alu", "achieved": pairs / bw / 1e9,
+                                    "peak": peak_instr_rate / BWD_INSTR_PER_PAIR, "unit": UNIT,
+                                    "frac": pairs / bw / 1e9 / (peak_instr_rate / BWD_INSTR_PER_PAIR)}}
+
+
+def run_trace_leg(dev, steps: int = 2):
+    """Sphere-tracing configuration: N = 262,144 noisy superquadric, 512 x 512
+    pinhole rays from distance 3, <= 48 steps, eps = 1e-4, t_max = 6, normals
+    at hits; pairs = sum over steps of live rays x N."""
+    import torch
+
+    import paper_2607_16946_b300 as ptsdf
+    from paper_2607_16946_b300 import _abi
+    import synth
+    L = _abi.lib()
+    p, n, a = synth.superquadric(262_144, 1003)
+    cl = ptsdf.Cloud(p, n, a)
+    org, dirs = synth.camera_rays(512, 512, 1003)
+    org = torch.as_tensor(org, dtype=torch.float32, device=dev)
+    dirs = torch.as_tensor(dirs, dtype=torch.float32, device=dev)
+    t, s, nrm = cl.trace(org, dirs)
+    torch.cuda.synchronize(dev)
+    L.sdf_profile_enable(1)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        t, s, nrm = cl.trace(org, dirs)
+    torch.cuda.synchronize(dev)
+    wall = (time.perf_counter() - t0) / steps
+    L.sdf_profile_enable(0)
+    prof = _profile_window(L, _abi)
+    evals = int(s.sum().item())                  # query evaluations = sum over steps of live rays
+    pairs = evals * 262_144
+    dev_ms = sum(v["ms"] for v in prof.values()) / steps
+    return {"workload": "sphere tracing: superquadric N=262144 (e1=0.5, e2=2, axes 1/0.7/0.5, noise 0.003), "
+                        "512x512 rays, 48 steps, eps 1e-4, t_max 6, normals at hits; FP32",
+            "gpairs_s": pairs / wall / 1e9, "device_gpairs_s": pairs / (dev_ms / 1e3) / 1e9,
+            "ms_per_image": wall * 1e3, "rays": int(s.numel()), "hits": int((t >= 0).sum().item()),
+            "evaluations": evals, "kernels": prof}
+
+
+def run_mixed_leg(dev, cloud, x, phi, points, normals, params, steps: int = 2):
+    """The dense-grid step with packed-half weights (SDF_F16X2, SDF_BF16X2):
+    device Gpairs/s, and the error against the FP64 oracle on 4,096 seeded
+    grid nodes, relative to the AABB diagonal, next to FP32's."""
+    import torch
+
+    import oracle
+    import synth
+    from paper_2607_16946_b300 import _abi
+    rng = np.random.Generator(np.random.PCG64(SEED + 11))
+    idx = rng.integers(0, GRID_RES ** 3, size=4096)
+    ref = oracle.Cloud(points, normals, params).phi(synth.grid_query_index(idx, GRID_RES))
+    diag = float(np.linalg.norm(points.max(0) - points.min(0)))
+    out = {}
+    for name, code in (("fp32", _abi.SDF_F32), ("f16x2", _abi.SDF_F16X2), ("bf16x2", _abi.SDF_BF16X2)):
+        cloud.query(x, out=phi, precision=code)
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            cloud.query(x, out=phi, precision=code)
+        e1.record()
+        torch.cuda.synchronize(dev)
+        s = e0.elapsed_time(e1) / 1e3 / steps
+        err = np.abs(phi[torch.as_tensor(idx, device=dev)].double().cpu().numpy() - ref) / diag
+        out[name] = {"value": x.shape[0] * N_POINTS / s / 1e9, "unit": UNIT, "ms_per_step": s * 1e3,
+                     "err_max_rel_diag": float(err.max()), "err_p99_rel_diag": float(np.quantile(err, 0.99))}
+    out["note"] = ("packed-half exp2 of a lane's two weights; distances, torus SDF and sums in FP32; "
+                   "error = |phi - phi_oracle| / AABB diagonal on 4096 seeded grid nodes")
+    return out
+
+
 def run_reference(args, rank, world):
     """The oracle as it stands on the host cores, same workload and metric."""
     if rank != 0:
@@ -300,6 +524,13 @@ def run_ours(args, rank, world, local):
         "clocks": cs,
         "outputs_finite": finite,
     }
+    if world == 1 and not args.no_extra_legs:
+        line["mixed"] = run_mixed_leg(dev, cloud, x, phi, p, n, a)
+        line["grad"] = run_grad_leg(dev, sms * fmax * 1e6 * THREAD_INSTR_PER_SM_CLK / 1e9)
+        line["trace"] = run_trace_leg(dev)
+    if world == 1 and args.serve_requests > 0:
+        del hx, hphi
+        line["served"] = run_served(args, dev, value)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(p, n, a)
     print(json.dumps(line), flush=True)
@@ -312,6 +543,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true", help="omit the CPU oracle leg")
+    ap.add_argument("--serve-requests", type=int, default=300, help="requests of the served leg (0: skip)")
+    ap.add_argument("--no-extra-legs", action="store_true", help="omit the gradient and tracing legs")
+    ap.add_argument("--serve-clouds", type=int, default=32)
+    ap.add_argument("--serve-load", type=float, default=0.7, help="offered load as a fraction of capacity")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

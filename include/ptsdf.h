@@ -57,6 +57,11 @@ typedef enum {
     SDF_EDEVICE = 6    /* a kernel reported a fault through the device status word */
 } sdf_status;
 
+/* Arithmetic of the weights exp(-lambda_x (d_i - d_min)) in sdf_query (and
+ * the calls built on it).  SDF_F32: FP32 throughout.  SDF_F16X2 / SDF_BF16X2:
+ * the exponents of a lane's two queries are packed into one register of
+ * half / bfloat16 values and evaluated by one packed exp2; distances, the
+ * torus SDF and all sums stay FP32.  Gradients are FP32 only. */
 typedef enum { SDF_F32 = 0, SDF_F16X2 = 1, SDF_BF16X2 = 2 } sdf_precision;
 
 typedef enum {
@@ -232,6 +237,74 @@ PTSDF_API sdf_status sdf_combine(int32_t op, const float* d_a, const float* d_b,
  * ------------------------------------------------------------------------- */
 PTSDF_API sdf_status sdf_query_noalloc(sdf_cloud cloud, const float* d_x, int64_t q, float* d_phi,
                                        const sdf_query_opts* opts, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Serving: a request loop over several resident clouds (Sec. 6 uses of the
+ * SDF: query batches of uneven size, sphere-tracing steps, offsets and
+ * Booleans).  A scheduler thread admits queued requests in arrival order
+ * when a slot (max_inflight) and enough of the memory budget are free and
+ * launches each at once on one of n_streams streams, so work that arrives
+ * while other requests run overlaps with them on the device.  A request's
+ * result depends only on its own inputs, cloud and options: it is the same
+ * alone and in a mix.
+ * ------------------------------------------------------------------------- */
+typedef struct sdf_server_s* sdf_server;
+
+typedef struct {
+    int64_t mem_budget_bytes;   /* device bytes the server may hold for staging and scratch */
+    int32_t max_inflight;       /* requests on the GPU at once (slots) */
+    int32_t n_streams;          /* CUDA streams the requests are spread over */
+    int32_t device;             /* CUDA device of the clouds */
+} sdf_serve_config;
+
+typedef enum {
+    SDF_REQ_QUERY = 0,       /* out[q]      = phi(x) - offset */
+    SDF_REQ_GRAD = 1,        /* out[4q]     = phi (q floats) then grad phi (q x 3) */
+    SDF_REQ_UNION = 2,       /* out[q]      = min(phi_a, phi_b) */
+    SDF_REQ_INTERSECT = 3,   /* out[q]      = max(phi_a, phi_b) */
+    SDF_REQ_DIFFERENCE = 4,  /* out[q]      = max(phi_a, -phi_b) */
+    SDF_REQ_TRACE_STEP = 5   /* out[q]      = phi(x + t dirs) - offset (one sphere-tracing step) */
+} sdf_request_kind;
+
+typedef struct {
+    int32_t kind;            /* sdf_request_kind */
+    int32_t cloud_id;        /* from sdf_serve_register */
+    int32_t cloud_id_b;      /* second cloud of a Boolean */
+    int32_t host_buffers;    /* 1: x, dirs, t, out are host pointers (staged by the server); 0: device */
+    const float* x;          /* q x 3 positions (TRACE_STEP: ray origins) */
+    const float* dirs;       /* TRACE_STEP: q x 3 directions; else NULL */
+    const float* t;          /* TRACE_STEP: q ray parameters; else NULL */
+    int64_t q;               /* >= 1 */
+    float* out;              /* see sdf_request_kind */
+    sdf_query_opts opts;
+} sdf_request;
+
+typedef struct {
+    int32_t status;          /* sdf_status of the request */
+    int32_t reserved;
+    int64_t arrive_ns;       /* host steady-clock times: submit, */
+    int64_t admit_ns;        /*   admission, */
+    int64_t start_ns;        /*   launch, */
+    int64_t done_ns;         /*   completion of the request's last operation */
+    double device_ms;        /* CUDA-event time of the request's work on its stream */
+} sdf_request_stats;
+
+/* Creates a server (and its scheduler thread and streams). */
+PTSDF_API sdf_status sdf_serve_create(const sdf_serve_config* cfg, sdf_server* out);
+/* Makes a built cloud addressable by requests; the cloud must outlive the server. */
+PTSDF_API sdf_status sdf_serve_register(sdf_server srv, sdf_cloud cloud, int32_t* cloud_id);
+/* Queues a request (any host thread).  Buffers must stay valid until the
+ * request is polled.  SDF_ENOMEM if the request alone exceeds the memory
+ * budget; SDF_EINVAL for bad arguments; SDF_EBUSY after shutdown began. */
+PTSDF_API sdf_status sdf_serve_submit(sdf_server srv, const sdf_request* req, uint64_t* ticket);
+/* Waits up to timeout_us (negative: without limit) for a request;
+ * SDF_ETIMEOUT if it is not finished (the ticket stays valid), else the
+ * request's status (the ticket is released) and its timestamps in *stats. */
+PTSDF_API sdf_status sdf_serve_poll(sdf_server srv, uint64_t ticket, int64_t timeout_us, sdf_request_stats* stats);
+/* Current queue length, requests in flight and bytes charged to the budget. */
+PTSDF_API sdf_status sdf_serve_stats(sdf_server srv, int32_t* queued, int32_t* inflight, int64_t* mem_in_use);
+/* Finishes every queued request, joins the scheduler and frees the server. */
+PTSDF_API sdf_status sdf_serve_shutdown(sdf_server srv);
 
 /* ---------------------------------------------------------------------------
  * Kernel timing (a tracing aid, not part of the method).  While enabled,

@@ -51,6 +51,12 @@ SIGNATURES = {
     "sdf_trace": (ctypes.c_int, [_P, _P, _P, _I64, _I32, _F, _F, _P, _P, _P, ctypes.POINTER(sdf_query_opts), _P]),
     "sdf_combine": (ctypes.c_int, [_I32, _P, _P, _I64, _P, _P]),
     "sdf_device_status": (ctypes.c_int, [_P, _P, ctypes.POINTER(_I32)]),
+    "sdf_serve_create": (ctypes.c_int, [_P, ctypes.POINTER(_P)]),
+    "sdf_serve_register": (ctypes.c_int, [_P, _P, ctypes.POINTER(_I32)]),
+    "sdf_serve_submit": (ctypes.c_int, [_P, _P, ctypes.POINTER(ctypes.c_uint64)]),
+    "sdf_serve_poll": (ctypes.c_int, [_P, ctypes.c_uint64, _I64, _P]),
+    "sdf_serve_stats": (ctypes.c_int, [_P, ctypes.POINTER(_I32), ctypes.POINTER(_I32), ctypes.POINTER(_I64)]),
+    "sdf_serve_shutdown": (ctypes.c_int, [_P]),
     "sdf_profile_enable": (ctypes.c_int, [_I32]),
     "sdf_profile_read": (ctypes.c_int, [_I32, ctypes.POINTER(_I64), ctypes.POINTER(ctypes.c_double)]),
     "sdf_kernel_name": (ctypes.c_char_p, [_I32]),

@@ -27,7 +27,8 @@ sdf_status cuda_error(cudaError_t e, const char* what) {
 sdf_status check_opts(const sdf_query_opts& o, const char* fn) {
     if (o.lambda_mode != SDF_LAMBDA_GLOBAL && o.lambda_mode != SDF_LAMBDA_FIXED)
         return set_error(SDF_EINVAL, std::string(fn) + ": unknown lambda_mode");
-    if (o.precision != SDF_F32) return set_error(SDF_EINVAL, std::string(fn) + ": unsupported precision");
+    if (o.precision != SDF_F32 && o.precision != SDF_F16X2 && o.precision != SDF_BF16X2)
+        return set_error(SDF_EINVAL, std::string(fn) + ": unknown precision");
     if (!(o.C > 0.f) || !std::isfinite(o.C)) return set_error(SDF_EINVAL, std::string(fn) + ": C must be > 0");
     if (o.lambda_mode == SDF_LAMBDA_FIXED && (!(o.fixed_lambda >= 0.f) || !std::isfinite(o.fixed_lambda)))
         return set_error(SDF_EINVAL, std::string(fn) + ": fixed_lambda must be >= 0");
@@ -86,6 +87,7 @@ extern "C" sdf_status sdf_query_grad(sdf_cloud cloud, const float* d_x, int64_t 
     const sdf_query_opts o = resolve_opts(opts);
     const sdf_status s = check_opts(o, "sdf_query_grad");
     if (s != SDF_OK) return s;
+    if (o.precision != SDF_F32) return set_error(SDF_EINVAL, "sdf_query_grad: gradients are computed in FP32 only");
     if (q == 0) return SDF_OK;
     if (!d_x || !d_phi || !d_grad) return set_error(SDF_EINVAL, "sdf_query_grad: NULL buffer");
     return launch_query_grad(*reinterpret_cast<const Cloud*>(cloud), d_x, q, d_phi, d_grad, d_saved, o,
@@ -101,6 +103,8 @@ extern "C" sdf_status sdf_backward_params(sdf_cloud cloud, const float* d_x, int
     const sdf_query_opts o = resolve_opts(opts);
     const sdf_status s = check_opts(o, "sdf_backward_params");
     if (s != SDF_OK) return s;
+    if (o.precision != SDF_F32)
+        return set_error(SDF_EINVAL, "sdf_backward_params: gradients are computed in FP32 only");
     const Cloud& c = *reinterpret_cast<const Cloud*>(cloud);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if (q == 0) {

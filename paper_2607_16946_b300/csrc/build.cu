@@ -10,10 +10,13 @@
 //                   and the slot -> point permutation.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <utility>
+#include <vector>
 
 #include "device_common.cuh"
 #include "fit_math.cuh"
@@ -200,10 +203,70 @@ using namespace ptsdf;
 
 namespace {
 
+// Spreads the low 10 bits of v to every third bit.
+uint32_t spread3(uint32_t v) {
+    v &= 0x3ffu;
+    v = (v | (v << 16)) & 0x030000ffu;
+    v = (v | (v << 8)) & 0x0300f00fu;
+    v = (v | (v << 4)) & 0x030c30c3u;
+    v = (v | (v << 2)) & 0x09249249u;
+    return v;
+}
+
+// Orders the prepass entries (-2 p', |p'|^2) along a 30-bit Morton curve of p'
+// and returns one bounding sphere (centre p'_c, radius) per kSphereTile
+// consecutive entries.  Radii are inflated by 1e-5 of the AABB diagonal plus a
+// relative 1e-6 so that FP32 rounding of the query-to-centre distance never
+// excludes a tile that holds an extreme point.
+void morton_order_and_spheres(const std::vector<float4>& in, const float* box, float diag,
+                              std::vector<float4>& out, std::vector<float4>& spheres) {
+    const size_t n = in.size();
+    const double half[3] = {0.5 * (box[3] - box[0]), 0.5 * (box[4] - box[1]), 0.5 * (box[5] - box[2])};
+    std::vector<std::pair<uint32_t, uint32_t>> key(n);
+    for (size_t i = 0; i < n; ++i) {
+        const double p[3] = {-0.5 * in[i].x, -0.5 * in[i].y, -0.5 * in[i].z};
+        uint32_t cell[3];
+        for (int k = 0; k < 3; ++k) {
+            const double u = half[k] > 0.0 ? (p[k] + half[k]) / (2.0 * half[k]) : 0.5;
+            const double cl = u < 0.0 ? 0.0 : (u > 1.0 ? 1.0 : u);
+            cell[k] = (uint32_t)(cl * 1023.0);
+        }
+        key[i] = {spread3(cell[0]) | (spread3(cell[1]) << 1) | (spread3(cell[2]) << 2), (uint32_t)i};
+    }
+    std::sort(key.begin(), key.end());
+    out.resize(n);
+    for (size_t i = 0; i < n; ++i) out[i] = in[key[i].second];
+    const size_t ns = (n + kSphereTile - 1) / kSphereTile;
+    spheres.resize(ns);
+    for (size_t t = 0; t < ns; ++t) {
+        const size_t a = t * kSphereTile, b = std::min(n, a + kSphereTile);
+        double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+        for (size_t i = a; i < b; ++i) {
+            const double p[3] = {-0.5 * out[i].x, -0.5 * out[i].y, -0.5 * out[i].z};
+            for (int k = 0; k < 3; ++k) {
+                lo[k] = std::min(lo[k], p[k]);
+                hi[k] = std::max(hi[k], p[k]);
+            }
+        }
+        const double cc[3] = {0.5 * (lo[0] + hi[0]), 0.5 * (lo[1] + hi[1]), 0.5 * (lo[2] + hi[2])};
+        double r2 = 0.0, cn = 0.0;
+        for (size_t i = a; i < b; ++i) {
+            const double p[3] = {-0.5 * out[i].x, -0.5 * out[i].y, -0.5 * out[i].z};
+            const double d2 = (p[0] - cc[0]) * (p[0] - cc[0]) + (p[1] - cc[1]) * (p[1] - cc[1]) +
+                              (p[2] - cc[2]) * (p[2] - cc[2]);
+            r2 = std::max(r2, d2);
+        }
+        cn = std::sqrt(cc[0] * cc[0] + cc[1] * cc[1] + cc[2] * cc[2]);
+        const double r = std::sqrt(r2) + 1e-5 * diag + 1e-6 * (cn + diag);
+        spheres[t] = make_float4((float)cc[0], (float)cc[1], (float)cc[2], (float)r);
+    }
+}
+
 void free_cloud(Cloud* c) {
     if (!c) return;
     cudaFree(c->rec);
     cudaFree(c->pre);
+    cudaFree(c->spheres);
     cudaFree(c->perm);
     cudaFree(c->src_points);
     cudaFree(c->src_normals);
@@ -309,6 +372,22 @@ extern "C" sdf_status sdf_build(const float* d_points, const float* d_normals, c
                                             c->rec, c->pre, c->perm);
     PTSDF_TRY(cudaGetLastError(), "sdf_build: k_partition launch");
     PTSDF_TRY(cudaStreamSynchronize(st), "sdf_build: sync");
+    {
+        // Morton order of the prepass array and one bounding sphere per
+        // kSphereTile points (host side: O(N log N) once per cloud)
+        std::vector<float4> hp((size_t)n);
+        PTSDF_TRY(cudaMemcpy(hp.data(), c->pre, (size_t)n * sizeof(float4), cudaMemcpyDeviceToHost),
+                  "sdf_build: prepass download");
+        std::vector<float4> sorted;
+        std::vector<float4> spheres;
+        morton_order_and_spheres(hp, c->aabb, c->aabb_diag, sorted, spheres);
+        c->n_spheres = (int64_t)spheres.size();
+        PTSDF_TRY(cudaMemcpy(c->pre, sorted.data(), (size_t)n * sizeof(float4), cudaMemcpyHostToDevice),
+                  "sdf_build: prepass upload");
+        PTSDF_TRY(cudaMalloc(&c->spheres, spheres.size() * sizeof(float4)), "sdf_build: sphere alloc");
+        PTSDF_TRY(cudaMemcpy(c->spheres, spheres.data(), spheres.size() * sizeof(float4), cudaMemcpyHostToDevice),
+                  "sdf_build: sphere upload");
+    }
 #undef PTSDF_TRY
     cudaFree(box);
     cudaFree(rec_tmp);

@@ -121,7 +121,7 @@ __device__ __forceinline__ QueryLam query_lambda(const QueryArgs& a, const float
     QueryLam r;
     float2 d2 = a.d2[qq];
     int32_t far = a.far ? a.far[qq] : 0;
-    for (int c = 1; c < a.split; ++c) {
+    for (int c = 1; c < a.pre_split; ++c) {
         const float2 v = a.d2[(size_t)c * a.q + qq];
         if (v.x > d2.x) {
             d2.x = v.x;
@@ -280,10 +280,12 @@ sdf_status launch_query_grad(const Cloud& c, const float* d_x, int64_t q, float*
         return e == cudaErrorMemoryAllocation ? set_error(SDF_ENOMEM, "sdf_query_grad: scratch")
                                               : cuda_error(e, "sdf_query_grad: scratch");
     };
-    cudaError_t e = cudaMallocAsync(&a.d2, (size_t)p.split * q * sizeof(float2), st);
+    const bool pruned = use_pruned_prepass(c, p, o);
+    a.pre_split = pruned ? 1 : p.split;
+    cudaError_t e = cudaMallocAsync(&a.d2, (size_t)a.pre_split * q * sizeof(float2), st);
     if (e != cudaSuccess) return oom(e);
     if (o.lambda_mode == SDF_LAMBDA_GLOBAL) {
-        e = cudaMallocAsync(&a.far, (size_t)p.split * q * sizeof(int32_t), st);
+        e = cudaMallocAsync(&a.far, (size_t)a.pre_split * q * sizeof(int32_t), st);
         if (e != cudaSuccess) return oom(e);
     }
     if (p.split > 1) {
@@ -294,7 +296,10 @@ sdf_status launch_query_grad(const Cloud& c, const float* d_x, int64_t q, float*
     const dim3 pre_grid((unsigned)p.pre_qblocks, (unsigned)p.split);
     {
         ProfRange pr(SDF_K_PREPASS, st);
-        if (o.lambda_mode == SDF_LAMBDA_GLOBAL)
+        if (pruned)
+            k_prepass_pruned<true><<<(unsigned)p.pre_qblocks, kPrunedThreads, 0, st>>>(c.pre, c.spheres, c.n,
+                                                                                    c.n_spheres, a);
+        else if (o.lambda_mode == SDF_LAMBDA_GLOBAL)
             k_prepass<SDF_LAMBDA_GLOBAL, true><<<pre_grid, kThreads, kStages * kPreBytes, st>>>(
                 c.pre, c.n, c.pre_tiles, p.pre_tiles_per_chunk, a, c.status);
         else

@@ -32,9 +32,12 @@ namespace ptsdf {
 //    r3 = (2 zeta n*.x, 2 zeta n*.y, 2 zeta n*.z, 0)
 // with sgn(0) := -1 (a zero curvature counts as convex).
 //
-// A second array holds, per point in the same partitioned order (compact,
-// padded to kPreTile), float4(-2 p', |p'|^2) with p' = p - (bounding-box
-// centre), for the d_max / d_min prepass.
+// A second array holds, per point, float4(-2 p', |p'|^2) with
+// p' = p - (bounding-box centre), for the d_max / d_min prepass.  It is
+// ordered along a Morton (Z-order) curve of p and padded to kPreTile; every
+// kSphereTile consecutive entries have a bounding sphere (centre p'_c,
+// radius), used to skip tiles that cannot hold a query's farthest or nearest
+// point.
 // Tuning constants can be overridden at compile time (-DPTSDF_TILE_RECS=...,
 // -DPTSDF_QPT=..., -DPTSDF_STAGES=...) to build variants for a sweep.
 #ifndef PTSDF_TILE_RECS
@@ -46,9 +49,13 @@ namespace ptsdf {
 #ifndef PTSDF_STAGES
 #define PTSDF_STAGES 4
 #endif
+#ifndef PTSDF_UNROLL
+#define PTSDF_UNROLL 2
+#endif
 constexpr int kTileRecs = PTSDF_TILE_RECS;   // records per main-loop tile (32 x 64 B = 2 KB)
 constexpr int kRecFloats = 16;
 constexpr int kPreTile = 256;        // points per prepass tile (4 KB)
+constexpr int kSphereTile = 64;      // points per bounding sphere of the pruned prepass
 
 struct Cloud {
     int device = 0;
@@ -60,6 +67,8 @@ struct Cloud {
     float aabb[6] = {0, 0, 0, 0, 0, 0};
     float4* rec = nullptr;           // (tiles_direct + tiles_kappa) * kTileRecs * 4 float4
     float4* pre = nullptr;           // pre_tiles * kPreTile float4
+    float4* spheres = nullptr;       // n_spheres x (centre', radius)
+    int64_t n_spheres = 0;
     int32_t* perm = nullptr;         // record slot -> original point index (-1 for padding)
     float* src_points = nullptr;     // copies of the inputs (N x 3, N x 3, N x 6), kept for
     float* src_normals = nullptr;    // the parameter gradient's chain through the fit
@@ -86,6 +95,7 @@ constexpr int kConsumerWarps = 8;
 constexpr int kQueriesPerThread = PTSDF_QPT;
 constexpr int kQueriesPerCta = kConsumerWarps * 32 * kQueriesPerThread;   // 512
 constexpr int kStages = PTSDF_STAGES;
+constexpr int kUnrollPts = PTSDF_UNROLL;      // points per unrolled step of the pair loop
 
 // queries_per_cta: queries one CTA of the main kernel holds (the prepass
 // always uses kQueriesPerCta).

@@ -49,22 +49,62 @@ struct QState {
     float w, s;        // tile partials
 };
 
-template <bool KAPPA>
+// Weights of two queries at once.  SDF_F32: two FP32 exp2 (one MUFU each).
+// SDF_F16X2 / SDF_BF16X2: the two exponents are packed into one 32-bit
+// register of half / bfloat16 values and evaluated by one packed exp2 (the
+// only packed-half MUFU operation of sm_103a besides tanh), then widened back
+// to FP32 for the FP32 accumulation.
+template <int PREC>
+__device__ __forceinline__ void weights2(float a0, float a1, float& w0, float& w1) {
+    if (PREC == SDF_F16X2) {
+        asm("{\n\t.reg .b32 t;\n\t.reg .f16 lo, hi;\n\t"
+            "cvt.rn.f16x2.f32 t, %2, %3;\n\t"
+            "ex2.approx.f16x2 t, t;\n\t"
+            "mov.b32 {lo, hi}, t;\n\t"
+            "cvt.f32.f16 %0, hi;\n\t"
+            "cvt.f32.f16 %1, lo;\n\t}"
+            : "=f"(w0), "=f"(w1)
+            : "f"(a0), "f"(a1));
+    } else if (PREC == SDF_BF16X2) {
+        uint32_t t;
+        asm("{\n\t.reg .b32 u;\n\t"
+            "cvt.rn.bf16x2.f32 u, %1, %2;\n\t"
+            "ex2.approx.ftz.bf16x2 %0, u;\n\t}"
+            : "=r"(t)
+            : "f"(a0), "f"(a1));
+        w0 = __uint_as_float(t & 0xffff0000u);    // high half: a0
+        w1 = __uint_as_float(t << 16);            // low half: a1
+    } else {
+        w0 = ex2_mufu(a0);
+        w1 = ex2_mufu(a1);
+    }
+}
+
+template <bool KAPPA, int PREC>
 __device__ __forceinline__ void pair_tile(const float4* __restrict__ tile, int cnt, QState (&qs)[kQueriesPerThread]) {
-#pragma unroll 2
+    static_assert(kQueriesPerThread % 2 == 0, "queries are paired for the packed weights");
+#pragma unroll kUnrollPts
     for (int j = 0; j < cnt; ++j) {
         const float4 r0 = tile[4 * j], r1 = tile[4 * j + 1], r2 = tile[4 * j + 2];
         float4 r3;
         if (KAPPA) r3 = tile[4 * j + 3];
 #pragma unroll
-        for (int k = 0; k < kQueriesPerThread; ++k) {
-            const float dx = qs[k].x - r0.x, dy = qs[k].y - r0.y, dz = qs[k].z - r0.z;
-            const float d = sqrt_mufu(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
-            const float g = KAPPA ? g_kappa(qs[k].x, qs[k].y, qs[k].z, r0, r1, r2, r3)
-                                  : g_direct(qs[k].x, qs[k].y, qs[k].z, r1, r2, r0.w);
-            const float w = ex2_mufu(fmaf(-qs[k].L, d, qs[k].A0));
-            qs[k].w += w;
-            qs[k].s = fmaf(w, g, qs[k].s);
+        for (int k = 0; k < kQueriesPerThread; k += 2) {
+            float arg[2], g[2];
+#pragma unroll
+            for (int m = 0; m < 2; ++m) {
+                const QState& s = qs[k + m];
+                const float dx = s.x - r0.x, dy = s.y - r0.y, dz = s.z - r0.z;
+                const float d = sqrt_mufu(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+                g[m] = KAPPA ? g_kappa(s.x, s.y, s.z, r0, r1, r2, r3) : g_direct(s.x, s.y, s.z, r1, r2, r0.w);
+                arg[m] = fmaf(-s.L, d, s.A0);
+            }
+            float w0, w1;
+            weights2<PREC>(arg[0], arg[1], w0, w1);
+            qs[k].w += w0;
+            qs[k].s = fmaf(w0, g[0], qs[k].s);
+            qs[k + 1].w += w1;
+            qs[k + 1].s = fmaf(w1, g[1], qs[k + 1].s);
         }
     }
 }
@@ -72,6 +112,7 @@ __device__ __forceinline__ void pair_tile(const float4* __restrict__ tile, int c
 // --------------------------------------------------------------------------
 // Forward pass
 // --------------------------------------------------------------------------
+template <int PREC>
 __global__ void __launch_bounds__(kThreads) k_fwd(const float4* __restrict__ rec, int64_t n_direct, int64_t n_kappa,
                                                   int64_t tiles_direct, int64_t tiles_total, int64_t tiles_per_chunk,
                                                   QueryArgs a, int32_t* status) {
@@ -100,7 +141,7 @@ __global__ void __launch_bounds__(kThreads) k_fwd(const float4* __restrict__ rec
         qs[k].y = a.x[3 * qq + 1];
         qs[k].z = a.x[3 * qq + 2];
         float2 d2 = a.d2[qq];
-        for (int c = 1; c < a.split; ++c) {
+        for (int c = 1; c < a.pre_split; ++c) {
             const float2 v = a.d2[(size_t)c * a.q + qq];
             d2.x = fmaxf(d2.x, v.x);
             d2.y = fminf(d2.y, v.y);
@@ -128,9 +169,9 @@ __global__ void __launch_bounds__(kThreads) k_fwd(const float4* __restrict__ rec
 #pragma unroll
         for (int k = 0; k < kQueriesPerThread; ++k) qs[k].w = qs[k].s = 0.f;
         if (kappa)
-            pair_tile<true>(tile, cnt, qs);
+            pair_tile<true, PREC>(tile, cnt, qs);
         else
-            pair_tile<false>(tile, cnt, qs);
+            pair_tile<false, PREC>(tile, cnt, qs);
         // blocked summation: tile partials are added to the totals once per
         // tile, which keeps the FP32 rounding of long sums small
 #pragma unroll
@@ -208,7 +249,11 @@ sdf_status launch_query(const Cloud& c, const float* d_x, int64_t q, float* d_ph
     a.cx = 0.5f * (c.aabb[0] + c.aabb[3]);
     a.cy = 0.5f * (c.aabb[1] + c.aabb[4]);
     a.cz = 0.5f * (c.aabb[2] + c.aabb[5]);
-    cudaError_t e = cudaMallocAsync(&a.d2, (size_t)p.split * q * sizeof(float2), st);
+    // the pruned prepass keeps one query block per CTA with no point split, so
+    // it is used once there are enough query blocks to fill the GPU
+    const bool pruned = use_pruned_prepass(c, p, o);
+    a.pre_split = pruned ? 1 : p.split;
+    cudaError_t e = cudaMallocAsync(&a.d2, (size_t)a.pre_split * q * sizeof(float2), st);
     if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? set_error(SDF_ENOMEM, "sdf_query: scratch")
                                                                 : cuda_error(e, "sdf_query: scratch");
     if (p.split > 1) {
@@ -223,7 +268,10 @@ sdf_status launch_query(const Cloud& c, const float* d_x, int64_t q, float* d_ph
     const dim3 pre_grid((unsigned)p.pre_qblocks, (unsigned)p.split);
     {
         ProfRange pr(SDF_K_PREPASS, st);
-        if (o.lambda_mode == SDF_LAMBDA_GLOBAL)
+        if (pruned)
+            k_prepass_pruned<false><<<(unsigned)p.pre_qblocks, kPrunedThreads, 0, st>>>(c.pre, c.spheres, c.n,
+                                                                                     c.n_spheres, a);
+        else if (o.lambda_mode == SDF_LAMBDA_GLOBAL)
             k_prepass<SDF_LAMBDA_GLOBAL><<<pre_grid, kThreads, kStages * kPreBytes, st>>>(
                 c.pre, c.n, c.pre_tiles, p.pre_tiles_per_chunk, a, c.status);
         else
@@ -233,9 +281,11 @@ sdf_status launch_query(const Cloud& c, const float* d_x, int64_t q, float* d_ph
     }
     if (e == cudaSuccess) {
         ProfRange pr(SDF_K_FWD, st);
-        k_fwd<<<grid, kThreads, kStages * kTileBytes, st>>>(c.rec, c.n_direct, c.n_kappa, c.tiles_direct,
-                                                           c.tiles_direct + c.tiles_kappa, p.tiles_per_chunk, a,
-                                                           c.status);
+        auto kern = o.precision == SDF_F16X2 ? k_fwd<SDF_F16X2> : o.precision == SDF_BF16X2 ? k_fwd<SDF_BF16X2>
+                                                                                            : k_fwd<SDF_F32>;
+        kern<<<grid, kThreads, kStages * kTileBytes, st>>>(c.rec, c.n_direct, c.n_kappa, c.tiles_direct,
+                                                          c.tiles_direct + c.tiles_kappa, p.tiles_per_chunk, a,
+                                                          c.status);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess && p.split > 1) {
@@ -344,6 +394,7 @@ extern "C" sdf_status sdf_query_noalloc(sdf_cloud cloud, const float* d_x, int64
     a.lam = o.fixed_lambda;
     a.offset = o.offset;
     a.far = nullptr;
+    a.pre_split = p.split;
     a.cx = 0.5f * (c.aabb[0] + c.aabb[3]);
     a.cy = 0.5f * (c.aabb[1] + c.aabb[4]);
     a.cz = 0.5f * (c.aabb[2] + c.aabb[5]);
@@ -361,7 +412,7 @@ extern "C" sdf_status sdf_query_noalloc(sdf_cloud cloud, const float* d_x, int64
             c.pre, c.n, c.pre_tiles, p.pre_tiles_per_chunk, a, c.status);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) {
-        k_fwd<<<grid, kThreads, kStages * kTileBytes, st>>>(c.rec, c.n_direct, c.n_kappa, c.tiles_direct,
+        k_fwd<SDF_F32><<<grid, kThreads, kStages * kTileBytes, st>>>(c.rec, c.n_direct, c.n_kappa, c.tiles_direct,
                                                            c.tiles_direct + c.tiles_kappa, p.tiles_per_chunk, a,
                                                            c.status);
         e = cudaGetLastError();

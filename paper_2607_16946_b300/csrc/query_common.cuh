@@ -27,7 +27,8 @@ struct QueryArgs {
     float2* d2;              // split x Q prepass partials (max, min of |x - p|^2)
     int32_t* far;            // split x Q index of the farthest point (prepass order), or null
     float cx, cy, cz;        // cloud bounding-box centre (prepass coordinates)
-    int split;
+    int split;               // point chunks of the main kernel
+    int pre_split;           // prepass partials per query (1 for the pruned prepass)
     int mode;                // sdf_lambda_mode
     float C;
     float lam;               // fixed lambda
@@ -121,6 +122,98 @@ __global__ void __launch_bounds__(kThreads) k_prepass(const float4* __restrict__
             if (ARGMAX) a.far[(size_t)chunk * a.q + qi[k]] = far[k];
         }
     }
+}
+
+// --------------------------------------------------------------------------
+// Pruned prepass (GLOBAL lambda): the same d_max / d_min as k_prepass, with
+// tiles that cannot hold either extreme skipped.  For every 64-point tile t
+// with bounding sphere (c_t, r_t) and a query x, all its points lie between
+// |x - c_t| - r_t and |x - c_t| + r_t.  Hence
+//   LB = max_t (|x - c_t| - r_t) <= d_max   and   UB = min_t (|x - c_t| + r_t) >= d_min,
+// and only tiles with |x - c_t| + r_t >= LB (may hold the farthest point) or
+// |x - c_t| - r_t <= UB (may hold the nearest) are scanned, point by point,
+// with exactly the arithmetic of k_prepass, so the results are identical.
+// A warp scans a tile when any of its lanes needs it.  Plain cached loads: the
+// tiles a warp visits differ from warp to warp.
+// --------------------------------------------------------------------------
+constexpr int kPrunedThreads = kConsumerWarps * 32;
+
+template <bool ARGMAX>
+__global__ void __launch_bounds__(kPrunedThreads) k_prepass_pruned(const float4* __restrict__ pre,
+                                                                   const float4* __restrict__ spheres, int64_t n,
+                                                                   int64_t nsph, QueryArgs a) {
+    float xs[kQueriesPerThread][3], hi[kQueriesPerThread], lo[kQueriesPerThread], xx[kQueriesPerThread];
+    float lbmax[kQueriesPerThread], ubmin[kQueriesPerThread];
+    int64_t qi[kQueriesPerThread];
+    int32_t far[kQueriesPerThread];
+#pragma unroll
+    for (int k = 0; k < kQueriesPerThread; ++k) {
+        qi[k] = (int64_t)blockIdx.x * kQueriesPerCta + k * (kConsumerWarps * 32) + threadIdx.x;
+        const int64_t qq = qi[k] < a.q ? qi[k] : a.q - 1;
+        xs[k][0] = a.x[3 * qq] - a.cx;
+        xs[k][1] = a.x[3 * qq + 1] - a.cy;
+        xs[k][2] = a.x[3 * qq + 2] - a.cz;
+        xx[k] = xs[k][0] * xs[k][0] + xs[k][1] * xs[k][1] + xs[k][2] * xs[k][2];
+        hi[k] = -INFINITY;
+        lo[k] = INFINITY;
+        lbmax[k] = -INFINITY;
+        ubmin[k] = INFINITY;
+        far[k] = 0;
+    }
+    // bounds from the spheres
+    for (int64_t t = 0; t < nsph; ++t) {
+        const float4 s = __ldg(spheres + t);
+#pragma unroll
+        for (int k = 0; k < kQueriesPerThread; ++k) {
+            const float dx = xs[k][0] - s.x, dy = xs[k][1] - s.y, dz = xs[k][2] - s.z;
+            const float dc = sqrt_mufu(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+            lbmax[k] = fmaxf(lbmax[k], dc - s.w);
+            ubmin[k] = fminf(ubmin[k], dc + s.w);
+        }
+    }
+    // exact scan of the tiles that may hold an extreme
+    for (int64_t t = 0; t < nsph; ++t) {
+        const float4 s = __ldg(spheres + t);
+        bool need = false;
+#pragma unroll
+        for (int k = 0; k < kQueriesPerThread; ++k) {
+            const float dx = xs[k][0] - s.x, dy = xs[k][1] - s.y, dz = xs[k][2] - s.z;
+            const float dc = sqrt_mufu(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+            need = need || (dc + s.w >= lbmax[k]) || (dc - s.w <= ubmin[k]);
+        }
+        if (!__any_sync(0xffffffffu, need)) continue;
+        const int64_t first = t * kSphereTile;
+        const int cnt = (int)(n - first < kSphereTile ? n - first : kSphereTile);
+        for (int j = 0; j < cnt; ++j) {
+            const float4 r = __ldg(pre + first + j);
+#pragma unroll
+            for (int k = 0; k < kQueriesPerThread; ++k) {
+                const float v = fmaf(xs[k][0], r.x, fmaf(xs[k][1], r.y, fmaf(xs[k][2], r.z, r.w)));
+                if (ARGMAX) {
+                    if (v > hi[k] || (v == hi[k] && (int32_t)(first + j) < far[k])) {
+                        hi[k] = v;
+                        far[k] = (int32_t)(first + j);
+                    }
+                } else {
+                    hi[k] = fmaxf(hi[k], v);
+                }
+                lo[k] = fminf(lo[k], v);
+            }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < kQueriesPerThread; ++k) {
+        if (qi[k] < a.q) {
+            a.d2[qi[k]] = make_float2(hi[k] + xx[k], lo[k] + xx[k]);
+            if (ARGMAX) a.far[qi[k]] = far[k];
+        }
+    }
+}
+
+// Pruned prepass for GLOBAL lambda once the query blocks fill the GPU (one
+// wave of 2 CTAs per SM); smaller batches keep the point-split prepass.
+__host__ inline bool use_pruned_prepass(const Cloud& c, const Plan& p, const sdf_query_opts& o) {
+    return o.lambda_mode == SDF_LAMBDA_GLOBAL && c.spheres != nullptr && p.pre_qblocks >= 2LL * c.num_sms;
 }
 
 // --------------------------------------------------------------------------

@@ -1,0 +1,146 @@
+"""Serving runtime on the GPU: continuous batching over resident clouds.
+
+Each request's result must be the same alone and in the mix: every request
+of a mixed, concurrently submitted workload (queries, gradients, Booleans,
+trace steps, offsets; host and device buffers; three submitting threads) is
+compared bit for bit with the same request run alone on a one-slot server,
+and (except trace steps) with the direct calls.  Admission is checked under a one-slot budget, oversized requests are
+refused, and a poll can time out.
+"""
+import threading
+
+import numpy as np
+import pytest
+
+import synth
+from workloads import f32
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2607_16946_b300 import build
+    build.build()
+    import paper_2607_16946_b300 as m
+    from paper_2607_16946_b300 import serve
+    clouds = [m.Cloud(*f32(*synth.sphere_fibonacci(3000, 1))),
+              m.Cloud(*f32(*synth.ring_torus(20000, 2))),
+              m.Cloud(*f32(*synth.ellipsoid(8000, 3))),
+              m.Cloud(*f32(*synth.superquadric(12000, 4, grid=256)))]
+    return m, serve, torch, clouds
+
+
+def alone(m, torch, clouds, kind, ca, cb, x, dirs=None, t=None, offset=0.0):
+    from paper_2607_16946_b300 import serve as S
+    c = clouds[ca]
+    if kind == S.SDF_REQ_QUERY:
+        return c.query(x, offset=offset)
+    if kind == S.SDF_REQ_GRAD:
+        phi, g, _ = c.query_grad(x, saved=False, offset=offset)
+        return torch.cat([phi, g.reshape(-1)])
+    a = c.query(x, offset=offset)
+    b = clouds[cb].query(x, offset=offset)
+    op = {S.SDF_REQ_UNION: m.SDF_UNION, S.SDF_REQ_INTERSECT: m.SDF_INTERSECT,
+          S.SDF_REQ_DIFFERENCE: m.SDF_DIFFERENCE}[kind]
+    return m.combine(op, a, b)
+
+
+def test_mixed_requests_equal_alone(env):
+    m, S, torch, clouds = env
+    srv = S.Server(mem_budget_bytes=2 << 30, max_inflight=6, n_streams=4)
+    ids = [srv.register(c) for c in clouds]
+    rng = np.random.Generator(np.random.PCG64(11))
+    reqs = []
+    for i in range(48):
+        kind = int(rng.choice([S.SDF_REQ_QUERY] * 4 + [S.SDF_REQ_GRAD, S.SDF_REQ_UNION, S.SDF_REQ_INTERSECT,
+                                                        S.SDF_REQ_DIFFERENCE, S.SDF_REQ_TRACE_STEP]))
+        q = int(np.exp(rng.uniform(np.log(100), np.log(60000))))
+        x = torch.as_tensor(f32(rng.uniform(-1.5, 1.5, size=(q, 3))), dtype=torch.float32, device="cuda")
+        dirs = t = None
+        if kind == S.SDF_REQ_TRACE_STEP:
+            d = synth._unit(rng.normal(size=(q, 3)))
+            dirs = torch.as_tensor(f32(d), dtype=torch.float32, device="cuda")
+            t = torch.as_tensor(f32(rng.uniform(0, 0.5, size=q)), dtype=torch.float32, device="cuda")
+        host = bool(rng.integers(0, 2)) and kind != S.SDF_REQ_TRACE_STEP
+        nout = 4 * q if kind == S.SDF_REQ_GRAD else q
+        out = np.empty(nout, np.float32) if host else torch.empty(nout, device="cuda")
+        xin = x.cpu().numpy() if host else x
+        offset = float(rng.choice([0.0, 0.05]))
+        reqs.append(dict(kind=kind, ca=int(rng.integers(0, 4)), cb=int(rng.integers(0, 4)), x=x, xin=xin,
+                         dirs=dirs, t=t, out=out, offset=offset))
+    torch.cuda.synchronize()
+    tickets = [None] * len(reqs)
+
+    def submitter(k):
+        for i in range(k, len(reqs), 3):
+            r = reqs[i]
+            tickets[i] = srv.submit(r["kind"], ids[r["ca"]], r["xin"], r["out"], cloud_id_b=ids[r["cb"]],
+                                    dirs=r["dirs"], t=r["t"], offset=r["offset"])
+
+    th = [threading.Thread(target=submitter, args=(k,)) for k in range(3)]
+    for x in th:
+        x.start()
+    for x in th:
+        x.join()
+    stats = [srv.poll(tk) for tk in tickets]
+    srv.shutdown()
+    # the same requests one at a time through a one-slot server
+    solo = S.Server(mem_budget_bytes=2 << 30, max_inflight=1, n_streams=1)
+    sid = [solo.register(c) for c in clouds]
+    for r, st in zip(reqs, stats):
+        got = r["out"] if isinstance(r["out"], np.ndarray) else r["out"].cpu().numpy()
+        out1 = np.empty_like(got) if isinstance(r["out"], np.ndarray) else torch.empty_like(r["out"])
+        solo.poll(solo.submit(r["kind"], sid[r["ca"]], r["xin"], out1, cloud_id_b=sid[r["cb"]],
+                              dirs=r["dirs"], t=r["t"], offset=r["offset"]))
+        one = out1 if isinstance(out1, np.ndarray) else out1.cpu().numpy()
+        np.testing.assert_array_equal(got, one)
+        if r["kind"] != S.SDF_REQ_TRACE_STEP:      # and equal to the direct calls
+            ref = alone(m, torch, clouds, r["kind"], r["ca"], r["cb"], r["x"], offset=r["offset"])
+            np.testing.assert_array_equal(got, ref.cpu().numpy())
+        assert st["arrive_ns"] <= st["admit_ns"] <= st["start_ns"] <= st["done_ns"]
+    solo.shutdown()
+
+
+def test_admission_one_slot_in_order(env):
+    m, S, torch, clouds = env
+    srv = S.Server(mem_budget_bytes=1 << 30, max_inflight=1, n_streams=2)
+    cid = srv.register(clouds[1])
+    xs = [torch.as_tensor(f32(synth.uniform_queries(5000 + 100 * i, 20 + i)), dtype=torch.float32, device="cuda")
+          for i in range(8)]
+    outs = [torch.empty(x.shape[0], device="cuda") for x in xs]
+    tk = [srv.submit(S.SDF_REQ_QUERY, cid, x, o) for x, o in zip(xs, outs)]
+    st = [srv.poll(t) for t in tk]
+    for a, b in zip(st, st[1:]):
+        assert b["admit_ns"] >= a["done_ns"] - 1_000_000      # one at a time, in arrival order
+    for x, o in zip(xs, outs):
+        np.testing.assert_array_equal(o.cpu().numpy(), clouds[1].query(x).cpu().numpy())
+    srv.shutdown()
+
+
+def test_refusals_and_timeout(env):
+    m, S, torch, clouds = env
+    from paper_2607_16946_b300 import SdfError
+    srv = S.Server(mem_budget_bytes=1 << 20, max_inflight=2, n_streams=1)
+    cid = srv.register(clouds[0])
+    x = torch.zeros((200_000, 3), device="cuda")
+    out = torch.empty(200_000, device="cuda")
+    with pytest.raises(SdfError) as e:
+        srv.submit(S.SDF_REQ_QUERY, cid, x, out)          # needs more than the 1 MiB budget
+    assert e.value.status == 2
+    with pytest.raises(SdfError) as e:
+        srv.submit(S.SDF_REQ_QUERY, 99, x[:10], out[:10])
+    assert e.value.status == 1
+    srv.shutdown()
+    srv = S.Server(mem_budget_bytes=4 << 30, max_inflight=2, n_streams=1)
+    cid = srv.register(clouds[1])
+    big = torch.as_tensor(f32(synth.uniform_queries(2_000_000, 5)), dtype=torch.float32, device="cuda")
+    ob = torch.empty(big.shape[0], device="cuda")
+    t = srv.submit(S.SDF_REQ_QUERY, cid, big, ob)
+    with pytest.raises(TimeoutError):
+        srv.poll(t, timeout_s=0.0)
+    srv.poll(t)
+    srv.shutdown()
