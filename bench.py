@@ -194,7 +194,7 @@ def make_serving_clouds(n_clouds: int, seed: int):
     return out
 
 
-def run_served(args, dev, pair_rate_gps: float):
+def run_served(args, dev, pair_rate_gps: float, policy: int = 0, clouds_np=None):
     """Continuous-batching run: Poisson arrivals at `load` x the measured pair
     rate, requests of Q log-uniform in [1,024, 4,194,304] against random
     resident clouds; kinds QUERY 70%, OFFSET 10%, UNION / DIFFERENCE 10%,
@@ -204,7 +204,8 @@ def run_served(args, dev, pair_rate_gps: float):
     import paper_2607_16946_b300 as ptsdf
     from paper_2607_16946_b300 import serve as S
 
-    clouds_np = make_serving_clouds(args.serve_clouds, SERVE_SEED)
+    if clouds_np is None:
+        clouds_np = make_serving_clouds(args.serve_clouds, SERVE_SEED)
     clouds = [ptsdf.Cloud(*c) for c in clouds_np]
     ns = [c.n for c in clouds]
     rng = np.random.Generator(np.random.PCG64(SERVE_SEED))
@@ -225,7 +226,7 @@ def run_served(args, dev, pair_rate_gps: float):
     mean_pairs = float(np.mean([r["pairs"] for r in reqs]))
     rate = args.serve_load * pair_rate_gps * 1e9 / mean_pairs          # requests per second
     arrivals = np.cumsum(rng.exponential(1.0 / rate, size=len(reqs)))
-    srv = S.Server(mem_budget_bytes=16 << 30, max_inflight=8, n_streams=4)
+    srv = S.Server(mem_budget_bytes=16 << 30, max_inflight=8, n_streams=4, policy=policy, starve_ms=2000)
     ids = [srv.register(c) for c in clouds]
     outs = [torch.empty(r["q"], device=dev) for r in reqs]
     torch.cuda.synchronize(dev)
@@ -266,7 +267,8 @@ def run_served(args, dev, pair_rate_gps: float):
             "service_p50_ms": float(np.percentile(service, 50)), "service_p99_ms": float(np.percentile(service, 99)),
             "offered_load": args.serve_load, "arrival_rate_per_s": rate, "mean_pairs_per_request": mean_pairs,
             "clouds": len(clouds), "points_total": int(sum(ns)), "outputs_finite": finite,
-            "server": {"max_inflight": 8, "n_streams": 4, "mem_budget_bytes": 16 << 30},
+            "server": {"max_inflight": 8, "n_streams": 4, "mem_budget_bytes": 16 << 30,
+                       "policy": "smallest_first (starve 2 s)" if policy else "fifo"},
             "workload": f"{len(clouds)} resident clouds N~logU[2048,500000] (sphere/torus/superquadric/ellipsoid), "
                         f"{len(reqs)} requests Q~logU[1024,4194304], Poisson arrivals at "
                         f"{args.serve_load} x measured capacity; FP32"}
@@ -530,7 +532,9 @@ def run_ours(args, rank, world, local):
         line["trace"] = run_trace_leg(dev)
     if world == 1 and args.serve_requests > 0:
         del hx, hphi
-        line["served"] = run_served(args, dev, value)
+        clouds_np = make_serving_clouds(args.serve_clouds, SERVE_SEED)
+        line["served"] = run_served(args, dev, value, policy=1, clouds_np=clouds_np)
+        line["served_fifo"] = run_served(args, dev, value, policy=0, clouds_np=clouds_np)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(p, n, a)
     print(json.dumps(line), flush=True)

@@ -241,8 +241,8 @@ PTSDF_API sdf_status sdf_query_noalloc(sdf_cloud cloud, const float* d_x, int64_
 /* ---------------------------------------------------------------------------
  * Serving: a request loop over several resident clouds (Sec. 6 uses of the
  * SDF: query batches of uneven size, sphere-tracing steps, offsets and
- * Booleans).  A scheduler thread admits queued requests in arrival order
- * when a slot (max_inflight) and enough of the memory budget are free and
+ * Booleans).  A scheduler thread admits queued requests (in arrival order, or
+ * smallest first) when a slot (max_inflight) and enough of the memory budget are free and
  * launches each at once on one of n_streams streams, so work that arrives
  * while other requests run overlaps with them on the device.  A request's
  * result depends only on its own inputs, cloud and options: it is the same
@@ -250,11 +250,20 @@ PTSDF_API sdf_status sdf_query_noalloc(sdf_cloud cloud, const float* d_x, int64_
  * ------------------------------------------------------------------------- */
 typedef struct sdf_server_s* sdf_server;
 
+typedef enum {
+    SDF_SERVE_FIFO = 0,            /* admit in arrival order */
+    SDF_SERVE_SMALLEST_FIRST = 1   /* admit the queued request with the fewest (query, point) pairs
+                                      first; a request queued longer than starve_ms goes first */
+} sdf_serve_policy;
+
 typedef struct {
     int64_t mem_budget_bytes;   /* device bytes the server may hold for staging and scratch */
     int32_t max_inflight;       /* requests on the GPU at once (slots) */
     int32_t n_streams;          /* CUDA streams the requests are spread over */
     int32_t device;             /* CUDA device of the clouds */
+    int32_t policy;             /* sdf_serve_policy */
+    int32_t starve_ms;          /* SMALLEST_FIRST: age after which a request is admitted first */
+    int32_t reserved;
 } sdf_serve_config;
 
 typedef enum {

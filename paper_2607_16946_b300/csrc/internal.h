@@ -52,6 +52,9 @@ namespace ptsdf {
 #ifndef PTSDF_UNROLL
 #define PTSDF_UNROLL 2
 #endif
+#ifndef PTSDF_FWD_MINB
+#define PTSDF_FWD_MINB 1
+#endif
 constexpr int kTileRecs = PTSDF_TILE_RECS;   // records per main-loop tile (32 x 64 B = 2 KB)
 constexpr int kRecFloats = 16;
 constexpr int kPreTile = 256;        // points per prepass tile (4 KB)
@@ -96,6 +99,7 @@ constexpr int kQueriesPerThread = PTSDF_QPT;
 constexpr int kQueriesPerCta = kConsumerWarps * 32 * kQueriesPerThread;   // 512
 constexpr int kStages = PTSDF_STAGES;
 constexpr int kUnrollPts = PTSDF_UNROLL;      // points per unrolled step of the pair loop
+constexpr int kFwdMinBlocks = PTSDF_FWD_MINB; // resident CTAs per SM the pair loop is compiled for
 
 // queries_per_cta: queries one CTA of the main kernel holds (the prepass
 // always uses kQueriesPerCta).

@@ -113,7 +113,7 @@ __device__ __forceinline__ void pair_tile(const float4* __restrict__ tile, int c
 // Forward pass
 // --------------------------------------------------------------------------
 template <int PREC>
-__global__ void __launch_bounds__(kThreads) k_fwd(const float4* __restrict__ rec, int64_t n_direct, int64_t n_kappa,
+__global__ void __launch_bounds__(kThreads, kFwdMinBlocks) k_fwd(const float4* __restrict__ rec, int64_t n_direct, int64_t n_kappa,
                                                   int64_t tiles_direct, int64_t tiles_total, int64_t tiles_per_chunk,
                                                   QueryArgs a, int32_t* status) {
     extern __shared__ __align__(128) char smem[];

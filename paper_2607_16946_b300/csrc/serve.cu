@@ -2,9 +2,9 @@
 // of Sec. 6's applications: batches of SDF queries of uneven size, sphere-
 // tracing steps, offsets and Booleans, against clouds kept on the device).
 //
-// Continuous batching: a scheduler thread admits queued requests in arrival
-// order whenever a slot (max_inflight) and enough of the memory budget are
-// free, and launches each admitted request at once on one of n_streams CUDA
+// Continuous batching: a scheduler thread admits queued requests (in arrival
+// order, or smallest first with an age guard) whenever a slot (max_inflight)
+// and enough of the memory budget are free, and launches each admitted request at once on one of n_streams CUDA
 // streams, so requests that arrive while others run overlap with them on the
 // device.  Completion is signalled by a host callback enqueued behind the
 // request's work (no polling of the GPU); the scheduler then returns the
@@ -60,6 +60,7 @@ struct Request {
     uint64_t ticket = 0;
     sdf_request r{};
     int64_t need = 0;               // bytes charged against the budget
+    double work = 0.0;              // (query, point) pairs, for smallest-first admission
     sdf_request_stats st{};
     int stream = 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -239,11 +240,18 @@ void scheduler(Server* S) {
                 ++it;
             }
         }
-        // admit in arrival order while a slot and the memory are free
-        while (!S->queue.empty() && (int)S->inflight.size() < S->cfg.max_inflight &&
-               S->mem_in_use + S->queue.front()->need <= S->cfg.mem_budget_bytes) {
-            std::shared_ptr<Request> R = S->queue.front();
-            S->queue.pop_front();
+        // admit while a slot and the memory are free: the head of the queue
+        // (FIFO, or a request older than starve_ms), else the smallest request
+        while (!S->queue.empty() && (int)S->inflight.size() < S->cfg.max_inflight) {
+            size_t pick = 0;
+            if (S->cfg.policy == SDF_SERVE_SMALLEST_FIRST &&
+                now_ns() - S->queue.front()->st.arrive_ns <= (int64_t)S->cfg.starve_ms * 1000000LL) {
+                for (size_t i = 1; i < S->queue.size(); ++i)
+                    if (S->queue[i]->work < S->queue[pick]->work) pick = i;
+            }
+            if (S->mem_in_use + S->queue[pick]->need > S->cfg.mem_budget_bytes) break;
+            std::shared_ptr<Request> R = S->queue[pick];
+            S->queue.erase(S->queue.begin() + (long)pick);
             R->st.admit_ns = now_ns();
             R->stream = S->next_stream;
             S->next_stream = (S->next_stream + 1) % (int)S->streams.size();
@@ -275,6 +283,8 @@ extern "C" sdf_status sdf_serve_create(const sdf_serve_config* cfg, sdf_server* 
     *out = nullptr;
     if (cfg->max_inflight < 1 || cfg->n_streams < 1 || cfg->mem_budget_bytes < 1)
         return set_error(SDF_EINVAL, "sdf_serve_create: need max_inflight >= 1, n_streams >= 1, budget > 0");
+    if ((cfg->policy != SDF_SERVE_FIFO && cfg->policy != SDF_SERVE_SMALLEST_FIRST) || cfg->starve_ms < 0)
+        return set_error(SDF_EINVAL, "sdf_serve_create: unknown policy or negative starve_ms");
     auto* h = new sdf_server_s();
     Server& S = h->s;
     S.cfg = *cfg;
@@ -328,6 +338,8 @@ extern "C" sdf_status sdf_serve_submit(sdf_server srv, const sdf_request* req, u
             return set_error(SDF_EINVAL, "sdf_serve_submit: unknown cloud id");
         if (S.stop) return set_error(SDF_EBUSY, "sdf_serve_submit: server is shutting down");
         R->need = request_need(S, r);
+        const bool pair2 = r.kind == SDF_REQ_UNION || r.kind == SDF_REQ_INTERSECT || r.kind == SDF_REQ_DIFFERENCE;
+        R->work = (double)r.q * (double)(S.clouds[r.cloud_id]->n + (pair2 ? S.clouds[r.cloud_id_b]->n : 0));
         if (R->need > S.cfg.mem_budget_bytes)
             return set_error(SDF_ENOMEM, "sdf_serve_submit: request needs " + std::to_string(R->need) +
                                              " bytes, more than the whole memory budget");

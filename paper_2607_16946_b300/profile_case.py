@@ -3,9 +3,10 @@
     python -m paper_2607_16946_b300.profile_case [--queries Q] [--launches K] [--warmup W]
 
 Builds the dense-grid cloud (ring torus, N = 100,000) and evaluates an evenly
-strided subset of Q nodes of the 256^3 grid with sdf_query, W times untimed
-and then K times, printing the device time of each call.  Used to give ncu a
-short, self-terminating run of the same kernels the benchmark times.
+strided subset of Q nodes of the 256^3 grid with sdf_query (or the gradient
+and backward calls), W times untimed and then K times, printing the device
+time of each call.  Used to give ncu a short, self-terminating run of the
+same kernels the benchmark times.
 """
 from __future__ import annotations
 
@@ -24,6 +25,10 @@ def main():
     ap.add_argument("--launches", type=int, default=1)
     ap.add_argument("--warmup", type=int, default=1)
     ap.add_argument("--points", type=int, default=100_000)
+    ap.add_argument("--mode", choices=["query", "grad", "backward"], default="query",
+                    help="query: sdf_query; grad: sdf_query_grad; backward: sdf_query_grad then "
+                         "sdf_backward_params (each call)")
+    ap.add_argument("--precision", type=int, default=0, help="sdf_precision of the query")
     args = ap.parse_args()
 
     import torch
@@ -40,13 +45,24 @@ def main():
     stride = max(1, x.shape[0] // args.queries)
     x = x[::stride][: args.queries].contiguous()
     phi = torch.empty(x.shape[0], device="cuda")
+    G = torch.ones(x.shape[0], device="cuda")
+
+    def call():
+        nonlocal phi
+        if args.mode == "query":
+            cloud.query(x, out=phi, precision=args.precision)
+        else:
+            phi, _, saved = cloud.query_grad(x)
+            if args.mode == "backward":
+                cloud.backward_params(x, saved, G)
+
     for _ in range(args.warmup):
-        cloud.query(x, out=phi)
+        call()
     torch.cuda.synchronize()
     for i in range(args.launches):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
-        cloud.query(x, out=phi)
+        call()
         e1.record()
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1)

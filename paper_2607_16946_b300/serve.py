@@ -23,9 +23,13 @@ from ._abi import check, lib, make_opts
 SDF_REQ_QUERY, SDF_REQ_GRAD, SDF_REQ_UNION, SDF_REQ_INTERSECT, SDF_REQ_DIFFERENCE, SDF_REQ_TRACE_STEP = range(6)
 
 
+SDF_SERVE_FIFO, SDF_SERVE_SMALLEST_FIRST = 0, 1
+
+
 class sdf_serve_config(ctypes.Structure):
     _fields_ = [("mem_budget_bytes", ctypes.c_int64), ("max_inflight", ctypes.c_int32),
-                ("n_streams", ctypes.c_int32), ("device", ctypes.c_int32)]
+                ("n_streams", ctypes.c_int32), ("device", ctypes.c_int32), ("policy", ctypes.c_int32),
+                ("starve_ms", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class sdf_request(ctypes.Structure):
@@ -54,10 +58,11 @@ def _ptr_and_kind(a):
 
 class Server:
     def __init__(self, mem_budget_bytes: int = 8 << 30, max_inflight: int = 8, n_streams: int = 4,
-                 device: int | None = None):
+                 device: int | None = None, policy: int = SDF_SERVE_FIFO, starve_ms: int = 2000):
         import torch
         cfg = sdf_serve_config(int(mem_budget_bytes), int(max_inflight), int(n_streams),
-                               torch.cuda.current_device() if device is None else int(device))
+                               torch.cuda.current_device() if device is None else int(device), int(policy),
+                               int(starve_ms), 0)
         h = ctypes.c_void_p()
         check(lib().sdf_serve_create(ctypes.byref(cfg), ctypes.byref(h)), "sdf_serve_create")
         self._h = h

@@ -71,14 +71,16 @@ def test_serve_host_side_validation(abi):
     L = abi.lib()
     h = ctypes.c_void_p()
     assert L.sdf_serve_create(None, ctypes.byref(h)) == abi.SDF_EINVAL
-    bad = serve.sdf_serve_config(1 << 20, 0, 1, 0)
+    bad = serve.sdf_serve_config(1 << 20, 0, 1, 0, 0, 0, 0)
     assert L.sdf_serve_create(ctypes.byref(bad), ctypes.byref(h)) == abi.SDF_EINVAL
-    bad = serve.sdf_serve_config(0, 1, 1, 0)
+    bad = serve.sdf_serve_config(0, 1, 1, 0, 0, 0, 0)
+    assert L.sdf_serve_create(ctypes.byref(bad), ctypes.byref(h)) == abi.SDF_EINVAL
+    bad = serve.sdf_serve_config(1 << 20, 1, 1, 0, 7, 0, 0)
     assert L.sdf_serve_create(ctypes.byref(bad), ctypes.byref(h)) == abi.SDF_EINVAL
     assert L.sdf_serve_submit(None, None, None) == abi.SDF_EINVAL
     assert L.sdf_serve_poll(None, 1, 0, None) == abi.SDF_EINVAL
     assert L.sdf_serve_shutdown(None) == abi.SDF_OK
     # the ctypes structures match the C layout (sizes from include/ptsdf.h)
-    assert ctypes.sizeof(serve.sdf_serve_config) == 24
+    assert ctypes.sizeof(serve.sdf_serve_config) == 32
     assert ctypes.sizeof(serve.sdf_request_stats) == 48
     assert ctypes.sizeof(serve.sdf_request) == 16 + 5 * 8 + ctypes.sizeof(abi.sdf_query_opts)

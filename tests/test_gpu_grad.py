@@ -166,3 +166,29 @@ def test_autograd_function(ptsdf):
     torch.testing.assert_close(x.grad, w[:, None] * g)
     gp = cl.backward_params(x.detach(), saved, w)
     torch.testing.assert_close(params.grad, gp)
+
+
+def test_grad_config4_full_size_sampled(ptsdf, oracle_mod):
+    """Full size in the benchmark's launch configuration: all 1e6 queries in
+    one sdf_query_grad call (N = 65,536); 200 sampled outputs against the
+    oracle's duals.  The parameter backward over all 1e6 queries with a
+    one-hot upstream gradient equals the oracle's d phi_j / d a for that query."""
+    import torch
+    p, n, a, x = config4()
+    cl = ptsdf.Cloud(p, n, a)
+    xt = torch.as_tensor(x, dtype=torch.float32, device="cuda")
+    phi, g, saved = cl.query_grad(xt)
+    torch.cuda.synchronize()
+    assert cl.device_status() == 0
+    rng = np.random.Generator(np.random.PCG64(9))
+    idx = rng.choice(x.shape[0], size=400, replace=False)
+    idx = idx[kink_free(p, x[idx], 1e-5)][:200]
+    ophi, og = oracle_mod.Cloud(p, n, a).grad_x(x[idx])
+    assert np.abs(phi.cpu().numpy()[idx] - ophi).max() <= 1e-4 * np.linalg.norm(p.max(0) - p.min(0))
+    check_close(g.cpu().numpy()[idx].astype(np.float64), og)
+    for j in idx[:2]:
+        G = torch.zeros(x.shape[0], device="cuda")
+        G[int(j)] = 1.0
+        gp = cl.backward_params(xt, saved, G).cpu().numpy().astype(np.float64)
+        ref = oracle_mod.Cloud(p, n, a).grad_params(x[j:j + 1], np.ones(1))
+        assert np.abs(gp - ref).max() <= 2e-3 * np.abs(ref).max()

@@ -105,6 +105,31 @@ def test_mixed_requests_equal_alone(env):
     solo.shutdown()
 
 
+def test_smallest_first_admission(env):
+    """SMALLEST_FIRST: with one slot busy on a large request, queued requests
+    are admitted smallest first; results are unchanged."""
+    m, S, torch, clouds = env
+    srv = S.Server(mem_budget_bytes=1 << 30, max_inflight=1, n_streams=1, policy=S.SDF_SERVE_SMALLEST_FIRST,
+                   starve_ms=60000)
+    cid = srv.register(clouds[1])
+    big = torch.as_tensor(f32(synth.uniform_queries(1_000_000, 30)), dtype=torch.float32, device="cuda")
+    sizes = [40_000, 5_000, 20_000, 1_000, 10_000]
+    xs = [torch.as_tensor(f32(synth.uniform_queries(s, 31 + i)), dtype=torch.float32, device="cuda")
+          for i, s in enumerate(sizes)]
+    torch.cuda.synchronize()
+    outb = torch.empty(big.shape[0], device="cuda")
+    tb = srv.submit(S.SDF_REQ_QUERY, cid, big, outb)
+    outs = [torch.empty(x.shape[0], device="cuda") for x in xs]
+    tk = [srv.submit(S.SDF_REQ_QUERY, cid, x, o) for x, o in zip(xs, outs)]
+    srv.poll(tb)
+    st = [srv.poll(t) for t in tk]
+    order = np.argsort([s["admit_ns"] for s in st])
+    assert list(np.array(sizes)[order]) == sorted(sizes)
+    for x, o in zip(xs, outs):
+        np.testing.assert_array_equal(o.cpu().numpy(), clouds[1].query(x).cpu().numpy())
+    srv.shutdown()
+
+
 def test_admission_one_slot_in_order(env):
     m, S, torch, clouds = env
     srv = S.Server(mem_budget_bytes=1 << 30, max_inflight=1, n_streams=2)

@@ -93,3 +93,21 @@ def test_combine_booleans(ptsdf):
     torch.testing.assert_close(u, torch.minimum(a, b), rtol=0, atol=0)
     torch.testing.assert_close(i, torch.maximum(a, b), rtol=0, atol=0)
     torch.testing.assert_close(d, torch.maximum(a, -b), rtol=0, atol=0)
+
+
+def test_trace_full_image_sampled(ptsdf, oracle_mod):
+    """Full size in the benchmark's launch configuration: all 512 x 512 rays
+    traced in one call (N = 262,144); 200 sampled rays against the oracle's
+    tracer (each ray's trace is independent of the batch)."""
+    p, n, a = f32(*synth.superquadric(262_144, 1003))
+    org, dirs = (f32(v) for v in synth.camera_rays(512, 512, 1003))
+    cl = ptsdf.Cloud(p, n, a)
+    t, steps, _ = gpu_trace(cl, org, dirs, max_steps=48, eps=1e-4, t_max=6.0, normals=False)
+    rows = np.random.Generator(np.random.PCG64(8)).choice(org.shape[0], size=200, replace=False)
+    to, so = oracle_mod.Cloud(p, n, a).trace(org[rows], dirs[rows], max_steps=48, eps=1e-4, t_max=6.0)
+    tg, sg = t[rows], steps[rows]
+    agree = (tg >= 0) == (to >= 0)
+    assert agree.mean() >= 0.98
+    both = (tg >= 0) & (to >= 0)
+    ok = (np.abs(tg[both] - to[both]) <= 1e-3) & (np.abs(sg[both] - so[both]) <= 1)
+    assert ok.mean() >= 0.98
