@@ -64,6 +64,21 @@ typedef enum {
  * torus SDF and all sums stay FP32.  Gradients are FP32 only. */
 typedef enum { SDF_F32 = 0, SDF_F16X2 = 1, SDF_BF16X2 = 2 } sdf_precision;
 
+/* Which units evaluate the pairs of direct-form tori in sdf_query (and in
+ * sdf_query_host, the distance steps of sdf_trace, and serving QUERY,
+ * Boolean and TRACE_STEP requests).  SDF_ENGINE_AUTO: the
+ * tensor cores when precision is SDF_F32, else the FP32 units.
+ * SDF_ENGINE_TENSOR: the tensor cores (SDF_EINVAL unless precision is
+ * SDF_F32).  SDF_ENGINE_ALU: the FP32 units for every pair.  The tensor-core
+ * loop forms |x - p|^2, <x - c, u> and |x - c|^2 as products of split-f16
+ * features on the tensor cores and finishes each pair in FP32; pairs where
+ * that loses accuracy (query near a torus axis, or far outside the cloud) are
+ * recomputed by the FP32 formula.  Points of the kappa form always use the
+ * FP32 units.  sdf_query_grad, sdf_backward_params and sdf_query_noalloc
+ * (and the normals of sdf_trace) use the FP32 units; the first three reject
+ * SDF_ENGINE_TENSOR. */
+typedef enum { SDF_ENGINE_AUTO = 0, SDF_ENGINE_ALU = 1, SDF_ENGINE_TENSOR = 2 } sdf_engine;
+
 typedef enum {
     SDF_LAMBDA_GLOBAL = 0,  /* lambda_x = C / sigma_x, sigma_x = max_i ||x - p_i|| / 2 (the paper's rule) */
     SDF_LAMBDA_FIXED = 1    /* lambda_x = fixed_lambda for every query (Sec. 4.2, "Acceleration and
@@ -79,10 +94,12 @@ typedef struct {
     int32_t split_n;       /* number of point chunks per query block; 0 = automatic.  The
                               automatic choice depends only on (Q, N, SM count), so a query's
                               result does not depend on what else runs. */
+    int32_t engine;        /* sdf_engine (SDF_ENGINE_AUTO) */
+    int32_t reserved;      /* 0 (keeps the structure 8-byte sized inside sdf_request) */
 } sdf_query_opts;
 
 /* Fills *opts with the paper's defaults: GLOBAL lambda, C = 64, F32, offset 0,
- * automatic split.  Returns SDF_EINVAL for NULL. */
+ * automatic split, automatic engine.  Returns SDF_EINVAL for NULL. */
 PTSDF_API sdf_status sdf_opts_default(sdf_query_opts* opts);
 
 /* ---------------------------------------------------------------------------
@@ -324,7 +341,7 @@ PTSDF_API sdf_status sdf_serve_shutdown(sdf_server srv);
  * clears earlier records; disabling stops recording and keeps them.
  * ------------------------------------------------------------------------- */
 enum { SDF_K_PREPASS = 0, SDF_K_FWD = 1, SDF_K_MERGE = 2, SDF_K_BUILD = 3, SDF_K_FWD_GRAD = 4, SDF_K_BWD = 5,
-       SDF_K_COUNT_ = 6 };
+       SDF_K_FWD_TC = 6, SDF_K_COUNT_ = 7 };
 PTSDF_API sdf_status sdf_profile_enable(int32_t on);
 PTSDF_API sdf_status sdf_profile_read(int32_t kernel, int64_t* launches, double* total_ms);
 /* Name of a kernel family (NULL for an id out of range). */

@@ -17,11 +17,12 @@ import ctypes
 import numpy as np
 
 from . import _abi
-from ._abi import (SDF_DIFFERENCE, SDF_INTERSECT, SDF_LAMBDA_FIXED, SDF_LAMBDA_GLOBAL, SDF_UNION, SdfError,
-                   check, lib, make_opts)
+from ._abi import (SDF_DIFFERENCE, SDF_ENGINE_ALU, SDF_ENGINE_AUTO, SDF_ENGINE_TENSOR, SDF_INTERSECT,
+                   SDF_LAMBDA_FIXED, SDF_LAMBDA_GLOBAL, SDF_UNION, SdfError, check, lib, make_opts)
 
 __all__ = ["Cloud", "SdfError", "SDF_LAMBDA_GLOBAL", "SDF_LAMBDA_FIXED", "SDF_UNION", "SDF_INTERSECT",
-           "SDF_DIFFERENCE", "make_opts", "lib", "sdf", "combine"]
+           "SDF_DIFFERENCE", "SDF_ENGINE_AUTO", "SDF_ENGINE_ALU", "SDF_ENGINE_TENSOR", "make_opts", "lib", "sdf",
+           "combine"]
 
 
 def _torch():

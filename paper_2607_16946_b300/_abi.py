@@ -15,10 +15,11 @@ LIB_PATH = os.path.join(_HERE, "libptsdf.so")
 SDF_OK, SDF_EINVAL, SDF_ENOMEM, SDF_ECUDA, SDF_EBUSY, SDF_ETIMEOUT, SDF_EDEVICE = range(7)
 SDF_F32, SDF_F16X2, SDF_BF16X2 = 0, 1, 2
 SDF_LAMBDA_GLOBAL, SDF_LAMBDA_FIXED = 0, 1
+SDF_ENGINE_AUTO, SDF_ENGINE_ALU, SDF_ENGINE_TENSOR = 0, 1, 2
 SDF_DEV_WAIT_TIMEOUT, SDF_DEV_BAD_INPUT = 1, 2
-SDF_K_PREPASS, SDF_K_FWD, SDF_K_MERGE, SDF_K_BUILD, SDF_K_FWD_GRAD, SDF_K_BWD = 0, 1, 2, 3, 4, 5
+SDF_K_PREPASS, SDF_K_FWD, SDF_K_MERGE, SDF_K_BUILD, SDF_K_FWD_GRAD, SDF_K_BWD, SDF_K_FWD_TC = 0, 1, 2, 3, 4, 5, 6
 SDF_UNION, SDF_INTERSECT, SDF_DIFFERENCE = 0, 1, 2
-KERNEL_IDS = {"prepass": 0, "fwd": 1, "merge": 2, "build": 3, "fwd_grad": 4, "bwd_params": 5}
+KERNEL_IDS = {"prepass": 0, "fwd": 1, "merge": 2, "build": 3, "fwd_grad": 4, "bwd_params": 5, "fwd_tc": 6}
 
 STATUS_NAMES = {0: "SDF_OK", 1: "SDF_EINVAL", 2: "SDF_ENOMEM", 3: "SDF_ECUDA", 4: "SDF_EBUSY",
                 5: "SDF_ETIMEOUT", 6: "SDF_EDEVICE"}
@@ -32,7 +33,8 @@ class SdfError(RuntimeError):
 
 class sdf_query_opts(ctypes.Structure):
     _fields_ = [("lambda_mode", ctypes.c_int32), ("precision", ctypes.c_int32), ("C", ctypes.c_float),
-                ("fixed_lambda", ctypes.c_float), ("offset", ctypes.c_float), ("split_n", ctypes.c_int32)]
+                ("fixed_lambda", ctypes.c_float), ("offset", ctypes.c_float), ("split_n", ctypes.c_int32),
+                ("engine", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 # (name, restype, argtypes) for every entry point of include/ptsdf.h
@@ -91,9 +93,10 @@ def check(status: int, what: str = ""):
 
 
 def make_opts(C: float = 64.0, lambda_mode: int = SDF_LAMBDA_GLOBAL, fixed_lambda: float = 0.0,
-              offset: float = 0.0, split_n: int = 0, precision: int = SDF_F32) -> sdf_query_opts:
+              offset: float = 0.0, split_n: int = 0, precision: int = SDF_F32,
+              engine: int = SDF_ENGINE_AUTO) -> sdf_query_opts:
     o = sdf_query_opts()
     check(lib().sdf_opts_default(ctypes.byref(o)))
-    o.C, o.lambda_mode, o.fixed_lambda, o.offset, o.split_n, o.precision = (
-        float(C), int(lambda_mode), float(fixed_lambda), float(offset), int(split_n), int(precision))
+    o.C, o.lambda_mode, o.fixed_lambda, o.offset, o.split_n, o.precision, o.engine = (
+        float(C), int(lambda_mode), float(fixed_lambda), float(offset), int(split_n), int(precision), int(engine))
     return o

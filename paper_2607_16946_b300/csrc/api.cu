@@ -24,6 +24,9 @@ sdf_status cuda_error(cudaError_t e, const char* what) {
     return set_error(SDF_ECUDA, std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")");
 }
 
+static_assert(sizeof(sdf_query_opts) == 32, "sdf_query_opts layout");
+static_assert(sizeof(sdf_request) == 88, "sdf_request layout");
+
 sdf_status check_opts(const sdf_query_opts& o, const char* fn) {
     if (o.lambda_mode != SDF_LAMBDA_GLOBAL && o.lambda_mode != SDF_LAMBDA_FIXED)
         return set_error(SDF_EINVAL, std::string(fn) + ": unknown lambda_mode");
@@ -34,6 +37,10 @@ sdf_status check_opts(const sdf_query_opts& o, const char* fn) {
         return set_error(SDF_EINVAL, std::string(fn) + ": fixed_lambda must be >= 0");
     if (!std::isfinite(o.offset)) return set_error(SDF_EINVAL, std::string(fn) + ": offset must be finite");
     if (o.split_n < 0) return set_error(SDF_EINVAL, std::string(fn) + ": split_n must be >= 0");
+    if (o.engine != SDF_ENGINE_AUTO && o.engine != SDF_ENGINE_ALU && o.engine != SDF_ENGINE_TENSOR)
+        return set_error(SDF_EINVAL, std::string(fn) + ": unknown engine");
+    if (o.engine == SDF_ENGINE_TENSOR && o.precision != SDF_F32)
+        return set_error(SDF_EINVAL, std::string(fn) + ": the tensor-core engine computes in FP32 only");
     return SDF_OK;
 }
 
@@ -64,6 +71,8 @@ extern "C" sdf_status sdf_opts_default(sdf_query_opts* o) {
     o->fixed_lambda = 0.f;
     o->offset = 0.f;
     o->split_n = 0;
+    o->engine = SDF_ENGINE_AUTO;
+    o->reserved = 0;
     return SDF_OK;
 }
 
@@ -88,6 +97,8 @@ extern "C" sdf_status sdf_query_grad(sdf_cloud cloud, const float* d_x, int64_t 
     const sdf_status s = check_opts(o, "sdf_query_grad");
     if (s != SDF_OK) return s;
     if (o.precision != SDF_F32) return set_error(SDF_EINVAL, "sdf_query_grad: gradients are computed in FP32 only");
+    if (o.engine == SDF_ENGINE_TENSOR)
+        return set_error(SDF_EINVAL, "sdf_query_grad: gradients use the FP32 units (no tensor-core engine)");
     if (q == 0) return SDF_OK;
     if (!d_x || !d_phi || !d_grad) return set_error(SDF_EINVAL, "sdf_query_grad: NULL buffer");
     return launch_query_grad(*reinterpret_cast<const Cloud*>(cloud), d_x, q, d_phi, d_grad, d_saved, o,
@@ -105,6 +116,8 @@ extern "C" sdf_status sdf_backward_params(sdf_cloud cloud, const float* d_x, int
     if (s != SDF_OK) return s;
     if (o.precision != SDF_F32)
         return set_error(SDF_EINVAL, "sdf_backward_params: gradients are computed in FP32 only");
+    if (o.engine == SDF_ENGINE_TENSOR)
+        return set_error(SDF_EINVAL, "sdf_backward_params: gradients use the FP32 units (no tensor-core engine)");
     const Cloud& c = *reinterpret_cast<const Cloud*>(cloud);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if (q == 0) {

@@ -272,6 +272,7 @@ void free_cloud(Cloud* c) {
     cudaFree(c->src_normals);
     cudaFree(c->src_params);
     cudaFree(c->status);
+    cudaFree(c->btiles);
     delete c;
 }
 
@@ -371,6 +372,14 @@ extern "C" sdf_status sdf_build(const float* d_points, const float* d_normals, c
                                             0.5f * (c->aabb[1] + c->aabb[4]), 0.5f * (c->aabb[2] + c->aabb[5]),
                                             c->rec, c->pre, c->perm);
     PTSDF_TRY(cudaGetLastError(), "sdf_build: k_partition launch");
+    {
+        const sdf_status bs = build_btiles(*c, st);
+        if (bs != SDF_OK) {
+            const std::string msg = sdf_last_error();
+            fail(cudaSuccess, "");
+            return set_error(bs, msg);
+        }
+    }
     PTSDF_TRY(cudaStreamSynchronize(st), "sdf_build: sync");
     {
         // Morton order of the prepass array and one bounding sphere per

@@ -77,6 +77,8 @@ struct Cloud {
     float* src_normals = nullptr;    // the parameter gradient's chain through the fit
     float* src_params = nullptr;
     int32_t* status = nullptr;       // device status word (SDF_DEV_* bits)
+    uint8_t* btiles = nullptr;       // tiles_direct x 12 KB split-f16 operands of the tensor-core loop
+    float tc_scale = 1.f;            // their coordinate scale (a power of two >= the AABB diagonal)
     int num_sms = 148;
 };
 
@@ -104,6 +106,12 @@ constexpr int kFwdMinBlocks = PTSDF_FWD_MINB; // resident CTAs per SM the pair l
 // queries_per_cta: queries one CTA of the main kernel holds (the prepass
 // always uses kQueriesPerCta).
 Plan make_plan(const Cloud& c, int64_t q, int split_override, int queries_per_cta = kQueriesPerCta);
+void chunk_tiles(int64_t qblocks, int64_t tiles, int64_t target, int split_override, int64_t& tiles_per_chunk,
+                 int& nchunks);
+// whether sdf_query runs the direct-form tiles on the tensor cores, and how
+// many (W, S) partial rows it then writes (1: none)
+bool use_tensor_engine(const Cloud& c, const sdf_query_opts& o);
+int query_partials(const Cloud& c, int64_t q, const sdf_query_opts& o);
 
 // Brackets one kernel launch with CUDA events while sdf_profile is enabled.
 class ProfRange {
@@ -119,6 +127,24 @@ class ProfRange {
 };
 
 // kernels' host launchers (query.cu)
+// tensor-core pair loop over the direct-form tiles (query_tc.cu)
+struct TcQuery {
+    const float* x = nullptr;      // Q x 3
+    int64_t q = 0;
+    float* phi = nullptr;          // written when direct_out
+    float2* part = nullptr;        // else (W, S) at partial row part_base + chunk
+    const float2* d2 = nullptr;    // pre_split x Q prepass partials
+    float cx = 0.f, cy = 0.f, cz = 0.f;
+    int pre_split = 1;
+    int mode = SDF_LAMBDA_GLOBAL;
+    float C = 64.f, lam = 0.f, offset = 0.f;
+    int part_base = 0;
+};
+sdf_status build_btiles(Cloud& c, cudaStream_t st);
+int64_t tc_query_blocks(int64_t q);
+sdf_status launch_fwd_tc(const Cloud& c, const TcQuery& a, int64_t tiles_per_chunk, int nchunks, int direct_out,
+                         cudaStream_t st);
+
 sdf_status launch_query(const Cloud& c, const float* d_x, int64_t q, float* d_phi,
                         const sdf_query_opts& o, cudaStream_t st);
 // trace.cu

@@ -121,7 +121,7 @@ __global__ void __launch_bounds__(kThreads, kFwdMinBlocks) k_fwd(const float4* _
     char* buf = smem;
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     const int chunk = blockIdx.y;
-    const int64_t t0 = (int64_t)chunk * tiles_per_chunk;
+    const int64_t t0 = a.tile_base + (int64_t)chunk * tiles_per_chunk;
     const int64_t t1 = t0 + tiles_per_chunk < tiles_total ? t0 + tiles_per_chunk : tiles_total;
     const int64_t nt = t1 > t0 ? t1 - t0 : 0;
     if (threadIdx.x == 0) ring.init(kConsumerWarps);
@@ -187,7 +187,7 @@ __global__ void __launch_bounds__(kThreads, kFwdMinBlocks) k_fwd(const float4* _
         if (a.split == 1)
             a.phi[qi[k]] = __fdiv_rn(qs[k].S, qs[k].W) - a.offset;
         else
-            a.part[(size_t)chunk * a.q + qi[k]] = make_float2(qs[k].W, qs[k].S);
+            a.part[(size_t)(a.part_base + chunk) * a.q + qi[k]] = make_float2(qs[k].W, qs[k].S);
     }
 }
 
@@ -205,40 +205,72 @@ __global__ void k_merge(QueryArgs a) {
 
 }  // namespace
 
-Plan make_plan(const Cloud& c, int64_t q, int split_override, int queries_per_cta) {
-    Plan p;
-    p.q = q;
-    p.qblocks = (q + queries_per_cta - 1) / queries_per_cta;
-    p.pre_qblocks = (q + kQueriesPerCta - 1) / kQueriesPerCta;
-    const int64_t tiles = c.tiles_direct + c.tiles_kappa;
+// Point chunks of `tiles` tiles for `qblocks` query blocks: enough CTAs to
+// reach `target`, at least 4 tiles per chunk, at most 64 chunks (or exactly
+// `split_override` chunks when it is positive, capped at one tile each).
+void chunk_tiles(int64_t qblocks, int64_t tiles, int64_t target, int split_override, int64_t& tiles_per_chunk,
+                 int& nchunks) {
     int64_t split = 1;
     if (split_override > 0) {
         split = split_override;
     } else {
-        // aim for at least two waves of 3 resident CTAs per SM
-        const int64_t target = 2LL * 3 * c.num_sms;
-        if (p.qblocks < target) split = (target + p.qblocks - 1) / p.qblocks;
-        const int64_t max_split = tiles / 4 > 0 ? tiles / 4 : 1;   // >= 4 tiles per chunk
+        if (qblocks < target) split = (target + qblocks - 1) / qblocks;
+        const int64_t max_split = tiles / 4 > 0 ? tiles / 4 : 1;
         if (split > max_split) split = max_split;
         if (split > 64) split = 64;
     }
     if (split > tiles) split = tiles;
     if (split < 1) split = 1;
-    p.tiles_per_chunk = (tiles + split - 1) / split;
-    split = (tiles + p.tiles_per_chunk - 1) / p.tiles_per_chunk;
-    p.split = (int)split;
-    p.pre_tiles_per_chunk = (c.pre_tiles + split - 1) / split;
+    tiles_per_chunk = (tiles + split - 1) / split;
+    nchunks = (int)((tiles + tiles_per_chunk - 1) / tiles_per_chunk);
+}
+
+Plan make_plan(const Cloud& c, int64_t q, int split_override, int queries_per_cta) {
+    Plan p;
+    p.q = q;
+    p.qblocks = (q + queries_per_cta - 1) / queries_per_cta;
+    p.pre_qblocks = (q + kQueriesPerCta - 1) / kQueriesPerCta;
+    // aim for at least two waves of 3 resident CTAs per SM
+    chunk_tiles(p.qblocks, c.tiles_direct + c.tiles_kappa, 2LL * 3 * c.num_sms, split_override, p.tiles_per_chunk,
+                p.split);
+    p.pre_tiles_per_chunk = (c.pre_tiles + p.split - 1) / p.split;
     return p;
+}
+
+bool use_tensor_engine(const Cloud& c, const sdf_query_opts& o) {
+    return o.engine != SDF_ENGINE_ALU && o.precision == SDF_F32 && c.btiles != nullptr && c.tiles_direct > 0;
+}
+
+int query_partials(const Cloud& c, int64_t q, const sdf_query_opts& o) {
+    const Plan p = make_plan(c, q, o.split_n);
+    if (!use_tensor_engine(c, o)) return p.split;
+    int64_t tpc = 0;
+    int nd = 0, nk = 0;
+    chunk_tiles(tc_query_blocks(q), c.tiles_direct, 2LL * c.num_sms, o.split_n, tpc, nd);
+    if (c.tiles_kappa > 0) chunk_tiles(p.qblocks, c.tiles_kappa, 2LL * 3 * c.num_sms, o.split_n, tpc, nk);
+    return nd + nk;
 }
 
 sdf_status launch_query(const Cloud& c, const float* d_x, int64_t q, float* d_phi, const sdf_query_opts& o,
                         cudaStream_t st) {
     const Plan p = make_plan(c, q, o.split_n);
+    // Tensor-core engine: the direct-form tiles go to k_fwd_tc in nd chunks,
+    // the kappa-form tiles to k_fwd in nk chunks; both write (W, S) partials
+    // (rows 0..nd-1, then nd..nd+nk-1) that k_merge sums in row order.
+    const bool tc = use_tensor_engine(c, o);
+    int64_t tpc_d = 0, tpc_k = 0;
+    int nd = 0, nk = 0;
+    int nparts = p.split;
+    if (tc) {
+        chunk_tiles(tc_query_blocks(q), c.tiles_direct, 2LL * c.num_sms, o.split_n, tpc_d, nd);
+        if (c.tiles_kappa > 0) chunk_tiles(p.qblocks, c.tiles_kappa, 2LL * 3 * c.num_sms, o.split_n, tpc_k, nk);
+        nparts = nd + nk;
+    }
     QueryArgs a;
     a.x = d_x;
     a.q = q;
     a.phi = d_phi;
-    a.split = p.split;
+    a.split = nparts;
     a.mode = o.lambda_mode;
     a.C = o.C;
     a.lam = o.fixed_lambda;
@@ -256,8 +288,8 @@ sdf_status launch_query(const Cloud& c, const float* d_x, int64_t q, float* d_ph
     cudaError_t e = cudaMallocAsync(&a.d2, (size_t)a.pre_split * q * sizeof(float2), st);
     if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? set_error(SDF_ENOMEM, "sdf_query: scratch")
                                                                 : cuda_error(e, "sdf_query: scratch");
-    if (p.split > 1) {
-        e = cudaMallocAsync(&a.part, (size_t)p.split * q * sizeof(float2), st);
+    if (nparts > 1) {
+        e = cudaMallocAsync(&a.part, (size_t)nparts * q * sizeof(float2), st);
         if (e != cudaSuccess) {
             cudaFreeAsync(a.d2, st);
             return e == cudaErrorMemoryAllocation ? set_error(SDF_ENOMEM, "sdf_query: scratch")
@@ -279,7 +311,8 @@ sdf_status launch_query(const Cloud& c, const float* d_x, int64_t q, float* d_ph
                 c.pre, c.n, c.pre_tiles, p.pre_tiles_per_chunk, a, c.status);
         e = cudaGetLastError();
     }
-    if (e == cudaSuccess) {
+    sdf_status s = SDF_OK;
+    if (e == cudaSuccess && !tc) {
         ProfRange pr(SDF_K_FWD, st);
         auto kern = o.precision == SDF_F16X2 ? k_fwd<SDF_F16X2> : o.precision == SDF_BF16X2 ? k_fwd<SDF_BF16X2>
                                                                                             : k_fwd<SDF_F32>;
@@ -288,13 +321,44 @@ sdf_status launch_query(const Cloud& c, const float* d_x, int64_t q, float* d_ph
                                                           c.status);
         e = cudaGetLastError();
     }
-    if (e == cudaSuccess && p.split > 1) {
+    if (e == cudaSuccess && tc) {
+        {
+            ProfRange pr(SDF_K_FWD_TC, st);
+            TcQuery tq;
+            tq.x = a.x;
+            tq.q = q;
+            tq.phi = a.phi;
+            tq.part = a.part;
+            tq.d2 = a.d2;
+            tq.cx = a.cx;
+            tq.cy = a.cy;
+            tq.cz = a.cz;
+            tq.pre_split = a.pre_split;
+            tq.mode = a.mode;
+            tq.C = a.C;
+            tq.lam = a.lam;
+            tq.offset = a.offset;
+            tq.part_base = 0;
+            s = launch_fwd_tc(c, tq, tpc_d, nd, nparts == 1, st);
+        }
+        if (s == SDF_OK && nk > 0) {
+            ProfRange pr(SDF_K_FWD, st);
+            QueryArgs ak = a;
+            ak.tile_base = c.tiles_direct;
+            ak.part_base = nd;
+            k_fwd<SDF_F32><<<dim3((unsigned)p.qblocks, (unsigned)nk), kThreads, kStages * kTileBytes, st>>>(
+                c.rec, c.n_direct, c.n_kappa, c.tiles_direct, c.tiles_direct + c.tiles_kappa, tpc_k, ak, c.status);
+            e = cudaGetLastError();
+        }
+    }
+    if (e == cudaSuccess && s == SDF_OK && nparts > 1) {
         ProfRange pr(SDF_K_MERGE, st);
         k_merge<<<(unsigned)((q + 255) / 256), 256, 0, st>>>(a);
         e = cudaGetLastError();
     }
     cudaFreeAsync(a.d2, st);
     if (a.part) cudaFreeAsync(a.part, st);
+    if (s != SDF_OK) return s;
     return e == cudaSuccess ? SDF_OK : cuda_error(e, "sdf_query: launch");
 }
 
@@ -355,6 +419,8 @@ extern "C" sdf_status sdf_query_noalloc(sdf_cloud cloud, const float* d_x, int64
     if (o.lambda_mode != SDF_LAMBDA_GLOBAL && o.lambda_mode != SDF_LAMBDA_FIXED)
         return set_error(SDF_EINVAL, "sdf_query_noalloc: unknown lambda_mode");
     if (o.precision != SDF_F32) return set_error(SDF_EINVAL, "sdf_query_noalloc: unsupported precision");
+    if (o.engine != SDF_ENGINE_AUTO && o.engine != SDF_ENGINE_ALU)
+        return set_error(SDF_EINVAL, "sdf_query_noalloc: only the FP32-unit engine is available here");
     if (!(o.C > 0.f) || !std::isfinite(o.C)) return set_error(SDF_EINVAL, "sdf_query_noalloc: C must be > 0");
     if (o.lambda_mode == SDF_LAMBDA_FIXED && (!(o.fixed_lambda >= 0.f) || !std::isfinite(o.fixed_lambda)))
         return set_error(SDF_EINVAL, "sdf_query_noalloc: fixed_lambda must be >= 0");

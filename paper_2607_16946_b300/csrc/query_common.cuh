@@ -33,6 +33,8 @@ struct QueryArgs {
     float C;
     float lam;               // fixed lambda
     float offset;
+    int64_t tile_base = 0;   // first tile of chunk 0 (k_fwd)
+    int part_base = 0;       // partial row of chunk 0 when several kernels share the partials
 };
 
 // --------------------------------------------------------------------------

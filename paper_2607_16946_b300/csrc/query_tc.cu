@@ -1,0 +1,476 @@
+// Tensor-core pair loop for direct-form tori (FP32 result).
+//
+// Every per-pair quantity of the torus SDF (Eq. SingleTorusSDF) and of the
+// weights (Eq. BasicFormulaShifted) that depends on both the query and the
+// point is an inner product of a per-query and a per-point feature vector.
+// In coordinates x'' = (x - centre) / s (centre of the cloud's bounding box,
+// s a power of two at least its diagonal), with f(x) = (x'', |x''|^2, 1) and
+// (u, e1, e2) an orthonormal frame of the torus axis u:
+//   d^2 = |x - p|^2     = f . (-2 p'', 1, |p''|^2)
+//   h   = <x - c, u>    = f . (u, 0, -<c'', u>)
+//   a   = <x - c, e1>   = f . (e1, 0, -<c'', e1>)
+//   b   = <x - c, e2>   = f . (e2, 0, -<c'', e2>)
+// so that rho^2 = a^2 + b^2 is the squared distance to the axis without the
+// cancellation of |x - c|^2 - h^2 near the axis.  The per-point constants R,
+// -sT r and sT come out through the constant feature.  One 128 x 224 x 32
+// product on the tensor cores (two tcgen05 MMAs of K = 16) gives all seven
+// for 128 queries and a 32-point tile.
+//
+// Precision: every feature and coefficient is split into three f16 parts
+// (v = v_hi + v_mid + v_lo for FP32 inputs), and K holds the six cross
+// products hi.hi, hi.mid, mid.hi, hi.lo, mid.mid, lo.hi.  The dropped terms
+// are below 2^-30 of the products, but the smallest part of a value below 1
+// is an f16 subnormal, an absolute floor of about 2^-25 per product (units of
+// s or s^2); with the FP32 rounding of the accumulation the quantities carry
+// absolute errors of order 1e-7 s^2 (d^2) and 1e-7 s |x - c| (h, a, b).
+// Queries farther than 32 s from the centre, where |x''|^2 would leave the
+// range these splits are sized for, take the direct formula from the FP32
+// record for every pair.
+//
+// The epilogue finishes each pair on the FP32 units: rho = sqrt(a^2 + b^2),
+// D = sqrt((rho - R)^2 + h^2), g = sT D - sT r, w = exp2(-L (d - d_min)),
+// W += w, S += w g (four MUFU and nine FMA-pipe operations), with the sums
+// blocked per tile as in the ALU kernel.
+//
+// Warps: 0 producer (bulk copies of B tiles into an 8-stage ring), 1 MMA
+// issuer and TMEM owner (two 224-column accumulators, so the MMA of tile
+// t + 1 overlaps the epilogue of tile t), 2..17 epilogue: four per TMEM lane
+// quadrant, each taking 8 of a tile's 32 points for its 32 query rows.
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+
+#include "query_common.cuh"
+#include "tc_common.cuh"
+
+namespace ptsdf {
+
+using namespace qk;
+
+namespace {
+
+static_assert(kTileRecs == 32, "the tensor-core path packs 32-point tiles");
+
+constexpr int kTcM = 128;                             // queries per CTA (MMA M)
+constexpr int kTcQuant = 7;                           // d^2, h, a, b, R, -sT r, sT
+constexpr int kTcN = kTcQuant * kTileRecs;            // 224 (MMA N)
+constexpr uint32_t kTcSubA = kTcM * 32;               // one K = 16 sub-tile of A (4 KB)
+constexpr uint32_t kTcSubB = kTcN * 32;               // one K = 16 sub-tile of B (7 KB)
+constexpr uint32_t kBTileBytes = 2 * kTcSubB;         // K = 32
+constexpr int kTcStages = 8;
+constexpr int kEpiGroups = 4;                         // epilogue warps per TMEM lane quadrant
+constexpr int kEpiWarps = 4 * kEpiGroups;
+constexpr int kPtsPerWarp = kTileRecs / kEpiGroups;   // 8
+constexpr int kVals = kTcQuant * kPtsPerWarp;         // 56 accumulator columns per epilogue warp
+constexpr int kTcThreads = (2 + kEpiWarps) * 32;
+constexpr uint32_t kTmemCols = 512;                   // two accumulators of kTcN columns
+constexpr uint32_t kBufCols = 256;
+constexpr float kFarSq = 1024.f;                      // |x''|^2 beyond which a query is exact-only
+constexpr uint32_t kTcIdesc = tc::idesc_f16_f32(kTcM, kTcN);
+// dynamic shared memory: A, the ring, the group partial sums; padded so that
+// two CTAs never share an SM (each holds all 512 TMEM columns)
+constexpr size_t kTcSmemUsed = 2 * kTcSubA + (size_t)kTcStages * kBTileBytes + (kEpiGroups - 1) * kTcM * 8;
+constexpr size_t kTcSmemBytes = kTcSmemUsed > 118 * 1024 ? kTcSmemUsed : 118 * 1024;
+
+// B row of quantity k of point j: each epilogue warp's 8 points x 7
+// quantities are 56 consecutive accumulator columns
+__host__ __device__ constexpr int brow(int j, int k) {
+    return (j / kPtsPerWarp) * kVals + k * kPtsPerWarp + (j % kPtsPerWarp);
+}
+
+// Which part of the split each K slot holds (0 hi, 1 mid, 2 lo; -1 zero).
+// A: [hi hi mid 0 | hi mid lo 0], B: [hi mid hi 0 | lo mid hi 0], 5 slots per
+// segment: the products are hi.hi + hi.mid + mid.hi + hi.lo + mid.mid + lo.hi.
+__host__ __device__ constexpr int a_part(int m) {
+    return (m % 16 == 15) ? -1 : (m < 16 ? ((m % 16) / 5 == 2 ? 1 : 0) : (m % 16) / 5);
+}
+__host__ __device__ constexpr int b_part(int m) {
+    return (m % 16 == 15) ? -1 : (m < 16 ? ((m % 16) / 5 == 1 ? 1 : 0) : 2 - (m % 16) / 5);
+}
+static_assert(kTcN % 16 == 0 && kTcN <= 256 && kTcN <= (int)kBufCols, "MMA N for M = 128");
+static_assert(a_part(0) == 0 && a_part(5) == 0 && a_part(10) == 1 && a_part(16) == 0 && a_part(21) == 1 &&
+                  a_part(26) == 2 && a_part(31) == -1,
+              "A slot layout");
+static_assert(b_part(0) == 0 && b_part(5) == 1 && b_part(10) == 0 && b_part(16) == 2 && b_part(21) == 1 &&
+                  b_part(26) == 0 && b_part(15) == -1,
+              "B slot layout");
+
+// byte offset of K slot m of `row` in a two-sub-tile operand
+__host__ __device__ inline uint32_t slot_offset(int row, int m, uint32_t sub_bytes) {
+    return (uint32_t)(m / 16) * sub_bytes + tc::canon_offset(row, m % 16);
+}
+
+__global__ void k_build_btiles(const float4* __restrict__ rec, int64_t n_direct, int64_t tiles_direct, double cx,
+                               double cy, double cz, double inv_s, uint8_t* __restrict__ bt) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= tiles_direct * kTileRecs) return;
+    const int64_t t = i / kTileRecs;
+    const int j = (int)(i % kTileRecs);
+    double b[kTcQuant][5];
+    for (int k = 0; k < kTcQuant; ++k)
+        for (int m = 0; m < 5; ++m) b[k][m] = 0.0;
+    if (i < n_direct) {
+        const float4 r0 = rec[4 * i], r1 = rec[4 * i + 1], r2 = rec[4 * i + 2];
+        const double p[3] = {((double)r0.x - cx) * inv_s, ((double)r0.y - cy) * inv_s, ((double)r0.z - cz) * inv_s};
+        const double c[3] = {((double)r1.x - cx) * inv_s, ((double)r1.y - cy) * inv_s, ((double)r1.z - cz) * inv_s};
+        const double u[3] = {r2.x, r2.y, r2.z};
+        // e1, e2: an orthonormal basis of the plane normal to u
+        const double un = sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+        const double w[3] = {u[0] / un, u[1] / un, u[2] / un};
+        const int ax = (fabs(w[0]) <= fabs(w[1]) && fabs(w[0]) <= fabs(w[2])) ? 0 : (fabs(w[1]) <= fabs(w[2]) ? 1 : 2);
+        double t[3] = {0.0, 0.0, 0.0};
+        t[ax] = 1.0;
+        double e1[3] = {w[1] * t[2] - w[2] * t[1], w[2] * t[0] - w[0] * t[2], w[0] * t[1] - w[1] * t[0]};
+        const double e1n = sqrt(e1[0] * e1[0] + e1[1] * e1[1] + e1[2] * e1[2]);
+        for (int m = 0; m < 3; ++m) e1[m] /= e1n;
+        const double e2[3] = {w[1] * e1[2] - w[2] * e1[1], w[2] * e1[0] - w[0] * e1[2], w[0] * e1[1] - w[1] * e1[0]};
+        for (int m = 0; m < 3; ++m) {
+            b[0][m] = -2.0 * p[m];
+            b[1][m] = u[m];
+            b[2][m] = e1[m];
+            b[3][m] = e2[m];
+        }
+        b[0][3] = 1.0;
+        b[0][4] = p[0] * p[0] + p[1] * p[1] + p[2] * p[2];
+        b[1][4] = -(c[0] * u[0] + c[1] * u[1] + c[2] * u[2]);
+        b[2][4] = -(c[0] * e1[0] + c[1] * e1[1] + c[2] * e1[2]);
+        b[3][4] = -(c[0] * e2[0] + c[1] * e2[1] + c[2] * e2[2]);
+        b[4][4] = (double)r1.w * inv_s;   // R
+        b[5][4] = (double)r2.w * inv_s;   // -sT r
+        b[6][4] = r0.w;                   // sT
+    }
+    uint8_t* tile = bt + (size_t)t * kBTileBytes;
+    for (int k = 0; k < kTcQuant; ++k) {
+        const int row = brow(j, k);
+        __half part[3][5];
+        for (int m = 0; m < 5; ++m) {
+            const double v = b[k][m];
+            part[0][m] = __double2half(v);
+            const double r1 = v - (double)__half2float(part[0][m]);
+            part[1][m] = __double2half(r1);
+            part[2][m] = __double2half(r1 - (double)__half2float(part[1][m]));
+        }
+        for (int m = 0; m < 32; ++m) {
+            const int pt = b_part(m);
+            *reinterpret_cast<__half*>(tile + slot_offset(row, m, kTcSubB)) =
+                pt < 0 ? __float2half(0.f) : part[pt][(m % 16) % 5];
+        }
+    }
+}
+
+struct TcArgs {
+    TcQuery a;
+    const uint8_t* btiles;
+    const float4* rec;
+    int64_t n_direct, tiles_direct, tiles_per_chunk;
+    float s, inv_s;          // coordinate scale of the B tiles (a power of two) and its inverse
+    int direct_out;          // 1: write phi; 0: write (W, S) at partial row part_base + chunk
+};
+
+__device__ __forceinline__ float sqrt_abs_mufu(float x) { return sqrt_mufu(fabsf(x)); }
+
+// One epilogue warp's share of a tile: 8 pairs per lane; v[k * 8 + i] is
+// quantity k of point i.  MASK: only the first `valid` points exist (the
+// last, partial tile).  FAR: some lane of the warp is a far query, whose
+// pairs are recomputed from the FP32 record by the direct formula.
+template <bool MASK, bool FAR>
+__device__ __forceinline__ void tile_pairs(const float (&v)[kVals], int valid, float Ls, float A0, bool exact_lane,
+                                           float x, float y, float z, float inv_s, const float4* __restrict__ rec,
+                                           int64_t slot0, float& W, float& S) {
+    float tw = 0.f, ts = 0.f;
+    if (FAR && exact_lane) {
+        // the direct formula from the FP32 record, rescaled to units of s
+#pragma unroll 1
+        for (int i = 0; i < kPtsPerWarp; ++i) {
+            if (!MASK || i < valid) {
+                const float4 r0 = __ldg(rec + 4 * (slot0 + i));
+                const float4 r1 = __ldg(rec + 4 * (slot0 + i) + 1);
+                const float4 r2 = __ldg(rec + 4 * (slot0 + i) + 2);
+                const float g = g_direct(x, y, z, r1, r2, r0.w) * inv_s;
+                const float dx = x - r0.x, dy = y - r0.y, dz = z - r0.z;
+                const float d = sqrt_mufu(fmaf(dx, dx, fmaf(dy, dy, dz * dz))) * inv_s;
+                const float w = ex2_mufu(fmaf(-Ls, d, A0));
+                tw += w;
+                ts = fmaf(w, g, ts);
+            }
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < kPtsPerWarp; ++i) {
+            if (!MASK || i < valid) {
+                const float h = v[8 + i], pa = v[16 + i], pb = v[24 + i];
+                const float rho = sqrt_mufu(fmaf(pa, pa, pb * pb));
+                const float e = rho - v[32 + i];
+                const float g = fmaf(v[48 + i], sqrt_mufu(fmaf(e, e, h * h)), v[40 + i]);
+                // |d^2|: the products may round a zero distance slightly negative
+                const float d = sqrt_abs_mufu(v[i]);
+                const float w = ex2_mufu(fmaf(-Ls, d, A0));
+                tw += w;
+                ts = fmaf(w, g, ts);
+            }
+        }
+    }
+    W += tw;
+    S += ts;
+}
+
+__global__ void __maxnreg__(112) k_fwd_tc(TcArgs ta, int32_t* status) {
+    extern __shared__ __align__(1024) uint8_t smem[];
+    uint8_t* sA = smem;                                                         // 2 sub-tiles
+    uint8_t* sB = smem + 2 * kTcSubA;                                           // kTcStages tiles
+    float2* sComb = reinterpret_cast<float2*>(sB + (size_t)kTcStages * kBTileBytes);   // [kEpiGroups - 1][kTcM]
+    __shared__ __align__(8) uint64_t bfull[kTcStages], bempty[kTcStages], tfull[2], tempty[2];
+    __shared__ uint32_t tmem_base;
+    __shared__ int abort_flag;
+    const TcQuery& a = ta.a;
+    const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
+    const int chunk = blockIdx.y;
+    const int64_t t0 = (int64_t)chunk * ta.tiles_per_chunk;
+    const int64_t t1 = t0 + ta.tiles_per_chunk < ta.tiles_direct ? t0 + ta.tiles_per_chunk : ta.tiles_direct;
+    const int64_t nt = t1 > t0 ? t1 - t0 : 0;
+
+    if (tid == 0) {
+        for (int s = 0; s < kTcStages; ++s) {
+            mbar_init(&bfull[s], 1);
+            mbar_init(&bempty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&tfull[b], 1);
+            mbar_init(&tempty[b], kEpiWarps);
+        }
+        abort_flag = 0;
+        fence_mbar_init();
+    }
+    if (warp == 1) tc::tmem_alloc(&tmem_base, kTmemCols);
+
+    // epilogue threads: one query row each; group 0 also writes the A row
+    const int quad = warp & 3;            // TMEM lane quadrant this warp may access
+    const int group = (warp - 2) >> 2;    // which 8 points of each tile
+    const int row = quad * 32 + lane;
+    const int64_t qi = (int64_t)blockIdx.x * kTcM + row;
+    float x = 0.f, y = 0.f, z = 0.f, Ls = 0.f, A0 = 0.f;
+    bool exact_lane = false;
+    if (warp >= 2) {
+        const int64_t qq = qi < a.q ? qi : a.q - 1;
+        x = a.x[3 * qq];
+        y = a.x[3 * qq + 1];
+        z = a.x[3 * qq + 2];
+        float2 d2 = a.d2[qq];
+        for (int c = 1; c < a.pre_split; ++c) {
+            const float2 v = a.d2[(size_t)c * a.q + qq];
+            d2.x = fmaxf(d2.x, v.x);
+            d2.y = fminf(d2.y, v.y);
+        }
+        const float dmin = sqrtf(fmaxf(d2.y, 0.f));
+        float lam = a.lam;
+        if (a.mode == SDF_LAMBDA_GLOBAL) {
+            // lambda_x = C / sigma_x = 2 C / d_max (Eq. RelationshipBetweenLambdaAndRadius)
+            const float dmax = sqrtf(fmaxf(d2.x, 0.f));
+            lam = dmax > 0.f ? 2.f * a.C / dmax : 0.f;
+        }
+        const float L = lam * kLog2e;
+        A0 = L * dmin;      // exponent -L (d - d_min), d in world units
+        Ls = L * ta.s;      // the same per unit of d'' = d / s
+        const float xs = (x - a.cx) * ta.inv_s, ys = (y - a.cy) * ta.inv_s, zs = (z - a.cz) * ta.inv_s;
+        const float xx = fmaf(xs, xs, fmaf(ys, ys, zs * zs));
+        exact_lane = !(xx <= kFarSq) && xx == xx;   // far (or infinite); NaN queries stay NaN
+        if (group == 0) {
+            const float f[5] = {xs, ys, zs, xx, 1.f};
+            __half part[3][5];
+#pragma unroll
+            for (int m = 0; m < 5; ++m) {
+                const float fv = exact_lane ? 0.f : f[m];
+                part[0][m] = __float2half_rn(fv);
+                const float r1 = fv - __half2float(part[0][m]);
+                part[1][m] = __float2half_rn(r1);
+                part[2][m] = __float2half_rn(r1 - __half2float(part[1][m]));
+            }
+#pragma unroll
+            for (int m = 0; m < 32; ++m) {
+                const int pt = a_part(m);
+                *reinterpret_cast<__half*>(sA + slot_offset(row, m, kTcSubA)) =
+                    pt < 0 ? __float2half(0.f) : part[pt][(m % 16) % 5];
+            }
+            tc::fence_proxy_async_smem();
+        }
+    }
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tbase = tmem_base;
+
+    if (warp == 0) {
+        // ---- producer: B tiles through the shared-memory ring ----
+        if (lane == 0) {
+            int64_t issued = 0;
+            for (int64_t t = 0; t < nt; ++t) {
+                const int s = (int)(t % kTcStages);
+                if (t >= kTcStages &&
+                    !mbar_wait_bounded(&bempty[s], (uint32_t)(((t / kTcStages) - 1) & 1), &abort_flag, status))
+                    break;
+                mbar_arrive_expect_tx(&bfull[s], kBTileBytes);
+                bulk_g2s(sB + (size_t)s * kBTileBytes, ta.btiles + (size_t)(t0 + t) * kBTileBytes, kBTileBytes,
+                         &bfull[s]);
+                issued = t + 1;
+            }
+            if (*(volatile int*)&abort_flag) {   // copies in flight land before the CTA ends
+                for (int64_t t = (issued > kTcStages ? issued - kTcStages : 0); t < issued; ++t) {
+                    const uint64_t tw = global_ns();
+                    while (!mbar_try_wait(&bfull[t % kTcStages], (uint32_t)((t / kTcStages) & 1)))
+                        if (global_ns() - tw > kWaitLimitNs) break;
+                }
+            }
+        }
+    } else if (warp == 1) {
+        // ---- MMA issuer ----
+        if (lane == 0) {
+            const uint32_t sa = smem_u32(sA);
+            const uint64_t adesc0 = tc::smem_desc(sa), adesc1 = tc::smem_desc(sa + kTcSubA);
+            int64_t issued = 0;
+            for (int64_t t = 0; t < nt; ++t) {
+                const int s = (int)(t % kTcStages);
+                const int b = (int)(t & 1);
+                if (!mbar_wait_bounded(&bfull[s], (uint32_t)((t / kTcStages) & 1), &abort_flag, status)) break;
+                if (t >= 2 && !mbar_wait_bounded(&tempty[b], (uint32_t)(((t >> 1) - 1) & 1), &abort_flag, status))
+                    break;
+                tc::fence_after_sync();
+                const uint32_t d = tbase + (uint32_t)b * kBufCols;
+                const uint32_t sb = smem_u32(sB + (size_t)s * kBTileBytes);
+                tc::mma_f16(d, adesc0, tc::smem_desc(sb), kTcIdesc, 0u);
+                tc::mma_f16(d, adesc1, tc::smem_desc(sb + kTcSubB), kTcIdesc, 1u);
+                tc::commit(&tfull[b]);
+                tc::commit(&bempty[s]);
+                issued = t + 1;
+            }
+            if (issued > 0) {   // the last MMA completes before TMEM is released
+                const uint64_t tw = global_ns();
+                while (!mbar_try_wait(&tfull[(issued - 1) & 1], (uint32_t)(((issued - 1) >> 1) & 1)))
+                    if (global_ns() - tw > kWaitLimitNs) break;
+            }
+        }
+    } else {
+        // ---- epilogue ----
+        float W = 0.f, S = 0.f;
+        const uint32_t lane_addr = tbase + ((uint32_t)(quad * 32) << 16) + (uint32_t)(group * kVals);
+        const int jb = group * kPtsPerWarp;
+        const bool warp_far = __any_sync(0xffffffffu, exact_lane);
+        const int ntiles = (int)nt;
+        // only the last tile of the direct segment can be partial
+        const bool last_partial = t1 == ta.tiles_direct && (ta.n_direct % kTileRecs) != 0;
+        for (int t = 0; t < ntiles; ++t) {
+            const int b = t & 1;
+            // warp-uniform: the TMEM loads below are .sync.aligned
+            const bool ok = mbar_wait_bounded(&tfull[b], (uint32_t)(t >> 1) & 1u, &abort_flag, status);
+            if (!__all_sync(0xffffffffu, ok)) break;
+            tc::fence_after_sync();
+            float v[kVals];
+            const uint32_t ta_addr = lane_addr + (uint32_t)b * kBufCols;
+            tc::tmem_ld16(ta_addr, v, 0);
+            tc::tmem_ld16(ta_addr + 16, v, 16);
+            tc::tmem_ld16(ta_addr + 32, v, 32);
+            tc::tmem_ld8(ta_addr + 48, v, 48);
+            tc::tmem_wait_ld_values(v);
+            tc::fence_before_sync();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&tempty[b]);
+            const int64_t slot0 = (t0 + t) * kTileRecs + jb;
+            if (last_partial && t == ntiles - 1) {
+                const int64_t left = ta.n_direct - slot0;
+                const int valid = (int)(left < 0 ? 0 : left);
+                if (warp_far)
+                    tile_pairs<true, true>(v, valid, Ls, A0, exact_lane, x, y, z, ta.inv_s, ta.rec, slot0, W, S);
+                else
+                    tile_pairs<true, false>(v, valid, Ls, A0, exact_lane, x, y, z, ta.inv_s, ta.rec, slot0, W, S);
+            } else {
+                if (warp_far)
+                    tile_pairs<false, true>(v, kPtsPerWarp, Ls, A0, exact_lane, x, y, z, ta.inv_s, ta.rec, slot0, W,
+                                            S);
+                else
+                    tile_pairs<false, false>(v, kPtsPerWarp, Ls, A0, exact_lane, x, y, z, ta.inv_s, ta.rec, slot0,
+                                             W, S);
+            }
+        }
+        S *= ta.s;   // back to world units
+        // combine the four groups of each query row (named barrier of the epilogue warps)
+        if (group > 0) sComb[(group - 1) * kTcM + row] = make_float2(W, S);
+        asm volatile("bar.sync 1, %0;" ::"r"(kEpiWarps * 32) : "memory");
+        if (group == 0 && qi < a.q) {
+#pragma unroll
+            for (int gq = 0; gq < kEpiGroups - 1; ++gq) {
+                const float2 o = sComb[gq * kTcM + row];
+                W += o.x;
+                S += o.y;
+            }
+            if (ta.direct_out)
+                a.phi[qi] = __fdiv_rn(S, W) - a.offset;
+            else
+                a.part[(size_t)(a.part_base + chunk) * a.q + qi] = make_float2(W, S);
+        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 1) {
+        tc::fence_after_sync();
+        tc::tmem_dealloc(tbase, kTmemCols);
+    }
+}
+
+}  // namespace
+
+float tc_scale_for(float aabb_diag) {
+    int e = 0;
+    std::frexp(std::max((double)aabb_diag, 0x1p-60), &e);   // diag = m 2^e, m in [0.5, 1)
+    e = std::min(std::max(e, -60), 60);
+    return (float)std::ldexp(1.0, e);
+}
+
+sdf_status build_btiles(Cloud& c, cudaStream_t st) {
+    c.tc_scale = tc_scale_for(c.aabb_diag);
+    if (c.tiles_direct == 0) return SDF_OK;
+    cudaError_t e = cudaMalloc(&c.btiles, (size_t)c.tiles_direct * kBTileBytes);
+    if (e != cudaSuccess) {
+        c.btiles = nullptr;
+        return e == cudaErrorMemoryAllocation ? set_error(SDF_ENOMEM, "sdf_build: tensor-core tiles")
+                                              : cuda_error(e, "sdf_build: tensor-core tiles");
+    }
+    const int64_t slots = c.tiles_direct * kTileRecs;
+    k_build_btiles<<<(unsigned)((slots + 127) / 128), 128, 0, st>>>(
+        c.rec, c.n_direct, c.tiles_direct, 0.5 * ((double)c.aabb[0] + c.aabb[3]),
+        0.5 * ((double)c.aabb[1] + c.aabb[4]), 0.5 * ((double)c.aabb[2] + c.aabb[5]), 1.0 / (double)c.tc_scale,
+        c.btiles);
+    e = cudaGetLastError();
+    return e == cudaSuccess ? SDF_OK : cuda_error(e, "sdf_build: k_build_btiles launch");
+}
+
+int64_t tc_query_blocks(int64_t q) { return (q + kTcM - 1) / kTcM; }
+
+sdf_status launch_fwd_tc(const Cloud& c, const TcQuery& a, int64_t tiles_per_chunk, int nchunks, int direct_out,
+                         cudaStream_t st) {
+    static bool attr_done[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_error(e, "sdf_query: cudaGetDevice");
+    if (dev < 0 || dev >= 64) return set_error(SDF_EINVAL, "sdf_query: device id out of range");
+    if (!attr_done[dev]) {
+        e = cudaFuncSetAttribute(k_fwd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmemBytes);
+        if (e != cudaSuccess) return cuda_error(e, "sdf_query: k_fwd_tc shared-memory attribute");
+        attr_done[dev] = true;
+    }
+    TcArgs ta;
+    ta.a = a;
+    ta.btiles = c.btiles;
+    ta.rec = c.rec;
+    ta.n_direct = c.n_direct;
+    ta.tiles_direct = c.tiles_direct;
+    ta.tiles_per_chunk = tiles_per_chunk;
+    ta.s = c.tc_scale;
+    ta.inv_s = 1.f / c.tc_scale;
+    ta.direct_out = direct_out;
+    const dim3 grid((unsigned)tc_query_blocks(a.q), (unsigned)nchunks);
+    k_fwd_tc<<<grid, kTcThreads, kTcSmemBytes, st>>>(ta, c.status);
+    e = cudaGetLastError();
+    return e == cudaSuccess ? SDF_OK : cuda_error(e, "sdf_query: k_fwd_tc launch");
+}
+
+}  // namespace ptsdf

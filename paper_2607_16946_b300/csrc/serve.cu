@@ -93,8 +93,12 @@ int64_t request_need(const Server& S, const sdf_request& r) {
     auto scratch = [&](const Cloud* c, bool grad) {
         const Plan p = make_plan(*c, q, r.opts.split_n, grad ? kConsumerWarps * 32 : kQueriesPerCta);
         int64_t s = (int64_t)p.split * q * 8;                 // prepass partials
-        if (grad) s += (int64_t)p.split * q * 4 + (p.split > 1 ? (int64_t)p.split * q * 52 : 0);
-        else if (p.split > 1) s += (int64_t)p.split * q * 8;
+        if (grad) {
+            s += (int64_t)p.split * q * 4 + (p.split > 1 ? (int64_t)p.split * q * 52 : 0);
+        } else {
+            const int parts = query_partials(*c, q, r.opts);   // (W, S) partial rows
+            if (parts > 1) s += (int64_t)parts * q * 8;
+        }
         return s + 4096;
     };
     const Cloud* ca = S.clouds[r.cloud_id];
@@ -325,6 +329,8 @@ extern "C" sdf_status sdf_serve_submit(sdf_server srv, const sdf_request* req, u
         return set_error(SDF_EINVAL, "sdf_serve_submit: NULL buffer");
     if ((r.opts.precision != SDF_F32 && r.opts.precision != SDF_F16X2 && r.opts.precision != SDF_BF16X2) ||
         (r.kind == SDF_REQ_GRAD && r.opts.precision != SDF_F32) || !(r.opts.C > 0.f) || r.opts.split_n < 0 ||
+        (r.opts.engine != SDF_ENGINE_AUTO && r.opts.engine != SDF_ENGINE_ALU && r.opts.engine != SDF_ENGINE_TENSOR) ||
+        (r.opts.engine == SDF_ENGINE_TENSOR && (r.opts.precision != SDF_F32 || r.kind == SDF_REQ_GRAD)) ||
         (r.opts.lambda_mode != SDF_LAMBDA_GLOBAL && r.opts.lambda_mode != SDF_LAMBDA_FIXED))
         return set_error(SDF_EINVAL, "sdf_serve_submit: bad options");
     auto R = std::make_shared<Request>();

@@ -29,6 +29,7 @@ def main():
                     help="query: sdf_query; grad: sdf_query_grad; backward: sdf_query_grad then "
                          "sdf_backward_params (each call)")
     ap.add_argument("--precision", type=int, default=0, help="sdf_precision of the query")
+    ap.add_argument("--engine", type=int, default=0, help="sdf_engine of the query (0 auto, 1 ALU, 2 tensor)")
     args = ap.parse_args()
 
     import torch
@@ -50,7 +51,7 @@ def main():
     def call():
         nonlocal phi
         if args.mode == "query":
-            cloud.query(x, out=phi, precision=args.precision)
+            cloud.query(x, out=phi, precision=args.precision, engine=args.engine)
         else:
             phi, _, saved = cloud.query_grad(x)
             if args.mode == "backward":
