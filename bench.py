@@ -16,7 +16,8 @@ One JSON line on stdout (rank 0):
   e2e     the same metric through sdf_query_host with pinned host buffers,
           host<->device copies inside the timed region
   roofline  the pair-loop kernel's pairs/s from CUDA events on its stream
-          against the instruction-issue ceiling of the SM array
+          against the ceiling of the SM array's MUFU (XU) pipe, which
+          binds: three square roots and one exp2 per pair
   cpu_baseline  the FP64 CPU oracle on a bounded sample of the same workload
 Under torchrun every rank evaluates its own full grid (weak scaling); the
 timed region is bracketed by barriers and the slowest rank's time is used.
@@ -46,15 +47,40 @@ GRID_RES = 256
 SEED = 1002
 WORKLOAD = ("dense_grid: ring torus N=100000 (R=1, r=0.35, noise 0.005, 2deg vMF normals, analytic "
             "curvature coefficients), Q=256^3 grid over [-1.6,1.6]^3")
-# Issue-slot ceiling of the pair loop.  Algorithmic work per pair (direct torus
-# form): 25 FP32 instructions (two 3-vector differences, two dots, the
-# perpendicular component and its norm, the tube distance, the blend and two
-# accumulations) + 4 MUFU (three square roots and exp2) = 29 issue slots; an SM
-# issues 4 warp-instructions (128 thread-instructions) per clock.  The MUFU pipe
-# sustains about 32 results/clk/SM on this part (ncu: 4 MUFU/pair keep it at 40%
-# while issue is at 82%), so issue, not MUFU, binds.
+# Ceilings of the pair loop, per SM and clock.
+#  Issue: an SM issues 4 warp-instructions (128 thread-instructions) per clock.
+#    FP32-unit loop, direct torus form: 25 FP32 instructions (two 3-vector
+#    differences, two dots, the perpendicular component and its norm, the tube
+#    distance, the blend and two accumulations) + 4 MUFU = 29 issue slots.
+#    Tensor-core loop: 9 FMA-pipe instructions + 4 MUFU per pair (the
+#    products come from the tensor cores).
+#  MUFU (XU pipe): sdf_probe_rates measures the unit rates on the box; on
+#    B300 (sm_103a) sqrt / rsqrt.approx retire 16 results per SM per clock
+#    and ex2.approx 32.  A pair needs three square roots (|x - p|, the axis
+#    distance, the tube distance) and one exp2: 3/16 + 1/32 = 7/32 SM-clocks,
+#    32/7 = 4.57 pairs/clk/SM.  This binds the tensor-core loop (issue
+#    ceiling 128/13 = 9.8) and nearly ties the FP32-unit loop's issue
+#    ceiling (128/29 = 4.41).
 INSTR_PER_PAIR = 29
+TC_INSTR_PER_PAIR = 13
 THREAD_INSTR_PER_SM_CLK = 128
+NOMINAL_RATES = {"sqrt": 16.0, "rsqrt": 16.0, "ex2": 32.0, "fma": 128.0}
+
+
+def probe_rates(L):
+    """Unit rates (results per SM per clock) measured by sdf_probe_rates, or
+    the nominal ones if the probe fails."""
+    buf = (ctypes.c_double * 4)()
+    if L.sdf_probe_rates(buf) != 0:
+        return dict(NOMINAL_RATES, source="nominal (probe failed)")
+    return {"sqrt": buf[0], "rsqrt": buf[1], "ex2": buf[2], "fma": buf[3], "source": "measured (sdf_probe_rates)"}
+
+
+def pair_ceiling(rates, instr_per_pair):
+    """pairs per SM clock: the lower of the MUFU and the issue ceilings."""
+    mufu = 1.0 / (3.0 / rates["sqrt"] + 1.0 / rates["ex2"])
+    issue = rates["fma"] / instr_per_pair
+    return min(mufu, issue), mufu, issue
 FALLBACK_MAX_SM_MHZ = 2032.0
 
 
@@ -127,16 +153,16 @@ class ClockSampler:
 
 def kernel_source_sha() -> str:
     h = hashlib.sha256()
-    for f in ("query.cu", "device_common.cuh", "internal.h"):
+    for f in ("query_tc.cu", "tc_common.cuh", "query_common.cuh", "device_common.cuh", "internal.h"):
         with open(os.path.join(ROOT, "paper_2607_16946_b300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
 def committed_traffic():
-    """dram bytes per pair-loop launch from the committed ncu summary, if it was
-    taken on the current kernel source; else None."""
-    path = os.path.join(ROOT, "profiles", "fwd_dense_grid_traffic.json")
+    """dram bytes per launch of the tensor-core pair loop from the committed
+    ncu summary, if it was taken on the current kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", "fwd_tc_dense_grid_traffic.json")
     try:
         with open(path) as fh:
             d = json.load(fh)
@@ -370,9 +396,10 @@ def run_trace_leg(dev, steps: int = 2):
 
 
 def run_mixed_leg(dev, cloud, x, phi, points, normals, params, steps: int = 2):
-    """The dense-grid step with packed-half weights (SDF_F16X2, SDF_BF16X2):
-    device Gpairs/s, and the error against the FP64 oracle on 4,096 seeded
-    grid nodes, relative to the AABB diagonal, next to FP32's."""
+    """The dense-grid step on each engine and precision: FP32 on the tensor
+    cores (the default), FP32 on the FP32 units, and packed-half weights
+    (SDF_F16X2, SDF_BF16X2, FP32 units): device Gpairs/s, and the error against
+    the FP64 oracle on 4,096 seeded grid nodes, relative to the AABB diagonal."""
     import torch
 
     import oracle
@@ -383,21 +410,25 @@ def run_mixed_leg(dev, cloud, x, phi, points, normals, params, steps: int = 2):
     ref = oracle.Cloud(points, normals, params).phi(synth.grid_query_index(idx, GRID_RES))
     diag = float(np.linalg.norm(points.max(0) - points.min(0)))
     out = {}
-    for name, code in (("fp32", _abi.SDF_F32), ("f16x2", _abi.SDF_F16X2), ("bf16x2", _abi.SDF_BF16X2)):
-        cloud.query(x, out=phi, precision=code)
+    for name, code, eng in (("fp32_tensor", _abi.SDF_F32, _abi.SDF_ENGINE_TENSOR),
+                            ("fp32_alu", _abi.SDF_F32, _abi.SDF_ENGINE_ALU),
+                            ("f16x2", _abi.SDF_F16X2, _abi.SDF_ENGINE_ALU),
+                            ("bf16x2", _abi.SDF_BF16X2, _abi.SDF_ENGINE_ALU)):
+        cloud.query(x, out=phi, precision=code, engine=eng)
         torch.cuda.synchronize(dev)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
         for _ in range(steps):
-            cloud.query(x, out=phi, precision=code)
+            cloud.query(x, out=phi, precision=code, engine=eng)
         e1.record()
         torch.cuda.synchronize(dev)
         s = e0.elapsed_time(e1) / 1e3 / steps
         err = np.abs(phi[torch.as_tensor(idx, device=dev)].double().cpu().numpy() - ref) / diag
         out[name] = {"value": x.shape[0] * N_POINTS / s / 1e9, "unit": UNIT, "ms_per_step": s * 1e3,
                      "err_max_rel_diag": float(err.max()), "err_p99_rel_diag": float(np.quantile(err, 0.99))}
-    out["note"] = ("packed-half exp2 of a lane's two weights; distances, torus SDF and sums in FP32; "
-                   "error = |phi - phi_oracle| / AABB diagonal on 4096 seeded grid nodes")
+    out["note"] = ("fp32_tensor: products on the tensor cores (split f16, FP32 accumulate), pairs finished in "
+                   "FP32; fp32_alu: FP32 units only; f16x2/bf16x2: packed-half exp2 of a lane's two weights on "
+                   "the FP32-unit loop; error = |phi - phi_oracle| / AABB diagonal on 4096 seeded grid nodes")
     return out
 
 
@@ -501,34 +532,49 @@ def run_ours(args, rank, world, local):
     cs = clk.summary()
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     fmax = cs["sm_max_mhz"] or FALLBACK_MAX_SM_MHZ
-    peak = sms * fmax * 1e6 * THREAD_INSTR_PER_SM_CLK / INSTR_PER_PAIR / 1e9
-    fwd = prof.get("fwd", {"launches": 0, "ms": float("nan")})
-    per_launch_s = fwd["ms"] / max(fwd["launches"], 1) / 1e3
-    achieved = pairs_per_step / per_launch_s / 1e9
-    traffic = committed_traffic()
+    # the dominant kernel: the tensor-core pair loop over the direct-form tiles
+    # (the kappa-form tiles, 2.6% of the points here, run on the FP32-unit loop)
+    n_direct = cloud.info()["n_direct"]
+    rates = probe_rates(L)
+    if "fwd_tc" in prof:
+        kname, kpairs = "k_fwd_tc", q * n_direct
+        per_sm_clk, mufu_c, issue_c = pair_ceiling(rates, TC_INSTR_PER_PAIR)
+        kp = prof["fwd_tc"]
+        traffic = committed_traffic()
+    else:
+        kname, kpairs = "k_fwd", pairs_per_step
+        per_sm_clk, mufu_c, issue_c = pair_ceiling(rates, INSTR_PER_PAIR)
+        kp = prof.get("fwd", {"launches": 0, "ms": float("nan")})
+        traffic = None
+    basis = (f"{'MUFU' if mufu_c <= issue_c else 'issue'} ceiling: {sms} SMs x {fmax:.0f} MHz x "
+             f"{per_sm_clk:.3f} pairs/clk/SM; MUFU 1/(3/sqrt + 1/ex2) = {mufu_c:.3f}, issue fma/"
+             f"{TC_INSTR_PER_PAIR if kname == 'k_fwd_tc' else INSTR_PER_PAIR} = {issue_c:.3f} "
+             f"(unit rates {rates['source']})")
+    peak = sms * fmax * 1e6 * per_sm_clk / 1e9
+    per_launch_s = kp["ms"] / max(kp["launches"], 1) / 1e3
+    achieved = kpairs / per_launch_s / 1e9
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": elapsed_s / args.steps * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "N": N_POINTS, "Q": q, "C": 64, "lambda": "global",
-                   "precision": "fp32", "parallelism": f"replicas{world}" if world > 1 else "single",
+                   "precision": "fp32", "engine": "auto (tensor cores for direct-form tiles)",
+                   "parallelism": f"replicas{world}" if world > 1 else "single",
                    "l2": "inputs larger than L2 (queries 201 MB, phi 67 MB); not flushed"},
         "queries_per_s": world * q * args.steps / elapsed_s,
         "e2e": {"value": world * pairs_per_step * args.steps / e2e_s / 1e9, "unit": UNIT,
                 "h2d_bytes_per_step": q * 12, "d2h_bytes_per_step": q * 4},
         "gpu_launches": launches_total,
         "kernels": prof,
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": UNIT, "frac": achieved / peak,
-                     "traffic": traffic,
-                     "peak_basis": f"issue ceiling: {sms} SMs x {fmax:.0f} MHz x {THREAD_INSTR_PER_SM_CLK} "
-                                   f"thread-instr/clk / {INSTR_PER_PAIR} instr per pair (derived from unit "
-                                   f"counts and the max SM clock, not measured)"},
+        "roofline": {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak, "unit": UNIT,
+                     "frac": achieved / peak, "traffic": traffic, "peak_basis": basis,
+                     "unit_rates_per_sm_clk": {k: v for k, v in rates.items()}},
         "clocks": cs,
         "outputs_finite": finite,
     }
     if world == 1 and not args.no_extra_legs:
         line["mixed"] = run_mixed_leg(dev, cloud, x, phi, p, n, a)
-        line["grad"] = run_grad_leg(dev, sms * fmax * 1e6 * THREAD_INSTR_PER_SM_CLK / 1e9)
+        line["grad"] = run_grad_leg(dev, sms * fmax * 1e6 * rates["fma"] / 1e9)
         line["trace"] = run_trace_leg(dev)
     if world == 1 and args.serve_requests > 0:
         del hx, hphi

@@ -340,6 +340,14 @@ PTSDF_API sdf_status sdf_serve_shutdown(sdf_server srv);
  * their total device time in milliseconds since the last enable.  Enabling
  * clears earlier records; disabling stops recording and keeps them.
  * ------------------------------------------------------------------------- */
+/* Measures, on the current device, the sustained throughput of the
+ * operations that bound the pair loops, in results per SM per SM clock:
+ * rates[0] sqrt.approx, rates[1] rsqrt.approx, rates[2] ex2.approx (the
+ * special-function unit) and rates[3] FP32 FMA.  A measurement aid for
+ * roofline reporting (about 20 ms of kernels on every SM); it does not touch
+ * any cloud.  rates must hold 4 doubles. */
+PTSDF_API sdf_status sdf_probe_rates(double* rates);
+
 enum { SDF_K_PREPASS = 0, SDF_K_FWD = 1, SDF_K_MERGE = 2, SDF_K_BUILD = 3, SDF_K_FWD_GRAD = 4, SDF_K_BWD = 5,
        SDF_K_FWD_TC = 6, SDF_K_COUNT_ = 7 };
 PTSDF_API sdf_status sdf_profile_enable(int32_t on);

@@ -41,6 +41,7 @@ class sdf_query_opts(ctypes.Structure):
 _P, _I64, _I32, _F = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_float
 SIGNATURES = {
     "sdf_opts_default": (ctypes.c_int, [ctypes.POINTER(sdf_query_opts)]),
+    "sdf_probe_rates": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double)]),
     "sdf_build": (ctypes.c_int, [_P, _P, _P, _I64, _P, ctypes.POINTER(_P)]),
     "sdf_destroy": (ctypes.c_int, [_P]),
     "sdf_cloud_info": (ctypes.c_int, [_P, ctypes.POINTER(_I64), ctypes.POINTER(_F), ctypes.POINTER(_I64),

@@ -53,7 +53,7 @@ namespace ptsdf {
 #define PTSDF_UNROLL 2
 #endif
 #ifndef PTSDF_FWD_MINB
-#define PTSDF_FWD_MINB 1
+#define PTSDF_FWD_MINB 4
 #endif
 constexpr int kTileRecs = PTSDF_TILE_RECS;   // records per main-loop tile (32 x 64 B = 2 KB)
 constexpr int kRecFloats = 16;

@@ -230,9 +230,9 @@ Plan make_plan(const Cloud& c, int64_t q, int split_override, int queries_per_ct
     p.q = q;
     p.qblocks = (q + queries_per_cta - 1) / queries_per_cta;
     p.pre_qblocks = (q + kQueriesPerCta - 1) / kQueriesPerCta;
-    // aim for at least two waves of 3 resident CTAs per SM
-    chunk_tiles(p.qblocks, c.tiles_direct + c.tiles_kappa, 2LL * 3 * c.num_sms, split_override, p.tiles_per_chunk,
-                p.split);
+    // aim for at least two waves of the resident CTAs per SM
+    chunk_tiles(p.qblocks, c.tiles_direct + c.tiles_kappa, 2LL * kFwdMinBlocks * c.num_sms, split_override,
+                p.tiles_per_chunk, p.split);
     p.pre_tiles_per_chunk = (c.pre_tiles + p.split - 1) / p.split;
     return p;
 }
@@ -247,7 +247,7 @@ int query_partials(const Cloud& c, int64_t q, const sdf_query_opts& o) {
     int64_t tpc = 0;
     int nd = 0, nk = 0;
     chunk_tiles(tc_query_blocks(q), c.tiles_direct, 2LL * c.num_sms, o.split_n, tpc, nd);
-    if (c.tiles_kappa > 0) chunk_tiles(p.qblocks, c.tiles_kappa, 2LL * 3 * c.num_sms, o.split_n, tpc, nk);
+    if (c.tiles_kappa > 0) chunk_tiles(p.qblocks, c.tiles_kappa, 2LL * kFwdMinBlocks * c.num_sms, o.split_n, tpc, nk);
     return nd + nk;
 }
 
@@ -263,7 +263,8 @@ sdf_status launch_query(const Cloud& c, const float* d_x, int64_t q, float* d_ph
     int nparts = p.split;
     if (tc) {
         chunk_tiles(tc_query_blocks(q), c.tiles_direct, 2LL * c.num_sms, o.split_n, tpc_d, nd);
-        if (c.tiles_kappa > 0) chunk_tiles(p.qblocks, c.tiles_kappa, 2LL * 3 * c.num_sms, o.split_n, tpc_k, nk);
+        if (c.tiles_kappa > 0)
+            chunk_tiles(p.qblocks, c.tiles_kappa, 2LL * kFwdMinBlocks * c.num_sms, o.split_n, tpc_k, nk);
         nparts = nd + nk;
     }
     QueryArgs a;

@@ -198,3 +198,16 @@ def test_engine_option_checks(ptsdf):
         cl.query(x, engine=7)
     with pytest.raises(ptsdf.SdfError):
         cl.query_grad(x, engine=ptsdf.SDF_ENGINE_TENSOR)
+
+
+def test_probe_rates(ptsdf):
+    """sdf_probe_rates returns plausible per-SM, per-clock unit rates: the
+    special-function unit slower than FMA, exp2 at least as fast as sqrt."""
+    import ctypes
+    buf = (ctypes.c_double * 4)()
+    assert ptsdf.lib().sdf_probe_rates(buf) == 0
+    sqrt_r, rsqrt_r, ex2_r, fma_r = list(buf)
+    for r in (sqrt_r, rsqrt_r, ex2_r):
+        assert 2.0 <= r <= 64.0, list(buf)
+    assert 32.0 <= fma_r <= 260.0, list(buf)
+    assert ex2_r >= 0.9 * sqrt_r and fma_r > ex2_r
