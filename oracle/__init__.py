@@ -68,6 +68,9 @@ def _load():
         _lib.or_fit_record.argtypes = [P, P, P, P]
         _lib.or_torus_sdf.argtypes = [P, P, f64, f64, P, i64, P]
         _lib.or_frame.argtypes = [P, P, P]
+        _lib.or_phi_radius.argtypes = [P, f64, f64, i32, P, i64, P, P, i32]
+        _lib.or_knn_mean_distance.argtypes = [P, i64, i32, i32]
+        _lib.or_knn_mean_distance.restype = f64
     return _lib
 
 
@@ -117,6 +120,22 @@ class Cloud:
                        _ptr(st) if stats else None, threads or default_threads())
         return (out, st) if stats else out
 
+    def phi_radius(self, x, lam: float, reval: float | None = None, C: float = 64.0, kfb: int = 32,
+                   threads: int | None = None, used: bool = False):
+        """Radius-limited blend (Sec. 4.2, "Acceleration and adaptive lambda"):
+        constant lambda, the points within R_eval (default 2 C / lambda), else
+        the kfb nearest.  used: also return, per query, the number of points
+        inside R_eval (or minus the number of fallback neighbours)."""
+        x = _f64(x, 3)
+        m = x.shape[0]
+        if reval is None:
+            reval = 2.0 * C / lam
+        out = np.empty(m)
+        u = np.empty(m) if used else None
+        _load().or_phi_radius(self._h, float(lam), float(reval), int(kfb), _ptr(x), m, _ptr(out),
+                              _ptr(u) if used else None, threads or default_threads())
+        return (out, u) if used else out
+
     def grad_x(self, x, C: float = 64.0, mode: int = GLOBAL, lam: float = 0.0,
                threads: int | None = None):
         x = _f64(x, 3)
@@ -156,6 +175,14 @@ class Cloud:
 FIT_FIELDS = {"q": slice(0, 3), "nstar": slice(3, 6), "vmin": slice(6, 9), "u": slice(9, 12),
               "c": slice(12, 15), "R": 15, "r": 16, "kmin": 17, "kmax": 18, "kplus": 19,
               "kminus": 20, "H": 21, "K": 22, "sign": 23, "flat": 24, "plane": 25}
+
+
+def knn_mean_distance(points, k: int = 64, threads: int | None = None) -> float:
+    """D of the paper's lambda heuristic (lambda = 10^3 / D): the mean distance
+    between a point and its k nearest other points, averaged over the cloud
+    (Sec. 4.2, "Acceleration and adaptive lambda").  Brute force, FP64."""
+    p = _f64(points, 3)
+    return float(_load().or_knn_mean_distance(_ptr(p), p.shape[0], int(k), threads or default_threads()))
 
 
 def fit_record(p, n, a) -> dict:

@@ -20,7 +20,10 @@
  *   - gradients by forward-mode dual numbers through the literal definition
  *     (App. D states the x-gradient; the dual numbers also carry the
  *     dependence of lambda_x on x, and d/d(a00..a20) through the fit)
- *   - a sphere tracer stepping by phi (Sec. 6, "Direct visualization").
+ *   - a sphere tracer stepping by phi (Sec. 6, "Direct visualization")
+ *   - the radius-limited blend with a constant lambda and the k-nearest
+ *     fallback, and the mean k-nearest-neighbour distance D of the lambda
+ *     heuristic (Sec. 4.2, "Acceleration and adaptive lambda").
  *
  * Readings taken where the paper is silent or garbled (each is listed in the
  * design notes with its evidence):
@@ -602,4 +605,155 @@ void or_trace(const or_cloud* C, int mode, double Cconst, double lambda,
         pthread_create(&th[k], NULL, trace_worker, &jobs[k]);
     }
     for (int k = 0; k < threads; ++k) pthread_join(th[k], NULL);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Radius-limited evaluation (Sec. 4.2, "Acceleration and adaptive lambda"). */
+/* lambda is one constant for the whole cloud; only the points with          */
+/* ||x - p_i|| <= R_eval enter the two sums of Eq. BasicFormulaShifted; a    */
+/* query with no point inside R_eval sums over its k_fb (32) nearest points. */
+/* The paper picks lambda = 10^3 / D, D the mean distance between a point    */
+/* and its 64 nearest neighbours averaged over the cloud, and               */
+/* R_eval = 2 C / lambda; both are arguments here so that tests can pin the */
+/* set selection by construction.  The exponent is shifted by the smallest  */
+/* distance in the set (the ratio does not depend on the shift, X13).       */
+/* ------------------------------------------------------------------------ */
+
+/* Keeps the k smallest (d, i) seen so far in ascending order; points arrive
+ * in increasing i, so a strict comparison leaves ties with the lower index. */
+static void topk_insert(double* bd, int64_t* bi, int* cnt, int k, double d, int64_t i) {
+    if (*cnt == k && !(d < bd[k - 1])) return;
+    int j = (*cnt < k) ? (*cnt)++ : k - 1;
+    while (j > 0 && d < bd[j - 1]) {
+        bd[j] = bd[j - 1];
+        bi[j] = bi[j - 1];
+        --j;
+    }
+    bd[j] = d;
+    bi[j] = i;
+}
+
+static double phi_radius_one(const or_cloud* C, double lambda, double reval, int kfb, const double x[3],
+                             double* used) {
+    const int64_t n = C->n;
+    int64_t inside = 0;
+    double dmin = INFINITY;
+    for (int64_t i = 0; i < n; ++i) {
+        const double* p = C->tori[i].p;
+        double w3[3] = {x[0] - p[0], x[1] - p[1], x[2] - p[2]};
+        double d = sqrt(dot3(w3, w3));
+        if (d <= reval) {
+            ++inside;
+            if (d < dmin) dmin = d;
+        }
+    }
+    double W = 0.0, S = 0.0;
+    if (inside > 0) {
+        for (int64_t i = 0; i < n; ++i) {
+            const double* p = C->tori[i].p;
+            double w3[3] = {x[0] - p[0], x[1] - p[1], x[2] - p[2]};
+            double d = sqrt(dot3(w3, w3));
+            if (d > reval) continue;
+            double w = exp(-lambda * (d - dmin));
+            W += w;
+            S += w * g_plain(&C->tori[i], x);
+        }
+        if (used) *used = (double)inside;
+        return S / W;
+    }
+    /* fallback: the k_fb nearest points */
+    int k = kfb < n ? kfb : (int)n;
+    double* bd = (double*)malloc(sizeof(double) * (size_t)k);
+    int64_t* bi = (int64_t*)malloc(sizeof(int64_t) * (size_t)k);
+    int cnt = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        const double* p = C->tori[i].p;
+        double w3[3] = {x[0] - p[0], x[1] - p[1], x[2] - p[2]};
+        topk_insert(bd, bi, &cnt, k, sqrt(dot3(w3, w3)), i);
+    }
+    for (int j = 0; j < cnt; ++j) {
+        double w = exp(-lambda * (bd[j] - bd[0]));
+        W += w;
+        S += w * g_plain(&C->tori[bi[j]], x);
+    }
+    free(bd);
+    free(bi);
+    if (used) *used = -(double)cnt;
+    return S / W;
+}
+
+typedef struct {
+    const or_cloud* C; double lambda, reval; int kfb; const double* x; double* phi; double* used;
+    int64_t q0, q1;
+} radius_job;
+
+static void* radius_worker(void* arg) {
+    radius_job* J = (radius_job*)arg;
+    for (int64_t j = J->q0; j < J->q1; ++j)
+        J->phi[j] = phi_radius_one(J->C, J->lambda, J->reval, J->kfb, J->x + 3 * j, J->used ? J->used + j : NULL);
+    return NULL;
+}
+
+/* phi at m queries, radius-limited; used[j] (optional) = the number of points
+ * inside R_eval, or minus the number of fallback neighbours. */
+void or_phi_radius(const or_cloud* C, double lambda, double reval, int kfb, const double* x, int64_t m,
+                   double* phi, double* used, int threads) {
+    threads = clamp_threads(threads, m);
+    pthread_t th[256];
+    radius_job jobs[256];
+    int64_t per = (m + threads - 1) / threads;
+    for (int k = 0; k < threads; ++k) {
+        int64_t q0 = k * per, q1 = q0 + per < m ? q0 + per : m;
+        jobs[k] = (radius_job){C, lambda, reval, kfb, x, phi, used, q0, q1 > q0 ? q1 : q0};
+        pthread_create(&th[k], NULL, radius_worker, &jobs[k]);
+    }
+    for (int k = 0; k < threads; ++k) pthread_join(th[k], NULL);
+}
+
+/* D of the lambda heuristic: for every point the mean of the distances to
+ * its k nearest other points (all n - 1 of them when n - 1 < k), averaged
+ * over the points.  Brute force.  n = 1 gives 0. */
+typedef struct { const double* pts; int64_t n; int k; int64_t i0, i1; double sum; } knn_job;
+
+static void* knn_worker(void* arg) {
+    knn_job* J = (knn_job*)arg;
+    int k = (int64_t)J->k < J->n - 1 ? J->k : (int)(J->n - 1);
+    double* bd = (double*)malloc(sizeof(double) * (size_t)(k > 0 ? k : 1));
+    int64_t* bi = (int64_t*)malloc(sizeof(int64_t) * (size_t)(k > 0 ? k : 1));
+    J->sum = 0.0;
+    for (int64_t i = J->i0; i < J->i1 && k > 0; ++i) {
+        int cnt = 0;
+        const double* a = J->pts + 3 * i;
+        for (int64_t j = 0; j < J->n; ++j) {
+            if (j == i) continue;
+            const double* b = J->pts + 3 * j;
+            double v[3] = {a[0] - b[0], a[1] - b[1], a[2] - b[2]};
+            topk_insert(bd, bi, &cnt, k, sqrt(dot3(v, v)), j);
+        }
+        double s = 0.0;
+        for (int t = 0; t < cnt; ++t) s += bd[t];
+        J->sum += s / cnt;
+    }
+    free(bd);
+    free(bi);
+    return NULL;
+}
+
+double or_knn_mean_distance(const double* pts, int64_t n, int k, int threads) {
+    if (n < 2 || k < 1) return 0.0;
+    threads = clamp_threads(threads, n);
+    pthread_t th[256];
+    knn_job jobs[256];
+    int64_t per = (n + threads - 1) / threads;
+    for (int t = 0; t < threads; ++t) {
+        int64_t i0 = t * per, i1 = i0 + per < n ? i0 + per : n;
+        jobs[t] = (knn_job){pts, n, k, i0, i1 > i0 ? i1 : i0, 0.0};
+        pthread_create(&th[t], NULL, knn_worker, &jobs[t]);
+    }
+    double total = 0.0;
+    for (int t = 0; t < threads; ++t) {
+        pthread_join(th[t], NULL);
+        total += jobs[t].sum;
+    }
+    return total / (double)n;
 }
