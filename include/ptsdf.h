@@ -81,9 +81,17 @@ typedef enum { SDF_ENGINE_AUTO = 0, SDF_ENGINE_ALU = 1, SDF_ENGINE_TENSOR = 2 } 
 
 typedef enum {
     SDF_LAMBDA_GLOBAL = 0,  /* lambda_x = C / sigma_x, sigma_x = max_i ||x - p_i|| / 2 (the paper's rule) */
-    SDF_LAMBDA_FIXED = 1    /* lambda_x = fixed_lambda for every query (Sec. 4.2, "Acceleration and
+    SDF_LAMBDA_FIXED = 1,   /* lambda_x = fixed_lambda for every query (Sec. 4.2, "Acceleration and
                                adaptive lambda", without the radius cut-off) */
+    SDF_LAMBDA_RADIUS = 2   /* Sec. 4.2, "Acceleration and adaptive lambda": lambda = fixed_lambda (> 0)
+                               for every query, and only the points within R_eval = 2 C / lambda of the
+                               query are summed; a query with none of them sums over its
+                               SDF_RADIUS_FALLBACK_K nearest points.  The paper's lambda is
+                               10^3 / D with D from sdf_knn_mean_distance(cloud, 64).  FP32 only;
+                               no gradients. */
 } sdf_lambda_mode;
+
+enum { SDF_RADIUS_FALLBACK_K = 32 };
 
 typedef struct {
     int32_t lambda_mode;   /* sdf_lambda_mode */
@@ -333,6 +341,17 @@ PTSDF_API sdf_status sdf_serve_stats(sdf_server srv, int32_t* queued, int32_t* i
 PTSDF_API sdf_status sdf_serve_shutdown(sdf_server srv);
 
 /* ---------------------------------------------------------------------------
+ * sdf_knn_mean_distance -- D of the lambda heuristic of Sec. 4.2
+ * ("Acceleration and adaptive lambda"): for every point of the cloud the
+ * mean of the distances to its k nearest other points (all of them when the
+ * cloud has k or fewer other points), averaged over the points, in FP64 from
+ * FP32 distances.  k in [1, 64] (the paper uses 64).  The paper then sets
+ * lambda = 10^3 / D and R_eval = 2 C / lambda (SDF_LAMBDA_RADIUS).
+ * Synchronous on `stream`; a one-point cloud gives D = 0.
+ * ------------------------------------------------------------------------- */
+PTSDF_API sdf_status sdf_knn_mean_distance(sdf_cloud cloud, int32_t k, double* D, void* stream);
+
+/* ---------------------------------------------------------------------------
  * Kernel timing (a tracing aid, not part of the method).  While enabled,
  * every kernel the library launches is bracketed by two CUDA events recorded
  * on the stream it is launched on.  sdf_profile_read waits for the recorded
@@ -349,7 +368,7 @@ PTSDF_API sdf_status sdf_serve_shutdown(sdf_server srv);
 PTSDF_API sdf_status sdf_probe_rates(double* rates);
 
 enum { SDF_K_PREPASS = 0, SDF_K_FWD = 1, SDF_K_MERGE = 2, SDF_K_BUILD = 3, SDF_K_FWD_GRAD = 4, SDF_K_BWD = 5,
-       SDF_K_FWD_TC = 6, SDF_K_COUNT_ = 7 };
+       SDF_K_FWD_TC = 6, SDF_K_RADIUS = 7, SDF_K_KNN = 8, SDF_K_COUNT_ = 9 };
 PTSDF_API sdf_status sdf_profile_enable(int32_t on);
 PTSDF_API sdf_status sdf_profile_read(int32_t kernel, int64_t* launches, double* total_ms);
 /* Name of a kernel family (NULL for an id out of range). */

@@ -18,9 +18,11 @@ import numpy as np
 
 from . import _abi
 from ._abi import (SDF_DIFFERENCE, SDF_ENGINE_ALU, SDF_ENGINE_AUTO, SDF_ENGINE_TENSOR, SDF_INTERSECT,
-                   SDF_LAMBDA_FIXED, SDF_LAMBDA_GLOBAL, SDF_UNION, SdfError, check, lib, make_opts)
+                   SDF_LAMBDA_FIXED, SDF_LAMBDA_GLOBAL, SDF_LAMBDA_RADIUS, SDF_UNION, SdfError, check, lib,
+                   make_opts)
 
-__all__ = ["Cloud", "SdfError", "SDF_LAMBDA_GLOBAL", "SDF_LAMBDA_FIXED", "SDF_UNION", "SDF_INTERSECT",
+__all__ = ["Cloud", "SdfError", "SDF_LAMBDA_GLOBAL", "SDF_LAMBDA_FIXED", "SDF_LAMBDA_RADIUS", "SDF_UNION",
+           "SDF_INTERSECT",
            "SDF_DIFFERENCE", "SDF_ENGINE_AUTO", "SDF_ENGINE_ALU", "SDF_ENGINE_TENSOR", "make_opts", "lib", "sdf",
            "combine"]
 
@@ -94,6 +96,18 @@ class Cloud:
         check(lib().sdf_query(self._h, ctypes.c_void_p(x.data_ptr()), q, ctypes.c_void_p(out.data_ptr()),
                               ctypes.byref(o), _stream_ptr(stream)), "sdf_query")
         return out
+
+    def knn_mean_distance(self, k: int = 64, stream=None) -> float:
+        """D of Sec. 4.2's lambda heuristic: the mean distance between a point and
+        its k nearest other points, averaged over the cloud (sdf_knn_mean_distance)."""
+        D = ctypes.c_double()
+        check(lib().sdf_knn_mean_distance(self._h, int(k), ctypes.byref(D), _stream_ptr(stream)),
+              "sdf_knn_mean_distance")
+        return D.value
+
+    def paper_lambda(self, k: int = 64) -> float:
+        """The paper's constant lambda for the radius-limited evaluation, 10^3 / D."""
+        return 1e3 / self.knn_mean_distance(k)
 
     def query_grad(self, x, stream=None, saved=True, **opts):
         """(phi, d phi / d x, saved statistics or None) at the rows of x."""

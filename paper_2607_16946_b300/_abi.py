@@ -14,12 +14,15 @@ LIB_PATH = os.path.join(_HERE, "libptsdf.so")
 
 SDF_OK, SDF_EINVAL, SDF_ENOMEM, SDF_ECUDA, SDF_EBUSY, SDF_ETIMEOUT, SDF_EDEVICE = range(7)
 SDF_F32, SDF_F16X2, SDF_BF16X2 = 0, 1, 2
-SDF_LAMBDA_GLOBAL, SDF_LAMBDA_FIXED = 0, 1
+SDF_LAMBDA_GLOBAL, SDF_LAMBDA_FIXED, SDF_LAMBDA_RADIUS = 0, 1, 2
+SDF_RADIUS_FALLBACK_K = 32
 SDF_ENGINE_AUTO, SDF_ENGINE_ALU, SDF_ENGINE_TENSOR = 0, 1, 2
 SDF_DEV_WAIT_TIMEOUT, SDF_DEV_BAD_INPUT = 1, 2
 SDF_K_PREPASS, SDF_K_FWD, SDF_K_MERGE, SDF_K_BUILD, SDF_K_FWD_GRAD, SDF_K_BWD, SDF_K_FWD_TC = 0, 1, 2, 3, 4, 5, 6
+SDF_K_RADIUS, SDF_K_KNN = 7, 8
 SDF_UNION, SDF_INTERSECT, SDF_DIFFERENCE = 0, 1, 2
-KERNEL_IDS = {"prepass": 0, "fwd": 1, "merge": 2, "build": 3, "fwd_grad": 4, "bwd_params": 5, "fwd_tc": 6}
+KERNEL_IDS = {"prepass": 0, "fwd": 1, "merge": 2, "build": 3, "fwd_grad": 4, "bwd_params": 5, "fwd_tc": 6,
+              "radius": 7, "knn": 8}
 
 STATUS_NAMES = {0: "SDF_OK", 1: "SDF_EINVAL", 2: "SDF_ENOMEM", 3: "SDF_ECUDA", 4: "SDF_EBUSY",
                 5: "SDF_ETIMEOUT", 6: "SDF_EDEVICE"}
@@ -42,6 +45,8 @@ _P, _I64, _I32, _F = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_f
 SIGNATURES = {
     "sdf_opts_default": (ctypes.c_int, [ctypes.POINTER(sdf_query_opts)]),
     "sdf_probe_rates": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double)]),
+    "sdf_knn_mean_distance": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
+                                             ctypes.c_void_p]),
     "sdf_build": (ctypes.c_int, [_P, _P, _P, _I64, _P, ctypes.POINTER(_P)]),
     "sdf_destroy": (ctypes.c_int, [_P]),
     "sdf_cloud_info": (ctypes.c_int, [_P, ctypes.POINTER(_I64), ctypes.POINTER(_F), ctypes.POINTER(_I64),

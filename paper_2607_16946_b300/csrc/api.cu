@@ -28,8 +28,14 @@ static_assert(sizeof(sdf_query_opts) == 32, "sdf_query_opts layout");
 static_assert(sizeof(sdf_request) == 88, "sdf_request layout");
 
 sdf_status check_opts(const sdf_query_opts& o, const char* fn) {
-    if (o.lambda_mode != SDF_LAMBDA_GLOBAL && o.lambda_mode != SDF_LAMBDA_FIXED)
+    if (o.lambda_mode != SDF_LAMBDA_GLOBAL && o.lambda_mode != SDF_LAMBDA_FIXED && o.lambda_mode != SDF_LAMBDA_RADIUS)
         return set_error(SDF_EINVAL, std::string(fn) + ": unknown lambda_mode");
+    if (o.lambda_mode == SDF_LAMBDA_RADIUS) {
+        if (!(o.fixed_lambda > 0.f) || !std::isfinite(o.fixed_lambda))
+            return set_error(SDF_EINVAL, std::string(fn) + ": SDF_LAMBDA_RADIUS needs fixed_lambda > 0");
+        if (o.precision != SDF_F32 || o.engine == SDF_ENGINE_TENSOR)
+            return set_error(SDF_EINVAL, std::string(fn) + ": SDF_LAMBDA_RADIUS runs in FP32 on the FP32 units");
+    }
     if (o.precision != SDF_F32 && o.precision != SDF_F16X2 && o.precision != SDF_BF16X2)
         return set_error(SDF_EINVAL, std::string(fn) + ": unknown precision");
     if (!(o.C > 0.f) || !std::isfinite(o.C)) return set_error(SDF_EINVAL, std::string(fn) + ": C must be > 0");
@@ -97,6 +103,8 @@ extern "C" sdf_status sdf_query_grad(sdf_cloud cloud, const float* d_x, int64_t 
     const sdf_status s = check_opts(o, "sdf_query_grad");
     if (s != SDF_OK) return s;
     if (o.precision != SDF_F32) return set_error(SDF_EINVAL, "sdf_query_grad: gradients are computed in FP32 only");
+    if (o.lambda_mode == SDF_LAMBDA_RADIUS)
+        return set_error(SDF_EINVAL, "sdf_query_grad: no gradient for SDF_LAMBDA_RADIUS");
     if (o.engine == SDF_ENGINE_TENSOR)
         return set_error(SDF_EINVAL, "sdf_query_grad: gradients use the FP32 units (no tensor-core engine)");
     if (q == 0) return SDF_OK;
@@ -116,6 +124,8 @@ extern "C" sdf_status sdf_backward_params(sdf_cloud cloud, const float* d_x, int
     if (s != SDF_OK) return s;
     if (o.precision != SDF_F32)
         return set_error(SDF_EINVAL, "sdf_backward_params: gradients are computed in FP32 only");
+    if (o.lambda_mode == SDF_LAMBDA_RADIUS)
+        return set_error(SDF_EINVAL, "sdf_backward_params: no gradient for SDF_LAMBDA_RADIUS");
     if (o.engine == SDF_ENGINE_TENSOR)
         return set_error(SDF_EINVAL, "sdf_backward_params: gradients use the FP32 units (no tensor-core engine)");
     const Cloud& c = *reinterpret_cast<const Cloud*>(cloud);

@@ -190,6 +190,22 @@ __global__ void k_partition(const float4* __restrict__ rec_tmp, const int8_t* __
     }
 }
 
+// Records in the Morton order of the prepass array (compact position order[m]:
+// direct points first, then kappa-form ones), flagged r3.w = 1 for the kappa
+// form, for the radius-limited evaluation and the k-nearest searches.
+__global__ void k_gather_morton(const float4* __restrict__ rec, const int32_t* __restrict__ order, int64_t n,
+                                int64_t n_direct, int64_t tiles_direct, float4* __restrict__ mrec) {
+    const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= n) return;
+    const int64_t cpos = order[m];
+    const bool kappa = cpos >= n_direct;
+    const int64_t slot = kappa ? tiles_direct * kTileRecs + (cpos - n_direct) : cpos;
+    for (int k = 0; k < 3; ++k) mrec[4 * m + k] = rec[4 * slot + k];
+    float4 r3 = rec[4 * slot + 3];
+    r3.w = kappa ? 1.f : 0.f;
+    mrec[4 * m + 3] = r3;
+}
+
 __global__ void k_fill_perm(int32_t* perm, int64_t m) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < m) perm[i] = -1;
@@ -219,7 +235,8 @@ uint32_t spread3(uint32_t v) {
 // relative 1e-6 so that FP32 rounding of the query-to-centre distance never
 // excludes a tile that holds an extreme point.
 void morton_order_and_spheres(const std::vector<float4>& in, const float* box, float diag,
-                              std::vector<float4>& out, std::vector<float4>& spheres) {
+                              std::vector<float4>& out, std::vector<float4>& spheres,
+                              std::vector<int32_t>& order) {
     const size_t n = in.size();
     const double half[3] = {0.5 * (box[3] - box[0]), 0.5 * (box[4] - box[1]), 0.5 * (box[5] - box[2])};
     std::vector<std::pair<uint32_t, uint32_t>> key(n);
@@ -235,7 +252,11 @@ void morton_order_and_spheres(const std::vector<float4>& in, const float* box, f
     }
     std::sort(key.begin(), key.end());
     out.resize(n);
-    for (size_t i = 0; i < n; ++i) out[i] = in[key[i].second];
+    order.resize(n);
+    for (size_t i = 0; i < n; ++i) {
+        out[i] = in[key[i].second];
+        order[i] = (int32_t)key[i].second;
+    }
     const size_t ns = (n + kSphereTile - 1) / kSphereTile;
     spheres.resize(ns);
     for (size_t t = 0; t < ns; ++t) {
@@ -273,6 +294,7 @@ void free_cloud(Cloud* c) {
     cudaFree(c->src_params);
     cudaFree(c->status);
     cudaFree(c->btiles);
+    cudaFree(c->mrec);
     delete c;
 }
 
@@ -389,13 +411,26 @@ extern "C" sdf_status sdf_build(const float* d_points, const float* d_normals, c
                   "sdf_build: prepass download");
         std::vector<float4> sorted;
         std::vector<float4> spheres;
-        morton_order_and_spheres(hp, c->aabb, c->aabb_diag, sorted, spheres);
+        std::vector<int32_t> order;
+        morton_order_and_spheres(hp, c->aabb, c->aabb_diag, sorted, spheres, order);
         c->n_spheres = (int64_t)spheres.size();
         PTSDF_TRY(cudaMemcpy(c->pre, sorted.data(), (size_t)n * sizeof(float4), cudaMemcpyHostToDevice),
                   "sdf_build: prepass upload");
         PTSDF_TRY(cudaMalloc(&c->spheres, spheres.size() * sizeof(float4)), "sdf_build: sphere alloc");
         PTSDF_TRY(cudaMemcpy(c->spheres, spheres.data(), spheres.size() * sizeof(float4), cudaMemcpyHostToDevice),
                   "sdf_build: sphere upload");
+        int32_t* d_order = nullptr;
+        PTSDF_TRY(cudaMalloc(&d_order, (size_t)n * sizeof(int32_t)), "sdf_build: order alloc");
+        cudaError_t oe = cudaMemcpy(d_order, order.data(), (size_t)n * sizeof(int32_t), cudaMemcpyHostToDevice);
+        if (oe == cudaSuccess) oe = cudaMalloc(&c->mrec, (size_t)n * 4 * sizeof(float4));
+        if (oe == cudaSuccess) {
+            k_gather_morton<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(c->rec, d_order, n, c->n_direct,
+                                                                       c->tiles_direct, c->mrec);
+            oe = cudaGetLastError();
+        }
+        if (oe == cudaSuccess) oe = cudaStreamSynchronize(st);
+        cudaFree(d_order);
+        PTSDF_TRY(oe, "sdf_build: Morton-ordered records");
     }
 #undef PTSDF_TRY
     cudaFree(box);

@@ -77,7 +77,8 @@ struct Cloud {
     float* src_normals = nullptr;    // the parameter gradient's chain through the fit
     float* src_params = nullptr;
     int32_t* status = nullptr;       // device status word (SDF_DEV_* bits)
-    uint8_t* btiles = nullptr;       // tiles_direct x 12 KB split-f16 operands of the tensor-core loop
+    uint8_t* btiles = nullptr;       // tiles_direct x 14 KB split-f16 operands of the tensor-core loop
+    float4* mrec = nullptr;          // n x 4 float4 records in the prepass (Morton) order, r3.w = 1 for kappa
     float tc_scale = 1.f;            // their coordinate scale (a power of two >= the AABB diagonal)
     int num_sms = 148;
 };
@@ -144,6 +145,11 @@ sdf_status build_btiles(Cloud& c, cudaStream_t st);
 int64_t tc_query_blocks(int64_t q);
 sdf_status launch_fwd_tc(const Cloud& c, const TcQuery& a, int64_t tiles_per_chunk, int nchunks, int direct_out,
                          cudaStream_t st);
+
+// radius-limited evaluation (radius.cu): the fallback neighbour count of Sec. 4.2
+constexpr int kRadiusFallbackK = 32;
+sdf_status launch_radius_query(const Cloud& c, const float* d_x, int64_t q, float* d_phi, const sdf_query_opts& o,
+                               cudaStream_t st);
 
 sdf_status launch_query(const Cloud& c, const float* d_x, int64_t q, float* d_phi,
                         const sdf_query_opts& o, cudaStream_t st);

@@ -253,6 +253,7 @@ int query_partials(const Cloud& c, int64_t q, const sdf_query_opts& o) {
 
 sdf_status launch_query(const Cloud& c, const float* d_x, int64_t q, float* d_phi, const sdf_query_opts& o,
                         cudaStream_t st) {
+    if (o.lambda_mode == SDF_LAMBDA_RADIUS) return launch_radius_query(c, d_x, q, d_phi, o, st);
     const Plan p = make_plan(c, q, o.split_n);
     // Tensor-core engine: the direct-form tiles go to k_fwd_tc in nd chunks,
     // the kappa-form tiles to k_fwd in nk chunks; both write (W, S) partials
@@ -418,7 +419,7 @@ extern "C" sdf_status sdf_query_noalloc(sdf_cloud cloud, const float* d_x, int64
     sdf_opts_default(&o);
     if (opts) o = *opts;
     if (o.lambda_mode != SDF_LAMBDA_GLOBAL && o.lambda_mode != SDF_LAMBDA_FIXED)
-        return set_error(SDF_EINVAL, "sdf_query_noalloc: unknown lambda_mode");
+        return set_error(SDF_EINVAL, "sdf_query_noalloc: GLOBAL or FIXED lambda only");
     if (o.precision != SDF_F32) return set_error(SDF_EINVAL, "sdf_query_noalloc: unsupported precision");
     if (o.engine != SDF_ENGINE_AUTO && o.engine != SDF_ENGINE_ALU)
         return set_error(SDF_EINVAL, "sdf_query_noalloc: only the FP32-unit engine is available here");

@@ -1,0 +1,281 @@
+// Radius-limited evaluation (Sec. 4.2, "Acceleration and adaptive lambda")
+// and the mean k-nearest-neighbour distance D of its lambda heuristic.
+//
+// lambda is one constant for the cloud; a query sums Eq. BasicFormulaShifted
+// over the points within R_eval = 2 C / lambda only, and over its 32 nearest
+// points when none lies within R_eval.  The paper finds both sets with a
+// kd-tree on the CPU.  Here the spatial index is the one the pruned prepass
+// already keeps: the points in Morton order, one bounding sphere per 64
+// consecutive points (radius inflated against FP32 rounding), and a copy of
+// the torus records in the same order.  A query
+//   1. bounds every sphere: points of sphere t lie in [|x - c_t| - r_t,
+//      |x - c_t| + r_t]; the spheres that can reach within R_eval are
+//      scanned point by point and their points inside R_eval summed, with
+//      the exponent shift following the smallest distance seen (the sums
+//      are rescaled when it drops);
+//   2. if no point was inside, seeds a sorted list of the k nearest
+//      (distance, then scan order) with the points of the sphere of smallest
+//      |x - c_t| + r_t, then scans every other sphere whose lower bound
+//      reaches below the current k-th distance, and sums over the k.
+// The k-nearest search of D is the same second step with the point itself
+// excluded, seeded with its own sphere and the next one in Morton order.
+// Distances come from the 16-byte prepass entries; records are read only for
+// the points that enter a sum.  One thread per query (or point); warps scan a
+// sphere when any of their lanes needs it.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <vector>
+
+#include "query_common.cuh"
+
+namespace ptsdf {
+
+using namespace qk;
+
+namespace {
+
+constexpr int kRadiusThreads = 128;
+constexpr int kKnnMax = 64;
+
+struct RadiusArgs {
+    const float* x;
+    int64_t q;
+    float* phi;
+    const float4* spheres;
+    int64_t nsph;
+    const float4* mrec;    // n x 4 float4 records in Morton order; r3.w = 1 for the kappa form
+    const float4* pre;     // n float4(-2 p', |p'|^2) in the same order (p' = p - AABB centre)
+    int64_t n;
+    float cx, cy, cz;
+    float L;               // lambda log2(e)
+    float reval;
+    float offset;
+    int kfb;
+};
+
+__device__ __forceinline__ float g_record(float x, float y, float z, const float4* __restrict__ r) {
+    const float4 r0 = __ldg(r), r1 = __ldg(r + 1), r2 = __ldg(r + 2), r3 = __ldg(r + 3);
+    return r3.w != 0.f ? g_kappa(x, y, z, r0, r1, r2, r3) : g_direct(x, y, z, r1, r2, r0.w);
+}
+
+__device__ __forceinline__ int sphere_count(int64_t t, int64_t n) {
+    const int64_t left = n - t * kSphereTile;
+    return (int)(left < kSphereTile ? left : kSphereTile);
+}
+
+// Squared distance from x' (coordinates centred on the AABB) to point j of
+// the Morton-ordered prepass array float4(-2 p', |p'|^2).
+__device__ __forceinline__ float dist2_pre(float xs, float ys, float zs, const float4* __restrict__ pre, int64_t j) {
+    const float4 e = __ldg(pre + j);
+    const float dx = fmaf(0.5f, e.x, xs), dy = fmaf(0.5f, e.y, ys), dz = fmaf(0.5f, e.z, zs);
+    return fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+}
+
+// Distance from x' to the centre of sphere s (the bounds add or subtract its
+// inflated radius; sqrt.approx's relative error is covered by the 1e-6 pad
+// the callers apply).
+__device__ __forceinline__ float centre_dist(float xs, float ys, float zs, const float4& s) {
+    const float dx = xs - s.x, dy = ys - s.y, dz = zs - s.z;
+    return sqrt_mufu(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+}
+
+// Inserts (d2, j) into the ascending top-k list (bd, bi) of cnt entries.
+__device__ __forceinline__ void topk_insert(float* bd, int* bi, int& cnt, int k, float d2, int j) {
+    if (cnt == k && !(d2 < bd[k - 1])) return;
+    int pos = cnt < k ? cnt++ : k - 1;
+    while (pos > 0 && d2 < bd[pos - 1]) {
+        bd[pos] = bd[pos - 1];
+        bi[pos] = bi[pos - 1];
+        --pos;
+    }
+    bd[pos] = d2;
+    bi[pos] = j;
+}
+
+__device__ __forceinline__ void scan_sphere(const RadiusArgs& a, float xs, float ys, float zs, int64_t t, int64_t self,
+                                            int k, float* bd, int* bi, int& cnt) {
+    const int64_t j0 = t * kSphereTile;
+    const int c = sphere_count(t, a.n);
+    for (int jj = 0; jj < c; ++jj) {
+        const int64_t j = j0 + jj;
+        if (j == self) continue;
+        topk_insert(bd, bi, cnt, k, dist2_pre(xs, ys, zs, a.pre, j), (int)j);
+    }
+}
+
+// The k nearest points of x' (Morton positions in bi, squared distances
+// ascending in bd), skipping Morton position `self` (or -1).  The list is
+// seeded from `seed` (and, for a point of the cloud, its Morton neighbour
+// sphere), then every other sphere whose lower bound reaches below the
+// current k-th distance is scanned.  Returns min(k, points available).
+__device__ int knn_scan(const RadiusArgs& a, float xs, float ys, float zs, int k, int64_t self, int64_t seed,
+                        float* bd, int* bi) {
+    int cnt = 0;
+    scan_sphere(a, xs, ys, zs, seed, self, k, bd, bi, cnt);
+    int64_t seed2 = -1;
+    if (self >= 0 && a.nsph > 1) {
+        seed2 = seed + 1 < a.nsph ? seed + 1 : seed - 1;
+        scan_sphere(a, xs, ys, zs, seed2, self, k, bd, bi, cnt);
+    }
+    for (int64_t t = 0; t < a.nsph; ++t) {
+        if (t == seed || t == seed2) continue;
+        const float4 s = __ldg(a.spheres + t);
+        const float lb = centre_dist(xs, ys, zs, s) - s.w;
+        const float lim = cnt < k ? INFINITY : sqrtf(bd[k - 1]) * (1.f + 1e-6f);
+        if (!(lb <= lim)) continue;
+        scan_sphere(a, xs, ys, zs, t, self, k, bd, bi, cnt);
+    }
+    return cnt;
+}
+
+__global__ void __launch_bounds__(kRadiusThreads) k_radius_query(RadiusArgs a) {
+    const int64_t qi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (qi >= a.q) return;
+    const float x = a.x[3 * qi], y = a.x[3 * qi + 1], z = a.x[3 * qi + 2];
+    const float xs = x - a.cx, ys = y - a.cy, zs = z - a.cz;
+    const float R2 = a.reval * a.reval;
+    const float lim = a.reval * (1.f + 1e-6f);
+    // 1. the points inside R_eval, online shift by the smallest distance; the
+    //    same pass finds the sphere of smallest upper bound holding kfb points
+    float W = 0.f, S = 0.f, m = INFINITY;
+    int inside = 0;
+    float best_ub = INFINITY;
+    int64_t best = 0;
+    for (int64_t t = 0; t < a.nsph; ++t) {
+        const float4 s = __ldg(a.spheres + t);
+        const float dc = centre_dist(xs, ys, zs, s);
+        if (dc + s.w < best_ub && sphere_count(t, a.n) >= a.kfb) {
+            best_ub = dc + s.w;
+            best = t;
+        }
+        if (!(dc - s.w <= lim)) continue;
+        const int64_t j0 = t * kSphereTile;
+        const int c = sphere_count(t, a.n);
+        for (int jj = 0; jj < c; ++jj) {
+            const float d2 = dist2_pre(xs, ys, zs, a.pre, j0 + jj);
+            if (!(d2 <= R2)) continue;
+            const float d = sqrtf(d2);
+            const float g = g_record(x, y, z, a.mrec + 4 * (j0 + jj));
+            if (d < m) {
+                const float f = inside ? exp2f(-a.L * (m - d)) : 0.f;
+                W = fmaf(W, f, 1.f);
+                S = fmaf(S, f, g);
+                m = d;
+            } else {
+                const float w = exp2f(-a.L * (d - m));
+                W += w;
+                S = fmaf(w, g, S);
+            }
+            ++inside;
+        }
+    }
+    if (inside == 0) {
+        // 2. the kfb nearest points
+        float bd[kKnnMax];
+        int bi[kKnnMax];
+        const int cnt = knn_scan(a, xs, ys, zs, a.kfb, -1, best, bd, bi);
+        const float d0 = sqrtf(bd[0]);
+        for (int j = 0; j < cnt; ++j) {
+            const float w = exp2f(-a.L * (sqrtf(bd[j]) - d0));
+            W += w;
+            S = fmaf(w, g_record(x, y, z, a.mrec + 4 * (int64_t)bi[j]), S);
+        }
+    }
+    a.phi[qi] = __fdiv_rn(S, W) - a.offset;
+}
+
+// Per point: mean of the distances to its k nearest other points; one
+// partial sum (double) per block.
+__global__ void __launch_bounds__(kRadiusThreads) k_knn_mean(RadiusArgs a, int k, double* __restrict__ partial) {
+    __shared__ double red[kRadiusThreads];
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double v = 0.0;
+    if (i < a.n) {
+        const float4 e = __ldg(a.pre + i);
+        float bd[kKnnMax];
+        int bi[kKnnMax];
+        const int cnt = knn_scan(a, -0.5f * e.x, -0.5f * e.y, -0.5f * e.z, k, i, i / kSphereTile, bd, bi);
+        double s = 0.0;
+        for (int j = 0; j < cnt; ++j) s += sqrt((double)bd[j]);
+        v = cnt > 0 ? s / cnt : 0.0;
+    }
+    red[threadIdx.x] = v;
+    __syncthreads();
+    for (int w = kRadiusThreads / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
+}
+
+RadiusArgs radius_args(const Cloud& c) {
+    RadiusArgs a;
+    a.x = nullptr;
+    a.q = 0;
+    a.phi = nullptr;
+    a.spheres = c.spheres;
+    a.nsph = c.n_spheres;
+    a.mrec = c.mrec;
+    a.pre = c.pre;
+    a.n = c.n;
+    a.cx = 0.5f * (c.aabb[0] + c.aabb[3]);
+    a.cy = 0.5f * (c.aabb[1] + c.aabb[4]);
+    a.cz = 0.5f * (c.aabb[2] + c.aabb[5]);
+    a.L = 0.f;
+    a.reval = 0.f;
+    a.offset = 0.f;
+    a.kfb = kRadiusFallbackK;
+    return a;
+}
+
+}  // namespace
+
+sdf_status launch_radius_query(const Cloud& c, const float* d_x, int64_t q, float* d_phi, const sdf_query_opts& o,
+                               cudaStream_t st) {
+    RadiusArgs a = radius_args(c);
+    a.x = d_x;
+    a.q = q;
+    a.phi = d_phi;
+    a.L = o.fixed_lambda * 1.4426950408889634f;
+    a.reval = 2.f * o.C / o.fixed_lambda;
+    a.offset = o.offset;
+    ProfRange pr(SDF_K_RADIUS, st);
+    k_radius_query<<<(unsigned)((q + kRadiusThreads - 1) / kRadiusThreads), kRadiusThreads, 0, st>>>(a);
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? SDF_OK : cuda_error(e, "sdf_query: k_radius_query launch");
+}
+
+}  // namespace ptsdf
+
+using namespace ptsdf;
+
+extern "C" sdf_status sdf_knn_mean_distance(sdf_cloud cloud, int32_t k, double* D, void* stream) {
+    if (!cloud || !D) return set_error(SDF_EINVAL, "sdf_knn_mean_distance: NULL argument");
+    if (k < 1 || k > kKnnMax) return set_error(SDF_EINVAL, "sdf_knn_mean_distance: k must be in [1, 64]");
+    const Cloud& c = *reinterpret_cast<const Cloud*>(cloud);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (c.n < 2) {
+        *D = 0.0;
+        return SDF_OK;
+    }
+    RadiusArgs a = radius_args(c);
+    const int64_t blocks = (c.n + kRadiusThreads - 1) / kRadiusThreads;
+    double* part = nullptr;
+    cudaError_t e = cudaMallocAsync(&part, (size_t)blocks * sizeof(double), st);
+    if (e != cudaSuccess) return cuda_error(e, "sdf_knn_mean_distance: scratch");
+    {
+        ProfRange pr(SDF_K_KNN, st);
+        k_knn_mean<<<(unsigned)blocks, kRadiusThreads, 0, st>>>(a, k, part);
+        e = cudaGetLastError();
+    }
+    std::vector<double> h((size_t)blocks);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h.data(), part, (size_t)blocks * sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFreeAsync(part, st);
+    if (e != cudaSuccess) return cuda_error(e, "sdf_knn_mean_distance");
+    double s = 0.0;
+    for (double v : h) s += v;   // fixed order: the result does not depend on scheduling
+    *D = s / (double)c.n;
+    return SDF_OK;
+}

@@ -90,7 +90,8 @@ struct Server {
 int64_t request_need(const Server& S, const sdf_request& r) {
     const int64_t q = r.q;
     int64_t b = 0;
-    auto scratch = [&](const Cloud* c, bool grad) {
+    auto scratch = [&](const Cloud* c, bool grad) -> int64_t {
+        if (r.opts.lambda_mode == SDF_LAMBDA_RADIUS) return 4096;   // no scratch
         const Plan p = make_plan(*c, q, r.opts.split_n, grad ? kConsumerWarps * 32 : kQueriesPerCta);
         int64_t s = (int64_t)p.split * q * 8;                 // prepass partials
         if (grad) {
@@ -331,7 +332,11 @@ extern "C" sdf_status sdf_serve_submit(sdf_server srv, const sdf_request* req, u
         (r.kind == SDF_REQ_GRAD && r.opts.precision != SDF_F32) || !(r.opts.C > 0.f) || r.opts.split_n < 0 ||
         (r.opts.engine != SDF_ENGINE_AUTO && r.opts.engine != SDF_ENGINE_ALU && r.opts.engine != SDF_ENGINE_TENSOR) ||
         (r.opts.engine == SDF_ENGINE_TENSOR && (r.opts.precision != SDF_F32 || r.kind == SDF_REQ_GRAD)) ||
-        (r.opts.lambda_mode != SDF_LAMBDA_GLOBAL && r.opts.lambda_mode != SDF_LAMBDA_FIXED))
+        (r.opts.lambda_mode != SDF_LAMBDA_GLOBAL && r.opts.lambda_mode != SDF_LAMBDA_FIXED &&
+         r.opts.lambda_mode != SDF_LAMBDA_RADIUS) ||
+        (r.opts.lambda_mode == SDF_LAMBDA_RADIUS &&
+         (r.kind == SDF_REQ_GRAD || !(r.opts.fixed_lambda > 0.f) || r.opts.precision != SDF_F32 ||
+          r.opts.engine == SDF_ENGINE_TENSOR)))
         return set_error(SDF_EINVAL, "sdf_serve_submit: bad options");
     auto R = std::make_shared<Request>();
     R->r = r;

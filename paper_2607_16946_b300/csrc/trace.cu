@@ -161,6 +161,8 @@ sdf_status launch_trace(const Cloud& c, const float* d_org, const float* d_dir, 
             k_hit_positions<<<blocks_for(nh), 256, 0, st>>>(hits, nh, d_org, d_dir, d_t_hit, xbuf);
             sdf_query_opts og = o;
             og.offset = 0.f;
+            // radius-limited tracing takes its normals from the all-pairs blend with the same lambda
+            if (og.lambda_mode == SDF_LAMBDA_RADIUS) og.lambda_mode = SDF_LAMBDA_FIXED;
             s = launch_query_grad(c, xbuf, nh, phi, grad, nullptr, og, st);
             if (s == SDF_OK) {
                 k_scatter_normals<<<blocks_for(nh), 256, 0, st>>>(hits, nh, grad, d_normals);

@@ -1,0 +1,167 @@
+"""GPU parity of the radius-limited evaluation (SDF_LAMBDA_RADIUS) and of D
+(sdf_knn_mean_distance) against the FP64 oracle (Sec. 4.2, "Acceleration and
+adaptive lambda").
+
+lambda and R_eval come from the oracle's own D (lambda = 10^3 / D), so no
+input or expected value comes from the CUDA path.  Set membership is decided
+in FP32 on the GPU and in FP64 by the oracle: for a query with a point within
+1e-5 of R_eval, or whose 32nd and 33rd nearest distances are within 1e-5, both
+memberships are correct, and the GPU value must match the oracle with R_eval
+moved 2e-5 inward or outward.  Tolerance: 1e-4 x AABB diagonal.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import synth
+from workloads import TOL_REL, aabb_diag, f32, mixed_cloud
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ptsdf():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2607_16946_b300 import build
+    build.build()
+    import paper_2607_16946_b300 as m
+    return m
+
+
+def run(ptsdf, cloud, x, lam, C=64.0, **kw):
+    import torch
+    xt = torch.as_tensor(np.asarray(x, np.float32), device="cuda")
+    phi = cloud.query(xt, lambda_mode=ptsdf.SDF_LAMBDA_RADIUS, fixed_lambda=lam, C=C, **kw)
+    torch.cuda.synchronize()
+    assert cloud.device_status() == 0
+    return phi.cpu().numpy().astype(np.float64)
+
+
+def check_against_oracle(orc, p, x, got, lam, C=64.0, tol=None):
+    """Element-wise check; queries whose sets FP32 may decide either way are
+    accepted against either oracle variant."""
+    R = 2.0 * C / lam
+    tol = TOL_REL * aabb_diag(p) if tol is None else tol
+    ref = orc.phi_radius(x, lam=lam, reval=R)
+    d = np.sqrt(((x[:, None, :].astype(np.float64) - p[None, :, :].astype(np.float64)) ** 2).sum(-1))
+    near_edge = (np.abs(d - R) < 1e-5 * R).any(1)
+    part = np.partition(d, [31, 32], axis=1) if d.shape[1] > 32 else None
+    knn_tie = np.zeros(len(x), bool) if part is None else (part[:, 32] - part[:, 31] < 1e-5 * part[:, 31])
+    amb = near_edge | knn_tie
+    ok = np.abs(got - ref) <= tol
+    if amb.any():
+        lo = orc.phi_radius(x[amb], lam=lam, reval=R * (1 - 2e-5))
+        hi = orc.phi_radius(x[amb], lam=lam, reval=R * (1 + 2e-5))
+        ok[amb] |= (np.abs(got[amb] - lo) <= tol) | (np.abs(got[amb] - hi) <= tol)
+    assert ok.all(), (np.abs(got - ref)[~ok][:5], np.nonzero(~ok)[0][:5], amb.sum())
+    return amb.sum()
+
+
+@pytest.mark.parametrize("k", [1, 2, 64])
+def test_knn_mean_distance(ptsdf, oracle_mod, k):
+    for p, n, a in (f32(*synth.ring_torus(5000, 31, noise=0.005, jitter_deg=2.0)),
+                    f32(*synth.sphere_fibonacci(4096, 1001)),
+                    mixed_cloud(6)):
+        cl = ptsdf.Cloud(p, n, a)
+        got = cl.knn_mean_distance(k)
+        ref = oracle_mod.knn_mean_distance(p, k)
+        assert abs(got - ref) <= 1e-5 * ref, (got, ref)
+
+
+def test_knn_mean_distance_polygon_and_tiny(ptsdf):
+    """Closed forms: a regular 200-gon; three points (fewer than k others)."""
+    N, rho = 200, 1.3
+    t = 2 * np.pi * np.arange(N) / N
+    p = f32(np.stack([rho * np.cos(t), rho * np.sin(t), np.zeros(N)], 1))
+    n = f32(np.tile([0.0, 0.0, 1.0], (N, 1)))
+    a = f32(np.zeros((N, 6)))
+    cl = ptsdf.Cloud(p, n, a)
+    ref = sum(2 * 2 * rho * math.sin(math.pi * m / N) for m in range(1, 33)) / 64
+    assert abs(cl.knn_mean_distance(64) - ref) <= 2e-6 * ref
+    side = 0.7
+    p3 = f32(np.array([[0, 0, 0], [side, 0, 0], [side / 2, side * math.sqrt(3) / 2, 0]]))
+    cl3 = ptsdf.Cloud(p3, n[:3], a[:3])
+    assert abs(cl3.knn_mean_distance(64) - side) <= 2e-6
+    cl1 = ptsdf.Cloud(p3[:1], n[:1], a[:1])
+    assert cl1.knn_mean_distance(64) == 0.0
+
+
+def test_ring_torus_paper_lambda(ptsdf, oracle_mod):
+    """The paper's setting: lambda = 10^3 / D (the oracle's D), R_eval = 2 C / lambda;
+    queries in the box (mostly the 32-nearest fallback) and next to the points
+    (mostly inside R_eval)."""
+    p, n, a = f32(*synth.ring_torus(4000, 32, noise=0.005, jitter_deg=2.0))
+    orc = oracle_mod.Cloud(p, n, a)
+    lam = 1e3 / oracle_mod.knn_mean_distance(p, 64)
+    cl = ptsdf.Cloud(p, n, a)
+    rng = np.random.Generator(np.random.PCG64(33))
+    near = p[rng.integers(0, len(p), 600)] + rng.normal(scale=0.004, size=(600, 3))
+    x = f32(np.concatenate([synth.uniform_queries(1400, 34, -1.6, 1.6), near]))
+    got = run(ptsdf, cl, x, lam)
+    _, used = orc.phi_radius(x, lam=lam, used=True)
+    assert (used > 0).sum() > 100 and (used < 0).sum() > 100   # both branches exercised
+    check_against_oracle(orc, p, x, got, lam)
+
+
+@pytest.mark.parametrize("lam", [30.0, 300.0])
+def test_mixed_cloud_both_forms(ptsdf, oracle_mod, lam):
+    """Direct and kappa-form records; R_eval = 2C/lambda large enough that
+    many queries sum over several points."""
+    p, n, a = mixed_cloud(7)
+    orc = oracle_mod.Cloud(p, n, a)
+    cl = ptsdf.Cloud(p, n, a)
+    assert cl.info()["n_kappa"] > 0
+    x = f32(synth.uniform_queries(1500, 35, -1.5, 1.5))
+    got = run(ptsdf, cl, x, lam, offset=0.0)
+    check_against_oracle(orc, p, x, got, lam)
+
+
+def test_sphere_exact(ptsdf):
+    """Every torus of the sphere cloud is the unit sphere: phi = |x| - 1 for
+    any set, in both branches."""
+    p, n, a = f32(*synth.sphere_fibonacci(4096, 1001))
+    cl = ptsdf.Cloud(p, n, a)
+    x = f32(synth.uniform_queries(4000, 36))
+    lam = 1e3 / cl.knn_mean_distance(64)
+    got = run(ptsdf, cl, x, lam)
+    assert np.abs(got - (np.linalg.norm(x.astype(np.float64), axis=1) - 1)).max() <= 2e-6
+
+
+def test_line_sets_by_construction(ptsdf):
+    """A line of plane points p_k = (0.1 k, 0, z_k): with lambda -> 0 the weights
+    are equal, so phi = z - mean(z_k) over the set: k = -2..2 inside R_eval =
+    0.25 around x = 0; k = -15..16 as the fallback above x = 0.025."""
+    h = 0.1
+    k = np.arange(-40, 41)
+    z = 0.001 * ((7 * k) % 5)
+    p = f32(np.stack([k * h, np.zeros_like(z), z], 1))
+    n = f32(np.tile([0.0, 0.0, 1.0], (k.size, 1)))
+    a = f32(np.zeros((k.size, 6)))
+    cl = ptsdf.Cloud(p, n, a)
+    lam = 1e-4
+    zk = p[:, 2].astype(np.float64)
+    # in radius: R_eval = 2 C / lambda = 0.25
+    got = run(ptsdf, cl, f32([[0.0, 0.0, 0.01]]), lam, C=0.25 * lam / 2)
+    assert abs(got[0] - (np.float32(0.01) - zk[np.abs(k) <= 2].mean())) < 2e-6
+    # fallback: R_eval = 0.5 below the distance 1 to the line
+    got = run(ptsdf, cl, f32([[0.025, 0.0, 1.0]]), lam, C=0.5 * lam / 2)
+    sel = (k >= -15) & (k <= 16)
+    assert abs(got[0] - (1.0 - zk[sel].mean())) < 2e-6
+
+
+def test_radius_options(ptsdf):
+    import torch
+    p, n, a = mixed_cloud(4)
+    cl = ptsdf.Cloud(p, n, a)
+    x = torch.zeros((4, 3), device="cuda")
+    for kw in ({"fixed_lambda": 0.0}, {"fixed_lambda": 10.0, "precision": 1},
+               {"fixed_lambda": 10.0, "engine": ptsdf.SDF_ENGINE_TENSOR}):
+        with pytest.raises(ptsdf.SdfError):
+            cl.query(x, lambda_mode=ptsdf.SDF_LAMBDA_RADIUS, **kw)
+    with pytest.raises(ptsdf.SdfError):
+        cl.query_grad(x, lambda_mode=ptsdf.SDF_LAMBDA_RADIUS, fixed_lambda=10.0)
+    with pytest.raises(ptsdf.SdfError):
+        cl.knn_mean_distance(65)
