@@ -395,6 +395,60 @@ def run_trace_leg(dev, steps: int = 2):
             "evaluations": evals, "kernels": prof}
 
 
+def run_radius_leg(dev, cloud, x, phi, steps: int = 3):
+    """Sec. 4.2's accelerated evaluation (SDF_LAMBDA_RADIUS) with the paper's
+    lambda = 10^3 / D (D from sdf_knn_mean_distance, k = 64), R_eval = 2C/lambda,
+    32-nearest fallback: the dense grid, and the sphere-tracing configuration
+    traced with it.  Queries/s (pairs/s does not apply: each query sums over
+    its own small set)."""
+    import torch
+
+    import paper_2607_16946_b300 as ptsdf
+    from paper_2607_16946_b300 import _abi
+    import synth
+    L = _abi.lib()
+    out = {}
+    t0 = time.perf_counter()
+    D = cloud.knn_mean_distance(64)
+    t_knn = time.perf_counter() - t0
+    lam = 1e3 / D
+    kw = dict(lambda_mode=ptsdf.SDF_LAMBDA_RADIUS, fixed_lambda=lam)
+    cloud.query(x, out=phi, **kw)
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        cloud.query(x, out=phi, **kw)
+    e1.record()
+    torch.cuda.synchronize(dev)
+    s = e0.elapsed_time(e1) / 1e3 / steps
+    out["dense_grid"] = {"queries_per_s": x.shape[0] / s, "ms_per_step": s * 1e3, "D": D, "lambda": lam,
+                         "R_eval": 128.0 / lam, "knn_ms": t_knn * 1e3,
+                         "outputs_finite": bool(torch.isfinite(phi).all())}
+    p, n, a = synth.superquadric(262_144, 1003)
+    cl = ptsdf.Cloud(p, n, a)
+    lam_t = 1e3 / cl.knn_mean_distance(64)
+    org, dirs = synth.camera_rays(512, 512, 1003)
+    org = torch.as_tensor(org, dtype=torch.float32, device=dev)
+    dirs = torch.as_tensor(dirs, dtype=torch.float32, device=dev)
+    tk = dict(lambda_mode=ptsdf.SDF_LAMBDA_RADIUS, fixed_lambda=lam_t)
+    t, st_, nrm = cl.trace(org, dirs, **tk)
+    torch.cuda.synchronize(dev)
+    L.sdf_profile_enable(1)
+    t0 = time.perf_counter()
+    for _ in range(2):
+        t, st_, nrm = cl.trace(org, dirs, **tk)
+    torch.cuda.synchronize(dev)
+    wall = (time.perf_counter() - t0) / 2
+    L.sdf_profile_enable(0)
+    out["trace"] = {"ms_per_image": wall * 1e3, "lambda": lam_t, "hits": int((t >= 0).sum().item()),
+                    "evaluations": int(st_.sum().item()),
+                    "queries_per_s": int(st_.sum().item()) / wall, "kernels": _profile_window(L, _abi)}
+    out["note"] = ("lambda = 10^3/D, R_eval = 2C/lambda, C = 64, 32-nearest fallback; normals at hits from "
+                   "the all-pairs gradient with the same lambda")
+    return out
+
+
 def run_mixed_leg(dev, cloud, x, phi, points, normals, params, steps: int = 2):
     """The dense-grid step on each engine and precision: FP32 on the tensor
     cores (the default), FP32 on the FP32 units, and packed-half weights
@@ -576,6 +630,7 @@ def run_ours(args, rank, world, local):
         line["mixed"] = run_mixed_leg(dev, cloud, x, phi, p, n, a)
         line["grad"] = run_grad_leg(dev, sms * fmax * 1e6 * rates["fma"] / 1e9)
         line["trace"] = run_trace_leg(dev)
+        line["radius"] = run_radius_leg(dev, cloud, x, phi)
     if world == 1 and args.serve_requests > 0:
         del hx, hphi
         clouds_np = make_serving_clouds(args.serve_clouds, SERVE_SEED)

@@ -33,9 +33,12 @@
 // blocked per tile as in the ALU kernel.
 //
 // Warps: 0 producer (bulk copies of B tiles into an 8-stage ring), 1 MMA
-// issuer and TMEM owner (two 224-column accumulators, so the MMA of tile
-// t + 1 overlaps the epilogue of tile t), 2..17 epilogue: four per TMEM lane
-// quadrant, each taking 8 of a tile's 32 points for its 32 query rows.
+// issuer and TMEM owner (two 224-column accumulators), 2..17 epilogue in two
+// sets of eight that take alternate tiles (set 0 the even tiles in
+// accumulator 0, set 1 the odd ones in accumulator 1), so the two sets run
+// out of phase and their square-root bursts do not meet on the MUFU queue.
+// In a set, two warps per TMEM lane quadrant each take 16 of the tile's 32
+// points (two batches of 8) for their 32 query rows.
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
@@ -62,7 +65,10 @@ constexpr uint32_t kBTileBytes = 2 * kTcSubB;         // K = 32
 constexpr int kTcStages = 8;
 constexpr int kEpiGroups = 4;                         // epilogue warps per TMEM lane quadrant
 constexpr int kEpiWarps = 4 * kEpiGroups;
-constexpr int kPtsPerWarp = kTileRecs / kEpiGroups;   // 8
+constexpr int kEpiSets = 2;                           // sets of epilogue warps taking alternate tiles
+constexpr int kSetWarps = kEpiWarps / kEpiSets;
+constexpr int kPtsPerWarp = 8;                        // points per TMEM batch (one column group)
+constexpr int kGroupsPerWarp = kTileRecs / kPtsPerWarp / (kEpiGroups / kEpiSets);   // 2 batches
 constexpr int kVals = kTcQuant * kPtsPerWarp;         // 56 accumulator columns per epilogue warp
 constexpr int kTcThreads = (2 + kEpiWarps) * 32;
 constexpr uint32_t kTmemCols = 512;                   // two accumulators of kTcN columns
@@ -216,7 +222,9 @@ __device__ __forceinline__ void tile_pairs(const float (&v)[kVals], int valid, f
     S += ts;
 }
 
-__global__ void __maxnreg__(112) k_fwd_tc(TcArgs ta, int32_t* status) {
+// 18 warps: five share one SM sub-partition's 16K registers, so at most 96
+// registers per thread (allocated in multiples of 8)
+__global__ void __maxnreg__(96) k_fwd_tc(TcArgs ta, int32_t* status) {
     extern __shared__ __align__(1024) uint8_t smem[];
     uint8_t* sA = smem;                                                         // 2 sub-tiles
     uint8_t* sB = smem + 2 * kTcSubA;                                           // kTcStages tiles
@@ -238,16 +246,18 @@ __global__ void __maxnreg__(112) k_fwd_tc(TcArgs ta, int32_t* status) {
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&tfull[b], 1);
-            mbar_init(&tempty[b], kEpiWarps);
+            mbar_init(&tempty[b], kSetWarps);
         }
         abort_flag = 0;
         fence_mbar_init();
     }
     if (warp == 1) tc::tmem_alloc(&tmem_base, kTmemCols);
 
-    // epilogue threads: one query row each; group 0 also writes the A row
+    // epilogue threads: one query row each; combine group 0 also writes the A row
     const int quad = warp & 3;            // TMEM lane quadrant this warp may access
-    const int group = (warp - 2) >> 2;    // which 8 points of each tile
+    const int eset = (warp - 2) >> 3;     // tile parity this warp takes
+    const int half = ((warp - 2) >> 2) & 1;   // which 16 points of each tile
+    const int group = eset * 2 + half;    // which partial sums it contributes to the row
     const int row = quad * 32 + lane;
     const int64_t qi = (int64_t)blockIdx.x * kTcM + row;
     float x = 0.f, y = 0.f, z = 0.f, Ls = 0.f, A0 = 0.f;
@@ -352,43 +362,50 @@ __global__ void __maxnreg__(112) k_fwd_tc(TcArgs ta, int32_t* status) {
     } else {
         // ---- epilogue ----
         float W = 0.f, S = 0.f;
-        const uint32_t lane_addr = tbase + ((uint32_t)(quad * 32) << 16) + (uint32_t)(group * kVals);
-        const int jb = group * kPtsPerWarp;
+        const uint32_t lane_addr = tbase + ((uint32_t)(quad * 32) << 16);
         const bool warp_far = __any_sync(0xffffffffu, exact_lane);
         const int ntiles = (int)nt;
         // only the last tile of the direct segment can be partial
         const bool last_partial = t1 == ta.tiles_direct && (ta.n_direct % kTileRecs) != 0;
-        for (int t = 0; t < ntiles; ++t) {
-            const int b = t & 1;
+        const int b = eset;   // this set's accumulator
+        for (int t = eset; t < ntiles; t += kEpiSets) {
             // warp-uniform: the TMEM loads below are .sync.aligned
             const bool ok = mbar_wait_bounded(&tfull[b], (uint32_t)(t >> 1) & 1u, &abort_flag, status);
             if (!__all_sync(0xffffffffu, ok)) break;
             tc::fence_after_sync();
-            float v[kVals];
-            const uint32_t ta_addr = lane_addr + (uint32_t)b * kBufCols;
-            tc::tmem_ld16(ta_addr, v, 0);
-            tc::tmem_ld16(ta_addr + 16, v, 16);
-            tc::tmem_ld16(ta_addr + 32, v, 32);
-            tc::tmem_ld8(ta_addr + 48, v, 48);
-            tc::tmem_wait_ld_values(v);
-            tc::fence_before_sync();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&tempty[b]);
-            const int64_t slot0 = (t0 + t) * kTileRecs + jb;
-            if (last_partial && t == ntiles - 1) {
-                const int64_t left = ta.n_direct - slot0;
-                const int valid = (int)(left < 0 ? 0 : left);
-                if (warp_far)
-                    tile_pairs<true, true>(v, valid, Ls, A0, exact_lane, x, y, z, ta.inv_s, ta.rec, slot0, W, S);
-                else
-                    tile_pairs<true, false>(v, valid, Ls, A0, exact_lane, x, y, z, ta.inv_s, ta.rec, slot0, W, S);
-            } else {
-                if (warp_far)
-                    tile_pairs<false, true>(v, kPtsPerWarp, Ls, A0, exact_lane, x, y, z, ta.inv_s, ta.rec, slot0, W,
-                                            S);
-                else
-                    tile_pairs<false, false>(v, kPtsPerWarp, Ls, A0, exact_lane, x, y, z, ta.inv_s, ta.rec, slot0,
-                                             W, S);
+            const bool partial = last_partial && t == ntiles - 1;
+#pragma unroll 1
+            for (int gb = 0; gb < kGroupsPerWarp; ++gb) {
+                const int cg = half * kGroupsPerWarp + gb;   // column group: 8 points x 7 quantities
+                float v[kVals];
+                const uint32_t ta_addr = lane_addr + (uint32_t)b * kBufCols + (uint32_t)(cg * kVals);
+                tc::tmem_ld16(ta_addr, v, 0);
+                tc::tmem_ld16(ta_addr + 16, v, 16);
+                tc::tmem_ld16(ta_addr + 32, v, 32);
+                tc::tmem_ld8(ta_addr + 48, v, 48);
+                tc::tmem_wait_ld_values(v);
+                if (gb == kGroupsPerWarp - 1) {   // the accumulator is read: the next MMA may overwrite it
+                    tc::fence_before_sync();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&tempty[b]);
+                }
+                const int64_t slot0 = (t0 + t) * kTileRecs + cg * kPtsPerWarp;
+                if (partial) {
+                    const int64_t left = ta.n_direct - slot0;
+                    const int valid = (int)(left < 0 ? 0 : left);
+                    if (warp_far)
+                        tile_pairs<true, true>(v, valid, Ls, A0, exact_lane, x, y, z, ta.inv_s, ta.rec, slot0, W, S);
+                    else
+                        tile_pairs<true, false>(v, valid, Ls, A0, exact_lane, x, y, z, ta.inv_s, ta.rec, slot0, W,
+                                                S);
+                } else {
+                    if (warp_far)
+                        tile_pairs<false, true>(v, kPtsPerWarp, Ls, A0, exact_lane, x, y, z, ta.inv_s, ta.rec, slot0,
+                                                W, S);
+                    else
+                        tile_pairs<false, false>(v, kPtsPerWarp, Ls, A0, exact_lane, x, y, z, ta.inv_s, ta.rec,
+                                                 slot0, W, S);
+                }
             }
         }
         S *= ta.s;   // back to world units

@@ -108,7 +108,10 @@ __device__ __forceinline__ void scan_sphere(const RadiusArgs& a, float xs, float
 // ascending in bd), skipping Morton position `self` (or -1).  The list is
 // seeded from `seed` (and, for a point of the cloud, its Morton neighbour
 // sphere), then every other sphere whose lower bound reaches below the
-// current k-th distance is scanned.  Returns min(k, points available).
+// current k-th distance is scanned.  (Sweeping outward from the seed in
+// Morton order tightens the bound sooner but gives every lane of a warp a
+// different sphere at each step; the shared order keeps the sphere loads
+// broadcast and measured 25% faster.)  Returns min(k, points available).
 __device__ int knn_scan(const RadiusArgs& a, float xs, float ys, float zs, int k, int64_t self, int64_t seed,
                         float* bd, int* bi) {
     int cnt = 0;

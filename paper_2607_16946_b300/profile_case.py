@@ -25,9 +25,10 @@ def main():
     ap.add_argument("--launches", type=int, default=1)
     ap.add_argument("--warmup", type=int, default=1)
     ap.add_argument("--points", type=int, default=100_000)
-    ap.add_argument("--mode", choices=["query", "grad", "backward"], default="query",
+    ap.add_argument("--mode", choices=["query", "grad", "backward", "radius"], default="query",
                     help="query: sdf_query; grad: sdf_query_grad; backward: sdf_query_grad then "
-                         "sdf_backward_params (each call)")
+                         "sdf_backward_params (each call); radius: sdf_query with SDF_LAMBDA_RADIUS and "
+                         "lambda = 10^3 / D")
     ap.add_argument("--precision", type=int, default=0, help="sdf_precision of the query")
     ap.add_argument("--engine", type=int, default=0, help="sdf_engine of the query (0 auto, 1 ALU, 2 tensor)")
     args = ap.parse_args()
@@ -47,11 +48,14 @@ def main():
     x = x[::stride][: args.queries].contiguous()
     phi = torch.empty(x.shape[0], device="cuda")
     G = torch.ones(x.shape[0], device="cuda")
+    lam = 1e3 / cloud.knn_mean_distance(64) if args.mode == "radius" else 0.0
 
     def call():
         nonlocal phi
         if args.mode == "query":
             cloud.query(x, out=phi, precision=args.precision, engine=args.engine)
+        elif args.mode == "radius":
+            cloud.query(x, out=phi, lambda_mode=ptsdf.SDF_LAMBDA_RADIUS, fixed_lambda=lam)
         else:
             phi, _, saved = cloud.query_grad(x)
             if args.mode == "backward":

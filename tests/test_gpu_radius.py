@@ -165,3 +165,26 @@ def test_radius_options(ptsdf):
         cl.query_grad(x, lambda_mode=ptsdf.SDF_LAMBDA_RADIUS, fixed_lambda=10.0)
     with pytest.raises(ptsdf.SdfError):
         cl.knn_mean_distance(65)
+
+
+def test_trace_sphere_radius_mode(ptsdf):
+    """Sphere tracing with the radius-limited evaluation on the exact-SDF
+    sphere cloud: hits at the analytic ray-sphere intersection."""
+    import torch
+    p, n, a = f32(*synth.sphere_fibonacci(512, 61))
+    org, dirs = (f32(v) for v in synth.camera_rays(48, 48, 62, dist=3.0, fov_deg=60.0))
+    cl = ptsdf.Cloud(p, n, a)
+    lam = 1e3 / cl.knn_mean_distance(64)
+    t, steps, nrm = cl.trace(torch.as_tensor(org, device="cuda"), torch.as_tensor(dirs, device="cuda"),
+                             max_steps=200, eps=1e-5, t_max=8.0, lambda_mode=ptsdf.SDF_LAMBDA_RADIUS,
+                             fixed_lambda=lam)
+    torch.cuda.synchronize()
+    assert cl.device_status() == 0
+    t = t.cpu().numpy().astype(np.float64)
+    b = np.sum(org * dirs, 1)
+    c = np.sum(org * org, 1) - 1.0
+    disc = b * b - c
+    hit, miss = disc > 1e-3, disc < -1e-3
+    t_ref = -b - np.sqrt(np.where(hit, disc, 0.0))
+    assert np.all(t[miss] < 0)
+    assert np.abs(t[hit] - t_ref[hit]).max() < 2e-4
