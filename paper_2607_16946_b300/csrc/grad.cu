@@ -269,6 +269,7 @@ sdf_status launch_query_grad(const Cloud& c, const float* d_x, int64_t q, float*
     a.cx = 0.5f * (c.aabb[0] + c.aabb[3]);
     a.cy = 0.5f * (c.aabb[1] + c.aabb[4]);
     a.cz = 0.5f * (c.aabb[2] + c.aabb[5]);
+    a.cloud_radius = 0.5f * c.aabb_diag * (1.f + 1e-6f);
     ga.pre = c.pre;
     ga.grad = d_grad;
     ga.saved = d_saved;

@@ -283,6 +283,7 @@ sdf_status launch_query(const Cloud& c, const float* d_x, int64_t q, float* d_ph
     a.cx = 0.5f * (c.aabb[0] + c.aabb[3]);
     a.cy = 0.5f * (c.aabb[1] + c.aabb[4]);
     a.cz = 0.5f * (c.aabb[2] + c.aabb[5]);
+    a.cloud_radius = 0.5f * c.aabb_diag * (1.f + 1e-6f);
     // the pruned prepass keeps one query block per CTA with no point split, so
     // it is used once there are enough query blocks to fill the GPU
     const bool pruned = use_pruned_prepass(c, p, o);
@@ -466,6 +467,7 @@ extern "C" sdf_status sdf_query_noalloc(sdf_cloud cloud, const float* d_x, int64
     a.cx = 0.5f * (c.aabb[0] + c.aabb[3]);
     a.cy = 0.5f * (c.aabb[1] + c.aabb[4]);
     a.cz = 0.5f * (c.aabb[2] + c.aabb[5]);
+    a.cloud_radius = 0.5f * c.aabb_diag * (1.f + 1e-6f);
     // every scratch entry is written before it is read, so nothing is cleared
     char* base = static_cast<char*>(scratch);
     a.d2 = reinterpret_cast<float2*>(base);

@@ -33,6 +33,7 @@ struct QueryArgs {
     float C;
     float lam;               // fixed lambda
     float offset;
+    float cloud_radius = 0.f;  // max |p'| (half the AABB diagonal): scale of the prepass's rounding
     int64_t tile_base = 0;   // first tile of chunk 0 (k_fwd)
     int part_base = 0;       // partial row of chunk 0 when several kernels share the partials
 };
@@ -162,16 +163,61 @@ __global__ void __launch_bounds__(kPrunedThreads) k_prepass_pruned(const float4*
         ubmin[k] = INFINITY;
         far[k] = 0;
     }
-    // bounds from the spheres
+    // bounds from the spheres; every lane also notes the spheres that gave its
+    // first query's bounds
+    int64_t t_far = 0, t_near = 0;
     for (int64_t t = 0; t < nsph; ++t) {
         const float4 s = __ldg(spheres + t);
 #pragma unroll
         for (int k = 0; k < kQueriesPerThread; ++k) {
             const float dx = xs[k][0] - s.x, dy = xs[k][1] - s.y, dz = xs[k][2] - s.z;
             const float dc = sqrt_mufu(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+            if (k == 0) {
+                if (dc - s.w > lbmax[0]) t_far = t;
+                if (dc + s.w < ubmin[0]) t_near = t;
+            }
             lbmax[k] = fmaxf(lbmax[k], dc - s.w);
             ubmin[k] = fminf(ubmin[k], dc + s.w);
         }
+    }
+    // Tighten the bounds with exact distances: scan (for every lane) the
+    // spheres lanes 0 and 31 found, which are near-best for the whole warp
+    // (its queries are neighbours), and take the farthest and nearest of their
+    // points (less a rounding margin) as the bounds.  Only the thresholds of the scan below change; every
+    // extreme still comes from the same arithmetic.
+    int64_t seeds[4] = {__shfl_sync(0xffffffffu, t_far, 0), __shfl_sync(0xffffffffu, t_near, 0),
+                        __shfl_sync(0xffffffffu, t_far, 31), __shfl_sync(0xffffffffu, t_near, 31)};
+    for (int seed = 0; seed < 4; ++seed) {
+        const int64_t t = seeds[seed];
+        bool dup = false;
+        for (int o = 0; o < seed; ++o) dup = dup || seeds[o] == t;
+        if (dup) continue;
+        const int64_t first = t * kSphereTile;
+        const int cnt = (int)(n - first < kSphereTile ? n - first : kSphereTile);
+        for (int j = 0; j < cnt; ++j) {
+            const float4 r = __ldg(pre + first + j);
+#pragma unroll
+            for (int k = 0; k < kQueriesPerThread; ++k) {
+                const float v = fmaf(xs[k][0], r.x, fmaf(xs[k][1], r.y, fmaf(xs[k][2], r.z, r.w)));
+                if (ARGMAX) {
+                    if (v > hi[k] || (v == hi[k] && (int32_t)(first + j) < far[k])) {
+                        hi[k] = v;
+                        far[k] = (int32_t)(first + j);
+                    }
+                } else {
+                    hi[k] = fmaxf(hi[k], v);
+                }
+                lo[k] = fminf(lo[k], v);
+            }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < kQueriesPerThread; ++k) {
+        // a computed |x' - p'|^2 = xx + v is within 4 eps (|x'| + |p'|)^2 of the
+        // exact one, so its distance is within 2^-11 (|x'| + |p'|)
+        const float margin = 4.8828125e-4f * (sqrtf(xx[k]) + a.cloud_radius);
+        lbmax[k] = fmaxf(lbmax[k], sqrtf(fmaxf(hi[k] + xx[k], 0.f)) - margin);
+        ubmin[k] = fminf(ubmin[k], sqrtf(fmaxf(lo[k] + xx[k], 0.f)) + margin);
     }
     // exact scan of the tiles that may hold an extreme
     for (int64_t t = 0; t < nsph; ++t) {
