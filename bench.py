@@ -449,6 +449,30 @@ def run_radius_leg(dev, cloud, x, phi, steps: int = 3):
     return out
 
 
+def run_mesh_leg(dev, cloud, x, phi, steps: int = 3):
+    """Offset surfaces (Sec. 6) of the dense-grid phi: the 0- and 0.05-level
+    surfaces of the 256^3 grid by marching tetrahedra (sdf_mesh_level_set)."""
+    import torch
+
+    import paper_2607_16946_b300 as ptsdf
+    cloud.query(x, out=phi)
+    grid = phi.reshape(GRID_RES, GRID_RES, GRID_RES)
+    h = 3.2 / (GRID_RES - 1)
+    out = {}
+    for level in (0.0, 0.05):
+        v, t = ptsdf.mesh_level_set(grid, (-1.6, -1.6, -1.6), (h, h, h), level)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            v, t = ptsdf.mesh_level_set(grid, (-1.6, -1.6, -1.6), (h, h, h), level)
+        torch.cuda.synchronize(dev)
+        s = (time.perf_counter() - t0) / steps
+        out[f"level_{level:g}"] = {"ms": s * 1e3, "vertices": int(v.shape[0]), "triangles": int(t.shape[0]),
+                                   "grid_nodes_per_s": GRID_RES ** 3 / s}
+    out["note"] = "host-timed, including the count pass and the output allocation"
+    return out
+
+
 def run_mixed_leg(dev, cloud, x, phi, points, normals, params, steps: int = 2):
     """The dense-grid step on each engine and precision: FP32 on the tensor
     cores (the default), FP32 on the FP32 units, and packed-half weights
@@ -631,6 +655,7 @@ def run_ours(args, rank, world, local):
         line["grad"] = run_grad_leg(dev, sms * fmax * 1e6 * rates["fma"] / 1e9)
         line["trace"] = run_trace_leg(dev)
         line["radius"] = run_radius_leg(dev, cloud, x, phi)
+        line["mesh"] = run_mesh_leg(dev, cloud, x, phi)
     if world == 1 and args.serve_requests > 0:
         del hx, hphi
         clouds_np = make_serving_clouds(args.serve_clouds, SERVE_SEED)

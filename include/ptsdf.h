@@ -352,6 +352,28 @@ PTSDF_API sdf_status sdf_serve_shutdown(sdf_server srv);
 PTSDF_API sdf_status sdf_knn_mean_distance(sdf_cloud cloud, int32_t k, double* D, void* stream);
 
 /* ---------------------------------------------------------------------------
+ * sdf_mesh_level_set -- the level-`level` surface of a phi grid (offset
+ * surfaces and morphological operations, Sec. 6), by marching tetrahedra.
+ *   d_phi: nz x ny x nx FP32 values (x fastest) on the device, node (i, j, k)
+ *   at origin + (i, j, k) * spacing (origin, spacing: 3 host floats each).
+ *   Every grid cube is split into the six tetrahedra of its Kuhn
+ *   triangulation, so the surface is watertight; a node is inside when
+ *   phi < level.  Vertices (one per cut edge of the triangulation, FP32
+ *   x, y, z) are numbered by (lower node index, edge direction x, y, z, xy,
+ *   xz, yz, xyz); triangles (3 int32 vertex numbers) are listed cube by cube
+ *   with normals pointing from phi < level to phi >= level.
+ *   Always sets *n_vertices and *n_triangles.  With d_vertices and
+ *   d_triangles NULL it only counts; with both given and large enough
+ *   (cap_* entries) it also writes them; otherwise SDF_EINVAL.  Synchronous
+ *   on `stream`.  SDF_EINVAL for a dimension below 2 or more than 2^31
+ *   nodes, vertices or triangles.
+ * ------------------------------------------------------------------------- */
+PTSDF_API sdf_status sdf_mesh_level_set(const float* d_phi, int32_t nx, int32_t ny, int32_t nz, const float* origin,
+                                        const float* spacing, float level, float* d_vertices, int64_t cap_vertices,
+                                        int32_t* d_triangles, int64_t cap_triangles, int64_t* n_vertices,
+                                        int64_t* n_triangles, void* stream);
+
+/* ---------------------------------------------------------------------------
  * Kernel timing (a tracing aid, not part of the method).  While enabled,
  * every kernel the library launches is bracketed by two CUDA events recorded
  * on the stream it is launched on.  sdf_profile_read waits for the recorded

@@ -23,7 +23,7 @@ from ._abi import (SDF_DIFFERENCE, SDF_ENGINE_ALU, SDF_ENGINE_AUTO, SDF_ENGINE_T
 
 __all__ = ["Cloud", "SdfError", "SDF_LAMBDA_GLOBAL", "SDF_LAMBDA_FIXED", "SDF_LAMBDA_RADIUS", "SDF_UNION",
            "SDF_INTERSECT",
-           "SDF_DIFFERENCE", "SDF_ENGINE_AUTO", "SDF_ENGINE_ALU", "SDF_ENGINE_TENSOR", "make_opts", "lib", "sdf",
+           "SDF_DIFFERENCE", "mesh_level_set", "SDF_ENGINE_AUTO", "SDF_ENGINE_ALU", "SDF_ENGINE_TENSOR", "make_opts", "lib", "sdf",
            "combine"]
 
 
@@ -227,3 +227,28 @@ def sdf(x, cloud: Cloud, params=None, **opts):
     if params is None:
         params = torch.zeros(0, device=x.device)
     return _SDFQuery.apply(x, params, cloud, opts)
+
+
+def mesh_level_set(phi, origin, spacing, level: float = 0.0, stream=None):
+    """The level-`level` surface of a phi grid (sdf_mesh_level_set): phi is a
+    CUDA float32 tensor of shape (nz, ny, nx) (x fastest), node (i, j, k) at
+    origin + (i, j, k) * spacing.  Returns (vertices V x 3 float32, triangles
+    T x 3 int32) as CUDA tensors; normals point towards phi >= level."""
+    torch = _torch()
+    if phi.dim() != 3 or phi.dtype != torch.float32 or not phi.is_cuda:
+        raise ValueError("phi must be a (nz, ny, nx) CUDA float32 tensor")
+    phi = phi.contiguous()
+    nz, ny, nx = phi.shape
+    o = (ctypes.c_float * 3)(*[float(v) for v in origin])
+    h = (ctypes.c_float * 3)(*[float(v) for v in spacing])
+    nv, nt = ctypes.c_int64(), ctypes.c_int64()
+    sp = _stream_ptr(stream)
+    check(lib().sdf_mesh_level_set(ctypes.c_void_p(phi.data_ptr()), nx, ny, nz, o, h, float(level), None, 0, None, 0,
+                                   ctypes.byref(nv), ctypes.byref(nt), sp), "sdf_mesh_level_set")
+    verts = torch.empty((nv.value, 3), device=phi.device, dtype=torch.float32)
+    tris = torch.empty((nt.value, 3), device=phi.device, dtype=torch.int32)
+    if nt.value:
+        check(lib().sdf_mesh_level_set(ctypes.c_void_p(phi.data_ptr()), nx, ny, nz, o, h, float(level),
+                                       ctypes.c_void_p(verts.data_ptr()), nv.value, ctypes.c_void_p(tris.data_ptr()),
+                                       nt.value, ctypes.byref(nv), ctypes.byref(nt), sp), "sdf_mesh_level_set")
+    return verts, tris
