@@ -69,6 +69,7 @@ def _load():
         _lib.or_torus_sdf.argtypes = [P, P, f64, f64, P, i64, P]
         _lib.or_frame.argtypes = [P, P, P]
         _lib.or_phi_radius.argtypes = [P, f64, f64, i32, P, i64, P, P, i32]
+        _lib.or_laplacian.argtypes = [P, i32, f64, f64, P, i64, P, P, P, i32]
         _lib.or_knn_mean_distance.argtypes = [P, i64, i32, i32]
         _lib.or_knn_mean_distance.restype = f64
     return _lib
@@ -119,6 +120,16 @@ class Cloud:
         _load().or_phi(self._h, mode, C, lam, shift, _ptr(x), m, _ptr(out),
                        _ptr(st) if stats else None, threads or default_threads())
         return (out, st) if stats else out
+
+    def laplacian(self, x, C: float = 64.0, mode: int = GLOBAL, lam: float = 0.0, threads: int | None = None):
+        """(phi, grad phi, lap phi) by second-order jets through the definition
+        (App. D; lambda_x(x) included for GLOBAL)."""
+        x = _f64(x, 3)
+        m = x.shape[0]
+        phi, g, lap = np.empty(m), np.empty((m, 3)), np.empty(m)
+        _load().or_laplacian(self._h, mode, C, lam, _ptr(x), m, _ptr(phi), _ptr(g), _ptr(lap),
+                             threads or default_threads())
+        return phi, g, lap
 
     def phi_radius(self, x, lam: float, reval: float | None = None, C: float = 64.0, kfb: int = 32,
                    threads: int | None = None, used: bool = False):

@@ -21,6 +21,8 @@
  *     (App. D states the x-gradient; the dual numbers also carry the
  *     dependence of lambda_x on x, and d/d(a00..a20) through the fit)
  *   - a sphere tracer stepping by phi (Sec. 6, "Direct visualization")
+ *   - the Laplacian of phi (App. D) by second-order Taylor jets along each
+ *     axis through the same definition
  *   - the radius-limited blend with a constant lambda and the k-nearest
  *     fallback, and the mean k-nearest-neighbour distance D of the lambda
  *     heuristic (Sec. 4.2, "Acceleration and adaptive lambda").
@@ -756,4 +758,145 @@ double or_knn_mean_distance(const double* pts, int64_t n, int k, int threads) {
         total += jobs[t].sum;
     }
     return total / (double)n;
+}
+
+/* ------------------------------------------------------------------------ */
+/* The Laplacian of phi (App. D, "Laplacian"), by second-order Taylor jets    */
+/* along each axis through the literal definition: the radius-form torus     */
+/* SDF of Eq. SingleTorusSDF (with its plane and cylinder limits, X5), the    */
+/* distances, lambda_x = C / sigma_x through the farthest point (GLOBAL; the  */
+/* lowest index on ties, X7), and the ratio.  lap phi is the sum of the three */
+/* second derivatives; the first derivatives give grad phi.                  */
+/* ------------------------------------------------------------------------ */
+typedef struct { double v, d1, d2; } jet;   /* f, f', f'' along one direction */
+
+static jet jconst(double v) { jet r = {v, 0.0, 0.0}; return r; }
+static jet jadd(jet a, jet b) { jet r = {a.v + b.v, a.d1 + b.d1, a.d2 + b.d2}; return r; }
+static jet jsub(jet a, jet b) { jet r = {a.v - b.v, a.d1 - b.d1, a.d2 - b.d2}; return r; }
+static jet jscale(jet a, double s) { jet r = {a.v * s, a.d1 * s, a.d2 * s}; return r; }
+static jet jmul(jet a, jet b) {
+    jet r = {a.v * b.v, a.d1 * b.v + a.v * b.d1, a.d2 * b.v + 2.0 * a.d1 * b.d1 + a.v * b.d2};
+    return r;
+}
+static jet jdiv(jet a, jet b) {
+    jet r;
+    r.v = a.v / b.v;
+    r.d1 = (a.d1 - r.v * b.d1) / b.v;
+    r.d2 = (a.d2 - 2.0 * r.d1 * b.d1 - r.v * b.d2) / b.v;
+    return r;
+}
+static jet jsqrt(jet a) {   /* s^2 = a: 2 s s' = a', 2 s'^2 + 2 s s'' = a'' */
+    jet r;
+    r.v = sqrt(a.v);
+    r.d1 = r.v > 0.0 ? a.d1 / (2.0 * r.v) : 0.0;
+    r.d2 = r.v > 0.0 ? (a.d2 - 2.0 * r.d1 * r.d1) / (2.0 * r.v) : 0.0;
+    return r;
+}
+static jet jexp(jet a) {
+    double e = exp(a.v);
+    jet r = {e, a.d1 * e, (a.d2 + a.d1 * a.d1) * e};
+    return r;
+}
+static jet jdot(const jet a[3], const double b[3]) {
+    return jadd(jadd(jscale(a[0], b[0]), jscale(a[1], b[1])), jscale(a[2], b[2]));
+}
+static jet jnorm(const jet a[3]) {
+    return jsqrt(jadd(jadd(jmul(a[0], a[0]), jmul(a[1], a[1])), jmul(a[2], a[2])));
+}
+
+static jet g_jet(const torus_t* T, const jet X[3]) {
+    jet w[3];
+    if (T->plane) {
+        for (int k = 0; k < 3; ++k) w[k] = jsub(X[k], jconst(T->q[k]));
+        return jdot(w, T->nstar);
+    }
+    jet phiT;
+    if (T->flat) {
+        for (int k = 0; k < 3; ++k) w[k] = jsub(X[k], jconst(T->q[k] + T->nstar[k] / T->kmax));
+        jet along = jdot(w, T->vmin);
+        jet pp[3];
+        for (int k = 0; k < 3; ++k) pp[k] = jsub(w[k], jscale(along, T->vmin[k]));
+        phiT = jsub(jnorm(pp), jconst(T->r));
+    } else {
+        for (int k = 0; k < 3; ++k) w[k] = jsub(X[k], jconst(T->c[k]));
+        jet cr[3] = {jsub(jscale(w[1], T->u[2]), jscale(w[2], T->u[1])),
+                     jsub(jscale(w[2], T->u[0]), jscale(w[0], T->u[2])),
+                     jsub(jscale(w[0], T->u[1]), jscale(w[1], T->u[0]))};
+        jet e = jsub(jnorm(cr), jconst(T->R));
+        jet h = jdot(w, T->u);
+        phiT = jsub(jsqrt(jadd(jmul(e, e), jmul(h, h))), jconst(T->r));
+    }
+    return jscale(phiT, (double)T->sign);
+}
+
+static double lap_one(const or_cloud* C, const or_opts* o, const double x[3], double g3[3]) {
+    const int64_t n = C->n;
+    int64_t imax = 0;
+    double dmax = -1.0, dmin = INFINITY;
+    for (int64_t i = 0; i < n; ++i) {
+        const double* p = C->tori[i].p;
+        double w[3] = {x[0] - p[0], x[1] - p[1], x[2] - p[2]};
+        double d = sqrt(dot3(w, w));
+        if (d > dmax) { dmax = d; imax = i; }
+        if (d < dmin) dmin = d;
+    }
+    double lap = 0.0, phi = 0.0;
+    for (int ax = 0; ax < 3; ++ax) {
+        jet X[3];
+        for (int k = 0; k < 3; ++k) { X[k].v = x[k]; X[k].d1 = k == ax ? 1.0 : 0.0; X[k].d2 = 0.0; }
+        jet lambda;
+        if (o->mode == OR_GLOBAL) {
+            jet wf[3];
+            for (int k = 0; k < 3; ++k) wf[k] = jsub(X[k], jconst(C->tori[imax].p[k]));
+            jet sigma = jscale(jnorm(wf), 0.5);
+            lambda = dmax > 0.0 ? jdiv(jconst(o->C), sigma) : jconst(0.0);   /* X9 */
+        } else {
+            lambda = jconst(o->lambda);
+        }
+        /* the shift cancels in the ratio; a constant one keeps the exponents small */
+        const double shift = dmin;
+        jet W = jconst(0.0), S = jconst(0.0);
+        for (int64_t i = 0; i < n; ++i) {
+            jet wp[3];
+            for (int k = 0; k < 3; ++k) wp[k] = jsub(X[k], jconst(C->tori[i].p[k]));
+            jet d = jnorm(wp);
+            jet wgt = jexp(jscale(jmul(lambda, jsub(d, jconst(shift))), -1.0));
+            W = jadd(W, wgt);
+            S = jadd(S, jmul(wgt, g_jet(&C->tori[i], X)));
+        }
+        jet ph = jdiv(S, W);
+        phi = ph.v;
+        g3[ax] = ph.d1;
+        lap += ph.d2;
+    }
+    g3[3] = lap;
+    return phi;
+}
+
+typedef struct { const or_cloud* C; const or_opts* o; const double* x; double* phi; double* grad; double* lap;
+                 int64_t q0, q1; } lap_job;
+static void* lap_worker(void* arg) {
+    lap_job* J = (lap_job*)arg;
+    for (int64_t j = J->q0; j < J->q1; ++j) {
+        double g4[4];
+        J->phi[j] = lap_one(J->C, J->o, J->x + 3 * j, g4);
+        for (int k = 0; k < 3; ++k) J->grad[3 * j + k] = g4[k];
+        J->lap[j] = g4[3];
+    }
+    return NULL;
+}
+
+void or_laplacian(const or_cloud* C, int mode, double Cconst, double lambda, const double* x, int64_t m,
+                  double* phi, double* grad, double* lap, int threads) {
+    or_opts o = {mode, Cconst, lambda, OR_SHIFT_DMIN};
+    threads = clamp_threads(threads, m);
+    pthread_t th[256];
+    lap_job jobs[256];
+    int64_t per = (m + threads - 1) / threads;
+    for (int k = 0; k < threads; ++k) {
+        int64_t q0 = k * per, q1 = q0 + per < m ? q0 + per : m;
+        jobs[k] = (lap_job){C, &o, x, phi, grad, lap, q0, q1 > q0 ? q1 : q0};
+        pthread_create(&th[k], NULL, lap_worker, &jobs[k]);
+    }
+    for (int k = 0; k < threads; ++k) pthread_join(th[k], NULL);
 }
