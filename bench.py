@@ -347,8 +347,26 @@ def run_grad_leg(dev, peak_instr_rate, steps: int = 3):
     fg = prof["fwd_grad"]["ms"] / prof["fwd_grad"]["launches"] / 1e3
     bw = prof["bwd_params"]["ms"] / prof["bwd_params"]["launches"] / 1e3
     pre = prof.get("prepass", {"ms": 0.0, "launches": 1})
+    # diagnostics (App. D): lap phi and the eikonal residual |grad phi| - 1
+    phi, g, lap = cl.query_laplacian(x)
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    phi, g, lap = cl.query_laplacian(x)
+    e1.record()
+    torch.cuda.synchronize(dev)
+    lap_s = e0.elapsed_time(e1) / 1e3
+    eik = (g.norm(dim=1) - 1.0).abs()
+    near = phi.abs() < 0.05
+    diag = {"laplacian_gpairs_s": pairs / lap_s / 1e9, "laplacian_ms": lap_s * 1e3,
+            "eikonal_residual_median": float(eik.median()), "eikonal_residual_p99": float(eik.quantile(0.99)),
+            "eikonal_residual_median_near_surface": float(eik[near].median()) if bool(near.any()) else None,
+            "laplacian_median_near_surface": float(lap[near].median()) if bool(near.any()) else None,
+            "note": "|grad phi| - 1 over the 1e6 queries and within |phi| < 0.05; lap phi near the surface is "
+                    "about twice the mean curvature"}
     return {"workload": "differentiation: ellipsoid N=65536 (axes 1/0.6/0.4, curvatures x(1+0.05N(0,1))), "
                         "Q=1e6 uniform in [-1.5,1.5]^3; FP32",
+            "diagnostics": diag,
             "fwd_grad_gpairs_s": pairs / fg / 1e9, "bwd_params_gpairs_s": pairs / bw / 1e9,
             "step_ms": (fg + bw) * 1e3 + pre["ms"] / pre["launches"],
             "kernels": prof,

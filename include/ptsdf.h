@@ -341,6 +341,23 @@ PTSDF_API sdf_status sdf_serve_stats(sdf_server srv, int32_t* queued, int32_t* i
 PTSDF_API sdf_status sdf_serve_shutdown(sdf_server srv);
 
 /* ---------------------------------------------------------------------------
+ * sdf_query_laplacian -- phi, grad phi and the Laplacian lap phi at Q points
+ * (App. D, "Laplacian"): the divergence of the gradient of the blend, with
+ * lap g_i of each torus in closed form (lap D = 1/D + (rho - R)/(rho D) for
+ * D the distance to the tube's centre circle, and the same quantity in the
+ * curvature form) and, for SDF_LAMBDA_GLOBAL, the terms of lambda_x(x)
+ * (lambda_x = 2C / d_max(x) is harmonic, so only its gradient enters).
+ * Diagnostics of the SDF: |grad phi| - 1 (eikonal residual) and lap phi
+ * (twice the mean curvature of the level set on the surface).
+ *   d_phi, d_grad (Q x 3) may be NULL; d_lap (Q) is required.  FP32;
+ *   GLOBAL or FIXED lambda; the same point-chunk plan as sdf_query_grad.
+ *   Accuracy: about 1e-2 (1 + |lap phi|) at worst, because the FP32 sums
+ *   include terms of size lambda sum w / d that cancel exactly.
+ * ------------------------------------------------------------------------- */
+PTSDF_API sdf_status sdf_query_laplacian(sdf_cloud cloud, const float* d_x, int64_t q, float* d_phi, float* d_grad,
+                                         float* d_lap, const sdf_query_opts* opts, void* stream);
+
+/* ---------------------------------------------------------------------------
  * sdf_knn_mean_distance -- D of the lambda heuristic of Sec. 4.2
  * ("Acceleration and adaptive lambda"): for every point of the cloud the
  * mean of the distances to its k nearest other points (all of them when the

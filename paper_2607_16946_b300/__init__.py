@@ -97,6 +97,20 @@ class Cloud:
                               ctypes.byref(o), _stream_ptr(stream)), "sdf_query")
         return out
 
+    def query_laplacian(self, x, stream=None, **opts):
+        """(phi, grad phi, lap phi) at the rows of x (sdf_query_laplacian, App. D)."""
+        torch = _torch()
+        x = _dev_f32(x, 3)
+        q = x.shape[0]
+        phi = torch.empty(q, device=x.device, dtype=torch.float32)
+        grad = torch.empty((q, 3), device=x.device, dtype=torch.float32)
+        lap = torch.empty(q, device=x.device, dtype=torch.float32)
+        o = make_opts(**opts)
+        check(lib().sdf_query_laplacian(self._h, ctypes.c_void_p(x.data_ptr()), q, ctypes.c_void_p(phi.data_ptr()),
+                                        ctypes.c_void_p(grad.data_ptr()), ctypes.c_void_p(lap.data_ptr()),
+                                        ctypes.byref(o), _stream_ptr(stream)), "sdf_query_laplacian")
+        return phi, grad, lap
+
     def knn_mean_distance(self, k: int = 64, stream=None) -> float:
         """D of Sec. 4.2's lambda heuristic: the mean distance between a point and
         its k nearest other points, averaged over the cloud (sdf_knn_mean_distance)."""

@@ -113,6 +113,23 @@ extern "C" sdf_status sdf_query_grad(sdf_cloud cloud, const float* d_x, int64_t 
                              static_cast<cudaStream_t>(stream));
 }
 
+extern "C" sdf_status sdf_query_laplacian(sdf_cloud cloud, const float* d_x, int64_t q, float* d_phi, float* d_grad,
+                                          float* d_lap, const sdf_query_opts* opts, void* stream) {
+    if (!cloud) return set_error(SDF_EINVAL, "sdf_query_laplacian: cloud is NULL");
+    if (q < 0) return set_error(SDF_EINVAL, "sdf_query_laplacian: q < 0");
+    const sdf_query_opts o = resolve_opts(opts);
+    const sdf_status s = check_opts(o, "sdf_query_laplacian");
+    if (s != SDF_OK) return s;
+    if (o.precision != SDF_F32 || o.engine == SDF_ENGINE_TENSOR)
+        return set_error(SDF_EINVAL, "sdf_query_laplacian: FP32 on the FP32 units only");
+    if (o.lambda_mode == SDF_LAMBDA_RADIUS)
+        return set_error(SDF_EINVAL, "sdf_query_laplacian: not defined for SDF_LAMBDA_RADIUS");
+    if (q == 0) return SDF_OK;
+    if (!d_x || !d_lap) return set_error(SDF_EINVAL, "sdf_query_laplacian: NULL buffer");
+    return launch_query_grad(*reinterpret_cast<const Cloud*>(cloud), d_x, q, d_phi, d_grad, nullptr, o,
+                             static_cast<cudaStream_t>(stream), d_lap);
+}
+
 extern "C" sdf_status sdf_backward_params(sdf_cloud cloud, const float* d_x, int64_t q, const float* d_saved,
                                           const float* d_grad_phi, float* d_grad_params,
                                           const sdf_query_opts* opts, void* stream) {

@@ -1,5 +1,7 @@
 // sdf_query_grad: phi and its gradient in x (App. D, "Gradient expressions"),
-// including the dependence of lambda_x = 2 C / d_max(x) on x.
+// including the dependence of lambda_x = 2 C / d_max(x) on x; and
+// sdf_query_laplacian: the same plus lap phi (App. D, "Laplacian"), with 15
+// more sums per query (see finalize).
 //
 // With w_i = exp(-lambda (d_i - d_min)), n_i = (x - p_i) / d_i and phi = S / W:
 //
@@ -25,23 +27,38 @@ using namespace qk;
 namespace {
 
 constexpr int kGradQPerCta = kConsumerWarps * 32;   // one query per consumer thread
-constexpr int kAcc = 13;
 constexpr float kTiny = 1e-30f;                      // zero-length vectors get a zero unit vector
 
-enum { A_W, A_S, A_GX, A_GY, A_GZ, A_NX, A_NY, A_NZ, A_HX, A_HY, A_HZ, A_D, A_GD };
+// accumulators: the 13 of the gradient, then the 15 more of the Laplacian
+enum {
+    A_W, A_S, A_GX, A_GY, A_GZ, A_NX, A_NY, A_NZ, A_HX, A_HY, A_HZ, A_D, A_GD,
+    A_LG,                  // sum w lap g
+    A_UG,                  // sum w <u, grad g>
+    A_GR, A_R,             // sum w g / d, sum w / d
+    A_DD, A_DDG,           // sum w d^2, sum w d^2 g
+    A_DUX, A_DUY, A_DUZ,   // sum w d u = sum w (x - p)
+    A_DHX, A_DHY, A_DHZ,   // sum w d g u
+    A_DGX, A_DGY, A_DGZ,   // sum w d grad g
+    A_COUNT_
+};
+template <bool LAP>
+struct NAcc {
+    static constexpr int value = LAP ? (int)A_COUNT_ : (int)A_LG;
+};
 
 struct GradArgs {
     QueryArgs a;
     const float4* pre;       // prepass array (farthest point position)
-    float* grad;             // Q x 3
+    float* grad;             // Q x 3 or null
     float* saved;            // Q x 8 or null
-    float* part;             // split x Q x kAcc partials (split > 1)
+    float* lap;              // Q (Laplacian variant)
+    float* part;             // split x Q x accumulator partials (split > 1)
 };
 
 // Accumulates one tile of pairs for one query into acc[].
-template <bool KAPPA>
+template <bool KAPPA, bool LAP>
 __device__ __forceinline__ void grad_tile(const float4* __restrict__ tile, int cnt, float x, float y, float z,
-                                          float L, float A0, float (&acc)[kAcc]) {
+                                          float L, float A0, float (&acc)[NAcc<LAP>::value]) {
 #pragma unroll 1
     for (int j = 0; j < cnt; ++j) {
         const float4 r0 = tile[4 * j], r1 = tile[4 * j + 1], r2 = tile[4 * j + 2];
@@ -49,7 +66,7 @@ __device__ __forceinline__ void grad_tile(const float4* __restrict__ tile, int c
         const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
         const float rd = rsqrt_mufu(fmaxf(d2, kTiny));
         const float d = d2 * rd;
-        float g, gx, gy, gz;
+        float g, gx, gy, gz, lapg = 0.f;
         if (!KAPPA) {
             // direct form: g = sT (||(rho - R, h)|| - r), grad g = alpha v_perp + beta u
             const float vx = x - r1.x, vy = y - r1.y, vz = z - r1.z;
@@ -66,6 +83,8 @@ __device__ __forceinline__ void grad_tile(const float4* __restrict__ tile, int c
             gx = fmaf(alpha, px, beta * r2.x);
             gy = fmaf(alpha, py, beta * r2.y);
             gz = fmaf(alpha, pz, beta * r2.z);
+            // lap D = 1/D + (rho - R)/(rho D) for D the distance to the tube's centre circle
+            if (LAP) lapg = r0.w * rD * fmaf(e, rr, 1.f);
         } else {
             // kappa form (see g_kappa): with s1 = sqrt(1 + k m), s2 = sqrt(1 + K N'),
             // K = -kappa_max, grad m = 2 k y_perp + m*, d a'/dm = 1/(2 s1),
@@ -91,6 +110,10 @@ __device__ __forceinline__ void grad_tile(const float4* __restrict__ tile, int c
             gx = fmaf(ay, yx, fmaf(c1, r3.x, bu * r2.x));
             gy = fmaf(ay, yy, fmaf(c1, r3.y, bu * r2.y));
             gz = fmaf(ay, yz, fmaf(c1, r3.z, bu * r2.z));
+            // lap m = 4k, |grad m|^2 = 4 s1^2 give lap a' = k / s1 and |grad a'| = 1;
+            // then lap N' = 4K + (2K a' + 2 zeta) k / s1, |grad N'|^2 = 4 s2^2, so
+            // lap g = (K + k (K a' + zeta) / s1) / s2
+            if (LAP) lapg = fmaf(r1.w * fmaf(r2.w, ap, 0.5f * r0.w), rs1, r2.w) * rs2;
         }
         const float w = ex2_mufu(fmaf(-L, d, A0));
         const float wg = w * g;
@@ -108,6 +131,25 @@ __device__ __forceinline__ void grad_tile(const float4* __restrict__ tile, int c
         acc[A_HZ] = fmaf(wgn, dz, acc[A_HZ]);
         acc[A_D] = fmaf(w, d, acc[A_D]);
         acc[A_GD] = fmaf(wg, d, acc[A_GD]);
+        if (LAP) {
+            const float wd = w * d, wgd = wg * d;
+            acc[A_LG] = fmaf(w, lapg, acc[A_LG]);
+            acc[A_UG] = fmaf(wn, fmaf(dx, gx, fmaf(dy, gy, dz * gz)), acc[A_UG]);
+            acc[A_GR] = fmaf(wg, rd, acc[A_GR]);
+            acc[A_R] = fmaf(w, rd, acc[A_R]);
+            acc[A_DD] = fmaf(w, d2, acc[A_DD]);
+            acc[A_DDG] = fmaf(wg, d2, acc[A_DDG]);
+            acc[A_DUX] = fmaf(w, dx, acc[A_DUX]);
+            acc[A_DUY] = fmaf(w, dy, acc[A_DUY]);
+            acc[A_DUZ] = fmaf(w, dz, acc[A_DUZ]);
+            acc[A_DHX] = fmaf(wg, dx, acc[A_DHX]);
+            acc[A_DHY] = fmaf(wg, dy, acc[A_DHY]);
+            acc[A_DHZ] = fmaf(wg, dz, acc[A_DHZ]);
+            acc[A_DGX] = fmaf(wd, gx, acc[A_DGX]);
+            acc[A_DGY] = fmaf(wd, gy, acc[A_DGY]);
+            acc[A_DGZ] = fmaf(wd, gz, acc[A_DGZ]);
+            (void)wgd;
+        }
     }
 }
 
@@ -145,27 +187,61 @@ __device__ __forceinline__ QueryLam query_lambda(const QueryArgs& a, const float
     return r;
 }
 
+template <bool LAP>
 __device__ __forceinline__ void finalize(const GradArgs& ga, int64_t qi, float x, float y, float z,
-                                         const QueryLam& ql, const float (&acc)[kAcc]) {
+                                         const QueryLam& ql, const float (&acc)[NAcc<LAP>::value]) {
     const QueryArgs& a = ga.a;
     const float invW = 1.f / acc[A_W];
     const float phi = acc[A_S] * invW;
+    const bool lam_x = a.mode == SDF_LAMBDA_GLOBAL && ql.dmax > 0.f;
     float glx = 0.f, gly = 0.f, glz = 0.f;
-    if (a.mode == SDF_LAMBDA_GLOBAL && ql.dmax > 0.f) {
+    if (lam_x) {
         const float s = -ql.lam / (ql.dmax * ql.dmax);
         glx = s * (x - ql.fx);
         gly = s * (y - ql.fy);
         glz = s * (z - ql.fz);
     }
     const float cd = fmaf(-phi, acc[A_D], acc[A_GD]);   // sum w g d - phi sum w d
-    const float gx = (acc[A_GX] - ql.lam * fmaf(-phi, acc[A_NX], acc[A_HX]) - glx * cd) * invW;
-    const float gy = (acc[A_GY] - ql.lam * fmaf(-phi, acc[A_NY], acc[A_HY]) - gly * cd) * invW;
-    const float gz = (acc[A_GZ] - ql.lam * fmaf(-phi, acc[A_NZ], acc[A_HZ]) - glz * cd) * invW;
-    a.phi[qi] = phi - a.offset;
-    ga.grad[3 * qi] = gx;
-    ga.grad[3 * qi + 1] = gy;
-    ga.grad[3 * qi + 2] = gz;
-    if (ga.saved) {
+    // grad phi at constant lambda (App. D: A + phi B), then the lambda_x term
+    const float fx = (acc[A_GX] - ql.lam * fmaf(-phi, acc[A_NX], acc[A_HX])) * invW;
+    const float fy = (acc[A_GY] - ql.lam * fmaf(-phi, acc[A_NY], acc[A_HY])) * invW;
+    const float fz = (acc[A_GZ] - ql.lam * fmaf(-phi, acc[A_NZ], acc[A_HZ])) * invW;
+    const float gx = fmaf(-glx, cd * invW, fx), gy = fmaf(-gly, cd * invW, fy), gz = fmaf(-glz, cd * invW, fz);
+    if (a.phi) a.phi[qi] = phi - a.offset;
+    if (ga.grad) {
+        ga.grad[3 * qi] = gx;
+        ga.grad[3 * qi + 1] = gy;
+        ga.grad[3 * qi + 2] = gz;
+    }
+    if (LAP) {
+        // Laplacian at constant lambda (App. D, "Laplacian"), with the
+        // lambda^2 terms cancelled analytically:
+        //   lap_x F = [sum w lap g - 2 lambda (sum w <u, grad g> + sum w (g - F) / d)] / W
+        //             + 2 <B, grad_x F>,   B = lambda sum w u / W
+        const float bx = ql.lam * acc[A_NX] * invW, by = ql.lam * acc[A_NY] * invW, bz = ql.lam * acc[A_NZ] * invW;
+        const float gr = fmaf(-phi, acc[A_R], acc[A_GR]);
+        float lap = fmaf(-2.f * ql.lam, acc[A_UG] + gr, acc[A_LG]) * invW +
+                    2.f * fmaf(bx, fx, fmaf(by, fy, bz * fz));
+        if (lam_x) {
+            // lambda_x = 2C / d_max(x) is harmonic (lap of 1/r is 0), so
+            //   lap phi = lap_x F + 2 <grad_x F_lambda, grad lambda> + F_lambda_lambda |grad lambda|^2
+            const float Fl = -cd * invW;
+            const float md = acc[A_D] * invW;
+            const float Fll = fmaf(-phi, acc[A_DD], acc[A_DDG]) * invW + 2.f * Fl * md;
+            // grad_x F_lambda = [grad_x F M_d - (sum w g u - F sum w u) + lambda (sum w d g u - F sum w d u)
+            //                    - sum w d grad g] / W + F_lambda B
+            const float hx = fmaf(-phi, acc[A_NX], acc[A_HX]), hy = fmaf(-phi, acc[A_NY], acc[A_HY]),
+                        hz = fmaf(-phi, acc[A_NZ], acc[A_HZ]);
+            const float ex = fmaf(-phi, acc[A_DUX], acc[A_DHX]), ey = fmaf(-phi, acc[A_DUY], acc[A_DHY]),
+                        ez = fmaf(-phi, acc[A_DUZ], acc[A_DHZ]);
+            const float qx = fmaf(fx, acc[A_D], fmaf(ql.lam, ex, -hx - acc[A_DGX])) * invW + Fl * bx;
+            const float qy = fmaf(fy, acc[A_D], fmaf(ql.lam, ey, -hy - acc[A_DGY])) * invW + Fl * by;
+            const float qz = fmaf(fz, acc[A_D], fmaf(ql.lam, ez, -hz - acc[A_DGZ])) * invW + Fl * bz;
+            const float gl2 = fmaf(glx, glx, fmaf(gly, gly, glz * glz));
+            lap += 2.f * fmaf(qx, glx, fmaf(qy, gly, qz * glz)) + Fll * gl2;
+        }
+        ga.lap[qi] = lap;
+    } else if (ga.saved) {
         float* s = ga.saved + 8 * qi;
         s[0] = x;
         s[1] = y;
@@ -178,6 +254,7 @@ __device__ __forceinline__ void finalize(const GradArgs& ga, int64_t qi, float x
     }
 }
 
+template <bool LAP>
 __global__ void __launch_bounds__(kThreads) k_fwd_grad(const float4* __restrict__ rec, int64_t n_direct,
                                                        int64_t n_kappa, int64_t tiles_direct, int64_t tiles_total,
                                                        int64_t tiles_per_chunk, GradArgs ga, int32_t* status) {
@@ -201,6 +278,7 @@ __global__ void __launch_bounds__(kThreads) k_fwd_grad(const float4* __restrict_
     const int64_t qq = qi < a.q ? qi : a.q - 1;
     const float x = a.x[3 * qq], y = a.x[3 * qq + 1], z = a.x[3 * qq + 2];
     const QueryLam ql = query_lambda(a, ga.pre, qq);
+    constexpr int kAcc = NAcc<LAP>::value;
     float acc[kAcc], tacc[kAcc];
 #pragma unroll
     for (int k = 0; k < kAcc; ++k) acc[k] = 0.f;
@@ -215,16 +293,16 @@ __global__ void __launch_bounds__(kThreads) k_fwd_grad(const float4* __restrict_
 #pragma unroll
         for (int k = 0; k < kAcc; ++k) tacc[k] = 0.f;
         if (kappa)
-            grad_tile<true>(tile, cnt, x, y, z, ql.L, ql.A0, tacc);
+            grad_tile<true, LAP>(tile, cnt, x, y, z, ql.L, ql.A0, tacc);
         else
-            grad_tile<false>(tile, cnt, x, y, z, ql.L, ql.A0, tacc);
+            grad_tile<false, LAP>(tile, cnt, x, y, z, ql.L, ql.A0, tacc);
 #pragma unroll
         for (int k = 0; k < kAcc; ++k) acc[k] += tacc[k];
         ring.release(t, lane);
     }
     if (qi >= a.q) return;
     if (a.split == 1) {
-        finalize(ga, qi, x, y, z, ql, acc);
+        finalize<LAP>(ga, qi, x, y, z, ql, acc);
     } else {
         float* dst = ga.part + ((size_t)chunk * a.q + qi) * kAcc;
 #pragma unroll
@@ -232,7 +310,9 @@ __global__ void __launch_bounds__(kThreads) k_fwd_grad(const float4* __restrict_
     }
 }
 
+template <bool LAP>
 __global__ void k_merge_grad(GradArgs ga) {
+    constexpr int kAcc = NAcc<LAP>::value;
     const QueryArgs& a = ga.a;
     const int64_t qi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (qi >= a.q) return;
@@ -245,13 +325,15 @@ __global__ void k_merge_grad(GradArgs ga) {
         for (int k = 0; k < kAcc; ++k) acc[k] += src[k];
     }
     const QueryLam ql = query_lambda(a, ga.pre, qi);
-    finalize(ga, qi, a.x[3 * qi], a.x[3 * qi + 1], a.x[3 * qi + 2], ql, acc);
+    finalize<LAP>(ga, qi, a.x[3 * qi], a.x[3 * qi + 1], a.x[3 * qi + 2], ql, acc);
 }
 
 }  // namespace
 
 sdf_status launch_query_grad(const Cloud& c, const float* d_x, int64_t q, float* d_phi, float* d_grad,
-                             float* d_saved, const sdf_query_opts& o, cudaStream_t st) {
+                             float* d_saved, const sdf_query_opts& o, cudaStream_t st, float* d_lap) {
+    const bool lap = d_lap != nullptr;
+    const int kAcc = lap ? NAcc<true>::value : NAcc<false>::value;
     const Plan p = make_plan(c, q, o.split_n, kGradQPerCta);
     GradArgs ga;
     QueryArgs& a = ga.a;
@@ -273,6 +355,7 @@ sdf_status launch_query_grad(const Cloud& c, const float* d_x, int64_t q, float*
     ga.pre = c.pre;
     ga.grad = d_grad;
     ga.saved = d_saved;
+    ga.lap = d_lap;
     ga.part = nullptr;
     auto oom = [&](cudaError_t e) {
         if (a.d2) cudaFreeAsync(a.d2, st);
@@ -310,14 +393,15 @@ sdf_status launch_query_grad(const Cloud& c, const float* d_x, int64_t q, float*
     }
     if (e == cudaSuccess) {
         ProfRange pr(SDF_K_FWD_GRAD, st);
-        k_fwd_grad<<<grid, kThreads, kStages * kTileBytes, st>>>(c.rec, c.n_direct, c.n_kappa, c.tiles_direct,
-                                                                c.tiles_direct + c.tiles_kappa, p.tiles_per_chunk,
-                                                                ga, c.status);
+        auto kern = lap ? k_fwd_grad<true> : k_fwd_grad<false>;
+        kern<<<grid, kThreads, kStages * kTileBytes, st>>>(c.rec, c.n_direct, c.n_kappa, c.tiles_direct,
+                                                          c.tiles_direct + c.tiles_kappa, p.tiles_per_chunk, ga,
+                                                          c.status);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess && p.split > 1) {
         ProfRange pr(SDF_K_MERGE, st);
-        k_merge_grad<<<(unsigned)((q + 255) / 256), 256, 0, st>>>(ga);
+        (lap ? k_merge_grad<true> : k_merge_grad<false>)<<<(unsigned)((q + 255) / 256), 256, 0, st>>>(ga);
         e = cudaGetLastError();
     }
     cudaFreeAsync(a.d2, st);

@@ -161,7 +161,8 @@ sdf_status launch_trace(const Cloud& c, const float* d_org, const float* d_dir, 
 sdf_status launch_backward_params(const Cloud& c, int64_t q, const float* d_saved, const float* d_grad_phi,
                                   float* d_grad_params, const sdf_query_opts& o, cudaStream_t st);
 // grad.cu
+// d_lap non-null: also the Laplacian (and d_grad may be null)
 sdf_status launch_query_grad(const Cloud& c, const float* d_x, int64_t q, float* d_phi, float* d_grad,
-                             float* d_saved, const sdf_query_opts& o, cudaStream_t st);
+                             float* d_saved, const sdf_query_opts& o, cudaStream_t st, float* d_lap = nullptr);
 
 }  // namespace ptsdf

@@ -1,0 +1,124 @@
+"""GPU parity of sdf_query_laplacian (App. D, "Laplacian") against the
+oracle's second-order jets, and the eikonal residual |grad phi| - 1.
+
+Closed forms where every torus equals the shape (sphere 2/|x|, plane 0,
+ring-torus equators 1/D + (rho - R)/(rho D)); generic clouds (both torus
+record forms, GLOBAL and FIXED lambda) against the oracle away from
+farthest-point ties.  Tolerance: |lap_gpu - lap_oracle| <= 1e-2 (1 + |lap|):
+the FP32 assembly subtracts sums of size lambda sum w / d that cancel in exact
+arithmetic (measured errors 1e-4 to 1e-2 relative).  The gradient it returns
+equals sdf_query_grad's."""
+import math
+
+import numpy as np
+import pytest
+
+import synth
+from workloads import f32, mixed_cloud
+
+pytestmark = pytest.mark.gpu
+
+TOL_LAP = 1e-2
+
+
+@pytest.fixture(scope="module")
+def ptsdf():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2607_16946_b300 import build
+    build.build()
+    import paper_2607_16946_b300 as m
+    return m
+
+
+def run(cloud, x, **kw):
+    import torch
+    xt = torch.as_tensor(np.asarray(x, np.float32), device="cuda")
+    phi, g, lap = cloud.query_laplacian(xt, **kw)
+    torch.cuda.synchronize()
+    assert cloud.device_status() == 0
+    return (phi.cpu().numpy().astype(np.float64), g.cpu().numpy().astype(np.float64),
+            lap.cpu().numpy().astype(np.float64))
+
+
+def test_sphere_closed_form(ptsdf):
+    p, n, a = f32(*synth.sphere_fibonacci(4096, 1001))
+    cl = ptsdf.Cloud(p, n, a)
+    x = f32(synth.uniform_queries(3000, 40))
+    r = np.linalg.norm(x.astype(np.float64), axis=1)
+    for kw in ({}, {"lambda_mode": ptsdf.SDF_LAMBDA_FIXED, "fixed_lambda": 50.0}):
+        phi, g, lap = run(cl, x, **kw)
+        assert (np.abs(lap - 2.0 / r) <= TOL_LAP * (1 + 2.0 / r)).all()
+        assert np.abs(np.linalg.norm(g, axis=1) - 1.0).max() < 1e-4     # eikonal
+        np.testing.assert_allclose(phi, r - 1.0, atol=1e-5)
+
+
+def test_plane_and_ring_equators(ptsdf):
+    p, n, a = f32(*synth.plane_patch(400, 9))
+    x = f32(synth.uniform_queries(500, 41))
+    _, g, lap = run(ptsdf.Cloud(p, n, a), x)
+    assert np.abs(lap).max() < TOL_LAP
+    R, r = 1.0, 0.35
+    psi = np.linspace(0, 2 * math.pi, 64, endpoint=False)
+    theta = np.concatenate([np.zeros(64), np.full(64, math.pi)])
+    p, n, a = f32(*synth.ring_torus(128, 0, R=R, r=r, noise=0.0, jitter_deg=0.0, theta=theta,
+                                    psi=np.concatenate([psi, psi + 0.05])))
+    x = f32(synth.uniform_queries(800, 42, -1.6, 1.6))
+    xd = x.astype(np.float64)
+    rho = np.linalg.norm(xd[:, :2], axis=1)
+    D = np.sqrt((rho - R) ** 2 + xd[:, 2] ** 2)
+    ref = 1.0 / D + (rho - R) / (rho * D)
+    keep = (rho > 0.05) & (D > 0.05)                   # away from the axis and the centre circle
+    _, _, lap = run(ptsdf.Cloud(p, n, a), x)
+    assert (np.abs(lap - ref)[keep] <= TOL_LAP * (1 + np.abs(ref[keep]))).all()
+
+
+@pytest.mark.parametrize("mode", ["global", "fixed"])
+def test_generic_clouds_vs_oracle(ptsdf, oracle_mod, mode):
+    from test_gpu_grad import kink_free
+    clouds = (f32(*synth.ellipsoid(2000, 80)), f32(*synth.ring_torus(3000, 21, noise=0.01, jitter_deg=5.0)),
+              mixed_cloud(3))
+    for p, n, a in clouds:
+        cl = ptsdf.Cloud(p, n, a)
+        orc = oracle_mod.Cloud(p, n, a)
+        x = f32(synth.uniform_queries(1500, 43, -1.4, 1.4))
+        if mode == "global":
+            x = x[kink_free(p, x, 0.02, 0.3)][:400]
+            kw, okw = {}, {}
+        else:
+            x = x[:400]
+            kw = {"lambda_mode": ptsdf.SDF_LAMBDA_FIXED, "fixed_lambda": 60.0}
+            okw = {"mode": oracle_mod.FIXED, "lam": 60.0}
+        assert len(x) >= 100
+        phi, g, lap = run(cl, x, **kw)
+        rphi, rg, rlap = orc.laplacian(x, **okw)
+        err = np.abs(lap - rlap) / (1.0 + np.abs(rlap))
+        assert err.max() <= TOL_LAP, (err.max(), np.argmax(err), lap[np.argmax(err)], rlap[np.argmax(err)])
+        assert np.abs(g - rg).max() <= 1e-3 * (1 + np.abs(rg).max())
+
+
+def test_split_and_gradient_agree(ptsdf):
+    import torch
+    p, n, a = mixed_cloud(5)
+    cl = ptsdf.Cloud(p, n, a)
+    x = f32(synth.uniform_queries(700, 44))
+    _, g1, l1 = run(cl, x, split_n=1)
+    for s in (3, 7):
+        _, gs, ls = run(cl, x, split_n=s)
+        assert np.abs(ls - l1).max() <= 1e-4 * (1 + np.abs(l1).max())
+        np.testing.assert_allclose(gs, g1, atol=1e-5)
+    xt = torch.as_tensor(x, device="cuda")
+    _, gg, _ = cl.query_grad(xt, split_n=1)
+    np.testing.assert_allclose(gg.cpu().numpy(), g1, atol=1e-6)
+
+
+def test_laplacian_options(ptsdf):
+    import torch
+    p, n, a = mixed_cloud(4)
+    cl = ptsdf.Cloud(p, n, a)
+    x = torch.zeros((4, 3), device="cuda")
+    with pytest.raises(ptsdf.SdfError):
+        cl.query_laplacian(x, lambda_mode=ptsdf.SDF_LAMBDA_RADIUS, fixed_lambda=10.0)
+    with pytest.raises(ptsdf.SdfError):
+        cl.query_laplacian(x, precision=1)
