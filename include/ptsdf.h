@@ -358,6 +358,29 @@ PTSDF_API sdf_status sdf_query_laplacian(sdf_cloud cloud, const float* d_x, int6
                                          float* d_lap, const sdf_query_opts* opts, void* stream);
 
 /* ---------------------------------------------------------------------------
+ * sdf_orient -- orientation repair of an inconsistently oriented cloud
+ * (Sec. 6, "Orienting inconsistently oriented point clouds").  Each
+ * iteration builds the cloud, evaluates grad phi at its points, and for every
+ * point i forms n~_i = sum over its k nearest other points j of
+ * exp(-M_i(p_i - p_j)) grad phi(p_j), with the curvature-scaled length
+ * M_i(r) = sqrt(kmin^2 <r, v_min>^2 + kmax^2 <r, v_max>^2 + eps^2 <r, n_i>^2)
+ * (principal curvatures and directions of point i's fit, eps = 1 / the mean
+ * distance to the k nearest).  Points with <n_i, n~_i> < 0 are flipped: n_i
+ * is negated and its six coefficients re-expressed, for the same quadratic
+ * patch, in the frame of -n_i (so its torus is the same torus with the
+ * opposite sign).  All points decide from the same cloud; iterations stop
+ * when nothing flips or after max_iter.
+ *   d_points N x 3 (read), d_normals N x 3 and d_params N x 6 (device, read
+ *   and overwritten).  k in [1, 64] (16 is a reasonable default); opts as for
+ *   sdf_query_grad (GLOBAL or FIXED lambda, FP32).  flips (host, max_iter
+ *   entries) receives the flip count of each iteration run, *iterations their
+ *   number.  Synchronous on `stream`.
+ * ------------------------------------------------------------------------- */
+PTSDF_API sdf_status sdf_orient(const float* d_points, float* d_normals, float* d_params, int64_t n, int32_t k,
+                                int32_t max_iter, const sdf_query_opts* opts, int32_t* flips, int32_t* iterations,
+                                void* stream);
+
+/* ---------------------------------------------------------------------------
  * sdf_knn_mean_distance -- D of the lambda heuristic of Sec. 4.2
  * ("Acceleration and adaptive lambda"): for every point of the cloud the
  * mean of the distances to its k nearest other points (all of them when the

@@ -23,7 +23,7 @@ from ._abi import (SDF_DIFFERENCE, SDF_ENGINE_ALU, SDF_ENGINE_AUTO, SDF_ENGINE_T
 
 __all__ = ["Cloud", "SdfError", "SDF_LAMBDA_GLOBAL", "SDF_LAMBDA_FIXED", "SDF_LAMBDA_RADIUS", "SDF_UNION",
            "SDF_INTERSECT",
-           "SDF_DIFFERENCE", "mesh_level_set", "SDF_ENGINE_AUTO", "SDF_ENGINE_ALU", "SDF_ENGINE_TENSOR", "make_opts", "lib", "sdf",
+           "SDF_DIFFERENCE", "mesh_level_set", "orient", "SDF_ENGINE_AUTO", "SDF_ENGINE_ALU", "SDF_ENGINE_TENSOR", "make_opts", "lib", "sdf",
            "combine"]
 
 
@@ -266,3 +266,21 @@ def mesh_level_set(phi, origin, spacing, level: float = 0.0, stream=None):
                                        ctypes.c_void_p(verts.data_ptr()), nv.value, ctypes.c_void_p(tris.data_ptr()),
                                        nt.value, ctypes.byref(nv), ctypes.byref(nt), sp), "sdf_mesh_level_set")
     return verts, tris
+
+
+def orient(points, normals, params, k: int = 16, max_iter: int = 10, stream=None, **opts):
+    """Orientation repair (sdf_orient, Sec. 6) on copies of the inputs: returns
+    (normals, params, flips per iteration) as CUDA tensors and a list."""
+    torch = _torch()
+    p = _dev_f32(points, 3)
+    nrm = _dev_f32(normals, 3).clone()
+    prm = torch.as_tensor(params, dtype=torch.float32, device=p.device).reshape(-1, 6).contiguous().clone()
+    if nrm.shape[0] != p.shape[0] or prm.shape[0] != p.shape[0]:
+        raise ValueError("points, normals and params must have the same length")
+    flips = (ctypes.c_int32 * max_iter)()
+    iters = ctypes.c_int32()
+    o = make_opts(**opts)
+    check(lib().sdf_orient(ctypes.c_void_p(p.data_ptr()), ctypes.c_void_p(nrm.data_ptr()),
+                           ctypes.c_void_p(prm.data_ptr()), p.shape[0], int(k), int(max_iter), ctypes.byref(o), flips,
+                           ctypes.byref(iters), _stream_ptr(stream)), "sdf_orient")
+    return nrm, prm, [flips[i] for i in range(iters.value)]

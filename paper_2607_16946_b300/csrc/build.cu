@@ -193,8 +193,9 @@ __global__ void k_partition(const float4* __restrict__ rec_tmp, const int8_t* __
 // Records in the Morton order of the prepass array (compact position order[m]:
 // direct points first, then kappa-form ones), flagged r3.w = 1 for the kappa
 // form, for the radius-limited evaluation and the k-nearest searches.
-__global__ void k_gather_morton(const float4* __restrict__ rec, const int32_t* __restrict__ order, int64_t n,
-                                int64_t n_direct, int64_t tiles_direct, float4* __restrict__ mrec) {
+__global__ void k_gather_morton(const float4* __restrict__ rec, const int32_t* __restrict__ order,
+                                const int32_t* __restrict__ perm, int64_t n, int64_t n_direct, int64_t tiles_direct,
+                                float4* __restrict__ mrec, int32_t* __restrict__ mperm) {
     const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= n) return;
     const int64_t cpos = order[m];
@@ -204,6 +205,7 @@ __global__ void k_gather_morton(const float4* __restrict__ rec, const int32_t* _
     float4 r3 = rec[4 * slot + 3];
     r3.w = kappa ? 1.f : 0.f;
     mrec[4 * m + 3] = r3;
+    mperm[m] = perm[slot];
 }
 
 __global__ void k_fill_perm(int32_t* perm, int64_t m) {
@@ -295,6 +297,7 @@ void free_cloud(Cloud* c) {
     cudaFree(c->status);
     cudaFree(c->btiles);
     cudaFree(c->mrec);
+    cudaFree(c->mperm);
     delete c;
 }
 
@@ -423,9 +426,10 @@ extern "C" sdf_status sdf_build(const float* d_points, const float* d_normals, c
         PTSDF_TRY(cudaMalloc(&d_order, (size_t)n * sizeof(int32_t)), "sdf_build: order alloc");
         cudaError_t oe = cudaMemcpy(d_order, order.data(), (size_t)n * sizeof(int32_t), cudaMemcpyHostToDevice);
         if (oe == cudaSuccess) oe = cudaMalloc(&c->mrec, (size_t)n * 4 * sizeof(float4));
+        if (oe == cudaSuccess) oe = cudaMalloc(&c->mperm, (size_t)n * sizeof(int32_t));
         if (oe == cudaSuccess) {
-            k_gather_morton<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(c->rec, d_order, n, c->n_direct,
-                                                                       c->tiles_direct, c->mrec);
+            k_gather_morton<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(c->rec, d_order, c->perm, n, c->n_direct,
+                                                                       c->tiles_direct, c->mrec, c->mperm);
             oe = cudaGetLastError();
         }
         if (oe == cudaSuccess) oe = cudaStreamSynchronize(st);

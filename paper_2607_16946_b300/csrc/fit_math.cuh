@@ -107,6 +107,21 @@ struct FitPoint {
     T u[3];                  // axis of revolution n* x v_min
 };
 
+// Branchless orthonormal frame (s, t) of a unit normal n (Duff et al. 2017,
+// "Building an Orthonormal Basis, Revisited"): the frame the six
+// coefficients are expressed in.
+__host__ __device__ inline void duff_frame(const double n[3], double s[3], double t[3]) {
+    const double sg = n[2] >= 0.0 ? 1.0 : -1.0;
+    const double fa = -1.0 / (sg + n[2]);
+    const double fb = n[0] * n[1] * fa;
+    s[0] = 1.0 + sg * n[0] * n[0] * fa;
+    s[1] = sg * fb;
+    s[2] = -sg * n[0];
+    t[0] = fb;
+    t[1] = sg + n[1] * n[1] * fa;
+    t[2] = -n[1];
+}
+
 // n must be unit length.  a = {a00, a01, a10, a11, a02, a20}.
 template <typename T>
 __device__ void fit_point(const double p[3], const double n[3], const T a[6], FitPoint<T>& f) {
@@ -116,12 +131,8 @@ __device__ void fit_point(const double p[3], const double n[3], const T a[6], Fi
     const T& a11 = a[3];
     const T& a02 = a[4];
     const T& a20 = a[5];
-    // branchless orthonormal frame of n (Duff et al. 2017)
-    const double sg = n[2] >= 0.0 ? 1.0 : -1.0;
-    const double fa = -1.0 / (sg + n[2]);
-    const double fb = n[0] * n[1] * fa;
-    const double s[3] = {1.0 + sg * n[0] * n[0] * fa, sg * fb, -sg * n[0]};
-    const double t[3] = {fb, sg + n[1] * n[1] * fa, -n[1]};
+    double s[3], t[3];
+    duff_frame(n, s, t);
 
     // fundamental forms at (0,0): I = [[E, F], [F, G]], II = [[2 a20, a11], [a11, 2 a02]] / A
     const T E = 1.0 + a10 * a10, G = 1.0 + a01 * a01, F = a10 * a01;

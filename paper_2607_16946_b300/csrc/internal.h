@@ -79,6 +79,7 @@ struct Cloud {
     int32_t* status = nullptr;       // device status word (SDF_DEV_* bits)
     uint8_t* btiles = nullptr;       // tiles_direct x 14 KB split-f16 operands of the tensor-core loop
     float4* mrec = nullptr;          // n x 4 float4 records in the prepass (Morton) order, r3.w = 1 for kappa
+    int32_t* mperm = nullptr;        // input index of each Morton position
     float tc_scale = 1.f;            // their coordinate scale (a power of two >= the AABB diagonal)
     int num_sms = 148;
 };
@@ -148,6 +149,9 @@ sdf_status launch_fwd_tc(const Cloud& c, const TcQuery& a, int64_t tiles_per_chu
 
 // radius-limited evaluation (radius.cu): the fallback neighbour count of Sec. 4.2
 constexpr int kRadiusFallbackK = 32;
+// the k (<= 64) nearest other points of every point, as input indices (n x k,
+// input order), and the mean of their distances (D of the lambda heuristic)
+sdf_status launch_knn_indices(const Cloud& c, int k, int32_t* d_idx, double* mean_dist, cudaStream_t st);
 sdf_status launch_radius_query(const Cloud& c, const float* d_x, int64_t q, float* d_phi, const sdf_query_opts& o,
                                cudaStream_t st);
 

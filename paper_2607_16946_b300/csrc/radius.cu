@@ -212,6 +212,35 @@ __global__ void __launch_bounds__(kRadiusThreads) k_knn_mean(RadiusArgs a, int k
     if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
 }
 
+// The k nearest of the point at Morton position i, written as input indices
+// at its input row; one partial sum of the mean distances per block.
+__global__ void __launch_bounds__(kRadiusThreads) k_knn_index(RadiusArgs a, int k, const int32_t* __restrict__ mperm,
+                                                              int32_t* __restrict__ idx, double* __restrict__ partial) {
+    __shared__ double red[kRadiusThreads];
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double v = 0.0;
+    if (i < a.n) {
+        const float4 e = __ldg(a.pre + i);
+        float bd[kKnnMax];
+        int bi[kKnnMax];
+        const int cnt = knn_scan(a, -0.5f * e.x, -0.5f * e.y, -0.5f * e.z, k, i, i / kSphereTile, bd, bi);
+        const int64_t row = mperm[i];
+        double s = 0.0;
+        for (int j = 0; j < k; ++j) {
+            idx[row * k + j] = j < cnt ? mperm[bi[j]] : -1;
+            if (j < cnt) s += sqrt((double)bd[j]);
+        }
+        v = cnt > 0 ? s / cnt : 0.0;
+    }
+    red[threadIdx.x] = v;
+    __syncthreads();
+    for (int w = kRadiusThreads / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
+}
+
 RadiusArgs radius_args(const Cloud& c) {
     RadiusArgs a;
     a.x = nullptr;
@@ -247,6 +276,29 @@ sdf_status launch_radius_query(const Cloud& c, const float* d_x, int64_t q, floa
     k_radius_query<<<(unsigned)((q + kRadiusThreads - 1) / kRadiusThreads), kRadiusThreads, 0, st>>>(a);
     const cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? SDF_OK : cuda_error(e, "sdf_query: k_radius_query launch");
+}
+
+sdf_status launch_knn_indices(const Cloud& c, int k, int32_t* d_idx, double* mean_dist, cudaStream_t st) {
+    if (k < 1 || k > kKnnMax) return set_error(SDF_EINVAL, "k-nearest search: k must be in [1, 64]");
+    RadiusArgs a = radius_args(c);
+    const int64_t blocks = (c.n + kRadiusThreads - 1) / kRadiusThreads;
+    double* part = nullptr;
+    cudaError_t e = cudaMallocAsync(&part, (size_t)blocks * sizeof(double), st);
+    if (e != cudaSuccess) return cuda_error(e, "k-nearest search: scratch");
+    {
+        ProfRange pr(SDF_K_KNN, st);
+        k_knn_index<<<(unsigned)blocks, kRadiusThreads, 0, st>>>(a, k, c.mperm, d_idx, part);
+        e = cudaGetLastError();
+    }
+    std::vector<double> h((size_t)blocks);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h.data(), part, (size_t)blocks * sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFreeAsync(part, st);
+    if (e != cudaSuccess) return cuda_error(e, "k-nearest search");
+    double s = 0.0;
+    for (double v : h) s += v;
+    if (mean_dist) *mean_dist = c.n > 0 ? s / (double)c.n : 0.0;
+    return SDF_OK;
 }
 
 }  // namespace ptsdf
