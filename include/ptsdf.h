@@ -429,6 +429,15 @@ PTSDF_API sdf_status sdf_mesh_level_set(const float* d_phi, int32_t nx, int32_t 
  * any cloud.  rates must hold 4 doubles. */
 PTSDF_API sdf_status sdf_probe_rates(double* rates);
 
+/* Self-test of the failure path (not part of the method): launches one
+ * kernel whose thread waits, through the same bounded mbarrier wait the pair
+ * loops use but with a limit of limit_us microseconds (1 .. 1e6), on a phase
+ * that nothing completes.  The wait gives up, the kernel records
+ * SDF_DEV_WAIT_TIMEOUT in its own status word and returns: *status_bits
+ * receives that word (SDF_DEV_WAIT_TIMEOUT expected) and *waited_ms the time
+ * the wait took.  Nothing faults or hangs, and the context stays usable. */
+PTSDF_API sdf_status sdf_selftest_wait_timeout(int32_t limit_us, int32_t* status_bits, double* waited_ms);
+
 enum { SDF_K_PREPASS = 0, SDF_K_FWD = 1, SDF_K_MERGE = 2, SDF_K_BUILD = 3, SDF_K_FWD_GRAD = 4, SDF_K_BWD = 5,
        SDF_K_FWD_TC = 6, SDF_K_RADIUS = 7, SDF_K_KNN = 8, SDF_K_COUNT_ = 9 };
 PTSDF_API sdf_status sdf_profile_enable(int32_t on);

@@ -92,21 +92,27 @@ __device__ __forceinline__ uint64_t global_ns() {
 constexpr uint64_t kWaitLimitNs = 2000000000ull;
 
 // Bounded wait on one mbarrier phase.  Returns false (and raises `abort` for
-// the whole CTA) if the phase did not complete in time or another thread of
-// the CTA already aborted.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, volatile int* abort,
-                                                  int32_t* status) {
+// the whole CTA) if the phase did not complete within limit_ns or another
+// thread of the CTA already aborted; a timeout also sets SDF_DEV_WAIT_TIMEOUT
+// in the device status word.
+__device__ __forceinline__ bool mbar_wait_bounded_ns(uint64_t* bar, uint32_t parity, volatile int* abort,
+                                                     int32_t* status, uint64_t limit_ns) {
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = global_ns();
     while (true) {
         if (mbar_try_wait(bar, parity)) return true;
         if (*abort) return false;
-        if (global_ns() - t0 > kWaitLimitNs) {
+        if (global_ns() - t0 > limit_ns) {
             *abort = 1;
             atomicOr(status, (int32_t)SDF_DEV_WAIT_TIMEOUT);
             return false;
         }
     }
+}
+
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, volatile int* abort,
+                                                  int32_t* status) {
+    return mbar_wait_bounded_ns(bar, parity, abort, status, kWaitLimitNs);
 }
 
 // --------------------------------------------------------------------------

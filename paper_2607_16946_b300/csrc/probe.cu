@@ -115,3 +115,55 @@ extern "C" sdf_status sdf_probe_rates(double* rates) {
     cudaFree(smid);
     return e == cudaSuccess ? SDF_OK : cuda_error(e, "sdf_probe_rates");
 }
+
+// ---------------------------------------------------------------------------
+// Self-test of the failure path: one thread waits, with a short limit, on an
+// mbarrier phase that nothing will complete (no thread ever arrives), through
+// the same bounded wait the pair loops use.  The wait must give up, record
+// SDF_DEV_WAIT_TIMEOUT and return; nothing faults and nothing hangs.
+// ---------------------------------------------------------------------------
+namespace ptsdf {
+namespace {
+
+__global__ void k_wait_selftest(uint64_t limit_ns, int32_t* status, unsigned long long* waited_ns) {
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ int abort_flag;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        abort_flag = 0;
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const uint64_t t0 = global_ns();
+        const bool completed = mbar_wait_bounded_ns(&bar, 0u, &abort_flag, status, limit_ns);
+        *waited_ns = global_ns() - t0;
+        if (completed) atomicOr(status, 0x40000000);   // cannot happen: nothing arrives
+    }
+}
+
+}  // namespace
+}  // namespace ptsdf
+
+extern "C" sdf_status sdf_selftest_wait_timeout(int32_t limit_us, int32_t* status_bits, double* waited_ms) {
+    if (!status_bits || !waited_ms || limit_us < 1 || limit_us > 1000000)
+        return set_error(SDF_EINVAL, "sdf_selftest_wait_timeout: limit_us in [1, 1e6] and non-NULL outputs");
+    int32_t* d_status = nullptr;
+    unsigned long long* d_waited = nullptr;
+    cudaError_t e = cudaMalloc(&d_status, sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMalloc(&d_waited, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemset(d_status, 0, sizeof(int32_t));
+    if (e == cudaSuccess) {
+        k_wait_selftest<<<1, 32>>>((uint64_t)limit_us * 1000ull, d_status, d_waited);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    unsigned long long w = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(status_bits, d_status, sizeof(int32_t), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(&w, d_waited, sizeof(w), cudaMemcpyDeviceToHost);
+    cudaFree(d_status);
+    cudaFree(d_waited);
+    if (e != cudaSuccess) return cuda_error(e, "sdf_selftest_wait_timeout");
+    *waited_ms = (double)w * 1e-6;
+    return SDF_OK;
+}

@@ -211,3 +211,20 @@ def test_probe_rates(ptsdf):
         assert 2.0 <= r <= 64.0, list(buf)
     assert 32.0 <= fma_r <= 260.0, list(buf)
     assert ex2_r >= 0.9 * sqrt_r and fma_r > ex2_r
+
+
+def test_wait_timeout_reports_and_recovers(ptsdf):
+    """Failure detection without a fault: a bounded wait on an mbarrier phase
+    that nothing completes gives up after its limit, the kernel records
+    SDF_DEV_WAIT_TIMEOUT and returns, and the context keeps working."""
+    import ctypes
+    import torch
+    from paper_2607_16946_b300 import _abi
+    bits, ms = ctypes.c_int32(), ctypes.c_double()
+    assert ptsdf.lib().sdf_selftest_wait_timeout(2000, ctypes.byref(bits), ctypes.byref(ms)) == 0
+    assert bits.value == _abi.SDF_DEV_WAIT_TIMEOUT
+    assert 2.0 <= ms.value < 1000.0
+    p, n, a, x = config1()
+    cl = ptsdf.Cloud(p, n, a)
+    phi = run(cl, x[:1000], ptsdf.SDF_ENGINE_TENSOR)
+    assert np.isfinite(phi).all()
