@@ -119,7 +119,7 @@ __global__ void k_fit(const float* __restrict__ P, const float* __restrict__ Nrm
         out[8] = (float)u[0]; out[9] = (float)u[1]; out[10] = (float)u[2]; out[11] = (float)(-kmax);
         out[12] = (float)(2.0 * zeta * nstar[0]); out[13] = (float)(2.0 * zeta * nstar[1]);
         out[14] = (float)(2.0 * zeta * nstar[2]); out[15] = 0.f;
-        kind[i] = 1;
+        kind[i] = out[7] == 0.f ? 2 : 1;   // 2: kappa_min = 0 (cylinders, planes): the shorter formula
     }
 }
 
@@ -149,43 +149,53 @@ __device__ int block_exclusive_scan(int v, int* warp_sums, int* total) {
     return base + x - v;
 }
 
+// counts[0] direct, counts[1] kappa form, counts[2] of those with kappa_min = 0
 __global__ void k_count(const int8_t* __restrict__ kind, int64_t n, int64_t* __restrict__ counts) {
     __shared__ int ws[32];
-    int64_t nk = 0;
+    int64_t nk = 0, nf = 0;
     for (int64_t base = 0; base < n; base += blockDim.x) {
         const int64_t i = base + threadIdx.x;
         int tot;
         block_exclusive_scan((i < n && kind[i]) ? 1 : 0, ws, &tot);
         nk += tot;
+        block_exclusive_scan((i < n && kind[i] == 2) ? 1 : 0, ws, &tot);
+        nf += tot;
     }
     if (threadIdx.x == 0) {
         counts[0] = n - nk;
         counts[1] = nk;
+        counts[2] = nf;
     }
 }
 
+// Order of the records: direct form | kappa form with kappa_min = 0 |
+// the other kappa-form records, each in input order.
 __global__ void k_partition(const float4* __restrict__ rec_tmp, const int8_t* __restrict__ kind,
-                            const float* __restrict__ P, int64_t n, int64_t n_direct, int64_t tiles_direct,
-                            float cx, float cy, float cz, float4* __restrict__ rec, float4* __restrict__ pre,
-                            int32_t* __restrict__ perm) {
+                            const float* __restrict__ P, int64_t n, int64_t n_direct, int64_t n_flat,
+                            int64_t tiles_direct, float cx, float cy, float cz, float4* __restrict__ rec,
+                            float4* __restrict__ pre, int32_t* __restrict__ perm) {
     __shared__ int ws[32];
-    int64_t pos_d = 0, pos_k = 0;
+    int64_t pos_d = 0, pos_f = 0, pos_k = 0;
     for (int64_t base = 0; base < n; base += blockDim.x) {
         const int64_t i = base + threadIdx.x;
         const bool valid = i < n;
-        const int isk = valid ? (int)kind[i] : 0;
-        int tot_k, tot_d;
-        const int ek = block_exclusive_scan(valid && isk ? 1 : 0, ws, &tot_k);
-        const int ed = block_exclusive_scan(valid && !isk ? 1 : 0, ws, &tot_d);
+        const int kd = valid ? (int)kind[i] : 0;
+        int tot_k, tot_d, tot_f;
+        const int ek = block_exclusive_scan(valid && kd == 1 ? 1 : 0, ws, &tot_k);
+        const int ef = block_exclusive_scan(valid && kd == 2 ? 1 : 0, ws, &tot_f);
+        const int ed = block_exclusive_scan(valid && kd == 0 ? 1 : 0, ws, &tot_d);
+        const int isk = kd != 0;
         if (valid) {
-            const int64_t slot = isk ? tiles_direct * kTileRecs + pos_k + ek : pos_d + ed;
-            const int64_t cpos = isk ? n_direct + pos_k + ek : pos_d + ed;
+            const int64_t kpos = kd == 2 ? pos_f + ef : n_flat + pos_k + ek;   // within the kappa segment
+            const int64_t slot = isk ? tiles_direct * kTileRecs + kpos : pos_d + ed;
+            const int64_t cpos = isk ? n_direct + kpos : pos_d + ed;
             for (int k = 0; k < 4; ++k) rec[slot * 4 + k] = rec_tmp[i * 4 + k];
             perm[slot] = (int32_t)i;
             const float px = P[3 * i] - cx, py = P[3 * i + 1] - cy, pz = P[3 * i + 2] - cz;
             pre[cpos] = make_float4(-2.f * px, -2.f * py, -2.f * pz, px * px + py * py + pz * pz);
         }
         pos_d += tot_d;
+        pos_f += tot_f;
         pos_k += tot_k;
     }
 }
@@ -341,7 +351,7 @@ extern "C" sdf_status sdf_build(const float* d_points, const float* d_normals, c
     PTSDF_TRY(cudaMalloc(&box, 6 * sizeof(float)), "sdf_build: box alloc");
     PTSDF_TRY(cudaMalloc(&rec_tmp, (size_t)n * kRecFloats * sizeof(float)), "sdf_build: temp alloc");
     PTSDF_TRY(cudaMalloc(&kind, (size_t)n), "sdf_build: temp alloc");
-    PTSDF_TRY(cudaMalloc(&counts, 2 * sizeof(int64_t)), "sdf_build: temp alloc");
+    PTSDF_TRY(cudaMalloc(&counts, 3 * sizeof(int64_t)), "sdf_build: temp alloc");
     PTSDF_TRY(cudaMalloc(&c->src_points, (size_t)n * 3 * sizeof(float)), "sdf_build: copy alloc");
     PTSDF_TRY(cudaMalloc(&c->src_normals, (size_t)n * 3 * sizeof(float)), "sdf_build: copy alloc");
     PTSDF_TRY(cudaMalloc(&c->src_params, (size_t)n * 6 * sizeof(float)), "sdf_build: copy alloc");
@@ -369,7 +379,7 @@ extern "C" sdf_status sdf_build(const float* d_points, const float* d_normals, c
     PTSDF_TRY(cudaGetLastError(), "sdf_build: k_fit launch");
     k_count<<<1, kPartThreads, 0, st>>>(kind, n, counts);
     PTSDF_TRY(cudaGetLastError(), "sdf_build: k_count launch");
-    int64_t hcounts[2];
+    int64_t hcounts[3];
     int32_t hstatus = 0;
     PTSDF_TRY(cudaMemcpyAsync(hcounts, counts, sizeof(hcounts), cudaMemcpyDeviceToHost, st), "sdf_build: counts");
     PTSDF_TRY(cudaMemcpyAsync(&hstatus, c->status, sizeof(int32_t), cudaMemcpyDeviceToHost, st), "sdf_build: status");
@@ -379,6 +389,7 @@ extern "C" sdf_status sdf_build(const float* d_points, const float* d_normals, c
         return set_error(SDF_EINVAL, "sdf_build: zero or non-finite normal, or non-finite point / coefficient");
     }
     c->n_direct = hcounts[0];
+    c->n_kappa_flat = hcounts[2];
     c->n_kappa = hcounts[1];
     c->tiles_direct = (c->n_direct + kTileRecs - 1) / kTileRecs;
     c->tiles_kappa = (c->n_kappa + kTileRecs - 1) / kTileRecs;
@@ -393,7 +404,8 @@ extern "C" sdf_status sdf_build(const float* d_points, const float* d_normals, c
     k_fill_perm<<<(unsigned)((slots + 255) / 256), 256, 0, st>>>(c->perm, slots);
     PTSDF_TRY(cudaGetLastError(), "sdf_build: k_fill_perm launch");
     k_partition<<<1, kPartThreads, 0, st>>>(reinterpret_cast<const float4*>(rec_tmp), kind, c->src_points, n,
-                                            c->n_direct, c->tiles_direct, 0.5f * (c->aabb[0] + c->aabb[3]),
+                                            c->n_direct, c->n_kappa_flat, c->tiles_direct,
+                                            0.5f * (c->aabb[0] + c->aabb[3]),
                                             0.5f * (c->aabb[1] + c->aabb[4]), 0.5f * (c->aabb[2] + c->aabb[5]),
                                             c->rec, c->pre, c->perm);
     PTSDF_TRY(cudaGetLastError(), "sdf_build: k_partition launch");

@@ -64,6 +64,7 @@ struct Cloud {
     int device = 0;
     int64_t n = 0;                   // points
     int64_t n_direct = 0, n_kappa = 0;
+    int64_t n_kappa_flat = 0;        // kappa-form points with kappa_min = 0, first in the kappa segment
     int64_t tiles_direct = 0, tiles_kappa = 0;
     int64_t pre_tiles = 0;
     float aabb_diag = 0.f;

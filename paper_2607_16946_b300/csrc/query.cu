@@ -80,7 +80,7 @@ __device__ __forceinline__ void weights2(float a0, float a1, float& w0, float& w
     }
 }
 
-template <bool KAPPA, int PREC>
+template <bool KAPPA, int PREC, bool FLAT = false>
 __device__ __forceinline__ void pair_tile(const float4* __restrict__ tile, int cnt, QState (&qs)[kQueriesPerThread]) {
     static_assert(kQueriesPerThread % 2 == 0, "queries are paired for the packed weights");
 #pragma unroll kUnrollPts
@@ -96,7 +96,8 @@ __device__ __forceinline__ void pair_tile(const float4* __restrict__ tile, int c
                 const QState& s = qs[k + m];
                 const float dx = s.x - r0.x, dy = s.y - r0.y, dz = s.z - r0.z;
                 const float d = sqrt_mufu(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
-                g[m] = KAPPA ? g_kappa(s.x, s.y, s.z, r0, r1, r2, r3) : g_direct(s.x, s.y, s.z, r1, r2, r0.w);
+                g[m] = !KAPPA ? g_direct(s.x, s.y, s.z, r1, r2, r0.w)
+                              : FLAT ? g_kappa_flat(s.x, s.y, s.z, r0, r1, r2, r3) : g_kappa(s.x, s.y, s.z, r0, r1, r2, r3);
                 arg[m] = fmaf(-s.L, d, s.A0);
             }
             float w0, w1;
@@ -115,7 +116,7 @@ __device__ __forceinline__ void pair_tile(const float4* __restrict__ tile, int c
 template <int PREC>
 __global__ void __launch_bounds__(kThreads, kFwdMinBlocks) k_fwd(const float4* __restrict__ rec, int64_t n_direct, int64_t n_kappa,
                                                   int64_t tiles_direct, int64_t tiles_total, int64_t tiles_per_chunk,
-                                                  QueryArgs a, int32_t* status) {
+                                                  QueryArgs a, int32_t* status, int64_t n_kappa_flat) {
     extern __shared__ __align__(128) char smem[];
     __shared__ TileRing<kStages> ring;
     char* buf = smem;
@@ -168,7 +169,9 @@ __global__ void __launch_bounds__(kThreads, kFwdMinBlocks) k_fwd(const float4* _
         const int cnt = (int)(seg - first < kTileRecs ? seg - first : kTileRecs);
 #pragma unroll
         for (int k = 0; k < kQueriesPerThread; ++k) qs[k].w = qs[k].s = 0.f;
-        if (kappa)
+        if (kappa && first + kTileRecs <= n_kappa_flat)   // every record of the tile has kappa_min = 0
+            pair_tile<true, PREC, true>(tile, cnt, qs);
+        else if (kappa)
             pair_tile<true, PREC>(tile, cnt, qs);
         else
             pair_tile<false, PREC>(tile, cnt, qs);
@@ -321,7 +324,7 @@ sdf_status launch_query(const Cloud& c, const float* d_x, int64_t q, float* d_ph
                                                                                             : k_fwd<SDF_F32>;
         kern<<<grid, kThreads, kStages * kTileBytes, st>>>(c.rec, c.n_direct, c.n_kappa, c.tiles_direct,
                                                           c.tiles_direct + c.tiles_kappa, p.tiles_per_chunk, a,
-                                                          c.status);
+                                                          c.status, c.n_kappa_flat);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess && tc) {
@@ -350,7 +353,8 @@ sdf_status launch_query(const Cloud& c, const float* d_x, int64_t q, float* d_ph
             ak.tile_base = c.tiles_direct;
             ak.part_base = nd;
             k_fwd<SDF_F32><<<dim3((unsigned)p.qblocks, (unsigned)nk), kThreads, kStages * kTileBytes, st>>>(
-                c.rec, c.n_direct, c.n_kappa, c.tiles_direct, c.tiles_direct + c.tiles_kappa, tpc_k, ak, c.status);
+                c.rec, c.n_direct, c.n_kappa, c.tiles_direct, c.tiles_direct + c.tiles_kappa, tpc_k, ak, c.status,
+                c.n_kappa_flat);
             e = cudaGetLastError();
         }
     }
@@ -484,7 +488,7 @@ extern "C" sdf_status sdf_query_noalloc(sdf_cloud cloud, const float* d_x, int64
     if (e == cudaSuccess) {
         k_fwd<SDF_F32><<<grid, kThreads, kStages * kTileBytes, st>>>(c.rec, c.n_direct, c.n_kappa, c.tiles_direct,
                                                            c.tiles_direct + c.tiles_kappa, p.tiles_per_chunk, a,
-                                                           c.status);
+                                                           c.status, c.n_kappa_flat);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess && p.split > 1) {

@@ -286,6 +286,18 @@ __device__ __forceinline__ float g_direct(float x, float y, float z, const float
 //   N' = -kappa_max (a'^2 + h^2) + 2 zeta a'
 //   g  = N' / (1 + sqrt(1 + (-kappa_max) N'))
 // which has no 1/k or 1/|kappa_max| and so no cancellation of large radii.
+// g_kappa for a record with kappa_min = 0 (k = r1.w = 0): m = <y, 2 zeta n*>,
+// s1 = 1 and a' = m / 2, which saves a square root and a reciprocal.
+__device__ __forceinline__ float g_kappa_flat(float x, float y, float z, const float4& r0, const float4& r1,
+                                              const float4& r2, const float4& r3) {
+    const float yx = x - r1.x, yy = y - r1.y, yz = z - r1.z;
+    const float h = fmaf(yx, r2.x, fmaf(yy, r2.y, yz * r2.z));
+    const float ap = 0.5f * fmaf(yx, r3.x, fmaf(yy, r3.y, yz * r3.z));
+    const float Np = fmaf(r2.w, fmaf(ap, ap, h * h), r0.w * ap);
+    const float s2 = sqrt_mufu(fmaxf(fmaf(r2.w, Np, 1.f), 0.f));
+    return Np * rcp_mufu(1.f + s2);
+}
+
 __device__ __forceinline__ float g_kappa(float x, float y, float z, const float4& r0, const float4& r1,
                                          const float4& r2, const float4& r3) {
     const float yx = x - r1.x, yy = y - r1.y, yz = z - r1.z;

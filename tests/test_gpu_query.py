@@ -69,6 +69,22 @@ def test_mixed_cloud_ragged(ptsdf, torch_mod, oracle_mod, q, split):
     assert np.abs(got - ref).max() <= TOL_REL * aabb_diag(p)
 
 
+@pytest.mark.parametrize("split", [0, 1, 5])
+def test_flat_kappa_tiles(ptsdf, torch_mod, oracle_mod, split):
+    """Noisy superquadric, N = 2,000: most kappa-form records have
+    kappa_min = 0 (whole tiles of them take the shorter formula), the rest
+    are curved, and the tile at the boundary mixes the two."""
+    p, n, a = synth.superquadric(2000, 5)
+    flat = sum(oracle_mod.fit_record(p[i], n[i], a[i])["kmin"] == 0.0 for i in range(len(p)))
+    assert flat > 64 and flat % 32 != 0
+    cl = ptsdf.Cloud(p, n, a)
+    assert cl.info()["n_kappa"] >= flat
+    x = f32(synth.uniform_queries(1537, 905, -1.3, 1.3))
+    got = run(cl, x, torch_mod, split_n=split)
+    ref = oracle_mod.Cloud(p, n, a).phi(x)
+    assert np.abs(got - ref).max() <= TOL_REL * aabb_diag(p)
+
+
 def test_split_factors_agree(ptsdf, torch_mod):
     """The merge of split chunks reproduces the unsplit sums (same shift)."""
     p, n, a = mixed_cloud(5)
