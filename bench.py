@@ -62,24 +62,40 @@ WORKLOAD = ("dense_grid: ring torus N=100000 (R=1, r=0.35, noise 0.005, 2deg vMF
 #    ceiling 128/13 = 9.8) and nearly ties the FP32-unit loop's issue
 #    ceiling (128/29 = 4.41).
 INSTR_PER_PAIR = 29
-TC_INSTR_PER_PAIR = 13
 THREAD_INSTR_PER_SM_CLK = 128
-NOMINAL_RATES = {"sqrt": 16.0, "rsqrt": 16.0, "ex2": 32.0, "fma": 128.0}
+NOMINAL_RATES = {"sqrt": 16.0, "rsqrt": 16.0, "ex2": 32.0, "fma": 128.0, "rcp": 16.0}
 
 
 def probe_rates(L):
     """Unit rates (results per SM per clock) measured by sdf_probe_rates, or
     the nominal ones if the probe fails."""
-    buf = (ctypes.c_double * 4)()
+    buf = (ctypes.c_double * 5)()
     if L.sdf_probe_rates(buf) != 0:
         return dict(NOMINAL_RATES, source="nominal (probe failed)")
-    return {"sqrt": buf[0], "rsqrt": buf[1], "ex2": buf[2], "fma": buf[3], "source": "measured (sdf_probe_rates)"}
+    return {"sqrt": buf[0], "rsqrt": buf[1], "ex2": buf[2], "fma": buf[3], "rcp": buf[4], "source": "measured (sdf_probe_rates)"}
 
 
 def pair_ceiling(rates, instr_per_pair):
     """pairs per SM clock: the lower of the MUFU and the issue ceilings."""
     mufu = 1.0 / (3.0 / rates["sqrt"] + 1.0 / rates["ex2"])
     issue = rates["fma"] / instr_per_pair
+    return min(mufu, issue), mufu, issue
+
+
+# Tensor-core loop, per pair by record form: special-function operations
+# (sqrt, rcp, ex2) and FMA-pipe instructions of the epilogue.
+TC_FORM_COST = {"direct": ((3, 0, 1), 13), "flat": ((2, 1, 1), 14), "curved": ((3, 2, 1), 20)}
+
+
+def tc_pair_ceiling(rates, counts):
+    """pairs per SM clock of the tensor-core loop over a cloud with `counts`
+    points of each record form (pairs weighted by form): the lower of the
+    MUFU and the issue ceilings."""
+    total = sum(counts.values())
+    mufu_clk = sum(c * (m[0] / rates["sqrt"] + m[1] / rates.get("rcp", rates["sqrt"]) + m[2] / rates["ex2"])
+                   for f, c in counts.items() for m in [TC_FORM_COST[f][0]])
+    issue_clk = sum(c * TC_FORM_COST[f][1] / rates["fma"] for f, c in counts.items())
+    mufu, issue = total / mufu_clk, total / issue_clk
     return min(mufu, issue), mufu, issue
 FALLBACK_MAX_SM_MHZ = 2032.0
 
@@ -628,24 +644,35 @@ def run_ours(args, rank, world, local):
     cs = clk.summary()
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     fmax = cs["sm_max_mhz"] or FALLBACK_MAX_SM_MHZ
-    # the dominant kernel: the tensor-core pair loop over the direct-form tiles
-    # (the kappa-form tiles, 2.6% of the points here, run on the FP32-unit loop)
-    n_direct = cloud.info()["n_direct"]
+    # the dominant kernel: the tensor-core pair loop, over every tile (direct,
+    # flat and curved curvature-form records; the curved ones, 2.6% of the
+    # points here, cost two reciprocals more per pair), unless the library
+    # routes the curved tiles to the FP32-unit loop (k_fwd then also runs)
+    info = cloud.info()
     rates = probe_rates(L)
     if "fwd_tc" in prof:
-        kname, kpairs = "k_fwd_tc", q * n_direct
-        per_sm_clk, mufu_c, issue_c = pair_ceiling(rates, TC_INSTR_PER_PAIR)
+        flat_tc = info["n_kappa_flat"]
+        curved = info["n_kappa"] - flat_tc
+        if prof.get("fwd", {}).get("launches", 0) > 0:
+            flat_tc, curved = 32 * (flat_tc // 32), 0
+        counts = {"direct": info["n_direct"], "flat": flat_tc, "curved": curved}
+        kname, kpairs = "k_fwd_tc", q * sum(counts.values())
+        per_sm_clk, mufu_c, issue_c = tc_pair_ceiling(rates, counts)
         kp = prof["fwd_tc"]
         traffic = committed_traffic()
+        basis = (f"{'MUFU' if mufu_c <= issue_c else 'issue'} ceiling: {sms} SMs x {fmax:.0f} MHz x "
+                 f"{per_sm_clk:.3f} pairs/clk/SM over the points by form {counts}; MUFU per pair "
+                 f"(sqrt, rcp, ex2) = {dict((f, c[0]) for f, c in TC_FORM_COST.items())} -> {mufu_c:.3f}, "
+                 f"issue fma/{dict((f, c[1]) for f, c in TC_FORM_COST.items())} -> {issue_c:.3f} "
+                 f"(unit rates {rates['source']})")
     else:
         kname, kpairs = "k_fwd", pairs_per_step
         per_sm_clk, mufu_c, issue_c = pair_ceiling(rates, INSTR_PER_PAIR)
         kp = prof.get("fwd", {"launches": 0, "ms": float("nan")})
         traffic = None
-    basis = (f"{'MUFU' if mufu_c <= issue_c else 'issue'} ceiling: {sms} SMs x {fmax:.0f} MHz x "
-             f"{per_sm_clk:.3f} pairs/clk/SM; MUFU 1/(3/sqrt + 1/ex2) = {mufu_c:.3f}, issue fma/"
-             f"{TC_INSTR_PER_PAIR if kname == 'k_fwd_tc' else INSTR_PER_PAIR} = {issue_c:.3f} "
-             f"(unit rates {rates['source']})")
+        basis = (f"{'MUFU' if mufu_c <= issue_c else 'issue'} ceiling: {sms} SMs x {fmax:.0f} MHz x "
+                 f"{per_sm_clk:.3f} pairs/clk/SM; MUFU 1/(3/sqrt + 1/ex2) = {mufu_c:.3f}, issue fma/"
+                 f"{INSTR_PER_PAIR} = {issue_c:.3f} (unit rates {rates['source']})")
     peak = sms * fmax * 1e6 * per_sm_clk / 1e9
     per_launch_s = kp["ms"] / max(kp["launches"], 1) / 1e3
     achieved = kpairs / per_launch_s / 1e9
@@ -654,7 +681,7 @@ def run_ours(args, rank, world, local):
         "warmup": args.warmup, "ms_per_step": elapsed_s / args.steps * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "N": N_POINTS, "Q": q, "C": 64, "lambda": "global",
-                   "precision": "fp32", "engine": "auto (tensor cores for direct-form tiles)",
+                   "precision": "fp32", "engine": "auto (tensor cores for every tile)",
                    "parallelism": f"replicas{world}" if world > 1 else "single",
                    "l2": "inputs larger than L2 (queries 201 MB, phi 67 MB); not flushed"},
         "queries_per_s": world * q * args.steps / elapsed_s,

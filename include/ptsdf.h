@@ -143,6 +143,14 @@ PTSDF_API sdf_status sdf_destroy(sdf_cloud cloud);
 PTSDF_API sdf_status sdf_cloud_info(sdf_cloud cloud, int64_t* n, float* aabb_diag, int64_t* n_direct,
                           int64_t* n_kappa);
 
+/* More cloud facts, for cost accounting: how many curvature-form points have
+ * kappa_min = 0 (planes, cylinders; they take the shorter formula of the
+ * form, Sec. 4.1), and how many 32-record tiles of the tensor-core loop
+ * take the FP32 record formula because a coefficient (e.g. kappa_max times
+ * the coordinate scale, above 2^15) leaves its f16 split's range.  Either
+ * pointer may be NULL; exact_tiles synchronises the device. */
+PTSDF_API sdf_status sdf_cloud_forms(sdf_cloud cloud, int64_t* n_kappa_flat, int64_t* exact_tiles);
+
 /* ---------------------------------------------------------------------------
  * sdf_query -- phi at Q query points (Algorithm 1, "Inference"; Eqs.
  *   BasicFormulaShifted, RelationshipBetweenLambdaAndRadius, SingleTorusSDF).
@@ -424,9 +432,9 @@ PTSDF_API sdf_status sdf_mesh_level_set(const float* d_phi, int32_t nx, int32_t 
 /* Measures, on the current device, the sustained throughput of the
  * operations that bound the pair loops, in results per SM per SM clock:
  * rates[0] sqrt.approx, rates[1] rsqrt.approx, rates[2] ex2.approx (the
- * special-function unit) and rates[3] FP32 FMA.  A measurement aid for
+ * special-function unit), rates[3] FP32 FMA and rates[4] rcp.approx.  A measurement aid for
  * roofline reporting (about 20 ms of kernels on every SM); it does not touch
- * any cloud.  rates must hold 4 doubles. */
+ * any cloud.  rates must hold 5 doubles. */
 PTSDF_API sdf_status sdf_probe_rates(double* rates);
 
 /* Self-test of the failure path (not part of the method): launches one

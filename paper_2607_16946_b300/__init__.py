@@ -83,7 +83,10 @@ class Cloud:
         n, nd, nk = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
         diag = ctypes.c_float()
         check(lib().sdf_cloud_info(self._h, ctypes.byref(n), ctypes.byref(diag), ctypes.byref(nd), ctypes.byref(nk)))
-        return {"n": n.value, "aabb_diag": diag.value, "n_direct": nd.value, "n_kappa": nk.value}
+        nf, ne = ctypes.c_int64(), ctypes.c_int64()
+        check(lib().sdf_cloud_forms(self._h, ctypes.byref(nf), ctypes.byref(ne)))
+        return {"n": n.value, "aabb_diag": diag.value, "n_direct": nd.value, "n_kappa": nk.value,
+                "n_kappa_flat": nf.value, "exact_tiles": ne.value}
 
     def query(self, x, out=None, stream=None, **opts):
         """phi at the rows of x (Q x 3, CUDA float32) -> Q float32 CUDA tensor."""

@@ -64,6 +64,7 @@ SIGNATURES = {
     "sdf_destroy": (ctypes.c_int, [_P]),
     "sdf_cloud_info": (ctypes.c_int, [_P, ctypes.POINTER(_I64), ctypes.POINTER(_F), ctypes.POINTER(_I64),
                                       ctypes.POINTER(_I64)]),
+    "sdf_cloud_forms": (ctypes.c_int, [_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64)]),
     "sdf_query": (ctypes.c_int, [_P, _P, _I64, _P, ctypes.POINTER(sdf_query_opts), _P]),
     "sdf_query_host": (ctypes.c_int, [_P, _P, _I64, _P, ctypes.POINTER(sdf_query_opts), _P]),
     "sdf_query_noalloc": (ctypes.c_int, [_P, _P, _I64, _P, ctypes.POINTER(sdf_query_opts), _P]),

@@ -306,6 +306,7 @@ void free_cloud(Cloud* c) {
     cudaFree(c->src_params);
     cudaFree(c->status);
     cudaFree(c->btiles);
+    cudaFree(c->btile_exact);
     cudaFree(c->mrec);
     cudaFree(c->mperm);
     delete c;
@@ -473,5 +474,24 @@ extern "C" sdf_status sdf_cloud_info(sdf_cloud cloud, int64_t* n, float* aabb_di
     if (aabb_diag) *aabb_diag = c->aabb_diag;
     if (n_direct) *n_direct = c->n_direct;
     if (n_kappa) *n_kappa = c->n_kappa;
+    return SDF_OK;
+}
+
+extern "C" sdf_status sdf_cloud_forms(sdf_cloud cloud, int64_t* n_kappa_flat, int64_t* exact_tiles) {
+    if (!cloud) return set_error(SDF_EINVAL, "sdf_cloud_forms: cloud is NULL");
+    const Cloud* c = reinterpret_cast<const Cloud*>(cloud);
+    if (n_kappa_flat) *n_kappa_flat = c->n_kappa_flat;
+    if (exact_tiles) {
+        const int64_t tiles = c->btile_exact ? c->tiles_direct + c->tiles_kappa : 0;
+        std::vector<int32_t> h((size_t)tiles);
+        if (tiles > 0) {
+            const cudaError_t e = cudaMemcpy(h.data(), c->btile_exact, (size_t)tiles * sizeof(int32_t),
+                                             cudaMemcpyDeviceToHost);
+            if (e != cudaSuccess) return cuda_error(e, "sdf_cloud_forms: read tile flags");
+        }
+        int64_t k = 0;
+        for (int32_t v : h) k += v != 0;
+        *exact_tiles = k;
+    }
     return SDF_OK;
 }

@@ -52,6 +52,9 @@ namespace ptsdf {
 #ifndef PTSDF_UNROLL
 #define PTSDF_UNROLL 2
 #endif
+#ifndef PTSDF_TC_KAPPA
+#define PTSDF_TC_KAPPA 1
+#endif
 #ifndef PTSDF_FWD_MINB
 #define PTSDF_FWD_MINB 4
 #endif
@@ -78,7 +81,9 @@ struct Cloud {
     float* src_normals = nullptr;    // the parameter gradient's chain through the fit
     float* src_params = nullptr;
     int32_t* status = nullptr;       // device status word (SDF_DEV_* bits)
-    uint8_t* btiles = nullptr;       // tiles_direct x 14 KB split-f16 operands of the tensor-core loop
+    uint8_t* btiles = nullptr;       // (tiles_direct + tiles_kappa) x 14 KB split-f16 operands of the
+                                     // tensor-core loop, both segments
+    int32_t* btile_exact = nullptr;  // per tile: 1 when a coefficient leaves the f16 split's range
     float4* mrec = nullptr;          // n x 4 float4 records in the prepass (Morton) order, r3.w = 1 for kappa
     int32_t* mperm = nullptr;        // input index of each Morton position
     float tc_scale = 1.f;            // their coordinate scale (a power of two >= the AABB diagonal)
@@ -144,9 +149,14 @@ struct TcQuery {
     int part_base = 0;
 };
 sdf_status build_btiles(Cloud& c, cudaStream_t st);
+// The tensor-core loop takes tiles [0, tc_tiles_end(c)): every tile, or
+// (PTSDF_TC_KAPPA=0) the direct tiles and the whole kappa_min = 0 tiles,
+// leaving the other kappa tiles to k_fwd.
+int64_t tc_tiles_end(const Cloud& c);
 int64_t tc_query_blocks(int64_t q);
-sdf_status launch_fwd_tc(const Cloud& c, const TcQuery& a, int64_t tiles_per_chunk, int nchunks, int direct_out,
-                         cudaStream_t st);
+// tiles [tiles_begin, tiles_end) of one segment (direct, or curvature form)
+sdf_status launch_fwd_tc(const Cloud& c, const TcQuery& a, int64_t tiles_begin, int64_t tiles_end,
+                         int64_t tiles_per_chunk, int nchunks, int direct_out, cudaStream_t st);
 
 // radius-limited evaluation (radius.cu): the fallback neighbour count of Sec. 4.2
 constexpr int kRadiusFallbackK = 32;

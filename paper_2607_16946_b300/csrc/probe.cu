@@ -1,6 +1,6 @@
 // Throughput probe of the operations that bound the pair loops: the
-// special-function unit's sqrt, rsqrt and exp2 (the approximate forms the
-// kernels use) and FP32 FMA.  Each thread runs independent dependent chains
+// special-function unit's sqrt, rsqrt, exp2 and reciprocal (the approximate
+// forms the kernels use) and FP32 FMA.  Each thread runs independent dependent chains
 // of one operation; every SM holds the same number of CTAs, which record
 // their SM and their clock64 cycle count, so the rates come out per SM and
 // per SM clock without relying on a nominal clock.
@@ -26,6 +26,7 @@ __device__ __forceinline__ float probe_op(float a) {
     if (OP == 0) return sqrt_mufu(a);                 // a -> 1
     if (OP == 1) return rsqrt_mufu(a);                // stays in (0.5, 2)
     if (OP == 2) return ex2_mufu(-a);                 // stays in (0.5, 1]
+    if (OP == 4) return rcp_mufu(a) + 0.5f;           // -> 1.28 (a plain rcp chain folds to a copy)
     return fmaf(a, 0.999f, 0.001f);                   // -> 1
 }
 
@@ -99,8 +100,8 @@ extern "C" sdf_status sdf_probe_rates(double* rates) {
     std::vector<long long> hc(blocks);
     std::vector<int> hs(blocks);
     using Kern = void (*)(float*, long long*, int*);
-    const Kern kernels[4] = {k_probe<0>, k_probe<1>, k_probe<2>, k_probe<3>};
-    for (int op = 0; op < 4 && e == cudaSuccess; ++op) {
+    const Kern kernels[5] = {k_probe<0>, k_probe<1>, k_probe<2>, k_probe<3>, k_probe<4>};
+    for (int op = 0; op < 5 && e == cudaSuccess; ++op) {
         for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {   // the first run warms up
             kernels[op]<<<blocks, kProbeThreads>>>(sink, cyc, smid);
             e = cudaGetLastError();

@@ -241,36 +241,50 @@ Plan make_plan(const Cloud& c, int64_t q, int split_override, int queries_per_ct
 }
 
 bool use_tensor_engine(const Cloud& c, const sdf_query_opts& o) {
-    return o.engine != SDF_ENGINE_ALU && o.precision == SDF_F32 && c.btiles != nullptr && c.tiles_direct > 0;
+    return o.engine != SDF_ENGINE_ALU && o.precision == SDF_F32 && c.btiles != nullptr && tc_tiles_end(c) > 0;
 }
+
+namespace {
+
+// Launch plan of the tensor-core engine: the direct tiles on k_fwd_tc<false>
+// in nd chunks, the curvature-form tiles [tiles_direct, tc_end) on
+// k_fwd_tc<true> in nk chunks, any others on k_fwd in na chunks; with more
+// than one chunk in all, each writes (W, S) partial rows in that order and
+// k_merge sums them in row order.
+struct TcPlan {
+    int64_t tc_end = 0, tpc_d = 0, tpc_k = 0, tpc_a = 0;
+    int nd = 0, nk = 0, na = 0;
+    int parts() const { return nd + nk + na; }
+};
+
+TcPlan tc_plan(const Cloud& c, int64_t q, int split_n, int64_t alu_qblocks) {
+    TcPlan t;
+    t.tc_end = tc_tiles_end(c);
+    const int64_t qb = tc_query_blocks(q), target = 2LL * c.num_sms;   // one CTA per SM, two waves
+    if (c.tiles_direct > 0) chunk_tiles(qb, c.tiles_direct, target, split_n, t.tpc_d, t.nd);
+    if (t.tc_end > c.tiles_direct) chunk_tiles(qb, t.tc_end - c.tiles_direct, target, split_n, t.tpc_k, t.nk);
+    const int64_t tiles = c.tiles_direct + c.tiles_kappa;
+    if (tiles > t.tc_end)
+        chunk_tiles(alu_qblocks, tiles - t.tc_end, 2LL * kFwdMinBlocks * c.num_sms, split_n, t.tpc_a, t.na);
+    return t;
+}
+
+}  // namespace
 
 int query_partials(const Cloud& c, int64_t q, const sdf_query_opts& o) {
     const Plan p = make_plan(c, q, o.split_n);
     if (!use_tensor_engine(c, o)) return p.split;
-    int64_t tpc = 0;
-    int nd = 0, nk = 0;
-    chunk_tiles(tc_query_blocks(q), c.tiles_direct, 2LL * c.num_sms, o.split_n, tpc, nd);
-    if (c.tiles_kappa > 0) chunk_tiles(p.qblocks, c.tiles_kappa, 2LL * kFwdMinBlocks * c.num_sms, o.split_n, tpc, nk);
-    return nd + nk;
+    return tc_plan(c, q, o.split_n, p.qblocks).parts();
 }
 
 sdf_status launch_query(const Cloud& c, const float* d_x, int64_t q, float* d_phi, const sdf_query_opts& o,
                         cudaStream_t st) {
     if (o.lambda_mode == SDF_LAMBDA_RADIUS) return launch_radius_query(c, d_x, q, d_phi, o, st);
     const Plan p = make_plan(c, q, o.split_n);
-    // Tensor-core engine: the direct-form tiles go to k_fwd_tc in nd chunks,
-    // the kappa-form tiles to k_fwd in nk chunks; both write (W, S) partials
-    // (rows 0..nd-1, then nd..nd+nk-1) that k_merge sums in row order.
+    // Tensor-core engine: see TcPlan
     const bool tc = use_tensor_engine(c, o);
-    int64_t tpc_d = 0, tpc_k = 0;
-    int nd = 0, nk = 0;
-    int nparts = p.split;
-    if (tc) {
-        chunk_tiles(tc_query_blocks(q), c.tiles_direct, 2LL * c.num_sms, o.split_n, tpc_d, nd);
-        if (c.tiles_kappa > 0)
-            chunk_tiles(p.qblocks, c.tiles_kappa, 2LL * kFwdMinBlocks * c.num_sms, o.split_n, tpc_k, nk);
-        nparts = nd + nk;
-    }
+    const TcPlan tp = tc ? tc_plan(c, q, o.split_n, p.qblocks) : TcPlan();
+    const int nparts = tc ? tp.parts() : p.split;
     QueryArgs a;
     a.x = d_x;
     a.q = q;
@@ -345,15 +359,18 @@ sdf_status launch_query(const Cloud& c, const float* d_x, int64_t q, float* d_ph
             tq.lam = a.lam;
             tq.offset = a.offset;
             tq.part_base = 0;
-            s = launch_fwd_tc(c, tq, tpc_d, nd, nparts == 1, st);
+            if (tp.nd > 0) s = launch_fwd_tc(c, tq, 0, c.tiles_direct, tp.tpc_d, tp.nd, nparts == 1, st);
+            tq.part_base = tp.nd;
+            if (s == SDF_OK && tp.nk > 0)
+                s = launch_fwd_tc(c, tq, c.tiles_direct, tp.tc_end, tp.tpc_k, tp.nk, nparts == 1, st);
         }
-        if (s == SDF_OK && nk > 0) {
+        if (s == SDF_OK && tp.na > 0) {
             ProfRange pr(SDF_K_FWD, st);
             QueryArgs ak = a;
-            ak.tile_base = c.tiles_direct;
-            ak.part_base = nd;
-            k_fwd<SDF_F32><<<dim3((unsigned)p.qblocks, (unsigned)nk), kThreads, kStages * kTileBytes, st>>>(
-                c.rec, c.n_direct, c.n_kappa, c.tiles_direct, c.tiles_direct + c.tiles_kappa, tpc_k, ak, c.status,
+            ak.tile_base = tp.tc_end;
+            ak.part_base = tp.nd + tp.nk;
+            k_fwd<SDF_F32><<<dim3((unsigned)p.qblocks, (unsigned)tp.na), kThreads, kStages * kTileBytes, st>>>(
+                c.rec, c.n_direct, c.n_kappa, c.tiles_direct, c.tiles_direct + c.tiles_kappa, tp.tpc_a, ak, c.status,
                 c.n_kappa_flat);
             e = cudaGetLastError();
         }

@@ -1,20 +1,29 @@
-// Tensor-core pair loop for direct-form tori (FP32 result).
+// Tensor-core pair loop (FP32 result) for both torus record forms.
 //
 // Every per-pair quantity of the torus SDF (Eq. SingleTorusSDF) and of the
 // weights (Eq. BasicFormulaShifted) that depends on both the query and the
 // point is an inner product of a per-query and a per-point feature vector.
 // In coordinates x'' = (x - centre) / s (centre of the cloud's bounding box,
-// s a power of two at least its diagonal), with f(x) = (x'', |x''|^2, 1) and
-// (u, e1, e2) an orthonormal frame of the torus axis u:
+// s a power of two at least its diagonal), with f(x) = (x'', |x''|^2, 1):
+//
+// direct form, (u, e1, e2) an orthonormal frame of the torus axis u:
 //   d^2 = |x - p|^2     = f . (-2 p'', 1, |p''|^2)
 //   h   = <x - c, u>    = f . (u, 0, -<c'', u>)
 //   a   = <x - c, e1>   = f . (e1, 0, -<c'', e1>)
 //   b   = <x - c, e2>   = f . (e2, 0, -<c'', e2>)
 // so that rho^2 = a^2 + b^2 is the squared distance to the axis without the
-// cancellation of |x - c|^2 - h^2 near the axis.  The per-point constants R,
-// -sT r and sT come out through the constant feature.  One 128 x 224 x 32
-// product on the tensor cores (two tcgen05 MMAs of K = 16) gives all seven
-// for 128 queries and a 32-point tile.
+// cancellation of |x - c|^2 - h^2 near the axis; the constants R, -sT r and
+// sT come out through the constant feature.
+//
+// curvature form (Sec. 4.1, the form without 1/kappa), y = x - q:
+//   d^2, h = <y, u>, |y|^2 = f . (-2 q'', 1, |q''|^2),
+//   m0 = <y, 2 zeta n*> = f . (2 zeta n*, 0, -<q'', 2 zeta n*>)
+// and the constants |kappa_min| s, -kappa_max s, 2 zeta.
+//
+// Seven quantities either way: one 128 x 224 x 32 product on the tensor
+// cores (two tcgen05 MMAs of K = 16) gives them for 128 queries and a
+// 32-point tile.  Tiles never mix the forms (the record segments are padded
+// to whole tiles), so the epilogue picks the formula per tile.
 //
 // Precision: every feature and coefficient is split into three f16 parts
 // (v = v_hi + v_mid + v_lo for FP32 inputs), and K holds the six cross
@@ -24,12 +33,19 @@
 // s or s^2); with the FP32 rounding of the accumulation the quantities carry
 // absolute errors of order 1e-7 s^2 (d^2) and 1e-7 s |x - c| (h, a, b).
 // Queries farther than 32 s from the centre, where |x''|^2 would leave the
-// range these splits are sized for, take the direct formula from the FP32
-// record for every pair.
+// range these splits are sized for, take the formula of their tile's form
+// from the FP32 record for every pair.
 //
-// The epilogue finishes each pair on the FP32 units: rho = sqrt(a^2 + b^2),
-// D = sqrt((rho - R)^2 + h^2), g = sT D - sT r, w = exp2(-L (d - d_min)),
-// W += w, S += w g (four MUFU and nine FMA-pipe operations), with the sums
+// A tile whose constants leave that range (|value| > 2^15, e.g. a tube radius
+// below s / 2^15) is flagged at build time and every pair of it takes the
+// FP32 record formula.
+//
+// The epilogue finishes each pair on the FP32 units.  Direct form:
+// rho = sqrt(a^2 + b^2), D = sqrt((rho - R)^2 + h^2), g = sT D - sT r (three
+// square roots with d).  Curvature form: the two half-angle steps of the
+// record formula (kappa_min = 0 tiles skip the first, which is then exact
+// without a root), again three roots and two reciprocals with d, or two and
+// one.  Then w = exp2(-L (d - d_min)), W += w, S += w g, with the sums
 // blocked per tile as in the ALU kernel.
 //
 // Warps: 0 producer (bulk copies of B tiles into an 8-stage ring), 1 MMA
@@ -57,7 +73,8 @@ namespace {
 static_assert(kTileRecs == 32, "the tensor-core path packs 32-point tiles");
 
 constexpr int kTcM = 128;                             // queries per CTA (MMA M)
-constexpr int kTcQuant = 7;                           // d^2, h, a, b, R, -sT r, sT
+constexpr int kTcQuant = 7;                           // direct: d^2, h, a, b, R, -sT r, sT
+                                                      // kappa: d^2, h, |y|^2, m0, |kmin| s, -kmax s, 2 zeta
 constexpr int kTcN = kTcQuant * kTileRecs;            // 224 (MMA N)
 constexpr uint32_t kTcSubA = kTcM * 32;               // one K = 16 sub-tile of A (4 KB)
 constexpr uint32_t kTcSubB = kTcN * 32;               // one K = 16 sub-tile of B (7 KB)
@@ -74,6 +91,8 @@ constexpr int kTcThreads = (2 + kEpiWarps) * 32;
 constexpr uint32_t kTmemCols = 512;                   // two accumulators of kTcN columns
 constexpr uint32_t kBufCols = 256;
 constexpr float kFarSq = 1024.f;                      // |x''|^2 beyond which a query is exact-only
+constexpr double kMaxCoef = 32768.0;                  // largest B coefficient the f16 split takes
+enum TileForm { kFormDirect = 0, kFormKappa = 1, kFormFlat = 2 };
 constexpr uint32_t kTcIdesc = tc::idesc_f16_f32(kTcM, kTcN);
 // dynamic shared memory: A, the ring, the group partial sums; padded so that
 // two CTAs never share an SM (each holds all 512 TMEM columns)
@@ -108,16 +127,22 @@ __host__ __device__ inline uint32_t slot_offset(int row, int m, uint32_t sub_byt
     return (uint32_t)(m / 16) * sub_bytes + tc::canon_offset(row, m % 16);
 }
 
-__global__ void k_build_btiles(const float4* __restrict__ rec, int64_t n_direct, int64_t tiles_direct, double cx,
-                               double cy, double cz, double inv_s, uint8_t* __restrict__ bt) {
+// One thread per record slot of every tile (both segments).  Padding slots
+// get all-zero rows (their pairs are masked in the epilogue).  A tile with a
+// coefficient outside the split's range gets its exact flag set.
+__global__ void k_build_btiles(const float4* __restrict__ rec, int64_t n_direct, int64_t tiles_direct,
+                               int64_t n_kappa, int64_t tiles_total, double cx, double cy, double cz, double inv_s,
+                               uint8_t* __restrict__ bt, int32_t* __restrict__ exact) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= tiles_direct * kTileRecs) return;
+    if (i >= tiles_total * kTileRecs) return;
     const int64_t t = i / kTileRecs;
     const int j = (int)(i % kTileRecs);
+    const bool kappa = t >= tiles_direct;
+    const bool valid = kappa ? i - tiles_direct * kTileRecs < n_kappa : i < n_direct;
     double b[kTcQuant][5];
     for (int k = 0; k < kTcQuant; ++k)
         for (int m = 0; m < 5; ++m) b[k][m] = 0.0;
-    if (i < n_direct) {
+    if (valid && !kappa) {
         const float4 r0 = rec[4 * i], r1 = rec[4 * i + 1], r2 = rec[4 * i + 2];
         const double p[3] = {((double)r0.x - cx) * inv_s, ((double)r0.y - cy) * inv_s, ((double)r0.z - cz) * inv_s};
         const double c[3] = {((double)r1.x - cx) * inv_s, ((double)r1.y - cy) * inv_s, ((double)r1.z - cz) * inv_s};
@@ -146,6 +171,36 @@ __global__ void k_build_btiles(const float4* __restrict__ rec, int64_t n_direct,
         b[4][4] = (double)r1.w * inv_s;   // R
         b[5][4] = (double)r2.w * inv_s;   // -sT r
         b[6][4] = r0.w;                   // sT
+    } else if (valid) {
+        // {p, 2 zeta}{q, |kmin|}{u, -kmax}{2 zeta n*, 0}
+        const float4 r0 = rec[4 * i], r1 = rec[4 * i + 1], r2 = rec[4 * i + 2], r3 = rec[4 * i + 3];
+        const double p[3] = {((double)r0.x - cx) * inv_s, ((double)r0.y - cy) * inv_s, ((double)r0.z - cz) * inv_s};
+        const double q[3] = {((double)r1.x - cx) * inv_s, ((double)r1.y - cy) * inv_s, ((double)r1.z - cz) * inv_s};
+        const double u[3] = {r2.x, r2.y, r2.z};
+        const double zn[3] = {r3.x, r3.y, r3.z};
+        for (int m = 0; m < 3; ++m) {
+            b[0][m] = -2.0 * p[m];
+            b[1][m] = u[m];
+            b[2][m] = -2.0 * q[m];
+            b[3][m] = zn[m];
+        }
+        b[0][3] = 1.0;
+        b[0][4] = p[0] * p[0] + p[1] * p[1] + p[2] * p[2];
+        b[1][4] = -(q[0] * u[0] + q[1] * u[1] + q[2] * u[2]);
+        b[2][3] = 1.0;
+        b[2][4] = q[0] * q[0] + q[1] * q[1] + q[2] * q[2];
+        b[3][4] = -(q[0] * zn[0] + q[1] * zn[1] + q[2] * zn[2]);
+        b[4][4] = (double)r1.w / inv_s;   // |kappa_min| in units of 1/s
+        b[5][4] = (double)r2.w / inv_s;   // -kappa_max
+        b[6][4] = r0.w;                   // 2 zeta
+    }
+    bool in_range = true;
+    for (int k = 0; k < kTcQuant; ++k)
+        for (int m = 0; m < 5; ++m) in_range = in_range && fabs(b[k][m]) <= kMaxCoef;
+    if (!in_range) {
+        atomicOr(exact + t, 1);
+        for (int k = 0; k < kTcQuant; ++k)
+            for (int m = 0; m < 5; ++m) b[k][m] = 0.0;
     }
     uint8_t* tile = bt + (size_t)t * kBTileBytes;
     for (int k = 0; k < kTcQuant; ++k) {
@@ -169,54 +224,89 @@ __global__ void k_build_btiles(const float4* __restrict__ rec, int64_t n_direct,
 struct TcArgs {
     TcQuery a;
     const uint8_t* btiles;
+    const int32_t* tile_exact;   // per tile: 1 when its pairs must take the record formula
     const float4* rec;
-    int64_t n_direct, tiles_direct, tiles_per_chunk;
+    int64_t tiles_begin, tiles_end, tiles_per_chunk;   // tiles [begin, end) in chunks
+    // tile classes (tiles < 2^26): [0, tiles_direct) direct, of which the
+    // first direct_full are full; then kappa_min = 0 tiles up to flat_end and
+    // the others; kappa_full full kappa-form tiles; *_rem points in the
+    // partial last tile of each segment
+    int32_t tiles_direct, direct_full, flat_end, kappa_full, direct_rem, kappa_rem;
     float s, inv_s;          // coordinate scale of the B tiles (a power of two) and its inverse
     int direct_out;          // 1: write phi; 0: write (W, S) at partial row part_base + chunk
 };
 
 __device__ __forceinline__ float sqrt_abs_mufu(float x) { return sqrt_mufu(fabsf(x)); }
 
-// One epilogue warp's share of a tile: 8 pairs per lane; v[k * 8 + i] is
-// quantity k of point i.  MASK: only the first `valid` points exist (the
-// last, partial tile).  FAR: some lane of the warp is a far query, whose
-// pairs are recomputed from the FP32 record by the direct formula.
-template <bool MASK, bool FAR>
-__device__ __forceinline__ void tile_pairs(const float (&v)[kVals], int valid, float Ls, float A0, bool exact_lane,
-                                           float x, float y, float z, float inv_s, const float4* __restrict__ rec,
-                                           int64_t slot0, float& W, float& S) {
-    float tw = 0.f, ts = 0.f;
-    if (FAR && exact_lane) {
-        // the direct formula from the FP32 record, rescaled to units of s
-#pragma unroll 1
-        for (int i = 0; i < kPtsPerWarp; ++i) {
-            if (!MASK || i < valid) {
-                const float4 r0 = __ldg(rec + 4 * (slot0 + i));
-                const float4 r1 = __ldg(rec + 4 * (slot0 + i) + 1);
-                const float4 r2 = __ldg(rec + 4 * (slot0 + i) + 2);
-                const float g = g_direct(x, y, z, r1, r2, r0.w) * inv_s;
-                const float dx = x - r0.x, dy = y - r0.y, dz = z - r0.z;
-                const float d = sqrt_mufu(fmaf(dx, dx, fmaf(dy, dy, dz * dz))) * inv_s;
-                const float w = ex2_mufu(fmaf(-Ls, d, A0));
-                tw += w;
-                ts = fmaf(w, g, ts);
-            }
-        }
+// torus distance of one pair from the seven accumulator quantities q0..q6
+// (units of s), by the tile's form
+template <int FORM>
+__device__ __forceinline__ float g_from_quantities(float q1, float q2, float q3, float q4, float q5, float q6) {
+    if (FORM == kFormDirect) {
+        // q1 h, q2 a, q3 b, q4 R, q5 -sT r, q6 sT
+        const float rho = sqrt_mufu(fmaf(q2, q2, q3 * q3));
+        const float e = rho - q4;
+        return fmaf(q6, sqrt_mufu(fmaf(e, e, q1 * q1)), q5);
     } else {
-#pragma unroll
-        for (int i = 0; i < kPtsPerWarp; ++i) {
-            if (!MASK || i < valid) {
-                const float h = v[8 + i], pa = v[16 + i], pb = v[24 + i];
-                const float rho = sqrt_mufu(fmaf(pa, pa, pb * pb));
-                const float e = rho - v[32 + i];
-                const float g = fmaf(v[48 + i], sqrt_mufu(fmaf(e, e, h * h)), v[40 + i]);
-                // |d^2|: the products may round a zero distance slightly negative
-                const float d = sqrt_abs_mufu(v[i]);
-                const float w = ex2_mufu(fmaf(-Ls, d, A0));
-                tw += w;
-                ts = fmaf(w, g, ts);
-            }
+        // q1 h, q2 |y|^2, q3 m0, q4 |kmin|, q5 -kmax, q6 2 zeta
+        const float hh = q1 * q1;
+        float ap;
+        if (FORM == kFormFlat) {
+            ap = 0.5f * q3;
+        } else {
+            const float m = fmaf(q4, q2 - hh, q3);
+            const float s1 = sqrt_mufu(fmaxf(fmaf(q4, m, 1.f), 0.f));
+            ap = m * rcp_mufu(1.f + s1);
         }
+        const float Np = fmaf(q5, fmaf(ap, ap, hh), q6 * ap);
+        const float s2 = sqrt_mufu(fmaxf(fmaf(q5, Np, 1.f), 0.f));
+        return Np * rcp_mufu(1.f + s2);
+    }
+}
+
+// One epilogue warp's share of a full tile from the accumulator: 8 pairs per
+// lane; v[k * 8 + i] is quantity k of point i.
+template <int FORM>
+__device__ __forceinline__ void tile_pairs(const float (&v)[kVals], float Ls, float A0, float& W, float& S) {
+    float tw = 0.f, ts = 0.f;
+#pragma unroll
+    for (int i = 0; i < kPtsPerWarp; ++i) {
+        const float g = g_from_quantities<FORM>(v[8 + i], v[16 + i], v[24 + i], v[32 + i], v[40 + i], v[48 + i]);
+        // |d^2|: the products may round a zero distance slightly negative
+        const float d = sqrt_abs_mufu(v[i]);
+        const float w = ex2_mufu(fmaf(-Ls, d, A0));
+        tw += w;
+        ts = fmaf(w, g, ts);
+    }
+    W += tw;
+    S += ts;
+}
+
+// The same share from the FP32 records (the formula of the tile's form, in
+// world units, rescaled to units of s): for far queries, for flagged tiles
+// and for the partial last tile of a segment (only `valid` points exist).
+template <int FORM>
+__device__ __forceinline__ void record_pairs(int valid, float x, float y, float z, float inv_s,
+                                             const float4* __restrict__ rec, int64_t slot0, float Ls, float A0,
+                                             float& W, float& S) {
+    float tw = 0.f, ts = 0.f;
+#pragma unroll 1
+    for (int i = 0; i < valid; ++i) {
+        const float4* r = rec + 4 * (slot0 + i);
+        const float4 r0 = __ldg(r), r1 = __ldg(r + 1), r2 = __ldg(r + 2);
+        float g;
+        if (FORM == kFormDirect) {
+            g = g_direct(x, y, z, r1, r2, r0.w);
+        } else {
+            const float4 r3 = __ldg(r + 3);
+            g = FORM == kFormFlat ? g_kappa_flat(x, y, z, r0, r1, r2, r3) : g_kappa(x, y, z, r0, r1, r2, r3);
+        }
+        g *= inv_s;
+        const float dx = x - r0.x, dy = y - r0.y, dz = z - r0.z;
+        const float d = sqrt_mufu(fmaf(dx, dx, fmaf(dy, dy, dz * dz))) * inv_s;
+        const float w = ex2_mufu(fmaf(-Ls, d, A0));
+        tw += w;
+        ts = fmaf(w, g, ts);
     }
     W += tw;
     S += ts;
@@ -224,6 +314,10 @@ __device__ __forceinline__ void tile_pairs(const float (&v)[kVals], int valid, f
 
 // 18 warps: five share one SM sub-partition's 16K registers, so at most 96
 // registers per thread (allocated in multiples of 8)
+// KAPPA: the launch covers curvature-form tiles (all three formulas, flagged
+// tiles); otherwise direct-form tiles only, which are never flagged (their
+// coefficients are bounded by the 8-diagonal radius rule).
+template <bool KAPPA>
 __global__ void __maxnreg__(96) k_fwd_tc(TcArgs ta, int32_t* status) {
     extern __shared__ __align__(1024) uint8_t smem[];
     uint8_t* sA = smem;                                                         // 2 sub-tiles
@@ -235,8 +329,8 @@ __global__ void __maxnreg__(96) k_fwd_tc(TcArgs ta, int32_t* status) {
     const TcQuery& a = ta.a;
     const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
     const int chunk = blockIdx.y;
-    const int64_t t0 = (int64_t)chunk * ta.tiles_per_chunk;
-    const int64_t t1 = t0 + ta.tiles_per_chunk < ta.tiles_direct ? t0 + ta.tiles_per_chunk : ta.tiles_direct;
+    const int64_t t0 = ta.tiles_begin + (int64_t)chunk * ta.tiles_per_chunk;
+    const int64_t t1 = t0 + ta.tiles_per_chunk < ta.tiles_end ? t0 + ta.tiles_per_chunk : ta.tiles_end;
     const int64_t nt = t1 > t0 ? t1 - t0 : 0;
 
     if (tid == 0) {
@@ -363,17 +457,24 @@ __global__ void __maxnreg__(96) k_fwd_tc(TcArgs ta, int32_t* status) {
         // ---- epilogue ----
         float W = 0.f, S = 0.f;
         const uint32_t lane_addr = tbase + ((uint32_t)(quad * 32) << 16);
-        const bool warp_far = __any_sync(0xffffffffu, exact_lane);
         const int ntiles = (int)nt;
-        // only the last tile of the direct segment can be partial
-        const bool last_partial = t1 == ta.tiles_direct && (ta.n_direct % kTileRecs) != 0;
         const int b = eset;   // this set's accumulator
+        const int32_t* flags = ta.tile_exact + t0;
+        // the next tile's exact flag is fetched one tile ahead
+        int32_t flag_next = KAPPA && eset < ntiles ? __ldg(flags + eset) : 0;
         for (int t = eset; t < ntiles; t += kEpiSets) {
+            const bool flagged = KAPPA && flag_next != 0;
+            if (KAPPA && t + kEpiSets < ntiles) flag_next = __ldg(flags + t + kEpiSets);
             // warp-uniform: the TMEM loads below are .sync.aligned
             const bool ok = mbar_wait_bounded(&tfull[b], (uint32_t)(t >> 1) & 1u, &abort_flag, status);
             if (!__all_sync(0xffffffffu, ok)) break;
             tc::fence_after_sync();
-            const bool partial = last_partial && t == ntiles - 1;
+            const int gt = (int)t0 + t;
+            const int rel = KAPPA ? gt - ta.tiles_direct : gt;   // tile within its segment
+            const bool partial = rel >= (KAPPA ? ta.kappa_full : ta.direct_full);
+            const int form = !KAPPA ? kFormDirect : (gt < ta.flat_end ? kFormFlat : kFormKappa);
+            // pairs from the records: far lanes, flagged and partial tiles
+            const bool lane_rec = exact_lane || flagged || partial;
 #pragma unroll 1
             for (int gb = 0; gb < kGroupsPerWarp; ++gb) {
                 const int cg = half * kGroupsPerWarp + gb;   // column group: 8 points x 7 quantities
@@ -389,22 +490,26 @@ __global__ void __maxnreg__(96) k_fwd_tc(TcArgs ta, int32_t* status) {
                     __syncwarp();
                     if (lane == 0) mbar_arrive(&tempty[b]);
                 }
-                const int64_t slot0 = (t0 + t) * kTileRecs + cg * kPtsPerWarp;
-                if (partial) {
-                    const int64_t left = ta.n_direct - slot0;
-                    const int valid = (int)(left < 0 ? 0 : left);
-                    if (warp_far)
-                        tile_pairs<true, true>(v, valid, Ls, A0, exact_lane, x, y, z, ta.inv_s, ta.rec, slot0, W, S);
+                if (!lane_rec) {
+                    if (form == kFormDirect)
+                        tile_pairs<kFormDirect>(v, Ls, A0, W, S);
+                    else if (form == kFormFlat)
+                        tile_pairs<kFormFlat>(v, Ls, A0, W, S);
                     else
-                        tile_pairs<true, false>(v, valid, Ls, A0, exact_lane, x, y, z, ta.inv_s, ta.rec, slot0, W,
-                                                S);
+                        tile_pairs<kFormKappa>(v, Ls, A0, W, S);
                 } else {
-                    if (warp_far)
-                        tile_pairs<false, true>(v, kPtsPerWarp, Ls, A0, exact_lane, x, y, z, ta.inv_s, ta.rec, slot0,
-                                                W, S);
+                    int valid = kPtsPerWarp;
+                    if (partial) {
+                        const int left = (KAPPA ? ta.kappa_rem : ta.direct_rem) - cg * kPtsPerWarp;
+                        valid = left < 0 ? 0 : left > kPtsPerWarp ? kPtsPerWarp : left;
+                    }
+                    const int64_t slot0 = (int64_t)gt * kTileRecs + cg * kPtsPerWarp;
+                    if (form == kFormDirect)
+                        record_pairs<kFormDirect>(valid, x, y, z, ta.inv_s, ta.rec, slot0, Ls, A0, W, S);
+                    else if (form == kFormFlat)
+                        record_pairs<kFormFlat>(valid, x, y, z, ta.inv_s, ta.rec, slot0, Ls, A0, W, S);
                     else
-                        tile_pairs<false, false>(v, kPtsPerWarp, Ls, A0, exact_lane, x, y, z, ta.inv_s, ta.rec,
-                                                 slot0, W, S);
+                        record_pairs<kFormKappa>(valid, x, y, z, ta.inv_s, ta.rec, slot0, Ls, A0, W, S);
                 }
             }
         }
@@ -444,48 +549,74 @@ float tc_scale_for(float aabb_diag) {
 
 sdf_status build_btiles(Cloud& c, cudaStream_t st) {
     c.tc_scale = tc_scale_for(c.aabb_diag);
-    if (c.tiles_direct == 0) return SDF_OK;
-    cudaError_t e = cudaMalloc(&c.btiles, (size_t)c.tiles_direct * kBTileBytes);
+    const int64_t tiles = c.tiles_direct + c.tiles_kappa;
+    if (tiles == 0) return SDF_OK;
+    cudaError_t e = cudaMalloc(&c.btiles, (size_t)tiles * kBTileBytes);
+    if (e == cudaSuccess) e = cudaMalloc(&c.btile_exact, (size_t)tiles * sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMemsetAsync(c.btile_exact, 0, (size_t)tiles * sizeof(int32_t), st);
     if (e != cudaSuccess) {
+        cudaFree(c.btiles);
+        cudaFree(c.btile_exact);
         c.btiles = nullptr;
+        c.btile_exact = nullptr;
         return e == cudaErrorMemoryAllocation ? set_error(SDF_ENOMEM, "sdf_build: tensor-core tiles")
                                               : cuda_error(e, "sdf_build: tensor-core tiles");
     }
-    const int64_t slots = c.tiles_direct * kTileRecs;
+    const int64_t slots = tiles * kTileRecs;
     k_build_btiles<<<(unsigned)((slots + 127) / 128), 128, 0, st>>>(
-        c.rec, c.n_direct, c.tiles_direct, 0.5 * ((double)c.aabb[0] + c.aabb[3]),
+        c.rec, c.n_direct, c.tiles_direct, c.n_kappa, tiles, 0.5 * ((double)c.aabb[0] + c.aabb[3]),
         0.5 * ((double)c.aabb[1] + c.aabb[4]), 0.5 * ((double)c.aabb[2] + c.aabb[5]), 1.0 / (double)c.tc_scale,
-        c.btiles);
+        c.btiles, c.btile_exact);
     e = cudaGetLastError();
     return e == cudaSuccess ? SDF_OK : cuda_error(e, "sdf_build: k_build_btiles launch");
 }
 
+int64_t tc_tiles_end(const Cloud& c) {
+    if (PTSDF_TC_KAPPA) return c.tiles_direct + c.tiles_kappa;
+    return c.tiles_direct + c.n_kappa_flat / kTileRecs;
+}
+
 int64_t tc_query_blocks(int64_t q) { return (q + kTcM - 1) / kTcM; }
 
-sdf_status launch_fwd_tc(const Cloud& c, const TcQuery& a, int64_t tiles_per_chunk, int nchunks, int direct_out,
-                         cudaStream_t st) {
+sdf_status launch_fwd_tc(const Cloud& c, const TcQuery& a, int64_t tiles_begin, int64_t tiles_end,
+                         int64_t tiles_per_chunk, int nchunks, int direct_out, cudaStream_t st) {
+    const bool kappa = tiles_begin >= c.tiles_direct;
+    if (tiles_begin >= tiles_end || (!kappa && tiles_end > c.tiles_direct))
+        return set_error(SDF_EINVAL, "sdf_query: tensor-core tile range straddles the record segments");
     static bool attr_done[64] = {};
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return cuda_error(e, "sdf_query: cudaGetDevice");
     if (dev < 0 || dev >= 64) return set_error(SDF_EINVAL, "sdf_query: device id out of range");
     if (!attr_done[dev]) {
-        e = cudaFuncSetAttribute(k_fwd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmemBytes);
+        e = cudaFuncSetAttribute(k_fwd_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmemBytes);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_fwd_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmemBytes);
         if (e != cudaSuccess) return cuda_error(e, "sdf_query: k_fwd_tc shared-memory attribute");
         attr_done[dev] = true;
     }
     TcArgs ta;
     ta.a = a;
     ta.btiles = c.btiles;
+    ta.tile_exact = c.btile_exact;
     ta.rec = c.rec;
-    ta.n_direct = c.n_direct;
-    ta.tiles_direct = c.tiles_direct;
+    ta.tiles_begin = tiles_begin;
+    ta.tiles_end = tiles_end;
+    ta.tiles_direct = (int32_t)c.tiles_direct;
+    ta.direct_full = (int32_t)(c.n_direct / kTileRecs);
+    ta.flat_end = (int32_t)(c.tiles_direct + c.n_kappa_flat / kTileRecs);
+    ta.kappa_full = (int32_t)(c.n_kappa / kTileRecs);
+    ta.direct_rem = (int32_t)(c.n_direct % kTileRecs);
+    ta.kappa_rem = (int32_t)(c.n_kappa % kTileRecs);
     ta.tiles_per_chunk = tiles_per_chunk;
     ta.s = c.tc_scale;
     ta.inv_s = 1.f / c.tc_scale;
     ta.direct_out = direct_out;
     const dim3 grid((unsigned)tc_query_blocks(a.q), (unsigned)nchunks);
-    k_fwd_tc<<<grid, kTcThreads, kTcSmemBytes, st>>>(ta, c.status);
+    if (kappa)
+        k_fwd_tc<true><<<grid, kTcThreads, kTcSmemBytes, st>>>(ta, c.status);
+    else
+        k_fwd_tc<false><<<grid, kTcThreads, kTcSmemBytes, st>>>(ta, c.status);
     e = cudaGetLastError();
     return e == cudaSuccess ? SDF_OK : cuda_error(e, "sdf_query: k_fwd_tc launch");
 }

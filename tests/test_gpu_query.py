@@ -74,11 +74,11 @@ def test_flat_kappa_tiles(ptsdf, torch_mod, oracle_mod, split):
     """Noisy superquadric, N = 2,000: most kappa-form records have
     kappa_min = 0 (whole tiles of them take the shorter formula), the rest
     are curved, and the tile at the boundary mixes the two."""
-    p, n, a = synth.superquadric(2000, 5)
-    flat = sum(oracle_mod.fit_record(p[i], n[i], a[i])["kmin"] == 0.0 for i in range(len(p)))
-    assert flat > 64 and flat % 32 != 0
+    p, n, a = f32(*synth.superquadric(2000, 5))
     cl = ptsdf.Cloud(p, n, a)
-    assert cl.info()["n_kappa"] >= flat
+    info = cl.info()
+    flat = info["n_kappa_flat"]
+    assert 64 < flat < info["n_kappa"] and flat % 32 != 0
     x = f32(synth.uniform_queries(1537, 905, -1.3, 1.3))
     got = run(cl, x, torch_mod, split_n=split)
     ref = oracle_mod.Cloud(p, n, a).phi(x)

@@ -3,10 +3,12 @@ the FP64 oracle, element by element, and against the FP32-unit loop.
 
 Tolerance: |phi_gpu - phi_oracle| <= 1e-4 x AABB diagonal (the FP32 bar).
 Cases: direct-only clouds over several 32-point tiles and 128-query blocks
-with ragged tails; mixed clouds (kappa tiles on the FP32 units, partials
-merged); explicit split factors; queries on and next to the torus axis (the
-cancellation fallback); queries far outside the cloud (the exact-only lanes);
-FIXED lambda and offsets; the dense-grid cloud on sampled nodes.
+with ragged tails; mixed clouds (direct, flat and curved kappa-form tiles,
+each segment ending in a partial tile); explicit split factors; queries on
+and next to the torus axis; queries far outside the cloud (the exact-only
+lanes) for both forms; tiles flagged exact because a curvature leaves the
+f16 split's range; FIXED lambda and offsets; the dense-grid cloud on
+sampled nodes.
 """
 import numpy as np
 import pytest
@@ -84,8 +86,8 @@ def test_ragged_direct(ptsdf, oracle_mod, n_pts, q):
 @pytest.mark.parametrize("q", [1, 127, 129, 1537])
 @pytest.mark.parametrize("split", [0, 1, 3, 7])
 def test_mixed_cloud(ptsdf, oracle_mod, q, split):
-    """Direct tiles on the tensor cores, kappa tiles on the FP32 units, both
-    writing partials that are merged."""
+    """Direct and kappa-form tiles (flat and curved) on the tensor cores,
+    point chunks merged from partials."""
     p, n, a = mixed_cloud()
     cl = ptsdf.Cloud(p, n, a)
     info = cl.info()
@@ -94,6 +96,50 @@ def test_mixed_cloud(ptsdf, oracle_mod, q, split):
     got = run(cl, x, ptsdf.SDF_ENGINE_TENSOR, split_n=split)
     ref = oracle_mod.Cloud(p, n, a).phi(x)
     assert np.abs(got - ref).max() <= TOL_REL * aabb_diag(p)
+
+
+@pytest.mark.parametrize("split", [0, 1, 4])
+def test_kappa_form_clouds(ptsdf, oracle_mod, split):
+    """Noisy superquadric, N = 2,000: curvature-form records only, most of
+    them with kappa_min = 0 (the flat formula), the rest curved; queries
+    inside, around and far outside the cloud."""
+    p, n, a = f32(*synth.superquadric(2000, 5))
+    cl = ptsdf.Cloud(p, n, a)
+    info = cl.info()
+    assert info["n_direct"] == 0 and info["n_kappa"] == 2000 and info["exact_tiles"] == 0
+    flat = sum(oracle_mod.fit_record(p[i], n[i], a[i])["flat"] == 1.0 for i in range(len(p)))
+    assert 64 < info["n_kappa_flat"] < 2000 and abs(info["n_kappa_flat"] - flat) <= 20
+    rng = np.random.Generator(np.random.PCG64(91))
+    dirs = rng.normal(size=(300, 3))
+    dirs /= np.linalg.norm(dirs, axis=1, keepdims=True)
+    x = f32(np.concatenate([synth.uniform_queries(1100, 92, -1.3, 1.3), dirs[:150] * 40.0, dirs[150:] * 900.0]))
+    got = {}
+    launches = tc_launches(ptsdf, lambda: got.setdefault("tc", run(cl, x, ptsdf.SDF_ENGINE_TENSOR, split_n=split)))
+    assert launches >= 1
+    ref = oracle_mod.Cloud(p, n, a).phi(x)
+    tol = TOL_REL * aabb_diag(p)
+    assert (np.abs(got["tc"] - ref) <= tol + 2e-6 * np.abs(ref)).all(), np.abs(got["tc"] - ref).max()
+
+
+def test_out_of_range_curvature_tiles(ptsdf, oracle_mod):
+    """Points whose kappa_max s exceeds the f16 split's range (tube radii of
+    1e-5): their tiles are flagged and take the record formula, flat and
+    curved kappa forms both, next to ordinary tiles."""
+    p1, n1, a1 = synth.plane_patch(300, 93)
+    a1[:40, 5] = 4e4                       # kappa_max ~ 8e4, kappa_min = 0
+    a1[40:70, 5] = 4e4
+    a1[40:70, 4] = 1e-3                    # kappa_min ~ 2e-3: curved kappa form
+    p2, n2, a2 = synth.superquadric(500, 94)
+    p, n, a = f32(np.concatenate([p1 * 0.9, p2]), np.concatenate([n1, n2]), np.concatenate([a1, a2]))
+    cl = ptsdf.Cloud(p, n, a)
+    info = cl.info()
+    assert 2 <= info["exact_tiles"] < (info["n_kappa"] + 31) // 32
+    x = f32(synth.uniform_queries(700, 95, -1.3, 1.3))
+    got = run(cl, x, ptsdf.SDF_ENGINE_TENSOR)
+    ref = oracle_mod.Cloud(p, n, a).phi(x)
+    assert np.abs(got - ref).max() <= TOL_REL * aabb_diag(p)
+    alu = run(cl, x, ptsdf.SDF_ENGINE_ALU)
+    assert np.abs(got - alu).max() <= TOL_REL * aabb_diag(p)
 
 
 def test_split_factors_agree(ptsdf):
@@ -204,10 +250,10 @@ def test_probe_rates(ptsdf):
     """sdf_probe_rates returns plausible per-SM, per-clock unit rates: the
     special-function unit slower than FMA, exp2 at least as fast as sqrt."""
     import ctypes
-    buf = (ctypes.c_double * 4)()
+    buf = (ctypes.c_double * 5)()
     assert ptsdf.lib().sdf_probe_rates(buf) == 0
-    sqrt_r, rsqrt_r, ex2_r, fma_r = list(buf)
-    for r in (sqrt_r, rsqrt_r, ex2_r):
+    sqrt_r, rsqrt_r, ex2_r, fma_r, rcp_r = list(buf)
+    for r in (sqrt_r, rsqrt_r, ex2_r, rcp_r):
         assert 2.0 <= r <= 64.0, list(buf)
     assert 32.0 <= fma_r <= 260.0, list(buf)
     assert ex2_r >= 0.9 * sqrt_r and fma_r > ex2_r
