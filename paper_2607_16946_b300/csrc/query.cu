@@ -343,7 +343,6 @@ sdf_status launch_query(const Cloud& c, const float* d_x, int64_t q, float* d_ph
     }
     if (e == cudaSuccess && tc) {
         {
-            ProfRange pr(SDF_K_FWD_TC, st);
             TcQuery tq;
             tq.x = a.x;
             tq.q = q;
@@ -359,10 +358,15 @@ sdf_status launch_query(const Cloud& c, const float* d_x, int64_t q, float* d_ph
             tq.lam = a.lam;
             tq.offset = a.offset;
             tq.part_base = 0;
-            if (tp.nd > 0) s = launch_fwd_tc(c, tq, 0, c.tiles_direct, tp.tpc_d, tp.nd, nparts == 1, st);
+            if (tp.nd > 0) {   // one profiled range per launch
+                ProfRange pr(SDF_K_FWD_TC, st);
+                s = launch_fwd_tc(c, tq, 0, c.tiles_direct, tp.tpc_d, tp.nd, nparts == 1, st);
+            }
             tq.part_base = tp.nd;
-            if (s == SDF_OK && tp.nk > 0)
+            if (s == SDF_OK && tp.nk > 0) {
+                ProfRange pr(SDF_K_FWD_TC, st);
                 s = launch_fwd_tc(c, tq, c.tiles_direct, tp.tc_end, tp.tpc_k, tp.nk, nparts == 1, st);
+            }
         }
         if (s == SDF_OK && tp.na > 0) {
             ProfRange pr(SDF_K_FWD, st);

@@ -2,10 +2,11 @@
 
     python -m paper_2607_16946_b300.profile_case [--queries Q] [--launches K] [--warmup W]
 
-Builds the dense-grid cloud (ring torus, N = 100,000) and evaluates an evenly
-strided subset of Q nodes of the 256^3 grid with sdf_query (or the gradient
-and backward calls), W times untimed and then K times, printing the device
-time of each call.  Used to give ncu a short, self-terminating run of the
+Builds the dense-grid cloud (ring torus, N = 100,000; or, with --cloud
+superquadric, the sphere-tracing cloud of N = 262,144 curvature-form points)
+and evaluates an evenly strided subset of Q nodes of the 256^3 grid over
+[-1.6, 1.6]^3 with sdf_query (or the gradient and backward calls), W times
+untimed and then K times, printing the device time of each call.  Used to give ncu a short, self-terminating run of the
 same kernels the benchmark times.
 """
 from __future__ import annotations
@@ -24,7 +25,8 @@ def main():
     ap.add_argument("--queries", type=int, default=1 << 20)
     ap.add_argument("--launches", type=int, default=1)
     ap.add_argument("--warmup", type=int, default=1)
-    ap.add_argument("--points", type=int, default=100_000)
+    ap.add_argument("--points", type=int, default=None, help="default 100,000 (torus) / 262,144 (superquadric)")
+    ap.add_argument("--cloud", choices=["torus", "superquadric"], default="torus")
     ap.add_argument("--mode", choices=["query", "grad", "backward", "radius"], default="query",
                     help="query: sdf_query; grad: sdf_query_grad; backward: sdf_query_grad then "
                          "sdf_backward_params (each call); radius: sdf_query with SDF_LAMBDA_RADIUS and "
@@ -38,7 +40,12 @@ def main():
     import paper_2607_16946_b300 as ptsdf
     import synth
 
-    p, n, a = synth.ring_torus(args.points, 1002, R=1.0, r=0.35, noise=0.005, jitter_deg=2.0)
+    if args.cloud == "torus":
+        args.points = args.points or 100_000
+        p, n, a = synth.ring_torus(args.points, 1002, R=1.0, r=0.35, noise=0.005, jitter_deg=2.0)
+    else:
+        args.points = args.points or 262_144
+        p, n, a = synth.superquadric(args.points, 1003)
     cloud = ptsdf.Cloud(p, n, a)
     res = 256
     g = torch.linspace(-1.6, 1.6, res, device="cuda", dtype=torch.float64)
