@@ -54,30 +54,45 @@ WORKLOAD = ("dense_grid: ring torus N=100000 (R=1, r=0.35, noise 0.005, 2deg vMF
 #    distance, the blend and two accumulations) + 4 MUFU = 29 issue slots.
 #    Tensor-core loop: 9 FMA-pipe instructions + 4 MUFU per pair (the
 #    products come from the tensor cores).
-#  MUFU (XU pipe): sdf_probe_rates measures the unit rates on the box; on
-#    B300 (sm_103a) sqrt / rsqrt.approx retire 16 results per SM per clock
-#    and ex2.approx 32.  A pair needs three square roots (|x - p|, the axis
-#    distance, the tube distance) and one exp2: 3/16 + 1/32 = 7/32 SM-clocks,
-#    32/7 = 4.57 pairs/clk/SM.  This binds the tensor-core loop (issue
-#    ceiling 128/13 = 9.8) and nearly ties the FP32-unit loop's issue
-#    ceiling (128/29 = 4.41).
+#  MUFU (XU pipe): sdf_probe_rates measures, on the box, the single
+#    operations (on B300 sqrt / rsqrt / rcp.approx about 17.9 results per SM
+#    per clock, ex2.approx about 40.5) and each record form's whole per-pair
+#    mix as dependent chains.  A direct pair needs three square roots (|x - p|,
+#    the axis distance, the tube distance) and one exp2; the measured mix rate
+#    is the MUFU ceiling.  It binds the tensor-core loop (issue ceiling
+#    128/13 = 9.8) and nearly ties the FP32-unit loop's issue ceiling
+#    (128/29 = 4.41).
 INSTR_PER_PAIR = 29
 THREAD_INSTR_PER_SM_CLK = 128
 NOMINAL_RATES = {"sqrt": 16.0, "rsqrt": 16.0, "ex2": 32.0, "fma": 128.0, "rcp": 16.0}
+PAIR_MIX_KEYS = {"direct": "pair_direct", "flat": "pair_flat", "curved": "pair_curved"}
 
 
 def probe_rates(L):
     """Unit rates (results per SM per clock) measured by sdf_probe_rates, or
     the nominal ones if the probe fails."""
-    buf = (ctypes.c_double * 5)()
+    buf = (ctypes.c_double * 8)()
     if L.sdf_probe_rates(buf) != 0:
         return dict(NOMINAL_RATES, source="nominal (probe failed)")
-    return {"sqrt": buf[0], "rsqrt": buf[1], "ex2": buf[2], "fma": buf[3], "rcp": buf[4], "source": "measured (sdf_probe_rates)"}
+    return {"sqrt": buf[0], "rsqrt": buf[1], "ex2": buf[2], "fma": buf[3], "rcp": buf[4],
+            "pair_direct": buf[5], "pair_flat": buf[6], "pair_curved": buf[7],
+            "source": "measured (sdf_probe_rates)"}
+
+
+def mix_cost(rates, form):
+    """SM-clocks of special-function work per pair of a record form: the
+    probe's measured rate of that form's whole mix, else the sum of the
+    single-operation costs."""
+    k = PAIR_MIX_KEYS[form]
+    if rates.get(k):
+        return 1.0 / rates[k]
+    m = TC_FORM_COST[form][0]
+    return m[0] / rates["sqrt"] + m[1] / rates.get("rcp", rates["sqrt"]) + m[2] / rates["ex2"]
 
 
 def pair_ceiling(rates, instr_per_pair):
     """pairs per SM clock: the lower of the MUFU and the issue ceilings."""
-    mufu = 1.0 / (3.0 / rates["sqrt"] + 1.0 / rates["ex2"])
+    mufu = 1.0 / mix_cost(rates, "direct")
     issue = rates["fma"] / instr_per_pair
     return min(mufu, issue), mufu, issue
 
@@ -92,8 +107,7 @@ def tc_pair_ceiling(rates, counts):
     points of each record form (pairs weighted by form): the lower of the
     MUFU and the issue ceilings."""
     total = sum(counts.values())
-    mufu_clk = sum(c * (m[0] / rates["sqrt"] + m[1] / rates.get("rcp", rates["sqrt"]) + m[2] / rates["ex2"])
-                   for f, c in counts.items() for m in [TC_FORM_COST[f][0]])
+    mufu_clk = sum(c * mix_cost(rates, f) for f, c in counts.items())
     issue_clk = sum(c * TC_FORM_COST[f][1] / rates["fma"] for f, c in counts.items())
     mufu, issue = total / mufu_clk, total / issue_clk
     return min(mufu, issue), mufu, issue
@@ -237,11 +251,13 @@ def make_serving_clouds(n_clouds: int, seed: int):
     return out
 
 
-def run_served(args, dev, pair_rate_gps: float, policy: int = 0, clouds_np=None):
+def run_served(args, dev, pair_rate_gps: float, policy: int = 0, clouds_np=None, precision: int = 0):
     """Continuous-batching run: Poisson arrivals at `load` x the measured pair
     rate, requests of Q log-uniform in [1,024, 4,194,304] against random
     resident clouds; kinds QUERY 70%, OFFSET 10%, UNION / DIFFERENCE 10%,
-    TRACE_STEP 10%.  Returns the latency / throughput summary."""
+    TRACE_STEP 10%; every request at `precision` (0 FP32 with the tensor
+    engine, 1 F16X2 packed-half weights).  Returns the latency / throughput
+    summary."""
     import torch
 
     import paper_2607_16946_b300 as ptsdf
@@ -286,7 +302,7 @@ def run_served(args, dev, pair_rate_gps: float, policy: int = 0, clouds_np=None)
             if r["kind"] == S.SDF_REQ_TRACE_STEP:
                 kw = dict(dirs=dpool[r["off"]:r["off"] + r["q"]], t=tpool[r["off"]:r["off"] + r["q"]])
             tickets[i] = srv.submit(r["kind"], ids[r["ca"]], x, outs[i], cloud_id_b=ids[r["cb"]],
-                                    offset=r["offset"], **kw)
+                                    offset=r["offset"], precision=precision, **kw)
 
     th = threading.Thread(target=submitter)
     th.start()
@@ -314,7 +330,8 @@ def run_served(args, dev, pair_rate_gps: float, policy: int = 0, clouds_np=None)
                        "policy": "smallest_first (starve 2 s)" if policy else "fifo"},
             "workload": f"{len(clouds)} resident clouds N~logU[2048,500000] (sphere/torus/superquadric/ellipsoid), "
                         f"{len(reqs)} requests Q~logU[1024,4194304], Poisson arrivals at "
-                        f"{args.serve_load} x measured capacity; FP32"}
+                        f"{args.serve_load} x measured capacity; "
+                        f"{'FP32 (tensor engine)' if precision == 0 else 'F16X2 packed-half weights, FP32 sums'}"}
 
 
 # Algorithmic issue slots per pair of the other pair loops (direct torus form,
@@ -677,7 +694,9 @@ def run_ours(args, rank, world, local):
         traffic = committed_traffic()
         basis = (f"{'MUFU' if mufu_c <= issue_c else 'issue'} ceiling: {sms} SMs x {fmax:.0f} MHz x "
                  f"{per_sm_clk:.3f} pairs/clk/SM over the points by form {counts}; MUFU per pair "
-                 f"(sqrt, rcp, ex2) = {dict((f, c[0]) for f, c in TC_FORM_COST.items())} -> {mufu_c:.3f}, "
+                 f"(sqrt, rcp, ex2) = {dict((f, c[0]) for f, c in TC_FORM_COST.items())}, each mix's "
+                 f"rate measured whole by sdf_probe_rates -> {mufu_c:.3f} (sum of the single-operation "
+                 f"rates: {sum(counts.values()) / sum(c * (m[0] / rates['sqrt'] + m[1] / rates.get('rcp', rates['sqrt']) + m[2] / rates['ex2']) for f, c in counts.items() for m in [TC_FORM_COST[f][0]]):.3f}), "
                  f"issue fma/{dict((f, c[1]) for f, c in TC_FORM_COST.items())} -> {issue_c:.3f} "
                  f"(unit rates {rates['source']})")
     else:
@@ -686,7 +705,8 @@ def run_ours(args, rank, world, local):
         kp = prof.get("fwd", {"launches": 0, "ms": float("nan")})
         traffic = None
         basis = (f"{'MUFU' if mufu_c <= issue_c else 'issue'} ceiling: {sms} SMs x {fmax:.0f} MHz x "
-                 f"{per_sm_clk:.3f} pairs/clk/SM; MUFU 1/(3/sqrt + 1/ex2) = {mufu_c:.3f}, issue fma/"
+                 f"{per_sm_clk:.3f} pairs/clk/SM; MUFU: the direct mix (3 sqrt + 1 ex2) measured whole = "
+                 f"{mufu_c:.3f}, issue fma/"
                  f"{INSTR_PER_PAIR} = {issue_c:.3f} (unit rates {rates['source']})")
     peak = sms * fmax * 1e6 * per_sm_clk / 1e9
     # per step: the pair loop runs as one launch per record segment present
@@ -723,6 +743,9 @@ def run_ours(args, rank, world, local):
         clouds_np = make_serving_clouds(args.serve_clouds, SERVE_SEED)
         line["served"] = run_served(args, dev, value, policy=1, clouds_np=clouds_np)
         line["served_fifo"] = run_served(args, dev, value, policy=0, clouds_np=clouds_np)
+        # the serving configuration's packed-half form, offered at 0.7 of its own measured rate
+        f16_rate = line.get("mixed", {}).get("f16x2", {}).get("value") or value
+        line["served_f16x2"] = run_served(args, dev, f16_rate, policy=1, clouds_np=clouds_np, precision=1)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(p, n, a)
     print(json.dumps(line), flush=True)

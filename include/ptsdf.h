@@ -432,9 +432,13 @@ PTSDF_API sdf_status sdf_mesh_level_set(const float* d_phi, int32_t nx, int32_t 
 /* Measures, on the current device, the sustained throughput of the
  * operations that bound the pair loops, in results per SM per SM clock:
  * rates[0] sqrt.approx, rates[1] rsqrt.approx, rates[2] ex2.approx (the
- * special-function unit), rates[3] FP32 FMA and rates[4] rcp.approx.  A measurement aid for
+ * special-function unit), rates[3] FP32 FMA and rates[4] rcp.approx; and,
+ * in pairs per SM per clock, the special-function work of one pair as the
+ * pair loops issue it: rates[5] direct form (3 sqrt + 1 exp2), rates[6]
+ * curvature form with kappa_min = 0 (2 sqrt + 1 rcp + 1 exp2), rates[7]
+ * other curvature form (3 sqrt + 2 rcp + 1 exp2).  A measurement aid for
  * roofline reporting (about 20 ms of kernels on every SM); it does not touch
- * any cloud.  rates must hold 5 doubles. */
+ * any cloud.  rates must hold 8 doubles. */
 PTSDF_API sdf_status sdf_probe_rates(double* rates);
 
 /* Self-test of the failure path (not part of the method): launches one

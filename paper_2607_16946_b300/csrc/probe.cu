@@ -1,6 +1,10 @@
 // Throughput probe of the operations that bound the pair loops: the
 // special-function unit's sqrt, rsqrt, exp2 and reciprocal (the approximate
-// forms the kernels use) and FP32 FMA.  Each thread runs independent dependent chains
+// forms the kernels use) and FP32 FMA, and the special-function work of one
+// pair of each torus form as a whole (the mix the pair loops issue: direct
+// 3 sqrt + 1 exp2; curvature form with kappa_min = 0, 2 sqrt + 1 rcp + 1
+// exp2; other curvature form, 3 sqrt + 2 rcp + 1 exp2), one pair per chain
+// step.  Each thread runs independent dependent chains
 // of one operation; every SM holds the same number of CTAs, which record
 // their SM and their clock64 cycle count, so the rates come out per SM and
 // per SM clock without relying on a nominal clock.
@@ -27,6 +31,9 @@ __device__ __forceinline__ float probe_op(float a) {
     if (OP == 1) return rsqrt_mufu(a);                // stays in (0.5, 2)
     if (OP == 2) return ex2_mufu(-a);                 // stays in (0.5, 1]
     if (OP == 4) return rcp_mufu(a) + 0.5f;           // -> 1.28 (a plain rcp chain folds to a copy)
+    if (OP == 5) return ex2_mufu(-sqrt_mufu(sqrt_mufu(sqrt_mufu(a))));                         // in (0.5, 0.6)
+    if (OP == 6) return ex2_mufu(-rcp_mufu(1.f + sqrt_mufu(sqrt_mufu(a))));                    // in (0.7, 0.8)
+    if (OP == 7) return ex2_mufu(-rcp_mufu(1.f + sqrt_mufu(rcp_mufu(1.f + sqrt_mufu(sqrt_mufu(a))))));
     return fmaf(a, 0.999f, 0.001f);                   // -> 1
 }
 
@@ -100,8 +107,9 @@ extern "C" sdf_status sdf_probe_rates(double* rates) {
     std::vector<long long> hc(blocks);
     std::vector<int> hs(blocks);
     using Kern = void (*)(float*, long long*, int*);
-    const Kern kernels[5] = {k_probe<0>, k_probe<1>, k_probe<2>, k_probe<3>, k_probe<4>};
-    for (int op = 0; op < 5 && e == cudaSuccess; ++op) {
+    const Kern kernels[8] = {k_probe<0>, k_probe<1>, k_probe<2>, k_probe<3>,
+                             k_probe<4>, k_probe<5>, k_probe<6>, k_probe<7>};
+    for (int op = 0; op < 8 && e == cudaSuccess; ++op) {
         for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {   // the first run warms up
             kernels[op]<<<blocks, kProbeThreads>>>(sink, cyc, smid);
             e = cudaGetLastError();

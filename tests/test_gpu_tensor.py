@@ -250,13 +250,16 @@ def test_probe_rates(ptsdf):
     """sdf_probe_rates returns plausible per-SM, per-clock unit rates: the
     special-function unit slower than FMA, exp2 at least as fast as sqrt."""
     import ctypes
-    buf = (ctypes.c_double * 5)()
+    buf = (ctypes.c_double * 8)()
     assert ptsdf.lib().sdf_probe_rates(buf) == 0
-    sqrt_r, rsqrt_r, ex2_r, fma_r, rcp_r = list(buf)
+    sqrt_r, rsqrt_r, ex2_r, fma_r, rcp_r, direct, flat, curved = list(buf)
     for r in (sqrt_r, rsqrt_r, ex2_r, rcp_r):
         assert 2.0 <= r <= 64.0, list(buf)
     assert 32.0 <= fma_r <= 260.0, list(buf)
     assert ex2_r >= 0.9 * sqrt_r and fma_r > ex2_r
+    # a whole pair's mix is slower than any of its operations alone, and the
+    # curved curvature form (six operations) the slowest
+    assert 0.5 <= curved < flat <= 1.1 * direct < sqrt_r, list(buf)
 
 
 def test_wait_timeout_reports_and_recovers(ptsdf):
