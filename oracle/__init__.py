@@ -7,9 +7,15 @@ never calls the CUDA library: the two share no code.
 The arithmetic lives in ``oracle.c`` (plain C, double precision, POSIX threads
 over queries); this module is a ctypes wrapper with numpy arrays.  Functions:
 
-  Cloud(points, normals, params)        fit every torus (Sec. 4.1, App. C)
+  Cloud(points, normals, params, weights=None)
+                                        fit every torus (Sec. 4.1, App. C); the
+                                        optional per-point weights A_i enter
+                                        every blend (the area weights of Eq.
+                                        SelfNormalizedConvolutionalDistanceFormula)
   Cloud.phi(x, C=64, ...)               shifted blend, Eqs. BasicFormulaShifted
                                         and RelationshipBetweenLambdaAndRadius
+  Cloud.lse(x, C=64, ...)               log-sum-exp distance, Eq.
+                                        ConvolutionalDistanceFormula (h = 1)
   Cloud.grad_x(x, ...)                  d phi / d x (forward-mode duals; App. D
                                         plus the x-dependence of lambda_x)
   Cloud.grad_params(x, G, ...)          d (sum_q G_q phi_q) / d a_i
@@ -68,7 +74,10 @@ def _load():
         _lib.or_fit_record.argtypes = [P, P, P, P]
         _lib.or_torus_sdf.argtypes = [P, P, f64, f64, P, i64, P]
         _lib.or_frame.argtypes = [P, P, P]
-        _lib.or_phi_radius.argtypes = [P, f64, f64, i32, P, i64, P, P, i32]
+        _lib.or_phi_radius.argtypes = [P, f64, f64, i32, P, i64, P, P, i32, i32]
+        _lib.or_set_weights.argtypes = [P, P]
+        _lib.or_set_weights.restype = i32
+        _lib.or_lse.argtypes = [P, i32, f64, f64, P, i64, P, i32]
         _lib.or_laplacian.argtypes = [P, i32, f64, f64, P, i64, P, P, P, i32]
         _lib.or_knn_mean_distance.argtypes = [P, i64, i32, i32]
         _lib.or_knn_mean_distance.restype = f64
@@ -93,7 +102,7 @@ def default_threads() -> int:
 class Cloud:
     """A fitted cloud held by the oracle."""
 
-    def __init__(self, points, normals, params):
+    def __init__(self, points, normals, params, weights=None):
         lib = _load()
         self._p = _f64(points, 3)
         self._n = _f64(normals, 3)
@@ -105,6 +114,11 @@ class Cloud:
         if not self._h:
             raise ValueError("oracle build rejected the cloud (empty, or a zero / non-finite normal)")
         self.n = n
+        self._w = None
+        if weights is not None:
+            self._w = _f64(weights).ravel()
+            if self._w.shape[0] != n or lib.or_set_weights(self._h, _ptr(self._w)) != 0:
+                raise ValueError("weights: one finite value > 0 per point")
 
     def __del__(self):
         if getattr(self, "_h", None):
@@ -131,12 +145,21 @@ class Cloud:
                              threads or default_threads())
         return phi, g, lap
 
+    def lse(self, x, C: float = 64.0, mode: int = GLOBAL, lam: float = 0.0, threads: int | None = None):
+        """Log-sum-exp distance -(1/lambda) log sum_i A_i exp(-lambda |x - p_i|)
+        (Eq. ConvolutionalDistanceFormula with h = 1), lambda as in phi."""
+        x = _f64(x, 3)
+        out = np.empty(x.shape[0])
+        _load().or_lse(self._h, mode, C, lam, _ptr(x), x.shape[0], _ptr(out), threads or default_threads())
+        return out
+
     def phi_radius(self, x, lam: float, reval: float | None = None, C: float = 64.0, kfb: int = 32,
-                   threads: int | None = None, used: bool = False):
+                   threads: int | None = None, used: bool = False, lse: bool = False):
         """Radius-limited blend (Sec. 4.2, "Acceleration and adaptive lambda"):
         constant lambda, the points within R_eval (default 2 C / lambda), else
         the kfb nearest.  used: also return, per query, the number of points
-        inside R_eval (or minus the number of fallback neighbours)."""
+        inside R_eval (or minus the number of fallback neighbours).  lse: the
+        log-sum-exp distance of the same set instead of the blend."""
         x = _f64(x, 3)
         m = x.shape[0]
         if reval is None:
@@ -144,7 +167,7 @@ class Cloud:
         out = np.empty(m)
         u = np.empty(m) if used else None
         _load().or_phi_radius(self._h, float(lam), float(reval), int(kfb), _ptr(x), m, _ptr(out),
-                              _ptr(u) if used else None, threads or default_threads())
+                              _ptr(u) if used else None, threads or default_threads(), int(lse))
         return (out, u) if used else out
 
     def grad_x(self, x, C: float = 64.0, mode: int = GLOBAL, lam: float = 0.0,

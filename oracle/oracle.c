@@ -277,7 +277,13 @@ typedef struct {
     torus_t* tori;
     double (*a)[6];          /* coefficients, kept for the parameter gradient */
     double (*nrm)[3];        /* unit input normals */
+    double* wt;              /* per-point weights A_i (NULL: all 1) */
 } or_cloud;
+
+/* The weight A_i of point i in every blend: the discretisation of the
+ * surface integral of Eq. SelfNormalizedConvolutionalDistanceFormula, which
+ * the paper's Eq. BasicFormulaShifted leaves out (all A_i = 1). */
+static double wt_of(const or_cloud* C, int64_t i) { return C->wt ? C->wt[i] : 1.0; }
 
 /* Builds the cloud: normalises each normal and fits its torus.  Returns NULL
  * for n <= 0 or a zero / non-finite normal. */
@@ -305,7 +311,18 @@ or_cloud* or_build(const double* points, const double* normals, const double* pa
 
 void or_free(or_cloud* C) {
     if (!C) return;
-    free(C->tori); free(C->a); free(C->nrm); free(C);
+    free(C->tori); free(C->a); free(C->nrm); free(C->wt); free(C);
+}
+
+/* Sets the per-point weights (n values, each finite and > 0), or clears them
+ * (w = NULL).  Returns 0, or -1 (weights unchanged) for an invalid weight. */
+int or_set_weights(or_cloud* C, const double* w) {
+    if (!w) { free(C->wt); C->wt = NULL; return 0; }
+    for (int64_t i = 0; i < C->n; ++i)
+        if (!(w[i] > 0.0) || !isfinite(w[i])) return -1;
+    if (!C->wt) C->wt = (double*)malloc((size_t)C->n * sizeof(double));
+    memcpy(C->wt, w, (size_t)C->n * sizeof(double));
+    return 0;
 }
 
 int64_t or_size(const or_cloud* C) { return C->n; }
@@ -388,7 +405,7 @@ static double phi_one(const or_cloud* C, const or_opts* o, const double x[3], do
         const double* p = C->tori[i].p;
         double w3[3] = {x[0] - p[0], x[1] - p[1], x[2] - p[2]};
         double d = sqrt(dot3(w3, w3));
-        double w = exp(-lambda * (d - shift));
+        double w = wt_of(C, i) * exp(-lambda * (d - shift));
         W += w;
         S += w * g_plain(&C->tori[i], x);
     }
@@ -434,6 +451,62 @@ void or_phi(const or_cloud* C, int mode, double Cconst, double lambda, int shift
 }
 
 /* ------------------------------------------------------------------------ */
+/* The log-sum-exp distance (Eq. ConvolutionalDistanceFormula with h = 1,    */
+/* the integral over the geometry discretised over the points with the      */
+/* weights A_i):                                                            */
+/*   d~(x) = -(1/lambda) log sum_i A_i exp(-lambda |x - p_i|)               */
+/*         = d_min - (1/lambda) log sum_i A_i exp(-lambda (|x - p_i| - d_min)) */
+/* with the screening of the blend: lambda = lambda_x = C / sigma_x (GLOBAL) */
+/* or the fixed lambda.  lambda = 0 (GLOBAL with every point at x) gives     */
+/* d_min, the distance to the points.                                       */
+/* ------------------------------------------------------------------------ */
+static double lse_one(const or_cloud* C, const or_opts* o, const double x[3]) {
+    const int64_t n = C->n;
+    double dmax = -1.0, dmin = INFINITY;
+    for (int64_t i = 0; i < n; ++i) {
+        const double* p = C->tori[i].p;
+        double w[3] = {x[0] - p[0], x[1] - p[1], x[2] - p[2]};
+        double d = sqrt(dot3(w, w));
+        if (d > dmax) dmax = d;
+        if (d < dmin) dmin = d;
+    }
+    double lambda;
+    if (o->mode == OR_GLOBAL) lambda = (dmax > 0.0) ? o->C / (0.5 * dmax) : 0.0;
+    else lambda = o->lambda;
+    if (!(lambda > 0.0)) return dmin;
+    double W = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        const double* p = C->tori[i].p;
+        double w3[3] = {x[0] - p[0], x[1] - p[1], x[2] - p[2]};
+        W += wt_of(C, i) * exp(-lambda * (sqrt(dot3(w3, w3)) - dmin));
+    }
+    return dmin - log(W) / lambda;
+}
+
+typedef struct { const or_cloud* C; const or_opts* o; const double* x; double* out; int64_t q0, q1; } lse_job;
+
+static void* lse_worker(void* arg) {
+    lse_job* J = (lse_job*)arg;
+    for (int64_t j = J->q0; j < J->q1; ++j) J->out[j] = lse_one(J->C, J->o, J->x + 3 * j);
+    return NULL;
+}
+
+void or_lse(const or_cloud* C, int mode, double Cconst, double lambda, const double* x, int64_t m, double* out,
+            int threads) {
+    or_opts o = {mode, Cconst, lambda, OR_SHIFT_DMIN};
+    threads = clamp_threads(threads, m);
+    pthread_t th[256];
+    lse_job jobs[256];
+    int64_t per = (m + threads - 1) / threads;
+    for (int k = 0; k < threads; ++k) {
+        int64_t q0 = k * per, q1 = q0 + per < m ? q0 + per : m;
+        jobs[k] = (lse_job){C, &o, x, out, q0, q1 > q0 ? q1 : q0};
+        pthread_create(&th[k], NULL, lse_worker, &jobs[k]);
+    }
+    for (int k = 0; k < threads; ++k) pthread_join(th[k], NULL);
+}
+
+/* ------------------------------------------------------------------------ */
 /* d phi / d x: forward-mode duals through the whole definition, including  */
 /* the dependence of lambda_x on x through the farthest point (App. D gives */
 /* the constant-lambda part; the farthest-point tie goes to the lowest      */
@@ -464,7 +537,7 @@ static double grad_one(const or_cloud* C, const or_opts* o, const double x[3], d
     dual W = dconst(0.0), S = dconst(0.0);
     for (int64_t i = 0; i < n; ++i) {
         dual d = dv_norm(dv_sub(X, dv_const(C->tori[i].p)));
-        dual w = dexp(dneg(dmul(lambda, dsub(d, shift))));
+        dual w = dscale(dexp(dneg(dmul(lambda, dsub(d, shift)))), wt_of(C, i));
         dtorus D;
         dtorus_const(&C->tori[i], &D);
         W = dadd(W, w);
@@ -523,7 +596,7 @@ static void* pgrad_worker(void* arg) {
             const double* xj = J->x + 3 * j;
             double w3[3] = {xj[0] - p[0], xj[1] - p[1], xj[2] - p[2]};
             double d = sqrt(dot3(w3, w3));
-            double w = exp(-J->lam[j] * (d - J->shift[j]));
+            double w = wt_of(C, i) * exp(-J->lam[j] * (d - J->shift[j]));
             double coef = J->G[j] * w / J->W[j];
             if (coef == 0.0) continue;
             dual g = g_dual(&D, dv_const(xj));
@@ -635,8 +708,12 @@ static void topk_insert(double* bd, int64_t* bi, int* cnt, int k, double d, int6
     bi[j] = i;
 }
 
+/* The set is the points within R_eval of x, else its kfb nearest; with s the
+ * smallest distance in the set, W = sum A_i exp(-lambda (d_i - s)) and
+ * S = sum A_i exp(-lambda (d_i - s)) g_i over it.  Returns S / W, or (lse)
+ * the log-sum-exp distance of the same set, s - log(W) / lambda. */
 static double phi_radius_one(const or_cloud* C, double lambda, double reval, int kfb, const double x[3],
-                             double* used) {
+                             double* used, int lse) {
     const int64_t n = C->n;
     int64_t inside = 0;
     double dmin = INFINITY;
@@ -656,12 +733,12 @@ static double phi_radius_one(const or_cloud* C, double lambda, double reval, int
             double w3[3] = {x[0] - p[0], x[1] - p[1], x[2] - p[2]};
             double d = sqrt(dot3(w3, w3));
             if (d > reval) continue;
-            double w = exp(-lambda * (d - dmin));
+            double w = wt_of(C, i) * exp(-lambda * (d - dmin));
             W += w;
-            S += w * g_plain(&C->tori[i], x);
+            S += lse ? 0.0 : w * g_plain(&C->tori[i], x);
         }
         if (used) *used = (double)inside;
-        return S / W;
+        return lse ? dmin - log(W) / lambda : S / W;
     }
     /* fallback: the k_fb nearest points */
     int k = kfb < n ? kfb : (int)n;
@@ -674,39 +751,42 @@ static double phi_radius_one(const or_cloud* C, double lambda, double reval, int
         topk_insert(bd, bi, &cnt, k, sqrt(dot3(w3, w3)), i);
     }
     for (int j = 0; j < cnt; ++j) {
-        double w = exp(-lambda * (bd[j] - bd[0]));
+        double w = wt_of(C, bi[j]) * exp(-lambda * (bd[j] - bd[0]));
         W += w;
-        S += w * g_plain(&C->tori[bi[j]], x);
+        S += lse ? 0.0 : w * g_plain(&C->tori[bi[j]], x);
     }
+    const double s0 = bd[0];
     free(bd);
     free(bi);
     if (used) *used = -(double)cnt;
-    return S / W;
+    return lse ? s0 - log(W) / lambda : S / W;
 }
 
 typedef struct {
     const or_cloud* C; double lambda, reval; int kfb; const double* x; double* phi; double* used;
-    int64_t q0, q1;
+    int64_t q0, q1; int lse;
 } radius_job;
 
 static void* radius_worker(void* arg) {
     radius_job* J = (radius_job*)arg;
     for (int64_t j = J->q0; j < J->q1; ++j)
-        J->phi[j] = phi_radius_one(J->C, J->lambda, J->reval, J->kfb, J->x + 3 * j, J->used ? J->used + j : NULL);
+        J->phi[j] = phi_radius_one(J->C, J->lambda, J->reval, J->kfb, J->x + 3 * j, J->used ? J->used + j : NULL,
+                                   J->lse);
     return NULL;
 }
 
-/* phi at m queries, radius-limited; used[j] (optional) = the number of points
- * inside R_eval, or minus the number of fallback neighbours. */
+/* phi (lse = 0) or the log-sum-exp distance (lse = 1) at m queries,
+ * radius-limited; used[j] (optional) = the number of points inside R_eval,
+ * or minus the number of fallback neighbours. */
 void or_phi_radius(const or_cloud* C, double lambda, double reval, int kfb, const double* x, int64_t m,
-                   double* phi, double* used, int threads) {
+                   double* phi, double* used, int threads, int lse) {
     threads = clamp_threads(threads, m);
     pthread_t th[256];
     radius_job jobs[256];
     int64_t per = (m + threads - 1) / threads;
     for (int k = 0; k < threads; ++k) {
         int64_t q0 = k * per, q1 = q0 + per < m ? q0 + per : m;
-        jobs[k] = (radius_job){C, lambda, reval, kfb, x, phi, used, q0, q1 > q0 ? q1 : q0};
+        jobs[k] = (radius_job){C, lambda, reval, kfb, x, phi, used, q0, q1 > q0 ? q1 : q0, lse};
         pthread_create(&th[k], NULL, radius_worker, &jobs[k]);
     }
     for (int k = 0; k < threads; ++k) pthread_join(th[k], NULL);
@@ -829,7 +909,8 @@ static jet g_jet(const torus_t* T, const jet X[3]) {
     return jscale(phiT, (double)T->sign);
 }
 
-static double lap_one(const or_cloud* C, const or_opts* o, const double x[3], double g3[3]) {
+/* Returns phi; g4 = {d phi / dx, d phi / dy, d phi / dz, lap phi}. */
+static double lap_one(const or_cloud* C, const or_opts* o, const double x[3], double g4[4]) {
     const int64_t n = C->n;
     int64_t imax = 0;
     double dmax = -1.0, dmin = INFINITY;
@@ -860,16 +941,16 @@ static double lap_one(const or_cloud* C, const or_opts* o, const double x[3], do
             jet wp[3];
             for (int k = 0; k < 3; ++k) wp[k] = jsub(X[k], jconst(C->tori[i].p[k]));
             jet d = jnorm(wp);
-            jet wgt = jexp(jscale(jmul(lambda, jsub(d, jconst(shift))), -1.0));
+            jet wgt = jscale(jexp(jscale(jmul(lambda, jsub(d, jconst(shift))), -1.0)), wt_of(C, i));
             W = jadd(W, wgt);
             S = jadd(S, jmul(wgt, g_jet(&C->tori[i], X)));
         }
         jet ph = jdiv(S, W);
         phi = ph.v;
-        g3[ax] = ph.d1;
+        g4[ax] = ph.d1;
         lap += ph.d2;
     }
-    g3[3] = lap;
+    g4[3] = lap;
     return phi;
 }
 
