@@ -93,6 +93,19 @@ typedef enum {
 
 enum { SDF_RADIUS_FALLBACK_K = 32 };
 
+typedef enum {
+    SDF_FORMULA_BLEND = 0,  /* phi = sum_i A_i w_i g_i / sum_i A_i w_i: Eq. BasicFormulaShifted (the
+                               self-normalised blend of the torus SDFs), A_i = 1 unless the cloud
+                               was built with weights */
+    SDF_FORMULA_LSE = 1     /* d~ = -(1/lambda) log sum_i A_i exp(-lambda ||x - p_i||): the log-sum-exp
+                               distance, Eq. ConvolutionalDistanceFormula with h = 1 (unsigned; the
+                               tori are not used).  lambda is the blend's: lambda_x under
+                               SDF_LAMBDA_GLOBAL (d~ = d_min where lambda_x = 0, every point at x),
+                               fixed_lambda (> 0) under FIXED and RADIUS (the RADIUS set's sum).
+                               Queries only: no gradients, parameter gradients, Laplacian or
+                               sphere tracing. */
+} sdf_formula;
+
 typedef struct {
     int32_t lambda_mode;   /* sdf_lambda_mode */
     int32_t precision;     /* sdf_precision (SDF_F32 is the reference path) */
@@ -103,11 +116,11 @@ typedef struct {
                               automatic choice depends only on (Q, N, SM count), so a query's
                               result does not depend on what else runs. */
     int32_t engine;        /* sdf_engine (SDF_ENGINE_AUTO) */
-    int32_t reserved;      /* 0 (keeps the structure 8-byte sized inside sdf_request) */
+    int32_t formula;       /* sdf_formula (SDF_FORMULA_BLEND) */
 } sdf_query_opts;
 
 /* Fills *opts with the paper's defaults: GLOBAL lambda, C = 64, F32, offset 0,
- * automatic split, automatic engine.  Returns SDF_EINVAL for NULL. */
+ * automatic split, automatic engine, the blend.  Returns SDF_EINVAL for NULL. */
 PTSDF_API sdf_status sdf_opts_default(sdf_query_opts* opts);
 
 /* ---------------------------------------------------------------------------
@@ -133,6 +146,20 @@ PTSDF_API sdf_status sdf_opts_default(sdf_query_opts* opts);
  * ------------------------------------------------------------------------- */
 PTSDF_API sdf_status sdf_build(const float* d_points, const float* d_normals, const float* d_params,
                      int64_t n, void* stream, sdf_cloud* out);
+
+/* sdf_build with per-point weights A_i: every sum over points (the blend,
+ * its gradients and Laplacian, the parameter gradient, the radius-limited
+ * sum and the log-sum-exp distance) weighs point i by A_i.  They are the
+ * area weights of the discretised surface integral of Eq.
+ * SelfNormalizedConvolutionalDistanceFormula, which Eq. BasicFormulaShifted
+ * leaves out (sdf_build: all A_i = 1).
+ *   d_weights  N float on the device, each in [2^-64, 2^64] (else SDF_EINVAL,
+ *              detected on the device; the range keeps every FP32 sum finite
+ *              and non-zero); NULL is sdf_build.
+ *   A weighted cloud is evaluated by the FP32-unit pair loops (SDF_ENGINE_AUTO
+ *   chooses them; SDF_ENGINE_TENSOR returns SDF_EINVAL). */
+PTSDF_API sdf_status sdf_build_weighted(const float* d_points, const float* d_normals, const float* d_params,
+                              const float* d_weights, int64_t n, void* stream, sdf_cloud* out);
 
 /* Releases a cloud (synchronises the device first).  NULL is a no-op. */
 PTSDF_API sdf_status sdf_destroy(sdf_cloud cloud);

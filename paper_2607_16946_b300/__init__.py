@@ -17,14 +17,13 @@ import ctypes
 import numpy as np
 
 from . import _abi
-from ._abi import (SDF_DIFFERENCE, SDF_ENGINE_ALU, SDF_ENGINE_AUTO, SDF_ENGINE_TENSOR, SDF_INTERSECT,
-                   SDF_LAMBDA_FIXED, SDF_LAMBDA_GLOBAL, SDF_LAMBDA_RADIUS, SDF_UNION, SdfError, check, lib,
-                   make_opts)
+from ._abi import (SDF_DIFFERENCE, SDF_ENGINE_ALU, SDF_ENGINE_AUTO, SDF_ENGINE_TENSOR, SDF_FORMULA_BLEND,
+                   SDF_FORMULA_LSE, SDF_INTERSECT, SDF_LAMBDA_FIXED, SDF_LAMBDA_GLOBAL, SDF_LAMBDA_RADIUS, SDF_UNION,
+                   SdfError, check, lib, make_opts)
 
 __all__ = ["Cloud", "SdfError", "SDF_LAMBDA_GLOBAL", "SDF_LAMBDA_FIXED", "SDF_LAMBDA_RADIUS", "SDF_UNION",
-           "SDF_INTERSECT",
-           "SDF_DIFFERENCE", "mesh_level_set", "orient", "SDF_ENGINE_AUTO", "SDF_ENGINE_ALU", "SDF_ENGINE_TENSOR", "make_opts", "lib", "sdf",
-           "combine"]
+           "SDF_INTERSECT", "SDF_DIFFERENCE", "SDF_ENGINE_AUTO", "SDF_ENGINE_ALU", "SDF_ENGINE_TENSOR",
+           "SDF_FORMULA_BLEND", "SDF_FORMULA_LSE", "mesh_level_set", "orient", "make_opts", "lib", "sdf", "combine"]
 
 
 def _torch():
@@ -52,17 +51,27 @@ def _dev_f32(a, cols=None):
 class Cloud:
     """A point cloud with one fitted torus per point, resident on the GPU."""
 
-    def __init__(self, points, normals, params, stream=None):
+    def __init__(self, points, normals, params, weights=None, stream=None):
+        """weights: optional per-point weights A_i (N values in [2^-64, 2^64]),
+        the area weights of the discretised surface integral; None = all 1."""
         lib()
         p, n, a = _dev_f32(points, 3), _dev_f32(normals, 3), _dev_f32(params, 6)
         if not (p.shape[0] == n.shape[0] == a.shape[0]):
             raise ValueError("points, normals and params must have the same length")
+        w = None
+        if weights is not None:
+            w = _dev_f32(weights, 1).reshape(-1)
+            if w.shape[0] != p.shape[0]:
+                raise ValueError("weights must have one value per point")
         h = ctypes.c_void_p()
-        check(lib().sdf_build(ctypes.c_void_p(p.data_ptr()), ctypes.c_void_p(n.data_ptr()),
-                              ctypes.c_void_p(a.data_ptr()), p.shape[0], _stream_ptr(stream), ctypes.byref(h)),
+        check(lib().sdf_build_weighted(ctypes.c_void_p(p.data_ptr()), ctypes.c_void_p(n.data_ptr()),
+                                       ctypes.c_void_p(a.data_ptr()),
+                                       ctypes.c_void_p(w.data_ptr()) if w is not None else None, p.shape[0],
+                                       _stream_ptr(stream), ctypes.byref(h)),
               "sdf_build")
         self._h = h
         self.n = int(p.shape[0])
+        self.weighted = w is not None
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:

@@ -17,6 +17,7 @@ SDF_F32, SDF_F16X2, SDF_BF16X2 = 0, 1, 2
 SDF_LAMBDA_GLOBAL, SDF_LAMBDA_FIXED, SDF_LAMBDA_RADIUS = 0, 1, 2
 SDF_RADIUS_FALLBACK_K = 32
 SDF_ENGINE_AUTO, SDF_ENGINE_ALU, SDF_ENGINE_TENSOR = 0, 1, 2
+SDF_FORMULA_BLEND, SDF_FORMULA_LSE = 0, 1
 SDF_DEV_WAIT_TIMEOUT, SDF_DEV_BAD_INPUT = 1, 2
 SDF_K_PREPASS, SDF_K_FWD, SDF_K_MERGE, SDF_K_BUILD, SDF_K_FWD_GRAD, SDF_K_BWD, SDF_K_FWD_TC = 0, 1, 2, 3, 4, 5, 6
 SDF_K_RADIUS, SDF_K_KNN = 7, 8
@@ -37,7 +38,7 @@ class SdfError(RuntimeError):
 class sdf_query_opts(ctypes.Structure):
     _fields_ = [("lambda_mode", ctypes.c_int32), ("precision", ctypes.c_int32), ("C", ctypes.c_float),
                 ("fixed_lambda", ctypes.c_float), ("offset", ctypes.c_float), ("split_n", ctypes.c_int32),
-                ("engine", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("engine", ctypes.c_int32), ("formula", ctypes.c_int32)]
 
 
 # (name, restype, argtypes) for every entry point of include/ptsdf.h
@@ -61,6 +62,7 @@ SIGNATURES = {
     "sdf_knn_mean_distance": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
                                              ctypes.c_void_p]),
     "sdf_build": (ctypes.c_int, [_P, _P, _P, _I64, _P, ctypes.POINTER(_P)]),
+    "sdf_build_weighted": (ctypes.c_int, [_P, _P, _P, _P, _I64, _P, ctypes.POINTER(_P)]),
     "sdf_destroy": (ctypes.c_int, [_P]),
     "sdf_cloud_info": (ctypes.c_int, [_P, ctypes.POINTER(_I64), ctypes.POINTER(_F), ctypes.POINTER(_I64),
                                       ctypes.POINTER(_I64)]),
@@ -114,9 +116,10 @@ def check(status: int, what: str = ""):
 
 def make_opts(C: float = 64.0, lambda_mode: int = SDF_LAMBDA_GLOBAL, fixed_lambda: float = 0.0,
               offset: float = 0.0, split_n: int = 0, precision: int = SDF_F32,
-              engine: int = SDF_ENGINE_AUTO) -> sdf_query_opts:
+              engine: int = SDF_ENGINE_AUTO, formula: int = SDF_FORMULA_BLEND) -> sdf_query_opts:
     o = sdf_query_opts()
     check(lib().sdf_opts_default(ctypes.byref(o)))
-    o.C, o.lambda_mode, o.fixed_lambda, o.offset, o.split_n, o.precision, o.engine = (
-        float(C), int(lambda_mode), float(fixed_lambda), float(offset), int(split_n), int(precision), int(engine))
+    o.C, o.lambda_mode, o.fixed_lambda, o.offset, o.split_n, o.precision, o.engine, o.formula = (
+        float(C), int(lambda_mode), float(fixed_lambda), float(offset), int(split_n), int(precision), int(engine),
+        int(formula))
     return o

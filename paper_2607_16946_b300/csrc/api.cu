@@ -47,7 +47,18 @@ sdf_status check_opts(const sdf_query_opts& o, const char* fn) {
         return set_error(SDF_EINVAL, std::string(fn) + ": unknown engine");
     if (o.engine == SDF_ENGINE_TENSOR && o.precision != SDF_F32)
         return set_error(SDF_EINVAL, std::string(fn) + ": the tensor-core engine computes in FP32 only");
+    if (o.formula != SDF_FORMULA_BLEND && o.formula != SDF_FORMULA_LSE)
+        return set_error(SDF_EINVAL, std::string(fn) + ": unknown formula");
+    if (o.formula == SDF_FORMULA_LSE && o.lambda_mode == SDF_LAMBDA_FIXED && !(o.fixed_lambda > 0.f))
+        return set_error(SDF_EINVAL, std::string(fn) + ": the log-sum-exp distance needs fixed_lambda > 0");
     return SDF_OK;
+}
+
+// The gradient-type calls evaluate the blend only.
+sdf_status blend_only(const sdf_query_opts& o, const char* fn) {
+    return o.formula == SDF_FORMULA_BLEND
+               ? SDF_OK
+               : set_error(SDF_EINVAL, std::string(fn) + ": the log-sum-exp distance is for sdf_query only");
 }
 
 // Booleans of two phi arrays (Sec. 6): union min, intersection max, difference max(a, -b)
@@ -78,7 +89,7 @@ extern "C" sdf_status sdf_opts_default(sdf_query_opts* o) {
     o->offset = 0.f;
     o->split_n = 0;
     o->engine = SDF_ENGINE_AUTO;
-    o->reserved = 0;
+    o->formula = SDF_FORMULA_BLEND;
     return SDF_OK;
 }
 
@@ -100,7 +111,8 @@ extern "C" sdf_status sdf_query_grad(sdf_cloud cloud, const float* d_x, int64_t 
     if (!cloud) return set_error(SDF_EINVAL, "sdf_query_grad: cloud is NULL");
     if (q < 0) return set_error(SDF_EINVAL, "sdf_query_grad: q < 0");
     const sdf_query_opts o = resolve_opts(opts);
-    const sdf_status s = check_opts(o, "sdf_query_grad");
+    sdf_status s = check_opts(o, "sdf_query_grad");
+    if (s == SDF_OK) s = blend_only(o, "sdf_query_grad");
     if (s != SDF_OK) return s;
     if (o.precision != SDF_F32) return set_error(SDF_EINVAL, "sdf_query_grad: gradients are computed in FP32 only");
     if (o.lambda_mode == SDF_LAMBDA_RADIUS)
@@ -118,7 +130,8 @@ extern "C" sdf_status sdf_query_laplacian(sdf_cloud cloud, const float* d_x, int
     if (!cloud) return set_error(SDF_EINVAL, "sdf_query_laplacian: cloud is NULL");
     if (q < 0) return set_error(SDF_EINVAL, "sdf_query_laplacian: q < 0");
     const sdf_query_opts o = resolve_opts(opts);
-    const sdf_status s = check_opts(o, "sdf_query_laplacian");
+    sdf_status s = check_opts(o, "sdf_query_laplacian");
+    if (s == SDF_OK) s = blend_only(o, "sdf_query_laplacian");
     if (s != SDF_OK) return s;
     if (o.precision != SDF_F32 || o.engine == SDF_ENGINE_TENSOR)
         return set_error(SDF_EINVAL, "sdf_query_laplacian: FP32 on the FP32 units only");
@@ -137,7 +150,8 @@ extern "C" sdf_status sdf_backward_params(sdf_cloud cloud, const float* d_x, int
     if (q < 0) return set_error(SDF_EINVAL, "sdf_backward_params: q < 0");
     if (!d_grad_params) return set_error(SDF_EINVAL, "sdf_backward_params: NULL output");
     const sdf_query_opts o = resolve_opts(opts);
-    const sdf_status s = check_opts(o, "sdf_backward_params");
+    sdf_status s = check_opts(o, "sdf_backward_params");
+    if (s == SDF_OK) s = blend_only(o, "sdf_backward_params");
     if (s != SDF_OK) return s;
     if (o.precision != SDF_F32)
         return set_error(SDF_EINVAL, "sdf_backward_params: gradients are computed in FP32 only");
@@ -163,7 +177,8 @@ extern "C" sdf_status sdf_trace(sdf_cloud cloud, const float* d_origins, const f
     if (max_steps < 1 || !(eps > 0.f) || !(t_max > 0.f) || !std::isfinite(t_max))
         return set_error(SDF_EINVAL, "sdf_trace: need max_steps >= 1, eps > 0, finite t_max > 0");
     const sdf_query_opts o = resolve_opts(opts);
-    const sdf_status s = check_opts(o, "sdf_trace");
+    sdf_status s = check_opts(o, "sdf_trace");
+    if (s == SDF_OK) s = blend_only(o, "sdf_trace");
     if (s != SDF_OK) return s;
     if (nrays == 0) return SDF_OK;
     if (!d_origins || !d_dirs || !d_t_hit || !d_steps) return set_error(SDF_EINVAL, "sdf_trace: NULL buffer");

@@ -53,7 +53,8 @@ __global__ void k_bwd_prep(const float* __restrict__ saved, const float* __restr
     }
 }
 
-template <bool KAPPA>
+// WEIGHTED: the weight is multiplied by this point's weight A_i (r3.w).
+template <bool KAPPA, bool WEIGHTED>
 __device__ __forceinline__ void bwd_tile(const float4* __restrict__ tile, const float4& r0, const float4& r1,
                                          const float4& r2, const float4& r3, float (&acc)[kNAcc]) {
 #pragma unroll 1
@@ -62,7 +63,8 @@ __device__ __forceinline__ void bwd_tile(const float4* __restrict__ tile, const 
         const float x = qa.x, y = qa.y, z = qa.z;
         const float dx = x - r0.x, dy = y - r0.y, dz = z - r0.z;
         const float d = sqrt_mufu(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
-        const float cw = qb.y * ex2_mufu(fmaf(-qa.w, d, qb.x));   // (G/W) w
+        const float cw = qb.y * (WEIGHTED ? ex2_mufu(fmaf(-qa.w, d, qb.x)) * r3.w
+                                          : ex2_mufu(fmaf(-qa.w, d, qb.x)));   // (G/W) w
         if (!KAPPA) {
             const float vx = x - r1.x, vy = y - r1.y, vz = z - r1.z;
             const float h = fmaf(vx, r2.x, fmaf(vy, r2.y, vz * r2.z));
@@ -115,6 +117,7 @@ __device__ __forceinline__ void bwd_tile(const float4* __restrict__ tile, const 
     }
 }
 
+template <bool WEIGHTED>
 __global__ void __launch_bounds__(kThreads) k_bwd_params(const float4* __restrict__ rec, int64_t slots,
                                                          int64_t direct_slots, const float4* __restrict__ qrec,
                                                          int64_t qtiles, int64_t qtiles_per_chunk,
@@ -148,9 +151,9 @@ __global__ void __launch_bounds__(kThreads) k_bwd_params(const float4* __restric
 #pragma unroll
         for (int k = 0; k < kNAcc; ++k) tacc[k] = 0.f;
         if (kappa)
-            bwd_tile<true>(tile, r0, r1, r2, r3, tacc);
+            bwd_tile<true, WEIGHTED>(tile, r0, r1, r2, r3, tacc);
         else
-            bwd_tile<false>(tile, r0, r1, r2, r3, tacc);
+            bwd_tile<false, WEIGHTED>(tile, r0, r1, r2, r3, tacc);
 #pragma unroll
         for (int k = 0; k < kNAcc; ++k) acc[k] += tacc[k];
         ring.release(t, lane);
@@ -254,7 +257,8 @@ sdf_status launch_backward_params(const Cloud& c, int64_t q, const float* d_save
         k_bwd_prep<<<(unsigned)((qp + 255) / 256), 256, 0, st>>>(d_saved, d_grad_phi, q, qp, qrec);
         e = cudaGetLastError();
         if (e == cudaSuccess) {
-            k_bwd_params<<<dim3((unsigned)pblocks, (unsigned)nchunks), kThreads, kStages * kQTileBytes, st>>>(
+            (c.weighted ? k_bwd_params<true> : k_bwd_params<false>)<<<dim3((unsigned)pblocks, (unsigned)nchunks),
+                                                                     kThreads, kStages * kQTileBytes, st>>>(
                 c.rec, slots, direct_slots, qrec, qtiles, per, part, c.status);
             e = cudaGetLastError();
         }

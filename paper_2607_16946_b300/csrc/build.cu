@@ -66,11 +66,14 @@ __global__ void k_aabb(const float* __restrict__ pts, int64_t n, float* __restri
     }
 }
 
-// One point: returns the record (16 floats) and its kind (0 direct, 1 kappa);
-// sets *bad for a zero / non-finite normal or non-finite input.
+// One point: returns the record (16 floats) and its kind (0 direct, 1 kappa,
+// 2 kappa with kappa_min = 0); sets *bad for a zero / non-finite normal,
+// non-finite input or a weight outside [2^-64, 2^64].  Both record forms
+// carry the point's weight A_i in their last float (1 without weights),
+// which the pair loops multiply onto w_i.
 __global__ void k_fit(const float* __restrict__ P, const float* __restrict__ Nrm, const float* __restrict__ A6,
-                      int64_t n, double thr, float* __restrict__ rec_tmp, int8_t* __restrict__ kind,
-                      int32_t* __restrict__ status) {
+                      const float* __restrict__ Wt, int64_t n, double thr, float* __restrict__ rec_tmp,
+                      int8_t* __restrict__ kind, int32_t* __restrict__ status) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     double p[3], nv[3], a[6];
@@ -83,6 +86,11 @@ __global__ void k_fit(const float* __restrict__ P, const float* __restrict__ Nrm
     for (int k = 0; k < 6; ++k) {
         a[k] = A6[6 * i + k];
         finite = finite && isfinite(a[k]);
+    }
+    float wa = 1.f;
+    if (Wt) {
+        wa = Wt[i];
+        finite = finite && wa >= 0x1p-64f && wa <= 0x1p64f;   // keeps every sum inside FP32's range
     }
     const double len = sqrt(nv[0] * nv[0] + nv[1] * nv[1] + nv[2] * nv[2]);
     float* out = rec_tmp + (size_t)i * kRecFloats;
@@ -110,7 +118,7 @@ __global__ void k_fit(const float* __restrict__ P, const float* __restrict__ Nrm
         out[0] = (float)p[0]; out[1] = (float)p[1]; out[2] = (float)p[2]; out[3] = (float)sT;
         out[4] = (float)c[0]; out[5] = (float)c[1]; out[6] = (float)c[2]; out[7] = (float)R;
         out[8] = (float)u[0]; out[9] = (float)u[1]; out[10] = (float)u[2]; out[11] = (float)(-sT * r);
-        out[12] = 0.f; out[13] = 0.f; out[14] = 0.f; out[15] = 0.f;
+        out[12] = 0.f; out[13] = 0.f; out[14] = 0.f; out[15] = wa;
         kind[i] = 0;
     } else {
         const double zeta = -sgn_convex(kmin);
@@ -118,7 +126,7 @@ __global__ void k_fit(const float* __restrict__ P, const float* __restrict__ Nrm
         out[4] = (float)q[0]; out[5] = (float)q[1]; out[6] = (float)q[2]; out[7] = (float)fabs(kmin);
         out[8] = (float)u[0]; out[9] = (float)u[1]; out[10] = (float)u[2]; out[11] = (float)(-kmax);
         out[12] = (float)(2.0 * zeta * nstar[0]); out[13] = (float)(2.0 * zeta * nstar[1]);
-        out[14] = (float)(2.0 * zeta * nstar[2]); out[15] = 0.f;
+        out[14] = (float)(2.0 * zeta * nstar[2]); out[15] = wa;
         kind[i] = out[7] == 0.f ? 2 : 1;   // 2: kappa_min = 0 (cylinders, planes): the shorter formula
     }
 }
@@ -201,8 +209,9 @@ __global__ void k_partition(const float4* __restrict__ rec_tmp, const int8_t* __
 }
 
 // Records in the Morton order of the prepass array (compact position order[m]:
-// direct points first, then kappa-form ones), flagged r3.w = 1 for the kappa
-// form, for the radius-limited evaluation and the k-nearest searches.
+// direct points first, then kappa-form ones), for the radius-limited
+// evaluation and the k-nearest searches.  The form is read back from r0.w:
+// sT = +-1 in the direct form, 2 zeta = +-2 in the kappa form.
 __global__ void k_gather_morton(const float4* __restrict__ rec, const int32_t* __restrict__ order,
                                 const int32_t* __restrict__ perm, int64_t n, int64_t n_direct, int64_t tiles_direct,
                                 float4* __restrict__ mrec, int32_t* __restrict__ mperm) {
@@ -211,10 +220,7 @@ __global__ void k_gather_morton(const float4* __restrict__ rec, const int32_t* _
     const int64_t cpos = order[m];
     const bool kappa = cpos >= n_direct;
     const int64_t slot = kappa ? tiles_direct * kTileRecs + (cpos - n_direct) : cpos;
-    for (int k = 0; k < 3; ++k) mrec[4 * m + k] = rec[4 * slot + k];
-    float4 r3 = rec[4 * slot + 3];
-    r3.w = kappa ? 1.f : 0.f;
-    mrec[4 * m + 3] = r3;
+    for (int k = 0; k < 4; ++k) mrec[4 * m + k] = rec[4 * slot + k];
     mperm[m] = perm[slot];
 }
 
@@ -316,6 +322,11 @@ void free_cloud(Cloud* c) {
 
 extern "C" sdf_status sdf_build(const float* d_points, const float* d_normals, const float* d_params, int64_t n,
                                 void* stream, sdf_cloud* out) {
+    return sdf_build_weighted(d_points, d_normals, d_params, nullptr, n, stream, out);
+}
+
+extern "C" sdf_status sdf_build_weighted(const float* d_points, const float* d_normals, const float* d_params,
+                                         const float* d_weights, int64_t n, void* stream, sdf_cloud* out) {
     if (!out) return set_error(SDF_EINVAL, "sdf_build: out is NULL");
     *out = nullptr;
     if (n < 1 || n > 0x7fffffffLL) return set_error(SDF_EINVAL, "sdf_build: n must be in [1, 2^31-1]");
@@ -323,6 +334,7 @@ extern "C" sdf_status sdf_build(const float* d_points, const float* d_normals, c
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     Cloud* c = new Cloud();
     c->n = n;
+    c->weighted = d_weights != nullptr;
     cudaError_t e = cudaGetDevice(&c->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
     if (e != cudaSuccess) {
@@ -376,7 +388,7 @@ extern "C" sdf_status sdf_build(const float* d_points, const float* d_normals, c
 
     const int fit_threads = 128;
     k_fit<<<(unsigned)((n + fit_threads - 1) / fit_threads), fit_threads, 0, st>>>(
-        c->src_points, c->src_normals, c->src_params, n, thr, rec_tmp, kind, c->status);
+        c->src_points, c->src_normals, c->src_params, d_weights, n, thr, rec_tmp, kind, c->status);
     PTSDF_TRY(cudaGetLastError(), "sdf_build: k_fit launch");
     k_count<<<1, kPartThreads, 0, st>>>(kind, n, counts);
     PTSDF_TRY(cudaGetLastError(), "sdf_build: k_count launch");
@@ -387,7 +399,8 @@ extern "C" sdf_status sdf_build(const float* d_points, const float* d_normals, c
     PTSDF_TRY(cudaStreamSynchronize(st), "sdf_build: sync");
     if (hstatus & SDF_DEV_BAD_INPUT) {
         fail(cudaSuccess, "");
-        return set_error(SDF_EINVAL, "sdf_build: zero or non-finite normal, or non-finite point / coefficient");
+        return set_error(SDF_EINVAL, "sdf_build: zero or non-finite normal, non-finite point / coefficient, or a "
+                                     "weight outside [2^-64, 2^64]");
     }
     c->n_direct = hcounts[0];
     c->n_kappa_flat = hcounts[2];

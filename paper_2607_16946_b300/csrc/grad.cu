@@ -55,8 +55,10 @@ struct GradArgs {
     float* part;             // split x Q x accumulator partials (split > 1)
 };
 
-// Accumulates one tile of pairs for one query into acc[].
-template <bool KAPPA, bool LAP>
+// Accumulates one tile of pairs for one query into acc[].  WEIGHTED: each
+// weight is multiplied by the point's weight A_i (record r3.w); A_i does not
+// depend on x, so every sum below is weighted the same way.
+template <bool KAPPA, bool LAP, bool WEIGHTED>
 __device__ __forceinline__ void grad_tile(const float4* __restrict__ tile, int cnt, float x, float y, float z,
                                           float L, float A0, float (&acc)[NAcc<LAP>::value]) {
 #pragma unroll 1
@@ -115,7 +117,7 @@ __device__ __forceinline__ void grad_tile(const float4* __restrict__ tile, int c
             // lap g = (K + k (K a' + zeta) / s1) / s2
             if (LAP) lapg = fmaf(r1.w * fmaf(r2.w, ap, 0.5f * r0.w), rs1, r2.w) * rs2;
         }
-        const float w = ex2_mufu(fmaf(-L, d, A0));
+        const float w = WEIGHTED ? ex2_mufu(fmaf(-L, d, A0)) * tile[4 * j + 3].w : ex2_mufu(fmaf(-L, d, A0));
         const float wg = w * g;
         const float wn = w * rd, wgn = wg * rd;
         acc[A_W] += w;
@@ -254,7 +256,7 @@ __device__ __forceinline__ void finalize(const GradArgs& ga, int64_t qi, float x
     }
 }
 
-template <bool LAP>
+template <bool LAP, bool WEIGHTED>
 __global__ void __launch_bounds__(kThreads) k_fwd_grad(const float4* __restrict__ rec, int64_t n_direct,
                                                        int64_t n_kappa, int64_t tiles_direct, int64_t tiles_total,
                                                        int64_t tiles_per_chunk, GradArgs ga, int32_t* status) {
@@ -293,9 +295,9 @@ __global__ void __launch_bounds__(kThreads) k_fwd_grad(const float4* __restrict_
 #pragma unroll
         for (int k = 0; k < kAcc; ++k) tacc[k] = 0.f;
         if (kappa)
-            grad_tile<true, LAP>(tile, cnt, x, y, z, ql.L, ql.A0, tacc);
+            grad_tile<true, LAP, WEIGHTED>(tile, cnt, x, y, z, ql.L, ql.A0, tacc);
         else
-            grad_tile<false, LAP>(tile, cnt, x, y, z, ql.L, ql.A0, tacc);
+            grad_tile<false, LAP, WEIGHTED>(tile, cnt, x, y, z, ql.L, ql.A0, tacc);
 #pragma unroll
         for (int k = 0; k < kAcc; ++k) acc[k] += tacc[k];
         ring.release(t, lane);
@@ -393,7 +395,8 @@ sdf_status launch_query_grad(const Cloud& c, const float* d_x, int64_t q, float*
     }
     if (e == cudaSuccess) {
         ProfRange pr(SDF_K_FWD_GRAD, st);
-        auto kern = lap ? k_fwd_grad<true> : k_fwd_grad<false>;
+        auto kern = lap ? (c.weighted ? k_fwd_grad<true, true> : k_fwd_grad<true, false>)
+                        : (c.weighted ? k_fwd_grad<false, true> : k_fwd_grad<false, false>);
         kern<<<grid, kThreads, kStages * kTileBytes, st>>>(c.rec, c.n_direct, c.n_kappa, c.tiles_direct,
                                                           c.tiles_direct + c.tiles_kappa, p.tiles_per_chunk, ga,
                                                           c.status);

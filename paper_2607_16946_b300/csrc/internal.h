@@ -68,6 +68,7 @@ struct Cloud {
     int64_t n = 0;                   // points
     int64_t n_direct = 0, n_kappa = 0;
     int64_t n_kappa_flat = 0;        // kappa-form points with kappa_min = 0, first in the kappa segment
+    bool weighted = false;           // built with per-point weights (record r3.w; 1 otherwise)
     int64_t tiles_direct = 0, tiles_kappa = 0;
     int64_t pre_tiles = 0;
     float aabb_diag = 0.f;
@@ -147,6 +148,7 @@ struct TcQuery {
     int mode = SDF_LAMBDA_GLOBAL;
     float C = 64.f, lam = 0.f, offset = 0.f;
     int part_base = 0;
+    int formula = SDF_FORMULA_BLEND;
 };
 sdf_status build_btiles(Cloud& c, cudaStream_t st);
 // The tensor-core loop takes tiles [0, tc_tiles_end(c)): every tile, or

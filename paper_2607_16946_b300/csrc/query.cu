@@ -80,14 +80,17 @@ __device__ __forceinline__ void weights2(float a0, float a1, float& w0, float& w
     }
 }
 
-template <bool KAPPA, int PREC, bool FLAT = false>
+// WEIGHTED: every weight is multiplied by the point's weight A_i (record r3.w),
+// after the exponential, so that the packed-half exponentials keep their
+// arguments near 0 for the points that matter.
+template <bool KAPPA, int PREC, bool WEIGHTED, bool FLAT = false>
 __device__ __forceinline__ void pair_tile(const float4* __restrict__ tile, int cnt, QState (&qs)[kQueriesPerThread]) {
     static_assert(kQueriesPerThread % 2 == 0, "queries are paired for the packed weights");
 #pragma unroll kUnrollPts
     for (int j = 0; j < cnt; ++j) {
         const float4 r0 = tile[4 * j], r1 = tile[4 * j + 1], r2 = tile[4 * j + 2];
-        float4 r3;
-        if (KAPPA) r3 = tile[4 * j + 3];
+        float4 r3 = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (KAPPA || WEIGHTED) r3 = tile[4 * j + 3];
 #pragma unroll
         for (int k = 0; k < kQueriesPerThread; k += 2) {
             float arg[2], g[2];
@@ -102,6 +105,10 @@ __device__ __forceinline__ void pair_tile(const float4* __restrict__ tile, int c
             }
             float w0, w1;
             weights2<PREC>(arg[0], arg[1], w0, w1);
+            if (WEIGHTED) {
+                w0 *= r3.w;
+                w1 *= r3.w;
+            }
             qs[k].w += w0;
             qs[k].s = fmaf(w0, g[0], qs[k].s);
             qs[k + 1].w += w1;
@@ -113,7 +120,7 @@ __device__ __forceinline__ void pair_tile(const float4* __restrict__ tile, int c
 // --------------------------------------------------------------------------
 // Forward pass
 // --------------------------------------------------------------------------
-template <int PREC>
+template <int PREC, bool WEIGHTED>
 __global__ void __launch_bounds__(kThreads, kFwdMinBlocks) k_fwd(const float4* __restrict__ rec, int64_t n_direct, int64_t n_kappa,
                                                   int64_t tiles_direct, int64_t tiles_total, int64_t tiles_per_chunk,
                                                   QueryArgs a, int32_t* status, int64_t n_kappa_flat) {
@@ -141,22 +148,8 @@ __global__ void __launch_bounds__(kThreads, kFwdMinBlocks) k_fwd(const float4* _
         qs[k].x = a.x[3 * qq];
         qs[k].y = a.x[3 * qq + 1];
         qs[k].z = a.x[3 * qq + 2];
-        float2 d2 = a.d2[qq];
-        for (int c = 1; c < a.pre_split; ++c) {
-            const float2 v = a.d2[(size_t)c * a.q + qq];
-            d2.x = fmaxf(d2.x, v.x);
-            d2.y = fminf(d2.y, v.y);
-        }
-        const float dmin = sqrtf(fmaxf(d2.y, 0.f));
-        float lam = a.lam;
-        if (a.mode == SDF_LAMBDA_GLOBAL) {
-            // lambda_x = C / sigma_x = 2 C / d_max (Eq. RelationshipBetweenLambdaAndRadius);
-            // d_max = 0 (one point, at the query) takes lambda = 0
-            const float dmax = sqrtf(fmaxf(d2.x, 0.f));
-            lam = dmax > 0.f ? 2.f * a.C / dmax : 0.f;
-        }
-        qs[k].L = lam * kLog2e;
-        qs[k].A0 = qs[k].L * dmin;   // exponent -L (d - d_min)
+        // exponent A0 - L d = -lambda_x (d - d_min) log2(e)
+        query_screening(a.d2, a.pre_split, a.q, qq, a.mode, a.C, a.lam, qs[k].L, qs[k].A0);
         qs[k].W = qs[k].S = 0.f;
     }
     for (int64_t t = 0; t < nt; ++t) {
@@ -170,11 +163,11 @@ __global__ void __launch_bounds__(kThreads, kFwdMinBlocks) k_fwd(const float4* _
 #pragma unroll
         for (int k = 0; k < kQueriesPerThread; ++k) qs[k].w = qs[k].s = 0.f;
         if (kappa && first + kTileRecs <= n_kappa_flat)   // every record of the tile has kappa_min = 0
-            pair_tile<true, PREC, true>(tile, cnt, qs);
+            pair_tile<true, PREC, WEIGHTED, true>(tile, cnt, qs);
         else if (kappa)
-            pair_tile<true, PREC>(tile, cnt, qs);
+            pair_tile<true, PREC, WEIGHTED>(tile, cnt, qs);
         else
-            pair_tile<false, PREC>(tile, cnt, qs);
+            pair_tile<false, PREC, WEIGHTED>(tile, cnt, qs);
         // blocked summation: tile partials are added to the totals once per
         // tile, which keeps the FP32 rounding of long sums small
 #pragma unroll
@@ -188,10 +181,20 @@ __global__ void __launch_bounds__(kThreads, kFwdMinBlocks) k_fwd(const float4* _
     for (int k = 0; k < kQueriesPerThread; ++k) {
         if (qi[k] >= a.q) continue;
         if (a.split == 1)
-            a.phi[qi[k]] = __fdiv_rn(qs[k].S, qs[k].W) - a.offset;
+            a.phi[qi[k]] = finish_sums(qs[k].W, qs[k].S, a.formula, qs[k].L, qs[k].A0, a.offset);
         else
             a.part[(size_t)(a.part_base + chunk) * a.q + qi[k]] = make_float2(qs[k].W, qs[k].S);
     }
+}
+
+using FwdKernel = decltype(&k_fwd<SDF_F32, false>);
+
+FwdKernel fwd_kernel(int precision, bool weighted) {
+    if (weighted)
+        return precision == SDF_F16X2 ? k_fwd<SDF_F16X2, true> : precision == SDF_BF16X2 ? k_fwd<SDF_BF16X2, true>
+                                                                                         : k_fwd<SDF_F32, true>;
+    return precision == SDF_F16X2 ? k_fwd<SDF_F16X2, false> : precision == SDF_BF16X2 ? k_fwd<SDF_BF16X2, false>
+                                                                                       : k_fwd<SDF_F32, false>;
 }
 
 __global__ void k_merge(QueryArgs a) {
@@ -203,7 +206,9 @@ __global__ void k_merge(QueryArgs a) {
         W += v.x;
         S += v.y;
     }
-    a.phi[i] = __fdiv_rn(S, W) - a.offset;
+    float L = 0.f, A0 = 0.f;
+    if (a.formula == SDF_FORMULA_LSE) query_screening(a.d2, a.pre_split, a.q, i, a.mode, a.C, a.lam, L, A0);
+    a.phi[i] = finish_sums(W, S, a.formula, L, A0, a.offset);
 }
 
 }  // namespace
@@ -241,7 +246,8 @@ Plan make_plan(const Cloud& c, int64_t q, int split_override, int queries_per_ct
 }
 
 bool use_tensor_engine(const Cloud& c, const sdf_query_opts& o) {
-    return o.engine != SDF_ENGINE_ALU && o.precision == SDF_F32 && c.btiles != nullptr && tc_tiles_end(c) > 0;
+    return o.engine != SDF_ENGINE_ALU && o.precision == SDF_F32 && !c.weighted && c.btiles != nullptr &&
+           tc_tiles_end(c) > 0;
 }
 
 namespace {
@@ -279,6 +285,8 @@ int query_partials(const Cloud& c, int64_t q, const sdf_query_opts& o) {
 
 sdf_status launch_query(const Cloud& c, const float* d_x, int64_t q, float* d_phi, const sdf_query_opts& o,
                         cudaStream_t st) {
+    if (o.engine == SDF_ENGINE_TENSOR && c.weighted)
+        return set_error(SDF_EINVAL, "sdf_query: the tensor-core engine does not take per-point weights");
     if (o.lambda_mode == SDF_LAMBDA_RADIUS) return launch_radius_query(c, d_x, q, d_phi, o, st);
     const Plan p = make_plan(c, q, o.split_n);
     // Tensor-core engine: see TcPlan
@@ -294,6 +302,7 @@ sdf_status launch_query(const Cloud& c, const float* d_x, int64_t q, float* d_ph
     a.C = o.C;
     a.lam = o.fixed_lambda;
     a.offset = o.offset;
+    a.formula = o.formula;
     a.part = nullptr;
     a.d2 = nullptr;
     a.far = nullptr;
@@ -334,8 +343,7 @@ sdf_status launch_query(const Cloud& c, const float* d_x, int64_t q, float* d_ph
     sdf_status s = SDF_OK;
     if (e == cudaSuccess && !tc) {
         ProfRange pr(SDF_K_FWD, st);
-        auto kern = o.precision == SDF_F16X2 ? k_fwd<SDF_F16X2> : o.precision == SDF_BF16X2 ? k_fwd<SDF_BF16X2>
-                                                                                            : k_fwd<SDF_F32>;
+        const FwdKernel kern = fwd_kernel(o.precision, c.weighted);
         kern<<<grid, kThreads, kStages * kTileBytes, st>>>(c.rec, c.n_direct, c.n_kappa, c.tiles_direct,
                                                           c.tiles_direct + c.tiles_kappa, p.tiles_per_chunk, a,
                                                           c.status, c.n_kappa_flat);
@@ -357,6 +365,7 @@ sdf_status launch_query(const Cloud& c, const float* d_x, int64_t q, float* d_ph
             tq.C = a.C;
             tq.lam = a.lam;
             tq.offset = a.offset;
+            tq.formula = a.formula;
             tq.part_base = 0;
             if (tp.nd > 0) {   // one profiled range per launch
                 ProfRange pr(SDF_K_FWD_TC, st);
@@ -373,7 +382,8 @@ sdf_status launch_query(const Cloud& c, const float* d_x, int64_t q, float* d_ph
             QueryArgs ak = a;
             ak.tile_base = tp.tc_end;
             ak.part_base = tp.nd + tp.nk;
-            k_fwd<SDF_F32><<<dim3((unsigned)p.qblocks, (unsigned)tp.na), kThreads, kStages * kTileBytes, st>>>(
+            fwd_kernel(SDF_F32, c.weighted)<<<dim3((unsigned)p.qblocks, (unsigned)tp.na), kThreads,
+                                               kStages * kTileBytes, st>>>(
                 c.rec, c.n_direct, c.n_kappa, c.tiles_direct, c.tiles_direct + c.tiles_kappa, tp.tpc_a, ak, c.status,
                 c.n_kappa_flat);
             e = cudaGetLastError();
@@ -487,6 +497,7 @@ extern "C" sdf_status sdf_query_noalloc(sdf_cloud cloud, const float* d_x, int64
     a.C = o.C;
     a.lam = o.fixed_lambda;
     a.offset = o.offset;
+    a.formula = o.formula;
     a.far = nullptr;
     a.pre_split = p.split;
     a.cx = 0.5f * (c.aabb[0] + c.aabb[3]);
@@ -507,7 +518,7 @@ extern "C" sdf_status sdf_query_noalloc(sdf_cloud cloud, const float* d_x, int64
             c.pre, c.n, c.pre_tiles, p.pre_tiles_per_chunk, a, c.status);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) {
-        k_fwd<SDF_F32><<<grid, kThreads, kStages * kTileBytes, st>>>(c.rec, c.n_direct, c.n_kappa, c.tiles_direct,
+        fwd_kernel(SDF_F32, c.weighted)<<<grid, kThreads, kStages * kTileBytes, st>>>(c.rec, c.n_direct, c.n_kappa, c.tiles_direct,
                                                            c.tiles_direct + c.tiles_kappa, p.tiles_per_chunk, a,
                                                            c.status, c.n_kappa_flat);
         e = cudaGetLastError();

@@ -36,7 +36,42 @@ struct QueryArgs {
     float cloud_radius = 0.f;  // max |p'| (half the AABB diagonal): scale of the prepass's rounding
     int64_t tile_base = 0;   // first tile of chunk 0 (k_fwd)
     int part_base = 0;       // partial row of chunk 0 when several kernels share the partials
+    int formula = SDF_FORMULA_BLEND;   // what the sums finish into (finish_sums)
 };
+
+// A query's screening from its prepass partials d2p[c * q + qq] (max, min of
+// |x - p|^2): L = lambda log2(e) and A0 = L d_min, so that a point's weight is
+// exp2(A0 - L d) = exp(-lambda (d - d_min)).  GLOBAL: lambda_x = C / sigma_x =
+// 2 C / d_max (Eq. RelationshipBetweenLambdaAndRadius; d_max = 0, every point
+// at the query, takes lambda = 0); FIXED: the given lambda.
+__device__ __forceinline__ void query_screening(const float2* __restrict__ d2p, int pre_split, int64_t q, int64_t qq,
+                                                int mode, float C, float lam_fixed, float& L, float& A0) {
+    float2 d2 = d2p[qq];
+    for (int c = 1; c < pre_split; ++c) {
+        const float2 v = d2p[(size_t)c * q + qq];
+        d2.x = fmaxf(d2.x, v.x);
+        d2.y = fminf(d2.y, v.y);
+    }
+    const float dmin = sqrtf(fmaxf(d2.y, 0.f));
+    float lam = lam_fixed;
+    if (mode == SDF_LAMBDA_GLOBAL) {
+        const float dmax = sqrtf(fmaxf(d2.x, 0.f));
+        lam = dmax > 0.f ? 2.f * C / dmax : 0.f;
+    }
+    L = lam * kLog2e;
+    A0 = L * dmin;
+}
+
+// What a query's sums W = sum A_i w_i, S = sum A_i w_i g_i finish into, less
+// the offset: the blend S / W (Eq. BasicFormulaShifted), or the log-sum-exp
+// distance -(1/lambda) log sum_i A_i exp(-lambda d_i) (Eq.
+// ConvolutionalDistanceFormula, h = 1) = d_min - ln(W) / lambda =
+// (A0 - log2 W) / L; where L = 0 (GLOBAL with every point at the query) it
+// is d_min = 0.
+__device__ __forceinline__ float finish_sums(float W, float S, int formula, float L, float A0, float offset) {
+    if (formula == SDF_FORMULA_LSE) return (L > 0.f ? (A0 - log2f(W)) / L : 0.f) - offset;
+    return __fdiv_rn(S, W) - offset;
+}
 
 // --------------------------------------------------------------------------
 // Prepass

@@ -361,21 +361,8 @@ __global__ void __maxnreg__(96) k_fwd_tc(TcArgs ta, int32_t* status) {
         x = a.x[3 * qq];
         y = a.x[3 * qq + 1];
         z = a.x[3 * qq + 2];
-        float2 d2 = a.d2[qq];
-        for (int c = 1; c < a.pre_split; ++c) {
-            const float2 v = a.d2[(size_t)c * a.q + qq];
-            d2.x = fmaxf(d2.x, v.x);
-            d2.y = fminf(d2.y, v.y);
-        }
-        const float dmin = sqrtf(fmaxf(d2.y, 0.f));
-        float lam = a.lam;
-        if (a.mode == SDF_LAMBDA_GLOBAL) {
-            // lambda_x = C / sigma_x = 2 C / d_max (Eq. RelationshipBetweenLambdaAndRadius)
-            const float dmax = sqrtf(fmaxf(d2.x, 0.f));
-            lam = dmax > 0.f ? 2.f * a.C / dmax : 0.f;
-        }
-        const float L = lam * kLog2e;
-        A0 = L * dmin;      // exponent -L (d - d_min), d in world units
+        float L;            // exponent A0 - L d = -lambda_x (d - d_min) log2(e), d in world units
+        query_screening(a.d2, a.pre_split, a.q, qq, a.mode, a.C, a.lam, L, A0);
         Ls = L * ta.s;      // the same per unit of d'' = d / s
         const float xs = (x - a.cx) * ta.inv_s, ys = (y - a.cy) * ta.inv_s, zs = (z - a.cz) * ta.inv_s;
         const float xx = fmaf(xs, xs, fmaf(ys, ys, zs * zs));
@@ -524,8 +511,8 @@ __global__ void __maxnreg__(96) k_fwd_tc(TcArgs ta, int32_t* status) {
                 W += o.x;
                 S += o.y;
             }
-            if (ta.direct_out)
-                a.phi[qi] = __fdiv_rn(S, W) - a.offset;
+            if (ta.direct_out)   // Ls / s = L, the exponent's lambda log2(e) per world unit
+                a.phi[qi] = finish_sums(W, S, a.formula, Ls * ta.inv_s, A0, a.offset);
             else
                 a.part[(size_t)(a.part_base + chunk) * a.q + qi] = make_float2(W, S);
         }

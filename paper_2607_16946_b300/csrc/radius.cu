@@ -44,7 +44,7 @@ struct RadiusArgs {
     float* phi;
     const float4* spheres;
     int64_t nsph;
-    const float4* mrec;    // n x 4 float4 records in Morton order; r3.w = 1 for the kappa form
+    const float4* mrec;    // n x 4 float4 records in Morton order (r3.w: the point's weight)
     const float4* pre;     // n float4(-2 p', |p'|^2) in the same order (p' = p - AABB centre)
     int64_t n;
     float cx, cy, cz;
@@ -52,11 +52,19 @@ struct RadiusArgs {
     float reval;
     float offset;
     int kfb;
+    int lse;               // 1: the log-sum-exp distance of the set instead of the blend
 };
 
-__device__ __forceinline__ float g_record(float x, float y, float z, const float4* __restrict__ r) {
-    const float4 r0 = __ldg(r), r1 = __ldg(r + 1), r2 = __ldg(r + 2), r3 = __ldg(r + 3);
-    return r3.w != 0.f ? g_kappa(x, y, z, r0, r1, r2, r3) : g_direct(x, y, z, r1, r2, r0.w);
+// The torus SDF of one record (the form read from r0.w: sT = +-1 direct,
+// 2 zeta = +-2 kappa; 0 when only the weights are wanted) and the point's
+// weight A_i.
+__device__ __forceinline__ float g_record(float x, float y, float z, const float4* __restrict__ r, bool want_g,
+                                          float& wa) {
+    const float4 r0 = __ldg(r), r3 = __ldg(r + 3);
+    wa = r3.w;
+    if (!want_g) return 0.f;
+    const float4 r1 = __ldg(r + 1), r2 = __ldg(r + 2);
+    return fabsf(r0.w) > 1.5f ? g_kappa(x, y, z, r0, r1, r2, r3) : g_direct(x, y, z, r1, r2, r0.w);
 }
 
 __device__ __forceinline__ int sphere_count(int64_t t, int64_t n) {
@@ -159,14 +167,16 @@ __global__ void __launch_bounds__(kRadiusThreads) k_radius_query(RadiusArgs a) {
             const float d2 = dist2_pre(xs, ys, zs, a.pre, j0 + jj);
             if (!(d2 <= R2)) continue;
             const float d = sqrtf(d2);
-            const float g = g_record(x, y, z, a.mrec + 4 * (j0 + jj));
+            float wa;
+            const float g = g_record(x, y, z, a.mrec + 4 * (j0 + jj), !a.lse, wa);
             if (d < m) {
+                // a new nearest point: the sums so far are rescaled to its distance
                 const float f = inside ? exp2f(-a.L * (m - d)) : 0.f;
-                W = fmaf(W, f, 1.f);
-                S = fmaf(S, f, g);
+                W = fmaf(W, f, wa);
+                S = fmaf(S, f, wa * g);
                 m = d;
             } else {
-                const float w = exp2f(-a.L * (d - m));
+                const float w = wa * exp2f(-a.L * (d - m));
                 W += w;
                 S = fmaf(w, g, S);
             }
@@ -178,14 +188,17 @@ __global__ void __launch_bounds__(kRadiusThreads) k_radius_query(RadiusArgs a) {
         float bd[kKnnMax];
         int bi[kKnnMax];
         const int cnt = knn_scan(a, xs, ys, zs, a.kfb, -1, best, bd, bi);
-        const float d0 = sqrtf(bd[0]);
+        m = sqrtf(bd[0]);
         for (int j = 0; j < cnt; ++j) {
-            const float w = exp2f(-a.L * (sqrtf(bd[j]) - d0));
+            float wa;
+            const float g = g_record(x, y, z, a.mrec + 4 * (int64_t)bi[j], !a.lse, wa);
+            const float w = wa * exp2f(-a.L * (sqrtf(bd[j]) - m));
             W += w;
-            S = fmaf(w, g_record(x, y, z, a.mrec + 4 * (int64_t)bi[j]), S);
+            S = fmaf(w, g, S);
         }
     }
-    a.phi[qi] = __fdiv_rn(S, W) - a.offset;
+    // the blend, or the log-sum-exp distance m - ln(W) / lambda = m - log2(W) / L
+    a.phi[qi] = (a.lse ? m - log2f(W) / a.L : __fdiv_rn(S, W)) - a.offset;
 }
 
 // Per point: mean of the distances to its k nearest other points; one
@@ -258,6 +271,7 @@ RadiusArgs radius_args(const Cloud& c) {
     a.reval = 0.f;
     a.offset = 0.f;
     a.kfb = kRadiusFallbackK;
+    a.lse = 0;
     return a;
 }
 
@@ -272,6 +286,7 @@ sdf_status launch_radius_query(const Cloud& c, const float* d_x, int64_t q, floa
     a.L = o.fixed_lambda * 1.4426950408889634f;
     a.reval = 2.f * o.C / o.fixed_lambda;
     a.offset = o.offset;
+    a.lse = o.formula == SDF_FORMULA_LSE ? 1 : 0;
     ProfRange pr(SDF_K_RADIUS, st);
     k_radius_query<<<(unsigned)((q + kRadiusThreads - 1) / kRadiusThreads), kRadiusThreads, 0, st>>>(a);
     const cudaError_t e = cudaGetLastError();

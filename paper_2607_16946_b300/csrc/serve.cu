@@ -336,7 +336,10 @@ extern "C" sdf_status sdf_serve_submit(sdf_server srv, const sdf_request* req, u
          r.opts.lambda_mode != SDF_LAMBDA_RADIUS) ||
         (r.opts.lambda_mode == SDF_LAMBDA_RADIUS &&
          (r.kind == SDF_REQ_GRAD || !(r.opts.fixed_lambda > 0.f) || r.opts.precision != SDF_F32 ||
-          r.opts.engine == SDF_ENGINE_TENSOR)))
+          r.opts.engine == SDF_ENGINE_TENSOR)) ||
+        (r.opts.formula != SDF_FORMULA_BLEND && r.opts.formula != SDF_FORMULA_LSE) ||
+        (r.opts.formula == SDF_FORMULA_LSE &&
+         (r.kind != SDF_REQ_QUERY || (r.opts.lambda_mode == SDF_LAMBDA_FIXED && !(r.opts.fixed_lambda > 0.f)))))
         return set_error(SDF_EINVAL, "sdf_serve_submit: bad options");
     auto R = std::make_shared<Request>();
     R->r = r;

@@ -40,12 +40,12 @@ def run(ptsdf, cloud, x, lam, C=64.0, **kw):
     return phi.cpu().numpy().astype(np.float64)
 
 
-def check_against_oracle(orc, p, x, got, lam, C=64.0, tol=None):
+def check_against_oracle(orc, p, x, got, lam, C=64.0, tol=None, lse=False):
     """Element-wise check; queries whose sets FP32 may decide either way are
     accepted against either oracle variant."""
     R = 2.0 * C / lam
     tol = TOL_REL * aabb_diag(p) if tol is None else tol
-    ref = orc.phi_radius(x, lam=lam, reval=R)
+    ref = orc.phi_radius(x, lam=lam, reval=R, lse=lse)
     d = np.sqrt(((x[:, None, :].astype(np.float64) - p[None, :, :].astype(np.float64)) ** 2).sum(-1))
     near_edge = (np.abs(d - R) < 1e-5 * R).any(1)
     part = np.partition(d, [31, 32], axis=1) if d.shape[1] > 32 else None
@@ -53,8 +53,8 @@ def check_against_oracle(orc, p, x, got, lam, C=64.0, tol=None):
     amb = near_edge | knn_tie
     ok = np.abs(got - ref) <= tol
     if amb.any():
-        lo = orc.phi_radius(x[amb], lam=lam, reval=R * (1 - 2e-5))
-        hi = orc.phi_radius(x[amb], lam=lam, reval=R * (1 + 2e-5))
+        lo = orc.phi_radius(x[amb], lam=lam, reval=R * (1 - 2e-5), lse=lse)
+        hi = orc.phi_radius(x[amb], lam=lam, reval=R * (1 + 2e-5), lse=lse)
         ok[amb] |= (np.abs(got[amb] - lo) <= tol) | (np.abs(got[amb] - hi) <= tol)
     assert ok.all(), (np.abs(got - ref)[~ok][:5], np.nonzero(~ok)[0][:5], amb.sum())
     return amb.sum()
