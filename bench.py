@@ -542,37 +542,51 @@ def run_mesh_leg(dev, cloud, x, phi, steps: int = 3):
 def run_mixed_leg(dev, cloud, x, phi, points, normals, params, steps: int = 2):
     """The dense-grid step on each engine and precision: FP32 on the tensor
     cores (the default), FP32 on the FP32 units, and packed-half weights
-    (SDF_F16X2, SDF_BF16X2, FP32 units): device Gpairs/s, and the error against
+    (SDF_F16X2, SDF_BF16X2, FP32 units); and the two other forms of the sum:
+    the log-sum-exp distance on the tensor cores, and the blend with seeded
+    per-point weights (FP32 units).  Device Gpairs/s, and the error against
     the FP64 oracle on 4,096 seeded grid nodes, relative to the AABB diagonal."""
     import torch
 
     import oracle
+    import paper_2607_16946_b300 as ptsdf
     import synth
     from paper_2607_16946_b300 import _abi
     rng = np.random.Generator(np.random.PCG64(SEED + 11))
     idx = rng.integers(0, GRID_RES ** 3, size=4096)
-    ref = oracle.Cloud(points, normals, params).phi(synth.grid_query_index(idx, GRID_RES))
+    xs = synth.grid_query_index(idx, GRID_RES)
+    orc = oracle.Cloud(points, normals, params)
+    ref = orc.phi(xs)
+    weights = np.exp(np.random.Generator(np.random.PCG64(SEED + 12)).uniform(np.log(0.5), np.log(2.0),
+                                                                             size=len(points))).astype(np.float32)
+    wcloud = ptsdf.Cloud(points, normals, params, weights=weights)
+    cases = (("fp32_tensor", cloud, dict(precision=_abi.SDF_F32, engine=_abi.SDF_ENGINE_TENSOR), ref),
+             ("fp32_alu", cloud, dict(precision=_abi.SDF_F32, engine=_abi.SDF_ENGINE_ALU), ref),
+             ("f16x2", cloud, dict(precision=_abi.SDF_F16X2, engine=_abi.SDF_ENGINE_ALU), ref),
+             ("bf16x2", cloud, dict(precision=_abi.SDF_BF16X2, engine=_abi.SDF_ENGINE_ALU), ref),
+             ("lse_tensor", cloud, dict(formula=_abi.SDF_FORMULA_LSE, engine=_abi.SDF_ENGINE_TENSOR), orc.lse(xs)),
+             ("weighted_fp32_alu", wcloud, dict(), oracle.Cloud(points, normals, params, weights=weights).phi(xs)))
     diag = float(np.linalg.norm(points.max(0) - points.min(0)))
     out = {}
-    for name, code, eng in (("fp32_tensor", _abi.SDF_F32, _abi.SDF_ENGINE_TENSOR),
-                            ("fp32_alu", _abi.SDF_F32, _abi.SDF_ENGINE_ALU),
-                            ("f16x2", _abi.SDF_F16X2, _abi.SDF_ENGINE_ALU),
-                            ("bf16x2", _abi.SDF_BF16X2, _abi.SDF_ENGINE_ALU)):
-        cloud.query(x, out=phi, precision=code, engine=eng)
+    for name, cl, kw, r in cases:
+        cl.query(x, out=phi, **kw)
         torch.cuda.synchronize(dev)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
         for _ in range(steps):
-            cloud.query(x, out=phi, precision=code, engine=eng)
+            cl.query(x, out=phi, **kw)
         e1.record()
         torch.cuda.synchronize(dev)
         s = e0.elapsed_time(e1) / 1e3 / steps
-        err = np.abs(phi[torch.as_tensor(idx, device=dev)].double().cpu().numpy() - ref) / diag
+        err = np.abs(phi[torch.as_tensor(idx, device=dev)].double().cpu().numpy() - r) / diag
         out[name] = {"value": x.shape[0] * N_POINTS / s / 1e9, "unit": UNIT, "ms_per_step": s * 1e3,
                      "err_max_rel_diag": float(err.max()), "err_p99_rel_diag": float(np.quantile(err, 0.99))}
+    wcloud.close()
     out["note"] = ("fp32_tensor: products on the tensor cores (split f16, FP32 accumulate), pairs finished in "
                    "FP32; fp32_alu: FP32 units only; f16x2/bf16x2: packed-half exp2 of a lane's two weights on "
-                   "the FP32-unit loop; error = |phi - phi_oracle| / AABB diagonal on 4096 seeded grid nodes")
+                   "the FP32-unit loop; lse_tensor: the log-sum-exp distance (Eq. ConvolutionalDistanceFormula, "
+                   "h = 1) from the same sums; weighted_fp32_alu: per-point weights log-uniform in [0.5, 2] "
+                   "(FP32 units); error = |out - oracle| / AABB diagonal on 4096 seeded grid nodes")
     return out
 
 
