@@ -544,7 +544,7 @@ def run_mixed_leg(dev, cloud, x, phi, points, normals, params, steps: int = 2):
     cores (the default), FP32 on the FP32 units, and packed-half weights
     (SDF_F16X2, SDF_BF16X2, FP32 units); and the two other forms of the sum:
     the log-sum-exp distance on the tensor cores, and the blend with seeded
-    per-point weights (FP32 units).  Device Gpairs/s, and the error against
+    per-point weights (default engine).  Device Gpairs/s, and the error against
     the FP64 oracle on 4,096 seeded grid nodes, relative to the AABB diagonal."""
     import torch
 
@@ -565,7 +565,7 @@ def run_mixed_leg(dev, cloud, x, phi, points, normals, params, steps: int = 2):
              ("f16x2", cloud, dict(precision=_abi.SDF_F16X2, engine=_abi.SDF_ENGINE_ALU), ref),
              ("bf16x2", cloud, dict(precision=_abi.SDF_BF16X2, engine=_abi.SDF_ENGINE_ALU), ref),
              ("lse_tensor", cloud, dict(formula=_abi.SDF_FORMULA_LSE, engine=_abi.SDF_ENGINE_TENSOR), orc.lse(xs)),
-             ("weighted_fp32_alu", wcloud, dict(), oracle.Cloud(points, normals, params, weights=weights).phi(xs)))
+             ("weighted_fp32", wcloud, dict(), oracle.Cloud(points, normals, params, weights=weights).phi(xs)))
     diag = float(np.linalg.norm(points.max(0) - points.min(0)))
     out = {}
     for name, cl, kw, r in cases:
@@ -585,8 +585,9 @@ def run_mixed_leg(dev, cloud, x, phi, points, normals, params, steps: int = 2):
     out["note"] = ("fp32_tensor: products on the tensor cores (split f16, FP32 accumulate), pairs finished in "
                    "FP32; fp32_alu: FP32 units only; f16x2/bf16x2: packed-half exp2 of a lane's two weights on "
                    "the FP32-unit loop; lse_tensor: the log-sum-exp distance (Eq. ConvolutionalDistanceFormula, "
-                   "h = 1) from the same sums; weighted_fp32_alu: per-point weights log-uniform in [0.5, 2] "
-                   "(FP32 units); error = |out - oracle| / AABB diagonal on 4096 seeded grid nodes")
+                   "h = 1) from the same sums; weighted_fp32: per-point weights log-uniform in [0.5, 2] "
+                   "(direct tiles on the tensor cores, curvature-form tiles on the FP32 units); "
+                   "error = |out - oracle| / AABB diagonal on 4096 seeded grid nodes")
     return out
 
 

@@ -156,8 +156,9 @@ PTSDF_API sdf_status sdf_build(const float* d_points, const float* d_normals, co
  *   d_weights  N float on the device, each in [2^-64, 2^64] (else SDF_EINVAL,
  *              detected on the device; the range keeps every FP32 sum finite
  *              and non-zero); NULL is sdf_build.
- *   A weighted cloud is evaluated by the FP32-unit pair loops (SDF_ENGINE_AUTO
- *   chooses them; SDF_ENGINE_TENSOR returns SDF_EINVAL). */
+ *   With the tensor engine, a weighted cloud's direct-form tiles take the
+ *   tensor cores (the weight scales the per-point constants of their B tiles)
+ *   and its curvature-form tiles the FP32 units. */
 PTSDF_API sdf_status sdf_build_weighted(const float* d_points, const float* d_normals, const float* d_params,
                               const float* d_weights, int64_t n, void* stream, sdf_cloud* out);
 

@@ -153,7 +153,8 @@ struct TcQuery {
 sdf_status build_btiles(Cloud& c, cudaStream_t st);
 // The tensor-core loop takes tiles [0, tc_tiles_end(c)): every tile, or
 // (PTSDF_TC_KAPPA=0) the direct tiles and the whole kappa_min = 0 tiles,
-// leaving the other kappa tiles to k_fwd.
+// leaving the other kappa tiles to k_fwd; for a weighted cloud only the
+// direct tiles.
 int64_t tc_tiles_end(const Cloud& c);
 int64_t tc_query_blocks(int64_t q);
 // tiles [tiles_begin, tiles_end) of one segment (direct, or curvature form)

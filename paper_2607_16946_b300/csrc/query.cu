@@ -246,8 +246,7 @@ Plan make_plan(const Cloud& c, int64_t q, int split_override, int queries_per_ct
 }
 
 bool use_tensor_engine(const Cloud& c, const sdf_query_opts& o) {
-    return o.engine != SDF_ENGINE_ALU && o.precision == SDF_F32 && !c.weighted && c.btiles != nullptr &&
-           tc_tiles_end(c) > 0;
+    return o.engine != SDF_ENGINE_ALU && o.precision == SDF_F32 && c.btiles != nullptr && tc_tiles_end(c) > 0;
 }
 
 namespace {
@@ -285,8 +284,6 @@ int query_partials(const Cloud& c, int64_t q, const sdf_query_opts& o) {
 
 sdf_status launch_query(const Cloud& c, const float* d_x, int64_t q, float* d_phi, const sdf_query_opts& o,
                         cudaStream_t st) {
-    if (o.engine == SDF_ENGINE_TENSOR && c.weighted)
-        return set_error(SDF_EINVAL, "sdf_query: the tensor-core engine does not take per-point weights");
     if (o.lambda_mode == SDF_LAMBDA_RADIUS) return launch_radius_query(c, d_x, q, d_phi, o, st);
     const Plan p = make_plan(c, q, o.split_n);
     // Tensor-core engine: see TcPlan

@@ -169,8 +169,11 @@ __global__ void k_build_btiles(const float4* __restrict__ rec, int64_t n_direct,
         b[2][4] = -(c[0] * e1[0] + c[1] * e1[1] + c[2] * e1[2]);
         b[3][4] = -(c[0] * e2[0] + c[1] * e2[1] + c[2] * e2[2]);
         b[4][4] = (double)r1.w * inv_s;   // R
-        b[5][4] = (double)r2.w * inv_s;   // -sT r
-        b[6][4] = r0.w;                   // sT
+        // -sT r and sT times the point's weight A (r3.w; 1 without weights):
+        // the epilogue's w (sT D - sT r) is then A w g, and |A sT| = A
+        const double A = rec[4 * i + 3].w;
+        b[5][4] = A * (double)r2.w * inv_s;   // -A sT r
+        b[6][4] = A * (double)r0.w;           // A sT
     } else if (valid) {
         // {p, 2 zeta}{q, |kmin|}{u, -kmax}{2 zeta n*, 0}
         const float4 r0 = rec[4 * i], r1 = rec[4 * i + 1], r2 = rec[4 * i + 2], r3 = rec[4 * i + 3];
@@ -265,8 +268,10 @@ __device__ __forceinline__ float g_from_quantities(float q1, float q2, float q3,
 }
 
 // One epilogue warp's share of a full tile from the accumulator: 8 pairs per
-// lane; v[k * 8 + i] is quantity k of point i.
-template <int FORM>
+// lane; v[k * 8 + i] is quantity k of point i.  WEIGHTED (direct form only):
+// quantity 6 is A sT, so W takes w |A sT| = A w (S takes A w g through the
+// scaled constants of g).
+template <int FORM, bool WEIGHTED = false>
 __device__ __forceinline__ void tile_pairs(const float (&v)[kVals], float Ls, float A0, float& W, float& S) {
     float tw = 0.f, ts = 0.f;
 #pragma unroll
@@ -275,7 +280,7 @@ __device__ __forceinline__ void tile_pairs(const float (&v)[kVals], float Ls, fl
         // |d^2|: the products may round a zero distance slightly negative
         const float d = sqrt_abs_mufu(v[i]);
         const float w = ex2_mufu(fmaf(-Ls, d, A0));
-        tw += w;
+        tw = WEIGHTED ? fmaf(w, fabsf(v[48 + i]), tw) : tw + w;
         ts = fmaf(w, g, ts);
     }
     W += tw;
@@ -285,7 +290,8 @@ __device__ __forceinline__ void tile_pairs(const float (&v)[kVals], float Ls, fl
 // The same share from the FP32 records (the formula of the tile's form, in
 // world units, rescaled to units of s): for far queries, for flagged tiles
 // and for the partial last tile of a segment (only `valid` points exist).
-template <int FORM>
+// WEIGHTED: each weight times the point's A (r3.w).
+template <int FORM, bool WEIGHTED = false>
 __device__ __forceinline__ void record_pairs(int valid, float x, float y, float z, float inv_s,
                                              const float4* __restrict__ rec, int64_t slot0, float Ls, float A0,
                                              float& W, float& S) {
@@ -304,7 +310,8 @@ __device__ __forceinline__ void record_pairs(int valid, float x, float y, float 
         g *= inv_s;
         const float dx = x - r0.x, dy = y - r0.y, dz = z - r0.z;
         const float d = sqrt_mufu(fmaf(dx, dx, fmaf(dy, dy, dz * dz))) * inv_s;
-        const float w = ex2_mufu(fmaf(-Ls, d, A0));
+        float w = ex2_mufu(fmaf(-Ls, d, A0));
+        if (WEIGHTED) w *= __ldg(r + 3).w;
         tw += w;
         ts = fmaf(w, g, ts);
     }
@@ -317,7 +324,9 @@ __device__ __forceinline__ void record_pairs(int valid, float x, float y, float 
 // KAPPA: the launch covers curvature-form tiles (all three formulas, flagged
 // tiles); otherwise direct-form tiles only, which are never flagged (their
 // coefficients are bounded by the 8-diagonal radius rule).
-template <bool KAPPA>
+// WEIGHTED (direct segment of a weighted cloud): the B tiles carry A sT, and
+// tiles whose scaled constants left the f16 split's range are flagged too.
+template <bool KAPPA, bool WEIGHTED>
 __global__ void __maxnreg__(96) k_fwd_tc(TcArgs ta, int32_t* status) {
     extern __shared__ __align__(1024) uint8_t smem[];
     uint8_t* sA = smem;                                                         // 2 sub-tiles
@@ -448,10 +457,10 @@ __global__ void __maxnreg__(96) k_fwd_tc(TcArgs ta, int32_t* status) {
         const int b = eset;   // this set's accumulator
         const int32_t* flags = ta.tile_exact + t0;
         // the next tile's exact flag is fetched one tile ahead
-        int32_t flag_next = KAPPA && eset < ntiles ? __ldg(flags + eset) : 0;
+        int32_t flag_next = (KAPPA || WEIGHTED) && eset < ntiles ? __ldg(flags + eset) : 0;
         for (int t = eset; t < ntiles; t += kEpiSets) {
-            const bool flagged = KAPPA && flag_next != 0;
-            if (KAPPA && t + kEpiSets < ntiles) flag_next = __ldg(flags + t + kEpiSets);
+            const bool flagged = (KAPPA || WEIGHTED) && flag_next != 0;
+            if ((KAPPA || WEIGHTED) && t + kEpiSets < ntiles) flag_next = __ldg(flags + t + kEpiSets);
             // warp-uniform: the TMEM loads below are .sync.aligned
             const bool ok = mbar_wait_bounded(&tfull[b], (uint32_t)(t >> 1) & 1u, &abort_flag, status);
             if (!__all_sync(0xffffffffu, ok)) break;
@@ -479,7 +488,7 @@ __global__ void __maxnreg__(96) k_fwd_tc(TcArgs ta, int32_t* status) {
                 }
                 if (!lane_rec) {
                     if (form == kFormDirect)
-                        tile_pairs<kFormDirect>(v, Ls, A0, W, S);
+                        tile_pairs<kFormDirect, WEIGHTED>(v, Ls, A0, W, S);
                     else if (form == kFormFlat)
                         tile_pairs<kFormFlat>(v, Ls, A0, W, S);
                     else
@@ -492,7 +501,7 @@ __global__ void __maxnreg__(96) k_fwd_tc(TcArgs ta, int32_t* status) {
                     }
                     const int64_t slot0 = (int64_t)gt * kTileRecs + cg * kPtsPerWarp;
                     if (form == kFormDirect)
-                        record_pairs<kFormDirect>(valid, x, y, z, ta.inv_s, ta.rec, slot0, Ls, A0, W, S);
+                        record_pairs<kFormDirect, WEIGHTED>(valid, x, y, z, ta.inv_s, ta.rec, slot0, Ls, A0, W, S);
                     else if (form == kFormFlat)
                         record_pairs<kFormFlat>(valid, x, y, z, ta.inv_s, ta.rec, slot0, Ls, A0, W, S);
                     else
@@ -559,6 +568,7 @@ sdf_status build_btiles(Cloud& c, cudaStream_t st) {
 }
 
 int64_t tc_tiles_end(const Cloud& c) {
+    if (c.weighted) return c.tiles_direct;   // weighted curvature-form tiles take the FP32 units
     if (PTSDF_TC_KAPPA) return c.tiles_direct + c.tiles_kappa;
     return c.tiles_direct + c.n_kappa_flat / kTileRecs;
 }
@@ -576,9 +586,14 @@ sdf_status launch_fwd_tc(const Cloud& c, const TcQuery& a, int64_t tiles_begin, 
     if (e != cudaSuccess) return cuda_error(e, "sdf_query: cudaGetDevice");
     if (dev < 0 || dev >= 64) return set_error(SDF_EINVAL, "sdf_query: device id out of range");
     if (!attr_done[dev]) {
-        e = cudaFuncSetAttribute(k_fwd_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmemBytes);
+        e = cudaFuncSetAttribute(k_fwd_tc<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kTcSmemBytes);
         if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_fwd_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmemBytes);
+            e = cudaFuncSetAttribute(k_fwd_tc<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)kTcSmemBytes);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_fwd_tc<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)kTcSmemBytes);
         if (e != cudaSuccess) return cuda_error(e, "sdf_query: k_fwd_tc shared-memory attribute");
         attr_done[dev] = true;
     }
@@ -601,9 +616,11 @@ sdf_status launch_fwd_tc(const Cloud& c, const TcQuery& a, int64_t tiles_begin, 
     ta.direct_out = direct_out;
     const dim3 grid((unsigned)tc_query_blocks(a.q), (unsigned)nchunks);
     if (kappa)
-        k_fwd_tc<true><<<grid, kTcThreads, kTcSmemBytes, st>>>(ta, c.status);
+        k_fwd_tc<true, false><<<grid, kTcThreads, kTcSmemBytes, st>>>(ta, c.status);
+    else if (c.weighted)
+        k_fwd_tc<false, true><<<grid, kTcThreads, kTcSmemBytes, st>>>(ta, c.status);
     else
-        k_fwd_tc<false><<<grid, kTcThreads, kTcSmemBytes, st>>>(ta, c.status);
+        k_fwd_tc<false, false><<<grid, kTcThreads, kTcSmemBytes, st>>>(ta, c.status);
     e = cudaGetLastError();
     return e == cudaSuccess ? SDF_OK : cuda_error(e, "sdf_query: k_fwd_tc launch");
 }

@@ -4,8 +4,9 @@ Each request's result must be the same alone and in the mix: every request
 of a mixed, concurrently submitted workload (queries, gradients, Booleans,
 trace steps, offsets; host and device buffers; three submitting threads) is
 compared bit for bit with the same request run alone on a one-slot server,
-and (except trace steps) with the direct calls.  Admission is checked under a one-slot budget, oversized requests are
-refused, and a poll can time out.
+and (except trace steps) with the direct calls; a weighted cloud and
+log-sum-exp queries likewise.  Admission is checked under a one-slot budget,
+oversized requests are refused, and a poll can time out.
 """
 import threading
 
@@ -169,3 +170,39 @@ def test_refusals_and_timeout(env):
         srv.poll(t, timeout_s=0.0)
     srv.poll(t)
     srv.shutdown()
+
+
+def test_weighted_cloud_and_lse_requests(env):
+    """A weighted cloud among resident clouds, and log-sum-exp queries: each
+    served result equals the direct call bit for bit; the log-sum-exp
+    formula is refused for request kinds other than QUERY."""
+    m, S, torch, clouds = env
+    p, n, a = f32(*synth.ring_torus(6000, 5))
+    w = f32(np.exp(np.random.Generator(np.random.PCG64(6)).uniform(-1.0, 1.0, size=len(p))))
+    weighted = m.Cloud(p, n, a, weights=w)
+    pool = clouds + [weighted]
+    srv = S.Server(mem_budget_bytes=2 << 30, max_inflight=4, n_streams=3)
+    ids = [srv.register(c) for c in pool]
+    rng = np.random.Generator(np.random.PCG64(7))
+    cases = []
+    for i in range(12):
+        ci = int(rng.integers(0, len(pool)))
+        kind = S.SDF_REQ_GRAD if i % 4 == 3 else S.SDF_REQ_QUERY
+        formula = m.SDF_FORMULA_LSE if (kind == S.SDF_REQ_QUERY and i % 2 == 0) else m.SDF_FORMULA_BLEND
+        q = int(rng.integers(500, 40000))
+        x = torch.as_tensor(f32(rng.uniform(-1.5, 1.5, size=(q, 3))), dtype=torch.float32, device="cuda")
+        out = torch.empty(4 * q if kind == S.SDF_REQ_GRAD else q, device="cuda")
+        cases.append((ci, kind, formula, x, out, srv.submit(kind, ids[ci], x, out, formula=formula)))
+    for ci, kind, formula, x, out, tk in cases:
+        srv.poll(tk)
+        if kind == S.SDF_REQ_GRAD:
+            phi, g, _ = pool[ci].query_grad(x, saved=False)
+            ref = torch.cat([phi, g.reshape(-1)])
+        else:
+            ref = pool[ci].query(x, formula=formula)
+        np.testing.assert_array_equal(out.cpu().numpy(), ref.cpu().numpy())
+    x = torch.zeros((10, 3), device="cuda")
+    with pytest.raises(m.SdfError):
+        srv.submit(S.SDF_REQ_GRAD, ids[0], x, torch.empty(40, device="cuda"), formula=m.SDF_FORMULA_LSE)
+    srv.shutdown()
+    weighted.close()

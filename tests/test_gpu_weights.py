@@ -66,12 +66,47 @@ def test_weighted_blend(ptsdf, oracle_mod, split):
     assert np.abs(got - orc.phi(x)).max() <= tol
     # the weights matter: the unweighted blend differs by far more than the tolerance
     assert np.abs(got - oracle_mod.Cloud(p, n, a).phi(x)).max() > 10 * tol
+    # both engines: the tensor cores take the direct tiles (weights in their B
+    # tiles' constants), the FP32 units the curvature-form ones
+    for engine in (1, 2):
+        assert np.abs(run(cl, x, split_n=split, engine=engine) - orc.phi(x)).max() <= tol, engine
     fixed = run(cl, x, lambda_mode=ptsdf.SDF_LAMBDA_FIXED, fixed_lambda=40.0)
     assert np.abs(fixed - orc.phi(x, mode=oracle_mod.FIXED, lam=40.0)).max() <= tol
     # packed-half weights of the FP32-unit loop, within their own stated bounds
     for prec, name in ((1, "f16x2"), (2, "bf16x2")):
         half = run(cl, x, precision=prec)
         assert np.abs(half - orc.phi(x)).max() <= BOUNDS[name] * aabb_diag(p), name
+
+
+def test_weighted_direct_tiles_on_tensor_cores(ptsdf, oracle_mod):
+    """A direct-form cloud (ring torus) with weights: all of it on the tensor
+    cores, including weights up to 2^40 whose scaled B-tile constants leave
+    the f16 split's range (those tiles are flagged and take the record
+    formula); log-sum-exp as well."""
+    import ctypes
+    p, n, a = f32(*synth.ring_torus(3000, 55, noise=0.005, jitter_deg=2.0))
+    w = weights_for(len(p), 56)
+    w[::97] = 2.0 ** 40
+    cl = ptsdf.Cloud(p, n, a, weights=w)
+    info = cl.info()
+    assert info["exact_tiles"] > 0 and info["n_direct"] > 0.9 * len(p)
+    x = f32(synth.uniform_queries(1200, 57, -1.6, 1.6))
+    orc = oracle_mod.Cloud(p, n, a, weights=w)
+    tol = TOL_REL * aabb_diag(p)
+    tc, alu = run(cl, x, engine=2), run(cl, x, engine=1)
+    assert np.abs(tc - orc.phi(x)).max() <= tol
+    assert np.abs(alu - orc.phi(x)).max() <= tol
+    lse = run(cl, x, engine=2, formula=ptsdf.SDF_FORMULA_LSE)
+    assert np.abs(lse - orc.lse(x)).max() <= tol
+    # the tensor-core loop did run
+    from paper_2607_16946_b300 import _abi
+    L = ptsdf.lib()
+    _abi.check(L.sdf_profile_enable(1))
+    run(cl, x, engine=2)
+    cnt, ms = ctypes.c_int64(0), ctypes.c_double(0)
+    _abi.check(L.sdf_profile_read(_abi.SDF_K_FWD_TC, ctypes.byref(cnt), ctypes.byref(ms)))
+    L.sdf_profile_enable(0)
+    assert cnt.value >= 1
 
 
 def test_integer_weights_equal_repeated_points(ptsdf):
@@ -195,9 +230,6 @@ def test_option_errors(ptsdf):
                  lambda: cl.query_laplacian(x, formula=ptsdf.SDF_FORMULA_LSE)):
         with pytest.raises(ptsdf.SdfError):
             call()
-    cw = ptsdf.Cloud(p, n, a, weights=np.ones(len(p), np.float32))
-    with pytest.raises(ptsdf.SdfError):
-        cw.query(x, engine=ptsdf.SDF_ENGINE_TENSOR)
     for bad in (0.0, -1.0, float("nan"), 1e30):
         w = np.ones(len(p), np.float32)
         w[5] = bad
