@@ -156,6 +156,9 @@ sdf_status build_btiles(Cloud& c, cudaStream_t st);
 // leaving the other kappa tiles to k_fwd; for a weighted cloud only the
 // direct tiles.
 int64_t tc_tiles_end(const Cloud& c);
+// End of the whole kappa_min = 0 tiles that follow the direct segment
+// (<= tc_tiles_end): the flat-formula instance takes [tiles_direct, that).
+int64_t tc_flat_end(const Cloud& c);
 int64_t tc_query_blocks(int64_t q);
 // tiles [tiles_begin, tiles_end) of one segment (direct, or curvature form)
 sdf_status launch_fwd_tc(const Cloud& c, const TcQuery& a, int64_t tiles_begin, int64_t tiles_end,

@@ -251,23 +251,26 @@ bool use_tensor_engine(const Cloud& c, const sdf_query_opts& o) {
 
 namespace {
 
-// Launch plan of the tensor-core engine: the direct tiles on k_fwd_tc<false>
-// in nd chunks, the curvature-form tiles [tiles_direct, tc_end) on
-// k_fwd_tc<true> in nk chunks, any others on k_fwd in na chunks; with more
-// than one chunk in all, each writes (W, S) partial rows in that order and
-// k_merge sums them in row order.
+// Launch plan of the tensor-core engine: the direct tiles on the direct
+// instance of k_fwd_tc in nd chunks, the whole kappa_min = 0 tiles
+// [tiles_direct, flat_end) on the flat instance in nf chunks, the other
+// curvature-form tiles [flat_end, tc_end) on the general one in nk chunks,
+// any others on k_fwd in na chunks; with more than one chunk in all, each
+// writes (W, S) partial rows in that order and k_merge sums them in row order.
 struct TcPlan {
-    int64_t tc_end = 0, tpc_d = 0, tpc_k = 0, tpc_a = 0;
-    int nd = 0, nk = 0, na = 0;
-    int parts() const { return nd + nk + na; }
+    int64_t tc_end = 0, flat_end = 0, tpc_d = 0, tpc_f = 0, tpc_k = 0, tpc_a = 0;
+    int nd = 0, nf = 0, nk = 0, na = 0;
+    int parts() const { return nd + nf + nk + na; }
 };
 
 TcPlan tc_plan(const Cloud& c, int64_t q, int split_n, int64_t alu_qblocks) {
     TcPlan t;
     t.tc_end = tc_tiles_end(c);
+    t.flat_end = tc_flat_end(c);
     const int64_t qb = tc_query_blocks(q), target = 2LL * c.num_sms;   // one CTA per SM, two waves
     if (c.tiles_direct > 0) chunk_tiles(qb, c.tiles_direct, target, split_n, t.tpc_d, t.nd);
-    if (t.tc_end > c.tiles_direct) chunk_tiles(qb, t.tc_end - c.tiles_direct, target, split_n, t.tpc_k, t.nk);
+    if (t.flat_end > c.tiles_direct) chunk_tiles(qb, t.flat_end - c.tiles_direct, target, split_n, t.tpc_f, t.nf);
+    if (t.tc_end > t.flat_end) chunk_tiles(qb, t.tc_end - t.flat_end, target, split_n, t.tpc_k, t.nk);
     const int64_t tiles = c.tiles_direct + c.tiles_kappa;
     if (tiles > t.tc_end)
         chunk_tiles(alu_qblocks, tiles - t.tc_end, 2LL * kFwdMinBlocks * c.num_sms, split_n, t.tpc_a, t.na);
@@ -369,16 +372,21 @@ sdf_status launch_query(const Cloud& c, const float* d_x, int64_t q, float* d_ph
                 s = launch_fwd_tc(c, tq, 0, c.tiles_direct, tp.tpc_d, tp.nd, nparts == 1, st);
             }
             tq.part_base = tp.nd;
+            if (s == SDF_OK && tp.nf > 0) {
+                ProfRange pr(SDF_K_FWD_TC, st);
+                s = launch_fwd_tc(c, tq, c.tiles_direct, tp.flat_end, tp.tpc_f, tp.nf, nparts == 1, st);
+            }
+            tq.part_base = tp.nd + tp.nf;
             if (s == SDF_OK && tp.nk > 0) {
                 ProfRange pr(SDF_K_FWD_TC, st);
-                s = launch_fwd_tc(c, tq, c.tiles_direct, tp.tc_end, tp.tpc_k, tp.nk, nparts == 1, st);
+                s = launch_fwd_tc(c, tq, tp.flat_end, tp.tc_end, tp.tpc_k, tp.nk, nparts == 1, st);
             }
         }
         if (s == SDF_OK && tp.na > 0) {
             ProfRange pr(SDF_K_FWD, st);
             QueryArgs ak = a;
             ak.tile_base = tp.tc_end;
-            ak.part_base = tp.nd + tp.nk;
+            ak.part_base = tp.nd + tp.nf + tp.nk;
             fwd_kernel(SDF_F32, c.weighted)<<<dim3((unsigned)p.qblocks, (unsigned)tp.na), kThreads,
                                                kStages * kTileBytes, st>>>(
                 c.rec, c.n_direct, c.n_kappa, c.tiles_direct, c.tiles_direct + c.tiles_kappa, tp.tpc_a, ak, c.status,

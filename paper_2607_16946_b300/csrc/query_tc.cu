@@ -231,10 +231,9 @@ struct TcArgs {
     const float4* rec;
     int64_t tiles_begin, tiles_end, tiles_per_chunk;   // tiles [begin, end) in chunks
     // tile classes (tiles < 2^26): [0, tiles_direct) direct, of which the
-    // first direct_full are full; then kappa_min = 0 tiles up to flat_end and
-    // the others; kappa_full full kappa-form tiles; *_rem points in the
-    // partial last tile of each segment
-    int32_t tiles_direct, direct_full, flat_end, kappa_full, direct_rem, kappa_rem;
+    // first direct_full are full; then the kappa-form tiles, kappa_full of
+    // them full; *_rem points in the partial last tile of each segment
+    int32_t tiles_direct, direct_full, kappa_full, direct_rem, kappa_rem;
     float s, inv_s;          // coordinate scale of the B tiles (a power of two) and its inverse
     int direct_out;          // 1: write phi; 0: write (W, S) at partial row part_base + chunk
 };
@@ -321,13 +320,17 @@ __device__ __forceinline__ void record_pairs(int valid, float x, float y, float 
 
 // 18 warps: five share one SM sub-partition's 16K registers, so at most 96
 // registers per thread (allocated in multiples of 8)
-// KAPPA: the launch covers curvature-form tiles (all three formulas, flagged
-// tiles); otherwise direct-form tiles only, which are never flagged (their
-// coefficients are bounded by the 8-diagonal radius rule).
+// FORMS: the one formula of the launch's tiles.  kFormDirect: direct-form
+// tiles, never flagged without weights (their coefficients are bounded by
+// the 8-diagonal radius rule).  kFormFlat: whole curvature-form tiles whose
+// points all have kappa_min = 0.  kFormKappa: the other curvature-form tiles
+// (the general formula, exact for kappa_min = 0 too, so the tile at the
+// flat boundary may mix them).  Curvature-form tiles may be flagged.
 // WEIGHTED (direct segment of a weighted cloud): the B tiles carry A sT, and
 // tiles whose scaled constants left the f16 split's range are flagged too.
-template <bool KAPPA, bool WEIGHTED>
+template <int FORMS, bool WEIGHTED>
 __global__ void __maxnreg__(96) k_fwd_tc(TcArgs ta, int32_t* status) {
+    constexpr bool KAPPA = FORMS != kFormDirect;
     extern __shared__ __align__(1024) uint8_t smem[];
     uint8_t* sA = smem;                                                         // 2 sub-tiles
     uint8_t* sB = smem + 2 * kTcSubA;                                           // kTcStages tiles
@@ -468,7 +471,6 @@ __global__ void __maxnreg__(96) k_fwd_tc(TcArgs ta, int32_t* status) {
             const int gt = (int)t0 + t;
             const int rel = KAPPA ? gt - ta.tiles_direct : gt;   // tile within its segment
             const bool partial = rel >= (KAPPA ? ta.kappa_full : ta.direct_full);
-            const int form = !KAPPA ? kFormDirect : (gt < ta.flat_end ? kFormFlat : kFormKappa);
             // pairs from the records: far lanes, flagged and partial tiles
             const bool lane_rec = exact_lane || flagged || partial;
 #pragma unroll 1
@@ -487,12 +489,7 @@ __global__ void __maxnreg__(96) k_fwd_tc(TcArgs ta, int32_t* status) {
                     if (lane == 0) mbar_arrive(&tempty[b]);
                 }
                 if (!lane_rec) {
-                    if (form == kFormDirect)
-                        tile_pairs<kFormDirect, WEIGHTED>(v, Ls, A0, W, S);
-                    else if (form == kFormFlat)
-                        tile_pairs<kFormFlat>(v, Ls, A0, W, S);
-                    else
-                        tile_pairs<kFormKappa>(v, Ls, A0, W, S);
+                    tile_pairs<FORMS, WEIGHTED>(v, Ls, A0, W, S);
                 } else {
                     int valid = kPtsPerWarp;
                     if (partial) {
@@ -500,12 +497,7 @@ __global__ void __maxnreg__(96) k_fwd_tc(TcArgs ta, int32_t* status) {
                         valid = left < 0 ? 0 : left > kPtsPerWarp ? kPtsPerWarp : left;
                     }
                     const int64_t slot0 = (int64_t)gt * kTileRecs + cg * kPtsPerWarp;
-                    if (form == kFormDirect)
-                        record_pairs<kFormDirect, WEIGHTED>(valid, x, y, z, ta.inv_s, ta.rec, slot0, Ls, A0, W, S);
-                    else if (form == kFormFlat)
-                        record_pairs<kFormFlat>(valid, x, y, z, ta.inv_s, ta.rec, slot0, Ls, A0, W, S);
-                    else
-                        record_pairs<kFormKappa>(valid, x, y, z, ta.inv_s, ta.rec, slot0, Ls, A0, W, S);
+                    record_pairs<FORMS, WEIGHTED>(valid, x, y, z, ta.inv_s, ta.rec, slot0, Ls, A0, W, S);
                 }
             }
         }
@@ -567,6 +559,11 @@ sdf_status build_btiles(Cloud& c, cudaStream_t st) {
     return e == cudaSuccess ? SDF_OK : cuda_error(e, "sdf_build: k_build_btiles launch");
 }
 
+int64_t tc_flat_end(const Cloud& c) {
+    const int64_t end = tc_tiles_end(c), flat = c.tiles_direct + c.n_kappa_flat / kTileRecs;
+    return flat < end ? flat : end;
+}
+
 int64_t tc_tiles_end(const Cloud& c) {
     if (c.weighted) return c.tiles_direct;   // weighted curvature-form tiles take the FP32 units
     if (PTSDF_TC_KAPPA) return c.tiles_direct + c.tiles_kappa;
@@ -577,23 +574,29 @@ int64_t tc_query_blocks(int64_t q) { return (q + kTcM - 1) / kTcM; }
 
 sdf_status launch_fwd_tc(const Cloud& c, const TcQuery& a, int64_t tiles_begin, int64_t tiles_end,
                          int64_t tiles_per_chunk, int nchunks, int direct_out, cudaStream_t st) {
-    const bool kappa = tiles_begin >= c.tiles_direct;
-    if (tiles_begin >= tiles_end || (!kappa && tiles_end > c.tiles_direct))
-        return set_error(SDF_EINVAL, "sdf_query: tensor-core tile range straddles the record segments");
+    // the range's one formula: direct tiles, whole kappa_min = 0 tiles, or the rest
+    const int64_t flat_end = tc_flat_end(c);
+    int forms;
+    if (tiles_end <= c.tiles_direct)
+        forms = kFormDirect;
+    else if (tiles_begin >= c.tiles_direct && tiles_end <= flat_end)
+        forms = kFormFlat;
+    else if (tiles_begin >= flat_end)
+        forms = kFormKappa;
+    else
+        forms = -1;
+    if (tiles_begin >= tiles_end || forms < 0 || (forms != kFormDirect && c.weighted))
+        return set_error(SDF_EINVAL, "sdf_query: tensor-core tile range straddles the record forms");
     static bool attr_done[64] = {};
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return cuda_error(e, "sdf_query: cudaGetDevice");
     if (dev < 0 || dev >= 64) return set_error(SDF_EINVAL, "sdf_query: device id out of range");
     if (!attr_done[dev]) {
-        e = cudaFuncSetAttribute(k_fwd_tc<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)kTcSmemBytes);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_fwd_tc<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)kTcSmemBytes);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_fwd_tc<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)kTcSmemBytes);
+        const void* kernels[4] = {(const void*)k_fwd_tc<kFormDirect, false>, (const void*)k_fwd_tc<kFormDirect, true>,
+                                  (const void*)k_fwd_tc<kFormFlat, false>, (const void*)k_fwd_tc<kFormKappa, false>};
+        for (int k = 0; k < 4 && e == cudaSuccess; ++k)
+            e = cudaFuncSetAttribute(kernels[k], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmemBytes);
         if (e != cudaSuccess) return cuda_error(e, "sdf_query: k_fwd_tc shared-memory attribute");
         attr_done[dev] = true;
     }
@@ -606,7 +609,6 @@ sdf_status launch_fwd_tc(const Cloud& c, const TcQuery& a, int64_t tiles_begin, 
     ta.tiles_end = tiles_end;
     ta.tiles_direct = (int32_t)c.tiles_direct;
     ta.direct_full = (int32_t)(c.n_direct / kTileRecs);
-    ta.flat_end = (int32_t)(c.tiles_direct + c.n_kappa_flat / kTileRecs);
     ta.kappa_full = (int32_t)(c.n_kappa / kTileRecs);
     ta.direct_rem = (int32_t)(c.n_direct % kTileRecs);
     ta.kappa_rem = (int32_t)(c.n_kappa % kTileRecs);
@@ -615,12 +617,14 @@ sdf_status launch_fwd_tc(const Cloud& c, const TcQuery& a, int64_t tiles_begin, 
     ta.inv_s = 1.f / c.tc_scale;
     ta.direct_out = direct_out;
     const dim3 grid((unsigned)tc_query_blocks(a.q), (unsigned)nchunks);
-    if (kappa)
-        k_fwd_tc<true, false><<<grid, kTcThreads, kTcSmemBytes, st>>>(ta, c.status);
+    if (forms == kFormFlat)
+        k_fwd_tc<kFormFlat, false><<<grid, kTcThreads, kTcSmemBytes, st>>>(ta, c.status);
+    else if (forms == kFormKappa)
+        k_fwd_tc<kFormKappa, false><<<grid, kTcThreads, kTcSmemBytes, st>>>(ta, c.status);
     else if (c.weighted)
-        k_fwd_tc<false, true><<<grid, kTcThreads, kTcSmemBytes, st>>>(ta, c.status);
+        k_fwd_tc<kFormDirect, true><<<grid, kTcThreads, kTcSmemBytes, st>>>(ta, c.status);
     else
-        k_fwd_tc<false, false><<<grid, kTcThreads, kTcSmemBytes, st>>>(ta, c.status);
+        k_fwd_tc<kFormDirect, false><<<grid, kTcThreads, kTcSmemBytes, st>>>(ta, c.status);
     e = cudaGetLastError();
     return e == cudaSuccess ? SDF_OK : cuda_error(e, "sdf_query: k_fwd_tc launch");
 }
