@@ -22,8 +22,14 @@
 //
 // Seven quantities either way: one 128 x 224 x 32 product on the tensor
 // cores (two tcgen05 MMAs of K = 16) gives them for 128 queries and a
-// 32-point tile.  Tiles never mix the forms (the record segments are padded
-// to whole tiles), so the epilogue picks the formula per tile.
+// 32-point tile.  Tiles never mix the two forms (the record segments are
+// padded to whole tiles), and the kernel is compiled once per formula (direct;
+// whole kappa_min = 0 tiles; the other curvature-form tiles), one launch per
+// range, so that no epilogue carries a per-tile choice.
+//
+// Per-point weights A (sdf_build_weighted) ride in the direct form's B tiles:
+// -sT r and sT are scaled by A, so the epilogue's w (sT D - sT r) is A w g and
+// W takes w |A sT| = A w (a separate instance of the direct loop).
 //
 // Precision: every feature and coefficient is split into three f16 parts
 // (v = v_hi + v_mid + v_lo for FP32 inputs), and K holds the six cross
@@ -46,7 +52,8 @@
 // record formula (kappa_min = 0 tiles skip the first, which is then exact
 // without a root), again three roots and two reciprocals with d, or two and
 // one.  Then w = exp2(-L (d - d_min)), W += w, S += w g, with the sums
-// blocked per tile as in the ALU kernel.
+// blocked per tile as in the ALU kernel; the sums finish into the blend S / W
+// or the log-sum-exp distance (finish_sums).
 //
 // Warps: 0 producer (bulk copies of B tiles into an 8-stage ring), 1 MMA
 // issuer and TMEM owner (two 224-column accumulators), 2..17 epilogue in two
