@@ -182,10 +182,16 @@ class ClockSampler:
 
 
 def kernel_source_sha() -> str:
+    """Hash of the pair loop's sources with comments and blank space removed,
+    so that a comment-only edit keeps a committed capture valid."""
+    import re
     h = hashlib.sha256()
     for f in ("query_tc.cu", "tc_common.cuh", "query_common.cuh", "device_common.cuh", "internal.h"):
-        with open(os.path.join(ROOT, "paper_2607_16946_b300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_2607_16946_b300", "csrc", f), encoding="utf-8") as fh:
+            src = fh.read()
+        src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", " ", src)
+        h.update(" ".join(src.split()).encode())
     return h.hexdigest()[:16]
 
 
