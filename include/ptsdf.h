@@ -377,6 +377,29 @@ PTSDF_API sdf_status sdf_serve_stats(sdf_server srv, int32_t* queued, int32_t* i
 PTSDF_API sdf_status sdf_serve_shutdown(sdf_server srv);
 
 /* ---------------------------------------------------------------------------
+ * sdf_project_level_set -- samples of a level set of phi with normals, the
+ *   first half of the paper's morphological operations (Sec. 6,
+ *   "Morphological operations": sample the -c level set of phi and take the
+ *   normals at the moved points from grad phi; the re-fit of tori at those
+ *   points needs the paper's network and is not done here).
+ *
+ *   Each seed x0 moves by Newton steps along the gradient,
+ *     x <- x - (phi(x) - level) grad phi(x) / |grad phi(x)|^2,
+ *   at most max_iter of them (0..100); a seed stops once |phi - level| <= tol
+ *   or its gradient vanishes.  Then phi and grad phi are evaluated once more.
+ *   d_x0       Q x 3 seeds (for erosion, the cloud's own points).
+ *   d_x        Q x 3 out: the moved points (may be d_x0: in place).
+ *   d_normals  Q x 3 out: grad phi / |grad phi| at the moved points.
+ *   d_residual Q out: phi - level there.
+ *   opts: as sdf_query_grad (FP32, GLOBAL or FIXED lambda, the blend); the
+ *   offset is ignored (level takes its part).  Costs max_iter + 1 gradient
+ *   evaluations of Q queries.
+ * ------------------------------------------------------------------------- */
+PTSDF_API sdf_status sdf_project_level_set(sdf_cloud cloud, const float* d_x0, int64_t q, float level,
+                                 int32_t max_iter, float tol, float* d_x, float* d_normals, float* d_residual,
+                                 const sdf_query_opts* opts, void* stream);
+
+/* ---------------------------------------------------------------------------
  * sdf_query_laplacian -- phi, grad phi and the Laplacian lap phi at Q points
  * (App. D, "Laplacian"): the divergence of the gradient of the blend, with
  * lap g_i of each torus in closed form (lap D = 1/D + (rho - R)/(rho D) for

@@ -150,6 +150,23 @@ class Cloud:
                                    ctypes.byref(o), _stream_ptr(stream)), "sdf_query_grad")
         return phi, grad, sv
 
+    def project_level_set(self, x0, level: float, max_iter: int = 10, tol: float = 0.0, stream=None, **opts):
+        """Samples of the `level` set with normals (Sec. 6, morphological
+        operations): each seed moved by Newton steps along grad phi
+        (sdf_project_level_set).  Returns (x, normals, phi - level)."""
+        torch = _torch()
+        x0 = _dev_f32(x0, 3)
+        q = x0.shape[0]
+        x = torch.empty_like(x0)
+        nrm = torch.empty_like(x0)
+        res = torch.empty(q, device=x0.device, dtype=torch.float32)
+        o = make_opts(**opts)
+        check(lib().sdf_project_level_set(self._h, ctypes.c_void_p(x0.data_ptr()), q, float(level), int(max_iter),
+                                          float(tol), ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(nrm.data_ptr()),
+                                          ctypes.c_void_p(res.data_ptr()), ctypes.byref(o), _stream_ptr(stream)),
+              "sdf_project_level_set")
+        return x, nrm, res
+
     def backward_params(self, x, saved, grad_phi, stream=None, **opts):
         """d(sum_q grad_phi[q] phi(x_q)) / d params, N x 6 in the input point order."""
         torch = _torch()

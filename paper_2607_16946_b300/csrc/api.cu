@@ -76,6 +76,35 @@ sdf_query_opts resolve_opts(const sdf_query_opts* o) {
     return o ? *o : r;
 }
 
+// One Newton step onto the `level` set of phi (Sec. 6, "Morphological
+// operations": sampling a level set): x -= (phi - level) grad / |grad|^2,
+// except where |phi - level| <= tol or the gradient vanishes.
+__global__ void k_level_step(float* __restrict__ x, const float* __restrict__ phi, const float* __restrict__ grad,
+                             int64_t q, float level, float tol) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= q) return;
+    const float r = phi[i] - level;
+    const float gx = grad[3 * i], gy = grad[3 * i + 1], gz = grad[3 * i + 2];
+    const float g2 = fmaf(gx, gx, fmaf(gy, gy, gz * gz));
+    if (!(fabsf(r) > tol) || !(g2 > 1e-30f)) return;
+    const float f = r / g2;
+    x[3 * i] -= f * gx;
+    x[3 * i + 1] -= f * gy;
+    x[3 * i + 2] -= f * gz;
+}
+
+// Normals grad / |grad| in place, residual phi - level in place.
+__global__ void k_level_finish(float* __restrict__ phi, float* __restrict__ grad, int64_t q, float level) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= q) return;
+    phi[i] -= level;
+    const float gx = grad[3 * i], gy = grad[3 * i + 1], gz = grad[3 * i + 2];
+    const float inv = rsqrtf(fmaxf(fmaf(gx, gx, fmaf(gy, gy, gz * gz)), 1e-30f));
+    grad[3 * i] = gx * inv;
+    grad[3 * i + 1] = gy * inv;
+    grad[3 * i + 2] = gz * inv;
+}
+
 }  // namespace ptsdf
 
 using namespace ptsdf;
@@ -123,6 +152,43 @@ extern "C" sdf_status sdf_query_grad(sdf_cloud cloud, const float* d_x, int64_t 
     if (!d_x || !d_phi || !d_grad) return set_error(SDF_EINVAL, "sdf_query_grad: NULL buffer");
     return launch_query_grad(*reinterpret_cast<const Cloud*>(cloud), d_x, q, d_phi, d_grad, d_saved, o,
                              static_cast<cudaStream_t>(stream));
+}
+
+extern "C" sdf_status sdf_project_level_set(sdf_cloud cloud, const float* d_x0, int64_t q, float level,
+                                            int32_t max_iter, float tol, float* d_x, float* d_normals,
+                                            float* d_residual, const sdf_query_opts* opts, void* stream) {
+    if (!cloud) return set_error(SDF_EINVAL, "sdf_project_level_set: cloud is NULL");
+    if (q < 0) return set_error(SDF_EINVAL, "sdf_project_level_set: q < 0");
+    if (max_iter < 0 || max_iter > 100) return set_error(SDF_EINVAL, "sdf_project_level_set: max_iter in [0, 100]");
+    if (!std::isfinite(level) || !(tol >= 0.f) || !std::isfinite(tol))
+        return set_error(SDF_EINVAL, "sdf_project_level_set: level finite, tol finite and >= 0");
+    sdf_query_opts o = resolve_opts(opts);
+    sdf_status s = check_opts(o, "sdf_project_level_set");
+    if (s == SDF_OK) s = blend_only(o, "sdf_project_level_set");
+    if (s != SDF_OK) return s;
+    if (o.precision != SDF_F32 || o.lambda_mode == SDF_LAMBDA_RADIUS || o.engine == SDF_ENGINE_TENSOR)
+        return set_error(SDF_EINVAL, "sdf_project_level_set: the gradient's options (FP32, GLOBAL or FIXED lambda)");
+    if (q == 0) return SDF_OK;
+    if (!d_x0 || !d_x || !d_normals || !d_residual) return set_error(SDF_EINVAL, "sdf_project_level_set: NULL buffer");
+    o.offset = 0.f;   // the level plays the offset's part
+    const Cloud& c = *reinterpret_cast<const Cloud*>(cloud);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaSuccess;
+    if (d_x != d_x0) e = cudaMemcpyAsync(d_x, d_x0, (size_t)q * 3 * sizeof(float), cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) return cuda_error(e, "sdf_project_level_set: copy");
+    const unsigned blocks = (unsigned)((q + 255) / 256);
+    // phi and grad phi land in the residual and normal outputs, which serve as scratch
+    for (int it = 0; it <= max_iter; ++it) {
+        s = launch_query_grad(c, d_x, q, d_residual, d_normals, nullptr, o, st);
+        if (s != SDF_OK) return s;
+        if (it == max_iter) break;
+        ptsdf::k_level_step<<<blocks, 256, 0, st>>>(d_x, d_residual, d_normals, q, level, tol);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_error(e, "sdf_project_level_set: k_level_step");
+    }
+    ptsdf::k_level_finish<<<blocks, 256, 0, st>>>(d_residual, d_normals, q, level);
+    e = cudaGetLastError();
+    return e == cudaSuccess ? SDF_OK : cuda_error(e, "sdf_project_level_set: k_level_finish");
 }
 
 extern "C" sdf_status sdf_query_laplacian(sdf_cloud cloud, const float* d_x, int64_t q, float* d_phi, float* d_grad,
