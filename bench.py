@@ -545,6 +545,30 @@ def run_mesh_leg(dev, cloud, x, phi, steps: int = 3):
     return out
 
 
+def run_morph_leg(dev, cloud, points, steps: int = 3, iters: int = 6, level: float = -0.05):
+    """Level-set sampling with normals (Sec. 6, morphological operations,
+    erosion's first half): the dense-grid cloud's own points moved onto the
+    -0.05 level set by 6 Newton steps along grad phi (sdf_project_level_set,
+    7 gradient evaluations of N queries against N points each)."""
+    import torch
+    seeds = torch.as_tensor(np.asarray(points, np.float32), device=dev)
+    x, nrm, res = cloud.project_level_set(seeds, level, max_iter=iters)
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        x, nrm, res = cloud.project_level_set(seeds, level, max_iter=iters)
+    e1.record()
+    torch.cuda.synchronize(dev)
+    s = e0.elapsed_time(e1) / 1e3 / steps
+    n = len(points)
+    r = res.abs().float()
+    return {"ms": s * 1e3, "points": n, "newton_steps": iters, "level": level,
+            "gpairs_s": (iters + 1) * n * n / s / 1e9,
+            "residual_median": float(r.median()), "residual_p99": float(torch.quantile(r, 0.99)),
+            "note": "device-timed; pairs = (steps + 1) gradient evaluations x N^2"}
+
+
 def run_mixed_leg(dev, cloud, x, phi, points, normals, params, steps: int = 2):
     """The dense-grid step on each engine and precision: FP32 on the tensor
     cores (the default), FP32 on the FP32 units, and packed-half weights
@@ -759,6 +783,7 @@ def run_ours(args, rank, world, local):
         line["trace"] = run_trace_leg(dev)
         line["radius"] = run_radius_leg(dev, cloud, x, phi)
         line["mesh"] = run_mesh_leg(dev, cloud, x, phi)
+        line["morph"] = run_morph_leg(dev, cloud, p)
     if world == 1 and args.serve_requests > 0:
         del hx, hphi
         clouds_np = make_serving_clouds(args.serve_clouds, SERVE_SEED)
