@@ -16,6 +16,7 @@ over queries); this module is a ctypes wrapper with numpy arrays.  Functions:
                                         and RelationshipBetweenLambdaAndRadius
   Cloud.lse(x, C=64, ...)               log-sum-exp distance, Eq.
                                         ConvolutionalDistanceFormula (h = 1)
+  Cloud.lse_grad(x, ...)                d~ and grad d~ (forward-mode duals)
   Cloud.grad_x(x, ...)                  d phi / d x (forward-mode duals; App. D
                                         plus the x-dependence of lambda_x)
   Cloud.grad_params(x, G, ...)          d (sum_q G_q phi_q) / d a_i
@@ -78,6 +79,7 @@ def _load():
         _lib.or_set_weights.argtypes = [P, P]
         _lib.or_set_weights.restype = i32
         _lib.or_lse.argtypes = [P, i32, f64, f64, P, i64, P, i32]
+        _lib.or_lse_grad.argtypes = [P, i32, f64, f64, P, i64, P, P, i32]
         _lib.or_laplacian.argtypes = [P, i32, f64, f64, P, i64, P, P, P, i32]
         _lib.or_knn_mean_distance.argtypes = [P, i64, i32, i32]
         _lib.or_knn_mean_distance.restype = f64
@@ -152,6 +154,15 @@ class Cloud:
         out = np.empty(x.shape[0])
         _load().or_lse(self._h, mode, C, lam, _ptr(x), x.shape[0], _ptr(out), threads or default_threads())
         return out
+
+    def lse_grad(self, x, C: float = 64.0, mode: int = GLOBAL, lam: float = 0.0, threads: int | None = None):
+        """(d~, grad d~) by forward-mode duals through the definition, the
+        x-dependence of lambda_x included (GLOBAL)."""
+        x = _f64(x, 3)
+        out, g = np.empty(x.shape[0]), np.empty((x.shape[0], 3))
+        _load().or_lse_grad(self._h, mode, C, lam, _ptr(x), x.shape[0], _ptr(out), _ptr(g),
+                            threads or default_threads())
+        return out, g
 
     def phi_radius(self, x, lam: float, reval: float | None = None, C: float = 64.0, kfb: int = 32,
                    threads: int | None = None, used: bool = False, lse: bool = False):

@@ -80,6 +80,7 @@ static dual dsqrt(dual a) {
 }
 static dual dabs(dual a) { return a.v < 0.0 ? dneg(a) : a; }
 static dual dexp(dual a) { dual r; r.v = exp(a.v); for (int k = 0; k < ND; ++k) r.d[k] = a.d[k] * r.v; return r; }
+static dual dlog(dual a) { dual r; r.v = log(a.v); for (int k = 0; k < ND; ++k) r.d[k] = a.d[k] / a.v; return r; }
 
 typedef struct { dual x, y, z; } dvec;
 static dvec dv_const(const double* p) { dvec r = {dconst(p[0]), dconst(p[1]), dconst(p[2])}; return r; }
@@ -502,6 +503,60 @@ void or_lse(const or_cloud* C, int mode, double Cconst, double lambda, const dou
         int64_t q0 = k * per, q1 = q0 + per < m ? q0 + per : m;
         jobs[k] = (lse_job){C, &o, x, out, q0, q1 > q0 ? q1 : q0};
         pthread_create(&th[k], NULL, lse_worker, &jobs[k]);
+    }
+    for (int k = 0; k < threads; ++k) pthread_join(th[k], NULL);
+}
+
+/* d~ and its gradient in x: forward-mode duals through the same definition,
+ * lambda_x(x) included for GLOBAL (the farthest point's tie goes to the
+ * lowest index); the constant shift d_min cancels exactly.  lambda = 0 gives
+ * d~ = d_min and a zero gradient. */
+static double lse_grad_one(const or_cloud* C, const or_opts* o, const double x[3], double g3[3]) {
+    const int64_t n = C->n;
+    dvec X = {dvar(x[0], 0), dvar(x[1], 1), dvar(x[2], 2)};
+    dual dmax = dconst(-1.0);
+    double dmin = INFINITY;
+    for (int64_t i = 0; i < n; ++i) {
+        dual d = dv_norm(dv_sub(X, dv_const(C->tori[i].p)));
+        if (d.v > dmax.v) dmax = d;
+        if (d.v < dmin) dmin = d.v;
+    }
+    dual lambda;
+    if (o->mode == OR_GLOBAL) lambda = (dmax.v > 0.0) ? ddiv(dconst(o->C), dscale(dmax, 0.5)) : dconst(0.0);
+    else lambda = dconst(o->lambda);
+    if (!(lambda.v > 0.0)) {
+        g3[0] = g3[1] = g3[2] = 0.0;
+        return dmin;
+    }
+    dual W = dconst(0.0);
+    for (int64_t i = 0; i < n; ++i) {
+        dual d = dv_norm(dv_sub(X, dv_const(C->tori[i].p)));
+        W = dadd(W, dscale(dexp(dneg(dmul(lambda, dsub(d, dconst(dmin))))), wt_of(C, i)));
+    }
+    dual v = dsub(dconst(dmin), ddiv(dlog(W), lambda));
+    g3[0] = v.d[0]; g3[1] = v.d[1]; g3[2] = v.d[2];
+    return v.v;
+}
+
+typedef struct { const or_cloud* C; const or_opts* o; const double* x; double* out; double* grad; int64_t q0, q1; } lseg_job;
+
+static void* lseg_worker(void* arg) {
+    lseg_job* J = (lseg_job*)arg;
+    for (int64_t j = J->q0; j < J->q1; ++j) J->out[j] = lse_grad_one(J->C, J->o, J->x + 3 * j, J->grad + 3 * j);
+    return NULL;
+}
+
+void or_lse_grad(const or_cloud* C, int mode, double Cconst, double lambda, const double* x, int64_t m, double* out,
+                 double* grad, int threads) {
+    or_opts o = {mode, Cconst, lambda, OR_SHIFT_DMIN};
+    threads = clamp_threads(threads, m);
+    pthread_t th[256];
+    lseg_job jobs[256];
+    int64_t per = (m + threads - 1) / threads;
+    for (int k = 0; k < threads; ++k) {
+        int64_t q0 = k * per, q1 = q0 + per < m ? q0 + per : m;
+        jobs[k] = (lseg_job){C, &o, x, out, grad, q0, q1 > q0 ? q1 : q0};
+        pthread_create(&th[k], NULL, lseg_worker, &jobs[k]);
     }
     for (int k = 0; k < threads; ++k) pthread_join(th[k], NULL);
 }

@@ -160,3 +160,41 @@ def test_invalid_weights_rejected(bad):
     w[3] = bad
     with pytest.raises(ValueError):
         oracle.Cloud(p, n, a, weights=w)
+
+
+@pytest.mark.parametrize("A", [1.0, 0.2, 7.5])
+def test_lse_gradient_single_point(A):
+    """One point: grad d~ = (x - p)/|x - p| for a fixed lambda, and
+    (1 - ln(A) / (2C)) (x - p)/|x - p| for lambda_x = 2C/|x - p|."""
+    p = np.array([[0.3, -0.2, 0.1]])
+    n = np.array([[0.0, 0.0, 1.0]])
+    a = np.array([[0.0, 0.0, 0.0, 0.0, -0.5, -0.5]])
+    cl = oracle.Cloud(p, n, a, weights=[A])
+    x = queries(25, 20)
+    u = (x - p) / np.linalg.norm(x - p, axis=1, keepdims=True)
+    _, g = cl.lse_grad(x, mode=oracle.FIXED, lam=13.0)
+    np.testing.assert_allclose(g, u, atol=1e-12)
+    _, g = cl.lse_grad(x)
+    np.testing.assert_allclose(g, (1 - np.log(A) / (2 * 64.0)) * u, atol=1e-12)
+
+
+@pytest.mark.parametrize("mode,lam", [(oracle.GLOBAL, 0.0), (oracle.FIXED, 25.0)])
+def test_lse_gradient_finite_differences(mode, lam):
+    """Central differences of d~ (h = 1e-4 and h / 2, Richardson) on a
+    weighted mixed cloud, lambda_x(x) included for GLOBAL."""
+    p, n, a = small_cloud(seed=21)
+    rng = np.random.Generator(np.random.PCG64(22))
+    A = rng.uniform(0.5, 2.0, size=len(p))
+    cl = oracle.Cloud(p, n, a, weights=A)
+    x = queries(30, 23)
+    v, g = cl.lse_grad(x, mode=mode, lam=lam)
+    np.testing.assert_allclose(v, cl.lse(x, mode=mode, lam=lam), rtol=1e-14, atol=1e-14)
+    fd = np.empty_like(g)
+    for k in range(3):
+        e = np.zeros(3)
+        e[k] = 1.0
+        est = []
+        for h in (1e-4, 5e-5):
+            est.append((cl.lse(x + h * e, mode=mode, lam=lam) - cl.lse(x - h * e, mode=mode, lam=lam)) / (2 * h))
+        fd[:, k] = (4 * est[1] - est[0]) / 3
+    np.testing.assert_allclose(g, fd, rtol=1e-6, atol=1e-7)
