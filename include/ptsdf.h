@@ -102,7 +102,9 @@ typedef enum {
                                tori are not used).  lambda is the blend's: lambda_x under
                                SDF_LAMBDA_GLOBAL (d~ = d_min where lambda_x = 0, every point at x),
                                fixed_lambda (> 0) under FIXED and RADIUS (the RADIUS set's sum).
-                               Queries only: no gradients, parameter gradients, Laplacian or
+                               sdf_query, and sdf_query_grad (d~ and grad d~ = sum A_i w_i n_i / W
+                               + (mean distance - d~) / lambda grad lambda_x; d_saved must be
+                               NULL); no parameter gradients, Laplacian, level-set sampling or
                                sphere tracing. */
 } sdf_formula;
 

@@ -136,8 +136,10 @@ class Cloud:
         return 1e3 / self.knn_mean_distance(k)
 
     def query_grad(self, x, stream=None, saved=True, **opts):
-        """(phi, d phi / d x, saved statistics or None) at the rows of x."""
+        """(phi, d phi / d x, saved statistics or None) at the rows of x.  With
+        formula=SDF_FORMULA_LSE: (d~, grad d~, None)."""
         torch = _torch()
+        saved = saved and opts.get("formula", SDF_FORMULA_BLEND) == SDF_FORMULA_BLEND
         x = _dev_f32(x, 3)
         q = x.shape[0]
         phi = torch.empty(q, device=x.device, dtype=torch.float32)

@@ -141,8 +141,10 @@ extern "C" sdf_status sdf_query_grad(sdf_cloud cloud, const float* d_x, int64_t 
     if (q < 0) return set_error(SDF_EINVAL, "sdf_query_grad: q < 0");
     const sdf_query_opts o = resolve_opts(opts);
     sdf_status s = check_opts(o, "sdf_query_grad");
-    if (s == SDF_OK) s = blend_only(o, "sdf_query_grad");
     if (s != SDF_OK) return s;
+    if (o.formula == SDF_FORMULA_LSE && d_saved)
+        return set_error(SDF_EINVAL, "sdf_query_grad: no saved statistics for the log-sum-exp distance "
+                                     "(they serve the blend's parameter gradient)");
     if (o.precision != SDF_F32) return set_error(SDF_EINVAL, "sdf_query_grad: gradients are computed in FP32 only");
     if (o.lambda_mode == SDF_LAMBDA_RADIUS)
         return set_error(SDF_EINVAL, "sdf_query_grad: no gradient for SDF_LAMBDA_RADIUS");

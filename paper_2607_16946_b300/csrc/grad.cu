@@ -203,6 +203,26 @@ __device__ __forceinline__ void finalize(const GradArgs& ga, int64_t qi, float x
         gly = s * (y - ql.fy);
         glz = s * (z - ql.fz);
     }
+    if (a.formula == SDF_FORMULA_LSE) {
+        // the log-sum-exp distance d~ = (A0 - log2 W) / L (Eq. ConvolutionalDistanceFormula,
+        // h = 1) and its gradient sum w n / W + ((sum w d / W - d~) / lambda) grad lambda:
+        // the second term is d d~ / d lambda times the gradient of lambda_x
+        const float dt = ql.L > 0.f ? (ql.A0 - log2f(acc[A_W])) / ql.L : 0.f;
+        float gx = acc[A_NX] * invW, gy = acc[A_NY] * invW, gz = acc[A_NZ] * invW;
+        if (lam_x) {
+            const float c = fmaf(acc[A_D], invW, -dt) / ql.lam;
+            gx = fmaf(c, glx, gx);
+            gy = fmaf(c, gly, gy);
+            gz = fmaf(c, glz, gz);
+        }
+        if (a.phi) a.phi[qi] = dt - a.offset;
+        if (ga.grad) {
+            ga.grad[3 * qi] = gx;
+            ga.grad[3 * qi + 1] = gy;
+            ga.grad[3 * qi + 2] = gz;
+        }
+        return;
+    }
     const float cd = fmaf(-phi, acc[A_D], acc[A_GD]);   // sum w g d - phi sum w d
     // grad phi at constant lambda (App. D: A + phi B), then the lambda_x term
     const float fx = (acc[A_GX] - ql.lam * fmaf(-phi, acc[A_NX], acc[A_HX])) * invW;
@@ -347,6 +367,7 @@ sdf_status launch_query_grad(const Cloud& c, const float* d_x, int64_t q, float*
     a.C = o.C;
     a.lam = o.fixed_lambda;
     a.offset = o.offset;
+    a.formula = o.formula;
     a.part = nullptr;
     a.d2 = nullptr;
     a.far = nullptr;

@@ -226,8 +226,8 @@ def test_option_errors(ptsdf):
         cl.query(x, formula=7)
     with pytest.raises(ptsdf.SdfError):   # FIXED lambda 0 has no log-sum-exp distance
         cl.query(x, formula=ptsdf.SDF_FORMULA_LSE, lambda_mode=ptsdf.SDF_LAMBDA_FIXED, fixed_lambda=0.0)
-    for call in (lambda: cl.query_grad(x, formula=ptsdf.SDF_FORMULA_LSE),
-                 lambda: cl.query_laplacian(x, formula=ptsdf.SDF_FORMULA_LSE)):
+    for call in (lambda: cl.query_laplacian(x, formula=ptsdf.SDF_FORMULA_LSE),
+                 lambda: cl.project_level_set(x, 0.0, formula=ptsdf.SDF_FORMULA_LSE)):
         with pytest.raises(ptsdf.SdfError):
             call()
     for bad in (0.0, -1.0, float("nan"), 1e30):
@@ -236,3 +236,34 @@ def test_option_errors(ptsdf):
         with pytest.raises(ptsdf.SdfError):
             ptsdf.Cloud(p, n, a, weights=w)
     torch.cuda.synchronize()
+
+
+@pytest.mark.parametrize("weighted", [False, True])
+@pytest.mark.parametrize("mode", ["global", "fixed"])
+def test_lse_gradient(ptsdf, oracle_mod, mode, weighted):
+    """sdf_query_grad with the log-sum-exp formula: d~ and grad d~ against the
+    oracle's duals (lambda_x(x) included for GLOBAL), away from ties of the
+    farthest point; the C ABI refuses a saved-statistics buffer for it."""
+    import ctypes
+    import torch
+    from paper_2607_16946_b300 import _abi
+    p, n, a = mixed_cloud(58)
+    w = weights_for(len(p), 59) if weighted else None
+    cl = ptsdf.Cloud(p, n, a, weights=w)
+    orc = oracle_mod.Cloud(p, n, a, weights=w)
+    x = f32(synth.uniform_queries(1500, 60, -1.5, 1.5))
+    x = x[kink_free(p, x, 1e-5)][:500]
+    kw, okw = ({}, {}) if mode == "global" else (
+        {"lambda_mode": ptsdf.SDF_LAMBDA_FIXED, "fixed_lambda": 40.0}, {"mode": oracle_mod.FIXED, "lam": 40.0})
+    xt = torch.as_tensor(x, dtype=torch.float32, device="cuda")
+    d, g, sv = cl.query_grad(xt, formula=ptsdf.SDF_FORMULA_LSE, **kw)
+    torch.cuda.synchronize()
+    assert sv is None and cl.device_status() == 0
+    od, og = orc.lse_grad(x, **okw)
+    assert np.abs(d.cpu().numpy() - od).max() <= TOL_REL * aabb_diag(p)
+    check_close(g.cpu().numpy().astype(np.float64), og)
+    saved = torch.empty((len(x), 8), device="cuda")
+    o = _abi.make_opts(formula=ptsdf.SDF_FORMULA_LSE, **kw)
+    assert ptsdf.lib().sdf_query_grad(cl.handle, ctypes.c_void_p(xt.data_ptr()), len(x), ctypes.c_void_p(d.data_ptr()),
+                                      ctypes.c_void_p(g.data_ptr()), ctypes.c_void_p(saved.data_ptr()),
+                                      ctypes.byref(o), None) != 0
