@@ -787,11 +787,15 @@ def run_ours(args, rank, world, local):
     if world == 1 and args.serve_requests > 0:
         del hx, hphi
         clouds_np = make_serving_clouds(args.serve_clouds, SERVE_SEED)
-        line["served"] = run_served(args, dev, value, policy=1, clouds_np=clouds_np)
-        line["served_fifo"] = run_served(args, dev, value, policy=0, clouds_np=clouds_np)
-        # the serving configuration's packed-half form, offered at 0.7 of its own measured rate
-        f16_rate = line.get("mixed", {}).get("f16x2", {}).get("value") or value
-        line["served_f16x2"] = run_served(args, dev, f16_rate, policy=1, clouds_np=clouds_np, precision=1)
+        variants = set(args.serve_variants.split(","))
+        if "fp32" in variants:
+            line["served"] = run_served(args, dev, value, policy=1, clouds_np=clouds_np)
+        if "fifo" in variants:
+            line["served_fifo"] = run_served(args, dev, value, policy=0, clouds_np=clouds_np)
+        if "f16x2" in variants:
+            # the serving configuration's packed-half form, offered at 0.7 of its own measured rate
+            f16_rate = line.get("mixed", {}).get("f16x2", {}).get("value") or value
+            line["served_f16x2"] = run_served(args, dev, f16_rate, policy=1, clouds_np=clouds_np, precision=1)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(p, n, a)
     print(json.dumps(line), flush=True)
@@ -807,6 +811,8 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=300, help="requests of the served leg (0: skip)")
     ap.add_argument("--no-extra-legs", action="store_true", help="omit the gradient and tracing legs")
     ap.add_argument("--serve-clouds", type=int, default=32)
+    ap.add_argument("--serve-variants", default="fp32,fifo,f16x2",
+                    help="served runs: fp32 (smallest-first), fifo, f16x2 (comma-separated)")
     ap.add_argument("--serve-load", type=float, default=0.7, help="offered load as a fraction of capacity")
     args = ap.parse_args()
     if args.warmup < 3:
