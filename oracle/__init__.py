@@ -26,9 +26,11 @@ over queries); this module is a ctypes wrapper with numpy arrays.  Functions:
   torus_sdf(c, u, R, r, x)              literal Eq. SingleTorusSDF for an explicit torus
   frame(n)                              the (s, t) frame convention
 
-Parity status: every function is pinned by tests/test_oracle_pins.py except
-the blend on noisy clouds with per-query lambda, which has no independent
-closed form ("parity unpinned" beyond the properties listed there).
+Parity status: every function is pinned (tests/test_oracle_*.py).  The blend
+on noisy clouds with per-query lambda has no closed form; its pins are the
+invariances of tests/test_oracle_invariances.py (rotations and reflections
+with re-expressed coefficients, uniform scale, duplicated points, point
+order) beside the limits and exact cases of tests/test_oracle_pins.py.
 """
 from __future__ import annotations
 

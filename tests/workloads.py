@@ -37,10 +37,11 @@ def config2_cloud():
 GRID_RES = 256
 
 
-def mixed_cloud(seed=77):
+def mixed_cloud(seed=77, rounded=True):
     """Plane, cylinder, large-radius sphere cap and random-coefficient points
     (both torus record forms, all sign cases, tilt and shift), N = 1,000 (not
-    a multiple of the 32-record tile)."""
+    a multiple of the 32-record tile).  rounded=False keeps the float64 values
+    (exactly rank-one cylinder forms, unit normals)."""
     rng = np.random.Generator(np.random.PCG64(seed))
     p1, n1, a1 = synth.plane_patch(150, seed + 1)
     p1 = p1 * 0.8 + np.array([0.0, 0.0, -1.0])
@@ -64,4 +65,5 @@ def mixed_cloud(seed=77):
     N = np.concatenate([n1, n2, n3, n4])
     A = np.concatenate([a1, a2, a3, a4])
     perm = rng.permutation(P.shape[0])
-    return f32(P[perm], N[perm], A[perm])
+    out = (P[perm], N[perm], A[perm])
+    return f32(*out) if rounded else out
