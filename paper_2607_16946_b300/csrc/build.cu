@@ -20,6 +20,7 @@
 
 #include "device_common.cuh"
 #include "fit_math.cuh"
+#include "sphere_index.h"
 #include "internal.h"
 
 namespace ptsdf {
@@ -249,7 +250,8 @@ uint32_t spread3(uint32_t v) {
 
 // Orders the prepass entries (-2 p', |p'|^2) along a 30-bit Morton curve of p'
 // and returns one bounding sphere (centre p'_c, radius) per kSphereTile
-// consecutive entries.  Radii are inflated by 1e-5 of the AABB diagonal plus a
+// consecutive entries, followed by one group sphere per kGroupSpheres
+// consecutive spheres.  Radii are inflated by 1e-5 of the AABB diagonal plus a
 // relative 1e-6 so that FP32 rounding of the query-to-centre distance never
 // excludes a tile that holds an extreme point.
 void morton_order_and_spheres(const std::vector<float4>& in, const float* box, float diag,
@@ -298,6 +300,34 @@ void morton_order_and_spheres(const std::vector<float4>& in, const float* box, f
         cn = std::sqrt(cc[0] * cc[0] + cc[1] * cc[1] + cc[2] * cc[2]);
         const double r = std::sqrt(r2) + 1e-5 * diag + 1e-6 * (cn + diag);
         spheres[t] = make_float4((float)cc[0], (float)cc[1], (float)cc[2], (float)r);
+    }
+    // Group spheres, from the FP32 centres and radii the kernels read: centre
+    // of the members' boxes (rounded to FP32 first), radius max |c_t - C| + r_t
+    // in double, inflated by a relative 1e-5 (the FP32 rounding of the radius
+    // and of both centre distances a kernel compares) and 1e-6 of |C| + diag.
+    const size_t ng = (size_t)group_count((int64_t)ns);
+    spheres.resize(ns + ng);
+    for (size_t g = 0; g < ng; ++g) {
+        const size_t a = g * kGroupSpheres, b = std::min(ns, a + kGroupSpheres);
+        double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+        for (size_t t = a; t < b; ++t) {
+            const float4 s = spheres[t];
+            const double c[3] = {s.x, s.y, s.z};
+            for (int k = 0; k < 3; ++k) {
+                lo[k] = std::min(lo[k], c[k] - s.w);
+                hi[k] = std::max(hi[k], c[k] + s.w);
+            }
+        }
+        const float cf[3] = {(float)(0.5 * (lo[0] + hi[0])), (float)(0.5 * (lo[1] + hi[1])),
+                             (float)(0.5 * (lo[2] + hi[2]))};
+        double rg = 0.0;
+        for (size_t t = a; t < b; ++t) {
+            const float4 s = spheres[t];
+            const double dx = (double)s.x - cf[0], dy = (double)s.y - cf[1], dz = (double)s.z - cf[2];
+            rg = std::max(rg, std::sqrt(dx * dx + dy * dy + dz * dz) + (double)s.w);
+        }
+        const double cn = std::sqrt((double)cf[0] * cf[0] + (double)cf[1] * cf[1] + (double)cf[2] * cf[2]);
+        spheres[ns + g] = make_float4(cf[0], cf[1], cf[2], (float)(rg * (1.0 + 1e-5) + 1e-6 * (cn + diag)));
     }
 }
 
@@ -442,7 +472,7 @@ extern "C" sdf_status sdf_build_weighted(const float* d_points, const float* d_n
         std::vector<float4> spheres;
         std::vector<int32_t> order;
         morton_order_and_spheres(hp, c->aabb, c->aabb_diag, sorted, spheres, order);
-        c->n_spheres = (int64_t)spheres.size();
+        c->n_spheres = (n + kSphereTile - 1) / kSphereTile;   // the group spheres follow them
         PTSDF_TRY(cudaMemcpy(c->pre, sorted.data(), (size_t)n * sizeof(float4), cudaMemcpyHostToDevice),
                   "sdf_build: prepass upload");
         PTSDF_TRY(cudaMalloc(&c->spheres, spheres.size() * sizeof(float4)), "sdf_build: sphere alloc");

@@ -75,7 +75,7 @@ struct Cloud {
     float aabb[6] = {0, 0, 0, 0, 0, 0};
     float4* rec = nullptr;           // (tiles_direct + tiles_kappa) * kTileRecs * 4 float4
     float4* pre = nullptr;           // pre_tiles * kPreTile float4
-    float4* spheres = nullptr;       // n_spheres x (centre', radius)
+    float4* spheres = nullptr;       // n_spheres x (centre', radius), then the group spheres (sphere_index.h)
     int64_t n_spheres = 0;
     int32_t* perm = nullptr;         // record slot -> original point index (-1 for padding)
     float* src_points = nullptr;     // copies of the inputs (N x 3, N x 3, N x 6), kept for

@@ -19,6 +19,10 @@
 //      reaches below the current k-th distance, and sums over the k.
 // The k-nearest search of D is the same second step with the point itself
 // excluded, seeded with its own sphere and the next one in Morton order.
+// Both steps walk the spheres group by group (kGroupSpheres per group sphere)
+// and pass over a group whose sphere shows that none of its members would be
+// scanned, nor become the seed: every per-point decision, the summation order
+// and so the results are those of the walk over every sphere.
 // Distances come from the 16-byte prepass entries; records are read only for
 // the points that enter a sum.  One thread per query (or point); warps scan a
 // sphere when any of their lanes needs it.
@@ -28,6 +32,7 @@
 #include <vector>
 
 #include "query_common.cuh"
+#include "sphere_index.h"
 
 namespace ptsdf {
 
@@ -44,6 +49,8 @@ struct RadiusArgs {
     float* phi;
     const float4* spheres;
     int64_t nsph;
+    const float4* groups;  // group spheres (after the spheres in the same array)
+    int64_t ngroups;
     const float4* mrec;    // n x 4 float4 records in Morton order (r3.w: the point's weight)
     const float4* pre;     // n float4(-2 p', |p'|^2) in the same order (p' = p - AABB centre)
     int64_t n;
@@ -88,6 +95,18 @@ __device__ __forceinline__ float centre_dist(float xs, float ys, float zs, const
     return sqrt_mufu(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
 }
 
+// Lower bound on |x' - c_t| - r_t and |x' - c_t| + r_t, as centre_dist gives
+// them, for every member t of group sphere gs: the relative pad covers the
+// rounding of both centre distances (each well inside 1e-6 relative).
+__device__ __forceinline__ float group_lower(float xs, float ys, float zs, const float4& gs) {
+    return centre_dist(xs, ys, zs, gs) * (1.f - 1e-5f) - gs.w;
+}
+
+__device__ __forceinline__ int64_t group_end(int64_t g, int64_t nsph) {
+    const int64_t e = (g + 1) * kGroupSpheres;
+    return e < nsph ? e : nsph;
+}
+
 // Inserts (d2, j) into the ascending top-k list (bd, bi) of cnt entries.
 __device__ __forceinline__ void topk_insert(float* bd, int* bi, int& cnt, int k, float d2, int j) {
     if (cnt == k && !(d2 < bd[k - 1])) return;
@@ -101,14 +120,21 @@ __device__ __forceinline__ void topk_insert(float* bd, int* bi, int& cnt, int k,
     bi[pos] = j;
 }
 
+// Offers the points of sphere t to the top-k list.  The current k-th squared
+// distance is kept in a register (the list lives in local memory), so a
+// rejected point costs no local load; the acceptance test is topk_insert's.
 __device__ __forceinline__ void scan_sphere(const RadiusArgs& a, float xs, float ys, float zs, int64_t t, int64_t self,
                                             int k, float* bd, int* bi, int& cnt) {
     const int64_t j0 = t * kSphereTile;
     const int c = sphere_count(t, a.n);
+    float kth = cnt == k ? bd[k - 1] : INFINITY;
     for (int jj = 0; jj < c; ++jj) {
         const int64_t j = j0 + jj;
         if (j == self) continue;
-        topk_insert(bd, bi, cnt, k, dist2_pre(xs, ys, zs, a.pre, j), (int)j);
+        const float d2 = dist2_pre(xs, ys, zs, a.pre, j);
+        if (cnt == k && !(d2 < kth)) continue;
+        topk_insert(bd, bi, cnt, k, d2, (int)j);
+        if (cnt == k) kth = bd[k - 1];
     }
 }
 
@@ -129,18 +155,26 @@ __device__ int knn_scan(const RadiusArgs& a, float xs, float ys, float zs, int k
         seed2 = seed + 1 < a.nsph ? seed + 1 : seed - 1;
         scan_sphere(a, xs, ys, zs, seed2, self, k, bd, bi, cnt);
     }
-    for (int64_t t = 0; t < a.nsph; ++t) {
-        if (t == seed || t == seed2) continue;
-        const float4 s = __ldg(a.spheres + t);
-        const float lb = centre_dist(xs, ys, zs, s) - s.w;
-        const float lim = cnt < k ? INFINITY : sqrtf(bd[k - 1]) * (1.f + 1e-6f);
-        if (!(lb <= lim)) continue;
-        scan_sphere(a, xs, ys, zs, t, self, k, bd, bi, cnt);
+    for (int64_t g = 0; g < a.ngroups; ++g) {
+        // the bound only tightens as the list fills, so a group beyond it now
+        // has no member within it later
+        const float glim = cnt < k ? INFINITY : sqrtf(bd[k - 1]) * (1.f + 1e-6f);
+        if (group_lower(xs, ys, zs, __ldg(a.groups + g)) > glim) continue;
+        for (int64_t t = g * kGroupSpheres, te = group_end(g, a.nsph); t < te; ++t) {
+            if (t == seed || t == seed2) continue;
+            const float4 s = __ldg(a.spheres + t);
+            const float lb = centre_dist(xs, ys, zs, s) - s.w;
+            const float lim = cnt < k ? INFINITY : sqrtf(bd[k - 1]) * (1.f + 1e-6f);
+            if (!(lb <= lim)) continue;
+            scan_sphere(a, xs, ys, zs, t, self, k, bd, bi, cnt);
+        }
     }
     return cnt;
 }
 
-__global__ void __launch_bounds__(kRadiusThreads) k_radius_query(RadiusArgs a) {
+// 12 resident blocks per SM (40 registers): the kernel waits on dependent loads,
+// so residency matters more than the few spilled registers.
+__global__ void __launch_bounds__(kRadiusThreads, 12) k_radius_query(RadiusArgs a) {
     const int64_t qi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (qi >= a.q) return;
     const float x = a.x[3 * qi], y = a.x[3 * qi + 1], z = a.x[3 * qi + 2];
@@ -153,34 +187,40 @@ __global__ void __launch_bounds__(kRadiusThreads) k_radius_query(RadiusArgs a) {
     int inside = 0;
     float best_ub = INFINITY;
     int64_t best = 0;
-    for (int64_t t = 0; t < a.nsph; ++t) {
-        const float4 s = __ldg(a.spheres + t);
-        const float dc = centre_dist(xs, ys, zs, s);
-        if (dc + s.w < best_ub && sphere_count(t, a.n) >= a.kfb) {
-            best_ub = dc + s.w;
-            best = t;
-        }
-        if (!(dc - s.w <= lim)) continue;
-        const int64_t j0 = t * kSphereTile;
-        const int c = sphere_count(t, a.n);
-        for (int jj = 0; jj < c; ++jj) {
-            const float d2 = dist2_pre(xs, ys, zs, a.pre, j0 + jj);
-            if (!(d2 <= R2)) continue;
-            const float d = sqrtf(d2);
-            float wa;
-            const float g = g_record(x, y, z, a.mrec + 4 * (j0 + jj), !a.lse, wa);
-            if (d < m) {
-                // a new nearest point: the sums so far are rescaled to its distance
-                const float f = inside ? exp2f(-a.L * (m - d)) : 0.f;
-                W = fmaf(W, f, wa);
-                S = fmaf(S, f, wa * g);
-                m = d;
-            } else {
-                const float w = wa * exp2f(-a.L * (d - m));
-                W += w;
-                S = fmaf(w, g, S);
+    for (int64_t gi = 0; gi < a.ngroups; ++gi) {
+        // a group none of whose spheres reaches R_eval or improves on the
+        // seed so far is passed over (a NaN bound passes neither test)
+        const float lo = group_lower(xs, ys, zs, __ldg(a.groups + gi));
+        if (lo > lim && !(lo < best_ub)) continue;
+        for (int64_t t = gi * kGroupSpheres, te = group_end(gi, a.nsph); t < te; ++t) {
+            const float4 s = __ldg(a.spheres + t);
+            const float dc = centre_dist(xs, ys, zs, s);
+            if (dc + s.w < best_ub && sphere_count(t, a.n) >= a.kfb) {
+                best_ub = dc + s.w;
+                best = t;
             }
-            ++inside;
+            if (!(dc - s.w <= lim)) continue;
+            const int64_t j0 = t * kSphereTile;
+            const int c = sphere_count(t, a.n);
+            for (int jj = 0; jj < c; ++jj) {
+                const float d2 = dist2_pre(xs, ys, zs, a.pre, j0 + jj);
+                if (!(d2 <= R2)) continue;
+                const float d = sqrtf(d2);
+                float wa;
+                const float g = g_record(x, y, z, a.mrec + 4 * (j0 + jj), !a.lse, wa);
+                if (d < m) {
+                    // a new nearest point: the sums so far are rescaled to its distance
+                    const float f = inside ? exp2f(-a.L * (m - d)) : 0.f;
+                    W = fmaf(W, f, wa);
+                    S = fmaf(S, f, wa * g);
+                    m = d;
+                } else {
+                    const float w = wa * exp2f(-a.L * (d - m));
+                    W += w;
+                    S = fmaf(w, g, S);
+                }
+                ++inside;
+            }
         }
     }
     if (inside == 0) {
@@ -261,6 +301,8 @@ RadiusArgs radius_args(const Cloud& c) {
     a.phi = nullptr;
     a.spheres = c.spheres;
     a.nsph = c.n_spheres;
+    a.groups = c.spheres ? c.spheres + c.n_spheres : nullptr;
+    a.ngroups = c.spheres ? group_count(c.n_spheres) : 0;
     a.mrec = c.mrec;
     a.pre = c.pre;
     a.n = c.n;
