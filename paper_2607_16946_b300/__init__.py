@@ -16,7 +16,7 @@ import ctypes
 
 import numpy as np
 
-from . import _abi
+from . import _abi, _buffers
 from ._abi import (SDF_DIFFERENCE, SDF_ENGINE_ALU, SDF_ENGINE_AUTO, SDF_ENGINE_TENSOR, SDF_FORMULA_BLEND,
                    SDF_FORMULA_LSE, SDF_INTERSECT, SDF_LAMBDA_FIXED, SDF_LAMBDA_GLOBAL, SDF_LAMBDA_RADIUS, SDF_UNION,
                    SdfError, check, lib, make_opts)
@@ -104,6 +104,8 @@ class Cloud:
         q = x.shape[0]
         if out is None:
             out = torch.empty(q, device=x.device, dtype=torch.float32)
+        else:
+            _buffers.device_f32(out, q, "out", x.device)
         o = make_opts(**opts)
         check(lib().sdf_query(self._h, ctypes.c_void_p(x.data_ptr()), q, ctypes.c_void_p(out.data_ptr()),
                               ctypes.byref(o), _stream_ptr(stream)), "sdf_query")
@@ -205,6 +207,8 @@ class Cloud:
         q = x.shape[0]
         if out is None:
             out = np.empty(q, dtype=np.float32)
+        else:
+            _buffers.host_f32(out, q, "out", writable=True)
         o = make_opts(**opts)
         check(lib().sdf_query_host(self._h, x.ctypes.data_as(ctypes.c_void_p), q,
                                    out.ctypes.data_as(ctypes.c_void_p), ctypes.byref(o), _stream_ptr(stream)),

@@ -17,7 +17,7 @@ import threading
 
 import numpy as np
 
-from . import _abi
+from . import _abi, _buffers
 from ._abi import check, lib, make_opts
 
 SDF_REQ_QUERY, SDF_REQ_GRAD, SDF_REQ_UNION, SDF_REQ_INTERSECT, SDF_REQ_DIFFERENCE, SDF_REQ_TRACE_STEP = range(6)
@@ -45,17 +45,6 @@ class sdf_request_stats(ctypes.Structure):
                 ("device_ms", ctypes.c_double)]
 
 
-def _ptr_and_kind(a):
-    """(address, is_host) of a CUDA tensor or a C-contiguous numpy array."""
-    if isinstance(a, np.ndarray):
-        if not a.flags.c_contiguous or a.dtype != np.float32:
-            raise ValueError("host buffers must be C-contiguous float32")
-        return a.ctypes.data, True
-    if not a.is_contiguous() or a.dtype.itemsize != 4:
-        raise ValueError("device buffers must be contiguous float32")
-    return a.data_ptr(), a.device.type != "cuda"
-
-
 class Server:
     def __init__(self, mem_budget_bytes: int = 8 << 30, max_inflight: int = 8, n_streams: int = 4,
                  device: int | None = None, policy: int = SDF_SERVE_FIFO, starve_ms: int = 2000):
@@ -77,16 +66,21 @@ class Server:
         return cid.value
 
     def submit(self, kind: int, cloud_id: int, x, out, cloud_id_b: int = -1, dirs=None, t=None, **opts) -> int:
-        xp, host = _ptr_and_kind(x)
-        op, ohost = _ptr_and_kind(out)
-        if host != ohost:
-            raise ValueError("x and out must both be host or both be device buffers")
-        q = (x.shape[0] if x.ndim == 2 else x.shape[0] // 3)
+        nx = x.size if isinstance(x, np.ndarray) else x.numel()
+        if nx % 3:
+            raise ValueError("x: must hold q x 3 floats")
+        q = nx // 3
+        xp, host = _buffers.request_buffer(x, 3 * q, "x")
+        # the library reads and writes every buffer of a request in the same memory space
+        op, ohost = _buffers.request_buffer(out, 4 * q if int(kind) == SDF_REQ_GRAD else q, "out", writable=True)
+        dp, dhost = _buffers.request_buffer(dirs, 3 * q, "dirs") if dirs is not None else (None, host)
+        tp, thost = _buffers.request_buffer(t, q, "t") if t is not None else (None, host)
+        if not host == ohost == dhost == thost:
+            raise ValueError("x, out, dirs and t must all be host or all be device buffers")
         r = sdf_request()
         r.kind, r.cloud_id, r.cloud_id_b, r.host_buffers = int(kind), int(cloud_id), int(cloud_id_b), int(host)
         r.x, r.q, r.out = xp, q, op
-        r.dirs = _ptr_and_kind(dirs)[0] if dirs is not None else None
-        r.t = _ptr_and_kind(t)[0] if t is not None else None
+        r.dirs, r.t = dp, tp
         r.opts = make_opts(**opts)
         ticket = ctypes.c_uint64()
         check(lib().sdf_serve_submit(self._h, ctypes.byref(r), ctypes.byref(ticket)), "sdf_serve_submit")
