@@ -175,7 +175,11 @@ class Cloud:
         """d(sum_q grad_phi[q] phi(x_q)) / d params, N x 6 in the input point order."""
         torch = _torch()
         x = _dev_f32(x, 3)
+        q = x.shape[0]
+        _buffers.device_f32(saved, 8 * q, "saved", x.device)      # from query_grad at the same x
         gphi = _dev_f32(grad_phi).reshape(-1)
+        if gphi.numel() != q:
+            raise ValueError(f"grad_phi: must hold {q} floats, holds {gphi.numel()}")
         out = torch.empty((self.n, 6), device=x.device, dtype=torch.float32)
         o = make_opts(**opts)
         check(lib().sdf_backward_params(self._h, ctypes.c_void_p(x.data_ptr()), x.shape[0],
@@ -259,8 +263,12 @@ def combine(op: int, a, b, out=None, stream=None):
     """Booleans of two phi arrays (CUDA tensors): SDF_UNION, SDF_INTERSECT, SDF_DIFFERENCE."""
     torch = _torch()
     a, b = _dev_f32(a).reshape(-1), _dev_f32(b).reshape(-1)
+    if a.numel() != b.numel():
+        raise ValueError(f"a and b must have the same length ({a.numel()} and {b.numel()})")
     if out is None:
         out = torch.empty_like(a)
+    else:
+        _buffers.device_f32(out, a.numel(), "out", a.device)
     check(lib().sdf_combine(int(op), ctypes.c_void_p(a.data_ptr()), ctypes.c_void_p(b.data_ptr()), a.shape[0],
                             ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)), "sdf_combine")
     return out
