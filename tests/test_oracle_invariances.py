@@ -21,6 +21,14 @@ hold for any cloud, with no closed form of the blend needed.
 - Every point twice: W and S double, d_max is unchanged, so phi is unchanged
   and the log-sum-exp distance drops by ln 2 / lambda_x = ln 2 d_max / (2 C).
 - Point order: no effect beyond rounding.
+- Every normal flipped (the same patches written over the frames of -n_i,
+  heights negated): kappa_min and kappa_max are chosen by magnitude, so each
+  torus keeps its shape and changes its sign (Eq. TorusSigns).  phi, grad phi
+  and the Laplacian negate; the log-sum-exp distance, which has no sign,
+  does not change.
+- The radius-limited sums (Sec. 4.2) under isometries, scale (lambda / c,
+  R_eval c) and the flip, and D, the mean k-nearest distance of the lambda
+  heuristic, under isometries (unchanged) and scale (times c).
 
 The cloud is the mixed test cloud in float64: its cylinder patches keep a
 curvature of exactly zero up to rounding at every scale.  (Rounded to FP32
@@ -46,11 +54,12 @@ def orthogonal(seed, proper=True):
     return q
 
 
-def moved_coefficients(n, a, M):
+def moved_coefficients(n, a, M, flip=False):
     """Coefficients a = (a00, a01, a10, a11, a02, a20) of the same patches
-    after the normals are moved to M n (frames recomputed from M n)."""
+    after the normals are moved to M n (frames recomputed from M n); with
+    flip, to -M n, the height then measured along the flipped normal."""
     s, t = synth.frame(n)
-    n2 = n @ M.T
+    n2 = -(n @ M.T) if flip else n @ M.T
     s2, t2 = synth.frame(n2)
     Ms, Mt = s @ M.T, t @ M.T
     B = np.empty((len(n), 2, 2))
@@ -69,7 +78,7 @@ def moved_coefficients(n, a, M):
     out[:, 1], out[:, 2] = lin2[:, 1], lin2[:, 0]
     out[:, 3] = 2.0 * Q2[:, 0, 1]
     out[:, 4], out[:, 5] = Q2[:, 1, 1], Q2[:, 0, 0]
-    return n2, out
+    return n2, -out if flip else out
 
 
 @pytest.fixture(scope="module")
@@ -80,13 +89,14 @@ def cloud():
     return p, n, a, x, w
 
 
-def test_moved_coefficients_describe_the_same_surface(cloud):
+@pytest.mark.parametrize("flip", [False, True])
+def test_moved_coefficients_describe_the_same_surface(cloud, flip):
     """The coefficient map itself: surface points of Eq. BivariatePolynomial
     before and after the move coincide (checked on the patches, not through
     the oracle)."""
     p, n, a, _, _ = cloud
     M = orthogonal(94)
-    n2, a2 = moved_coefficients(n, a, M)
+    n2, a2 = moved_coefficients(n, a, M, flip)
     s, t = synth.frame(n)
     s2, t2 = synth.frame(n2)
     g = rng(95)
@@ -157,3 +167,54 @@ def test_point_order(oracle_mod, cloud):
     c2 = oracle_mod.Cloud(p[perm], n[perm], a[perm], weights=w[perm])
     np.testing.assert_allclose(c2.phi(x), c1.phi(x), atol=1e-12)
     np.testing.assert_allclose(c2.lse(x), c1.lse(x), atol=1e-12)
+
+
+def test_every_normal_flipped(oracle_mod, cloud):
+    p, n, a, x, w = cloud
+    n2, a2 = moved_coefficients(n, a, np.eye(3), flip=True)
+    c1 = oracle_mod.Cloud(p, n, a, weights=w)
+    c2 = oracle_mod.Cloud(p, n2, a2, weights=w)
+    np.testing.assert_allclose(c2.phi(x), -c1.phi(x), atol=1e-9)
+    np.testing.assert_allclose(c2.lse(x), c1.lse(x), atol=1e-12)
+    _, g1 = c1.grad_x(x)
+    _, g2 = c2.grad_x(x)
+    np.testing.assert_allclose(g2, -g1, atol=1e-8)
+    np.testing.assert_allclose(c2.laplacian(x[:40])[2], -c1.laplacian(x[:40])[2], atol=1e-6)
+    lam = 12.0
+    np.testing.assert_allclose(c2.phi_radius(x, lam), -c1.phi_radius(x, lam), atol=1e-9)
+
+
+@pytest.mark.parametrize("proper", [True, False])
+def test_radius_limited_isometry(oracle_mod, cloud, proper):
+    p, n, a, x, w = cloud
+    M = orthogonal(98 + proper, proper)
+    tr = np.array([-3.0, 0.25, 1.5])
+    n2, a2 = moved_coefficients(n, a, M)
+    c1 = oracle_mod.Cloud(p, n, a, weights=w)
+    c2 = oracle_mod.Cloud(p @ M.T + tr, n2, a2, weights=w)
+    x2 = x @ M.T + tr
+    for lam, reval in ((12.0, None), (300.0, 0.05)):       # sums within R_eval, and the 32-nearest fallback
+        r1, u1 = c1.phi_radius(x, lam, reval, used=True)
+        r2, u2 = c2.phi_radius(x2, lam, reval, used=True)
+        np.testing.assert_array_equal(u2, u1)
+        np.testing.assert_allclose(r2, r1, atol=1e-9)
+        np.testing.assert_allclose(c2.phi_radius(x2, lam, reval, lse=True), c1.phi_radius(x, lam, reval, lse=True),
+                                   atol=1e-9)
+    assert (u1 < 0).any() and (u1 > 0).any()
+    np.testing.assert_allclose(oracle_mod.knn_mean_distance(p @ M.T + tr, 16), oracle_mod.knn_mean_distance(p, 16),
+                               rtol=1e-12)
+
+
+@pytest.mark.parametrize("c", [0.05, 40.0])
+def test_radius_limited_scale(oracle_mod, cloud, c):
+    p, n, a, x, w = cloud
+    a2 = a * np.array([c, 1.0, 1.0, 1.0 / c, 1.0 / c, 1.0 / c])
+    c1 = oracle_mod.Cloud(p, n, a, weights=w)
+    c2 = oracle_mod.Cloud(c * p, n, a2, weights=w)
+    for lam, reval in ((12.0, None), (300.0, 0.05)):
+        r1, u1 = c1.phi_radius(x, lam, reval, used=True)
+        r2, u2 = c2.phi_radius(c * x, lam / c, None if reval is None else reval * c, used=True)
+        np.testing.assert_array_equal(u2, u1)
+        np.testing.assert_allclose(r2, c * r1, rtol=1e-9, atol=1e-12 * c)
+    np.testing.assert_allclose(oracle_mod.knn_mean_distance(c * p, 16), c * oracle_mod.knn_mean_distance(p, 16),
+                               rtol=1e-12)
