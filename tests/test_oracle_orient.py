@@ -1,7 +1,9 @@
 """Pins of the oracle's orientation repair (Sec. 6): the coefficient flip
 keeps the torus and negates its SDF (checked through the independently
-pinned fit and torus SDF), flipping twice is the identity, and clouds with
-30% of their normals reversed come back to the known outward orientation."""
+pinned fit and torus SDF), flipping twice is the identity, one step's
+scores equal the neighbour sums with the Mahalanobis length built from
+principal curvatures and directions computed here, and clouds with 30% of
+their normals reversed come back to the known outward orientation."""
 import numpy as np
 import pytest
 
@@ -38,6 +40,48 @@ def test_flip_keeps_the_torus(oracle_mod):
         np.testing.assert_allclose(f2["nstar"], -f1["nstar"], atol=1e-12)
         np.testing.assert_allclose(np.abs(f2["kmin"]), np.abs(f1["kmin"]), rtol=1e-9, atol=1e-12)
         np.testing.assert_allclose(orient.flip_coefficients(-n[i], a2), a[i], atol=1e-12)
+
+
+def _principal(n, a):
+    """|kappa_min|, |kappa_max| and unit 3-D principal directions (v_min,
+    v_max) of the patch Q*(s, t) = p + s s_i + t t_i + f(s, t) n_i at (0, 0):
+    the generalised eigenproblem II w = kappa I w of the second and first
+    fundamental forms (I = [[1 + a10^2, a10 a01], [a10 a01, 1 + a01^2]],
+    II = [[2 a20, a11], [a11, 2 a02]] / sqrt(1 + a10^2 + a01^2)), with each
+    w mapped to w_s (s + a10 n) + w_t (t + a01 n)."""
+    import scipy.linalg
+    a00, a01, a10, a11, a02, a20 = a
+    I = np.array([[1 + a10 ** 2, a10 * a01], [a10 * a01, 1 + a01 ** 2]])
+    II = np.array([[2 * a20, a11], [a11, 2 * a02]]) / np.sqrt(1 + a10 ** 2 + a01 ** 2)
+    kap, W = scipy.linalg.eigh(II, I)
+    s, t = synth.frame(n[None])
+    Qs, Qt = s[0] + a10 * n, t[0] + a01 * n
+    V = [w[0] * Qs + w[1] * Qt for w in W.T]
+    V = [v / np.linalg.norm(v) for v in V]
+    lo = int(np.argmin(np.abs(kap)))
+    return abs(kap[lo]), abs(kap[1 - lo]), V[lo], V[1 - lo]
+
+
+def test_step_scores_use_the_principal_mahalanobis_length(oracle_mod):
+    """score_i = sum_j exp(-M_i(p_i - p_j)) <n_i, grad phi(p_j)> with
+    M_i(r)^2 = kmin^2 <r, v_min>^2 + kmax^2 <r, v_max>^2 + eps^2 <r, n_i>^2:
+    curvatures and directions from _principal, grad phi from the oracle's
+    pinned gradient, neighbours and eps given."""
+    rng = np.random.Generator(np.random.PCG64(95))
+    m = 60
+    p = rng.uniform(-0.5, 0.5, (m, 3))
+    n = rng.normal(size=(m, 3))
+    n /= np.linalg.norm(n, axis=1, keepdims=True)
+    a = _random_coeffs(rng, m)
+    nbr = orient.knn_indices(p, 6)
+    eps = 3.0
+    _, score = orient.orientation_step(p, n, a, nbr, eps)
+    _, g = oracle_mod.Cloud(p, n, a).grad_x(p)
+    for i in range(m):
+        kmin, kmax, vmin, vmax = _principal(n[i], a[i])
+        r = p[i] - p[nbr[i]]
+        M = np.sqrt((kmin * (r @ vmin)) ** 2 + (kmax * (r @ vmax)) ** 2 + (eps * (r @ n[i])) ** 2)
+        np.testing.assert_allclose(score[i], np.exp(-M) @ (g[nbr[i]] @ n[i]), rtol=1e-9, atol=1e-12)
 
 
 def _scramble(p, n, a, frac, seed):
