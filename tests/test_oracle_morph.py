@@ -4,7 +4,8 @@ grad phi.
 
 - A unit-sphere cloud has phi(x) = |x| - 1 exactly (pinned in
   test_oracle_pins.py), so every seed lands on the sphere of radius 1 + c,
-  x0 (1 + c) / |x0|, in one step, with normal x0 / |x0| (closed form).
+  x0 (1 + c) / |x0|, in one step, with normal x0 / |x0| (closed form); with
+  no step the residual is the signed |x0| - 1 - c.
 - A plane cloud on z = 0 has phi = z: seeds land on z = c with normal +z.
 - On a noisy mixed cloud the residual |phi - c| falls quadratically (Newton)
   to rounding within a few steps, the normals are unit vectors, and seeds
@@ -29,6 +30,11 @@ def test_sphere_closed_form():
         np.testing.assert_allclose(x, x0 * (1 + c) / r0, atol=1e-12)
         np.testing.assert_allclose(nrm, x0 / r0, atol=1e-12)
         assert np.abs(res).max() < 1e-12
+        # no step: the seeds themselves, and the signed residual phi - c = |x0| - 1 - c
+        x, nrm, res = project_level_set(cl, x0, c, max_iter=0)
+        np.testing.assert_array_equal(x, x0)
+        np.testing.assert_allclose(res, r0[:, 0] - 1.0 - c, atol=1e-12)
+        np.testing.assert_allclose(nrm, x0 / r0, atol=1e-12)
 
 
 def test_plane_closed_form():
