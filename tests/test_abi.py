@@ -84,3 +84,50 @@ def test_serve_host_side_validation(abi):
     assert ctypes.sizeof(serve.sdf_serve_config) == 32
     assert ctypes.sizeof(serve.sdf_request_stats) == 48
     assert ctypes.sizeof(serve.sdf_request) == 16 + 5 * 8 + ctypes.sizeof(abi.sdf_query_opts)
+
+
+def _refusals(abi):
+    """(call, expected message) for a refusal of every entry point taking a
+    cloud or device buffers, each decided before any CUDA call."""
+    L = abi.lib()
+    o = abi.make_opts()
+    f, i64, i32, d = ctypes.c_float(), ctypes.c_int64(), ctypes.c_int32(), ctypes.c_double()
+    fake = ctypes.c_void_p(16)          # a non-NULL device address the checks must refuse before using
+    one = (ctypes.c_float * 3)(1.0, 1.0, 1.0)
+    return [
+        (lambda: L.sdf_query_grad(None, None, 4, None, None, None, ctypes.byref(o), None), b"sdf_query_grad: cloud"),
+        (lambda: L.sdf_query_laplacian(None, None, 4, None, None, None, ctypes.byref(o), None),
+         b"sdf_query_laplacian: cloud"),
+        (lambda: L.sdf_project_level_set(None, None, 4, 0.0, 3, 0.0, None, None, None, ctypes.byref(o), None),
+         b"sdf_project_level_set: cloud"),
+        (lambda: L.sdf_backward_params(None, None, 4, None, None, None, ctypes.byref(o), None),
+         b"sdf_backward_params: cloud"),
+        (lambda: L.sdf_trace(None, None, None, 4, 48, 1e-4, 6.0, None, None, None, ctypes.byref(o), None),
+         b"sdf_trace: cloud"),
+        (lambda: L.sdf_query_noalloc(None, None, 4, None, ctypes.byref(o), None), b"sdf_query_noalloc: cloud"),
+        (lambda: L.sdf_knn_mean_distance(None, 64, ctypes.byref(d), None), b"sdf_knn_mean_distance"),
+        (lambda: L.sdf_cloud_info(None, ctypes.byref(i64), ctypes.byref(f), None, None), b"sdf_cloud_info: cloud"),
+        (lambda: L.sdf_cloud_forms(None, ctypes.byref(i64), None), b"sdf_cloud_forms: cloud"),
+        (lambda: L.sdf_build_weighted(fake, fake, fake, fake, 0, None, ctypes.byref(ctypes.c_void_p())),
+         b"n must be"),
+        (lambda: L.sdf_combine(7, fake, fake, 4, fake, None), b"sdf_combine: unknown op"),
+        (lambda: L.sdf_combine(0, fake, fake, -1, fake, None), b"sdf_combine: q < 0"),
+        (lambda: L.sdf_combine(0, None, fake, 4, fake, None), b"sdf_combine: NULL buffer"),
+        (lambda: L.sdf_orient(fake, fake, fake, 1, 16, 3, ctypes.byref(o), ctypes.byref(i32), ctypes.byref(i32), None),
+         b"sdf_orient: n must be"),
+        (lambda: L.sdf_orient(fake, fake, fake, 100, 65, 3, ctypes.byref(o), ctypes.byref(i32), ctypes.byref(i32),
+                              None), b"sdf_orient: k must be"),
+        (lambda: L.sdf_orient(fake, fake, fake, 100, 16, 0, ctypes.byref(o), ctypes.byref(i32), ctypes.byref(i32),
+                              None), b"sdf_orient: max_iter"),
+        (lambda: L.sdf_mesh_level_set(fake, 1, 4, 4, one, one, 0.0, fake, 10, fake, 10, ctypes.byref(i64),
+                                      ctypes.byref(i64), None), b"sdf_mesh_level_set: need at least 2"),
+        (lambda: L.sdf_mesh_level_set(None, 4, 4, 4, one, one, 0.0, fake, 10, fake, 10, ctypes.byref(i64),
+                                      ctypes.byref(i64), None), b"sdf_mesh_level_set: NULL"),
+    ]
+
+
+def test_every_entry_point_refuses_bad_arguments_on_the_host(abi):
+    L = abi.lib()
+    for call, msg in _refusals(abi):
+        assert call() == abi.SDF_EINVAL, msg
+        assert msg in L.sdf_last_error(), (msg, L.sdf_last_error())
