@@ -189,8 +189,10 @@ PTSDF_API sdf_status sdf_cloud_forms(sdf_cloud cloud, int64_t* n_kappa_flat, int
  *   q       number of queries, >= 0 (0 is a no-op).
  *   d_phi   Q float, receives phi(x) - opts->offset.
  *   opts    NULL = sdf_opts_default.
- *   Every (query, point) pair is evaluated (no cut-off).  Scratch memory is
- *   taken from the stream-ordered allocator and returned on the stream.
+ *   Under SDF_LAMBDA_GLOBAL and SDF_LAMBDA_FIXED every (query, point) pair
+ *   is evaluated (no cut-off); SDF_LAMBDA_RADIUS sums each query's radius set
+ *   only (see sdf_lambda_mode).  Scratch memory is taken from the
+ *   stream-ordered allocator and returned on the stream.
  *   Errors: SDF_EINVAL (NULL pointers with q > 0, bad opts); SDF_ENOMEM;
  *   SDF_ECUDA.  Kernel faults show up in sdf_device_status.
  * ------------------------------------------------------------------------- */
