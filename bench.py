@@ -621,6 +621,12 @@ def run_mixed_leg(dev, cloud, x, phi, points, normals, params, steps: int = 2):
     return out
 
 
+def workload_config(q: int, world: int) -> dict:
+    """The workload both arms run (the main arm adds how it runs it)."""
+    return {"workload": WORKLOAD, "N": N_POINTS, "Q": q, "C": 64, "lambda": "global",
+            "parallelism": f"replicas{world}" if world > 1 else "single"}
+
+
 def run_reference(args, rank, world):
     """The oracle as it stands on the host cores, same workload and metric."""
     if rank != 0:
@@ -645,7 +651,7 @@ def run_reference(args, rank, world):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "N": N_POINTS, "Q": GRID_RES ** 3, "C": 64, "lambda": "global"},
+            "config": workload_config(GRID_RES ** 3, world),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
                              "sample": sample_desc},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -761,10 +767,8 @@ def run_ours(args, rank, world, local):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": elapsed_s / args.steps * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "N": N_POINTS, "Q": q, "C": 64, "lambda": "global",
-                   "precision": "fp32", "engine": "auto (tensor cores for every tile)",
-                   "parallelism": f"replicas{world}" if world > 1 else "single",
-                   "l2": "inputs larger than L2 (queries 201 MB, phi 67 MB); not flushed"},
+        "config": dict(workload_config(q, world), precision="fp32", engine="auto (tensor cores for every tile)",
+                       l2="inputs larger than L2 (queries 201 MB, phi 67 MB); not flushed"),
         "queries_per_s": world * q * args.steps / elapsed_s,
         "e2e": {"value": world * pairs_per_step * args.steps / e2e_s / 1e9, "unit": UNIT,
                 "h2d_bytes_per_step": q * 12, "d2h_bytes_per_step": q * 4},

@@ -81,3 +81,9 @@ def test_traffic_used_only_for_the_captured_source(tree):
     assert bench.committed_traffic() is None                       # taken on another source
     path.write_text("{not json")
     assert bench.committed_traffic() is None
+
+
+def test_both_arms_describe_the_same_workload():
+    c1, c4 = bench.workload_config(256 ** 3, 1), bench.workload_config(256 ** 3, 4)
+    assert c1["Q"] == 256 ** 3 and c1["N"] == bench.N_POINTS and c1["workload"] == bench.WORKLOAD
+    assert c1["parallelism"] == "single" and c4["parallelism"] == "replicas4"
