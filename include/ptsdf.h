@@ -28,6 +28,12 @@
  *    instead of trapping; sdf_device_status() reads and clears it.
  *  - Work is not thread-safe per cloud for concurrent *builds*; queries on
  *    one cloud from several host threads/streams are safe (read-only).
+ *  - Every call that computes cites the passage of the paper it implements.
+ *    The calls that manage resources, report status or measure the device
+ *    (sdf_destroy, sdf_cloud_info, sdf_cloud_forms, sdf_device_status, the
+ *    sdf_serve_* bookkeeping, sdf_probe_rates, sdf_selftest_wait_timeout,
+ *    sdf_profile_*, sdf_kernel_name, sdf_last_error, sdf_version) have no
+ *    counterpart in the paper.
  */
 #ifndef PTSDF_H
 #define PTSDF_H
@@ -199,7 +205,7 @@ PTSDF_API sdf_status sdf_cloud_forms(sdf_cloud cloud, int64_t* n_kappa_flat, int
 PTSDF_API sdf_status sdf_query(sdf_cloud cloud, const float* d_x, int64_t q, float* d_phi,
                      const sdf_query_opts* opts, void* stream);
 
-/* As sdf_query with HOST buffers: copies h_x to the device, evaluates, copies
+/* As sdf_query (Algorithm 1, "Inference") with HOST buffers: copies h_x to the device, evaluates, copies
  * phi back into h_phi, and synchronises `stream` before returning (so h_phi
  * is valid on return).  Large batches are cut into chunks whose copies
  * overlap the evaluation of the previous chunk.  Pinned host memory gives
@@ -276,8 +282,9 @@ PTSDF_API sdf_status sdf_combine(int32_t op, const float* d_a, const float* d_b,
                        void* stream);
 
 /* ---------------------------------------------------------------------------
- * sdf_query_noalloc -- sdf_query that allocates nothing.  The paper has no
- *   counterpart; this is a service of this library.
+ * sdf_query_noalloc -- sdf_query (Algorithm 1, "Inference") that allocates
+ *   nothing.  The allocation-free form has no counterpart in the paper; it
+ *   is a service of this library.
  *
  *   For callers that must not touch the CUDA allocator once they are running:
  *   latency-bound loops (a renderer asking for phi every frame, a controller
