@@ -423,3 +423,41 @@ def test_trace_sphere_closed_form(oracle_mod):
     assert np.all(t[~hit] < 0)
     np.testing.assert_allclose(t[hit], t_ref[hit], atol=2e-9)
     assert steps.max() <= 200
+
+
+def test_trace_offset_steps_and_limits(oracle_mod):
+    """Sphere tracing of phi = c on the exact sphere cloud (Sec. 6): rays hit
+    the sphere of radius 1 + c; a ray aimed at the centre reaches it in one
+    step, so it stops at the second evaluation; a ray leaving the cloud stops
+    once t passes t_max; with too few steps a ray reports a miss after
+    exactly max_steps evaluations."""
+    p, n, a = synth.sphere_fibonacci(128, 2)
+    cl = oracle_mod.Cloud(p, n, a)
+    org, dirs = synth.camera_rays(16, 16, 4, dist=3.0, fov_deg=60.0)
+    for c in (-0.3, 0.2):
+        t, _ = cl.trace(org, dirs, max_steps=300, eps=1e-9, t_max=8.0, offset=c)
+        b = np.sum(org * dirs, 1)
+        disc = b * b - (np.sum(org * org, 1) - (1.0 + c) ** 2)
+        hit, miss = disc > 1e-2, disc < -1e-2      # near-tangent rays converge too slowly to compare
+        assert hit.sum() > 20 and miss.sum() > 20
+        # tracing stops once phi - c < eps; the ray then still has eps / cos(incidence) to go,
+        # cos(incidence) = sqrt(disc) / (1 + c)
+        tol = 2e-9 * (1.0 + c) / np.sqrt(np.where(hit, disc, 1.0))
+        t_ref = -b - np.sqrt(np.where(hit, disc, 0.0))
+        assert np.all(np.abs(t[hit] - t_ref[hit]) <= tol[hit])
+        assert np.all(t[hit] <= t_ref[hit] + 1e-12)  # from outside, never past the surface
+        assert np.all(t[miss] < 0)
+    o = np.array([[0.0, 0.0, 3.0], [0.0, 0.0, 3.0], [0.0, 0.0, 3.0]])
+    d = np.array([[0.0, 0.0, -1.0], [0.0, 0.0, 1.0], [0.0, 0.0, -1.0]])
+    t, steps = cl.trace(o[:1], d[:1], max_steps=10, eps=1e-9, t_max=8.0, offset=0.25)
+    np.testing.assert_allclose(t, [3.0 - 1.25], atol=1e-12)
+    assert steps[0] == 2
+    t, steps = cl.trace(o[1:2], d[1:2], max_steps=100, eps=1e-9, t_max=8.0)
+    assert t[0] < 0 and steps[0] == 3          # phi = 2 + t: t = 0 -> 2 -> 6 -> 14 > t_max after 3 evaluations
+    # a ray passing 0.95 from the centre hits, but slowly near the tangent
+    sa = 0.95 / 3.0
+    g = np.array([[sa, 0.0, -np.sqrt(1.0 - sa * sa)]])
+    t, steps = cl.trace(o[2:], g, max_steps=3, eps=1e-9, t_max=8.0)
+    assert t[0] < 0 and steps[0] == 3
+    t, steps = cl.trace(o[2:], g, max_steps=300, eps=1e-9, t_max=8.0)
+    assert t[0] > 0 and 3 < steps[0] < 300
