@@ -21,16 +21,26 @@ over queries); this module is a ctypes wrapper with numpy arrays.  Functions:
                                         plus the x-dependence of lambda_x)
   Cloud.grad_params(x, G, ...)          d (sum_q G_q phi_q) / d a_i
   Cloud.g(i, x)                         g_i(x) = sign(T_i) phi_T(x), Eq. SingleTorusSDF
+  Cloud.laplacian(x, ...)               phi, grad phi and lap phi by second-order
+                                        jets (App. D plus the x-dependence of lambda_x)
+  Cloud.phi_radius(x, lam, ...)         radius-limited blend or log-sum-exp distance
+                                        (Sec. 4.2, "Acceleration and adaptive lambda")
   Cloud.trace(org, dir, ...)            sphere tracing (Sec. 6)
+  knn_mean_distance(points, k)          D of the lambda heuristic (Sec. 4.2)
   fit_record(p, n, a)                   the fitted torus of one point
   torus_sdf(c, u, R, r, x)              literal Eq. SingleTorusSDF for an explicit torus
   frame(n)                              the (s, t) frame convention
+
+Submodules (numpy on top of the above): oracle.orient (orientation repair,
+Sec. 6), oracle.mesh (marching tetrahedra of a phi grid, offset surfaces,
+Sec. 6), oracle.morph (level-set sampling with normals, Sec. 6).
 
 Parity status: every function is pinned (tests/test_oracle_*.py).  The blend
 on noisy clouds with per-query lambda has no closed form; its pins are the
 invariances of tests/test_oracle_invariances.py (rotations and reflections
 with re-expressed coefficients, uniform scale, duplicated points, point
-order) beside the limits and exact cases of tests/test_oracle_pins.py.
+order, every normal flipped) beside the limits and exact cases of
+tests/test_oracle_pins.py.
 """
 from __future__ import annotations
 
