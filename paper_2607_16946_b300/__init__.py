@@ -9,6 +9,12 @@ supplies device memory and the current CUDA stream.
     phi = cloud.query(x)                           # x: Q x 3 (CUDA tensor) -> Q
     phi = cloud.query_host(x_numpy)                # host arrays in and out
     phi = sdf(x, cloud, params)                    # differentiable in x and params
+
+Also on Cloud: query_grad, query_laplacian, backward_params, trace,
+project_level_set, knn_mean_distance / paper_lambda, info, device_status;
+module functions combine, mesh_level_set and orient; serving in
+paper_2607_16946_b300.serve.  Options (lambda mode, formula, precision,
+engine, offset, ...) are keyword arguments mapped onto sdf_query_opts.
 """
 from __future__ import annotations
 
