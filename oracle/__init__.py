@@ -17,10 +17,15 @@ over queries); this module is a ctypes wrapper with numpy arrays.  Functions:
   Cloud.lse(x, C=64, ...)               log-sum-exp distance, Eq.
                                         ConvolutionalDistanceFormula (h = 1)
   Cloud.lse_grad(x, ...)                d~ and grad d~ (forward-mode duals)
+  Cloud.sspd(x, ...)                    smoothed signed planar distance, Eq.
+                                        SmoothedSignedPlanarDistance
+  Cloud.shc(x, ...)                     signed Hopf-Cole distance, Eq.
+                                        ScreenedWindingNumber
   Cloud.grad_x(x, ...)                  d phi / d x (forward-mode duals; App. D
                                         plus the x-dependence of lambda_x)
   Cloud.grad_params(x, G, ...)          d (sum_q G_q phi_q) / d a_i
   Cloud.g(i, x)                         g_i(x) = sign(T_i) phi_T(x), Eq. SingleTorusSDF
+  Cloud.set_params(i, a)                refit point i's torus from new coefficients
   Cloud.laplacian(x, ...)               phi, grad phi and lap phi by second-order
                                         jets (App. D plus the x-dependence of lambda_x)
   Cloud.phi_radius(x, lam, ...)         radius-limited blend or log-sum-exp distance
@@ -90,6 +95,9 @@ def _load():
         _lib.or_phi_radius.argtypes = [P, f64, f64, i32, P, i64, P, P, i32, i32]
         _lib.or_set_weights.argtypes = [P, P]
         _lib.or_set_weights.restype = i32
+        _lib.or_set_params.argtypes = [P, i64, P]
+        _lib.or_baseline.argtypes = [P, i32, i32, f64, f64, P, i64, P, P, i32]
+        _lib.or_set_params.restype = i32
         _lib.or_lse.argtypes = [P, i32, f64, f64, P, i64, P, i32]
         _lib.or_lse_grad.argtypes = [P, i32, f64, f64, P, i64, P, P, i32]
         _lib.or_laplacian.argtypes = [P, i32, f64, f64, P, i64, P, P, P, i32]
@@ -134,6 +142,14 @@ class Cloud:
             if self._w.shape[0] != n or lib.or_set_weights(self._h, _ptr(self._w)) != 0:
                 raise ValueError("weights: one finite value > 0 per point")
 
+    def set_params(self, i: int, a):
+        """Replaces point i's six coefficients and refits its torus (for finite
+        differences of phi in the coefficients)."""
+        a = _f64(a).ravel()
+        if a.shape[0] != 6 or _load().or_set_params(self._h, int(i), _ptr(a)) != 0:
+            raise ValueError("set_params: six coefficients and a point index in range")
+        self._a[int(i)] = a
+
     def __del__(self):
         if getattr(self, "_h", None):
             _load().or_free(self._h)
@@ -166,6 +182,27 @@ class Cloud:
         out = np.empty(x.shape[0])
         _load().or_lse(self._h, mode, C, lam, _ptr(x), x.shape[0], _ptr(out), threads or default_threads())
         return out
+
+    def sspd(self, x, C: float = 64.0, mode: int = GLOBAL, lam: float = 0.0, threads: int | None = None):
+        """Smoothed signed planar distance (Eq. SmoothedSignedPlanarDistance):
+        the self-normalised blend of <x - p_i, n_i>, lambda as in phi."""
+        x = _f64(x, 3)
+        out = np.empty(x.shape[0])
+        _load().or_baseline(self._h, 0, mode, C, lam, _ptr(x), x.shape[0], _ptr(out), None,
+                            threads or default_threads())
+        return out
+
+    def shc(self, x, C: float = 64.0, mode: int = GLOBAL, lam: float = 0.0, threads: int | None = None,
+            cond: bool = False):
+        """Signed Hopf-Cole distance (Eq. ScreenedWindingNumber): sign(w)
+        (-(1/lambda) log|w| + sigma_x) of the screened double-layer sum w,
+        lambda as in phi.  cond: also sum |terms| / |w| per query."""
+        x = _f64(x, 3)
+        out = np.empty(x.shape[0])
+        c = np.empty(x.shape[0]) if cond else None
+        _load().or_baseline(self._h, 1, mode, C, lam, _ptr(x), x.shape[0], _ptr(out), _ptr(c) if cond else None,
+                            threads or default_threads())
+        return (out, c) if cond else out
 
     def lse_grad(self, x, C: float = 64.0, mode: int = GLOBAL, lam: float = 0.0, threads: int | None = None):
         """(d~, grad d~) by forward-mode duals through the definition, the

@@ -59,6 +59,7 @@
 /* ------------------------------------------------------------------------ */
 #define ND 6
 #define FLAT_EPS 1e-8   /* |kappa| at or below this is a zero curvature (X5) */
+#define OR_PI 3.14159265358979323846
 typedef struct { double v; double d[ND]; } dual;
 
 static dual dconst(double v) { dual r; r.v = v; for (int k = 0; k < ND; ++k) r.d[k] = 0.0; return r; }
@@ -328,6 +329,19 @@ int or_set_weights(or_cloud* C, const double* w) {
 
 int64_t or_size(const or_cloud* C) { return C->n; }
 
+/* Replaces the six coefficients of point i and refits its torus (Sec. 4.1),
+ * so that tests can take finite differences of phi in the coefficients.
+ * Returns 0, or -1 for an index out of range. */
+int or_set_params(or_cloud* C, int64_t i, const double a_new[6]) {
+    if (i < 0 || i >= C->n) return -1;
+    dual a[6];
+    for (int k = 0; k < 6; ++k) { C->a[i][k] = a_new[k]; a[k] = dconst(a_new[k]); }
+    dtorus D;
+    fit_dual(C->tori[i].p, C->nrm[i], a, &D);
+    torus_from_dual(C->tori[i].p, &D, &C->tori[i]);
+    return 0;
+}
+
 /* Per-point fit record, for tests.  out[32] =
  * {q(3), nstar(3), vmin(3), u(3), c(3), R, r, kmin, kmax, kplus, kminus, H, K,
  *  sign, flat, plane, 0...} */
@@ -503,6 +517,115 @@ void or_lse(const or_cloud* C, int mode, double Cconst, double lambda, const dou
         int64_t q0 = k * per, q1 = q0 + per < m ? q0 + per : m;
         jobs[k] = (lse_job){C, &o, x, out, q0, q1 > q0 ? q1 : q0};
         pthread_create(&th[k], NULL, lse_worker, &jobs[k]);
+    }
+    for (int k = 0; k < threads; ++k) pthread_join(th[k], NULL);
+}
+
+/* ------------------------------------------------------------------------ */
+/* The paper's two convolutional baselines (Sec. 5, "Signed distance         */
+/* accuracy"), on the blend's screening: lambda = lambda_x = C / sigma_x,    */
+/* sigma_x = d_max / 2 (GLOBAL), or the fixed lambda (FIXED).               */
+/*                                                                          */
+/* phi_SSPD, Eq. SmoothedSignedPlanarDistance: the self-normalised blend of */
+/* the signed distances to the points' tangent planes,                      */
+/*   sum_i A_i <x - p_i, n_i> e_i / sum_i A_i e_i,                          */
+/*   e_i = exp(-lambda (d_i - sigma_x)),  d_i = ||x - p_i||.                */
+/*                                                                          */
+/* phi_SHC, Eq. ScreenedWindingNumber: the signed Hopf-Cole (signed         */
+/* log-sum-exp) distance of the screened double-layer sum                   */
+/*   w(x) = sum_i A_i (lambda d_i + 1) <x - p_i, n_i> / (2 pi d_i^3) e_i,   */
+/*   phi_SHC = sign(w) (-(1/lambda) log|w| + sigma_x).                      */
+/*                                                                          */
+/* The shift sigma_x cancels in both (phi_SHC: log|w| carries               */
+/* lambda sigma_x); GLOBAL uses it as printed (lambda sigma_x = C keeps the */
+/* exponentials finite), FIXED shifts by d_min instead (a fixed lambda      */
+/* times d_max / 2 can overflow double).  Readings (listed with the others): */
+/*   X24 lambda of both is the blend's (per query under GLOBAL);            */
+/*   X25 n_i is the unit input normal; A_i the per-point weights (all 1     */
+/*       unless set);                                                       */
+/*   X26 a point at the query (d_i = 0) adds nothing to w (its planar term  */
+/*       <x - p_i, n_i> is 0 as well); lambda = 0 (GLOBAL with every point   */
+/*       at x) gives phi_SHC = 0; w = 0 gives sign(w) := +1 and             */
+/*       phi_SHC = +inf, the limit of -(1/lambda) log|w| as |w| -> 0.       */
+/* ------------------------------------------------------------------------ */
+static void screening(const or_cloud* C, const or_opts* o, const double x[3], double* lambda, double* shift) {
+    double dmax = -1.0, dmin = INFINITY;
+    for (int64_t i = 0; i < C->n; ++i) {
+        const double* p = C->tori[i].p;
+        double w[3] = {x[0] - p[0], x[1] - p[1], x[2] - p[2]};
+        double d = sqrt(dot3(w, w));
+        if (d > dmax) dmax = d;
+        if (d < dmin) dmin = d;
+    }
+    if (o->mode == OR_GLOBAL) {
+        *lambda = (dmax > 0.0) ? o->C / (0.5 * dmax) : 0.0;
+        *shift = 0.5 * dmax;
+    } else {
+        *lambda = o->lambda;
+        *shift = dmin;
+    }
+}
+
+static double sspd_one(const or_cloud* C, const or_opts* o, const double x[3]) {
+    double lambda, shift;
+    screening(C, o, x, &lambda, &shift);
+    double W = 0.0, S = 0.0;
+    for (int64_t i = 0; i < C->n; ++i) {
+        const double* p = C->tori[i].p;
+        double y[3] = {x[0] - p[0], x[1] - p[1], x[2] - p[2]};
+        double e = wt_of(C, i) * exp(-lambda * (sqrt(dot3(y, y)) - shift));
+        W += e;
+        S += e * dot3(y, C->nrm[i]);
+    }
+    return S / W;
+}
+
+/* out: phi_SHC; cond (if not NULL): sum_i |term_i| / |sum_i term_i|, the
+ * condition number of w (large where the terms cancel, near w = 0). */
+static double shc_one(const or_cloud* C, const or_opts* o, const double x[3], double* cond) {
+    double lambda, shift;
+    screening(C, o, x, &lambda, &shift);
+    if (cond) *cond = 1.0;
+    if (!(lambda > 0.0)) return 0.0;
+    double w = 0.0, wabs = 0.0;
+    for (int64_t i = 0; i < C->n; ++i) {
+        const double* p = C->tori[i].p;
+        double y[3] = {x[0] - p[0], x[1] - p[1], x[2] - p[2]};
+        double d = sqrt(dot3(y, y));
+        if (d == 0.0) continue;
+        double t = wt_of(C, i) * (lambda * d + 1.0) * dot3(y, C->nrm[i]) / (2.0 * OR_PI * d * d * d) *
+                   exp(-lambda * (d - shift));
+        w += t;
+        wabs += fabs(t);
+    }
+    if (cond) *cond = wabs / fabs(w);
+    if (w == 0.0) return INFINITY;
+    return (w > 0.0 ? 1.0 : -1.0) * (-log(fabs(w)) / lambda + shift);
+}
+
+typedef struct { const or_cloud* C; const or_opts* o; const double* x; double* out; double* cond; int kind;
+                 int64_t q0, q1; } baseline_job;
+
+static void* baseline_worker(void* arg) {
+    baseline_job* J = (baseline_job*)arg;
+    for (int64_t j = J->q0; j < J->q1; ++j)
+        J->out[j] = J->kind == 0 ? sspd_one(J->C, J->o, J->x + 3 * j)
+                                 : shc_one(J->C, J->o, J->x + 3 * j, J->cond ? J->cond + j : NULL);
+    return NULL;
+}
+
+/* kind 0: phi_SSPD, kind 1: phi_SHC (cond: NULL or m doubles). */
+void or_baseline(const or_cloud* C, int kind, int mode, double Cconst, double lambda, const double* x, int64_t m,
+                 double* out, double* cond, int threads) {
+    or_opts o = {mode, Cconst, lambda, OR_SHIFT_SIGMA};
+    threads = clamp_threads(threads, m);
+    pthread_t th[256];
+    baseline_job jobs[256];
+    int64_t per = (m + threads - 1) / threads;
+    for (int k = 0; k < threads; ++k) {
+        int64_t q0 = k * per, q1 = q0 + per < m ? q0 + per : m;
+        jobs[k] = (baseline_job){C, &o, x, out, cond, kind, q0, q1 > q0 ? q1 : q0};
+        pthread_create(&th[k], NULL, baseline_worker, &jobs[k]);
     }
     for (int k = 0; k < threads; ++k) pthread_join(th[k], NULL);
 }
