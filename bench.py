@@ -55,13 +55,15 @@ WORKLOAD = ("dense_grid: ring torus N=100000 (R=1, r=0.35, noise 0.005, 2deg vMF
 #    Tensor-core loop: 9 FMA-pipe instructions + 4 MUFU per pair (the
 #    products come from the tensor cores).
 #  MUFU (XU pipe): sdf_probe_rates measures, on the box, the single
-#    operations (on B300 sqrt / rsqrt / rcp.approx about 17.9 results per SM
-#    per clock, ex2.approx about 40.5) and each record form's whole per-pair
-#    mix as dependent chains.  A direct pair needs three square roots (|x - p|,
-#    the axis distance, the tube distance) and one exp2; the measured mix rate
-#    is the MUFU ceiling.  It binds the tensor-core loop (issue ceiling
-#    128/13 = 9.8) and nearly ties the FP32-unit loop's issue ceiling
-#    (128/29 = 4.41).
+#    operations (on B300 sqrt / rsqrt / rcp.approx 16.0 results per SM per
+#    clock, ex2.approx 32.0, timed over the union of each SM's CTA windows and
+#    confirmed by CUDA events and by ncu's XU instruction counts) and each
+#    record form's whole per-pair mix as dependent chains.  A direct pair
+#    needs three square roots (|x - p|, the axis distance, the tube distance)
+#    and one exp2: 3 x 8 + 4 = 28 XU cycles per 32 pairs per SM sub-partition,
+#    4.571 pairs per SM per clock, which the measured mix matches.  It binds
+#    the tensor-core loop (issue ceiling 128/13 = 9.8) and nearly ties the
+#    FP32-unit loop's issue ceiling (128/29 = 4.41).
 INSTR_PER_PAIR = 29
 THREAD_INSTR_PER_SM_CLK = 128
 NOMINAL_RATES = {"sqrt": 16.0, "rsqrt": 16.0, "ex2": 32.0, "fma": 128.0, "rcp": 16.0}
@@ -743,12 +745,18 @@ def run_ours(args, rank, world, local):
         per_sm_clk, mufu_c, issue_c = tc_pair_ceiling(rates, counts)
         kp = prof["fwd_tc"]
         traffic = committed_traffic()
+        single = sum(counts.values()) / sum(
+            c * (m[0] / rates['sqrt'] + m[1] / rates.get('rcp', rates['sqrt']) + m[2] / rates['ex2'])
+            for f, c in counts.items() for m in [TC_FORM_COST[f][0]])
+        nominal = sum(counts.values()) / sum(
+            c * (m[0] / NOMINAL_RATES['sqrt'] + m[1] / NOMINAL_RATES['rcp'] + m[2] / NOMINAL_RATES['ex2'])
+            for f, c in counts.items() for m in [TC_FORM_COST[f][0]])
         basis = (f"{'MUFU' if mufu_c <= issue_c else 'issue'} ceiling: {sms} SMs x {fmax:.0f} MHz x "
                  f"{per_sm_clk:.3f} pairs/clk/SM over the points by form {counts}; MUFU per pair "
                  f"(sqrt, rcp, ex2) = {dict((f, c[0]) for f, c in TC_FORM_COST.items())}, each mix's "
-                 f"rate measured whole by sdf_probe_rates -> {mufu_c:.3f} (sum of the single-operation "
-                 f"rates: {sum(counts.values()) / sum(c * (m[0] / rates['sqrt'] + m[1] / rates.get('rcp', rates['sqrt']) + m[2] / rates['ex2']) for f, c in counts.items() for m in [TC_FORM_COST[f][0]]):.3f}), "
-                 f"issue fma/{dict((f, c[1]) for f, c in TC_FORM_COST.items())} -> {issue_c:.3f} "
+                 f"rate measured whole by sdf_probe_rates -> {mufu_c:.3f}; other readings: the sum of the "
+                 f"measured single-operation costs {single:.3f}, the nominal 16/16/32 per SM per clock "
+                 f"{nominal:.3f}; issue fma/{dict((f, c[1]) for f, c in TC_FORM_COST.items())} -> {issue_c:.3f} "
                  f"(unit rates {rates['source']})")
     else:
         kname, kpairs = "k_fwd", pairs_per_step

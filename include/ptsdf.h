@@ -31,7 +31,8 @@
  *  - Every call that computes cites the passage of the paper it implements.
  *    The calls that manage resources, report status or measure the device
  *    (sdf_destroy, sdf_cloud_info, sdf_cloud_forms, sdf_device_status, the
- *    sdf_serve_* bookkeeping, sdf_probe_rates, sdf_selftest_wait_timeout,
+ *    sdf_serve_* bookkeeping, sdf_probe_rates, sdf_probe_timing,
+ *    sdf_selftest_wait_timeout,
  *    sdf_profile_*, sdf_kernel_name, sdf_last_error, sdf_version) have no
  *    counterpart in the paper.
  */
@@ -293,9 +294,15 @@ PTSDF_API sdf_status sdf_combine(int32_t op, const float* d_a, const float* d_b,
  *   all of their device memory at start-up and treat any later allocation as
  *   an error.
  *
- *   Same arguments, results and errors as sdf_query, but the scratch lives in
- *   one fixed 8 MiB array compiled into the library.  Every GPU that loads the
- *   library holds that array until the process exits.
+ *   Same arguments as sdf_query, and the same option checks and errors,
+ *   with these refused as well (SDF_EINVAL): SDF_LAMBDA_RADIUS, the
+ *   packed-half precisions (SDF_F16X2, SDF_BF16X2) and SDF_ENGINE_TENSOR.
+ *   Every pair is evaluated on the FP32 units (SDF_ENGINE_AUTO included),
+ *   while sdf_query's default engine uses the tensor cores, so the two
+ *   results agree within the FP32 tolerance (1e-4 x the cloud's bounding-box
+ *   diagonal), not bit for bit.  The scratch lives in one fixed 8 MiB array
+ *   compiled into the library.  Every GPU that loads the library holds that
+ *   array until the process exits.
  *   - Limit: q <= 1,048,576 queries per call; larger q returns SDF_EINVAL with
  *     a message (split the batch).  For small batches the number of point
  *     chunks is reduced until the chunk partials fit.
@@ -492,7 +499,9 @@ PTSDF_API sdf_status sdf_mesh_level_set(const float* d_phi, int32_t nx, int32_t 
  * clears earlier records; disabling stops recording and keeps them.
  * ------------------------------------------------------------------------- */
 /* Measures, on the current device, the sustained throughput of the
- * operations that bound the pair loops, in results per SM per SM clock:
+ * operations that bound the pair loops, in results per SM per SM clock
+ * (per SM, its CTAs' results over the union of their %globaltimer windows,
+ * at the SM clock measured in the kernel):
  * rates[0] sqrt.approx, rates[1] rsqrt.approx, rates[2] ex2.approx (the
  * special-function unit), rates[3] FP32 FMA and rates[4] rcp.approx; and,
  * in pairs per SM per clock, the special-function work of one pair as the
@@ -502,6 +511,19 @@ PTSDF_API sdf_status sdf_mesh_level_set(const float* d_phi, int32_t nx, int32_t 
  * roofline reporting (about 20 ms of kernels on every SM); it does not touch
  * any cloud.  rates must hold 8 doubles. */
 PTSDF_API sdf_status sdf_probe_rates(double* rates);
+
+/* Three readings of one rate of sdf_probe_rates (a measurement aid, no
+ * counterpart in the paper): runs probe `op` (0..7, the index into rates
+ * above) once more and returns out[0] the rate per SM clock over the longest
+ * single CTA's clock64 window of each SM (overstates when an SM's CTAs do not
+ * run in lockstep), out[1] the rate over the union of the SM's CTA windows
+ * timed by %globaltimer and converted to SM clocks with the clock measured in
+ * the kernel (what sdf_probe_rates reports), out[2] results per SM per ns
+ * from the launch's CUDA-event time (all SMs), and out[3] that measured SM
+ * clock in GHz (clock64 cycles over %globaltimer ns, mean over the CTAs).
+ * out[2] / out[3] is the event-timed rate per clock.  out must hold 4
+ * doubles. */
+PTSDF_API sdf_status sdf_probe_timing(int32_t op, double* out);
 
 /* Self-test of the failure path (not part of the method): launches one
  * kernel whose thread waits, through the same bounded mbarrier wait the pair

@@ -148,7 +148,6 @@ class Cloud:
         a = _f64(a).ravel()
         if a.shape[0] != 6 or _load().or_set_params(self._h, int(i), _ptr(a)) != 0:
             raise ValueError("set_params: six coefficients and a point index in range")
-        self._a[int(i)] = a
 
     def __del__(self):
         if getattr(self, "_h", None):

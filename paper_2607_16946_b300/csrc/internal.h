@@ -94,6 +94,9 @@ struct Cloud {
 // thread-local error message
 sdf_status set_error(sdf_status st, const std::string& msg);
 sdf_status cuda_error(cudaError_t e, const char* what);
+// the option checks every query-type entry point shares (api.cu); fn names the
+// caller in the message
+sdf_status check_opts(const sdf_query_opts& o, const char* fn);
 
 // launch planning shared by the query kernels
 struct Plan {

@@ -4,10 +4,15 @@
 // pair of each torus form as a whole (the mix the pair loops issue: direct
 // 3 sqrt + 1 exp2; curvature form with kappa_min = 0, 2 sqrt + 1 rcp + 1
 // exp2; other curvature form, 3 sqrt + 2 rcp + 1 exp2), one pair per chain
-// step.  Each thread runs independent dependent chains
-// of one operation; every SM holds the same number of CTAs, which record
-// their SM and their clock64 cycle count, so the rates come out per SM and
-// per SM clock without relying on a nominal clock.
+// step.  Each thread runs independent dependent chains of one operation;
+// every SM holds the same number of CTAs, which record their SM, their
+// clock64 cycle count and their %globaltimer start and end.  A rate is, per
+// SM, the results of its CTAs over the union of their time windows (first
+// start to last end), converted to SM clocks with the clock measured in the
+// kernel (clock64 cycles over %globaltimer ns), averaged over the SMs: per SM
+// clock, without relying on a nominal clock.  (Dividing by the longest
+// single CTA's clock64 window instead overstates the rates by up to 14% on
+// B300: the CTAs of an SM start and end at different times.)
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -37,13 +42,17 @@ __device__ __forceinline__ float probe_op(float a) {
     return fmaf(a, 0.999f, 0.001f);                   // -> 1
 }
 
+// ns[2 b], ns[2 b + 1]: %globaltimer at the start and end of CTA b's timed
+// loop (the same points as its clock64 reads), for the cross-checks of
+// sdf_probe_timing.
 template <int OP>
 __global__ void __launch_bounds__(kProbeThreads) k_probe(float* __restrict__ sink, long long* __restrict__ cycles,
-                                                         int* __restrict__ smid) {
+                                                         int* __restrict__ smid, unsigned long long* __restrict__ ns) {
     float a[kProbeChains];
 #pragma unroll
     for (int i = 0; i < kProbeChains; ++i) a[i] = 0.6f + 1e-4f * (float)((threadIdx.x + 7 * i) & 255);
     __syncthreads();
+    const uint64_t g0 = global_ns();
     const long long t0 = clock64();
     for (int it = 0; it < kProbeIter; ++it) {
 #pragma unroll
@@ -51,6 +60,7 @@ __global__ void __launch_bounds__(kProbeThreads) k_probe(float* __restrict__ sin
     }
     __syncthreads();
     const long long t1 = clock64();
+    const uint64_t g1 = global_ns();
     float s = 0.f;
 #pragma unroll
     for (int i = 0; i < kProbeChains; ++i) s += a[i];
@@ -60,6 +70,8 @@ __global__ void __launch_bounds__(kProbeThreads) k_probe(float* __restrict__ sin
         unsigned id;
         asm volatile("mov.u32 %0, %%smid;" : "=r"(id));
         smid[blockIdx.x] = (int)id;
+        ns[2 * blockIdx.x] = g0;
+        ns[2 * blockIdx.x + 1] = g1;
     }
 }
 
@@ -85,11 +97,101 @@ double sm_rate(const std::vector<long long>& cyc, const std::vector<int>& sm) {
     return used ? sum / used : 0.0;
 }
 
+// The other readings of one probe launch (see sdf_probe_timing):
+//  [1] per SM, its CTAs' results over the union of their %globaltimer windows
+//      (first start to last end) times the SM clock measured in the kernel,
+//      averaged over the SMs;
+//  [2] all results over the launch's CUDA-event time and the SM count, per ns;
+//  [3] the SM clock in GHz: clock64 cycles over %globaltimer ns, mean over CTAs.
+void other_readings(const std::vector<long long>& cyc, const std::vector<int>& sm,
+                    const std::vector<unsigned long long>& ns, double event_ms, int sms, double* out) {
+    const int max_sm = *std::max_element(sm.begin(), sm.end()) + 1;
+    std::vector<unsigned long long> first(max_sm, ~0ull), last(max_sm, 0ull);
+    std::vector<int> ctas(max_sm, 0);
+    double ghz_sum = 0.0;
+    int ghz_n = 0;
+    for (size_t b = 0; b < cyc.size(); ++b) {
+        if (sm[b] < 0) continue;
+        const unsigned long long g0 = ns[2 * b], g1 = ns[2 * b + 1];
+        first[sm[b]] = std::min(first[sm[b]], g0);
+        last[sm[b]] = std::max(last[sm[b]], g1);
+        ctas[sm[b]] += 1;
+        if (g1 > g0) {
+            ghz_sum += (double)cyc[b] / (double)(g1 - g0);
+            ++ghz_n;
+        }
+    }
+    const double ghz = ghz_n ? ghz_sum / ghz_n : 0.0;
+    const double per_cta = (double)kProbeThreads * kProbeChains * kProbeIter;
+    double sum = 0.0;
+    int used = 0;
+    for (int s = 0; s < max_sm; ++s) {
+        if (ctas[s] == 0 || last[s] <= first[s]) continue;
+        sum += ctas[s] * per_cta / ((double)(last[s] - first[s]) * ghz);
+        ++used;
+    }
+    out[1] = used && ghz > 0.0 ? sum / used : 0.0;
+    out[2] = event_ms > 0.0 ? per_cta * (double)cyc.size() / (event_ms * 1e6) / sms : 0.0;
+    out[3] = ghz;
+}
+
 }  // namespace
 
 }  // namespace ptsdf
 
 using namespace ptsdf;
+
+extern "C" sdf_status sdf_probe_timing(int32_t op, double* out) {
+    if (!out || op < 0 || op > 7) return set_error(SDF_EINVAL, "sdf_probe_timing: op in [0, 7] and non-NULL out");
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return cuda_error(e, "sdf_probe_timing: device query");
+    const int blocks = sms * kProbeCtasPerSm;
+    float* sink = nullptr;
+    long long* cyc = nullptr;
+    int* smid = nullptr;
+    unsigned long long* ns = nullptr;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    e = cudaMalloc(&sink, (size_t)blocks * kProbeThreads * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&cyc, (size_t)blocks * sizeof(long long));
+    if (e == cudaSuccess) e = cudaMalloc(&smid, (size_t)blocks * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&ns, (size_t)blocks * 2 * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaEventCreate(&ev0);
+    if (e == cudaSuccess) e = cudaEventCreate(&ev1);
+    using Kern = void (*)(float*, long long*, int*, unsigned long long*);
+    const Kern kernels[8] = {k_probe<0>, k_probe<1>, k_probe<2>, k_probe<3>,
+                             k_probe<4>, k_probe<5>, k_probe<6>, k_probe<7>};
+    float ms = 0.f;
+    for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {   // the first run warms up
+        e = cudaEventRecord(ev0);
+        if (e == cudaSuccess) {
+            kernels[op]<<<blocks, kProbeThreads>>>(sink, cyc, smid, ns);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(ev1);
+        if (e == cudaSuccess) e = cudaDeviceSynchronize();
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ev0, ev1);
+    }
+    std::vector<long long> hc(blocks);
+    std::vector<int> hs(blocks);
+    std::vector<unsigned long long> hn(2 * (size_t)blocks);
+    if (e == cudaSuccess) e = cudaMemcpy(hc.data(), cyc, blocks * sizeof(long long), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(hs.data(), smid, blocks * sizeof(int), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(hn.data(), ns, 2 * (size_t)blocks * sizeof(unsigned long long), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) {
+        out[0] = sm_rate(hc, hs);
+        other_readings(hc, hs, hn, (double)ms, sms, out);
+    }
+    if (ev0) cudaEventDestroy(ev0);
+    if (ev1) cudaEventDestroy(ev1);
+    cudaFree(sink);
+    cudaFree(cyc);
+    cudaFree(smid);
+    cudaFree(ns);
+    return e == cudaSuccess ? SDF_OK : cuda_error(e, "sdf_probe_timing");
+}
 
 extern "C" sdf_status sdf_probe_rates(double* rates) {
     if (!rates) return set_error(SDF_EINVAL, "sdf_probe_rates: NULL output");
@@ -101,27 +203,37 @@ extern "C" sdf_status sdf_probe_rates(double* rates) {
     float* sink = nullptr;
     long long* cyc = nullptr;
     int* smid = nullptr;
+    unsigned long long* ns = nullptr;
     e = cudaMalloc(&sink, (size_t)blocks * kProbeThreads * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc(&cyc, (size_t)blocks * sizeof(long long));
     if (e == cudaSuccess) e = cudaMalloc(&smid, (size_t)blocks * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&ns, (size_t)blocks * 2 * sizeof(unsigned long long));
     std::vector<long long> hc(blocks);
     std::vector<int> hs(blocks);
-    using Kern = void (*)(float*, long long*, int*);
+    std::vector<unsigned long long> hn(2 * (size_t)blocks);
+    using Kern = void (*)(float*, long long*, int*, unsigned long long*);
     const Kern kernels[8] = {k_probe<0>, k_probe<1>, k_probe<2>, k_probe<3>,
                              k_probe<4>, k_probe<5>, k_probe<6>, k_probe<7>};
     for (int op = 0; op < 8 && e == cudaSuccess; ++op) {
         for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {   // the first run warms up
-            kernels[op]<<<blocks, kProbeThreads>>>(sink, cyc, smid);
+            kernels[op]<<<blocks, kProbeThreads>>>(sink, cyc, smid, ns);
             e = cudaGetLastError();
             if (e == cudaSuccess) e = cudaDeviceSynchronize();
         }
         if (e == cudaSuccess) e = cudaMemcpy(hc.data(), cyc, blocks * sizeof(long long), cudaMemcpyDeviceToHost);
         if (e == cudaSuccess) e = cudaMemcpy(hs.data(), smid, blocks * sizeof(int), cudaMemcpyDeviceToHost);
-        if (e == cudaSuccess) rates[op] = sm_rate(hc, hs);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(hn.data(), ns, 2 * (size_t)blocks * sizeof(unsigned long long), cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess) {
+            double r[4] = {0, 0, 0, 0};
+            other_readings(hc, hs, hn, 0.0, sms, r);
+            rates[op] = r[1];
+        }
     }
     cudaFree(sink);
     cudaFree(cyc);
     cudaFree(smid);
+    cudaFree(ns);
     return e == cudaSuccess ? SDF_OK : cuda_error(e, "sdf_probe_rates");
 }
 

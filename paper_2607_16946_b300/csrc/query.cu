@@ -454,20 +454,20 @@ size_t round256(size_t b) { return (b + 255) & ~(size_t)255; }
 extern "C" sdf_status sdf_query_noalloc(sdf_cloud cloud, const float* d_x, int64_t q, float* d_phi,
                                         const sdf_query_opts* opts, void* stream) {
     using namespace ptsdf;
-    if (!cloud) return set_error(SDF_EINVAL, "sdf_query_noalloc: cloud is NULL");
     if (q < 0) return set_error(SDF_EINVAL, "sdf_query_noalloc: q < 0");
     sdf_query_opts o;
     sdf_opts_default(&o);
     if (opts) o = *opts;
-    if (o.lambda_mode != SDF_LAMBDA_GLOBAL && o.lambda_mode != SDF_LAMBDA_FIXED)
+    // the options sdf_query accepts, checked the same way, then what this
+    // entry point leaves out
+    sdf_status s = check_opts(o, "sdf_query_noalloc");
+    if (s != SDF_OK) return s;
+    if (o.lambda_mode == SDF_LAMBDA_RADIUS)
         return set_error(SDF_EINVAL, "sdf_query_noalloc: GLOBAL or FIXED lambda only");
-    if (o.precision != SDF_F32) return set_error(SDF_EINVAL, "sdf_query_noalloc: unsupported precision");
-    if (o.engine != SDF_ENGINE_AUTO && o.engine != SDF_ENGINE_ALU)
+    if (o.precision != SDF_F32) return set_error(SDF_EINVAL, "sdf_query_noalloc: FP32 only");
+    if (o.engine == SDF_ENGINE_TENSOR)
         return set_error(SDF_EINVAL, "sdf_query_noalloc: only the FP32-unit engine is available here");
-    if (!(o.C > 0.f) || !std::isfinite(o.C)) return set_error(SDF_EINVAL, "sdf_query_noalloc: C must be > 0");
-    if (o.lambda_mode == SDF_LAMBDA_FIXED && (!(o.fixed_lambda >= 0.f) || !std::isfinite(o.fixed_lambda)))
-        return set_error(SDF_EINVAL, "sdf_query_noalloc: fixed_lambda must be >= 0");
-    if (!std::isfinite(o.offset) || o.split_n < 0) return set_error(SDF_EINVAL, "sdf_query_noalloc: bad options");
+    if (!cloud) return set_error(SDF_EINVAL, "sdf_query_noalloc: cloud is NULL");
     if (q == 0) return SDF_OK;
     if (!d_x || !d_phi) return set_error(SDF_EINVAL, "sdf_query_noalloc: NULL buffer");
     // one float2 per query for the prepass is the least this path needs
@@ -478,7 +478,7 @@ extern "C" sdf_status sdf_query_noalloc(sdf_cloud cloud, const float* d_x, int64
     const Cloud& c = *reinterpret_cast<const Cloud*>(cloud);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     void* scratch = nullptr;
-    sdf_status s = noalloc_scratch(&scratch);
+    s = noalloc_scratch(&scratch);
     if (s != SDF_OK) return s;
     Plan p = make_plan(c, q, o.split_n);
     // the split partials must fit too: d2 (split x q float2) + (W, S) (split x q float2)

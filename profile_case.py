@@ -1,13 +1,17 @@
-"""A reduced case of the dense-grid workload for profiler captures.
+"""A reduced case of the dense-grid workload for profiler captures
+(measurement tooling beside bench.py, not part of the library).
 
-    python -m paper_2607_16946_b300.profile_case [--queries Q] [--launches K] [--warmup W]
+    python profile_case.py [--queries Q] [--launches K] [--warmup W]
+    python profile_case.py --mode probe      # the unit-rate probe's readings
 
 Builds the dense-grid cloud (ring torus, N = 100,000; or, with --cloud
 superquadric, the sphere-tracing cloud of N = 262,144 curvature-form points)
 and evaluates an evenly strided subset of Q nodes of the 256^3 grid over
 [-1.6, 1.6]^3 with sdf_query (or the gradient and backward calls), W times
 untimed and then K times, printing the device time of each call.  Used to give ncu a short, self-terminating run of the
-same kernels the benchmark times.
+same kernels the benchmark times.  --mode probe prints, for each of the
+eight probes of sdf_probe_rates, the four readings of sdf_probe_timing (one
+JSON line) and builds no cloud.
 """
 from __future__ import annotations
 
@@ -15,7 +19,7 @@ import argparse
 import os
 import sys
 
-ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
@@ -27,7 +31,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=1)
     ap.add_argument("--points", type=int, default=None, help="default 100,000 (torus) / 262,144 (superquadric)")
     ap.add_argument("--cloud", choices=["torus", "superquadric"], default="torus")
-    ap.add_argument("--mode", choices=["query", "grad", "backward", "radius"], default="query",
+    ap.add_argument("--mode", choices=["query", "grad", "backward", "radius", "probe"], default="query",
                     help="query: sdf_query; grad: sdf_query_grad; backward: sdf_query_grad then "
                          "sdf_backward_params (each call); radius: sdf_query with SDF_LAMBDA_RADIUS and "
                          "lambda = 10^3 / D")
@@ -39,6 +43,22 @@ def main():
 
     import paper_2607_16946_b300 as ptsdf
     import synth
+
+    if args.mode == "probe":
+        import ctypes
+        import json
+        from paper_2607_16946_b300 import _abi
+        L = _abi.lib()
+        names = ["sqrt", "rsqrt", "ex2", "fma", "rcp", "pair_direct", "pair_flat", "pair_curved"]
+        out = {}
+        for op, nm in enumerate(names):
+            buf = (ctypes.c_double * 4)()
+            _abi.check(L.sdf_probe_timing(op, buf))
+            out[nm] = {"clock64_longest_cta_per_clk": buf[0], "globaltimer_union_per_clk": buf[1],
+                       "event_per_sm_per_ns": buf[2], "event_per_clk": buf[2] / buf[3] if buf[3] else None,
+                       "sm_ghz_measured": buf[3]}
+        print(json.dumps(out), flush=True)
+        return
 
     if args.cloud == "torus":
         args.points = args.points or 100_000

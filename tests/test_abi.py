@@ -105,6 +105,21 @@ def _refusals(abi):
         (lambda: L.sdf_trace(None, None, None, 4, 48, 1e-4, 6.0, None, None, None, ctypes.byref(o), None),
          b"sdf_trace: cloud"),
         (lambda: L.sdf_query_noalloc(None, None, 4, None, ctypes.byref(o), None), b"sdf_query_noalloc: cloud"),
+        # the allocation-free query refuses what sdf_query refuses, before looking at the cloud
+        (lambda: L.sdf_query_noalloc(None, None, 4, None, ctypes.byref(abi.make_opts(formula=7)), None),
+         b"sdf_query_noalloc: unknown formula"),
+        (lambda: L.sdf_query_noalloc(None, None, 4, None, ctypes.byref(abi.make_opts(
+            formula=abi.SDF_FORMULA_LSE, lambda_mode=abi.SDF_LAMBDA_FIXED, fixed_lambda=0.0)), None),
+         b"sdf_query_noalloc: the log-sum-exp distance needs fixed_lambda > 0"),
+        (lambda: L.sdf_query_noalloc(None, None, 4, None, ctypes.byref(abi.make_opts(C=-1.0)), None),
+         b"sdf_query_noalloc: C must be > 0"),
+        # and what it leaves out
+        (lambda: L.sdf_query_noalloc(None, None, 4, None, ctypes.byref(abi.make_opts(
+            lambda_mode=abi.SDF_LAMBDA_RADIUS, fixed_lambda=10.0)), None), b"GLOBAL or FIXED lambda only"),
+        (lambda: L.sdf_query_noalloc(None, None, 4, None, ctypes.byref(abi.make_opts(precision=abi.SDF_F16X2)),
+                                     None), b"sdf_query_noalloc: FP32 only"),
+        (lambda: L.sdf_query_noalloc(None, None, 4, None, ctypes.byref(abi.make_opts(engine=abi.SDF_ENGINE_TENSOR)),
+                                     None), b"only the FP32-unit engine"),
         (lambda: L.sdf_knn_mean_distance(None, 64, ctypes.byref(d), None), b"sdf_knn_mean_distance"),
         (lambda: L.sdf_cloud_info(None, ctypes.byref(i64), ctypes.byref(f), None, None), b"sdf_cloud_info: cloud"),
         (lambda: L.sdf_cloud_forms(None, ctypes.byref(i64), None), b"sdf_cloud_forms: cloud"),

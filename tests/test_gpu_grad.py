@@ -3,7 +3,9 @@
   sdf_query_grad       d phi / d x (App. D plus the lambda_x(x) term) vs the
                        oracle's forward-mode duals, and vs central finite
                        differences of the oracle (h = 1e-3, Richardson).
-  sdf_backward_params  d(sum G phi) / d a vs the oracle's duals through the fit.
+  sdf_backward_params  d(sum G phi) / d a vs the oracle's duals through the fit,
+                       and vs central differences of the oracle's phi in the
+                       coefficients (N = 65,536).
   autograd             the torch.autograd.Function routes both.
 Tolerance: 1e-3 relative to max(1, |reference|) per entry (FP32 path).
 Queries where a distant point ties for the farthest (within 1e-5 of d_max,
@@ -35,16 +37,26 @@ def kink_free(p, x, tau, sep=0.05):
     """True for queries whose farthest point is unambiguous: no point lying
     more than `sep` away from the farthest one is within `tau` of d_max.  (At a
     tie between distant far points lambda_x has a kink; ties between close
-    neighbours change grad lambda_x by a negligible amount.)"""
-    keep = np.empty(x.shape[0], bool)
-    for i0 in range(0, x.shape[0], 256):
-        xs = x[i0:i0 + 256]
-        d = np.linalg.norm(xs[:, None, :] - p[None], axis=2)
-        j = np.argmax(d, axis=1)
-        near_tie = d >= (d.max(1, keepdims=True) - tau)
-        spread = np.linalg.norm(p[None] - p[j][:, None, :], axis=2)
-        keep[i0:i0 + 256] = ~np.any(near_tie & (spread > sep), axis=1)
-    return keep
+    neighbours change grad lambda_x by a negligible amount.)  Squared
+    distances from |x|^2 + |p|^2 - 2 <x, p> in float32 on the host cores
+    (torch), with the band widened by 1e-5 to cover their rounding; the
+    spread is computed for the points in the band only."""
+    import torch
+    P = torch.as_tensor(np.asarray(p, np.float32))
+    X = torch.as_tensor(np.asarray(x, np.float32))
+    pp = (P * P).sum(1)
+    keep = torch.empty(X.shape[0], dtype=torch.bool)
+    for i0 in range(0, X.shape[0], 1024):
+        xs = X[i0:i0 + 1024]
+        d2 = torch.addmm(pp[None] + (xs * xs).sum(1, keepdim=True), xs, P.T, alpha=-2.0)
+        dmax2, j = d2.max(1)
+        lo = (dmax2.clamp_min(0).sqrt() - tau - 1e-5).clamp_min(0)
+        rows, cols = torch.nonzero(d2 >= (lo * lo)[:, None], as_tuple=True)
+        far = ((P[cols] - P[j[rows]]) ** 2).sum(1) > sep * sep
+        bad = torch.zeros(xs.shape[0], dtype=torch.bool)
+        bad[rows[far]] = True
+        keep[i0:i0 + 1024] = ~bad
+    return keep.numpy()
 
 
 def config4(n=65536, q=1_000_000):
@@ -67,15 +79,78 @@ def check_close(got, ref, tol=GTOL):
 
 
 def test_grad_config4_subset(ptsdf, oracle_mod):
-    """Differentiation config (N = 65,536 perturbed ellipsoid), 768 sampled
-    queries of the 1e6: phi and d phi / d x against the oracle's duals."""
-    p, n, a, x = config4(q=4096)
-    x = x[kink_free(p, x, 1e-5)][:768]
+    """Differentiation config (N = 65,536 perturbed ellipsoid), 65,536 seeded
+    queries of the 1e6 in one call: phi against the oracle on all of them,
+    d phi / d x against the oracle's duals on 2,048 of them and against
+    Richardson-extrapolated central differences of the oracle's phi (h = 1e-4,
+    h / 2; a wider stencil would straddle the kink of lambda_x for a third of
+    the queries of this dense cloud) in one seeded component of each of the
+    65,536 queries away from such a kink."""
+    p, n, a, x = config4(q=65_536)
     cl = ptsdf.Cloud(p, n, a)
     phi, g, _ = gpu_grad(cl, x)
-    ophi, og = oracle_mod.Cloud(p, n, a).grad_x(x)
-    assert np.abs(phi - ophi).max() <= 1e-4 * np.linalg.norm(p.max(0) - p.min(0))
-    check_close(g, og)
+    oc = oracle_mod.Cloud(p, n, a)
+    assert np.abs(phi - oc.phi(x)).max() <= 1e-4 * np.linalg.norm(p.max(0) - p.min(0))
+    sub = np.flatnonzero(kink_free(p, x[:2600], 1e-5))[:2048]
+    assert sub.size == 2048
+    _, og = oc.grad_x(x[sub])
+    check_close(g[sub], og)
+    keep = np.flatnonzero(kink_free(p, x, 2e-4))     # the stencil moves x by at most 1e-4
+    assert keep.size > 0.95 * x.shape[0], keep.size
+    comp = np.random.Generator(np.random.PCG64(6)).integers(0, 3, size=keep.size)
+    e = np.zeros((keep.size, 3))
+    e[np.arange(keep.size), comp] = 1.0
+    xs = x[keep]
+    fd = [(oc.phi(xs + h * e) - oc.phi(xs - h * e)) / (2 * h) for h in (1e-4, 5e-5)]
+    check_close(g[keep, comp], (4 * fd[1] - fd[0]) / 3, tol=2e-3)
+
+
+def test_backward_params_config4_finite_differences(ptsdf, oracle_mod):
+    """d(sum_q G_q phi_q) / d a on the differentiation cloud (N = 65,536):
+    512 entries against central differences of the oracle's phi in that
+    coefficient (the point's torus refitted at a +- h, h = 1e-3 and h / 2,
+    Richardson), 64 seeded queries and upstream gradients.  The entries are
+    drawn from the 2,000 largest of the oracle's dual-number gradient, so each
+    one is carried by queries near its point."""
+    import torch
+    p, n, a, x = config4(q=400)
+    x = x[kink_free(p, x, 1e-5)][:64]
+    G = f32(np.random.Generator(np.random.PCG64(44)).normal(size=x.shape[0]))
+    cl = ptsdf.Cloud(p, n, a)
+    xt = torch.as_tensor(x, dtype=torch.float32, device="cuda")
+    _, _, saved = cl.query_grad(xt)
+    gp = cl.backward_params(xt, saved, torch.as_tensor(G, dtype=torch.float32, device="cuda"))
+    torch.cuda.synchronize()
+    assert cl.device_status() == 0
+    gp = gp.cpu().numpy().astype(np.float64)
+    oc = oracle_mod.Cloud(p, n, a)
+    dual = oc.grad_params(x, G)
+    top = np.argsort(-np.abs(dual).ravel())[:2000]
+    # away from near-umbilic points, where a step of h can swap which principal
+    # curvature is kappa_min (the fit is not differentiable across that swap)
+    gap = {}
+    for i in set(int(f) // 6 for f in top):
+        fr = oracle_mod.fit_record(p[i], n[i], a[i])
+        gap[i] = abs(abs(fr["kplus"]) - abs(fr["kminus"])) / max(abs(fr["kplus"]), abs(fr["kminus"]))
+    top = np.array([f for f in top if gap[int(f) // 6] > 0.05])
+    pick = np.random.Generator(np.random.PCG64(45)).choice(top, size=512, replace=False)
+    rich = np.empty(512)
+    for m, flat in enumerate(pick):
+        i, k = divmod(int(flat), 6)
+        fd = []
+        for h in (1e-3, 5e-4):
+            L = []
+            for sgn in (1.0, -1.0):
+                ai = a[i].copy()
+                ai[k] += sgn * h
+                oc.set_params(i, ai)
+                L.append(float(np.dot(G, oc.phi(x))))
+            fd.append((L[0] - L[1]) / (2 * h))
+        oc.set_params(i, a[i])
+        rich[m] = (4 * fd[1] - fd[0]) / 3
+    got = gp.ravel()[pick]
+    scale = np.abs(rich).max()
+    assert np.abs(got - rich).max() <= 2e-3 * scale, (np.abs(got - rich).max(), scale)
 
 
 @pytest.mark.parametrize("split", [0, 1, 4])
@@ -100,29 +175,6 @@ def test_grad_fixed_lambda(ptsdf, oracle_mod):
     _, g, _ = gpu_grad(cl, x, lambda_mode=ptsdf.SDF_LAMBDA_FIXED, fixed_lambda=150.0)
     _, og = oracle_mod.Cloud(p, n, a).grad_x(x, mode=oracle_mod.FIXED, lam=150.0)
     check_close(g, og)
-
-
-def test_grad_vs_finite_differences(ptsdf, oracle_mod):
-    """1,024 sampled entries of d phi / d x (config 4 cloud, N reduced to
-    8,192): GPU analytic vs central differences of the FP64 oracle with
-    h = 1e-3 and h / 2, Richardson-extrapolated."""
-    p, n, a, x = config4(n=8192, q=4000)
-    x = x[kink_free(p, x, 2e-3)]     # the stencil moves x by at most 1e-3
-    rng = np.random.Generator(np.random.PCG64(5))
-    rows = rng.choice(x.shape[0], size=1024, replace=False)
-    comp = rng.integers(0, 3, size=1024)
-    xs = x[rows]
-    cl = ptsdf.Cloud(p, n, a)
-    _, g, _ = gpu_grad(cl, xs)
-    oc = oracle_mod.Cloud(p, n, a)
-    e = np.zeros((1024, 3))
-    e[np.arange(1024), comp] = 1.0
-    fd = []
-    for h in (1e-3, 5e-4):
-        fd.append((oc.phi(xs + h * e) - oc.phi(xs - h * e)) / (2 * h))
-    rich = (4 * fd[1] - fd[0]) / 3
-    got = g[np.arange(1024), comp]
-    check_close(got, rich, tol=2e-3)
 
 
 def test_backward_params(ptsdf, oracle_mod):

@@ -5,9 +5,12 @@ FP64 Newton iteration (oracle/morph.py).
 - Unit-sphere cloud: every seed lands on radius 1 + c with normal x0 / |x0|
   (closed form; phi = |x| - 1 there).
 - Mixed cloud, the cloud's own points as seeds, level -0.05 (erosion's first
-  half): moved points within 1e-4 x AABB diagonal of the oracle's and normals
-  within 1e-3, on the seeds both iterations settle (residual below 1e-5 of
-  the diagonal on the GPU, 1e-8 in the oracle); at least 90% of the seeds.
+  half), 6 Newton steps: for EVERY seed the moved point agrees with the
+  oracle's within 1e-4 x the AABB diagonal and the residual within the FP32
+  bar, whether or not the iteration has settled (some seeds, started where
+  |grad phi| is small, are still moving after 6 steps on both sides); the
+  residual is the oracle's phi - c at the returned point; the normal is the
+  oracle's unit gradient there (where |grad phi| >= 0.2, to 2e-3 / |grad phi|).
 - In place (d_x = d_x0) through the C ABI, and option errors.
 """
 import ctypes
@@ -16,7 +19,7 @@ import numpy as np
 import pytest
 
 import synth
-from workloads import aabb_diag, f32, mixed_cloud
+from workloads import TOL_REL, aabb_diag, f32, mixed_cloud
 
 pytestmark = pytest.mark.gpu
 
@@ -53,16 +56,25 @@ def test_mixed_cloud_vs_oracle(ptsdf, oracle_mod):
     p, n, a = mixed_cloud(81)
     cl = ptsdf.Cloud(p, n, a)
     seeds = p[::4]
-    x, nrm, res = cl.project_level_set(seeds, -0.05, max_iter=6)
+    level, iters = -0.05, 6
+    x, nrm, res = cl.project_level_set(seeds, level, max_iter=iters)
     x, nrm, res = (t.cpu().numpy().astype(np.float64) for t in (x, nrm, res))
-    ox, onrm, ores = project_level_set(oracle_mod.Cloud(p, n, a), seeds, -0.05, max_iter=6)
+    oc = oracle_mod.Cloud(p, n, a)
+    ox, onrm, ores = project_level_set(oc, seeds, level, max_iter=iters)
     diag = aabb_diag(p)
-    settled = (np.abs(res) <= 1e-5 * diag) & (np.abs(ores) <= 1e-8)
-    assert settled.mean() >= 0.9
-    close = np.linalg.norm(x - ox, axis=1) <= 1e-4 * diag
-    assert close[settled].mean() >= 0.9, close[settled].mean()
-    both = settled & close
-    assert np.abs(nrm[both] - onrm[both]).max() <= 1e-3
+    dx = np.linalg.norm(x - ox, axis=1)
+    print("max |x - x_oracle| / diag", dx.max() / diag, "settled", np.mean(np.abs(ores) <= 1e-8))
+    assert dx.max() <= 1e-4 * diag, (int(dx.argmax()), dx.max())
+    assert np.abs(res - ores).max() <= TOL_REL * diag
+    # what the GPU returns is valid in the oracle's field at the returned point
+    fphi, fg = oc.grad_x(x)
+    assert np.abs(res - (fphi - level)).max() <= TOL_REL * diag
+    gnorm = np.linalg.norm(fg, axis=1)
+    ok = gnorm >= 0.2
+    assert ok.mean() > 0.9
+    unit = fg[ok] / gnorm[ok, None]
+    assert (np.abs(nrm[ok] - unit).max(1) <= 2e-3 * np.maximum(1.0, gnorm[ok]) / gnorm[ok]).all()
+    assert (np.abs(nrm[ok] - onrm[ok]).max(1) <= 2e-3 * np.maximum(1.0, gnorm[ok]) / gnorm[ok]).all()
 
 
 def test_in_place_and_errors(ptsdf):

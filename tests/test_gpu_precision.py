@@ -10,8 +10,17 @@ from workloads import aabb_diag, config2_cloud, f32, mixed_cloud
 
 pytestmark = pytest.mark.gpu
 
-# max |phi - phi_oracle| / AABB diagonal allowed for each variant
-BOUNDS = {"f16x2": 2e-3, "bf16x2": 2e-2}
+# max |phi - phi_oracle| / AABB diagonal allowed for each variant and cloud,
+# about 3x the error measured on a B300 (max over the 3,000 queries of the
+# test; dense-grid torus: F16X2 4.4e-7, BF16X2 7.1e-6; mixed cloud: F16X2
+# 1.4e-4, BF16X2 6.9e-4; mixed cloud with weights log-uniform in [0.1, 10]:
+# F16X2 5.1e-5, BF16X2 8.4e-4).  On the mixed cloud both exceed the FP32
+# bar (1e-4): rounding the exponent A0 - L d to 11 (8) bits costs up to
+# 2^-11 (2^-8) of |A0 - L d| in it, and the cloud's points spread their g_i
+# widely within the screening length.
+BOUNDS = {("f16x2", "torus"): 1.5e-6, ("bf16x2", "torus"): 2.5e-5,
+          ("f16x2", "mixed"): 4.5e-4, ("bf16x2", "mixed"): 2.2e-3,
+          ("f16x2", "mixed_weighted"): 1.6e-4, ("bf16x2", "mixed_weighted"): 2.6e-3}
 
 
 @pytest.fixture(scope="module")
@@ -43,7 +52,7 @@ def test_packed_weights_error(ptsdf, oracle_mod, prec, cloud):
     err32 = np.abs(f32r.cpu().numpy() - ref) / aabb_diag(p)
     print(prec, cloud, "max", err.max(), "p99", np.quantile(err, 0.99), "fp32 max", err32.max())
     assert np.isfinite(err).all()
-    assert err.max() <= BOUNDS[prec]
+    assert err.max() <= BOUNDS[(prec, cloud)]
     assert err32.max() <= 1e-4
 
 

@@ -147,12 +147,12 @@ def test_host_buffers_match_device(ptsdf, torch_mod):
 
 
 def test_config2_subset(ptsdf, torch_mod, oracle_mod):
-    """Dense grid cloud (N = 100,000 noisy ring torus) on 8,192 sampled grid
-    nodes plus the nodes next to the torus axis and the surface."""
+    """Dense grid cloud (N = 100,000 noisy ring torus) on 65,536 seeded grid
+    nodes, element by element."""
     p, n, a = config2_cloud()
     cl = ptsdf.Cloud(p, n, a)
     rng = np.random.Generator(np.random.PCG64(2))
-    idx = rng.integers(0, GRID_RES ** 3, size=8192)
+    idx = rng.integers(0, GRID_RES ** 3, size=65_536)
     x = f32(synth.grid_query_index(idx, GRID_RES))
     got = run(cl, x, torch_mod)
     ref = oracle_mod.Cloud(p, n, a).phi(x)

@@ -1,10 +1,20 @@
 """GPU parity of sphere tracing (Sec. 6) and of the Boolean combinations.
 
-Tracing decides integers (hit or miss, step counts) from floating point, so
-rays are compared by outcome: both sides must agree on hit / miss for at
-least 99% of rays; where both hit, t_hit agrees to 1e-3 and the step counts
-to within 1 for 99% of rays.  The disagreeing rays must be borderline: their
-oracle values at the deciding step lie within 1e-3 of eps or of t_max.
+Tracing decides integers (hit or miss, step counts) from floating point.  A
+ray agrees with the oracle's tracer when both hit within 1e-3 in t_hit and
+1 in the step count, or both miss.  Every other ray must be borderline, shown
+against the oracle's own trajectory (t_k, f_k = phi(o + t_k d) - offset),
+which the test re-traces step by step with the oracle's phi:
+  - the side that stopped first stopped marginally: the oracle's f at that
+    stop is within DELTA_F of eps (the oracle stopped with f in
+    [eps - DELTA_F, eps), or at the GPU's stop the oracle's field, or an
+    oracle step within DELTA_T in t, is below eps + DELTA_F);
+  - or the step budget decided it (a side used max_steps - 1 or more
+    evaluations), or t_max did (a stop or the oracle's last t within DELTA_T
+    of t_max).
+DELTA_F = 2e-5 is a fifth of eps, about 10x the FP32 error of phi near the
+surface on these clouds; DELTA_T = 1e-3.  At most 1% of the rays may be
+borderline disagreements.
 """
 import numpy as np
 import pytest
@@ -55,6 +65,77 @@ def test_trace_sphere_closed_form(ptsdf):
     assert np.all(nrm[~(t > 0)] == 0)
 
 
+DELTA_F = 2e-5
+DELTA_T = 1e-3
+
+
+def oracle_paths(oc, org, dirs, max_steps, eps, t_max, offset=0.0):
+    """The oracle tracer's trajectory of every ray, [(t_k, f_k)], by the same
+    stepping rule as its tracer (each step one oracle phi per live ray)."""
+    m = org.shape[0]
+    t = np.zeros(m)
+    live = np.ones(m, bool)
+    paths = [[] for _ in range(m)]
+    for _ in range(max_steps):
+        idx = np.flatnonzero(live)
+        if idx.size == 0:
+            break
+        f = oc.phi(org[idx] + t[idx, None] * dirs[idx]) - offset
+        for j, fj in zip(idx, f):
+            paths[j].append((t[j], fj))
+        hit = f < eps
+        live[idx[hit]] = False
+        go = idx[~hit]
+        t[go] += f[~hit]
+        live[go[t[go] > t_max]] = False
+    return paths
+
+
+def borderline(path, t_g, s_g, t_o, s_o, f_at_gpu_stop, eps, t_max, max_steps):
+    """Why a disagreeing ray may disagree (None: no reason found)."""
+    if max(s_g, s_o) >= max_steps - 1:
+        return "step budget"
+    last_t = path[-1][0] + (path[-1][1] if path[-1][1] >= eps else 0.0)
+    if abs(last_t - t_max) <= DELTA_T or max(t_g, t_o) >= t_max - DELTA_T:
+        return "t_max"
+    gpu_first = t_g >= 0 and (t_o < 0 or t_g < t_o)
+    if gpu_first:
+        if f_at_gpu_stop <= eps + DELTA_F:
+            return "gpu stop marginal in the oracle's field"
+        if any(abs(tk - t_g) <= DELTA_T and fk <= eps + DELTA_F for tk, fk in path):
+            return "oracle passed the gpu stop marginally"
+    elif t_o >= 0 and path[-1][1] >= eps - DELTA_F:
+        return "oracle stop marginal"
+    return None
+
+
+def check_trace_against_oracle(oc, org, dirs, t, steps, max_steps=48, eps=1e-4, t_max=6.0, max_frac=0.01):
+    to, so = oc.trace(org, dirs, max_steps=max_steps, eps=eps, t_max=t_max)
+    agree = ((t < 0) & (to < 0)) | ((t >= 0) & (to >= 0) & (np.abs(t - to) <= 1e-3) & (np.abs(steps - so) <= 1))
+    bad = np.flatnonzero(~agree)
+    assert bad.size <= max_frac * t.size, (bad.size, t.size)
+    if bad.size == 0:
+        return to, so
+    paths = oracle_paths(oc, org[bad], dirs[bad], max_steps, eps, t_max)
+    # the re-trace reproduces the oracle's tracer exactly (same phi, same steps)
+    for k, j in enumerate(bad):
+        hit = paths[k][-1][1] < eps
+        assert len(paths[k]) == so[j] and (paths[k][-1][0] == to[j] if hit else to[j] < 0), j
+    tg = np.where(t[bad] >= 0, t[bad], 0.0)
+    f_gpu_stop = oc.phi(org[bad] + tg[:, None] * dirs[bad])
+    unexplained = []
+    for k, j in enumerate(bad):
+        why = borderline(paths[k], t[j], steps[j], to[j], so[j], f_gpu_stop[k] if t[j] >= 0 else np.inf,
+                         eps, t_max, max_steps)
+        print(f"ray {j}: gpu (t {t[j]:.6f}, steps {steps[j]}), oracle (t {to[j]:.6f}, steps {so[j]}), "
+              f"oracle f at gpu stop {f_gpu_stop[k] if t[j] >= 0 else float('nan'):.3e}, "
+              f"oracle min f {min(f for _, f in paths[k]):.3e}, last f {paths[k][-1][1]:.3e}: {why}")
+        if why is None:
+            unexplained.append(int(j))
+    assert not unexplained, unexplained
+    return to, so
+
+
 def test_trace_superquadric_subset(ptsdf, oracle_mod):
     """Sphere-tracing configuration (N = 262,144 noisy superquadric, pinhole
     camera at distance 3): 1,024 seeded rays of the 512 x 512 image, 48 steps,
@@ -67,14 +148,9 @@ def test_trace_superquadric_subset(ptsdf, oracle_mod):
     cl = ptsdf.Cloud(p, n, a)
     t, steps, nrm = gpu_trace(cl, org, dirs, max_steps=48, eps=1e-4, t_max=6.0)
     oc = oracle_mod.Cloud(p, n, a)
-    to, so = oc.trace(org, dirs, max_steps=48, eps=1e-4, t_max=6.0)
-    gh, oh = t >= 0, to >= 0
-    agree = gh == oh
-    assert agree.mean() >= 0.99, agree.mean()
-    both = gh & oh
+    to, so = check_trace_against_oracle(oc, org, dirs, t, steps)
+    both = (t >= 0) & (to >= 0) & (np.abs(t - to) <= 1e-3)
     assert both.sum() > 50
-    ok = (np.abs(t[both] - to[both]) <= 1e-3) & (np.abs(steps[both] - so[both]) <= 1)
-    assert ok.mean() >= 0.99, ok.mean()
     # normals at hits where both sides hit
     xh = org[both] + to[both, None] * dirs[both]
     _, og = oc.grad_x(xh)
@@ -104,10 +180,5 @@ def test_trace_full_image_sampled(ptsdf, oracle_mod):
     cl = ptsdf.Cloud(p, n, a)
     t, steps, _ = gpu_trace(cl, org, dirs, max_steps=48, eps=1e-4, t_max=6.0, normals=False)
     rows = np.random.Generator(np.random.PCG64(8)).choice(org.shape[0], size=200, replace=False)
-    to, so = oracle_mod.Cloud(p, n, a).trace(org[rows], dirs[rows], max_steps=48, eps=1e-4, t_max=6.0)
-    tg, sg = t[rows], steps[rows]
-    agree = (tg >= 0) == (to >= 0)
-    assert agree.mean() >= 0.98
-    both = (tg >= 0) & (to >= 0)
-    ok = (np.abs(tg[both] - to[both]) <= 1e-3) & (np.abs(sg[both] - so[both]) <= 1)
-    assert ok.mean() >= 0.98
+    check_trace_against_oracle(oracle_mod.Cloud(p, n, a), org[rows], dirs[rows], t[rows], steps[rows],
+                               max_frac=0.02)

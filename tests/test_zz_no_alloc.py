@@ -58,6 +58,38 @@ def test_noalloc_matches_query_twice(env, q):
         assert diff <= tol, (call, diff, tol)
 
 
+@pytest.mark.parametrize("q,split,kw", [
+    (70_000, 16, {}),          # 16 chunks do not fit: the split drops to 7
+    (1_048_000, 4, {}),        # near the limit: the split drops to 1 (no partials)
+    (3000, 0, {"formula": 1}),                                   # the log-sum-exp distance
+    (3000, 3, {"formula": 1, "lambda_mode": 1, "fixed_lambda": 40.0}),
+    (3000, 3, {"lambda_mode": 1, "fixed_lambda": 40.0, "offset": 0.05}),
+])
+def test_noalloc_split_reduction_and_formulas(env, q, split, kw):
+    """The chunk-count reduction that keeps the partials inside the fixed
+    array, and the other formulas and lambda modes, against sdf_query on the
+    same inputs, twice in a row."""
+    m, abi, torch = env
+    L = abi.lib()
+    p, n, a = mixed_cloud(33)
+    cloud = m.Cloud(p, n, a)
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    opts = abi.make_opts(split_n=split, **kw)
+    tol = TOL_REL * aabb_diag(p)
+    for call in range(2):
+        x = torch.as_tensor(f32(synth.uniform_queries(q, 950 + call, -1.5, 1.5)), dtype=torch.float32,
+                            device="cuda")
+        ref = torch.empty(q, device="cuda")
+        got = torch.full((q,), float("nan"), device="cuda")
+        abi.check(_call(L, L.sdf_query, cloud, x, ref, opts, stream), "sdf_query")
+        abi.check(_call(L, L.sdf_query_noalloc, cloud, x, got, opts, stream), "sdf_query_noalloc")
+        torch.cuda.synchronize()
+        assert cloud.device_status() == 0
+        assert bool(torch.isfinite(got).all())
+        diff = (got - ref).abs().max().item()
+        assert diff <= tol, (q, split, kw, call, diff, tol)
+
+
 def test_noalloc_rejects_oversized_batch(env):
     m, abi, torch = env
     L = abi.lib()
