@@ -483,9 +483,9 @@ def run_radius_leg(dev, cloud, x, phi, steps: int = 3):
     L = _abi.lib()
     out = {}
     t0 = time.perf_counter()
-    D = cloud.knn_mean_distance(64)
+    lam = cloud.paper_lambda()            # sdf_paper_lambda: 10^3 / D, D = sdf_knn_mean_distance(64)
     t_knn = time.perf_counter() - t0
-    lam = 1e3 / D
+    D = 1e3 / lam
     kw = dict(lambda_mode=ptsdf.SDF_LAMBDA_RADIUS, fixed_lambda=lam)
     cloud.query(x, out=phi, **kw)
     torch.cuda.synchronize(dev)
@@ -501,7 +501,7 @@ def run_radius_leg(dev, cloud, x, phi, steps: int = 3):
                          "outputs_finite": bool(torch.isfinite(phi).all())}
     p, n, a = synth.superquadric(262_144, 1003)
     cl = ptsdf.Cloud(p, n, a)
-    lam_t = 1e3 / cl.knn_mean_distance(64)
+    lam_t = cl.paper_lambda()
     org, dirs = synth.camera_rays(512, 512, 1003)
     org = torch.as_tensor(org, dtype=torch.float32, device=dev)
     dirs = torch.as_tensor(dirs, dtype=torch.float32, device=dev)
@@ -592,34 +592,97 @@ def run_mixed_leg(dev, cloud, x, phi, points, normals, params, steps: int = 2):
     weights = np.exp(np.random.Generator(np.random.PCG64(SEED + 12)).uniform(np.log(0.5), np.log(2.0),
                                                                              size=len(points))).astype(np.float32)
     wcloud = ptsdf.Cloud(points, normals, params, weights=weights)
-    cases = (("fp32_tensor", cloud, dict(precision=_abi.SDF_F32, engine=_abi.SDF_ENGINE_TENSOR), ref),
-             ("fp32_alu", cloud, dict(precision=_abi.SDF_F32, engine=_abi.SDF_ENGINE_ALU), ref),
-             ("f16x2", cloud, dict(precision=_abi.SDF_F16X2, engine=_abi.SDF_ENGINE_ALU), ref),
-             ("bf16x2", cloud, dict(precision=_abi.SDF_BF16X2, engine=_abi.SDF_ENGINE_ALU), ref),
-             ("lse_tensor", cloud, dict(formula=_abi.SDF_FORMULA_LSE, engine=_abi.SDF_ENGINE_TENSOR), orc.lse(xs)),
-             ("weighted_fp32", wcloud, dict(), oracle.Cloud(points, normals, params, weights=weights).phi(xs)))
+    shc_ref, shc_cond = orc.shc(xs, cond=True)
+    well = shc_cond <= 1e3         # phi_SHC is compared where its double-layer sum is not a cancellation
+    cases = (("fp32_tensor", cloud, dict(precision=_abi.SDF_F32, engine=_abi.SDF_ENGINE_TENSOR), ref, None),
+             ("fp32_alu", cloud, dict(precision=_abi.SDF_F32, engine=_abi.SDF_ENGINE_ALU), ref, None),
+             ("f16x2", cloud, dict(precision=_abi.SDF_F16X2, engine=_abi.SDF_ENGINE_ALU), ref, None),
+             ("bf16x2", cloud, dict(precision=_abi.SDF_BF16X2, engine=_abi.SDF_ENGINE_ALU), ref, None),
+             ("lse_tensor", cloud, dict(formula=_abi.SDF_FORMULA_LSE, engine=_abi.SDF_ENGINE_TENSOR), orc.lse(xs),
+              None),
+             ("weighted_fp32", wcloud, dict(), oracle.Cloud(points, normals, params, weights=weights).phi(xs), None),
+             ("sspd", cloud, dict(formula=_abi.SDF_FORMULA_SSPD), orc.sspd(xs), None),
+             ("shc", cloud, dict(formula=_abi.SDF_FORMULA_SHC), shc_ref, well))
     diag = float(np.linalg.norm(points.max(0) - points.min(0)))
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    rates = probe_rates(_abi.lib())
+    L = _abi.lib()
     out = {}
-    for name, cl, kw, r in cases:
+    for name, cl, kw, r, mask in cases:
         cl.query(x, out=phi, **kw)
         torch.cuda.synchronize(dev)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        L.sdf_profile_enable(1)
         e0.record()
         for _ in range(steps):
             cl.query(x, out=phi, **kw)
         e1.record()
         torch.cuda.synchronize(dev)
+        L.sdf_profile_enable(0)
+        prof = _profile_window(L, _abi)
         s = e0.elapsed_time(e1) / 1e3 / steps
         err = np.abs(phi[torch.as_tensor(idx, device=dev)].double().cpu().numpy() - r) / diag
+        if mask is not None:
+            err = err[mask]
         out[name] = {"value": x.shape[0] * N_POINTS / s / 1e9, "unit": UNIT, "ms_per_step": s * 1e3,
                      "err_max_rel_diag": float(err.max()), "err_p99_rel_diag": float(np.quantile(err, 0.99))}
+        if mask is not None:
+            out[name]["compared"] = f"{int(mask.sum())} of {mask.size} nodes (oracle condition number <= 1e3)"
+        if "plane" in prof:
+            # the baselines' pair loop: 1 sqrt (SSPD) or rsqrt (SHC) + 1 exp2 per pair on the XU pipe
+            mufu = 1.0 / (1.0 / rates["sqrt"] + 1.0 / rates["ex2"])
+            peak = sms * FALLBACK_MAX_SM_MHZ * 1e6 * mufu / 1e9
+            ach = x.shape[0] * N_POINTS / (prof["plane"]["ms"] / steps / 1e3) / 1e9
+            out[name]["roofline"] = {"bound": "alu", "kernel": "k_fwd_plane", "achieved": ach, "peak": peak,
+                                     "unit": UNIT, "frac": ach / peak,
+                                     "peak_basis": f"XU: 1 sqrt/rsqrt + 1 ex2 per pair at the measured rates = "
+                                                   f"{mufu:.2f} pairs/clk/SM x {sms} SMs x "
+                                                   f"{FALLBACK_MAX_SM_MHZ:.0f} MHz"}
     wcloud.close()
     out["note"] = ("fp32_tensor: products on the tensor cores (split f16, FP32 accumulate), pairs finished in "
                    "FP32; fp32_alu: FP32 units only; f16x2/bf16x2: packed-half exp2 of a lane's two weights on "
                    "the FP32-unit loop; lse_tensor: the log-sum-exp distance (Eq. ConvolutionalDistanceFormula, "
                    "h = 1) from the same sums; weighted_fp32: per-point weights log-uniform in [0.5, 2] "
                    "(direct tiles on the tensor cores, curvature-form tiles on the FP32 units); "
+                   "sspd / shc: the paper's baselines phi_SSPD (Eq. SmoothedSignedPlanarDistance) and phi_SHC "
+                   "(Eq. ScreenedWindingNumber) on the FP32 units with packed .f32x2 arithmetic; "
                    "error = |out - oracle| / AABB diagonal on 4096 seeded grid nodes")
+    return out
+
+
+def compact_summary(line: dict) -> dict:
+    """The other legs in a few numbers each (value, roofline fraction,
+    error against the oracle), rounded."""
+    def r(v, d=4):
+        return None if v is None else float(f"{v:.{d}g}")
+    out = {"dense_grid": {"gpairs_s": r(line["value"]), "frac": r(line["roofline"]["frac"], 3),
+                          "e2e_gpairs_s": r(line["e2e"]["value"])}}
+    for k, v in line.get("mixed", {}).items():
+        if isinstance(v, dict):
+            out[k] = {"gpairs_s": r(v["value"]), "err_max": r(v["err_max_rel_diag"], 2)}
+            if "roofline" in v:
+                out[k]["frac"] = r(v["roofline"]["frac"], 3)
+    g = line.get("grad")
+    if g:
+        out["grad"] = {"fwd_grad_gpairs_s": r(g["fwd_grad_gpairs_s"]), "bwd_gpairs_s": r(g["bwd_params_gpairs_s"]),
+                       "fwd_grad_frac": r(g["roofline_fwd_grad"]["frac"], 3),
+                       "bwd_frac": r(g["roofline_bwd_params"]["frac"], 3),
+                       "laplacian_gpairs_s": r(g["diagnostics"]["laplacian_gpairs_s"])}
+    t = line.get("trace")
+    if t:
+        out["trace"] = {"gpairs_s": r(t["gpairs_s"]), "ms_per_image": r(t["ms_per_image"]),
+                        "frac": r((t.get("roofline") or {}).get("frac"), 3)}
+    rd = line.get("radius")
+    if rd:
+        out["radius"] = {"grid_queries_s": r(rd["dense_grid"]["queries_per_s"]),
+                         "trace_ms_per_image": r(rd["trace"]["ms_per_image"])}
+        if "large_cloud" in rd:
+            out["radius"]["large_cloud_queries_s"] = r(rd["large_cloud"]["queries_per_s"])
+    for k in ("served", "served_fifo", "served_f16x2"):
+        if k in line:
+            out[k] = {"gpairs_s": r(line[k]["value"]), "p50_ms": r(line[k]["p50_ms"]), "p99_ms": r(line[k]["p99_ms"])}
+    if "cpu_baseline" in line:
+        out["cpu_oracle_gpairs_s"] = r(line["cpu_baseline"]["value"])
     return out
 
 
@@ -810,6 +873,7 @@ def run_ours(args, rank, world, local):
             line["served_f16x2"] = run_served(args, dev, f16_rate, policy=1, clouds_np=clouds_np, precision=1)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(p, n, a)
+    line["summary"] = compact_summary(line)     # last, so that a truncated record still shows it
     print(json.dumps(line), flush=True)
 
 

@@ -104,7 +104,7 @@ typedef enum {
     SDF_FORMULA_BLEND = 0,  /* phi = sum_i A_i w_i g_i / sum_i A_i w_i: Eq. BasicFormulaShifted (the
                                self-normalised blend of the torus SDFs), A_i = 1 unless the cloud
                                was built with weights */
-    SDF_FORMULA_LSE = 1     /* d~ = -(1/lambda) log sum_i A_i exp(-lambda ||x - p_i||): the log-sum-exp
+    SDF_FORMULA_LSE = 1,    /* d~ = -(1/lambda) log sum_i A_i exp(-lambda ||x - p_i||): the log-sum-exp
                                distance, Eq. ConvolutionalDistanceFormula with h = 1 (unsigned; the
                                tori are not used).  lambda is the blend's: lambda_x under
                                SDF_LAMBDA_GLOBAL (d~ = d_min where lambda_x = 0, every point at x),
@@ -113,6 +113,19 @@ typedef enum {
                                + (mean distance - d~) / lambda grad lambda_x; d_saved must be
                                NULL); no parameter gradients, Laplacian, level-set sampling or
                                sphere tracing. */
+    SDF_FORMULA_SSPD = 2,   /* phi_SSPD = sum_i A_i <x - p_i, n_i> e_i / sum_i A_i e_i: the smoothed signed
+                               planar distance, Eq. SmoothedSignedPlanarDistance (Sec. 5's first
+                               baseline), e_i = exp(-lambda (||x - p_i|| - sigma_x)), n_i the unit input
+                               normal; the tori are not used.  lambda is the blend's (lambda_x under
+                               GLOBAL, fixed_lambda >= 0 under FIXED). */
+    SDF_FORMULA_SHC = 3     /* phi_SHC = sign(w) (-(1/lambda) log|w| + sigma_x) with the screened
+                               double-layer sum w = sum_i A_i (lambda d_i + 1) <x - p_i, n_i> e_i /
+                               (2 pi d_i^3): the signed Hopf-Cole distance (screened winding number),
+                               Eq. ScreenedWindingNumber (Sec. 5's second baseline).  lambda_x under
+                               GLOBAL, fixed_lambda > 0 under FIXED.  A point at the query adds
+                               nothing to w; w = 0 gives +inf; a query at every point gives 0.
+                               SSPD and SHC: sdf_query and sdf_query_host only; FP32, GLOBAL or
+                               FIXED lambda, on the FP32 units (SDF_ENGINE_TENSOR is refused). */
 } sdf_formula;
 
 typedef struct {
@@ -468,6 +481,13 @@ PTSDF_API sdf_status sdf_orient(const float* d_points, float* d_normals, float* 
  * ------------------------------------------------------------------------- */
 PTSDF_API sdf_status sdf_knn_mean_distance(sdf_cloud cloud, int32_t k, double* D, void* stream);
 
+/* The paper's constant lambda of the radius-limited evaluation (Sec. 4.2,
+ * "Acceleration and adaptive lambda"): *lambda = 10^3 / D with D =
+ * sdf_knn_mean_distance(cloud, 64) (also returned in *D unless D is NULL).
+ * Synchronous on `stream`.  SDF_EINVAL when D = 0 (one point, or all points
+ * coincide). */
+PTSDF_API sdf_status sdf_paper_lambda(sdf_cloud cloud, double* lambda, double* D, void* stream);
+
 /* ---------------------------------------------------------------------------
  * sdf_mesh_level_set -- the level-`level` surface of a phi grid (offset
  * surfaces and morphological operations, Sec. 6), by marching tetrahedra.
@@ -535,7 +555,7 @@ PTSDF_API sdf_status sdf_probe_timing(int32_t op, double* out);
 PTSDF_API sdf_status sdf_selftest_wait_timeout(int32_t limit_us, int32_t* status_bits, double* waited_ms);
 
 enum { SDF_K_PREPASS = 0, SDF_K_FWD = 1, SDF_K_MERGE = 2, SDF_K_BUILD = 3, SDF_K_FWD_GRAD = 4, SDF_K_BWD = 5,
-       SDF_K_FWD_TC = 6, SDF_K_RADIUS = 7, SDF_K_KNN = 8, SDF_K_COUNT_ = 9 };
+       SDF_K_FWD_TC = 6, SDF_K_RADIUS = 7, SDF_K_KNN = 8, SDF_K_PLANE = 9, SDF_K_COUNT_ = 10 };
 PTSDF_API sdf_status sdf_profile_enable(int32_t on);
 PTSDF_API sdf_status sdf_profile_read(int32_t kernel, int64_t* launches, double* total_ms);
 /* Name of a kernel family (NULL for an id out of range). */

@@ -24,12 +24,13 @@ import numpy as np
 
 from . import _abi, _buffers
 from ._abi import (SDF_DIFFERENCE, SDF_ENGINE_ALU, SDF_ENGINE_AUTO, SDF_ENGINE_TENSOR, SDF_FORMULA_BLEND,
-                   SDF_FORMULA_LSE, SDF_INTERSECT, SDF_LAMBDA_FIXED, SDF_LAMBDA_GLOBAL, SDF_LAMBDA_RADIUS, SDF_UNION,
-                   SdfError, check, lib, make_opts)
+                   SDF_FORMULA_LSE, SDF_FORMULA_SHC, SDF_FORMULA_SSPD, SDF_INTERSECT, SDF_LAMBDA_FIXED,
+                   SDF_LAMBDA_GLOBAL, SDF_LAMBDA_RADIUS, SDF_UNION, SdfError, check, lib, make_opts)
 
 __all__ = ["Cloud", "SdfError", "SDF_LAMBDA_GLOBAL", "SDF_LAMBDA_FIXED", "SDF_LAMBDA_RADIUS", "SDF_UNION",
            "SDF_INTERSECT", "SDF_DIFFERENCE", "SDF_ENGINE_AUTO", "SDF_ENGINE_ALU", "SDF_ENGINE_TENSOR",
-           "SDF_FORMULA_BLEND", "SDF_FORMULA_LSE", "mesh_level_set", "orient", "make_opts", "lib", "sdf", "combine"]
+           "SDF_FORMULA_BLEND", "SDF_FORMULA_LSE", "SDF_FORMULA_SSPD", "SDF_FORMULA_SHC", "mesh_level_set",
+           "orient", "make_opts", "lib", "sdf", "combine"]
 
 
 def _torch():
@@ -139,9 +140,12 @@ class Cloud:
               "sdf_knn_mean_distance")
         return D.value
 
-    def paper_lambda(self, k: int = 64) -> float:
-        """The paper's constant lambda for the radius-limited evaluation, 10^3 / D."""
-        return 1e3 / self.knn_mean_distance(k)
+    def paper_lambda(self, stream=None) -> float:
+        """The paper's constant lambda for the radius-limited evaluation, 10^3 / D
+        with D = knn_mean_distance(64) (sdf_paper_lambda)."""
+        lam = ctypes.c_double()
+        check(lib().sdf_paper_lambda(self._h, ctypes.byref(lam), None, _stream_ptr(stream)), "sdf_paper_lambda")
+        return lam.value
 
     def query_grad(self, x, stream=None, saved=True, **opts):
         """(phi, d phi / d x, saved statistics or None) at the rows of x.  With

@@ -17,13 +17,13 @@ SDF_F32, SDF_F16X2, SDF_BF16X2 = 0, 1, 2
 SDF_LAMBDA_GLOBAL, SDF_LAMBDA_FIXED, SDF_LAMBDA_RADIUS = 0, 1, 2
 SDF_RADIUS_FALLBACK_K = 32
 SDF_ENGINE_AUTO, SDF_ENGINE_ALU, SDF_ENGINE_TENSOR = 0, 1, 2
-SDF_FORMULA_BLEND, SDF_FORMULA_LSE = 0, 1
+SDF_FORMULA_BLEND, SDF_FORMULA_LSE, SDF_FORMULA_SSPD, SDF_FORMULA_SHC = 0, 1, 2, 3
 SDF_DEV_WAIT_TIMEOUT, SDF_DEV_BAD_INPUT = 1, 2
 SDF_K_PREPASS, SDF_K_FWD, SDF_K_MERGE, SDF_K_BUILD, SDF_K_FWD_GRAD, SDF_K_BWD, SDF_K_FWD_TC = 0, 1, 2, 3, 4, 5, 6
-SDF_K_RADIUS, SDF_K_KNN = 7, 8
+SDF_K_RADIUS, SDF_K_KNN, SDF_K_PLANE = 7, 8, 9
 SDF_UNION, SDF_INTERSECT, SDF_DIFFERENCE = 0, 1, 2
 KERNEL_IDS = {"prepass": 0, "fwd": 1, "merge": 2, "build": 3, "fwd_grad": 4, "bwd_params": 5, "fwd_tc": 6,
-              "radius": 7, "knn": 8}
+              "radius": 7, "knn": 8, "plane": 9}
 
 STATUS_NAMES = {0: "SDF_OK", 1: "SDF_EINVAL", 2: "SDF_ENOMEM", 3: "SDF_ECUDA", 4: "SDF_EBUSY",
                 5: "SDF_ETIMEOUT", 6: "SDF_EDEVICE"}
@@ -62,6 +62,8 @@ SIGNATURES = {
                                           ctypes.POINTER(ctypes.c_int64), ctypes.c_void_p]),
     "sdf_knn_mean_distance": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
                                              ctypes.c_void_p]),
+    "sdf_paper_lambda": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
+                                        ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]),
     "sdf_build": (ctypes.c_int, [_P, _P, _P, _I64, _P, ctypes.POINTER(_P)]),
     "sdf_build_weighted": (ctypes.c_int, [_P, _P, _P, _P, _I64, _P, ctypes.POINTER(_P)]),
     "sdf_project_level_set": (ctypes.c_int, [_P, _P, _I64, ctypes.c_float, ctypes.c_int32, ctypes.c_float, _P, _P,

@@ -47,10 +47,18 @@ sdf_status check_opts(const sdf_query_opts& o, const char* fn) {
         return set_error(SDF_EINVAL, std::string(fn) + ": unknown engine");
     if (o.engine == SDF_ENGINE_TENSOR && o.precision != SDF_F32)
         return set_error(SDF_EINVAL, std::string(fn) + ": the tensor-core engine computes in FP32 only");
-    if (o.formula != SDF_FORMULA_BLEND && o.formula != SDF_FORMULA_LSE)
+    if (o.formula != SDF_FORMULA_BLEND && o.formula != SDF_FORMULA_LSE && o.formula != SDF_FORMULA_SSPD &&
+        o.formula != SDF_FORMULA_SHC)
         return set_error(SDF_EINVAL, std::string(fn) + ": unknown formula");
     if (o.formula == SDF_FORMULA_LSE && o.lambda_mode == SDF_LAMBDA_FIXED && !(o.fixed_lambda > 0.f))
         return set_error(SDF_EINVAL, std::string(fn) + ": the log-sum-exp distance needs fixed_lambda > 0");
+    if (o.formula == SDF_FORMULA_SSPD || o.formula == SDF_FORMULA_SHC) {
+        if (o.lambda_mode == SDF_LAMBDA_RADIUS || o.precision != SDF_F32 || o.engine == SDF_ENGINE_TENSOR)
+            return set_error(SDF_EINVAL, std::string(fn) + ": the SSPD and SHC baselines run in FP32 on the FP32 "
+                                                            "units, with GLOBAL or FIXED lambda");
+        if (o.formula == SDF_FORMULA_SHC && o.lambda_mode == SDF_LAMBDA_FIXED && !(o.fixed_lambda > 0.f))
+            return set_error(SDF_EINVAL, std::string(fn) + ": the signed Hopf-Cole distance needs fixed_lambda > 0");
+    }
     return SDF_OK;
 }
 
@@ -58,7 +66,8 @@ sdf_status check_opts(const sdf_query_opts& o, const char* fn) {
 sdf_status blend_only(const sdf_query_opts& o, const char* fn) {
     return o.formula == SDF_FORMULA_BLEND
                ? SDF_OK
-               : set_error(SDF_EINVAL, std::string(fn) + ": the log-sum-exp distance is for sdf_query only");
+               : set_error(SDF_EINVAL, std::string(fn) + ": the log-sum-exp distance and the SSPD and SHC "
+                                                         "baselines are for sdf_query only");
 }
 
 // Booleans of two phi arrays (Sec. 6): union min, intersection max, difference max(a, -b)
@@ -142,6 +151,8 @@ extern "C" sdf_status sdf_query_grad(sdf_cloud cloud, const float* d_x, int64_t 
     const sdf_query_opts o = resolve_opts(opts);
     sdf_status s = check_opts(o, "sdf_query_grad");
     if (s != SDF_OK) return s;
+    if (o.formula == SDF_FORMULA_SSPD || o.formula == SDF_FORMULA_SHC)
+        return set_error(SDF_EINVAL, "sdf_query_grad: no gradient of the SSPD and SHC baselines");
     if (o.formula == SDF_FORMULA_LSE && d_saved)
         return set_error(SDF_EINVAL, "sdf_query_grad: no saved statistics for the log-sum-exp distance "
                                      "(they serve the blend's parameter gradient)");

@@ -345,6 +345,7 @@ void free_cloud(Cloud* c) {
     cudaFree(c->btile_exact);
     cudaFree(c->mrec);
     cudaFree(c->mperm);
+    cudaFree(c->prec);
     delete c;
 }
 
@@ -454,7 +455,8 @@ extern "C" sdf_status sdf_build_weighted(const float* d_points, const float* d_n
                                             c->rec, c->pre, c->perm);
     PTSDF_TRY(cudaGetLastError(), "sdf_build: k_partition launch");
     {
-        const sdf_status bs = build_btiles(*c, st);
+        sdf_status bs = build_btiles(*c, st);
+        if (bs == SDF_OK) bs = build_plane_records(*c, d_weights, st);   // the SSPD / SHC baselines
         if (bs != SDF_OK) {
             const std::string msg = sdf_last_error();
             fail(cudaSuccess, "");

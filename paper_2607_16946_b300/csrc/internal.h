@@ -62,6 +62,7 @@ constexpr int kTileRecs = PTSDF_TILE_RECS;   // records per main-loop tile (32 x
 constexpr int kRecFloats = 16;
 constexpr int kPreTile = 256;        // points per prepass tile (4 KB)
 constexpr int kSphereTile = 64;      // points per bounding sphere of the pruned prepass
+constexpr int kPlaneTile = 64;       // points per tile of the baselines' plane records (4 KB)
 
 struct Cloud {
     int device = 0;
@@ -85,6 +86,9 @@ struct Cloud {
     uint8_t* btiles = nullptr;       // (tiles_direct + tiles_kappa) x 14 KB split-f16 operands of the
                                      // tensor-core loop, both segments
     int32_t* btile_exact = nullptr;  // per tile: 1 when a coefficient leaves the f16 split's range
+    float4* prec = nullptr;          // plane records of the baselines: per point (px,px,py,py) (pz,pz,A,A)
+                                     // (nx,nx,ny,ny) (nz,nz,0,0), input order, plane_tiles x kPlaneTile points
+    int64_t plane_tiles = 0;
     float4* mrec = nullptr;          // n x 4 float4 records in the prepass (Morton) order, r3.w = 1 for kappa
     int32_t* mperm = nullptr;        // input index of each Morton position
     float tc_scale = 1.f;            // their coordinate scale (a power of two >= the AABB diagonal)
@@ -177,6 +181,10 @@ sdf_status launch_radius_query(const Cloud& c, const float* d_x, int64_t q, floa
 
 sdf_status launch_query(const Cloud& c, const float* d_x, int64_t q, float* d_phi,
                         const sdf_query_opts& o, cudaStream_t st);
+// the two convolutional baselines, phi_SSPD and phi_SHC (baselines.cu)
+sdf_status launch_plane_query(const Cloud& c, const float* d_x, int64_t q, float* d_phi, const sdf_query_opts& o,
+                              cudaStream_t st);
+sdf_status build_plane_records(Cloud& c, const float* d_weights, cudaStream_t st);
 // trace.cu
 sdf_status launch_trace(const Cloud& c, const float* d_org, const float* d_dir, int64_t nrays, int32_t max_steps,
                         float eps, float t_max, float* d_t_hit, int32_t* d_steps, float* d_normals,

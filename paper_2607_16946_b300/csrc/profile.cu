@@ -17,7 +17,7 @@ struct Rec {
 std::mutex g_mu;
 bool g_on = false;
 std::vector<Rec> g_recs;
-const char* kNames[SDF_K_COUNT_] = {"prepass", "fwd", "merge", "build", "fwd_grad", "bwd_params", "fwd_tc", "radius", "knn"};
+const char* kNames[SDF_K_COUNT_] = {"prepass", "fwd", "merge", "build", "fwd_grad", "bwd_params", "fwd_tc", "radius", "knn", "plane"};
 
 void clear_locked() {
     for (auto& r : g_recs) {

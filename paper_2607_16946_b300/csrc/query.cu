@@ -197,20 +197,6 @@ FwdKernel fwd_kernel(int precision, bool weighted) {
                                                                                        : k_fwd<SDF_F32, false>;
 }
 
-__global__ void k_merge(QueryArgs a) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= a.q) return;
-    float W = 0.f, S = 0.f;
-    for (int c = 0; c < a.split; ++c) {
-        const float2 v = a.part[(size_t)c * a.q + i];
-        W += v.x;
-        S += v.y;
-    }
-    float L = 0.f, A0 = 0.f;
-    if (a.formula == SDF_FORMULA_LSE) query_screening(a.d2, a.pre_split, a.q, i, a.mode, a.C, a.lam, L, A0);
-    a.phi[i] = finish_sums(W, S, a.formula, L, A0, a.offset);
-}
-
 }  // namespace
 
 // Point chunks of `tiles` tiles for `qblocks` query blocks: enough CTAs to
@@ -288,6 +274,7 @@ int query_partials(const Cloud& c, int64_t q, const sdf_query_opts& o) {
 sdf_status launch_query(const Cloud& c, const float* d_x, int64_t q, float* d_phi, const sdf_query_opts& o,
                         cudaStream_t st) {
     if (o.lambda_mode == SDF_LAMBDA_RADIUS) return launch_radius_query(c, d_x, q, d_phi, o, st);
+    if (o.formula == SDF_FORMULA_SSPD || o.formula == SDF_FORMULA_SHC) return launch_plane_query(c, d_x, q, d_phi, o, st);
     const Plan p = make_plan(c, q, o.split_n);
     // Tensor-core engine: see TcPlan
     const bool tc = use_tensor_engine(c, o);
@@ -467,6 +454,8 @@ extern "C" sdf_status sdf_query_noalloc(sdf_cloud cloud, const float* d_x, int64
     if (o.precision != SDF_F32) return set_error(SDF_EINVAL, "sdf_query_noalloc: FP32 only");
     if (o.engine == SDF_ENGINE_TENSOR)
         return set_error(SDF_EINVAL, "sdf_query_noalloc: only the FP32-unit engine is available here");
+    if (o.formula == SDF_FORMULA_SSPD || o.formula == SDF_FORMULA_SHC)
+        return set_error(SDF_EINVAL, "sdf_query_noalloc: the blend and the log-sum-exp distance only");
     if (!cloud) return set_error(SDF_EINVAL, "sdf_query_noalloc: cloud is NULL");
     if (q == 0) return SDF_OK;
     if (!d_x || !d_phi) return set_error(SDF_EINVAL, "sdf_query_noalloc: NULL buffer");

@@ -62,15 +62,42 @@ __device__ __forceinline__ void query_screening(const float2* __restrict__ d2p, 
     A0 = L * dmin;
 }
 
+constexpr float kLog2TwoPi = 2.6514961294723187f;   // log2(2 pi)
+
 // What a query's sums W = sum A_i w_i, S = sum A_i w_i g_i finish into, less
-// the offset: the blend S / W (Eq. BasicFormulaShifted), or the log-sum-exp
+// the offset: the blend S / W (Eq. BasicFormulaShifted; with g_i = <x - p_i,
+// n_i> it is phi_SSPD, Eq. SmoothedSignedPlanarDistance), or the log-sum-exp
 // distance -(1/lambda) log sum_i A_i exp(-lambda d_i) (Eq.
 // ConvolutionalDistanceFormula, h = 1) = d_min - ln(W) / lambda =
 // (A0 - log2 W) / L; where L = 0 (GLOBAL with every point at the query) it
-// is d_min = 0.
+// is d_min = 0.  SDF_FORMULA_SHC: S = 2 pi w e^(-lambda d_min) for the
+// screened double-layer sum w of Eq. ScreenedWindingNumber, and
+// phi_SHC = sign(w) (-(1/lambda) ln|w|) = sign(S) (A0 - log2|S| + log2 2pi) / L
+// (the paper's + sigma_x cancels its shift inside w); L = 0 gives 0 and S = 0
+// gives +inf (the limit as |w| -> 0).
 __device__ __forceinline__ float finish_sums(float W, float S, int formula, float L, float A0, float offset) {
     if (formula == SDF_FORMULA_LSE) return (L > 0.f ? (A0 - log2f(W)) / L : 0.f) - offset;
+    if (formula == SDF_FORMULA_SHC) {
+        if (!(L > 0.f)) return -offset;
+        return copysignf((A0 - log2f(fabsf(S)) + kLog2TwoPi) / L, S) - offset;
+    }
     return __fdiv_rn(S, W) - offset;
+}
+
+// Sums the (W, S) partials of every chunk in chunk order and finishes them.
+__global__ void k_merge(QueryArgs a) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.q) return;
+    float W = 0.f, S = 0.f;
+    for (int c = 0; c < a.split; ++c) {
+        const float2 v = a.part[(size_t)c * a.q + i];
+        W += v.x;
+        S += v.y;
+    }
+    float L = 0.f, A0 = 0.f;
+    if (a.formula == SDF_FORMULA_LSE || a.formula == SDF_FORMULA_SHC)
+        query_screening(a.d2, a.pre_split, a.q, i, a.mode, a.C, a.lam, L, A0);
+    a.phi[i] = finish_sums(W, S, a.formula, L, A0, a.offset);
 }
 
 // --------------------------------------------------------------------------

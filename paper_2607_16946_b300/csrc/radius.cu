@@ -391,3 +391,17 @@ extern "C" sdf_status sdf_knn_mean_distance(sdf_cloud cloud, int32_t k, double* 
     *D = s / (double)c.n;
     return SDF_OK;
 }
+
+// Sec. 4.2, "Acceleration and adaptive lambda": the paper's constant lambda =
+// 10^3 / D with D the mean distance between a point and its 64 nearest
+// neighbours, averaged over the cloud.
+extern "C" sdf_status sdf_paper_lambda(sdf_cloud cloud, double* lambda, double* D, void* stream) {
+    if (!cloud || !lambda) return set_error(SDF_EINVAL, "sdf_paper_lambda: NULL argument");
+    double d = 0.0;
+    const sdf_status s = sdf_knn_mean_distance(cloud, 64, &d, stream);
+    if (s != SDF_OK) return s;
+    if (D) *D = d;
+    if (!(d > 0.0)) return set_error(SDF_EINVAL, "sdf_paper_lambda: D = 0 (a single point, or coincident points)");
+    *lambda = 1e3 / d;
+    return SDF_OK;
+}

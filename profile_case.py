@@ -31,10 +31,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=1)
     ap.add_argument("--points", type=int, default=None, help="default 100,000 (torus) / 262,144 (superquadric)")
     ap.add_argument("--cloud", choices=["torus", "superquadric"], default="torus")
-    ap.add_argument("--mode", choices=["query", "grad", "backward", "radius", "probe"], default="query",
+    ap.add_argument("--mode", choices=["query", "grad", "backward", "radius", "probe", "sspd", "shc"],
+                    default="query",
                     help="query: sdf_query; grad: sdf_query_grad; backward: sdf_query_grad then "
                          "sdf_backward_params (each call); radius: sdf_query with SDF_LAMBDA_RADIUS and "
-                         "lambda = 10^3 / D")
+                         "lambda = 10^3 / D; sspd / shc: sdf_query with the SSPD / SHC baseline")
     ap.add_argument("--precision", type=int, default=0, help="sdf_precision of the query")
     ap.add_argument("--engine", type=int, default=0, help="sdf_engine of the query (0 auto, 1 ALU, 2 tensor)")
     args = ap.parse_args()
@@ -75,7 +76,7 @@ def main():
     x = x[::stride][: args.queries].contiguous()
     phi = torch.empty(x.shape[0], device="cuda")
     G = torch.ones(x.shape[0], device="cuda")
-    lam = 1e3 / cloud.knn_mean_distance(64) if args.mode == "radius" else 0.0
+    lam = cloud.paper_lambda() if args.mode == "radius" else 0.0
 
     def call():
         nonlocal phi
@@ -83,6 +84,8 @@ def main():
             cloud.query(x, out=phi, precision=args.precision, engine=args.engine)
         elif args.mode == "radius":
             cloud.query(x, out=phi, lambda_mode=ptsdf.SDF_LAMBDA_RADIUS, fixed_lambda=lam)
+        elif args.mode in ("sspd", "shc"):
+            cloud.query(x, out=phi, formula=ptsdf.SDF_FORMULA_SSPD if args.mode == "sspd" else ptsdf.SDF_FORMULA_SHC)
         else:
             phi, _, saved = cloud.query_grad(x)
             if args.mode == "backward":

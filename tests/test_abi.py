@@ -121,6 +121,7 @@ def _refusals(abi):
         (lambda: L.sdf_query_noalloc(None, None, 4, None, ctypes.byref(abi.make_opts(engine=abi.SDF_ENGINE_TENSOR)),
                                      None), b"only the FP32-unit engine"),
         (lambda: L.sdf_knn_mean_distance(None, 64, ctypes.byref(d), None), b"sdf_knn_mean_distance"),
+        (lambda: L.sdf_paper_lambda(None, ctypes.byref(d), None, None), b"sdf_paper_lambda: NULL"),
         (lambda: L.sdf_cloud_info(None, ctypes.byref(i64), ctypes.byref(f), None, None), b"sdf_cloud_info: cloud"),
         (lambda: L.sdf_cloud_forms(None, ctypes.byref(i64), None), b"sdf_cloud_forms: cloud"),
         (lambda: L.sdf_build_weighted(fake, fake, fake, fake, 0, None, ctypes.byref(ctypes.c_void_p())),

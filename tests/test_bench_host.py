@@ -10,8 +10,9 @@ import pytest
 
 import bench
 
-RATES = {"sqrt": 17.9, "rsqrt": 17.9, "ex2": 40.5, "fma": 128.5, "rcp": 17.8,
-         "pair_direct": 4.71, "pair_flat": 4.71, "pair_curved": 2.96}
+# the rates measured on a B300 (results, or pairs, per SM per clock)
+RATES = {"sqrt": 16.0, "rsqrt": 16.0, "ex2": 32.0, "fma": 124.1, "rcp": 16.0,
+         "pair_direct": 4.571, "pair_flat": 4.571, "pair_curved": 2.909}
 
 
 def test_single_form_ceiling_is_its_measured_mix():
@@ -29,23 +30,25 @@ def test_mixed_forms_share_the_clocks():
     counts = {"direct": 97904, "curved": 2096}
     _, mufu, _ = bench.tc_pair_ceiling(RATES, counts)
     assert RATES["pair_curved"] < mufu < RATES["pair_direct"]
-    assert mufu == pytest.approx(100000 / (97904 / 4.71 + 2096 / 2.96))
+    assert mufu == pytest.approx(100000 / (97904 / 4.571 + 2096 / 2.909))
     assert bench.tc_pair_ceiling(RATES, {k: 2 * v for k, v in counts.items()})[1] == pytest.approx(mufu)
     assert bench.tc_pair_ceiling(RATES, {"direct": 97904, "curved": 20960})[1] < mufu
 
 
 def test_unmeasured_mix_falls_back_to_single_operations():
     single = {k: v for k, v in RATES.items() if not k.startswith("pair_")}
-    assert bench.mix_cost(single, "direct") == pytest.approx(3 / 17.9 + 1 / 40.5)
-    assert bench.mix_cost(single, "curved") == pytest.approx(3 / 17.9 + 2 / 17.8 + 1 / 40.5)
-    # the measured mix is slower than the sum of its parts on this part
-    assert bench.mix_cost(RATES, "direct") > bench.mix_cost(single, "direct")
+    assert bench.mix_cost(single, "direct") == pytest.approx(3 / 16.0 + 1 / 32.0)
+    assert bench.mix_cost(single, "curved") == pytest.approx(3 / 16.0 + 2 / 16.0 + 1 / 32.0)
+    # with the measured rates the mixes are additive: the single-operation sums
+    # equal the measured mixes
+    assert 1 / bench.mix_cost(single, "direct") == pytest.approx(RATES["pair_direct"], rel=1e-3)
+    assert 1 / bench.mix_cost(single, "curved") == pytest.approx(RATES["pair_curved"], rel=1e-3)
 
 
 def test_fp32_unit_loop_ceiling():
     best, mufu, issue = bench.pair_ceiling(RATES, bench.INSTR_PER_PAIR)
-    assert mufu == pytest.approx(4.71)
-    assert issue == pytest.approx(128.5 / 29)
+    assert mufu == pytest.approx(RATES["pair_direct"])
+    assert issue == pytest.approx(RATES["fma"] / 29)
     assert best == min(mufu, issue)
 
 
@@ -87,3 +90,16 @@ def test_both_arms_describe_the_same_workload():
     c1, c4 = bench.workload_config(256 ** 3, 1), bench.workload_config(256 ** 3, 4)
     assert c1["Q"] == 256 ** 3 and c1["N"] == bench.N_POINTS and c1["workload"] == bench.WORKLOAD
     assert c1["parallelism"] == "single" and c4["parallelism"] == "replicas4"
+
+
+def test_compact_summary_comes_from_the_legs():
+    line = {"value": 1051.3, "e2e": {"value": 1046.5}, "roofline": {"frac": 0.8071},
+            "mixed": {"sspd": {"value": 2500.0, "err_max_rel_diag": 1.2e-7,
+                               "roofline": {"frac": 0.75}}, "note": "text"},
+            "served": {"value": 700.0, "p50_ms": 500.0, "p99_ms": 2500.0},
+            "cpu_baseline": {"value": 0.65}}
+    s = bench.compact_summary(line)
+    assert s["dense_grid"] == {"gpairs_s": 1051.0, "frac": 0.807, "e2e_gpairs_s": 1046.0}
+    assert s["sspd"] == {"gpairs_s": 2500.0, "err_max": 1.2e-7, "frac": 0.75}
+    assert s["served"]["p99_ms"] == 2500.0 and s["cpu_oracle_gpairs_s"] == 0.65
+    assert "note" not in s

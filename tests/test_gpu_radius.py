@@ -97,6 +97,7 @@ def test_ring_torus_paper_lambda(ptsdf, oracle_mod):
     orc = oracle_mod.Cloud(p, n, a)
     lam = 1e3 / oracle_mod.knn_mean_distance(p, 64)
     cl = ptsdf.Cloud(p, n, a)
+    assert abs(cl.paper_lambda() - lam) <= 1e-5 * lam      # sdf_paper_lambda
     rng = np.random.Generator(np.random.PCG64(33))
     near = p[rng.integers(0, len(p), 600)] + rng.normal(scale=0.004, size=(600, 3))
     x = f32(np.concatenate([synth.uniform_queries(1400, 34, -1.6, 1.6), near]))
@@ -125,7 +126,8 @@ def test_sphere_exact(ptsdf):
     p, n, a = f32(*synth.sphere_fibonacci(4096, 1001))
     cl = ptsdf.Cloud(p, n, a)
     x = f32(synth.uniform_queries(4000, 36))
-    lam = 1e3 / cl.knn_mean_distance(64)
+    lam = cl.paper_lambda()
+    assert lam == 1e3 / cl.knn_mean_distance(64)
     got = run(ptsdf, cl, x, lam)
     assert np.abs(got - (np.linalg.norm(x.astype(np.float64), axis=1) - 1)).max() <= 2e-6
 
