@@ -241,6 +241,7 @@ def cpu_baseline(points, normals, params, target_s: float = 12.0):
 
 
 SERVE_SEED = 1005
+SERVE_SPLIT_GPAIRS = 100        # requests above 1e11 (query, point) pairs run as interleaved query chunks
 
 
 def make_serving_clouds(n_clouds: int, seed: int):
@@ -293,7 +294,8 @@ def run_served(args, dev, pair_rate_gps: float, policy: int = 0, clouds_np=None,
     mean_pairs = float(np.mean([r["pairs"] for r in reqs]))
     rate = args.serve_load * pair_rate_gps * 1e9 / mean_pairs          # requests per second
     arrivals = np.cumsum(rng.exponential(1.0 / rate, size=len(reqs)))
-    srv = S.Server(mem_budget_bytes=16 << 30, max_inflight=8, n_streams=4, policy=policy, starve_ms=2000)
+    srv = S.Server(mem_budget_bytes=16 << 30, max_inflight=8, n_streams=4, policy=policy, starve_ms=2000,
+                   split_gpairs=SERVE_SPLIT_GPAIRS)
     ids = [srv.register(c) for c in clouds]
     outs = [torch.empty(r["q"], device=dev) for r in reqs]
     torch.cuda.synchronize(dev)
@@ -335,7 +337,9 @@ def run_served(args, dev, pair_rate_gps: float, policy: int = 0, clouds_np=None,
             "offered_load": args.serve_load, "arrival_rate_per_s": rate, "mean_pairs_per_request": mean_pairs,
             "clouds": len(clouds), "points_total": int(sum(ns)), "outputs_finite": finite,
             "server": {"max_inflight": 8, "n_streams": 4, "mem_budget_bytes": 16 << 30,
-                       "policy": "smallest_first (starve 2 s)" if policy else "fifo"},
+                       "policy": "smallest_first (starve 2 s)" if policy else "fifo",
+                       "split_pairs": SERVE_SPLIT_GPAIRS * 1e9,
+                       "requests_split": sum(1 for st in stats if st["chunks"] > 1)},
             "workload": f"{len(clouds)} resident clouds N~logU[2048,500000] (sphere/torus/superquadric/ellipsoid), "
                         f"{len(reqs)} requests Q~logU[1024,4194304], Poisson arrivals at "
                         f"{args.serve_load} x measured capacity; "
@@ -518,6 +522,44 @@ def run_radius_leg(dev, cloud, x, phi, steps: int = 3):
     out["trace"] = {"ms_per_image": wall * 1e3, "lambda": lam_t, "hits": int((t >= 0).sum().item()),
                     "evaluations": int(st_.sum().item()),
                     "queries_per_s": int(st_.sum().item()) / wall, "kernels": _profile_window(L, _abi)}
+    # the paper's scale for this path: a cloud of 2^21 points (the tracing
+    # surface, sampled 8x denser), queried on a 128^3 grid and traced
+    pL, nL, aL = synth.superquadric(1 << 21, 2021)
+    cL = ptsdf.Cloud(pL, nL, aL)
+    del pL, nL, aL
+    t0 = time.perf_counter()
+    lam_L = cL.paper_lambda()
+    t_knn_L = time.perf_counter() - t0
+    kL = dict(lambda_mode=ptsdf.SDF_LAMBDA_RADIUS, fixed_lambda=lam_L)
+    g = torch.linspace(-1.2, 1.2, 128, device=dev, dtype=torch.float64)
+    zz, yy, xx = torch.meshgrid(g, g, g, indexing="ij")
+    xg = torch.stack([xx.reshape(-1), yy.reshape(-1), zz.reshape(-1)], 1).to(torch.float32).contiguous()
+    phiL = torch.empty(xg.shape[0], device=dev)
+    cL.query(xg, out=phiL, **kL)
+    torch.cuda.synchronize(dev)
+    L.sdf_profile_enable(1)
+    e0.record()
+    for _ in range(steps):
+        cL.query(xg, out=phiL, **kL)
+    e1.record()
+    torch.cuda.synchronize(dev)
+    L.sdf_profile_enable(0)
+    sL = e0.elapsed_time(e1) / 1e3 / steps
+    out["large_cloud"] = {"points": 1 << 21, "queries_per_s": xg.shape[0] / sL, "ms_per_step": sL * 1e3,
+                          "queries": xg.shape[0], "lambda": lam_L, "R_eval": 128.0 / lam_L,
+                          "paper_lambda_ms": t_knn_L * 1e3, "kernels": _profile_window(L, _abi),
+                          "outputs_finite": bool(torch.isfinite(phiL).all())}
+    t, st_, nrm = cL.trace(org, dirs, **kL)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    t, st_, nrm = cL.trace(org, dirs, **kL)
+    torch.cuda.synchronize(dev)
+    out["large_cloud"]["trace_ms_per_image"] = (time.perf_counter() - t0) * 1e3
+    out["large_cloud"]["trace_hits"] = int((t >= 0).sum().item())
+    out["large_cloud"]["workload"] = ("superquadric N=2^21 (e1=0.5, e2=2, axes 1/0.7/0.5, noise 0.003), "
+                                      "lambda = 10^3/D; 128^3 grid over [-1.2,1.2]^3, and the 512x512 "
+                                      "tracing camera (normals from the all-pairs gradient)")
+    cL.close()
     out["note"] = ("lambda = 10^3/D, R_eval = 2C/lambda, C = 64, 32-nearest fallback; normals at hits from "
                    "the all-pairs gradient with the same lambda")
     return out

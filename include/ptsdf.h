@@ -32,7 +32,7 @@
  *    The calls that manage resources, report status or measure the device
  *    (sdf_destroy, sdf_cloud_info, sdf_cloud_forms, sdf_device_status, the
  *    sdf_serve_* bookkeeping, sdf_probe_rates, sdf_probe_timing,
- *    sdf_selftest_wait_timeout,
+ *    sdf_selftest_wait_timeout, sdf_selftest_soft_sqrt,
  *    sdf_profile_*, sdf_kernel_name, sdf_last_error, sdf_version) have no
  *    counterpart in the paper.
  */
@@ -355,7 +355,12 @@ typedef struct {
     int32_t device;             /* CUDA device of the clouds */
     int32_t policy;             /* sdf_serve_policy */
     int32_t starve_ms;          /* SMALLEST_FIRST: age after which a request is admitted first */
-    int32_t reserved;
+    int32_t split_gpairs;       /* requests of more (query, point) pairs than split_gpairs x 1e9 run as
+                                   query chunks that are admitted one after another, each queued
+                                   behind the requests waiting when the previous one started (0:
+                                   never split).  A chunk keeps at least 2 x 4 x SMs x 512 queries,
+                                   so every query's result is exactly that of the unsplit request;
+                                   GRAD requests are not split. */
 } sdf_serve_config;
 
 typedef enum {
@@ -382,12 +387,12 @@ typedef struct {
 
 typedef struct {
     int32_t status;          /* sdf_status of the request */
-    int32_t reserved;
+    int32_t chunks;          /* query chunks it ran as (1 unless split, see split_gpairs) */
     int64_t arrive_ns;       /* host steady-clock times: submit, */
-    int64_t admit_ns;        /*   admission, */
-    int64_t start_ns;        /*   launch, */
+    int64_t admit_ns;        /*   admission (of the first chunk), */
+    int64_t start_ns;        /*   launch (of the first chunk), */
     int64_t done_ns;         /*   completion of the request's last operation */
-    double device_ms;        /* CUDA-event time of the request's work on its stream */
+    double device_ms;        /* CUDA-event time of the request's work on its stream (summed over chunks) */
 } sdf_request_stats;
 
 /* Creates a server (and its scheduler thread and streams). */
@@ -553,6 +558,13 @@ PTSDF_API sdf_status sdf_probe_timing(int32_t op, double* out);
  * receives that word (SDF_DEV_WAIT_TIMEOUT expected) and *waited_ms the time
  * the wait took.  Nothing faults or hangs, and the context stays usable. */
 PTSDF_API sdf_status sdf_selftest_wait_timeout(int32_t limit_us, int32_t* status_bits, double* waited_ms);
+
+/* Self-test of the square root the tensor-core epilogue computes on the FMA
+ * pipe (no counterpart in the paper): over 2^25 positive normal floats from
+ * 1e-30 up, the largest relative difference from CUDA's correctly rounded
+ * sqrtf (about 4.6e-6 expected: two Newton steps from a bit-level
+ * estimate). */
+PTSDF_API sdf_status sdf_selftest_soft_sqrt(double* max_rel_err);
 
 enum { SDF_K_PREPASS = 0, SDF_K_FWD = 1, SDF_K_MERGE = 2, SDF_K_BUILD = 3, SDF_K_FWD_GRAD = 4, SDF_K_BWD = 5,
        SDF_K_FWD_TC = 6, SDF_K_RADIUS = 7, SDF_K_KNN = 8, SDF_K_PLANE = 9, SDF_K_COUNT_ = 10 };

@@ -32,6 +32,7 @@ over queries); this module is a ctypes wrapper with numpy arrays.  Functions:
                                         (Sec. 4.2, "Acceleration and adaptive lambda")
   Cloud.trace(org, dir, ...)            sphere tracing (Sec. 6)
   knn_mean_distance(points, k)          D of the lambda heuristic (Sec. 4.2)
+  knn_mean_distance_sample(points, idx) its mean over sampled points only
   fit_record(p, n, a)                   the fitted torus of one point
   torus_sdf(c, u, R, r, x)              literal Eq. SingleTorusSDF for an explicit torus
   frame(n)                              the (s, t) frame convention
@@ -103,6 +104,8 @@ def _load():
         _lib.or_laplacian.argtypes = [P, i32, f64, f64, P, i64, P, P, P, i32]
         _lib.or_knn_mean_distance.argtypes = [P, i64, i32, i32]
         _lib.or_knn_mean_distance.restype = f64
+        _lib.or_knn_mean_distance_sample.argtypes = [P, i64, P, i64, i32, i32]
+        _lib.or_knn_mean_distance_sample.restype = f64
     return _lib
 
 
@@ -276,6 +279,17 @@ def knn_mean_distance(points, k: int = 64, threads: int | None = None) -> float:
     (Sec. 4.2, "Acceleration and adaptive lambda").  Brute force, FP64."""
     p = _f64(points, 3)
     return float(_load().or_knn_mean_distance(_ptr(p), p.shape[0], int(k), threads or default_threads()))
+
+
+def knn_mean_distance_sample(points, idx, k: int = 64, threads: int | None = None) -> float:
+    """The same mean over the points idx only (each against all points): an
+    estimate of D for clouds too large for the all-points brute force."""
+    p = _f64(points, 3)
+    ix = np.ascontiguousarray(np.asarray(idx, dtype=np.int64).ravel())
+    if ix.size == 0 or ix.min() < 0 or ix.max() >= p.shape[0]:
+        raise ValueError("idx: indices of points")
+    return float(_load().or_knn_mean_distance_sample(_ptr(p), p.shape[0], _ptr(ix), ix.size, int(k),
+                                                     threads or default_threads()))
 
 
 def fit_record(p, n, a) -> dict:

@@ -973,7 +973,11 @@ void or_phi_radius(const or_cloud* C, double lambda, double reval, int kfb, cons
 /* D of the lambda heuristic: for every point the mean of the distances to
  * its k nearest other points (all n - 1 of them when n - 1 < k), averaged
  * over the points.  Brute force.  n = 1 gives 0. */
-typedef struct { const double* pts; int64_t n; int k; int64_t i0, i1; double sum; } knn_job;
+typedef struct {
+    const double* pts; int64_t n; int k;
+    const int64_t* idx;      /* the points whose distances are averaged (NULL: every point) */
+    int64_t i0, i1; double sum;
+} knn_job;
 
 static void* knn_worker(void* arg) {
     knn_job* J = (knn_job*)arg;
@@ -981,7 +985,8 @@ static void* knn_worker(void* arg) {
     double* bd = (double*)malloc(sizeof(double) * (size_t)(k > 0 ? k : 1));
     int64_t* bi = (int64_t*)malloc(sizeof(int64_t) * (size_t)(k > 0 ? k : 1));
     J->sum = 0.0;
-    for (int64_t i = J->i0; i < J->i1 && k > 0; ++i) {
+    for (int64_t e = J->i0; e < J->i1 && k > 0; ++e) {
+        const int64_t i = J->idx ? J->idx[e] : e;
         int cnt = 0;
         const double* a = J->pts + 3 * i;
         for (int64_t j = 0; j < J->n; ++j) {
@@ -999,15 +1004,18 @@ static void* knn_worker(void* arg) {
     return NULL;
 }
 
-double or_knn_mean_distance(const double* pts, int64_t n, int k, int threads) {
-    if (n < 2 || k < 1) return 0.0;
-    threads = clamp_threads(threads, n);
+/* The mean over m of the points (indices idx; all n when idx is NULL, m = n)
+ * of the mean distance to their k nearest other points: D of the lambda
+ * heuristic, or an estimate of it from a sample of the points. */
+static double knn_mean(const double* pts, int64_t n, const int64_t* idx, int64_t m, int k, int threads) {
+    if (n < 2 || k < 1 || m < 1) return 0.0;
+    threads = clamp_threads(threads, m);
     pthread_t th[256];
     knn_job jobs[256];
-    int64_t per = (n + threads - 1) / threads;
+    int64_t per = (m + threads - 1) / threads;
     for (int t = 0; t < threads; ++t) {
-        int64_t i0 = t * per, i1 = i0 + per < n ? i0 + per : n;
-        jobs[t] = (knn_job){pts, n, k, i0, i1 > i0 ? i1 : i0, 0.0};
+        int64_t i0 = t * per, i1 = i0 + per < m ? i0 + per : m;
+        jobs[t] = (knn_job){pts, n, k, idx, i0, i1 > i0 ? i1 : i0, 0.0};
         pthread_create(&th[t], NULL, knn_worker, &jobs[t]);
     }
     double total = 0.0;
@@ -1015,7 +1023,15 @@ double or_knn_mean_distance(const double* pts, int64_t n, int k, int threads) {
         pthread_join(th[t], NULL);
         total += jobs[t].sum;
     }
-    return total / (double)n;
+    return total / (double)m;
+}
+
+double or_knn_mean_distance(const double* pts, int64_t n, int k, int threads) {
+    return knn_mean(pts, n, NULL, n, k, threads);
+}
+
+double or_knn_mean_distance_sample(const double* pts, int64_t n, const int64_t* idx, int64_t m, int k, int threads) {
+    return knn_mean(pts, n, idx, m, k, threads);
 }
 
 /* ------------------------------------------------------------------------ */

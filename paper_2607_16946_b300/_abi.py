@@ -47,6 +47,7 @@ SIGNATURES = {
     "sdf_opts_default": (ctypes.c_int, [ctypes.POINTER(sdf_query_opts)]),
     "sdf_probe_rates": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double)]),
     "sdf_probe_timing": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(ctypes.c_double)]),
+    "sdf_selftest_soft_sqrt": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double)]),
     "sdf_selftest_wait_timeout": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
                                                  ctypes.POINTER(ctypes.c_double)]),
     "sdf_orient": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32,

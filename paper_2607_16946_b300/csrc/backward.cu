@@ -34,22 +34,125 @@ namespace {
 constexpr int kThreads = (kConsumerWarps + 1) * 32;
 constexpr int kPointsPerCta = kConsumerWarps * 32;     // one record per consumer thread
 constexpr int kQTile = 64;                             // queries per streamed tile
-constexpr uint32_t kQTileBytes = kQTile * 8 * sizeof(float);
+constexpr uint32_t kQTileBytes = kQTile * 6 * sizeof(float);   // 32 pairs x 3 float4
 constexpr int kNAcc = 11;
 constexpr float kTiny = 1e-30f;
 
-// qrec[j] = {x, y, z, L, A0, G / W, 0, 0}; padding rows have coefficient 0.
+// The queries' streamed records, two queries side by side: for queries 2k and
+// 2k + 1, (x, x', y, y'), (z, z', L, L'), (A0, A0', G / W, G' / W'), so that
+// every 128-bit shared load gives two .f32x2 operands.  Padding queries have
+// coefficient 0.
 __global__ void k_bwd_prep(const float* __restrict__ saved, const float* __restrict__ G, int64_t q,
-                           int64_t q_padded, float4* __restrict__ qrec) {
+                           int64_t q_padded, float* __restrict__ qrec) {
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= q_padded) return;
+    float v[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};   // x, y, z, L, A0, G / W
     if (j < q) {
         const float* s = saved + 8 * j;
-        qrec[2 * j] = make_float4(s[0], s[1], s[2], s[3]);
-        qrec[2 * j + 1] = make_float4(s[4], G[j] / s[5], 0.f, 0.f);
-    } else {
-        qrec[2 * j] = make_float4(0.f, 0.f, 0.f, 0.f);
-        qrec[2 * j + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
+        v[0] = s[0];
+        v[1] = s[1];
+        v[2] = s[2];
+        v[3] = s[3];
+        v[4] = s[4];
+        v[5] = G[j] / s[5];
+    }
+    float* dst = qrec + (j >> 1) * 12 + (j & 1);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) dst[2 * k] = v[k];
+}
+
+__device__ __forceinline__ f32x2 f2_splat(float v) { return f2_pack(v, v); }
+__device__ __forceinline__ f32x2 f2_rsqrt_clamped(f32x2 v) {
+    return f2_pack(rsqrt_mufu(fmaxf(f2_lo(v), kTiny)), rsqrt_mufu(fmaxf(f2_hi(v), kTiny)));
+}
+__device__ __forceinline__ f32x2 f2_max0(f32x2 v) { return f2_pack(fmaxf(f2_lo(v), 0.f), fmaxf(f2_hi(v), 0.f)); }
+__device__ __forceinline__ f32x2 f2_rcp(f32x2 v) { return f2_pack(rcp_mufu(f2_lo(v)), rcp_mufu(f2_hi(v))); }
+
+// The record of this thread's point as pairs (both halves the same value).
+struct Rec2 {
+    f32x2 p[3], c[3], u[3], m[3];   // r0.xyz, r1.xyz, r2.xyz, r3.xyz
+    f32x2 s0, s1, s2, s3;           // r0.w, r1.w, r2.w, r3.w
+};
+
+__device__ __forceinline__ Rec2 rec2_of(const float4& r0, const float4& r1, const float4& r2, const float4& r3) {
+    Rec2 R;
+    R.p[0] = f2_splat(r0.x); R.p[1] = f2_splat(r0.y); R.p[2] = f2_splat(r0.z);
+    R.c[0] = f2_splat(r1.x); R.c[1] = f2_splat(r1.y); R.c[2] = f2_splat(r1.z);
+    R.u[0] = f2_splat(r2.x); R.u[1] = f2_splat(r2.y); R.u[2] = f2_splat(r2.z);
+    R.m[0] = f2_splat(r3.x); R.m[1] = f2_splat(r3.y); R.m[2] = f2_splat(r3.z);
+    R.s0 = f2_splat(r0.w); R.s1 = f2_splat(r1.w); R.s2 = f2_splat(r2.w); R.s3 = f2_splat(r3.w);
+    return R;
+}
+
+// The sums of bwd_tile for two queries at a time (one per half of every
+// pair), the FP32 arithmetic as .f32x2, one special-function step per query.
+template <bool KAPPA, bool WEIGHTED>
+__device__ __forceinline__ void bwd_tile2(const ulonglong2* __restrict__ tile, const Rec2& R,
+                                          f32x2 (&acc)[kNAcc]) {
+    const f32x2 ONE = f2_splat(1.f), MONE = f2_splat(-1.f);
+#pragma unroll 1
+    for (int j = 0; j < kQTile / 2; ++j) {
+        const ulonglong2 qa = tile[3 * j], qb = tile[3 * j + 1], qc = tile[3 * j + 2];
+        const f32x2 X = qa.x, Y = qa.y, Z = qb.x;
+        const f32x2 DX = f2_sub(X, R.p[0]), DY = f2_sub(Y, R.p[1]), DZ = f2_sub(Z, R.p[2]);
+        const f32x2 D2 = f2_fma(DX, DX, f2_fma(DY, DY, f2_mul(DZ, DZ)));
+        const f32x2 D = f2_pack(sqrt_mufu(f2_lo(D2)), sqrt_mufu(f2_hi(D2)));
+        const f32x2 ARG = f2_sub(qc.x, f2_mul(qb.y, D));                    // A0 - L d
+        f32x2 CW = f2_mul(qc.y, f2_pack(ex2_mufu(f2_lo(ARG)), ex2_mufu(f2_hi(ARG))));   // (G/W) w
+        if (WEIGHTED) CW = f2_mul(CW, R.s3);
+        if (!KAPPA) {
+            const f32x2 VX = f2_sub(X, R.c[0]), VY = f2_sub(Y, R.c[1]), VZ = f2_sub(Z, R.c[2]);
+            const f32x2 H = f2_fma(VX, R.u[0], f2_fma(VY, R.u[1], f2_mul(VZ, R.u[2])));
+            const f32x2 NH = f2_mul(H, MONE);
+            const f32x2 PX = f2_fma(NH, R.u[0], VX), PY = f2_fma(NH, R.u[1], VY), PZ = f2_fma(NH, R.u[2], VZ);
+            const f32x2 RHO2 = f2_fma(PX, PX, f2_fma(PY, PY, f2_mul(PZ, PZ)));
+            const f32x2 RR = f2_rsqrt_clamped(RHO2);
+            const f32x2 E = f2_sub(f2_mul(RHO2, RR), R.s1);
+            const f32x2 RD = f2_rsqrt_clamped(f2_fma(E, E, f2_mul(H, H)));
+            const f32x2 SR = f2_mul(R.s0, RD);
+            const f32x2 CA = f2_mul(CW, f2_mul(f2_mul(E, RR), SR)), CB = f2_mul(CW, f2_mul(H, SR));
+            const f32x2 NCA = f2_mul(CA, MONE), NCB = f2_mul(CB, MONE), NCHA = f2_mul(NH, CA);
+            acc[0] = f2_fma(NCA, PX, f2_fma(NCB, R.u[0], acc[0]));
+            acc[1] = f2_fma(NCA, PY, f2_fma(NCB, R.u[1], acc[1]));
+            acc[2] = f2_fma(NCA, PZ, f2_fma(NCB, R.u[2], acc[2]));
+            acc[3] = f2_fma(CB, VX, f2_fma(NCHA, PX, acc[3]));
+            acc[4] = f2_fma(CB, VY, f2_fma(NCHA, PY, acc[4]));
+            acc[5] = f2_fma(CB, VZ, f2_fma(NCHA, PZ, acc[5]));
+            acc[6] = f2_fma(f2_mul(CW, MONE), f2_mul(E, SR), acc[6]);
+            acc[7] = f2_add(acc[7], CW);                                      // times -sT at the end
+        } else {
+            const f32x2 YX = f2_sub(X, R.c[0]), YY = f2_sub(Y, R.c[1]), YZ = f2_sub(Z, R.c[2]);
+            const f32x2 H = f2_fma(YX, R.u[0], f2_fma(YY, R.u[1], f2_mul(YZ, R.u[2])));
+            const f32x2 HH = f2_mul(H, H);
+            const f32x2 T2 = f2_sub(f2_fma(YX, YX, f2_fma(YY, YY, f2_mul(YZ, YZ))), HH);
+            const f32x2 M = f2_fma(R.s1, T2, f2_fma(YX, R.m[0], f2_fma(YY, R.m[1], f2_mul(YZ, R.m[2]))));
+            const f32x2 Z1 = f2_max0(f2_fma(R.s1, M, ONE));
+            const f32x2 RS1 = f2_rsqrt_clamped(Z1);
+            const f32x2 AP = f2_mul(M, f2_rcp(f2_fma(Z1, RS1, ONE)));
+            const f32x2 AA = f2_mul(AP, AP);
+            const f32x2 NP = f2_fma(R.s2, f2_add(AA, HH), f2_mul(R.s0, AP));
+            const f32x2 Z2 = f2_max0(f2_fma(R.s2, NP, ONE));
+            const f32x2 RS2 = f2_rsqrt_clamped(Z2);
+            const f32x2 G = f2_mul(NP, f2_rcp(f2_fma(Z2, RS2, ONE)));
+            const f32x2 C1 = f2_mul(f2_mul(f2_splat(0.25f), f2_mul(RS1, RS2)), f2_fma(f2_add(R.s2, R.s2), AP, R.s0));
+            const f32x2 AY = f2_mul(f2_add(C1, C1), R.s1);
+            const f32x2 BU = f2_mul(H, f2_sub(f2_mul(RS2, R.s2), AY));
+            const f32x2 CAY = f2_mul(CW, AY), CC1 = f2_mul(CW, C1), CBU = f2_mul(CW, BU);
+            const f32x2 NCAY = f2_mul(CAY, MONE), NCC1 = f2_mul(CC1, MONE), NCBU = f2_mul(CBU, MONE);
+            // dg/dq = -(ay y + c1 m* + bu u)
+            acc[0] = f2_fma(NCAY, YX, f2_fma(NCC1, R.m[0], f2_fma(NCBU, R.u[0], acc[0])));
+            acc[1] = f2_fma(NCAY, YY, f2_fma(NCC1, R.m[1], f2_fma(NCBU, R.u[1], acc[1])));
+            acc[2] = f2_fma(NCAY, YZ, f2_fma(NCC1, R.m[2], f2_fma(NCBU, R.u[2], acc[2])));
+            acc[3] = f2_fma(CBU, YX, acc[3]);                                 // dg/du = bu y
+            acc[4] = f2_fma(CBU, YY, acc[4]);
+            acc[5] = f2_fma(CBU, YZ, acc[5]);
+            acc[6] = f2_fma(CC1, YX, acc[6]);                                 // dg/dm* = c1 y
+            acc[7] = f2_fma(CC1, YY, acc[7]);
+            acc[8] = f2_fma(CC1, YZ, acc[8]);
+            acc[9] = f2_fma(CC1, f2_sub(T2, AA), acc[9]);                     // dg/dk
+            acc[10] = f2_fma(f2_mul(f2_splat(0.5f), f2_mul(CW, RS2)),        // dg/dK
+                             f2_sub(f2_add(AA, HH), f2_mul(G, G)), acc[10]);
+        }
     }
 }
 
@@ -119,7 +222,7 @@ __device__ __forceinline__ void bwd_tile(const float4* __restrict__ tile, const 
 
 template <bool WEIGHTED>
 __global__ void __launch_bounds__(kThreads) k_bwd_params(const float4* __restrict__ rec, int64_t slots,
-                                                         int64_t direct_slots, const float4* __restrict__ qrec,
+                                                         int64_t direct_slots, const float* __restrict__ qrec,
                                                          int64_t qtiles, int64_t qtiles_per_chunk,
                                                          float* __restrict__ part, int32_t* status) {
     extern __shared__ __align__(128) char smem[];
@@ -134,7 +237,7 @@ __global__ void __launch_bounds__(kThreads) k_bwd_params(const float4* __restric
     __syncthreads();
     if (warp == kConsumerWarps) {
         if (lane == 0)
-            ring.produce(buf, reinterpret_cast<const char*>(qrec + t0 * kQTile * 2), nt, kQTileBytes, status);
+            ring.produce(buf, reinterpret_cast<const char*>(qrec) + (size_t)t0 * kQTileBytes, nt, kQTileBytes, status);
         return;
     }
     const int64_t slot = (int64_t)blockIdx.x * kPointsPerCta + threadIdx.x;
@@ -142,22 +245,23 @@ __global__ void __launch_bounds__(kThreads) k_bwd_params(const float4* __restric
     const float4 r0 = rec[4 * sl], r1 = rec[4 * sl + 1], r2 = rec[4 * sl + 2], r3 = rec[4 * sl + 3];
     // each warp holds one 32-record tile, all of one form
     const bool kappa = ((int64_t)blockIdx.x * kPointsPerCta + warp * 32) >= direct_slots;
-    float acc[kNAcc], tacc[kNAcc];
+    const Rec2 R = rec2_of(r0, r1, r2, r3);
+    // two queries' sums side by side (each half sums every other query)
+    f32x2 acc2[kNAcc];
 #pragma unroll
-    for (int k = 0; k < kNAcc; ++k) acc[k] = 0.f;
+    for (int k = 0; k < kNAcc; ++k) acc2[k] = f2_splat(0.f);
     for (int64_t t = 0; t < nt; ++t) {
         if (!ring.wait_full(t, status)) return;
-        const float4* tile = reinterpret_cast<const float4*>(buf + (size_t)(t % kStages) * kQTileBytes);
-#pragma unroll
-        for (int k = 0; k < kNAcc; ++k) tacc[k] = 0.f;
+        const ulonglong2* tile = reinterpret_cast<const ulonglong2*>(buf + (size_t)(t % kStages) * kQTileBytes);
         if (kappa)
-            bwd_tile<true, WEIGHTED>(tile, r0, r1, r2, r3, tacc);
+            bwd_tile2<true, WEIGHTED>(tile, R, acc2);
         else
-            bwd_tile<false, WEIGHTED>(tile, r0, r1, r2, r3, tacc);
-#pragma unroll
-        for (int k = 0; k < kNAcc; ++k) acc[k] += tacc[k];
+            bwd_tile2<false, WEIGHTED>(tile, R, acc2);
         ring.release(t, lane);
     }
+    float acc[kNAcc];
+#pragma unroll
+    for (int k = 0; k < kNAcc; ++k) acc[k] = f2_lo(acc2[k]) + f2_hi(acc2[k]);
     if (slot < slots) {
         float* dst = part + ((size_t)chunk * slots + slot) * kNAcc;
 #pragma unroll
@@ -242,9 +346,9 @@ sdf_status launch_backward_params(const Cloud& c, int64_t q, const float* d_save
     const int64_t per = (qtiles + nchunks - 1) / nchunks;
     nchunks = (qtiles + per - 1) / per;
 
-    float4* qrec = nullptr;
+    float* qrec = nullptr;
     float* part = nullptr;
-    cudaError_t e = cudaMallocAsync(&qrec, (size_t)qtiles * kQTile * 2 * sizeof(float4), st);
+    cudaError_t e = cudaMallocAsync(&qrec, (size_t)qtiles * kQTileBytes, st);
     if (e == cudaSuccess) e = cudaMallocAsync(&part, (size_t)nchunks * slots * kNAcc * sizeof(float), st);
     if (e != cudaSuccess) {
         if (qrec) cudaFreeAsync(qrec, st);

@@ -346,6 +346,7 @@ void free_cloud(Cloud* c) {
     cudaFree(c->mrec);
     cudaFree(c->mperm);
     cudaFree(c->prec);
+    cudaFree(c->rec2);
     delete c;
 }
 
@@ -457,6 +458,7 @@ extern "C" sdf_status sdf_build_weighted(const float* d_points, const float* d_n
     {
         sdf_status bs = build_btiles(*c, st);
         if (bs == SDF_OK) bs = build_plane_records(*c, d_weights, st);   // the SSPD / SHC baselines
+        if (bs == SDF_OK) bs = build_pair_records(*c, st);               // the packed gradient loop
         if (bs != SDF_OK) {
             const std::string msg = sdf_last_error();
             fail(cudaSuccess, "");

@@ -155,6 +155,115 @@ __device__ __forceinline__ void grad_tile(const float4* __restrict__ tile, int c
     }
 }
 
+// --------------------------------------------------------------------------
+// The same tile two points at a time (the gradient without the Laplacian):
+// the records come pair-interleaved (rec2: for points 2k, 2k+1 of a tile and
+// each record float4 r_m, (r_m.x, r_m.x', r_m.y, r_m.y') then (r_m.z, r_m.z',
+// r_m.w, r_m.w')), so every 128-bit shared load gives two .f32x2 operands and
+// every FP32 step of the pair term runs for both points in one instruction;
+// the special-function steps stay one per point.  acc2 holds the two points'
+// partial sums side by side.  A pair's second point past the tile's `cnt`
+// (a zero record) gets weight 0.
+// --------------------------------------------------------------------------
+__device__ __forceinline__ f32x2 f2_rsqrt_clamped(f32x2 v) {
+    return f2_pack(rsqrt_mufu(fmaxf(f2_lo(v), kTiny)), rsqrt_mufu(fmaxf(f2_hi(v), kTiny)));
+}
+__device__ __forceinline__ f32x2 f2_max0(f32x2 v) { return f2_pack(fmaxf(f2_lo(v), 0.f), fmaxf(f2_hi(v), 0.f)); }
+__device__ __forceinline__ f32x2 f2_rcp(f32x2 v) { return f2_pack(rcp_mufu(f2_lo(v)), rcp_mufu(f2_hi(v))); }
+__device__ __forceinline__ f32x2 f2_splat(float v) { return f2_pack(v, v); }
+
+template <bool KAPPA, bool WEIGHTED>
+__device__ __forceinline__ void grad_tile2(const ulonglong2* __restrict__ tile, int cnt, f32x2 X, f32x2 Y, f32x2 Z,
+                                           f32x2 NL, f32x2 A0, f32x2 (&acc2)[A_LG]) {
+    const f32x2 ONE = f2_splat(1.f), MONE = f2_splat(-1.f);
+#pragma unroll 1
+    for (int j = 0; j < cnt; j += 2) {
+        const ulonglong2* r = tile + 4 * j;   // 8 x 16 B per pair of points
+        const ulonglong2 a0 = r[0], b0 = r[1], a1 = r[2], b1 = r[3], a2 = r[4], b2 = r[5];
+        const f32x2 DX = f2_sub(X, a0.x), DY = f2_sub(Y, a0.y), DZ = f2_sub(Z, b0.x);
+        const f32x2 D2 = f2_fma(DX, DX, f2_fma(DY, DY, f2_mul(DZ, DZ)));
+        const f32x2 RD = f2_rsqrt_clamped(D2);
+        const f32x2 D = f2_mul(D2, RD);
+        f32x2 G, GX, GY, GZ;
+        if (!KAPPA) {
+            // direct form (see grad_tile): g = sT (||(rho - R, h)|| - r), grad g = alpha v_perp + beta u
+            const f32x2 VX = f2_sub(X, a1.x), VY = f2_sub(Y, a1.y), VZ = f2_sub(Z, b1.x);
+            const f32x2 H = f2_fma(VX, a2.x, f2_fma(VY, a2.y, f2_mul(VZ, b2.x)));
+            const f32x2 NH = f2_mul(H, MONE);
+            const f32x2 PX = f2_fma(NH, a2.x, VX), PY = f2_fma(NH, a2.y, VY), PZ = f2_fma(NH, b2.x, VZ);
+            const f32x2 RHO2 = f2_fma(PX, PX, f2_fma(PY, PY, f2_mul(PZ, PZ)));
+            const f32x2 RR = f2_rsqrt_clamped(RHO2);
+            const f32x2 E = f2_sub(f2_mul(RHO2, RR), b1.y);            // rho - R
+            const f32x2 DT2 = f2_fma(E, E, f2_mul(H, H));
+            const f32x2 RDT = f2_rsqrt_clamped(DT2);
+            G = f2_fma(b0.y, f2_mul(DT2, RDT), b2.y);                  // sT D - sT r
+            const f32x2 SR = f2_mul(b0.y, RDT);
+            const f32x2 ALPHA = f2_mul(f2_mul(E, RR), SR), BETA = f2_mul(H, SR);
+            GX = f2_fma(ALPHA, PX, f2_mul(BETA, a2.x));
+            GY = f2_fma(ALPHA, PY, f2_mul(BETA, a2.y));
+            GZ = f2_fma(ALPHA, PZ, f2_mul(BETA, b2.x));
+        } else {
+            // curvature form (see grad_tile)
+            const ulonglong2 a3 = r[6], b3 = r[7];
+            const f32x2 YX = f2_sub(X, a1.x), YY = f2_sub(Y, a1.y), YZ = f2_sub(Z, b1.x);
+            const f32x2 H = f2_fma(YX, a2.x, f2_fma(YY, a2.y, f2_mul(YZ, b2.x)));
+            const f32x2 HH = f2_mul(H, H);
+            const f32x2 T2 = f2_sub(f2_fma(YX, YX, f2_fma(YY, YY, f2_mul(YZ, YZ))), HH);
+            const f32x2 M = f2_fma(b1.y, T2, f2_fma(YX, a3.x, f2_fma(YY, a3.y, f2_mul(YZ, b3.x))));
+            const f32x2 Z1 = f2_max0(f2_fma(b1.y, M, ONE));
+            const f32x2 RS1 = f2_rsqrt_clamped(Z1);
+            const f32x2 AP = f2_mul(M, f2_rcp(f2_fma(Z1, RS1, ONE)));
+            const f32x2 NP = f2_fma(b2.y, f2_fma(AP, AP, HH), f2_mul(b0.y, AP));
+            const f32x2 Z2 = f2_max0(f2_fma(b2.y, NP, ONE));
+            const f32x2 RS2 = f2_rsqrt_clamped(Z2);
+            G = f2_mul(NP, f2_rcp(f2_fma(Z2, RS2, ONE)));
+            const f32x2 C1 = f2_mul(f2_mul(f2_splat(0.25f), f2_mul(RS1, RS2)),
+                                    f2_fma(f2_add(b2.y, b2.y), AP, b0.y));
+            const f32x2 AY = f2_mul(f2_add(C1, C1), b1.y);             // coefficient of y_perp
+            const f32x2 BU = f2_mul(H, f2_sub(f2_mul(RS2, b2.y), AY)); // u coefficient after y_perp = y - h u
+            GX = f2_fma(AY, YX, f2_fma(C1, a3.x, f2_mul(BU, a2.x)));
+            GY = f2_fma(AY, YY, f2_fma(C1, a3.y, f2_mul(BU, a2.y)));
+            GZ = f2_fma(AY, YZ, f2_fma(C1, b3.x, f2_mul(BU, b2.x)));
+        }
+        const f32x2 ARG = f2_fma(NL, D, A0);
+        float w0 = ex2_mufu(f2_lo(ARG)), w1 = ex2_mufu(f2_hi(ARG));
+        if (j + 1 >= cnt) w1 = 0.f;                                     // no second point
+        f32x2 W = f2_pack(w0, w1);
+        if (WEIGHTED) W = f2_mul(W, r[7].y);                            // (A, A') = r3.w of both
+        const f32x2 WG = f2_mul(W, G), WN = f2_mul(W, RD), WGN = f2_mul(WG, RD);
+        acc2[A_W] = f2_add(acc2[A_W], W);
+        acc2[A_S] = f2_add(acc2[A_S], WG);
+        acc2[A_GX] = f2_fma(W, GX, acc2[A_GX]);
+        acc2[A_GY] = f2_fma(W, GY, acc2[A_GY]);
+        acc2[A_GZ] = f2_fma(W, GZ, acc2[A_GZ]);
+        acc2[A_NX] = f2_fma(WN, DX, acc2[A_NX]);
+        acc2[A_NY] = f2_fma(WN, DY, acc2[A_NY]);
+        acc2[A_NZ] = f2_fma(WN, DZ, acc2[A_NZ]);
+        acc2[A_HX] = f2_fma(WGN, DX, acc2[A_HX]);
+        acc2[A_HY] = f2_fma(WGN, DY, acc2[A_HY]);
+        acc2[A_HZ] = f2_fma(WGN, DZ, acc2[A_HZ]);
+        acc2[A_D] = f2_fma(W, D, acc2[A_D]);
+        acc2[A_GD] = f2_fma(WG, D, acc2[A_GD]);
+    }
+}
+
+// Pair-interleaved copy of the records (see grad_tile2), one thread per slot.
+__global__ void k_pair_records(const float4* __restrict__ rec, int64_t slots, float* __restrict__ rec2) {
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= slots) return;
+    const int64_t pair = s >> 1;   // tiles hold an even number of records, so pairs never straddle tiles
+    const int half = (int)(s & 1);
+    float* dst = rec2 + pair * 32;
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        const float4 v = rec[4 * s + m];
+        dst[8 * m + half] = v.x;
+        dst[8 * m + 2 + half] = v.y;
+        dst[8 * m + 4 + half] = v.z;
+        dst[8 * m + 6 + half] = v.w;
+    }
+}
+
 // Per-query lambda and shift from the prepass partials; p_far for GLOBAL.
 struct QueryLam {
     float L, A0, lam, dmax;
@@ -277,7 +386,7 @@ __device__ __forceinline__ void finalize(const GradArgs& ga, int64_t qi, float x
 }
 
 template <bool LAP, bool WEIGHTED>
-__global__ void __launch_bounds__(kThreads) k_fwd_grad(const float4* __restrict__ rec, int64_t n_direct,
+__global__ void __launch_bounds__(kThreads) __maxnreg__(LAP ? 112 : 96) k_fwd_grad(const float4* __restrict__ rec, int64_t n_direct,
                                                        int64_t n_kappa, int64_t tiles_direct, int64_t tiles_total,
                                                        int64_t tiles_per_chunk, GradArgs ga, int32_t* status) {
     extern __shared__ __align__(128) char smem[];
@@ -301,26 +410,53 @@ __global__ void __launch_bounds__(kThreads) k_fwd_grad(const float4* __restrict_
     const float x = a.x[3 * qq], y = a.x[3 * qq + 1], z = a.x[3 * qq + 2];
     const QueryLam ql = query_lambda(a, ga.pre, qq);
     constexpr int kAcc = NAcc<LAP>::value;
-    float acc[kAcc], tacc[kAcc];
+    float acc[kAcc];
 #pragma unroll
     for (int k = 0; k < kAcc; ++k) acc[k] = 0.f;
-    for (int64_t t = 0; t < nt; ++t) {
-        if (!ring.wait_full(t, status)) return;
-        const float4* tile = reinterpret_cast<const float4*>(buf + (size_t)(t % kStages) * kTileBytes);
-        const int64_t gt = t0 + t;
-        const bool kappa = gt >= tiles_direct;
-        const int64_t first = (kappa ? gt - tiles_direct : gt) * kTileRecs;
-        const int64_t seg = kappa ? n_kappa : n_direct;
-        const int cnt = (int)(seg - first < kTileRecs ? seg - first : kTileRecs);
+    if (LAP) {
+        // the Laplacian's 28 sums: one point at a time from the plain records
+        float tacc[kAcc];
+        for (int64_t t = 0; t < nt; ++t) {
+            if (!ring.wait_full(t, status)) return;
+            const float4* tile = reinterpret_cast<const float4*>(buf + (size_t)(t % kStages) * kTileBytes);
+            const int64_t gt = t0 + t;
+            const bool kappa = gt >= tiles_direct;
+            const int64_t first = (kappa ? gt - tiles_direct : gt) * kTileRecs;
+            const int64_t seg = kappa ? n_kappa : n_direct;
+            const int cnt = (int)(seg - first < kTileRecs ? seg - first : kTileRecs);
 #pragma unroll
-        for (int k = 0; k < kAcc; ++k) tacc[k] = 0.f;
-        if (kappa)
-            grad_tile<true, LAP, WEIGHTED>(tile, cnt, x, y, z, ql.L, ql.A0, tacc);
-        else
-            grad_tile<false, LAP, WEIGHTED>(tile, cnt, x, y, z, ql.L, ql.A0, tacc);
+            for (int k = 0; k < kAcc; ++k) tacc[k] = 0.f;
+            if (kappa)
+                grad_tile<true, LAP, WEIGHTED>(tile, cnt, x, y, z, ql.L, ql.A0, tacc);
+            else
+                grad_tile<false, LAP, WEIGHTED>(tile, cnt, x, y, z, ql.L, ql.A0, tacc);
 #pragma unroll
-        for (int k = 0; k < kAcc; ++k) acc[k] += tacc[k];
-        ring.release(t, lane);
+            for (int k = 0; k < kAcc; ++k) acc[k] += tacc[k];
+            ring.release(t, lane);
+        }
+    } else {
+        // the gradient's 13 sums: two points at a time from the pair-interleaved records
+        // (each half sums every other point; no per-tile blocking, to keep two CTAs per SM)
+        const f32x2 X = f2_splat(x), Y = f2_splat(y), Z = f2_splat(z), NL = f2_splat(-ql.L), A0 = f2_splat(ql.A0);
+        f32x2 acc2[A_LG];
+#pragma unroll
+        for (int k = 0; k < A_LG; ++k) acc2[k] = f2_splat(0.f);
+        for (int64_t t = 0; t < nt; ++t) {
+            if (!ring.wait_full(t, status)) return;
+            const ulonglong2* tile = reinterpret_cast<const ulonglong2*>(buf + (size_t)(t % kStages) * kTileBytes);
+            const int64_t gt = t0 + t;
+            const bool kappa = gt >= tiles_direct;
+            const int64_t first = (kappa ? gt - tiles_direct : gt) * kTileRecs;
+            const int64_t seg = kappa ? n_kappa : n_direct;
+            const int cnt = (int)(seg - first < kTileRecs ? seg - first : kTileRecs);
+            if (kappa)
+                grad_tile2<true, WEIGHTED>(tile, cnt, X, Y, Z, NL, A0, acc2);
+            else
+                grad_tile2<false, WEIGHTED>(tile, cnt, X, Y, Z, NL, A0, acc2);
+            ring.release(t, lane);
+        }
+#pragma unroll
+        for (int k = 0; k < A_LG; ++k) acc[k] = f2_lo(acc2[k]) + f2_hi(acc2[k]);
     }
     if (qi >= a.q) return;
     if (a.split == 1) {
@@ -418,7 +554,8 @@ sdf_status launch_query_grad(const Cloud& c, const float* d_x, int64_t q, float*
         ProfRange pr(SDF_K_FWD_GRAD, st);
         auto kern = lap ? (c.weighted ? k_fwd_grad<true, true> : k_fwd_grad<true, false>)
                         : (c.weighted ? k_fwd_grad<false, true> : k_fwd_grad<false, false>);
-        kern<<<grid, kThreads, kStages * kTileBytes, st>>>(c.rec, c.n_direct, c.n_kappa, c.tiles_direct,
+        // the gradient takes the pair-interleaved copy, the Laplacian the plain records
+        kern<<<grid, kThreads, kStages * kTileBytes, st>>>(lap ? c.rec : c.rec2, c.n_direct, c.n_kappa, c.tiles_direct,
                                                           c.tiles_direct + c.tiles_kappa, p.tiles_per_chunk, ga,
                                                           c.status);
         e = cudaGetLastError();
@@ -432,6 +569,18 @@ sdf_status launch_query_grad(const Cloud& c, const float* d_x, int64_t q, float*
     if (a.far) cudaFreeAsync(a.far, st);
     if (ga.part) cudaFreeAsync(ga.part, st);
     return e == cudaSuccess ? SDF_OK : cuda_error(e, "sdf_query_grad: launch");
+}
+
+sdf_status build_pair_records(Cloud& c, cudaStream_t st) {
+    const int64_t slots = (c.tiles_direct + c.tiles_kappa) * kTileRecs;
+    if (slots == 0) return SDF_OK;
+    cudaError_t e = cudaMalloc(&c.rec2, (size_t)slots * 4 * sizeof(float4));
+    if (e != cudaSuccess)
+        return e == cudaErrorMemoryAllocation ? set_error(SDF_ENOMEM, "sdf_build: paired records")
+                                              : cuda_error(e, "sdf_build: paired records");
+    k_pair_records<<<(unsigned)((slots + 255) / 256), 256, 0, st>>>(c.rec, slots, reinterpret_cast<float*>(c.rec2));
+    e = cudaGetLastError();
+    return e == cudaSuccess ? SDF_OK : cuda_error(e, "sdf_build: k_pair_records");
 }
 
 }  // namespace ptsdf

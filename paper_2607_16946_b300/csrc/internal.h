@@ -58,6 +58,9 @@ namespace ptsdf {
 #ifndef PTSDF_FWD_MINB
 #define PTSDF_FWD_MINB 4
 #endif
+#ifndef PTSDF_TC_SOFTSQRT
+#define PTSDF_TC_SOFTSQRT 1   // direct-form tensor-core epilogue: d on the FMA pipe, .f32x2 arithmetic (0: scalar)
+#endif
 constexpr int kTileRecs = PTSDF_TILE_RECS;   // records per main-loop tile (32 x 64 B = 2 KB)
 constexpr int kRecFloats = 16;
 constexpr int kPreTile = 256;        // points per prepass tile (4 KB)
@@ -75,6 +78,7 @@ struct Cloud {
     float aabb_diag = 0.f;
     float aabb[6] = {0, 0, 0, 0, 0, 0};
     float4* rec = nullptr;           // (tiles_direct + tiles_kappa) * kTileRecs * 4 float4
+    float4* rec2 = nullptr;          // the same records pair-interleaved for the packed gradient loop
     float4* pre = nullptr;           // pre_tiles * kPreTile float4
     float4* spheres = nullptr;       // n_spheres x (centre', radius), then the group spheres (sphere_index.h)
     int64_t n_spheres = 0;
@@ -185,6 +189,8 @@ sdf_status launch_query(const Cloud& c, const float* d_x, int64_t q, float* d_ph
 sdf_status launch_plane_query(const Cloud& c, const float* d_x, int64_t q, float* d_phi, const sdf_query_opts& o,
                               cudaStream_t st);
 sdf_status build_plane_records(Cloud& c, const float* d_weights, cudaStream_t st);
+// grad.cu: the pair-interleaved records of the gradient loop (from c.rec)
+sdf_status build_pair_records(Cloud& c, cudaStream_t st);
 // trace.cu
 sdf_status launch_trace(const Cloud& c, const float* d_org, const float* d_dir, int64_t nrays, int32_t max_steps,
                         float eps, float t_max, float* d_t_hit, int32_t* d_steps, float* d_normals,

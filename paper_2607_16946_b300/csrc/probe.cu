@@ -16,6 +16,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstring>
 #include <vector>
 
 #include "device_common.cuh"
@@ -286,5 +287,50 @@ extern "C" sdf_status sdf_selftest_wait_timeout(int32_t limit_us, int32_t* statu
     cudaFree(d_waited);
     if (e != cudaSuccess) return cuda_error(e, "sdf_selftest_wait_timeout");
     *waited_ms = (double)w * 1e-6;
+    return SDF_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Accuracy of sqrt2_newton<2> (the FMA-pipe square root of the tensor-core
+// epilogue) against CUDA's correctly rounded sqrtf: every positive normal
+// float whose bit pattern is a multiple of 64 (2^25 inputs from 1.2e-38 to
+// 3.4e38), as relative errors; the largest is returned.
+// ---------------------------------------------------------------------------
+namespace ptsdf {
+namespace {
+
+__global__ void k_soft_sqrt_check(uint32_t n, unsigned int* worst_bits) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float x0 = __uint_as_float(0x00800000u + 128u * i), x1 = __uint_as_float(0x00800000u + 128u * i + 64u);
+    const f32x2 r = sqrt2_newton<2>(x0, x1);
+    float e = 0.f;
+    if (x0 >= 1e-30f) e = fmaxf(e, fabsf(f2_lo(r) - sqrtf(x0)) / sqrtf(x0));
+    if (x1 >= 1e-30f) e = fmaxf(e, fabsf(f2_hi(r) - sqrtf(x1)) / sqrtf(x1));
+    if (!(e == e)) e = 1.f;   // a NaN counts as a total miss
+    atomicMax(worst_bits, __float_as_uint(e));
+}
+
+}  // namespace
+}  // namespace ptsdf
+
+extern "C" sdf_status sdf_selftest_soft_sqrt(double* max_rel_err) {
+    if (!max_rel_err) return set_error(SDF_EINVAL, "sdf_selftest_soft_sqrt: NULL output");
+    // normal floats 0x00800000 .. 0x7f7fffff, two per thread, 64 bit patterns apart
+    const uint32_t n = (0x7f7fffffu - 0x00800000u) / 128u;
+    unsigned int* d = nullptr;
+    cudaError_t e = cudaMalloc(&d, sizeof(unsigned int));
+    if (e == cudaSuccess) e = cudaMemset(d, 0, sizeof(unsigned int));
+    if (e == cudaSuccess) {
+        k_soft_sqrt_check<<<(n + 255) / 256, 256>>>(n, d);
+        e = cudaGetLastError();
+    }
+    unsigned int h = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&h, d, sizeof(h), cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    if (e != cudaSuccess) return cuda_error(e, "sdf_selftest_soft_sqrt");
+    float f;
+    std::memcpy(&f, &h, sizeof(f));
+    *max_rel_err = (double)f;
     return SDF_OK;
 }

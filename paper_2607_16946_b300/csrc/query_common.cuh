@@ -79,7 +79,9 @@ __device__ __forceinline__ float finish_sums(float W, float S, int formula, floa
     if (formula == SDF_FORMULA_LSE) return (L > 0.f ? (A0 - log2f(W)) / L : 0.f) - offset;
     if (formula == SDF_FORMULA_SHC) {
         if (!(L > 0.f)) return -offset;
-        return copysignf((A0 - log2f(fabsf(S)) + kLog2TwoPi) / L, S) - offset;
+        // sign(w) times the distance term, which is negative where |w| > e^(lambda d_min)
+        const float v = (A0 - log2f(fabsf(S)) + kLog2TwoPi) / L;
+        return (S < 0.f ? -v : v) - offset;
     }
     return __fdiv_rn(S, W) - offset;
 }

@@ -172,9 +172,13 @@ __device__ int knn_scan(const RadiusArgs& a, float xs, float ys, float zs, int k
     return cnt;
 }
 
-// 12 resident blocks per SM (40 registers): the kernel waits on dependent loads,
-// so residency matters more than the few spilled registers.
-__global__ void __launch_bounds__(kRadiusThreads, 12) k_radius_query(RadiusArgs a) {
+// Phase 1, one thread per query: the points within R_eval.  A query with
+// none of them is appended, with the seed sphere its pass found, to a list
+// that phase 2 (k_radius_fallback) works through a warp per query.
+// 12 resident blocks per SM: the kernel waits on dependent loads, so
+// residency matters more than a few spilled registers.
+__global__ void __launch_bounds__(kRadiusThreads, 12) k_radius_query(RadiusArgs a, int* __restrict__ fb_count,
+                                                                     int2* __restrict__ fb_list) {
     const int64_t qi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (qi >= a.q) return;
     const float x = a.x[3 * qi], y = a.x[3 * qi + 1], z = a.x[3 * qi + 2];
@@ -224,21 +228,175 @@ __global__ void __launch_bounds__(kRadiusThreads, 12) k_radius_query(RadiusArgs 
         }
     }
     if (inside == 0) {
-        // 2. the kfb nearest points
-        float bd[kKnnMax];
-        int bi[kKnnMax];
-        const int cnt = knn_scan(a, xs, ys, zs, a.kfb, -1, best, bd, bi);
-        m = sqrtf(bd[0]);
-        for (int j = 0; j < cnt; ++j) {
-            float wa;
-            const float g = g_record(x, y, z, a.mrec + 4 * (int64_t)bi[j], !a.lse, wa);
-            const float w = wa * exp2f(-a.L * (sqrtf(bd[j]) - m));
-            W += w;
-            S = fmaf(w, g, S);
-        }
+        // 2. the kfb nearest points: deferred to phase 2 (one list slot per
+        //    query, claimed by one atomic per warp)
+        const unsigned mask = __activemask();
+        const int lane = (int)(threadIdx.x & 31);
+        const int leader = __ffs(mask) - 1;
+        int base = 0;
+        if (lane == leader) base = atomicAdd(fb_count, __popc(mask));
+        base = __shfl_sync(mask, base, leader);
+        fb_list[base + __popc(mask & ((1u << lane) - 1u))] = make_int2((int)qi, (int)best);
+        return;
     }
     // the blend, or the log-sum-exp distance m - ln(W) / lambda = m - log2(W) / L
     a.phi[qi] = (a.lse ? m - log2f(W) / a.L : __fdiv_rn(S, W)) - a.offset;
+}
+
+// ---------------------------------------------------------------------------
+// Phase 2: the k = 32 nearest points of each listed query, a warp per query.
+// The list is held one entry per lane, sorted ascending across the lanes by
+// (squared distance, Morton position).  Candidates come 32 at a time (half a
+// sphere); when any of them beats the 32nd entry they are sorted by a bitonic
+// network of shuffles and merged: the elementwise minimum of the ascending
+// list and the descending candidates holds the 32 smallest of both as a
+// bitonic sequence, which five more shuffle steps sort.  Spheres are visited
+// as in knn_scan: the seed first, then every sphere of a group within reach
+// whose lower bound reaches below the current 32nd distance, so the list is
+// the exact 32 nearest (ties by Morton position).
+// ---------------------------------------------------------------------------
+constexpr int kFallbackThreads = 256;
+constexpr unsigned kFull = 0xffffffffu;
+static_assert(kRadiusFallbackK == 32, "the fallback list is one entry per lane");
+
+__device__ __forceinline__ bool lex_less(float da, int ia, float db, int ib) {
+    return da < db || (da == db && ia < ib);
+}
+
+// Ascending bitonic sort of the 32 (d, i) pairs held by the lanes.
+__device__ __forceinline__ void warp_bitonic_sort(float& d, int& i, int lane) {
+#pragma unroll
+    for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            const float od = __shfl_xor_sync(kFull, d, j);
+            const int oi = __shfl_xor_sync(kFull, i, j);
+            const bool take_min = ((lane & j) == 0) == ((lane & k) == 0 || k == 32);
+            const bool other_less = lex_less(od, oi, d, i);
+            if (take_min == other_less) {
+                d = od;
+                i = oi;
+            }
+        }
+    }
+}
+
+// Merges the lanes' candidates (cd, ci) into the sorted list (ld, li).
+__device__ __forceinline__ void warp_merge(float cd, int ci, float& ld, int& li, int lane) {
+    warp_bitonic_sort(cd, ci, lane);
+    const float rd = __shfl_sync(kFull, cd, 31 - lane);
+    const int ri = __shfl_sync(kFull, ci, 31 - lane);
+    if (lex_less(rd, ri, ld, li)) {
+        ld = rd;
+        li = ri;
+    }
+#pragma unroll
+    for (int j = 16; j > 0; j >>= 1) {
+        const float od = __shfl_xor_sync(kFull, ld, j);
+        const int oi = __shfl_xor_sync(kFull, li, j);
+        const bool other_less = lex_less(od, oi, ld, li);
+        if (((lane & j) == 0) == other_less) {
+            ld = od;
+            li = oi;
+        }
+    }
+}
+
+// Offers the points of sphere t (two halves of 32) to the list; kd, ki: the
+// current 32nd entry (every lane holds it).
+__device__ __forceinline__ void warp_scan_sphere(const RadiusArgs& a, float xs, float ys, float zs, int64_t t,
+                                                 int lane, float& ld, int& li, float& kd, int& ki) {
+    const int64_t j0 = t * kSphereTile;
+    const int c = sphere_count(t, a.n);
+#pragma unroll
+    for (int h = 0; h < kSphereTile; h += 32) {
+        float d2 = INFINITY;
+        int idx = 0x7fffffff;
+        if (h + lane < c) {
+            d2 = dist2_pre(xs, ys, zs, a.pre, j0 + h + lane);
+            idx = (int)(j0 + h + lane);
+        }
+        if (!__any_sync(kFull, lex_less(d2, idx, kd, ki))) continue;
+        warp_merge(d2, idx, ld, li, lane);
+        kd = __shfl_sync(kFull, ld, 31);
+        ki = __shfl_sync(kFull, li, 31);
+    }
+}
+
+__global__ void __launch_bounds__(kFallbackThreads) k_radius_fallback(RadiusArgs a, const int* __restrict__ fb_count,
+                                                                      const int2* __restrict__ fb_list) {
+    const int lane = (int)(threadIdx.x & 31);
+    const int64_t warps = (int64_t)gridDim.x * (kFallbackThreads / 32);
+    const int count = *fb_count;
+    for (int64_t e = (int64_t)blockIdx.x * (kFallbackThreads / 32) + threadIdx.x / 32; e < count; e += warps) {
+        const int2 job = fb_list[e];
+        const int64_t qi = job.x, seed = job.y;
+        const float x = a.x[3 * qi], y = a.x[3 * qi + 1], z = a.x[3 * qi + 2];
+        const float xs = x - a.cx, ys = y - a.cy, zs = z - a.cz;
+        float ld = INFINITY, kd = INFINITY;
+        int li = 0x7fffffff, ki = 0x7fffffff;
+        warp_scan_sphere(a, xs, ys, zs, seed, lane, ld, li, kd, ki);
+        for (int64_t g0 = 0; g0 < a.ngroups; g0 += 32) {
+            // the bound only tightens as the list fills, so a group beyond it now
+            // has no member within it later
+            const float glim = kd < INFINITY ? sqrtf(kd) * (1.f + 1e-6f) : INFINITY;
+            const int64_t g = g0 + lane;
+            const bool reach = g < a.ngroups && group_lower(xs, ys, zs, __ldg(a.groups + g)) <= glim;
+            unsigned gm = __ballot_sync(kFull, reach);
+            while (gm) {
+                const int64_t gg = g0 + __ffs(gm) - 1;
+                gm &= gm - 1;
+                const int64_t te = group_end(gg, a.nsph);
+                for (int64_t t0 = gg * kGroupSpheres; t0 < te; t0 += 32) {
+                    // lanes past the group's last sphere, and the seed, take no part
+                    const int64_t t = t0 + lane;
+                    const bool real = t < te && t != seed;
+                    float lb = INFINITY;
+                    if (real) {
+                        const float4 sp = __ldg(a.spheres + t);
+                        lb = centre_dist(xs, ys, zs, sp) - sp.w;
+                    }
+                    const float slim = kd < INFINITY ? sqrtf(kd) * (1.f + 1e-6f) : INFINITY;
+                    unsigned sm = __ballot_sync(kFull, real && lb <= slim);
+                    while (sm) {
+                        const int b = __ffs(sm) - 1;
+                        sm &= sm - 1;
+                        // re-checked against the bound as it stands now
+                        const float lbb = __shfl_sync(kFull, lb, b);
+                        if (!(lbb <= (kd < INFINITY ? sqrtf(kd) * (1.f + 1e-6f) : INFINITY))) continue;
+                        warp_scan_sphere(a, xs, ys, zs, t0 + b, lane, ld, li, kd, ki);
+                    }
+                }
+            }
+        }
+        // the blend (or log-sum-exp distance) over the list, shifted by its
+        // nearest.  Far from the surface lambda d is large (lambda = 10^3 / D
+        // gives 10^4 - 10^5 there), so the weights would amplify the FP32
+        // rounding of d by that much: the 32 distances are taken again in
+        // FP64 from the input coordinates (the records' p), and only their
+        // differences to the nearest enter the exponent.
+        double dd = 0.0;
+        if (li != 0x7fffffff) {
+            const float4 r0 = __ldg(a.mrec + 4 * (int64_t)li);
+            const double ex = (double)x - r0.x, ey = (double)y - r0.y, ez = (double)z - r0.z;
+            dd = sqrt(ex * ex + ey * ey + ez * ez);
+        }
+        const double m0 = __shfl_sync(kFull, dd, 0);
+        const float m = (float)m0;
+        float W = 0.f, S = 0.f;
+        if (li != 0x7fffffff) {
+            float wa;
+            const float g = g_record(x, y, z, a.mrec + 4 * (int64_t)li, !a.lse, wa);
+            W = wa * exp2f(-a.L * (float)(dd - m0));
+            S = W * g;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            W += __shfl_xor_sync(kFull, W, o);
+            S += __shfl_xor_sync(kFull, S, o);
+        }
+        if (lane == 0) a.phi[qi] = (a.lse ? m - log2f(W) / a.L : __fdiv_rn(S, W)) - a.offset;
+    }
 }
 
 // Per point: mean of the distances to its k nearest other points; one
@@ -321,6 +479,7 @@ RadiusArgs radius_args(const Cloud& c) {
 
 sdf_status launch_radius_query(const Cloud& c, const float* d_x, int64_t q, float* d_phi, const sdf_query_opts& o,
                                cudaStream_t st) {
+    if (q > 0x7fffffffLL) return set_error(SDF_EINVAL, "sdf_query: SDF_LAMBDA_RADIUS takes at most 2^31 - 1 queries");
     RadiusArgs a = radius_args(c);
     a.x = d_x;
     a.q = q;
@@ -329,10 +488,32 @@ sdf_status launch_radius_query(const Cloud& c, const float* d_x, int64_t q, floa
     a.reval = 2.f * o.C / o.fixed_lambda;
     a.offset = o.offset;
     a.lse = o.formula == SDF_FORMULA_LSE ? 1 : 0;
-    ProfRange pr(SDF_K_RADIUS, st);
-    k_radius_query<<<(unsigned)((q + kRadiusThreads - 1) / kRadiusThreads), kRadiusThreads, 0, st>>>(a);
-    const cudaError_t e = cudaGetLastError();
-    return e == cudaSuccess ? SDF_OK : cuda_error(e, "sdf_query: k_radius_query launch");
+    // scratch: the fallback count (16 B) and list (one int2 per query)
+    char* scratch = nullptr;
+    cudaError_t e = cudaMallocAsync(&scratch, 16 + (size_t)q * sizeof(int2), st);
+    if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? set_error(SDF_ENOMEM, "sdf_query: radius scratch")
+                                                                : cuda_error(e, "sdf_query: radius scratch");
+    int* fb_count = reinterpret_cast<int*>(scratch);
+    int2* fb_list = reinterpret_cast<int2*>(scratch + 16);
+    e = cudaMemsetAsync(fb_count, 0, sizeof(int), st);
+    {
+        ProfRange pr(SDF_K_RADIUS, st);
+        if (e == cudaSuccess) {
+            k_radius_query<<<(unsigned)((q + kRadiusThreads - 1) / kRadiusThreads), kRadiusThreads, 0, st>>>(
+                a, fb_count, fb_list);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) {
+            // enough warps to cover the list when every query falls back, at
+            // most 8 blocks per SM; each warp loops over its share
+            const int64_t need = (q + kFallbackThreads / 32 - 1) / (kFallbackThreads / 32);
+            const int64_t cap = 8LL * c.num_sms;
+            k_radius_fallback<<<(unsigned)(need < cap ? need : cap), kFallbackThreads, 0, st>>>(a, fb_count, fb_list);
+            e = cudaGetLastError();
+        }
+    }
+    cudaFreeAsync(scratch, st);
+    return e == cudaSuccess ? SDF_OK : cuda_error(e, "sdf_query: radius-limited launch");
 }
 
 sdf_status launch_knn_indices(const Cloud& c, int k, int32_t* d_idx, double* mean_dist, cudaStream_t st) {

@@ -13,6 +13,14 @@
 // A request's work depends only on its own inputs, cloud and options (the
 // launch plan is a function of Q, N and the SM count), so its result is the
 // same whether it runs alone or in a mix.
+//
+// Large requests are cut into query chunks (split_gpairs of the config): a
+// ticket names a job, and a job of more (query, point) pairs than the budget
+// runs as chunks of at least one full wave of unsplit query blocks on either
+// engine (2 x resident blocks x SMs x 512 queries), so that every query's
+// arithmetic is exactly that of the unsplit call.  A chunk's successor is
+// queued at the tail when the chunk is admitted: other requests interleave
+// with the chunks of a large one instead of waiting for all of it.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -56,16 +64,30 @@ __global__ void k_serve_combine(int op, const float* __restrict__ a, const float
     out[i] = op == SDF_REQ_UNION ? fminf(x, y) : op == SDF_REQ_INTERSECT ? fmaxf(x, y) : fmaxf(x, -y);
 }
 
-struct Request {
+// A submitted request (what a ticket names), run as `chunks` query chunks.
+struct Job {
     uint64_t ticket = 0;
     sdf_request r{};
+    sdf_request_stats st{};         // of the whole job; st.chunks = chunks
+    int chunks = 1;
+    int issued = 0;                 // chunks queued so far
+    int remaining = 1;              // chunks not finished
+    int64_t chunk_q = 0;            // queries per chunk (the last one takes the rest)
+    bool finished = false;          // stats final, waiting for poll
+};
+
+// One schedulable unit: a job, or one chunk of it (queries [q0, q0 + q)).
+struct Request {
+    std::shared_ptr<Job> job;
+    int64_t q0 = 0, q = 0;
     int64_t need = 0;               // bytes charged against the budget
     double work = 0.0;              // (query, point) pairs, for smallest-first admission
-    sdf_request_stats st{};
+    int32_t status = SDF_OK;
+    int64_t queued_ns = 0;          // when it joined the queue (the age guard of SMALLEST_FIRST)
+    int64_t done_ns = 0;
     int stream = 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     std::atomic<bool> done{false};
-    bool finished = false;          // stats final, waiting for poll
 };
 
 struct Server {
@@ -77,7 +99,7 @@ struct Server {
     std::condition_variable done_cv;  // pollers
     std::deque<std::shared_ptr<Request>> queue;
     std::vector<std::shared_ptr<Request>> inflight;
-    std::unordered_map<uint64_t, std::shared_ptr<Request>> all;
+    std::unordered_map<uint64_t, std::shared_ptr<Job>> all;
     int64_t mem_in_use = 0;
     uint64_t next_ticket = 1;
     bool stop = false;
@@ -85,13 +107,12 @@ struct Server {
     std::thread worker;
 };
 
-// bytes a request needs on the device: staging of host buffers plus the
-// scratch of the query kernels for its plan
-int64_t request_need(const Server& S, const sdf_request& r) {
-    const int64_t q = r.q;
+// bytes a request (or a chunk of q of its queries) needs on the device:
+// staging of host buffers plus the scratch of the query kernels for its plan
+int64_t request_need(const Server& S, const sdf_request& r, int64_t q) {
     int64_t b = 0;
     auto scratch = [&](const Cloud* c, bool grad) -> int64_t {
-        if (r.opts.lambda_mode == SDF_LAMBDA_RADIUS) return 4096;   // no scratch
+        if (r.opts.lambda_mode == SDF_LAMBDA_RADIUS) return q * 8 + 4096;   // the fallback list
         const Plan p = make_plan(*c, q, r.opts.split_n, grad ? kConsumerWarps * 32 : kQueriesPerCta);
         int64_t s = (int64_t)p.split * q * 8;                 // prepass partials
         if (grad) {
@@ -129,18 +150,26 @@ void CUDART_CB on_request_done(void* p) {
     Server* S = pr->first;
     Request* R = pr->second;
     delete pr;
-    R->st.done_ns = now_ns();
+    R->done_ns = now_ns();
     R->done.store(true, std::memory_order_release);
     S->cv.notify_all();
 }
 
 unsigned nblk(int64_t n) { return (unsigned)((n + 255) / 256); }
 
-// Enqueues one admitted request on its stream.
+// Enqueues one admitted request (or chunk) on its stream.
 sdf_status launch_request(Server& S, Request& R) {
     cudaStream_t st = S.streams[R.stream];
-    const sdf_request& r = R.r;
-    const int64_t q = r.q;
+    // the chunk's view of the job's buffers (a GRAD job is never cut)
+    sdf_request r = R.job->r;
+    const int64_t q = R.q;
+    if (R.q0 > 0) {
+        r.x += 3 * R.q0;
+        r.out += R.q0;
+        if (r.dirs) r.dirs += 3 * R.q0;
+        if (r.t) r.t += R.q0;
+    }
+    r.q = q;
     const Cloud& ca = *S.clouds[r.cloud_id];
     cudaError_t e = cudaEventRecord(R.ev0, st);
     if (e != cudaSuccess) return cuda_error(e, "serve: event");
@@ -218,29 +247,54 @@ sdf_status launch_request(Server& S, Request& R) {
         // no callback will come: wait for the stream here and finish the request
         delete arg;
         cudaStreamSynchronize(st);
-        R.st.done_ns = now_ns();
+        R.done_ns = now_ns();
         R.done.store(true, std::memory_order_release);
         return cuda_error(e, "serve: completion callback");
     }
     return s;
 }
 
+// Queries of one launch plan with no point split on either engine: two waves
+// of the FP32-unit loop's query blocks (the tensor-core loop needs fewer).
+int64_t min_chunk_queries(const Cloud& c) { return 2LL * kFwdMinBlocks * c.num_sms * kQueriesPerCta; }
+
+// The job's next chunk as a schedulable request (queries and charges).
+std::shared_ptr<Request> make_chunk(const Server& S, const std::shared_ptr<Job>& job) {
+    Job& J = *job;
+    auto R = std::make_shared<Request>();
+    R->job = job;
+    R->q0 = (int64_t)J.issued * J.chunk_q;
+    R->q = J.issued + 1 < J.chunks ? J.chunk_q : J.r.q - R->q0;
+    const sdf_request& r = J.r;
+    const bool two = r.kind == SDF_REQ_UNION || r.kind == SDF_REQ_INTERSECT || r.kind == SDF_REQ_DIFFERENCE;
+    R->need = request_need(S, r, R->q);
+    R->work = (double)R->q * (double)(S.clouds[r.cloud_id]->n + (two ? S.clouds[r.cloud_id_b]->n : 0));
+    R->queued_ns = J.issued == 0 ? J.st.arrive_ns : now_ns();
+    ++J.issued;
+    return R;
+}
+
 void scheduler(Server* S) {
     cudaSetDevice(S->cfg.device);
     std::unique_lock<std::mutex> lk(S->mu);
     while (true) {
-        // retire finished requests
+        // retire finished requests and chunks; a job is finished with its last chunk
         for (auto it = S->inflight.begin(); it != S->inflight.end();) {
             Request& R = **it;
             if (R.done.load(std::memory_order_acquire)) {
+                Job& J = *R.job;
                 float ms = 0.f;
-                if (cudaEventElapsedTime(&ms, R.ev0, R.ev1) == cudaSuccess) R.st.device_ms = ms;
+                if (cudaEventElapsedTime(&ms, R.ev0, R.ev1) == cudaSuccess) J.st.device_ms += ms;
                 cudaEventDestroy(R.ev0);
                 cudaEventDestroy(R.ev1);
                 S->mem_in_use -= R.need;
-                R.finished = true;
+                if (R.status != SDF_OK && J.st.status == SDF_OK) J.st.status = R.status;
+                J.st.done_ns = std::max(J.st.done_ns, R.done_ns);
+                if (--J.remaining == 0) {
+                    J.finished = true;
+                    S->done_cv.notify_all();
+                }
                 it = S->inflight.erase(it);
-                S->done_cv.notify_all();
             } else {
                 ++it;
             }
@@ -250,23 +304,24 @@ void scheduler(Server* S) {
         while (!S->queue.empty() && (int)S->inflight.size() < S->cfg.max_inflight) {
             size_t pick = 0;
             if (S->cfg.policy == SDF_SERVE_SMALLEST_FIRST &&
-                now_ns() - S->queue.front()->st.arrive_ns <= (int64_t)S->cfg.starve_ms * 1000000LL) {
+                now_ns() - S->queue.front()->queued_ns <= (int64_t)S->cfg.starve_ms * 1000000LL) {
                 for (size_t i = 1; i < S->queue.size(); ++i)
                     if (S->queue[i]->work < S->queue[pick]->work) pick = i;
             }
             if (S->mem_in_use + S->queue[pick]->need > S->cfg.mem_budget_bytes) break;
             std::shared_ptr<Request> R = S->queue[pick];
             S->queue.erase(S->queue.begin() + (long)pick);
-            R->st.admit_ns = now_ns();
+            Job& J = *R->job;
+            if (R->q0 == 0) J.st.admit_ns = now_ns();
             R->stream = S->next_stream;
             S->next_stream = (S->next_stream + 1) % (int)S->streams.size();
             S->mem_in_use += R->need;
             cudaEventCreate(&R->ev0);
             cudaEventCreate(&R->ev1);
-            R->st.start_ns = now_ns();
-            const sdf_status s = launch_request(*S, *R);
-            R->st.status = s;
+            if (R->q0 == 0) J.st.start_ns = now_ns();
+            R->status = launch_request(*S, *R);
             S->inflight.push_back(R);
+            if (J.issued < J.chunks) S->queue.push_back(make_chunk(*S, R->job));   // the next chunk, at the tail
         }
         if (S->stop && S->queue.empty() && S->inflight.empty()) break;
         S->cv.wait_for(lk, std::chrono::milliseconds(2));
@@ -341,9 +396,9 @@ extern "C" sdf_status sdf_serve_submit(sdf_server srv, const sdf_request* req, u
         (r.opts.formula == SDF_FORMULA_LSE &&
          (r.kind != SDF_REQ_QUERY || (r.opts.lambda_mode == SDF_LAMBDA_FIXED && !(r.opts.fixed_lambda > 0.f)))))
         return set_error(SDF_EINVAL, "sdf_serve_submit: bad options");
-    auto R = std::make_shared<Request>();
-    R->r = r;
-    R->st.arrive_ns = t_arrive;
+    auto J = std::make_shared<Job>();
+    J->r = r;
+    J->st.arrive_ns = t_arrive;
     {
         std::lock_guard<std::mutex> lk(S.mu);
         const bool two = r.kind == SDF_REQ_UNION || r.kind == SDF_REQ_INTERSECT || r.kind == SDF_REQ_DIFFERENCE;
@@ -351,16 +406,27 @@ extern "C" sdf_status sdf_serve_submit(sdf_server srv, const sdf_request* req, u
             (two && (r.cloud_id_b < 0 || r.cloud_id_b >= (int32_t)S.clouds.size())))
             return set_error(SDF_EINVAL, "sdf_serve_submit: unknown cloud id");
         if (S.stop) return set_error(SDF_EBUSY, "sdf_serve_submit: server is shutting down");
-        R->need = request_need(S, r);
-        const bool pair2 = r.kind == SDF_REQ_UNION || r.kind == SDF_REQ_INTERSECT || r.kind == SDF_REQ_DIFFERENCE;
-        R->work = (double)r.q * (double)(S.clouds[r.cloud_id]->n + (pair2 ? S.clouds[r.cloud_id_b]->n : 0));
-        if (R->need > S.cfg.mem_budget_bytes)
-            return set_error(SDF_ENOMEM, "sdf_serve_submit: request needs " + std::to_string(R->need) +
+        // cut a large job into chunks of at least min_chunk_queries each
+        const Cloud& ca = *S.clouds[r.cloud_id];
+        const double pairs = (double)r.q * (double)(ca.n + (two ? S.clouds[r.cloud_id_b]->n : 0));
+        if (S.cfg.split_gpairs > 0 && r.kind != SDF_REQ_GRAD && pairs > S.cfg.split_gpairs * 1e9) {
+            const int64_t most = r.q / (min_chunk_queries(ca) + kQueriesPerCta);
+            const double want = std::ceil(pairs / (S.cfg.split_gpairs * 1e9));
+            J->chunks = (int)std::max<int64_t>(1, std::min<int64_t>(most, (int64_t)std::min(want, 1e6)));
+        }
+        J->chunk_q = J->chunks > 1 ? (r.q / J->chunks) / kQueriesPerCta * kQueriesPerCta : r.q;
+        J->remaining = J->chunks;
+        J->st.chunks = J->chunks;
+        // the largest chunk (the last) must fit the budget on its own
+        const int64_t last_q = r.q - (int64_t)(J->chunks - 1) * J->chunk_q;
+        const int64_t need = request_need(S, r, last_q);
+        if (need > S.cfg.mem_budget_bytes)
+            return set_error(SDF_ENOMEM, "sdf_serve_submit: request needs " + std::to_string(need) +
                                              " bytes, more than the whole memory budget");
-        R->ticket = S.next_ticket++;
-        S.all[R->ticket] = R;
-        S.queue.push_back(R);
-        *ticket = R->ticket;
+        J->ticket = S.next_ticket++;
+        S.all[J->ticket] = J;
+        S.queue.push_back(make_chunk(S, J));
+        *ticket = J->ticket;
     }
     S.cv.notify_all();
     return SDF_OK;
@@ -373,21 +439,21 @@ extern "C" sdf_status sdf_serve_poll(sdf_server srv, uint64_t ticket, int64_t ti
     std::unique_lock<std::mutex> lk(S.mu);
     auto it = S.all.find(ticket);
     if (it == S.all.end()) return set_error(SDF_EINVAL, "sdf_serve_poll: unknown ticket");
-    std::shared_ptr<Request> R = it->second;
+    std::shared_ptr<Job> J = it->second;
     if (timeout_us < 0) {
-        S.done_cv.wait(lk, [&] { return R->finished; });
+        S.done_cv.wait(lk, [&] { return J->finished; });
     } else {
         // clamp to a day so that the deadline cannot overflow the clock
         const int64_t us = std::min<int64_t>(timeout_us, 86400LL * 1000000LL);
         const auto deadline = std::chrono::steady_clock::now() + std::chrono::microseconds(us);
-        while (!R->finished) {
-            if (S.done_cv.wait_until(lk, deadline) == std::cv_status::timeout && !R->finished)
+        while (!J->finished) {
+            if (S.done_cv.wait_until(lk, deadline) == std::cv_status::timeout && !J->finished)
                 return set_error(SDF_ETIMEOUT, "sdf_serve_poll: not finished");
         }
     }
-    if (stats) *stats = R->st;
+    if (stats) *stats = J->st;
     S.all.erase(it);
-    return R->st.status == SDF_OK ? SDF_OK : (sdf_status)R->st.status;
+    return J->st.status == SDF_OK ? SDF_OK : (sdf_status)J->st.status;
 }
 
 extern "C" sdf_status sdf_serve_stats(sdf_server srv, int32_t* queued, int32_t* inflight, int64_t* mem_in_use) {

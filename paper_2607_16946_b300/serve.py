@@ -29,7 +29,7 @@ SDF_SERVE_FIFO, SDF_SERVE_SMALLEST_FIRST = 0, 1
 class sdf_serve_config(ctypes.Structure):
     _fields_ = [("mem_budget_bytes", ctypes.c_int64), ("max_inflight", ctypes.c_int32),
                 ("n_streams", ctypes.c_int32), ("device", ctypes.c_int32), ("policy", ctypes.c_int32),
-                ("starve_ms", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("starve_ms", ctypes.c_int32), ("split_gpairs", ctypes.c_int32)]
 
 
 class sdf_request(ctypes.Structure):
@@ -40,18 +40,21 @@ class sdf_request(ctypes.Structure):
 
 
 class sdf_request_stats(ctypes.Structure):
-    _fields_ = [("status", ctypes.c_int32), ("reserved", ctypes.c_int32), ("arrive_ns", ctypes.c_int64),
+    _fields_ = [("status", ctypes.c_int32), ("chunks", ctypes.c_int32), ("arrive_ns", ctypes.c_int64),
                 ("admit_ns", ctypes.c_int64), ("start_ns", ctypes.c_int64), ("done_ns", ctypes.c_int64),
                 ("device_ms", ctypes.c_double)]
 
 
 class Server:
     def __init__(self, mem_budget_bytes: int = 8 << 30, max_inflight: int = 8, n_streams: int = 4,
-                 device: int | None = None, policy: int = SDF_SERVE_FIFO, starve_ms: int = 2000):
+                 device: int | None = None, policy: int = SDF_SERVE_FIFO, starve_ms: int = 2000,
+                 split_gpairs: int = 0):
+        """split_gpairs: requests above split_gpairs x 1e9 (query, point) pairs
+        run as query chunks interleaved with other requests (0: never)."""
         import torch
         cfg = sdf_serve_config(int(mem_budget_bytes), int(max_inflight), int(n_streams),
                                torch.cuda.current_device() if device is None else int(device), int(policy),
-                               int(starve_ms), 0)
+                               int(starve_ms), int(split_gpairs))
         h = ctypes.c_void_p()
         check(lib().sdf_serve_create(ctypes.byref(cfg), ctypes.byref(h)), "sdf_serve_create")
         self._h = h
@@ -99,7 +102,7 @@ class Server:
             self._keep.pop(ticket, None)
         check(s, "sdf_serve_poll")
         return {"arrive_ns": st.arrive_ns, "admit_ns": st.admit_ns, "start_ns": st.start_ns,
-                "done_ns": st.done_ns, "device_ms": st.device_ms}
+                "done_ns": st.done_ns, "device_ms": st.device_ms, "chunks": st.chunks}
 
     def stats(self) -> dict:
         q, f, m = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64()

@@ -108,9 +108,11 @@ def test_split_and_gradient_agree(ptsdf):
         _, gs, ls = run(cl, x, split_n=s)
         assert np.abs(ls - l1).max() <= 1e-4 * (1 + np.abs(l1).max())
         np.testing.assert_allclose(gs, g1, atol=1e-5)
+    # sdf_query_grad sums two points at a time (the packed loop), the Laplacian
+    # call one at a time: the same sums in another order
     xt = torch.as_tensor(x, device="cuda")
     _, gg, _ = cl.query_grad(xt, split_n=1)
-    np.testing.assert_allclose(gg.cpu().numpy(), g1, atol=1e-6)
+    np.testing.assert_allclose(gg.cpu().numpy(), g1, atol=1e-5)
 
 
 def test_laplacian_options(ptsdf):

@@ -40,17 +40,31 @@ def run(ptsdf, cloud, x, lam, C=64.0, **kw):
     return phi.cpu().numpy().astype(np.float64)
 
 
+def ambiguous_sets(p, x, R, chunk=16):
+    """Queries with a point within 1e-5 of R_eval, or whose 32nd and 33rd
+    nearest distances are within 1e-5 (relative): distances on the host cores
+    in float64, a chunk of queries at a time."""
+    import torch
+    P = torch.as_tensor(np.asarray(p, np.float64))
+    X = torch.as_tensor(np.asarray(x, np.float64))
+    out = np.zeros(len(x), bool)
+    for i0 in range(0, len(x), chunk):
+        d = torch.cdist(X[i0:i0 + chunk], P, compute_mode="donot_use_mm_for_euclid_dist")
+        amb = (torch.abs(d - R) < 1e-5 * R).any(1)
+        if d.shape[1] > 32:
+            v = torch.topk(d, 33, dim=1, largest=False, sorted=True).values
+            amb |= v[:, 32] - v[:, 31] < 1e-5 * v[:, 31]
+        out[i0:i0 + chunk] = amb.numpy()
+    return out
+
+
 def check_against_oracle(orc, p, x, got, lam, C=64.0, tol=None, lse=False):
     """Element-wise check; queries whose sets FP32 may decide either way are
     accepted against either oracle variant."""
     R = 2.0 * C / lam
     tol = TOL_REL * aabb_diag(p) if tol is None else tol
     ref = orc.phi_radius(x, lam=lam, reval=R, lse=lse)
-    d = np.sqrt(((x[:, None, :].astype(np.float64) - p[None, :, :].astype(np.float64)) ** 2).sum(-1))
-    near_edge = (np.abs(d - R) < 1e-5 * R).any(1)
-    part = np.partition(d, [31, 32], axis=1) if d.shape[1] > 32 else None
-    knn_tie = np.zeros(len(x), bool) if part is None else (part[:, 32] - part[:, 31] < 1e-5 * part[:, 31])
-    amb = near_edge | knn_tie
+    amb = ambiguous_sets(p, x, R)
     ok = np.abs(got - ref) <= tol
     if amb.any():
         lo = orc.phi_radius(x[amb], lam=lam, reval=R * (1 - 2e-5), lse=lse)
@@ -105,6 +119,30 @@ def test_ring_torus_paper_lambda(ptsdf, oracle_mod):
     _, used = orc.phi_radius(x, lam=lam, used=True)
     assert (used > 0).sum() > 100 and (used < 0).sum() > 100   # both branches exercised
     check_against_oracle(orc, p, x, got, lam)
+
+
+def test_large_superquadric_paper_lambda(ptsdf, oracle_mod):
+    """The radius-limited path at the scale the paper uses it for (clouds of
+    10^6 - 10^7 points): the noisy superquadric of the sphere-tracing
+    configuration with N = 2^21 points, lambda = 10^3 / D with D estimated by
+    the oracle from 2,000 seeded points (the all-points brute force is out of
+    reach), 1,536 queries: 1,024 in the box (mostly the 32-nearest fallback)
+    and 512 next to the points (mostly sums inside R_eval)."""
+    p, n, a = f32(*synth.superquadric(1 << 21, 2021))
+    rng = np.random.Generator(np.random.PCG64(2022))
+    D = oracle_mod.knn_mean_distance_sample(p, rng.choice(len(p), 2000, replace=False), 64)
+    lam = 1e3 / D
+    cl = ptsdf.Cloud(p, n, a)
+    assert abs(cl.knn_mean_distance(64) - D) <= 0.03 * D      # the sample's D is an estimate
+    near = p[rng.integers(0, len(p), 512)] + rng.normal(scale=0.04 * D, size=(512, 3))   # R_eval = 0.128 D
+    x = f32(np.concatenate([synth.uniform_queries(1024, 2023, -1.2, 1.2), near]))
+    got = run(ptsdf, cl, x, lam)
+    orc = oracle_mod.Cloud(p, n, a)
+    _, used = orc.phi_radius(x, lam=lam, used=True)
+    assert (used > 0).sum() > 100 and (used < 0).sum() > 500   # both branches exercised
+    check_against_oracle(orc, p, x, got, lam)
+    lse = run(ptsdf, cl, x, lam, formula=ptsdf.SDF_FORMULA_LSE)
+    check_against_oracle(orc, p, x, lse, lam, lse=True)
 
 
 @pytest.mark.parametrize("lam", [30.0, 300.0])

@@ -206,3 +206,40 @@ def test_weighted_cloud_and_lse_requests(env):
         srv.submit(S.SDF_REQ_GRAD, ids[0], x, torch.empty(40, device="cuda"), formula=m.SDF_FORMULA_LSE)
     srv.shutdown()
     weighted.close()
+
+
+def test_large_requests_run_as_chunks_equal_direct(env):
+    """Requests above the split budget (split_gpairs) run as query chunks that
+    other requests interleave with; each chunk keeps at least one unsplit wave
+    of query blocks, so the result equals the direct call bit for bit: a
+    device-buffer query, a host-buffer query and a Boolean, submitted with
+    small requests in between."""
+    m, S, torch, clouds = env
+    srv = S.Server(mem_budget_bytes=4 << 30, max_inflight=3, n_streams=3, split_gpairs=1)
+    ids = [srv.register(c) for c in clouds]
+    rng = np.random.Generator(np.random.PCG64(21))
+    q = 2_000_000                                  # 4e10 pairs on the 20,000-point torus
+    x = torch.as_tensor(f32(rng.uniform(-1.5, 1.5, size=(q, 3))), dtype=torch.float32, device="cuda")
+    xh = x[:1_300_000].cpu().numpy()
+    jobs = []
+    out = torch.empty(q, device="cuda")
+    jobs.append((srv.submit(S.SDF_REQ_QUERY, ids[1], x, out), out, lambda: clouds[1].query(x), 3))
+    small_x = [torch.as_tensor(f32(rng.uniform(-1.5, 1.5, size=(2000, 3))), dtype=torch.float32, device="cuda")
+               for _ in range(6)]
+    for k, sx in enumerate(small_x):
+        o = torch.empty(2000, device="cuda")
+        jobs.append((srv.submit(S.SDF_REQ_QUERY, ids[k % 4], sx, o), o,
+                     (lambda c=clouds[k % 4], sx=sx: c.query(sx)), 1))
+    oh = np.empty(xh.shape[0], np.float32)
+    jobs.append((srv.submit(S.SDF_REQ_QUERY, ids[1], xh, oh), oh, lambda: clouds[1].query(xh), 2))
+    ou = torch.empty(q, device="cuda")
+    jobs.append((srv.submit(S.SDF_REQ_UNION, ids[1], x, ou, cloud_id_b=ids[2]), ou,
+                 lambda: m.combine(m.SDF_UNION, clouds[1].query(x), clouds[2].query(x)), 3))
+    for ticket, o, direct, chunks in jobs:
+        st = srv.poll(ticket)
+        assert st["chunks"] == chunks
+        ref = direct()
+        torch.cuda.synchronize()
+        got = torch.as_tensor(o) if isinstance(o, np.ndarray) else o.cpu()
+        assert torch.equal(got, ref.cpu()), ticket
+    srv.shutdown()
