@@ -52,21 +52,22 @@ WORKLOAD = ("dense_grid: ring torus N=100000 (R=1, r=0.35, noise 0.005, 2deg vMF
 #    FP32-unit loop, direct torus form: 25 FP32 instructions (two 3-vector
 #    differences, two dots, the perpendicular component and its norm, the tube
 #    distance, the blend and two accumulations) + 4 MUFU = 29 issue slots.
-#    Tensor-core loop: 9 FMA-pipe instructions + 4 MUFU per pair (the
-#    products come from the tensor cores).
 #  MUFU (XU pipe): sdf_probe_rates measures, on the box, the single
 #    operations (on B300 sqrt / rsqrt / rcp.approx 16.0 results per SM per
 #    clock, ex2.approx 32.0, timed over the union of each SM's CTA windows and
-#    confirmed by CUDA events and by ncu's XU instruction counts) and each
-#    record form's whole per-pair mix as dependent chains.  A direct pair
+#    confirmed by CUDA events and by ncu's XU instruction counts) and the
+#    per-pair mixes as dependent chains.  The FP32-unit loop's direct pair
 #    needs three square roots (|x - p|, the axis distance, the tube distance)
 #    and one exp2: 3 x 8 + 4 = 28 XU cycles per 32 pairs per SM sub-partition,
-#    4.571 pairs per SM per clock, which the measured mix matches.  It binds
-#    the tensor-core loop (issue ceiling 128/13 = 9.8) and nearly ties the
-#    FP32-unit loop's issue ceiling (128/29 = 4.41).
+#    4.571 pairs per SM per clock, which the measured mix matches; it nearly
+#    ties that loop's issue ceiling (128/29 = 4.41).
+#  FMA pipe: 128 FP32 lanes per SM (sdf_probe_rates: 124.1 results per clock);
+#    an .f32x2 instruction occupies it for two operations.
 INSTR_PER_PAIR = 29
 THREAD_INSTR_PER_SM_CLK = 128
 NOMINAL_RATES = {"sqrt": 16.0, "rsqrt": 16.0, "ex2": 32.0, "fma": 128.0, "rcp": 16.0}
+# probe mixes timed whole: the FP32-unit loop's direct pair, and the
+# tensor-core loop's curvature-form pairs
 PAIR_MIX_KEYS = {"direct": "pair_direct", "flat": "pair_flat", "curved": "pair_curved"}
 
 
@@ -81,38 +82,52 @@ def probe_rates(L):
             "source": "measured (sdf_probe_rates)"}
 
 
-def mix_cost(rates, form):
-    """SM-clocks of special-function work per pair of a record form: the
-    probe's measured rate of that form's whole mix, else the sum of the
-    single-operation costs."""
-    k = PAIR_MIX_KEYS[form]
-    if rates.get(k):
-        return 1.0 / rates[k]
-    m = TC_FORM_COST[form][0]
-    return m[0] / rates["sqrt"] + m[1] / rates.get("rcp", rates["sqrt"]) + m[2] / rates["ex2"]
+def single_op_cost(rates, mix):
+    """SM-clocks of special-function work of one pair with `mix` = (sqrt, rcp,
+    exp2) operations: the sum of the single-operation costs."""
+    return mix[0] / rates["sqrt"] + mix[1] / rates.get("rcp", rates["sqrt"]) + mix[2] / rates["ex2"]
 
 
 def pair_ceiling(rates, instr_per_pair):
-    """pairs per SM clock: the lower of the MUFU and the issue ceilings."""
-    mufu = 1.0 / mix_cost(rates, "direct")
+    """FP32-unit loop, pairs per SM clock: the lower of the MUFU ceiling (its
+    3 sqrt + 1 exp2 mix, measured whole, else the single-operation sum) and
+    the issue ceiling."""
+    mufu = rates.get("pair_direct") or 1.0 / single_op_cost(rates, (3, 0, 1))
     issue = rates["fma"] / instr_per_pair
     return min(mufu, issue), mufu, issue
 
 
 # Tensor-core loop, per pair by record form: special-function operations
-# (sqrt, rcp, ex2) and FMA-pipe instructions of the epilogue.
-TC_FORM_COST = {"direct": ((3, 0, 1), 13), "flat": ((2, 1, 1), 14), "curved": ((3, 2, 1), 20)}
+# (sqrt, rcp, ex2) and FP32 operations on the FMA pipe (the products come from
+# the tensor cores).  Direct form: a, b -> rho (MUFU sqrt), the tube distance
+# (MUFU sqrt), the weight's exp2 (MUFU), and d = sqrt(d^2) by two Newton steps
+# on the FMA pipe (8 of its 17 operations, as .f32x2 pairs); the probe does not
+# time this mix whole, so its cost is the sum of the single-operation costs
+# (the mixes it does time equal those sums).  Flat and curved curvature-form
+# pairs keep the scalar epilogue: 11 and 15 FP32 operations, mixes timed whole.
+TC_FORM_COST = {"direct": ((2, 0, 1), 17), "flat": ((2, 1, 1), 11), "curved": ((3, 2, 1), 15)}
+TC_MIX_KEYS = {"flat": "pair_flat", "curved": "pair_curved"}
+
+
+def mix_cost(rates, form):
+    """SM-clocks of special-function work per tensor-core pair of a record
+    form: the probe's measured rate of that form's whole mix where it times
+    one, else the sum of the single-operation costs."""
+    k = TC_MIX_KEYS.get(form)
+    if k and rates.get(k):
+        return 1.0 / rates[k]
+    return single_op_cost(rates, TC_FORM_COST[form][0])
 
 
 def tc_pair_ceiling(rates, counts):
     """pairs per SM clock of the tensor-core loop over a cloud with `counts`
     points of each record form (pairs weighted by form): the lower of the
-    MUFU and the issue ceilings."""
+    MUFU and the FMA-pipe ceilings."""
     total = sum(counts.values())
     mufu_clk = sum(c * mix_cost(rates, f) for f, c in counts.items())
-    issue_clk = sum(c * TC_FORM_COST[f][1] / rates["fma"] for f, c in counts.items())
-    mufu, issue = total / mufu_clk, total / issue_clk
-    return min(mufu, issue), mufu, issue
+    fma_clk = sum(c * TC_FORM_COST[f][1] / rates["fma"] for f, c in counts.items())
+    mufu, fma = total / mufu_clk, total / fma_clk
+    return min(mufu, fma), mufu, fma
 FALLBACK_MAX_SM_MHZ = 2032.0
 
 
@@ -183,12 +198,16 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def kernel_source_sha() -> str:
-    """Hash of the pair loop's sources with comments and blank space removed,
-    so that a comment-only edit keeps a committed capture valid."""
+TC_SOURCES = ("query_tc.cu", "tc_common.cuh", "query_common.cuh", "device_common.cuh", "internal.h")
+RADIUS_SOURCES = ("radius.cu", "sphere_index.h", "query_common.cuh", "device_common.cuh", "internal.h")
+
+
+def kernel_source_sha(files=TC_SOURCES) -> str:
+    """Hash of a kernel's sources with comments and blank space removed, so
+    that a comment-only edit keeps a committed capture valid."""
     import re
     h = hashlib.sha256()
-    for f in ("query_tc.cu", "tc_common.cuh", "query_common.cuh", "device_common.cuh", "internal.h"):
+    for f in files:
         with open(os.path.join(ROOT, "paper_2607_16946_b300", "csrc", f), encoding="utf-8") as fh:
             src = fh.read()
         src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
@@ -197,19 +216,41 @@ def kernel_source_sha() -> str:
     return h.hexdigest()[:16]
 
 
+def _committed_capture(name, files):
+    """A committed ncu summary (profiles/<name>) if it was taken on the
+    current source of the kernel it describes; else None."""
+    try:
+        with open(os.path.join(ROOT, "profiles", name)) as fh:
+            d = json.load(fh)
+    except (OSError, ValueError):
+        return None
+    return d if isinstance(d, dict) and d.get("kernel_sha") == kernel_source_sha(files) else None
+
+
 def committed_traffic():
     """dram bytes per step of the tensor-core pair loop (its launches of one
     query call) from the committed ncu summary, if it was taken on the
     current kernel source; else None."""
-    path = os.path.join(ROOT, "profiles", "fwd_tc_dense_grid_traffic.json")
-    try:
-        with open(path) as fh:
-            d = json.load(fh)
-    except (OSError, ValueError):
+    d = _committed_capture("fwd_tc_dense_grid_traffic.json", TC_SOURCES)
+    return d.get("dram_bytes_per_step") if d else None
+
+
+def radius_issue_roofline(step_s, sms, fmax_mhz):
+    """Issue-slot roofline of the radius-limited query on the 2^21-point
+    workload: the warp-instructions ncu counted for one query call (both
+    kernels), over the measured time of a call, against 4 warp-instructions
+    per SM per clock.  None without a capture of the current source."""
+    d = _committed_capture("radius_large_cloud_counts.json", RADIUS_SOURCES)
+    if not d or not step_s:
         return None
-    if d.get("kernel_sha") != kernel_source_sha():
-        return None
-    return d.get("dram_bytes_per_step")
+    achieved = d["warp_instructions_per_call"] / step_s / 1e9
+    peak = 4 * sms * fmax_mhz * 1e6 / 1e9
+    return {"bound": "issue", "kernel": "k_radius_query + k_radius_fallback", "achieved": achieved,
+            "peak": peak, "unit": "G warp-instructions/s", "frac": achieved / peak,
+            "traffic": d.get("dram_bytes_per_call"),
+            "peak_basis": f"{sms} SMs x {fmax_mhz:.0f} MHz x 4 warp-instructions per clock; "
+                          f"{d['warp_instructions_per_call']:.4g} warp-instructions per call counted by ncu "
+                          f"on this workload"}
 
 
 def _timed_oracle_sample(cl, rng, threads, target_s: float, chunk: int = 2048, max_chunks: int = 64):
@@ -346,12 +387,19 @@ def run_served(args, dev, pair_rate_gps: float, policy: int = 0, clouds_np=None,
                         f"{'FP32 (tensor engine)' if precision == 0 else 'F16X2 packed-half weights, FP32 sums'}"}
 
 
-# Algorithmic issue slots per pair of the other pair loops (direct torus form,
-# counted from their arithmetic): the gradient term is 54 FP32 (distance,
-# torus, grad g, weight, 13 accumulations) + 4 MUFU; the parameter-backward
-# term is 47 FP32 (distance, weight, torus, 8 record derivatives) + 4 MUFU.
-GRAD_INSTR_PER_PAIR = 58
-BWD_INSTR_PER_PAIR = 51
+# Algorithmic FP32 work per pair of the other pair loops (direct torus form,
+# counted from their arithmetic), against the FMA pipe's measured rate (the
+# .f32x2 instructions issue half as often but occupy the pipe for both
+# operations, and the pipe is what binds them): the gradient term is 54 FP32
+# operations (distance, torus, grad g, weight, 13 accumulations) + 4 MUFU; the
+# parameter-backward term is 47 FP32 (distance, weight, torus, 8 record
+# derivatives) + 4 MUFU.  The a-priori per-pair counts of the hot-path plan
+# are reported beside them: the gradient is the forward's 23 FP32 plus about
+# 20 (43), the backward about twice the forward's 23 (46).
+GRAD_FP32_PER_PAIR = 54
+BWD_FP32_PER_PAIR = 47
+GRAD_PLAN_FP32 = 43
+BWD_PLAN_FP32 = 46
 
 
 def _profile_window(L, abi):
@@ -416,12 +464,24 @@ def run_grad_leg(dev, peak_instr_rate, steps: int = 3):
             "fwd_grad_gpairs_s": pairs / fg / 1e9, "bwd_params_gpairs_s": pairs / bw / 1e9,
             "step_ms": (fg + bw) * 1e3 + pre["ms"] / pre["launches"],
             "kernels": prof,
-            "roofline_fwd_grad": {"bound": "alu", "achieved": pairs / fg / 1e9,
-                                  "peak": peak_instr_rate / GRAD_INSTR_PER_PAIR, "unit": UNIT,
-                                  "frac": pairs / fg / 1e9 / (peak_instr_rate / GRAD_INSTR_PER_PAIR)},
-            "roofline_bwd_params": {"bound": "alu", "achieved": pairs / bw / 1e9,
-                                    "peak": peak_instr_rate / BWD_INSTR_PER_PAIR, "unit": UNIT,
-                                    "frac": pairs / bw / 1e9 / (peak_instr_rate / BWD_INSTR_PER_PAIR)}}
+            "roofline_fwd_grad": grad_roofline(pairs / fg / 1e9, peak_instr_rate, GRAD_FP32_PER_PAIR,
+                                               GRAD_PLAN_FP32),
+            "roofline_bwd_params": grad_roofline(pairs / bw / 1e9, peak_instr_rate, BWD_FP32_PER_PAIR,
+                                                 BWD_PLAN_FP32)}
+
+
+def grad_roofline(achieved, fma_rate, counted, plan):
+    """Roofline of a gradient pair loop against the FMA pipe (G FP32
+    operations/s): over the operations counted from its arithmetic, and over
+    the plan's a-priori per-pair count."""
+    peak = fma_rate / counted
+    return {"bound": "alu", "unit_bound": "FMA pipe", "achieved": achieved, "peak": peak, "unit": UNIT,
+            "frac": achieved / peak,
+            "peak_basis": f"FMA pipe {fma_rate:.0f} G FP32 operations/s / {counted} per pair (counted)",
+            "frac_plan_count": achieved / (fma_rate / plan),
+            "plan_count_basis": f"/ {plan} FP32 operations per pair (the plan's "
+                                + ("forward 23 + about 20 for the gradient)" if plan == GRAD_PLAN_FP32
+                                   else "twice the forward's 23)")}
 
 
 def run_trace_leg(dev, steps: int = 2):
@@ -459,13 +519,14 @@ def run_trace_leg(dev, steps: int = 2):
         counts = {"direct": info["n_direct"], "flat": info["n_kappa_flat"],
                   "curved": info["n_kappa"] - info["n_kappa_flat"]}
         rates = probe_rates(L)
-        per_sm_clk, mufu_c, issue_c = tc_pair_ceiling(rates, counts)
+        per_sm_clk, mufu_c, fma_c = tc_pair_ceiling(rates, counts)
         sms = torch.cuda.get_device_properties(dev).multi_processor_count
         peak = sms * FALLBACK_MAX_SM_MHZ * 1e6 * per_sm_clk / 1e9
         achieved = pairs / (prof["fwd_tc"]["ms"] / steps / 1e3) / 1e9
         roof = {"bound": "alu", "kernel": "k_fwd_tc", "achieved": achieved, "peak": peak, "unit": UNIT,
                 "frac": achieved / peak,
-                "peak_basis": f"MUFU ceiling at {FALLBACK_MAX_SM_MHZ:.0f} MHz over the points by form {counts}"}
+                "peak_basis": f"{'MUFU' if mufu_c <= fma_c else 'FMA-pipe'} ceiling at {FALLBACK_MAX_SM_MHZ:.0f} MHz "
+                              f"over the points by form {counts}"}
     return {"workload": "sphere tracing: superquadric N=262144 (e1=0.5, e2=2, axes 1/0.7/0.5, noise 0.003), "
                         "512x512 rays, 48 steps, eps 1e-4, t_max 6, normals at hits; FP32",
             "gpairs_s": pairs / wall / 1e9, "device_gpairs_s": pairs / (dev_ms / 1e3) / 1e9,
@@ -549,6 +610,10 @@ def run_radius_leg(dev, cloud, x, phi, steps: int = 3):
                           "queries": xg.shape[0], "lambda": lam_L, "R_eval": 128.0 / lam_L,
                           "paper_lambda_ms": t_knn_L * 1e3, "kernels": _profile_window(L, _abi),
                           "outputs_finite": bool(torch.isfinite(phiL).all())}
+    kr = out["large_cloud"]["kernels"].get("radius")
+    out["large_cloud"]["roofline"] = radius_issue_roofline(
+        kr["ms"] / kr["launches"] / 1e3 if kr else None, torch.cuda.get_device_properties(dev).multi_processor_count,
+        FALLBACK_MAX_SM_MHZ)
     t, st_, nrm = cL.trace(org, dirs, **kL)
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
@@ -720,6 +785,8 @@ def compact_summary(line: dict) -> dict:
                          "trace_ms_per_image": r(rd["trace"]["ms_per_image"])}
         if "large_cloud" in rd:
             out["radius"]["large_cloud_queries_s"] = r(rd["large_cloud"]["queries_per_s"])
+            if rd["large_cloud"].get("roofline"):
+                out["radius"]["large_cloud_issue_frac"] = r(rd["large_cloud"]["roofline"]["frac"], 3)
     for k in ("served", "served_fifo", "served_f16x2"):
         if k in line:
             out[k] = {"gpairs_s": r(line[k]["value"]), "p50_ms": r(line[k]["p50_ms"]), "p99_ms": r(line[k]["p99_ms"])}
@@ -847,22 +914,18 @@ def run_ours(args, rank, world, local):
             flat_tc, curved = 32 * (flat_tc // 32), 0
         counts = {"direct": info["n_direct"], "flat": flat_tc, "curved": curved}
         kname, kpairs = "k_fwd_tc", q * sum(counts.values())
-        per_sm_clk, mufu_c, issue_c = tc_pair_ceiling(rates, counts)
+        per_sm_clk, mufu_c, fma_c = tc_pair_ceiling(rates, counts)
         kp = prof["fwd_tc"]
         traffic = committed_traffic()
-        single = sum(counts.values()) / sum(
-            c * (m[0] / rates['sqrt'] + m[1] / rates.get('rcp', rates['sqrt']) + m[2] / rates['ex2'])
-            for f, c in counts.items() for m in [TC_FORM_COST[f][0]])
-        nominal = sum(counts.values()) / sum(
-            c * (m[0] / NOMINAL_RATES['sqrt'] + m[1] / NOMINAL_RATES['rcp'] + m[2] / NOMINAL_RATES['ex2'])
-            for f, c in counts.items() for m in [TC_FORM_COST[f][0]])
-        basis = (f"{'MUFU' if mufu_c <= issue_c else 'issue'} ceiling: {sms} SMs x {fmax:.0f} MHz x "
+        nominal = sum(counts.values()) / sum(c * single_op_cost(NOMINAL_RATES, TC_FORM_COST[f][0])
+                                             for f, c in counts.items())
+        basis = (f"{'MUFU' if mufu_c <= fma_c else 'FMA-pipe'} ceiling: {sms} SMs x {fmax:.0f} MHz x "
                  f"{per_sm_clk:.3f} pairs/clk/SM over the points by form {counts}; MUFU per pair "
-                 f"(sqrt, rcp, ex2) = {dict((f, c[0]) for f, c in TC_FORM_COST.items())}, each mix's "
-                 f"rate measured whole by sdf_probe_rates -> {mufu_c:.3f}; other readings: the sum of the "
-                 f"measured single-operation costs {single:.3f}, the nominal 16/16/32 per SM per clock "
-                 f"{nominal:.3f}; issue fma/{dict((f, c[1]) for f, c in TC_FORM_COST.items())} -> {issue_c:.3f} "
-                 f"(unit rates {rates['source']})")
+                 f"(sqrt, rcp, ex2) = {dict((f, c[0]) for f, c in TC_FORM_COST.items())}: direct from the "
+                 f"measured single-operation rates, flat and curved mixes measured whole by sdf_probe_rates "
+                 f"-> {mufu_c:.3f} (nominal 16/16/32 per SM per clock: {nominal:.3f}); FMA pipe "
+                 f"{rates['fma']:.1f}/{dict((f, c[1]) for f, c in TC_FORM_COST.items())} FP32 operations "
+                 f"-> {fma_c:.3f} (unit rates {rates['source']})")
     else:
         kname, kpairs = "k_fwd", pairs_per_step
         per_sm_clk, mufu_c, issue_c = pair_ceiling(rates, INSTR_PER_PAIR)

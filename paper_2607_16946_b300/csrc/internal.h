@@ -58,9 +58,6 @@ namespace ptsdf {
 #ifndef PTSDF_FWD_MINB
 #define PTSDF_FWD_MINB 4
 #endif
-#ifndef PTSDF_TC_SOFTSQRT
-#define PTSDF_TC_SOFTSQRT 1   // direct-form tensor-core epilogue: d on the FMA pipe, .f32x2 arithmetic (0: scalar)
-#endif
 constexpr int kTileRecs = PTSDF_TILE_RECS;   // records per main-loop tile (32 x 64 B = 2 KB)
 constexpr int kRecFloats = 16;
 constexpr int kPreTile = 256;        // points per prepass tile (4 KB)

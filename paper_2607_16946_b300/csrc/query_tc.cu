@@ -247,30 +247,23 @@ struct TcArgs {
 
 __device__ __forceinline__ float sqrt_abs_mufu(float x) { return sqrt_mufu(fabsf(x)); }
 
-// torus distance of one pair from the seven accumulator quantities q0..q6
-// (units of s), by the tile's form
+// torus distance of one curvature-form pair from the accumulator quantities
+// q1..q6 (units of s): h, |y|^2, m0, |kmin|, -kmax, 2 zeta
 template <int FORM>
 __device__ __forceinline__ float g_from_quantities(float q1, float q2, float q3, float q4, float q5, float q6) {
-    if (FORM == kFormDirect) {
-        // q1 h, q2 a, q3 b, q4 R, q5 -sT r, q6 sT
-        const float rho = sqrt_mufu(fmaf(q2, q2, q3 * q3));
-        const float e = rho - q4;
-        return fmaf(q6, sqrt_mufu(fmaf(e, e, q1 * q1)), q5);
+    static_assert(FORM != kFormDirect, "direct-form pairs go through tile_pairs_direct2");
+    const float hh = q1 * q1;
+    float ap;
+    if (FORM == kFormFlat) {
+        ap = 0.5f * q3;
     } else {
-        // q1 h, q2 |y|^2, q3 m0, q4 |kmin|, q5 -kmax, q6 2 zeta
-        const float hh = q1 * q1;
-        float ap;
-        if (FORM == kFormFlat) {
-            ap = 0.5f * q3;
-        } else {
-            const float m = fmaf(q4, q2 - hh, q3);
-            const float s1 = sqrt_mufu(fmaxf(fmaf(q4, m, 1.f), 0.f));
-            ap = m * rcp_mufu(1.f + s1);
-        }
-        const float Np = fmaf(q5, fmaf(ap, ap, hh), q6 * ap);
-        const float s2 = sqrt_mufu(fmaxf(fmaf(q5, Np, 1.f), 0.f));
-        return Np * rcp_mufu(1.f + s2);
+        const float m = fmaf(q4, q2 - hh, q3);
+        const float s1 = sqrt_mufu(fmaxf(fmaf(q4, m, 1.f), 0.f));
+        ap = m * rcp_mufu(1.f + s1);
     }
+    const float Np = fmaf(q5, fmaf(ap, ap, hh), q6 * ap);
+    const float s2 = sqrt_mufu(fmaxf(fmaf(q5, Np, 1.f), 0.f));
+    return Np * rcp_mufu(1.f + s2);
 }
 
 // The direct form's share, two points at a time: the FP32 arithmetic of a
@@ -278,9 +271,12 @@ __device__ __forceinline__ float g_from_quantities(float q1, float q2, float q3,
 // the weight) on the FMA pipe (sqrt2_newton, two Newton steps: 4.6e-6
 // relative), so that the special-function unit does 2 sqrt + 1 exp2 per pair
 // (20 of its cycles per 32 pairs instead of 28).  On the dense grid this
-// runs 3.8% faster than the scalar epilogue with three MUFU square roots
+// runs 3.8% faster than a scalar epilogue with three MUFU square roots
 // (1,091 against 1,051 Gpairs/s per step); a third Newton step, or fitted
-// constants for the two, cost more issue slots or registers than they save.
+// constants for the two, cost more issue slots or registers than they save,
+// and so did keeping the MUFU root for one pair in two or in four (1,072 and
+// 1,064).  FMA-pipe work per pair: 17 FP32 operations (8 of them the square
+// root); ALU: the clamp and the integer estimate.
 template <bool WEIGHTED>
 __device__ __forceinline__ void tile_pairs_direct2(const float (&v)[kVals], float Ls, float A0, float& W, float& S) {
     const f32x2 NLs = f2_pack(-Ls, -Ls), A0v = f2_pack(A0, A0);
@@ -312,24 +308,22 @@ __device__ __forceinline__ void tile_pairs_direct2(const float (&v)[kVals], floa
 // scaled constants of g).
 template <int FORM, bool WEIGHTED = false>
 __device__ __forceinline__ void tile_pairs(const float (&v)[kVals], float Ls, float A0, float& W, float& S) {
-#if PTSDF_TC_SOFTSQRT
-    if (FORM == kFormDirect) {
+    if constexpr (FORM == kFormDirect) {
         tile_pairs_direct2<WEIGHTED>(v, Ls, A0, W, S);
-        return;
-    }
-#endif
-    float tw = 0.f, ts = 0.f;
+    } else {
+        float tw = 0.f, ts = 0.f;
 #pragma unroll
-    for (int i = 0; i < kPtsPerWarp; ++i) {
-        const float g = g_from_quantities<FORM>(v[8 + i], v[16 + i], v[24 + i], v[32 + i], v[40 + i], v[48 + i]);
-        // |d^2|: the products may round a zero distance slightly negative
-        const float d = sqrt_abs_mufu(v[i]);
-        const float w = ex2_mufu(fmaf(-Ls, d, A0));
-        tw = WEIGHTED ? fmaf(w, fabsf(v[48 + i]), tw) : tw + w;
-        ts = fmaf(w, g, ts);
+        for (int i = 0; i < kPtsPerWarp; ++i) {
+            const float g = g_from_quantities<FORM>(v[8 + i], v[16 + i], v[24 + i], v[32 + i], v[40 + i], v[48 + i]);
+            // |d^2|: the products may round a zero distance slightly negative
+            const float d = sqrt_abs_mufu(v[i]);
+            const float w = ex2_mufu(fmaf(-Ls, d, A0));
+            tw = WEIGHTED ? fmaf(w, fabsf(v[48 + i]), tw) : tw + w;
+            ts = fmaf(w, g, ts);
+        }
+        W += tw;
+        S += ts;
     }
-    W += tw;
-    S += ts;
 }
 
 // The same share from the FP32 records (the formula of the tile's form, in

@@ -7,7 +7,8 @@
 Builds the dense-grid cloud (ring torus, N = 100,000; or, with --cloud
 superquadric, the sphere-tracing cloud of N = 262,144 curvature-form points)
 and evaluates an evenly strided subset of Q nodes of the 256^3 grid over
-[-1.6, 1.6]^3 with sdf_query (or the gradient and backward calls), W times
+[-1.6, 1.6]^3 (--grid-res, --extent) with sdf_query (or the gradient,
+Laplacian and backward calls), W times
 untimed and then K times, printing the device time of each call.  Used to give ncu a short, self-terminating run of the
 same kernels the benchmark times.  --mode probe prints, for each of the
 eight probes of sdf_probe_rates, the four readings of sdf_probe_timing (one
@@ -31,11 +32,15 @@ def main():
     ap.add_argument("--warmup", type=int, default=1)
     ap.add_argument("--points", type=int, default=None, help="default 100,000 (torus) / 262,144 (superquadric)")
     ap.add_argument("--cloud", choices=["torus", "superquadric"], default="torus")
-    ap.add_argument("--mode", choices=["query", "grad", "backward", "radius", "probe", "sspd", "shc"],
+    ap.add_argument("--seed", type=int, default=None, help="cloud seed (default 1002 torus, 1003 superquadric)")
+    ap.add_argument("--grid-res", type=int, default=256, help="query grid nodes per axis")
+    ap.add_argument("--extent", type=float, default=1.6, help="query grid over [-extent, extent]^3")
+    ap.add_argument("--mode", choices=["query", "grad", "backward", "laplacian", "radius", "probe", "sspd", "shc"],
                     default="query",
                     help="query: sdf_query; grad: sdf_query_grad; backward: sdf_query_grad then "
-                         "sdf_backward_params (each call); radius: sdf_query with SDF_LAMBDA_RADIUS and "
-                         "lambda = 10^3 / D; sspd / shc: sdf_query with the SSPD / SHC baseline")
+                         "sdf_backward_params (each call); laplacian: sdf_query_laplacian; radius: sdf_query "
+                         "with SDF_LAMBDA_RADIUS and lambda = 10^3 / D; sspd / shc: sdf_query with the SSPD / "
+                         "SHC baseline")
     ap.add_argument("--precision", type=int, default=0, help="sdf_precision of the query")
     ap.add_argument("--engine", type=int, default=0, help="sdf_engine of the query (0 auto, 1 ALU, 2 tensor)")
     args = ap.parse_args()
@@ -63,13 +68,13 @@ def main():
 
     if args.cloud == "torus":
         args.points = args.points or 100_000
-        p, n, a = synth.ring_torus(args.points, 1002, R=1.0, r=0.35, noise=0.005, jitter_deg=2.0)
+        p, n, a = synth.ring_torus(args.points, args.seed or 1002, R=1.0, r=0.35, noise=0.005, jitter_deg=2.0)
     else:
         args.points = args.points or 262_144
-        p, n, a = synth.superquadric(args.points, 1003)
+        p, n, a = synth.superquadric(args.points, args.seed or 1003)
     cloud = ptsdf.Cloud(p, n, a)
-    res = 256
-    g = torch.linspace(-1.6, 1.6, res, device="cuda", dtype=torch.float64)
+    res = args.grid_res
+    g = torch.linspace(-args.extent, args.extent, res, device="cuda", dtype=torch.float64)
     zz, yy, xx = torch.meshgrid(g, g, g, indexing="ij")
     x = torch.stack([xx.reshape(-1), yy.reshape(-1), zz.reshape(-1)], 1).to(torch.float32)
     stride = max(1, x.shape[0] // args.queries)
@@ -86,6 +91,8 @@ def main():
             cloud.query(x, out=phi, lambda_mode=ptsdf.SDF_LAMBDA_RADIUS, fixed_lambda=lam)
         elif args.mode in ("sspd", "shc"):
             cloud.query(x, out=phi, formula=ptsdf.SDF_FORMULA_SSPD if args.mode == "sspd" else ptsdf.SDF_FORMULA_SHC)
+        elif args.mode == "laplacian":
+            phi, _, _ = cloud.query_laplacian(x)
         else:
             phi, _, saved = cloud.query_grad(x)
             if args.mode == "backward":

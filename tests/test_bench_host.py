@@ -1,7 +1,7 @@
-"""Host-side arithmetic of bench.py, on the CPU: the form-weighted MUFU
-ceiling the tensor-core loop's roofline is reported against, its fallback to
-single-operation costs, and the key that ties the committed DRAM-traffic
-capture to the kernel source it was taken on."""
+"""Host-side arithmetic of bench.py, on the CPU: the form-weighted MUFU and
+FMA-pipe ceilings the tensor-core loop's roofline is reported against, the
+single-operation costs, the gradient loops' two counts, and the key that ties
+the committed DRAM-traffic capture to the kernel source it was taken on."""
 import json
 import os
 import shutil
@@ -15,12 +15,20 @@ RATES = {"sqrt": 16.0, "rsqrt": 16.0, "ex2": 32.0, "fma": 124.1, "rcp": 16.0,
          "pair_direct": 4.571, "pair_flat": 4.571, "pair_curved": 2.909}
 
 
-def test_single_form_ceiling_is_its_measured_mix():
-    for form, key in bench.PAIR_MIX_KEYS.items():
-        best, mufu, issue = bench.tc_pair_ceiling(RATES, {form: 1000})
-        assert mufu == pytest.approx(RATES[key])
-        assert issue == pytest.approx(RATES["fma"] / bench.TC_FORM_COST[form][1])
-        assert best == min(mufu, issue)
+def test_single_form_ceiling():
+    """Curvature-form pairs: the probe's whole mix; direct pairs (|x - p| on
+    the FMA pipe): 2 sqrt + 1 exp2 from the single-operation rates."""
+    for form in ("direct", "flat", "curved"):
+        best, mufu, fma = bench.tc_pair_ceiling(RATES, {form: 1000})
+        if form in bench.TC_MIX_KEYS:
+            assert mufu == pytest.approx(RATES[bench.TC_MIX_KEYS[form]])
+        else:
+            assert mufu == pytest.approx(1.0 / (2 / 16.0 + 1 / 32.0))        # 6.4 pairs per SM per clock
+        assert fma == pytest.approx(RATES["fma"] / bench.TC_FORM_COST[form][1])
+        assert best == min(mufu, fma)
+    # the direct form is bound by its special-function unit, not the FMA pipe
+    best, mufu, fma = bench.tc_pair_ceiling(RATES, {"direct": 1})
+    assert mufu < fma and best == mufu
 
 
 def test_mixed_forms_share_the_clocks():
@@ -29,25 +37,28 @@ def test_mixed_forms_share_the_clocks():
     unchanged when every count doubles, lower with more curved points."""
     counts = {"direct": 97904, "curved": 2096}
     _, mufu, _ = bench.tc_pair_ceiling(RATES, counts)
-    assert RATES["pair_curved"] < mufu < RATES["pair_direct"]
-    assert mufu == pytest.approx(100000 / (97904 / 4.571 + 2096 / 2.909))
+    assert RATES["pair_curved"] < mufu < 6.4
+    assert mufu == pytest.approx(100000 / (97904 / 6.4 + 2096 / 2.909))
     assert bench.tc_pair_ceiling(RATES, {k: 2 * v for k, v in counts.items()})[1] == pytest.approx(mufu)
     assert bench.tc_pair_ceiling(RATES, {"direct": 97904, "curved": 20960})[1] < mufu
 
 
 def test_unmeasured_mix_falls_back_to_single_operations():
     single = {k: v for k, v in RATES.items() if not k.startswith("pair_")}
-    assert bench.mix_cost(single, "direct") == pytest.approx(3 / 16.0 + 1 / 32.0)
+    assert bench.mix_cost(single, "direct") == pytest.approx(2 / 16.0 + 1 / 32.0)
     assert bench.mix_cost(single, "curved") == pytest.approx(3 / 16.0 + 2 / 16.0 + 1 / 32.0)
     # with the measured rates the mixes are additive: the single-operation sums
     # equal the measured mixes
-    assert 1 / bench.mix_cost(single, "direct") == pytest.approx(RATES["pair_direct"], rel=1e-3)
+    assert 1 / bench.single_op_cost(single, (3, 0, 1)) == pytest.approx(RATES["pair_direct"], rel=1e-3)
     assert 1 / bench.mix_cost(single, "curved") == pytest.approx(RATES["pair_curved"], rel=1e-3)
 
 
 def test_fp32_unit_loop_ceiling():
+    """The FP32-unit loop keeps three MUFU square roots per pair."""
     best, mufu, issue = bench.pair_ceiling(RATES, bench.INSTR_PER_PAIR)
     assert mufu == pytest.approx(RATES["pair_direct"])
+    single = {k: v for k, v in RATES.items() if not k.startswith("pair_")}
+    assert bench.pair_ceiling(single, bench.INSTR_PER_PAIR)[1] == pytest.approx(1 / (3 / 16.0 + 1 / 32.0))
     assert issue == pytest.approx(RATES["fma"] / 29)
     assert best == min(mufu, issue)
 
@@ -103,3 +114,31 @@ def test_compact_summary_comes_from_the_legs():
     assert s["sspd"] == {"gpairs_s": 2500.0, "err_max": 1.2e-7, "frac": 0.75}
     assert s["served"]["p99_ms"] == 2500.0 and s["cpu_oracle_gpairs_s"] == 0.65
     assert "note" not in s
+
+
+def test_gradient_rooflines_carry_both_counts():
+    r = bench.grad_roofline(500.0, 37000.0, bench.GRAD_FP32_PER_PAIR, bench.GRAD_PLAN_FP32)
+    assert r["frac"] == pytest.approx(500.0 / (37000.0 / 54))
+    assert r["frac_plan_count"] == pytest.approx(500.0 / (37000.0 / 43))
+    assert r["frac_plan_count"] < r["frac"]
+    b = bench.grad_roofline(500.0, 37000.0, bench.BWD_FP32_PER_PAIR, bench.BWD_PLAN_FP32)
+    assert b["frac_plan_count"] == pytest.approx(500.0 / (37000.0 / 46)) and "twice" in b["plan_count_basis"]
+
+
+def test_radius_roofline_needs_a_capture_of_the_current_source(tmp_path, monkeypatch):
+    src = os.path.join(bench.ROOT, "paper_2607_16946_b300", "csrc")
+    dst = tmp_path / "paper_2607_16946_b300" / "csrc"
+    dst.mkdir(parents=True)
+    for f in set(bench.RADIUS_SOURCES):
+        shutil.copy(os.path.join(src, f), dst / f)
+    (tmp_path / "profiles").mkdir()
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.radius_issue_roofline(0.1, 148, 2032.0) is None
+    path = tmp_path / "profiles" / "radius_large_cloud_counts.json"
+    path.write_text(json.dumps({"kernel_sha": bench.kernel_source_sha(bench.RADIUS_SOURCES),
+                                "warp_instructions_per_call": 6.0e10, "dram_bytes_per_call": 1.0e9}))
+    r = bench.radius_issue_roofline(0.1, 148, 2032.0)
+    assert r["achieved"] == pytest.approx(600.0) and r["peak"] == pytest.approx(4 * 148 * 2.032)
+    assert r["frac"] == pytest.approx(600.0 / (4 * 148 * 2.032)) and r["traffic"] == 1.0e9
+    path.write_text(json.dumps({"kernel_sha": "0" * 16, "warp_instructions_per_call": 6.0e10}))
+    assert bench.radius_issue_roofline(0.1, 148, 2032.0) is None
