@@ -370,11 +370,18 @@ def run_served(args, dev, pair_rate_gps: float, policy: int = 0, clouds_np=None,
     span_s = (max(s["done_ns"] for s in stats) - min(s["arrive_ns"] for s in stats)) / 1e9
     total_pairs = float(sum(r["pairs"] for r in reqs))
     finite = all(bool(torch.isfinite(o).all()) for o in outs)
+    # each request's time alone at the measured pair rate (at least 1 ms): the
+    # slowdown says how much sharing the device delayed a request for its size,
+    # and the largest request's time alone is a floor under the latency tail
+    alone = np.array([max(r["pairs"] / (pair_rate_gps * 1e9) * 1e3, 1.0) for r in reqs])
+    slow = lat / alone
     return {"value": total_pairs / span_s / 1e9, "unit": UNIT, "requests": len(reqs),
             "queries_per_s": float(sum(r["q"] for r in reqs)) / span_s,
             "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
             "queue_p50_ms": float(np.percentile(queue, 50)), "queue_p99_ms": float(np.percentile(queue, 99)),
             "service_p50_ms": float(np.percentile(service, 50)), "service_p99_ms": float(np.percentile(service, 99)),
+            "slowdown_p50": float(np.percentile(slow, 50)), "slowdown_p99": float(np.percentile(slow, 99)),
+            "largest_request_alone_ms": float(alone.max()),
             "offered_load": args.serve_load, "arrival_rate_per_s": rate, "mean_pairs_per_request": mean_pairs,
             "clouds": len(clouds), "points_total": int(sum(ns)), "outputs_finite": finite,
             "server": {"max_inflight": 8, "n_streams": 4, "mem_budget_bytes": 16 << 30,
@@ -410,6 +417,12 @@ def _profile_window(L, abi):
         if cnt.value:
             out[name] = {"launches": cnt.value, "ms": ms.value}
     return out
+
+
+# FP32 operations per pair of the baselines' loop: x - p (3), d^2 (3), <x - p, n> (3), then SSPD
+# the exponent, W and S (3); SHC d = d^2 / sqrt(d^2), the exponent, lambda d + 1, 1 / d^3 (2)
+# and the dipole term into S (3)
+PLANE_FP32_PER_PAIR = {"sspd": 12, "shc": 17}
 
 
 def run_grad_leg(dev, peak_instr_rate, steps: int = 3):
@@ -736,14 +749,19 @@ def run_mixed_leg(dev, cloud, x, phi, points, normals, params, steps: int = 2):
         if mask is not None:
             out[name]["compared"] = f"{int(mask.sum())} of {mask.size} nodes (oracle condition number <= 1e3)"
         if "plane" in prof:
-            # the baselines' pair loop: 1 sqrt (SSPD) or rsqrt (SHC) + 1 exp2 per pair on the XU pipe
+            # the baselines' pair loop: 1 sqrt (SSPD) or rsqrt (SHC) + 1 exp2 per pair
+            # on the XU pipe, and PLANE_FP32_PER_PAIR operations on the FMA pipe
             mufu = 1.0 / (1.0 / rates["sqrt"] + 1.0 / rates["ex2"])
-            peak = sms * FALLBACK_MAX_SM_MHZ * 1e6 * mufu / 1e9
+            fma = rates["fma"] / PLANE_FP32_PER_PAIR[name]
+            per_clk = min(mufu, fma)
+            peak = sms * FALLBACK_MAX_SM_MHZ * 1e6 * per_clk / 1e9
             ach = x.shape[0] * N_POINTS / (prof["plane"]["ms"] / steps / 1e3) / 1e9
             out[name]["roofline"] = {"bound": "alu", "kernel": "k_fwd_plane", "achieved": ach, "peak": peak,
                                      "unit": UNIT, "frac": ach / peak,
-                                     "peak_basis": f"XU: 1 sqrt/rsqrt + 1 ex2 per pair at the measured rates = "
-                                                   f"{mufu:.2f} pairs/clk/SM x {sms} SMs x "
+                                     "peak_basis": f"{'XU' if mufu <= fma else 'FMA pipe'}: XU 1 sqrt/rsqrt + 1 ex2 "
+                                                   f"per pair at the measured rates = {mufu:.2f} pairs/clk/SM, FMA "
+                                                   f"pipe {rates['fma']:.1f} / {PLANE_FP32_PER_PAIR[name]} FP32 "
+                                                   f"operations = {fma:.2f}; x {sms} SMs x "
                                                    f"{FALLBACK_MAX_SM_MHZ:.0f} MHz"}
     wcloud.close()
     out["note"] = ("fp32_tensor: products on the tensor cores (split f16, FP32 accumulate), pairs finished in "
@@ -789,7 +807,8 @@ def compact_summary(line: dict) -> dict:
                 out["radius"]["large_cloud_issue_frac"] = r(rd["large_cloud"]["roofline"]["frac"], 3)
     for k in ("served", "served_fifo", "served_f16x2"):
         if k in line:
-            out[k] = {"gpairs_s": r(line[k]["value"]), "p50_ms": r(line[k]["p50_ms"]), "p99_ms": r(line[k]["p99_ms"])}
+            out[k] = {"gpairs_s": r(line[k]["value"]), "p50_ms": r(line[k]["p50_ms"]), "p99_ms": r(line[k]["p99_ms"]),
+                      "slowdown_p99": r(line[k].get("slowdown_p99"), 3)}
     if "cpu_baseline" in line:
         out["cpu_oracle_gpairs_s"] = r(line["cpu_baseline"]["value"])
     return out
