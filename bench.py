@@ -283,6 +283,8 @@ def cpu_baseline(points, normals, params, target_s: float = 12.0):
 
 SERVE_SEED = 1005
 SERVE_SPLIT_GPAIRS = 100        # requests above 1e11 (query, point) pairs run as interleaved query chunks
+SERVE_EXPRESS_GPAIRS = 10.0     # requests of at most 1e10 pairs (about three in four) on high-priority streams
+SERVE_STREAMS = 8               # four express and four bulk streams for the eight slots
 
 
 def make_serving_clouds(n_clouds: int, seed: int):
@@ -335,8 +337,8 @@ def run_served(args, dev, pair_rate_gps: float, policy: int = 0, clouds_np=None,
     mean_pairs = float(np.mean([r["pairs"] for r in reqs]))
     rate = args.serve_load * pair_rate_gps * 1e9 / mean_pairs          # requests per second
     arrivals = np.cumsum(rng.exponential(1.0 / rate, size=len(reqs)))
-    srv = S.Server(mem_budget_bytes=16 << 30, max_inflight=8, n_streams=4, policy=policy, starve_ms=2000,
-                   split_gpairs=SERVE_SPLIT_GPAIRS)
+    srv = S.Server(mem_budget_bytes=16 << 30, max_inflight=8, n_streams=args.serve_streams, policy=policy,
+                   starve_ms=2000, split_gpairs=SERVE_SPLIT_GPAIRS, express_gpairs=args.serve_express)
     ids = [srv.register(c) for c in clouds]
     outs = [torch.empty(r["q"], device=dev) for r in reqs]
     torch.cuda.synchronize(dev)
@@ -382,9 +384,14 @@ def run_served(args, dev, pair_rate_gps: float, policy: int = 0, clouds_np=None,
             "service_p50_ms": float(np.percentile(service, 50)), "service_p99_ms": float(np.percentile(service, 99)),
             "slowdown_p50": float(np.percentile(slow, 50)), "slowdown_p99": float(np.percentile(slow, 99)),
             "largest_request_alone_ms": float(alone.max()),
+            # the three requests of largest slowdown: pairs, latency, queueing, service (ms), chunks
+            "worst_slowdown": [{"pairs": float(reqs[i]["pairs"]), "latency_ms": float(lat[i]),
+                                "queue_ms": float(queue[i]), "service_ms": float(service[i]),
+                                "chunks": int(stats[i]["chunks"])} for i in np.argsort(-slow)[:3]],
             "offered_load": args.serve_load, "arrival_rate_per_s": rate, "mean_pairs_per_request": mean_pairs,
             "clouds": len(clouds), "points_total": int(sum(ns)), "outputs_finite": finite,
-            "server": {"max_inflight": 8, "n_streams": 4, "mem_budget_bytes": 16 << 30,
+            "server": {"max_inflight": 8, "n_streams": args.serve_streams, "mem_budget_bytes": 16 << 30,
+                       "express_pairs": args.serve_express * 1e9,
                        "policy": "smallest_first (starve 2 s)" if policy else "fifo",
                        "split_pairs": SERVE_SPLIT_GPAIRS * 1e9,
                        "requests_split": sum(1 for st in stats if st["chunks"] > 1)},
@@ -1009,6 +1016,9 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true", help="omit the CPU oracle leg")
     ap.add_argument("--serve-requests", type=int, default=300, help="requests of the served leg (0: skip)")
+    ap.add_argument("--serve-streams", type=int, default=SERVE_STREAMS, help="CUDA streams of the served leg")
+    ap.add_argument("--serve-express", type=float, default=SERVE_EXPRESS_GPAIRS,
+                    help="requests of at most this many Gpairs run on high-priority streams (0: one priority)")
     ap.add_argument("--no-extra-legs", action="store_true", help="omit the gradient and tracing legs")
     ap.add_argument("--serve-clouds", type=int, default=32)
     ap.add_argument("--serve-variants", default="fp32,fifo,f16x2",

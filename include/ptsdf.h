@@ -335,8 +335,9 @@ PTSDF_API sdf_status sdf_query_noalloc(sdf_cloud cloud, const float* d_x, int64_
  * SDF: query batches of uneven size, sphere-tracing steps, offsets and
  * Booleans).  A scheduler thread admits queued requests (in arrival order, or
  * smallest first) when a slot (max_inflight) and enough of the memory budget are free and
- * launches each at once on one of n_streams streams, so work that arrives
- * while other requests run overlaps with them on the device.  A request's
+ * launches each at once on one of n_streams streams (the least loaded of its
+ * priority class), so work that arrives while other requests run overlaps
+ * with them on the device.  A request's
  * result depends only on its own inputs, cloud and options: it is the same
  * alone and in a mix.
  * ------------------------------------------------------------------------- */
@@ -361,6 +362,16 @@ typedef struct {
                                    never split).  A chunk keeps at least 2 x 4 x SMs x 512 queries,
                                    so every query's result is exactly that of the unsplit request;
                                    GRAD requests are not split. */
+    float express_gpairs;       /* > 0: requests (and chunks) of at most express_gpairs x 1e9 pairs
+                                   run on the first half of the streams, created at the device's
+                                   highest stream priority, the others on the second half at the
+                                   lowest, so the block scheduler starts a small request's blocks
+                                   before the queued blocks of large ones; and the larger requests
+                                   hold at most max_inflight - max_inflight / 2 slots at once, so
+                                   a small one never waits for a slot behind them.  0: one
+                                   priority, no reservation.  Either way a request goes to the
+                                   stream of its class with the least work in flight.  Needs
+                                   n_streams >= 2 when > 0. */
 } sdf_serve_config;
 
 typedef enum {

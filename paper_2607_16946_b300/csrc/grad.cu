@@ -27,6 +27,19 @@ using namespace qk;
 namespace {
 
 constexpr int kGradQPerCta = kConsumerWarps * 32;   // one query per consumer thread
+// The Laplacian's 28 sums take 112 registers, so one CTA fills an SM's
+// registers; it runs more consumer warps than the gradient (whose two CTAs of
+// eight fit at 96): at most four warps of 3,584 registers per 16K sub-partition.
+#ifndef PTSDF_LAP_WARPS
+#define PTSDF_LAP_WARPS 12
+#endif
+constexpr int kLapWarps = PTSDF_LAP_WARPS;
+static_assert(kLapWarps + 1 <= 16, "four warps per sub-partition at 112 registers");
+template <bool LAP>
+struct GradGeom {
+    static constexpr int warps = LAP ? kLapWarps : kConsumerWarps;   // consumer warps
+    static constexpr int threads = (warps + 1) * 32;                 // + producer warp
+};
 constexpr float kTiny = 1e-30f;                      // zero-length vectors get a zero unit vector
 
 // accumulators: the 13 of the gradient, then the 15 more of the Laplacian
@@ -386,7 +399,7 @@ __device__ __forceinline__ void finalize(const GradArgs& ga, int64_t qi, float x
 }
 
 template <bool LAP, bool WEIGHTED>
-__global__ void __launch_bounds__(kThreads) __maxnreg__(LAP ? 112 : 96) k_fwd_grad(const float4* __restrict__ rec, int64_t n_direct,
+__global__ void __launch_bounds__(GradGeom<LAP>::threads) __maxnreg__(LAP ? 112 : 96) k_fwd_grad(const float4* __restrict__ rec, int64_t n_direct,
                                                        int64_t n_kappa, int64_t tiles_direct, int64_t tiles_total,
                                                        int64_t tiles_per_chunk, GradArgs ga, int32_t* status) {
     extern __shared__ __align__(128) char smem[];
@@ -398,14 +411,15 @@ __global__ void __launch_bounds__(kThreads) __maxnreg__(LAP ? 112 : 96) k_fwd_gr
     const int64_t t0 = (int64_t)chunk * tiles_per_chunk;
     const int64_t t1 = t0 + tiles_per_chunk < tiles_total ? t0 + tiles_per_chunk : tiles_total;
     const int64_t nt = t1 > t0 ? t1 - t0 : 0;
-    if (threadIdx.x == 0) ring.init(kConsumerWarps);
+    constexpr int kWarps = GradGeom<LAP>::warps;
+    if (threadIdx.x == 0) ring.init(kWarps);
     __syncthreads();
-    if (warp == kConsumerWarps) {
+    if (warp == kWarps) {
         if (lane == 0)
             ring.produce(buf, reinterpret_cast<const char*>(rec + t0 * kTileRecs * 4), nt, kTileBytes, status);
         return;
     }
-    const int64_t qi = (int64_t)blockIdx.x * kGradQPerCta + threadIdx.x;
+    const int64_t qi = (int64_t)blockIdx.x * (kWarps * 32) + threadIdx.x;
     const int64_t qq = qi < a.q ? qi : a.q - 1;
     const float x = a.x[3 * qq], y = a.x[3 * qq + 1], z = a.x[3 * qq + 2];
     const QueryLam ql = query_lambda(a, ga.pre, qq);
@@ -492,7 +506,7 @@ sdf_status launch_query_grad(const Cloud& c, const float* d_x, int64_t q, float*
                              float* d_saved, const sdf_query_opts& o, cudaStream_t st, float* d_lap) {
     const bool lap = d_lap != nullptr;
     const int kAcc = lap ? NAcc<true>::value : NAcc<false>::value;
-    const Plan p = make_plan(c, q, o.split_n, kGradQPerCta);
+    const Plan p = make_plan(c, q, o.split_n, lap ? GradGeom<true>::warps * 32 : kGradQPerCta);
     GradArgs ga;
     QueryArgs& a = ga.a;
     a.x = d_x;
@@ -555,9 +569,9 @@ sdf_status launch_query_grad(const Cloud& c, const float* d_x, int64_t q, float*
         auto kern = lap ? (c.weighted ? k_fwd_grad<true, true> : k_fwd_grad<true, false>)
                         : (c.weighted ? k_fwd_grad<false, true> : k_fwd_grad<false, false>);
         // the gradient takes the pair-interleaved copy, the Laplacian the plain records
-        kern<<<grid, kThreads, kStages * kTileBytes, st>>>(lap ? c.rec : c.rec2, c.n_direct, c.n_kappa, c.tiles_direct,
-                                                          c.tiles_direct + c.tiles_kappa, p.tiles_per_chunk, ga,
-                                                          c.status);
+        kern<<<grid, lap ? GradGeom<true>::threads : GradGeom<false>::threads, kStages * kTileBytes, st>>>(
+            lap ? c.rec : c.rec2, c.n_direct, c.n_kappa, c.tiles_direct, c.tiles_direct + c.tiles_kappa,
+            p.tiles_per_chunk, ga, c.status);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess && p.split > 1) {

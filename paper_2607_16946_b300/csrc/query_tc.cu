@@ -86,7 +86,10 @@ constexpr int kTcN = kTcQuant * kTileRecs;            // 224 (MMA N)
 constexpr uint32_t kTcSubA = kTcM * 32;               // one K = 16 sub-tile of A (4 KB)
 constexpr uint32_t kTcSubB = kTcN * 32;               // one K = 16 sub-tile of B (7 KB)
 constexpr uint32_t kBTileBytes = 2 * kTcSubB;         // K = 32
-constexpr int kTcStages = 8;
+#ifndef PTSDF_TC_STAGES
+#define PTSDF_TC_STAGES 8
+#endif
+constexpr int kTcStages = PTSDF_TC_STAGES;
 constexpr int kEpiGroups = 4;                         // epilogue warps per TMEM lane quadrant
 constexpr int kEpiWarps = 4 * kEpiGroups;
 constexpr int kEpiSets = 2;                           // sets of epilogue warps taking alternate tiles

@@ -86,6 +86,7 @@ struct Request {
     int64_t queued_ns = 0;          // when it joined the queue (the age guard of SMALLEST_FIRST)
     int64_t done_ns = 0;
     int stream = 0;
+    bool bulk = false;              // above express_gpairs (when the server has express streams)
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     std::atomic<bool> done{false};
 };
@@ -103,7 +104,9 @@ struct Server {
     int64_t mem_in_use = 0;
     uint64_t next_ticket = 1;
     bool stop = false;
-    int next_stream = 0;
+    std::vector<double> stream_work;   // pairs of the requests in flight on each stream
+    int n_express = 0;                 // streams [0, n_express) take the express class
+    int bulk_inflight = 0;             // bulk requests in flight (at most max_inflight - max_inflight / 2)
     std::thread worker;
 };
 
@@ -156,6 +159,28 @@ void CUDART_CB on_request_done(void* p) {
 }
 
 unsigned nblk(int64_t n) { return (unsigned)((n + 255) / 256); }
+
+// The stream of a request of `work` pairs: within its priority class (the
+// express streams for small requests when express_gpairs > 0), the one with
+// the least work in flight, so a request never waits in a stream's order
+// behind a larger one while another stream of its class has less.
+bool is_bulk(const Server& S, double work) {
+    return S.n_express > 0 && work > (double)S.cfg.express_gpairs * 1e9;
+}
+
+int pick_stream(const Server& S, double work) {
+    int lo = 0, hi = (int)S.streams.size();
+    if (S.n_express > 0) {
+        if (is_bulk(S, work))
+            lo = S.n_express;
+        else
+            hi = S.n_express;
+    }
+    int best = lo;
+    for (int i = lo + 1; i < hi; ++i)
+        if (S.stream_work[i] < S.stream_work[best]) best = i;
+    return best;
+}
 
 // Enqueues one admitted request (or chunk) on its stream.
 sdf_status launch_request(Server& S, Request& R) {
@@ -288,6 +313,8 @@ void scheduler(Server* S) {
                 cudaEventDestroy(R.ev0);
                 cudaEventDestroy(R.ev1);
                 S->mem_in_use -= R.need;
+                S->stream_work[R.stream] -= R.work;
+                if (R.bulk) --S->bulk_inflight;
                 if (R.status != SDF_OK && J.st.status == SDF_OK) J.st.status = R.status;
                 J.st.done_ns = std::max(J.st.done_ns, R.done_ns);
                 if (--J.remaining == 0) {
@@ -300,21 +327,35 @@ void scheduler(Server* S) {
             }
         }
         // admit while a slot and the memory are free: the head of the queue
-        // (FIFO, or a request older than starve_ms), else the smallest request
+        // (FIFO, or a request older than starve_ms), else the smallest request.
+        // With express streams, bulk requests hold at most the slots that
+        // max_inflight / 2 leaves, so a small request never waits for a slot
+        // behind large ones that share the device at low priority.
         while (!S->queue.empty() && (int)S->inflight.size() < S->cfg.max_inflight) {
-            size_t pick = 0;
-            if (S->cfg.policy == SDF_SERVE_SMALLEST_FIRST &&
-                now_ns() - S->queue.front()->queued_ns <= (int64_t)S->cfg.starve_ms * 1000000LL) {
-                for (size_t i = 1; i < S->queue.size(); ++i)
-                    if (S->queue[i]->work < S->queue[pick]->work) pick = i;
+            const bool bulk_full = S->n_express > 0 &&
+                                   S->bulk_inflight >= S->cfg.max_inflight - S->cfg.max_inflight / 2;
+            auto admissible = [&](const Request& R) { return !(bulk_full && is_bulk(*S, R.work)); };
+            size_t pick = S->queue.size();
+            const bool starving = now_ns() - S->queue.front()->queued_ns > (int64_t)S->cfg.starve_ms * 1000000LL;
+            for (size_t i = 0; i < S->queue.size(); ++i) {
+                if (!admissible(*S->queue[i])) continue;
+                if (pick == S->queue.size()) {
+                    pick = i;
+                    if (S->cfg.policy != SDF_SERVE_SMALLEST_FIRST || (i == 0 && starving)) break;
+                } else if (S->queue[i]->work < S->queue[pick]->work) {
+                    pick = i;
+                }
             }
+            if (pick == S->queue.size()) break;
             if (S->mem_in_use + S->queue[pick]->need > S->cfg.mem_budget_bytes) break;
             std::shared_ptr<Request> R = S->queue[pick];
             S->queue.erase(S->queue.begin() + (long)pick);
             Job& J = *R->job;
             if (R->q0 == 0) J.st.admit_ns = now_ns();
-            R->stream = S->next_stream;
-            S->next_stream = (S->next_stream + 1) % (int)S->streams.size();
+            R->stream = pick_stream(*S, R->work);
+            R->bulk = is_bulk(*S, R->work);
+            if (R->bulk) ++S->bulk_inflight;
+            S->stream_work[R->stream] += R->work;
             S->mem_in_use += R->need;
             cudaEventCreate(&R->ev0);
             cudaEventCreate(&R->ev1);
@@ -345,15 +386,22 @@ extern "C" sdf_status sdf_serve_create(const sdf_serve_config* cfg, sdf_server* 
         return set_error(SDF_EINVAL, "sdf_serve_create: need max_inflight >= 1, n_streams >= 1, budget > 0");
     if ((cfg->policy != SDF_SERVE_FIFO && cfg->policy != SDF_SERVE_SMALLEST_FIRST) || cfg->starve_ms < 0)
         return set_error(SDF_EINVAL, "sdf_serve_create: unknown policy or negative starve_ms");
+    if (!(cfg->express_gpairs >= 0.f) || (cfg->express_gpairs > 0.f && cfg->n_streams < 2))
+        return set_error(SDF_EINVAL, "sdf_serve_create: express_gpairs must be >= 0, and > 0 needs n_streams >= 2");
     auto* h = new sdf_server_s();
     Server& S = h->s;
     S.cfg = *cfg;
     cudaError_t e = cudaSetDevice(cfg->device);
+    // express streams at the highest priority, the others at the lowest
+    int least = 0, greatest = 0;
+    if (e == cudaSuccess) e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
+    S.n_express = cfg->express_gpairs > 0.f ? cfg->n_streams / 2 : 0;
     for (int i = 0; e == cudaSuccess && i < cfg->n_streams; ++i) {
         cudaStream_t st;
-        e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+        e = cudaStreamCreateWithPriority(&st, cudaStreamNonBlocking, i < S.n_express ? greatest : least);
         if (e == cudaSuccess) S.streams.push_back(st);
     }
+    S.stream_work.assign(S.streams.size(), 0.0);
     if (e != cudaSuccess) {
         for (auto st : S.streams) cudaStreamDestroy(st);
         delete h;

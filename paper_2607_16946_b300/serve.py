@@ -29,7 +29,7 @@ SDF_SERVE_FIFO, SDF_SERVE_SMALLEST_FIRST = 0, 1
 class sdf_serve_config(ctypes.Structure):
     _fields_ = [("mem_budget_bytes", ctypes.c_int64), ("max_inflight", ctypes.c_int32),
                 ("n_streams", ctypes.c_int32), ("device", ctypes.c_int32), ("policy", ctypes.c_int32),
-                ("starve_ms", ctypes.c_int32), ("split_gpairs", ctypes.c_int32)]
+                ("starve_ms", ctypes.c_int32), ("split_gpairs", ctypes.c_int32), ("express_gpairs", ctypes.c_float)]
 
 
 class sdf_request(ctypes.Structure):
@@ -48,13 +48,16 @@ class sdf_request_stats(ctypes.Structure):
 class Server:
     def __init__(self, mem_budget_bytes: int = 8 << 30, max_inflight: int = 8, n_streams: int = 4,
                  device: int | None = None, policy: int = SDF_SERVE_FIFO, starve_ms: int = 2000,
-                 split_gpairs: int = 0):
+                 split_gpairs: int = 0, express_gpairs: float = 0.0):
         """split_gpairs: requests above split_gpairs x 1e9 (query, point) pairs
-        run as query chunks interleaved with other requests (0: never)."""
+        run as query chunks interleaved with other requests (0: never).
+        express_gpairs: requests (and chunks) of at most express_gpairs x 1e9
+        pairs run on high-priority streams, the others on low-priority ones
+        (0: one priority; > 0 needs n_streams >= 2)."""
         import torch
         cfg = sdf_serve_config(int(mem_budget_bytes), int(max_inflight), int(n_streams),
                                torch.cuda.current_device() if device is None else int(device), int(policy),
-                               int(starve_ms), int(split_gpairs))
+                               int(starve_ms), int(split_gpairs), float(express_gpairs))
         h = ctypes.c_void_p()
         check(lib().sdf_serve_create(ctypes.byref(cfg), ctypes.byref(h)), "sdf_serve_create")
         self._h = h

@@ -77,11 +77,16 @@ def test_serve_host_side_validation(abi):
     assert L.sdf_serve_create(ctypes.byref(bad), ctypes.byref(h)) == abi.SDF_EINVAL
     bad = serve.sdf_serve_config(1 << 20, 1, 1, 0, 7, 0, 0)
     assert L.sdf_serve_create(ctypes.byref(bad), ctypes.byref(h)) == abi.SDF_EINVAL
+    # express streams: a negative or NaN threshold, or one stream for two classes
+    for express, streams in ((-1.0, 4), (float("nan"), 4), (1.0, 1)):
+        bad = serve.sdf_serve_config(1 << 20, 1, streams, 0, 0, 0, 0, express)
+        assert L.sdf_serve_create(ctypes.byref(bad), ctypes.byref(h)) == abi.SDF_EINVAL
+        assert b"express_gpairs" in L.sdf_last_error()
     assert L.sdf_serve_submit(None, None, None) == abi.SDF_EINVAL
     assert L.sdf_serve_poll(None, 1, 0, None) == abi.SDF_EINVAL
     assert L.sdf_serve_shutdown(None) == abi.SDF_OK
     # the ctypes structures match the C layout (sizes from include/ptsdf.h)
-    assert ctypes.sizeof(serve.sdf_serve_config) == 32
+    assert ctypes.sizeof(serve.sdf_serve_config) == 40
     assert ctypes.sizeof(serve.sdf_request_stats) == 48
     assert ctypes.sizeof(serve.sdf_request) == 16 + 5 * 8 + ctypes.sizeof(abi.sdf_query_opts)
 

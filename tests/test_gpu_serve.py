@@ -2,7 +2,8 @@
 
 Each request's result must be the same alone and in the mix: every request
 of a mixed, concurrently submitted workload (queries, gradients, Booleans,
-trace steps, offsets; host and device buffers; three submitting threads) is
+trace steps, offsets; host and device buffers; three submitting threads; one
+stream priority, or small requests on high-priority streams) is
 compared bit for bit with the same request run alone on a one-slot server,
 and (except trace steps) with the direct calls; a weighted cloud and
 log-sum-exp queries likewise.  Admission is checked under a one-slot budget,
@@ -50,9 +51,12 @@ def alone(m, torch, clouds, kind, ca, cb, x, dirs=None, t=None, offset=0.0):
     return m.combine(op, a, b)
 
 
-def test_mixed_requests_equal_alone(env):
+@pytest.mark.parametrize("express", [0.0, 0.5])
+def test_mixed_requests_equal_alone(env, express):
+    """express = 0.5: requests of at most 5e8 pairs (about half of this mix)
+    on two high-priority streams, the others on two low-priority ones."""
     m, S, torch, clouds = env
-    srv = S.Server(mem_budget_bytes=2 << 30, max_inflight=6, n_streams=4)
+    srv = S.Server(mem_budget_bytes=2 << 30, max_inflight=6, n_streams=4, express_gpairs=express)
     ids = [srv.register(c) for c in clouds]
     rng = np.random.Generator(np.random.PCG64(11))
     reqs = []
@@ -127,6 +131,31 @@ def test_smallest_first_admission(env):
     order = np.argsort([s["admit_ns"] for s in st])
     assert list(np.array(sizes)[order]) == sorted(sizes)
     for x, o in zip(xs, outs):
+        np.testing.assert_array_equal(o.cpu().numpy(), clouds[1].query(x).cpu().numpy())
+    srv.shutdown()
+
+
+def test_express_slot_reserved(env):
+    """express_gpairs: with two slots, large requests hold at most one, so
+    a small request submitted behind three large ones is admitted before the
+    second large one starts, and runs on a high-priority stream; every result
+    equals the direct call."""
+    m, S, torch, clouds = env
+    srv = S.Server(mem_budget_bytes=1 << 30, max_inflight=2, n_streams=2, express_gpairs=1.0)
+    cid = srv.register(clouds[1])                      # 20,000 points
+    bigs = [torch.as_tensor(f32(synth.uniform_queries(2_000_000, 40 + i)), dtype=torch.float32, device="cuda")
+            for i in range(3)]                         # 4e10 pairs each (about 40 ms): bulk
+    small = torch.as_tensor(f32(synth.uniform_queries(2_000, 45)), dtype=torch.float32, device="cuda")
+    torch.cuda.synchronize()
+    outs = [torch.empty(x.shape[0], device="cuda") for x in bigs]
+    tb = [srv.submit(S.SDF_REQ_QUERY, cid, x, o) for x, o in zip(bigs, outs)]
+    outs_small = torch.empty(small.shape[0], device="cuda")
+    ts = srv.submit(S.SDF_REQ_QUERY, cid, small, outs_small)
+    st_small = srv.poll(ts)
+    st = [srv.poll(t) for t in tb]
+    assert st_small["admit_ns"] < st[1]["admit_ns"] and st_small["admit_ns"] < st[2]["admit_ns"]
+    assert st[1]["admit_ns"] >= st[0]["done_ns"] - 1_000_000      # one large request at a time
+    for x, o in zip(bigs + [small], outs + [outs_small]):
         np.testing.assert_array_equal(o.cpu().numpy(), clouds[1].query(x).cpu().numpy())
     srv.shutdown()
 
