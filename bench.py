@@ -66,8 +66,8 @@ WORKLOAD = ("dense_grid: ring torus N=100000 (R=1, r=0.35, noise 0.005, 2deg vMF
 INSTR_PER_PAIR = 29
 THREAD_INSTR_PER_SM_CLK = 128
 NOMINAL_RATES = {"sqrt": 16.0, "rsqrt": 16.0, "ex2": 32.0, "fma": 128.0, "rcp": 16.0}
-# probe mixes timed whole: the FP32-unit loop's direct pair, and the
-# tensor-core loop's curvature-form pairs
+# probe mixes timed whole (the FP32-unit loop's three-root direct pair and
+# the scalar curvature-form pairs); the single-operation sums equal them
 PAIR_MIX_KEYS = {"direct": "pair_direct", "flat": "pair_flat", "curved": "pair_curved"}
 
 
@@ -99,23 +99,19 @@ def pair_ceiling(rates, instr_per_pair):
 
 # Tensor-core loop, per pair by record form: special-function operations
 # (sqrt, rcp, ex2) and FP32 operations on the FMA pipe (the products come from
-# the tensor cores).  Direct form: a, b -> rho (MUFU sqrt), the tube distance
-# (MUFU sqrt), the weight's exp2 (MUFU), and d = sqrt(d^2) by two Newton steps
-# on the FMA pipe (8 of its 17 operations, as .f32x2 pairs); the probe does not
-# time this mix whole, so its cost is the sum of the single-operation costs
-# (the mixes it does time equal those sums).  Flat and curved curvature-form
-# pairs keep the scalar epilogue: 11 and 15 FP32 operations, mixes timed whole.
-TC_FORM_COST = {"direct": ((2, 0, 1), 17), "flat": ((2, 1, 1), 11), "curved": ((3, 2, 1), 15)}
-TC_MIX_KEYS = {"flat": "pair_flat", "curved": "pair_curved"}
+# the tensor cores).  Every form takes d = sqrt(d^2) on the FMA pipe by two
+# Newton steps (8 of its FP32 operations, as .f32x2 pairs) and the rest of
+# its arithmetic as .f32x2.  Direct: a, b -> rho (MUFU sqrt), the tube
+# distance (MUFU sqrt), the weight's exp2; flat curvature form: one half-angle
+# step (sqrt + rcp); curved: two.  The probe does not time these mixes whole,
+# so their cost is the sum of the single-operation costs (the mixes it does
+# time equal those sums).
+TC_FORM_COST = {"direct": ((2, 0, 1), 17), "flat": ((1, 1, 1), 19), "curved": ((2, 2, 1), 23)}
 
 
 def mix_cost(rates, form):
     """SM-clocks of special-function work per tensor-core pair of a record
-    form: the probe's measured rate of that form's whole mix where it times
-    one, else the sum of the single-operation costs."""
-    k = TC_MIX_KEYS.get(form)
-    if k and rates.get(k):
-        return 1.0 / rates[k]
+    form: the sum of its single-operation costs."""
     return single_op_cost(rates, TC_FORM_COST[form][0])
 
 
@@ -947,9 +943,8 @@ def run_ours(args, rank, world, local):
                                              for f, c in counts.items())
         basis = (f"{'MUFU' if mufu_c <= fma_c else 'FMA-pipe'} ceiling: {sms} SMs x {fmax:.0f} MHz x "
                  f"{per_sm_clk:.3f} pairs/clk/SM over the points by form {counts}; MUFU per pair "
-                 f"(sqrt, rcp, ex2) = {dict((f, c[0]) for f, c in TC_FORM_COST.items())}: direct from the "
-                 f"measured single-operation rates, flat and curved mixes measured whole by sdf_probe_rates "
-                 f"-> {mufu_c:.3f} (nominal 16/16/32 per SM per clock: {nominal:.3f}); FMA pipe "
+                 f"(sqrt, rcp, ex2) = {dict((f, c[0]) for f, c in TC_FORM_COST.items())} at the measured "
+                 f"single-operation rates -> {mufu_c:.3f} (nominal 16/16/32 per SM per clock: {nominal:.3f}); FMA pipe "
                  f"{rates['fma']:.1f}/{dict((f, c[1]) for f, c in TC_FORM_COST.items())} FP32 operations "
                  f"-> {fma_c:.3f} (unit rates {rates['source']})")
     else:
