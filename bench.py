@@ -48,10 +48,10 @@ SEED = 1002
 WORKLOAD = ("dense_grid: ring torus N=100000 (R=1, r=0.35, noise 0.005, 2deg vMF normals, analytic "
             "curvature coefficients), Q=256^3 grid over [-1.6,1.6]^3")
 # Ceilings of the pair loop, per SM and clock.
-#  Issue: an SM issues 4 warp-instructions (128 thread-instructions) per clock.
-#    FP32-unit loop, direct torus form: 25 FP32 instructions (two 3-vector
+#  FP32-unit loop, direct torus form: 25 FP32 operations (two 3-vector
 #    differences, two dots, the perpendicular component and its norm, the tube
-#    distance, the blend and two accumulations) + 4 MUFU = 29 issue slots.
+#    distance, the blend and two accumulations), issued as .f32x2 for two
+#    points at a time, + 4 MUFU.
 #  MUFU (XU pipe): sdf_probe_rates measures, on the box, the single
 #    operations (on B300 sqrt / rsqrt / rcp.approx 16.0 results per SM per
 #    clock, ex2.approx 32.0, timed over the union of each SM's CTA windows and
@@ -59,12 +59,11 @@ WORKLOAD = ("dense_grid: ring torus N=100000 (R=1, r=0.35, noise 0.005, 2deg vMF
 #    per-pair mixes as dependent chains.  The FP32-unit loop's direct pair
 #    needs three square roots (|x - p|, the axis distance, the tube distance)
 #    and one exp2: 3 x 8 + 4 = 28 XU cycles per 32 pairs per SM sub-partition,
-#    4.571 pairs per SM per clock, which the measured mix matches; it nearly
-#    ties that loop's issue ceiling (128/29 = 4.41).
+#    4.571 pairs per SM per clock, which the measured mix matches, below that
+#    loop's FMA-pipe ceiling (124 / 25 = 4.96).
 #  FMA pipe: 128 FP32 lanes per SM (sdf_probe_rates: 124.1 results per clock);
 #    an .f32x2 instruction occupies it for two operations.
-INSTR_PER_PAIR = 29
-THREAD_INSTR_PER_SM_CLK = 128
+FP32_PER_PAIR = 25
 NOMINAL_RATES = {"sqrt": 16.0, "rsqrt": 16.0, "ex2": 32.0, "fma": 128.0, "rcp": 16.0}
 # probe mixes timed whole (the FP32-unit loop's three-root direct pair and
 # the scalar curvature-form pairs); the single-operation sums equal them
@@ -88,12 +87,12 @@ def single_op_cost(rates, mix):
     return mix[0] / rates["sqrt"] + mix[1] / rates.get("rcp", rates["sqrt"]) + mix[2] / rates["ex2"]
 
 
-def pair_ceiling(rates, instr_per_pair):
+def pair_ceiling(rates, fp32_per_pair):
     """FP32-unit loop, pairs per SM clock: the lower of the MUFU ceiling (its
     3 sqrt + 1 exp2 mix, measured whole, else the single-operation sum) and
-    the issue ceiling."""
+    the FMA-pipe ceiling."""
     mufu = rates.get("pair_direct") or 1.0 / single_op_cost(rates, (3, 0, 1))
-    issue = rates["fma"] / instr_per_pair
+    issue = rates["fma"] / fp32_per_pair
     return min(mufu, issue), mufu, issue
 
 
@@ -949,13 +948,13 @@ def run_ours(args, rank, world, local):
                  f"-> {fma_c:.3f} (unit rates {rates['source']})")
     else:
         kname, kpairs = "k_fwd", pairs_per_step
-        per_sm_clk, mufu_c, issue_c = pair_ceiling(rates, INSTR_PER_PAIR)
+        per_sm_clk, mufu_c, issue_c = pair_ceiling(rates, FP32_PER_PAIR)
         kp = prof.get("fwd", {"launches": 0, "ms": float("nan")})
         traffic = None
-        basis = (f"{'MUFU' if mufu_c <= issue_c else 'issue'} ceiling: {sms} SMs x {fmax:.0f} MHz x "
+        basis = (f"{'MUFU' if mufu_c <= issue_c else 'FMA-pipe'} ceiling: {sms} SMs x {fmax:.0f} MHz x "
                  f"{per_sm_clk:.3f} pairs/clk/SM; MUFU: the direct mix (3 sqrt + 1 ex2) measured whole = "
-                 f"{mufu_c:.3f}, issue fma/"
-                 f"{INSTR_PER_PAIR} = {issue_c:.3f} (unit rates {rates['source']})")
+                 f"{mufu_c:.3f}, FMA pipe {rates['fma']:.1f}/"
+                 f"{FP32_PER_PAIR} = {issue_c:.3f} (unit rates {rates['source']})")
     peak = sms * fmax * 1e6 * per_sm_clk / 1e9
     # per step: the pair loop runs as one launch per record segment present
     per_step_s = kp["ms"] / args.steps / 1e3

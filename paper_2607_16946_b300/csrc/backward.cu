@@ -24,6 +24,7 @@
 #include <cmath>
 
 #include "device_common.cuh"
+#include "f32x2_ops.cuh"
 #include "fit_math.cuh"
 #include "internal.h"
 
@@ -61,12 +62,9 @@ __global__ void k_bwd_prep(const float* __restrict__ saved, const float* __restr
     for (int k = 0; k < 6; ++k) dst[2 * k] = v[k];
 }
 
-__device__ __forceinline__ f32x2 f2_splat(float v) { return f2_pack(v, v); }
 __device__ __forceinline__ f32x2 f2_rsqrt_clamped(f32x2 v) {
     return f2_pack(rsqrt_mufu(fmaxf(f2_lo(v), kTiny)), rsqrt_mufu(fmaxf(f2_hi(v), kTiny)));
 }
-__device__ __forceinline__ f32x2 f2_max0(f32x2 v) { return f2_pack(fmaxf(f2_lo(v), 0.f), fmaxf(f2_hi(v), 0.f)); }
-__device__ __forceinline__ f32x2 f2_rcp(f32x2 v) { return f2_pack(rcp_mufu(f2_lo(v)), rcp_mufu(f2_hi(v))); }
 
 // The record of this thread's point as pairs (both halves the same value).
 struct Rec2 {

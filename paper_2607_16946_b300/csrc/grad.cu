@@ -19,6 +19,7 @@
 #include <cmath>
 
 #include "query_common.cuh"
+#include "f32x2_ops.cuh"
 
 namespace ptsdf {
 
@@ -181,9 +182,6 @@ __device__ __forceinline__ void grad_tile(const float4* __restrict__ tile, int c
 __device__ __forceinline__ f32x2 f2_rsqrt_clamped(f32x2 v) {
     return f2_pack(rsqrt_mufu(fmaxf(f2_lo(v), kTiny)), rsqrt_mufu(fmaxf(f2_hi(v), kTiny)));
 }
-__device__ __forceinline__ f32x2 f2_max0(f32x2 v) { return f2_pack(fmaxf(f2_lo(v), 0.f), fmaxf(f2_hi(v), 0.f)); }
-__device__ __forceinline__ f32x2 f2_rcp(f32x2 v) { return f2_pack(rcp_mufu(f2_lo(v)), rcp_mufu(f2_hi(v))); }
-__device__ __forceinline__ f32x2 f2_splat(float v) { return f2_pack(v, v); }
 
 template <bool KAPPA, bool WEIGHTED>
 __device__ __forceinline__ void grad_tile2(const ulonglong2* __restrict__ tile, int cnt, f32x2 X, f32x2 Y, f32x2 Z,

@@ -35,6 +35,14 @@
 #include <string>
 
 #include "query_common.cuh"
+#include "f32x2_ops.cuh"
+
+#ifndef PTSDF_FWD_PAIRS
+#define PTSDF_FWD_PAIRS 1   // k_fwd: two points per .f32x2 step over the pair-interleaved records (0: scalar)
+#endif
+#ifndef PTSDF_FWD_PAIR_BLOCKS
+#define PTSDF_FWD_PAIR_BLOCKS 3   // resident CTAs per SM the packed k_fwd is compiled for
+#endif
 
 namespace ptsdf {
 
@@ -117,11 +125,84 @@ __device__ __forceinline__ void pair_tile(const float4* __restrict__ tile, int c
     }
 }
 
+// The same tile two points at a time, over the pair-interleaved records
+// (Cloud::rec2: for points 2k, 2k+1 each record float4 r_m is stored as
+// (r_m.x, r_m.x', r_m.y, r_m.y') (r_m.z, r_m.z', r_m.w, r_m.w')): every 128-bit
+// shared load gives two .f32x2 operands, and every FP32 step of a pair runs
+// for both points in one instruction against the lane's query broadcast into
+// both halves (the special-function steps stay one per point).  The pair
+// arithmetic is that of pair_tile, operation for operation; a pair's second
+// point past the tile's `cnt` (a zero record) gets weight 0.
+struct QPair {
+    f32x2 X, Y, Z, NL, A0;   // the query and its exponent, in both halves
+    f32x2 w, s;              // tile partials of the two points' halves
+};
+
+template <bool KAPPA, int PREC, bool WEIGHTED, bool FLAT = false>
+__device__ __forceinline__ void pair_tile2(const ulonglong2* __restrict__ tile, int cnt,
+                                           QPair (&qp)[kQueriesPerThread]) {
+    const f32x2 ONE = f2_splat(1.f);
+#pragma unroll 1
+    for (int j = 0; j < cnt; j += 2) {
+        const ulonglong2* r = tile + 4 * j;   // 8 x 16 B per pair of points
+        const ulonglong2 a0 = r[0], b0 = r[1], a1 = r[2], b1 = r[3], a2 = r[4], b2 = r[5];
+        ulonglong2 a3 = make_ulonglong2(0ull, 0ull), b3 = a3;
+        if (KAPPA || WEIGHTED) {
+            a3 = r[6];
+            b3 = r[7];
+        }
+        const bool second = j + 1 < cnt;
+#pragma unroll
+        for (int k = 0; k < kQueriesPerThread; ++k) {
+            QPair& q = qp[k];
+            const f32x2 DX = f2_sub(q.X, a0.x), DY = f2_sub(q.Y, a0.y), DZ = f2_sub(q.Z, b0.x);
+            const f32x2 D = f2_sqrt(f2_fma(DX, DX, f2_fma(DY, DY, f2_mul(DZ, DZ))));
+            f32x2 G;
+            if (!KAPPA) {
+                // g_direct: v = x - c, h = <v, u>, w = v - h u, rho = |w|, D = |(rho - R, h)|
+                const f32x2 VX = f2_sub(q.X, a1.x), VY = f2_sub(q.Y, a1.y), VZ = f2_sub(q.Z, b1.x);
+                const f32x2 H = f2_fma(VX, a2.x, f2_fma(VY, a2.y, f2_mul(VZ, b2.x)));
+                const f32x2 NH = f2_sub(f2_splat(0.f), H);
+                const f32x2 WX = f2_fma(NH, a2.x, VX), WY = f2_fma(NH, a2.y, VY), WZ = f2_fma(NH, b2.x, VZ);
+                const f32x2 RHO = f2_sqrt(f2_fma(WX, WX, f2_fma(WY, WY, f2_mul(WZ, WZ))));
+                const f32x2 E = f2_sub(RHO, b1.y);
+                G = f2_fma(b0.y, f2_sqrt(f2_fma(E, E, f2_mul(H, H))), b2.y);
+            } else {
+                // g_kappa / g_kappa_flat
+                const f32x2 YX = f2_sub(q.X, a1.x), YY = f2_sub(q.Y, a1.y), YZ = f2_sub(q.Z, b1.x);
+                const f32x2 H = f2_fma(YX, a2.x, f2_fma(YY, a2.y, f2_mul(YZ, b2.x)));
+                const f32x2 HH = f2_mul(H, H);
+                const f32x2 YN = f2_fma(YX, a3.x, f2_fma(YY, a3.y, f2_mul(YZ, b3.x)));
+                f32x2 AP;
+                if (FLAT) {
+                    AP = f2_mul(f2_splat(0.5f), YN);
+                } else {
+                    const f32x2 T2 = f2_sub(f2_fma(YX, YX, f2_fma(YY, YY, f2_mul(YZ, YZ))), HH);
+                    const f32x2 M = f2_fma(b1.y, T2, YN);
+                    const f32x2 S1 = f2_sqrt(f2_max0(f2_fma(b1.y, M, ONE)));
+                    AP = f2_mul(M, f2_rcp(f2_add(ONE, S1)));
+                }
+                const f32x2 NP = f2_fma(b2.y, f2_fma(AP, AP, HH), f2_mul(b0.y, AP));
+                const f32x2 S2 = f2_sqrt(f2_max0(f2_fma(b2.y, NP, ONE)));
+                G = f2_mul(NP, f2_rcp(f2_add(ONE, S2)));
+            }
+            const f32x2 ARG = f2_fma(q.NL, D, q.A0);
+            float w0, w1;
+            weights2<PREC>(f2_lo(ARG), f2_hi(ARG), w0, w1);
+            if (!second) w1 = 0.f;                                      // no second point
+            f32x2 W = f2_pack(w0, w1);
+            if (WEIGHTED) W = f2_mul(W, b3.y);                          // (A, A') = r3.w of both
+            q.w = f2_add(q.w, W);
+            q.s = f2_fma(W, G, q.s);
+        }
+    }
+}
+
 // --------------------------------------------------------------------------
 // Forward pass
 // --------------------------------------------------------------------------
 template <int PREC, bool WEIGHTED>
-__global__ void __launch_bounds__(kThreads, kFwdMinBlocks) k_fwd(const float4* __restrict__ rec, int64_t n_direct, int64_t n_kappa,
+__global__ void __launch_bounds__(kThreads, PTSDF_FWD_PAIRS ? PTSDF_FWD_PAIR_BLOCKS : kFwdMinBlocks) k_fwd(const float4* __restrict__ rec, int64_t n_direct, int64_t n_kappa,
                                                   int64_t tiles_direct, int64_t tiles_total, int64_t tiles_per_chunk,
                                                   QueryArgs a, int32_t* status, int64_t n_kappa_flat) {
     extern __shared__ __align__(128) char smem[];
@@ -139,6 +220,10 @@ __global__ void __launch_bounds__(kThreads, kFwdMinBlocks) k_fwd(const float4* _
             ring.produce(buf, reinterpret_cast<const char*>(rec + t0 * kTileRecs * 4), nt, kTileBytes, status);
         return;
     }
+#if PTSDF_FWD_PAIRS
+    QPair qp[kQueriesPerThread];
+    float Wt[kQueriesPerThread], St[kQueriesPerThread];
+#endif
     QState qs[kQueriesPerThread];
     int64_t qi[kQueriesPerThread];
 #pragma unroll
@@ -151,6 +236,14 @@ __global__ void __launch_bounds__(kThreads, kFwdMinBlocks) k_fwd(const float4* _
         // exponent A0 - L d = -lambda_x (d - d_min) log2(e)
         query_screening(a.d2, a.pre_split, a.q, qq, a.mode, a.C, a.lam, qs[k].L, qs[k].A0);
         qs[k].W = qs[k].S = 0.f;
+#if PTSDF_FWD_PAIRS
+        qp[k].X = f2_splat(qs[k].x);
+        qp[k].Y = f2_splat(qs[k].y);
+        qp[k].Z = f2_splat(qs[k].z);
+        qp[k].NL = f2_splat(-qs[k].L);
+        qp[k].A0 = f2_splat(qs[k].A0);
+        Wt[k] = St[k] = 0.f;
+#endif
     }
     for (int64_t t = 0; t < nt; ++t) {
         if (!ring.wait_full(t, status)) return;
@@ -160,6 +253,23 @@ __global__ void __launch_bounds__(kThreads, kFwdMinBlocks) k_fwd(const float4* _
         const int64_t first = (kappa ? gt - tiles_direct : gt) * kTileRecs;
         const int64_t seg = kappa ? n_kappa : n_direct;
         const int cnt = (int)(seg - first < kTileRecs ? seg - first : kTileRecs);
+#if PTSDF_FWD_PAIRS
+        const ulonglong2* tile2 = reinterpret_cast<const ulonglong2*>(tile);
+#pragma unroll
+        for (int k = 0; k < kQueriesPerThread; ++k) qp[k].w = qp[k].s = f2_splat(0.f);
+        if (kappa && first + kTileRecs <= n_kappa_flat)   // every record of the tile has kappa_min = 0
+            pair_tile2<true, PREC, WEIGHTED, true>(tile2, cnt, qp);
+        else if (kappa)
+            pair_tile2<true, PREC, WEIGHTED>(tile2, cnt, qp);
+        else
+            pair_tile2<false, PREC, WEIGHTED>(tile2, cnt, qp);
+        // blocked summation, the two halves of a tile's partials first
+#pragma unroll
+        for (int k = 0; k < kQueriesPerThread; ++k) {
+            Wt[k] += f2_lo(qp[k].w) + f2_hi(qp[k].w);
+            St[k] += f2_lo(qp[k].s) + f2_hi(qp[k].s);
+        }
+#else
 #pragma unroll
         for (int k = 0; k < kQueriesPerThread; ++k) qs[k].w = qs[k].s = 0.f;
         if (kappa && first + kTileRecs <= n_kappa_flat)   // every record of the tile has kappa_min = 0
@@ -175,8 +285,16 @@ __global__ void __launch_bounds__(kThreads, kFwdMinBlocks) k_fwd(const float4* _
             qs[k].W += qs[k].w;
             qs[k].S += qs[k].s;
         }
+#endif
         ring.release(t, lane);
     }
+#if PTSDF_FWD_PAIRS
+#pragma unroll
+    for (int k = 0; k < kQueriesPerThread; ++k) {
+        qs[k].W = Wt[k];
+        qs[k].S = St[k];
+    }
+#endif
 #pragma unroll
     for (int k = 0; k < kQueriesPerThread; ++k) {
         if (qi[k] >= a.q) continue;
@@ -188,6 +306,9 @@ __global__ void __launch_bounds__(kThreads, kFwdMinBlocks) k_fwd(const float4* _
 }
 
 using FwdKernel = decltype(&k_fwd<SDF_F32, false>);
+
+// the records k_fwd reads: pair-interleaved for the packed pair loop
+const float4* fwd_records(const Cloud& c) { return PTSDF_FWD_PAIRS ? c.rec2 : c.rec; }
 
 FwdKernel fwd_kernel(int precision, bool weighted) {
     if (weighted)
@@ -331,7 +452,7 @@ sdf_status launch_query(const Cloud& c, const float* d_x, int64_t q, float* d_ph
     if (e == cudaSuccess && !tc) {
         ProfRange pr(SDF_K_FWD, st);
         const FwdKernel kern = fwd_kernel(o.precision, c.weighted);
-        kern<<<grid, kThreads, kStages * kTileBytes, st>>>(c.rec, c.n_direct, c.n_kappa, c.tiles_direct,
+        kern<<<grid, kThreads, kStages * kTileBytes, st>>>(fwd_records(c), c.n_direct, c.n_kappa, c.tiles_direct,
                                                           c.tiles_direct + c.tiles_kappa, p.tiles_per_chunk, a,
                                                           c.status, c.n_kappa_flat);
         e = cudaGetLastError();
@@ -376,8 +497,8 @@ sdf_status launch_query(const Cloud& c, const float* d_x, int64_t q, float* d_ph
             ak.part_base = tp.nd + tp.nf + tp.nk;
             fwd_kernel(SDF_F32, c.weighted)<<<dim3((unsigned)p.qblocks, (unsigned)tp.na), kThreads,
                                                kStages * kTileBytes, st>>>(
-                c.rec, c.n_direct, c.n_kappa, c.tiles_direct, c.tiles_direct + c.tiles_kappa, tp.tpc_a, ak, c.status,
-                c.n_kappa_flat);
+                fwd_records(c), c.n_direct, c.n_kappa, c.tiles_direct, c.tiles_direct + c.tiles_kappa, tp.tpc_a, ak,
+                c.status, c.n_kappa_flat);
             e = cudaGetLastError();
         }
     }
@@ -512,7 +633,7 @@ extern "C" sdf_status sdf_query_noalloc(sdf_cloud cloud, const float* d_x, int64
             c.pre, c.n, c.pre_tiles, p.pre_tiles_per_chunk, a, c.status);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) {
-        fwd_kernel(SDF_F32, c.weighted)<<<grid, kThreads, kStages * kTileBytes, st>>>(c.rec, c.n_direct, c.n_kappa, c.tiles_direct,
+        fwd_kernel(SDF_F32, c.weighted)<<<grid, kThreads, kStages * kTileBytes, st>>>(fwd_records(c), c.n_direct, c.n_kappa, c.tiles_direct,
                                                            c.tiles_direct + c.tiles_kappa, p.tiles_per_chunk, a,
                                                            c.status, c.n_kappa_flat);
         e = cudaGetLastError();
