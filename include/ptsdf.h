@@ -184,6 +184,29 @@ PTSDF_API sdf_status sdf_build(const float* d_points, const float* d_normals, co
 PTSDF_API sdf_status sdf_build_weighted(const float* d_points, const float* d_normals, const float* d_params,
                               const float* d_weights, int64_t n, void* stream, sdf_cloud* out);
 
+/* ---------------------------------------------------------------------------
+ * Checkpoint of a built cloud (no counterpart in the paper; its precomputation
+ * is Algorithm 1 "Precomputation": the tori fitted from the per-point
+ * coefficients, Sec. 4.1).
+ *
+ * sdf_export -- writes the cloud into a host buffer: its inputs (points,
+ *   normals, the six coefficients, the weights of a weighted cloud) and the
+ *   fitted torus records, so that sdf_import rebuilds it without fitting.
+ *   buf == NULL: *size receives the bytes needed and nothing else happens.
+ *   Else cap must be at least that size (SDF_EINVAL otherwise) and *size
+ *   receives the bytes written.  Synchronous (device-wide copies).  The
+ *   layout is this library's: a 24-byte header ("PTSDFCK", version 1, the
+ *   weighted flag, n), then the arrays in host byte order.
+ * sdf_import -- builds a cloud on the current device from an sdf_export
+ *   buffer of `size` bytes; every query of the imported cloud equals that of
+ *   the exported one bit for bit.  SDF_EINVAL (before any CUDA call) for a
+ *   buffer that is not an export of version 1 or whose size does not match
+ *   its header; the records are taken as written (the export checked them).
+ *   Synchronises `stream` before returning.
+ * ------------------------------------------------------------------------- */
+PTSDF_API sdf_status sdf_export(sdf_cloud cloud, void* buf, int64_t cap, int64_t* size);
+PTSDF_API sdf_status sdf_import(const void* buf, int64_t size, void* stream, sdf_cloud* out);
+
 /* Releases a cloud (synchronises the device first).  NULL is a no-op. */
 PTSDF_API sdf_status sdf_destroy(sdf_cloud cloud);
 

@@ -10,7 +10,8 @@ supplies device memory and the current CUDA stream.
     phi = cloud.query_host(x_numpy)                # host arrays in and out
     phi = sdf(x, cloud, params)                    # differentiable in x and params
 
-Also on Cloud: query_grad, query_laplacian, backward_params, trace,
+Also on Cloud: query_grad, query_laplacian, backward_params, trace, export /
+from_export (checkpoint),
 project_level_set, knn_mean_distance / paper_lambda, info, device_status;
 module functions combine, mesh_level_set and orient; serving in
 paper_2607_16946_b300.serve.  Options (lambda mode, formula, precision,
@@ -79,6 +80,29 @@ class Cloud:
         self._h = h
         self.n = int(p.shape[0])
         self.weighted = w is not None
+
+    def export(self) -> bytes:
+        """The cloud as a checkpoint (sdf_export): inputs and fitted records."""
+        size = ctypes.c_int64()
+        check(lib().sdf_export(self._h, None, 0, ctypes.byref(size)), "sdf_export")
+        buf = ctypes.create_string_buffer(size.value)
+        check(lib().sdf_export(self._h, buf, size.value, ctypes.byref(size)), "sdf_export")
+        return buf.raw[: size.value]
+
+    @classmethod
+    def from_export(cls, data: bytes, stream=None) -> "Cloud":
+        """A cloud rebuilt from Cloud.export() / sdf_export without fitting
+        (sdf_import); its queries equal the exported cloud's bit for bit."""
+        h = ctypes.c_void_p()
+        buf = ctypes.create_string_buffer(bytes(data), len(data))
+        check(lib().sdf_import(buf, len(data), _stream_ptr(stream), ctypes.byref(h)), "sdf_import")
+        self = cls.__new__(cls)
+        self._h = h
+        n = ctypes.c_int64()
+        check(lib().sdf_cloud_info(h, ctypes.byref(n), None, None, None))
+        self.n = int(n.value)
+        self.weighted = bool(int.from_bytes(bytes(data[12:16]), "little"))
+        return self
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:

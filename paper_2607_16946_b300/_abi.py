@@ -70,6 +70,8 @@ SIGNATURES = {
     "sdf_project_level_set": (ctypes.c_int, [_P, _P, _I64, ctypes.c_float, ctypes.c_int32, ctypes.c_float, _P, _P,
                                              _P, ctypes.POINTER(sdf_query_opts), _P]),
     "sdf_destroy": (ctypes.c_int, [_P]),
+    "sdf_export": (ctypes.c_int, [_P, _P, _I64, ctypes.POINTER(_I64)]),
+    "sdf_import": (ctypes.c_int, [_P, _I64, _P, ctypes.POINTER(_P)]),
     "sdf_cloud_info": (ctypes.c_int, [_P, ctypes.POINTER(_I64), ctypes.POINTER(_F), ctypes.POINTER(_I64),
                                       ctypes.POINTER(_I64)]),
     "sdf_cloud_forms": (ctypes.c_int, [_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64)]),

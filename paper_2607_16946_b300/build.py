@@ -46,7 +46,7 @@ def build(force: bool = False, verbose: bool = False, defines=(), lib_path: str 
             cmd.insert(1, "-Xptxas=-v")
         subprocess.run(cmd, check=True)
     if force or not os.path.exists(lib_path) or os.path.getmtime(lib_path) < max(os.path.getmtime(o) for o in objs):
-        subprocess.run([NVCC, *ARCH, "-shared", "-o", lib_path, *objs, "-lpthread"], check=True)
+        subprocess.run([NVCC, *ARCH, "-shared", "-o", lib_path, *objs, "-lpthread", "-ldl"], check=True)
     return lib_path
 
 

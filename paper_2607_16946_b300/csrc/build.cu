@@ -350,20 +350,11 @@ void free_cloud(Cloud* c) {
     delete c;
 }
 
-}  // namespace
-
-extern "C" sdf_status sdf_build(const float* d_points, const float* d_normals, const float* d_params, int64_t n,
-                                void* stream, sdf_cloud* out) {
-    return sdf_build_weighted(d_points, d_normals, d_params, nullptr, n, stream, out);
-}
-
-extern "C" sdf_status sdf_build_weighted(const float* d_points, const float* d_normals, const float* d_params,
-                                         const float* d_weights, int64_t n, void* stream, sdf_cloud* out) {
-    if (!out) return set_error(SDF_EINVAL, "sdf_build: out is NULL");
-    *out = nullptr;
-    if (n < 1 || n > 0x7fffffffLL) return set_error(SDF_EINVAL, "sdf_build: n must be in [1, 2^31-1]");
-    if (!d_points || !d_normals || !d_params) return set_error(SDF_EINVAL, "sdf_build: NULL input pointer");
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
+// The build from device inputs.  d_rec_in / d_kind_in (n x 16 floats and n
+// kinds, input order, as k_fit writes them): the fitted records of an
+// export, used instead of fitting again; NULL: fit.
+sdf_status build_impl(const float* d_points, const float* d_normals, const float* d_params, const float* d_weights,
+                      int64_t n, cudaStream_t st, sdf_cloud* out, const float* d_rec_in, const int8_t* d_kind_in) {
     Cloud* c = new Cloud();
     c->n = n;
     c->weighted = d_weights != nullptr;
@@ -418,10 +409,17 @@ extern "C" sdf_status sdf_build_weighted(const float* d_points, const float* d_n
     // zero curvatures, use the kappa form
     const double thr = 8.0 * std::fmax((double)c->aabb_diag, 1e-6);
 
-    const int fit_threads = 128;
-    k_fit<<<(unsigned)((n + fit_threads - 1) / fit_threads), fit_threads, 0, st>>>(
-        c->src_points, c->src_normals, c->src_params, d_weights, n, thr, rec_tmp, kind, c->status);
-    PTSDF_TRY(cudaGetLastError(), "sdf_build: k_fit launch");
+    if (d_rec_in) {
+        PTSDF_TRY(cudaMemcpyAsync(rec_tmp, d_rec_in, (size_t)n * kRecFloats * sizeof(float), cudaMemcpyDeviceToDevice,
+                                  st),
+                  "sdf_import: records");
+        PTSDF_TRY(cudaMemcpyAsync(kind, d_kind_in, (size_t)n, cudaMemcpyDeviceToDevice, st), "sdf_import: kinds");
+    } else {
+        const int fit_threads = 128;
+        k_fit<<<(unsigned)((n + fit_threads - 1) / fit_threads), fit_threads, 0, st>>>(
+            c->src_points, c->src_normals, c->src_params, d_weights, n, thr, rec_tmp, kind, c->status);
+        PTSDF_TRY(cudaGetLastError(), "sdf_build: k_fit launch");
+    }
     k_count<<<1, kPartThreads, 0, st>>>(kind, n, counts);
     PTSDF_TRY(cudaGetLastError(), "sdf_build: k_count launch");
     int64_t hcounts[3];
@@ -503,6 +501,129 @@ extern "C" sdf_status sdf_build_weighted(const float* d_points, const float* d_n
     cudaFree(counts);
     *out = reinterpret_cast<sdf_cloud>(c);
     return SDF_OK;
+}
+
+// Checkpoint layout (host byte order): the header, then the points (n x 3),
+// normals (n x 3), coefficients (n x 6) and, for a weighted cloud, weights (n)
+// as float; the fitted records (n x 16 float, input order) and their kinds
+// (n bytes).
+struct ExportHeader {
+    char magic[8];        // "PTSDFCK\0"
+    uint32_t version;     // 1
+    uint32_t weighted;    // 0 or 1
+    int64_t n;
+};
+constexpr char kExportMagic[8] = {'P', 'T', 'S', 'D', 'F', 'C', 'K', 0};
+
+int64_t export_bytes(int64_t n, bool weighted) {
+    return (int64_t)sizeof(ExportHeader) + n * (int64_t)((12 + (weighted ? 1 : 0) + kRecFloats) * sizeof(float)) + n;
+}
+
+}  // namespace
+
+extern "C" sdf_status sdf_build(const float* d_points, const float* d_normals, const float* d_params, int64_t n,
+                                void* stream, sdf_cloud* out) {
+    return sdf_build_weighted(d_points, d_normals, d_params, nullptr, n, stream, out);
+}
+
+extern "C" sdf_status sdf_build_weighted(const float* d_points, const float* d_normals, const float* d_params,
+                                         const float* d_weights, int64_t n, void* stream, sdf_cloud* out) {
+    if (!out) return set_error(SDF_EINVAL, "sdf_build: out is NULL");
+    *out = nullptr;
+    if (n < 1 || n > 0x7fffffffLL) return set_error(SDF_EINVAL, "sdf_build: n must be in [1, 2^31-1]");
+    if (!d_points || !d_normals || !d_params) return set_error(SDF_EINVAL, "sdf_build: NULL input pointer");
+    return build_impl(d_points, d_normals, d_params, d_weights, n, static_cast<cudaStream_t>(stream), out, nullptr,
+                      nullptr);
+}
+
+extern "C" sdf_status sdf_export(sdf_cloud cloud, void* buf, int64_t cap, int64_t* size) {
+    if (!cloud || !size) return set_error(SDF_EINVAL, "sdf_export: cloud or size is NULL");
+    const Cloud* c = reinterpret_cast<const Cloud*>(cloud);
+    const int64_t n = c->n, need = export_bytes(n, c->weighted);
+    *size = need;
+    if (!buf) return SDF_OK;
+    if (cap < need) return set_error(SDF_EINVAL, "sdf_export: buffer smaller than the size sdf_export reports");
+    char* out = static_cast<char*>(buf);
+    ExportHeader h{};
+    std::memcpy(h.magic, kExportMagic, sizeof(h.magic));
+    h.version = 1;
+    h.weighted = c->weighted ? 1u : 0u;
+    h.n = n;
+    std::memcpy(out, &h, sizeof(h));
+    char* p = out + sizeof(h);
+    // the inputs, then the records fitted from them again (k_fit is deterministic)
+    float* d_w = nullptr;
+    float* d_rec = nullptr;
+    int8_t* d_kind = nullptr;
+    int32_t* d_status = nullptr;
+    cudaError_t e = cudaMemcpy(p, c->src_points, (size_t)n * 3 * sizeof(float), cudaMemcpyDeviceToHost);
+    p += n * 3 * sizeof(float);
+    if (e == cudaSuccess) e = cudaMemcpy(p, c->src_normals, (size_t)n * 3 * sizeof(float), cudaMemcpyDeviceToHost);
+    p += n * 3 * sizeof(float);
+    if (e == cudaSuccess) e = cudaMemcpy(p, c->src_params, (size_t)n * 6 * sizeof(float), cudaMemcpyDeviceToHost);
+    p += n * 6 * sizeof(float);
+    if (e == cudaSuccess && c->weighted) {
+        // A_i sits in the plane records, (pz, pz, A, A) at float4 4 i + 1, input order
+        e = cudaMalloc(&d_w, (size_t)n * sizeof(float));
+        if (e == cudaSuccess)
+            e = cudaMemcpy2D(d_w, sizeof(float), reinterpret_cast<const char*>(c->prec) + sizeof(float4) + 2 * sizeof(float),
+                             4 * sizeof(float4), sizeof(float), (size_t)n, cudaMemcpyDeviceToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(p, d_w, (size_t)n * sizeof(float), cudaMemcpyDeviceToHost);
+        p += n * sizeof(float);
+    }
+    if (e == cudaSuccess) e = cudaMalloc(&d_rec, (size_t)n * kRecFloats * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&d_kind, (size_t)n);
+    if (e == cudaSuccess) e = cudaMalloc(&d_status, sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMemset(d_status, 0, sizeof(int32_t));
+    if (e == cudaSuccess) {
+        const double thr = 8.0 * std::fmax((double)c->aabb_diag, 1e-6);
+        k_fit<<<(unsigned)((n + 127) / 128), 128>>>(c->src_points, c->src_normals, c->src_params, d_w, n, thr, d_rec,
+                                                     d_kind, d_status);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(p, d_rec, (size_t)n * kRecFloats * sizeof(float), cudaMemcpyDeviceToHost);
+    p += n * kRecFloats * sizeof(float);
+    if (e == cudaSuccess) e = cudaMemcpy(p, d_kind, (size_t)n, cudaMemcpyDeviceToHost);
+    cudaFree(d_w);
+    cudaFree(d_rec);
+    cudaFree(d_kind);
+    cudaFree(d_status);
+    return e == cudaSuccess ? SDF_OK : cuda_error(e, "sdf_export");
+}
+
+extern "C" sdf_status sdf_import(const void* buf, int64_t size, void* stream, sdf_cloud* out) {
+    if (!buf || !out) return set_error(SDF_EINVAL, "sdf_import: buf or out is NULL");
+    *out = nullptr;
+    ExportHeader h{};
+    if (size < (int64_t)sizeof(h)) return set_error(SDF_EINVAL, "sdf_import: buffer shorter than the header");
+    std::memcpy(&h, buf, sizeof(h));
+    if (std::memcmp(h.magic, kExportMagic, sizeof(h.magic)) != 0 || h.version != 1 || h.weighted > 1)
+        return set_error(SDF_EINVAL, "sdf_import: not an sdf_export buffer of version 1");
+    if (h.n < 1 || h.n > 0x7fffffffLL || size != export_bytes(h.n, h.weighted != 0))
+        return set_error(SDF_EINVAL, "sdf_import: the buffer's size does not match its header");
+    const int64_t n = h.n;
+    const bool weighted = h.weighted != 0;
+    const int64_t inputs = n * (12 + (weighted ? 1 : 0));
+    const char* p = static_cast<const char*>(buf) + sizeof(h);
+    float* d_in = nullptr;      // points, normals, coefficients, weights, records
+    int8_t* d_kind = nullptr;
+    cudaError_t e = cudaMalloc(&d_in, (size_t)(inputs + n * kRecFloats) * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&d_kind, (size_t)n);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(d_in, p, (size_t)(inputs + n * kRecFloats) * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(d_kind, p + (inputs + n * kRecFloats) * sizeof(float), (size_t)n, cudaMemcpyHostToDevice);
+    sdf_status s;
+    if (e != cudaSuccess) {
+        s = e == cudaErrorMemoryAllocation ? set_error(SDF_ENOMEM, "sdf_import: staging") : cuda_error(e, "sdf_import");
+    } else {
+        s = build_impl(d_in, d_in + 3 * n, d_in + 6 * n, weighted ? d_in + 12 * n : nullptr, n,
+                       static_cast<cudaStream_t>(stream), out, d_in + inputs, d_kind);
+    }
+    cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+    cudaFree(d_in);
+    cudaFree(d_kind);
+    return s;
 }
 
 extern "C" sdf_status sdf_destroy(sdf_cloud cloud) {

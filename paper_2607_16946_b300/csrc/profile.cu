@@ -1,6 +1,10 @@
 // Kernel timing by CUDA events (sdf_profile_*): a tracing aid used to measure
-// each kernel family's device time inside a longer timed region.
+// each kernel family's device time inside a longer timed region.  Every range
+// is also an NVTX range named "ptsdf:<family>" on the launching host thread,
+// which a profiler attached to the process shows around the launches (the
+// header-only NVTX API does nothing when no tool is attached).
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <mutex>
 #include <vector>
@@ -18,6 +22,8 @@ std::mutex g_mu;
 bool g_on = false;
 std::vector<Rec> g_recs;
 const char* kNames[SDF_K_COUNT_] = {"prepass", "fwd", "merge", "build", "fwd_grad", "bwd_params", "fwd_tc", "radius", "knn", "plane"};
+const char* kNvtxNames[SDF_K_COUNT_] = {"ptsdf:prepass", "ptsdf:fwd", "ptsdf:merge", "ptsdf:build", "ptsdf:fwd_grad",
+                                        "ptsdf:bwd_params", "ptsdf:fwd_tc", "ptsdf:radius", "ptsdf:knn", "ptsdf:plane"};
 
 void clear_locked() {
     for (auto& r : g_recs) {
@@ -29,6 +35,7 @@ void clear_locked() {
 }  // namespace
 
 ProfRange::ProfRange(int kernel, cudaStream_t st) : st_(st), idx_(-1) {
+    nvtxRangePushA(kernel >= 0 && kernel < SDF_K_COUNT_ ? kNvtxNames[kernel] : "ptsdf");
     std::lock_guard<std::mutex> lk(g_mu);
     if (!g_on) return;
     Rec r{kernel, nullptr, nullptr};
@@ -43,6 +50,7 @@ ProfRange::ProfRange(int kernel, cudaStream_t st) : st_(st), idx_(-1) {
 }
 
 ProfRange::~ProfRange() {
+    nvtxRangePop();
     if (idx_ < 0) return;
     std::lock_guard<std::mutex> lk(g_mu);
     if (idx_ < (int)g_recs.size()) cudaEventRecord(g_recs[idx_].b, st_);

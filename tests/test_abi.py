@@ -152,3 +152,29 @@ def test_every_entry_point_refuses_bad_arguments_on_the_host(abi):
     for call, msg in _refusals(abi):
         assert call() == abi.SDF_EINVAL, msg
         assert msg in L.sdf_last_error(), (msg, L.sdf_last_error())
+
+
+def test_import_refuses_what_is_not_an_export(abi):
+    """sdf_import checks the header and the size before any CUDA call."""
+    import struct
+    L = abi.lib()
+    h = ctypes.c_void_p()
+    n = 5
+    good_size = 24 + n * (12 + 16) * 4 + n
+
+    def blob(magic=b"PTSDFCK\0", version=1, weighted=0, count=n, size=good_size):
+        head = magic + struct.pack("<IIq", version, weighted, count)
+        return ctypes.create_string_buffer(head + b"\0" * (size - len(head)), size)
+
+    cases = [(None, 100, b"buf or out is NULL"), (blob(), 10, b"shorter than the header"),
+             (blob(magic=b"PTSDFCX\0"), good_size, b"not an sdf_export buffer"),
+             (blob(version=2), good_size, b"not an sdf_export buffer"),
+             (blob(weighted=3), good_size, b"not an sdf_export buffer"),
+             (blob(count=0, size=24), 24, b"does not match its header"),
+             (blob(), good_size - 1, b"does not match its header"),
+             (blob(weighted=1), good_size, b"does not match its header")]
+    for buf, size, msg in cases:
+        assert L.sdf_import(buf, size, None, ctypes.byref(h)) == abi.SDF_EINVAL
+        assert msg in L.sdf_last_error(), (msg, L.sdf_last_error())
+    size = ctypes.c_int64()
+    assert L.sdf_export(None, None, 0, ctypes.byref(size)) == abi.SDF_EINVAL
