@@ -596,7 +596,7 @@ PTSDF_API sdf_status sdf_selftest_wait_timeout(int32_t limit_us, int32_t* status
 /* Self-test of the square root the tensor-core epilogue computes on the FMA
  * pipe (no counterpart in the paper): over 2^25 positive normal floats from
  * 1e-30 up, the largest relative difference from CUDA's correctly rounded
- * sqrtf (about 4.6e-6 expected: two Newton steps from a bit-level
+ * sqrtf (about 4.7e-6 expected: two Newton steps from a bit-level
  * estimate). */
 PTSDF_API sdf_status sdf_selftest_soft_sqrt(double* max_rel_err);
 

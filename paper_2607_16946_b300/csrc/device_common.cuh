@@ -83,19 +83,30 @@ __device__ __forceinline__ f32x2 f2_fma(f32x2 a, f32x2 b, f32x2 c) {
 // integer and FMA pipes, the latter as .f32x2): 1/sqrt(x) starts from the
 // bit-level estimate of Lomont, "Fast Inverse Square Root" (2003): the
 // integer 0x5f375a86 minus half of x's bit pattern, within 3.5% of 1/sqrt(x);
-// ITERS Newton-Raphson steps for 1/y^2 = x, y <- y (3 - x y^2) / 2, square
-// the relative error each (about 1.8e-3, 4.6e-6, then FP32 rounding); and
-// sqrt(x) = x y.  x is clamped to >= 1e-30 (a zero comes out as 1e-15).
-template <int ITERS = 3>
+// then two Newton-Raphson steps for 1/y^2 = x, y <- y (c - x y^2 / 2), and
+// sqrt(x) = x y.  With c = 3/2 each step squares the relative error and
+// leaves y below 1/sqrt(x) (about -1.8e-3, then -4.7e-6).  Raising c by
+// delta lifts a step's result by about delta times itself: c1 = 1.5009 and
+// c2 = 1.5000006 centre the two error intervals (found by sweeping the
+// constants over one period of the estimate), within 7.6e-7 relative, but
+// the tensor-core pair loop compiled with them ran 1.2% slower (the two
+// constants changed its register allocation), so 3/2 stays the default.
+// x is clamped to >= 1e-30 (a zero comes out as 1e-15).
+#ifndef PTSDF_SQRT_C1
+#define PTSDF_SQRT_C1 1.5f   // the first step's constant (1.5009f: centred)
+#endif
+#ifndef PTSDF_SQRT_C2
+#define PTSDF_SQRT_C2 1.5f   // the second step's (1.5000006f: centred)
+#endif
 __device__ __forceinline__ f32x2 sqrt2_newton(float x0, float x1) {
     x0 = fmaxf(x0, 1e-30f);
     x1 = fmaxf(x1, 1e-30f);
     const f32x2 X = f2_pack(x0, x1);
-    const f32x2 NH = f2_mul(X, f2_pack(-0.5f, -0.5f)), C15 = f2_pack(1.5f, 1.5f);
+    const f32x2 NH = f2_mul(X, f2_pack(-0.5f, -0.5f));
     f32x2 Y = f2_pack(__int_as_float(0x5f375a86 - (__float_as_int(x0) >> 1)),
                       __int_as_float(0x5f375a86 - (__float_as_int(x1) >> 1)));
-#pragma unroll
-    for (int it = 0; it < ITERS; ++it) Y = f2_mul(Y, f2_fma(NH, f2_mul(Y, Y), C15));
+    Y = f2_mul(Y, f2_fma(NH, f2_mul(Y, Y), f2_pack(PTSDF_SQRT_C1, PTSDF_SQRT_C1)));
+    Y = f2_mul(Y, f2_fma(NH, f2_mul(Y, Y), f2_pack(PTSDF_SQRT_C2, PTSDF_SQRT_C2)));
     return f2_mul(X, Y);
 }
 

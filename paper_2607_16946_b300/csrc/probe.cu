@@ -291,7 +291,7 @@ extern "C" sdf_status sdf_selftest_wait_timeout(int32_t limit_us, int32_t* statu
 }
 
 // ---------------------------------------------------------------------------
-// Accuracy of sqrt2_newton<2> (the FMA-pipe square root of the tensor-core
+// Accuracy of sqrt2_newton (the FMA-pipe square root of the tensor-core
 // epilogue) against CUDA's correctly rounded sqrtf: every positive normal
 // float whose bit pattern is a multiple of 64 (2^25 inputs from 1.2e-38 to
 // 3.4e38), as relative errors; the largest is returned.
@@ -303,7 +303,7 @@ __global__ void k_soft_sqrt_check(uint32_t n, unsigned int* worst_bits) {
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const float x0 = __uint_as_float(0x00800000u + 128u * i), x1 = __uint_as_float(0x00800000u + 128u * i + 64u);
-    const f32x2 r = sqrt2_newton<2>(x0, x1);
+    const f32x2 r = sqrt2_newton(x0, x1);
     float e = 0.f;
     if (x0 >= 1e-30f) e = fmaxf(e, fabsf(f2_lo(r) - sqrtf(x0)) / sqrtf(x0));
     if (x1 >= 1e-30f) e = fmaxf(e, fabsf(f2_hi(r) - sqrtf(x1)) / sqrtf(x1));

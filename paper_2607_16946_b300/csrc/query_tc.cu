@@ -274,7 +274,7 @@ __device__ __forceinline__ float g_from_quantities(float q1, float q2, float q3,
 
 // The direct form's share, two points at a time: the FP32 arithmetic of a
 // lane's two pairs as .f32x2, and the square root of d^2 (which only sets
-// the weight) on the FMA pipe (sqrt2_newton, two Newton steps: 4.6e-6
+// the weight) on the FMA pipe (sqrt2_newton, two Newton steps: 4.7e-6
 // relative), so that the special-function unit does 2 sqrt + 1 exp2 per pair
 // (20 of its cycles per 32 pairs instead of 28).  On the dense grid this
 // runs 3.8% faster than a scalar epilogue with three MUFU square roots
@@ -298,7 +298,7 @@ __device__ __forceinline__ void tile_pairs_direct2(const float (&v)[kVals], floa
         const f32x2 ee = f2_fma(e, e, f2_mul(h, h));
         const f32x2 g = f2_fma(sT, f2_pack(sqrt_mufu(f2_lo(ee)), sqrt_mufu(f2_hi(ee))), nsr);
         // |d^2|: the products may round a zero distance slightly negative
-        const f32x2 d = sqrt2_newton<2>(fabsf(v[i]), fabsf(v[i + 1]));
+        const f32x2 d = sqrt2_newton(fabsf(v[i]), fabsf(v[i + 1]));
         const f32x2 arg = f2_fma(NLs, d, A0v);
         const f32x2 w = f2_pack(ex2_mufu(f2_lo(arg)), ex2_mufu(f2_hi(arg)));
         tw = WEIGHTED ? f2_fma(w, f2_pack(fabsf(v[48 + i]), fabsf(v[49 + i])), tw) : f2_add(tw, w);
@@ -338,7 +338,7 @@ __device__ __forceinline__ void tile_pairs_kappa2(const float (&v)[kVals], float
         const f32x2 den2 = f2_add(ONE, f2_pack(sqrt_mufu(fmaxf(f2_lo(t2), 0.f)), sqrt_mufu(fmaxf(f2_hi(t2), 0.f))));
         const f32x2 g = f2_mul(Np, f2_pack(rcp_mufu(f2_lo(den2)), rcp_mufu(f2_hi(den2))));
         // |d^2|: the products may round a zero distance slightly negative
-        const f32x2 d = sqrt2_newton<2>(fabsf(v[i]), fabsf(v[i + 1]));
+        const f32x2 d = sqrt2_newton(fabsf(v[i]), fabsf(v[i + 1]));
         const f32x2 arg = f2_fma(NLs, d, A0v);
         const f32x2 w = f2_pack(ex2_mufu(f2_lo(arg)), ex2_mufu(f2_hi(arg)));
         tw = f2_add(tw, w);

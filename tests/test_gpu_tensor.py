@@ -282,7 +282,7 @@ def test_wait_timeout_reports_and_recovers(ptsdf):
 def test_fma_pipe_square_root_matches_sqrtf(ptsdf):
     """The tensor-core epilogue takes the weight's distance d = sqrt(d^2) on
     the FMA pipe (Lomont's bit-level estimate of 1/sqrt and two Newton steps,
-    at most 4.6e-6 in exact arithmetic): against CUDA's correctly rounded
+    within 4.8e-6 by the CPU emulation): against CUDA's correctly rounded
     sqrtf over 2^25 normal floats it stays within 5e-6."""
     import ctypes
     err = ctypes.c_double()
