@@ -136,7 +136,10 @@ typedef struct {
     float offset;          /* returned value is phi(x) - offset (offset surfaces, Sec. 6) */
     int32_t split_n;       /* number of point chunks per query block; 0 = automatic.  The
                               automatic choice depends only on (Q, N, SM count), so a query's
-                              result does not depend on what else runs. */
+                              result does not depend on what else runs.  An explicit split also
+                              makes a batch too small for the one-thread-per-query pruned
+                              prepass take the point-split full scan rather than the
+                              warp-per-query pruned one (the same d_max, d_min bit for bit). */
     int32_t engine;        /* sdf_engine (SDF_ENGINE_AUTO) */
     int32_t formula;       /* sdf_formula (SDF_FORMULA_BLEND) */
 } sdf_query_opts;

@@ -20,6 +20,7 @@
 
 #include "query_common.cuh"
 #include "f32x2_ops.cuh"
+#include "prepass_warp.cuh"
 
 namespace ptsdf {
 
@@ -535,8 +536,8 @@ sdf_status launch_query_grad(const Cloud& c, const float* d_x, int64_t q, float*
         return e == cudaErrorMemoryAllocation ? set_error(SDF_ENOMEM, "sdf_query_grad: scratch")
                                               : cuda_error(e, "sdf_query_grad: scratch");
     };
-    const bool pruned = use_pruned_prepass(c, p, o);
-    a.pre_split = pruned ? 1 : p.split;
+    const bool pruned = use_pruned_prepass(c, p, o), warp_pre = use_warp_prepass(c, p, o);
+    a.pre_split = pruned || warp_pre ? 1 : p.split;
     cudaError_t e = cudaMallocAsync(&a.d2, (size_t)a.pre_split * q * sizeof(float2), st);
     if (e != cudaSuccess) return oom(e);
     if (o.lambda_mode == SDF_LAMBDA_GLOBAL) {
@@ -554,6 +555,8 @@ sdf_status launch_query_grad(const Cloud& c, const float* d_x, int64_t q, float*
         if (pruned)
             k_prepass_pruned<true><<<(unsigned)p.pre_qblocks, kPrunedThreads, 0, st>>>(c.pre, c.spheres, c.n,
                                                                                     c.n_spheres, a);
+        else if (warp_pre)
+            launch_prepass_warp(c, a, true, st);
         else if (o.lambda_mode == SDF_LAMBDA_GLOBAL)
             k_prepass<SDF_LAMBDA_GLOBAL, true><<<pre_grid, kThreads, kStages * kPreBytes, st>>>(
                 c.pre, c.n, c.pre_tiles, p.pre_tiles_per_chunk, a, c.status);

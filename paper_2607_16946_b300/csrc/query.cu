@@ -36,6 +36,7 @@
 
 #include "query_common.cuh"
 #include "f32x2_ops.cuh"
+#include "prepass_warp.cuh"
 
 #ifndef PTSDF_FWD_PAIRS
 #define PTSDF_FWD_PAIRS 1   // k_fwd: two points per .f32x2 step over the pair-interleaved records (0: scalar)
@@ -420,8 +421,8 @@ sdf_status launch_query(const Cloud& c, const float* d_x, int64_t q, float* d_ph
     a.cloud_radius = 0.5f * c.aabb_diag * (1.f + 1e-6f);
     // the pruned prepass keeps one query block per CTA with no point split, so
     // it is used once there are enough query blocks to fill the GPU
-    const bool pruned = use_pruned_prepass(c, p, o);
-    a.pre_split = pruned ? 1 : p.split;
+    const bool pruned = use_pruned_prepass(c, p, o), warp_pre = use_warp_prepass(c, p, o);
+    a.pre_split = pruned || warp_pre ? 1 : p.split;
     cudaError_t e = cudaMallocAsync(&a.d2, (size_t)a.pre_split * q * sizeof(float2), st);
     if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? set_error(SDF_ENOMEM, "sdf_query: scratch")
                                                                 : cuda_error(e, "sdf_query: scratch");
@@ -440,6 +441,8 @@ sdf_status launch_query(const Cloud& c, const float* d_x, int64_t q, float* d_ph
         if (pruned)
             k_prepass_pruned<false><<<(unsigned)p.pre_qblocks, kPrunedThreads, 0, st>>>(c.pre, c.spheres, c.n,
                                                                                      c.n_spheres, a);
+        else if (warp_pre)
+            launch_prepass_warp(c, a, false, st);
         else if (o.lambda_mode == SDF_LAMBDA_GLOBAL)
             k_prepass<SDF_LAMBDA_GLOBAL><<<pre_grid, kThreads, kStages * kPreBytes, st>>>(
                 c.pre, c.n, c.pre_tiles, p.pre_tiles_per_chunk, a, c.status);
