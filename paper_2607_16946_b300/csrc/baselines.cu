@@ -194,7 +194,7 @@ sdf_status launch_plane_query(const Cloud& c, const float* d_x, int64_t q, float
     a.cy = 0.5f * (c.aabb[1] + c.aabb[4]);
     a.cz = 0.5f * (c.aabb[2] + c.aabb[5]);
     a.cloud_radius = 0.5f * c.aabb_diag * (1.f + 1e-6f);
-    const bool pruned = use_pruned_prepass(c, p, o), warp_pre = use_warp_prepass(c, p, o);
+    const bool warp_pre = use_warp_prepass(c, p, o), pruned = !warp_pre && use_pruned_prepass(c, p, o);
     a.pre_split = pruned || warp_pre ? 1 : p.split;
     cudaError_t e = cudaMallocAsync(&a.d2, (size_t)a.pre_split * q * sizeof(float2), st);
     if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? set_error(SDF_ENOMEM, "sdf_query: scratch")

@@ -536,7 +536,7 @@ sdf_status launch_query_grad(const Cloud& c, const float* d_x, int64_t q, float*
         return e == cudaErrorMemoryAllocation ? set_error(SDF_ENOMEM, "sdf_query_grad: scratch")
                                               : cuda_error(e, "sdf_query_grad: scratch");
     };
-    const bool pruned = use_pruned_prepass(c, p, o), warp_pre = use_warp_prepass(c, p, o);
+    const bool warp_pre = use_warp_prepass(c, p, o), pruned = !warp_pre && use_pruned_prepass(c, p, o);
     a.pre_split = pruned || warp_pre ? 1 : p.split;
     cudaError_t e = cudaMallocAsync(&a.d2, (size_t)a.pre_split * q * sizeof(float2), st);
     if (e != cudaSuccess) return oom(e);

@@ -20,6 +20,9 @@
 #ifndef PTSDF_WARP_PREPASS
 #define PTSDF_WARP_PREPASS 1   // 0: such batches take the point-split full scan
 #endif
+#ifndef PTSDF_WARP_PREPASS_ALL
+#define PTSDF_WARP_PREPASS_ALL 0   // 1: large batches too (instead of a thread per query)
+#endif
 
 namespace ptsdf {
 namespace qk {
@@ -152,7 +155,7 @@ __global__ void __launch_bounds__(kWarpPreThreads) k_prepass_warp(const float4* 
 // the same results: the tests compare the two that way).
 __host__ inline bool use_warp_prepass(const Cloud& c, const Plan& p, const sdf_query_opts& o) {
     return PTSDF_WARP_PREPASS && o.lambda_mode == SDF_LAMBDA_GLOBAL && o.split_n == 0 && c.spheres != nullptr &&
-           !use_pruned_prepass(c, p, o);
+           (PTSDF_WARP_PREPASS_ALL || !use_pruned_prepass(c, p, o));
 }
 
 // Writes a.d2[qi] = (d_max^2, d_min^2) for every query (pre_split = 1) and,
