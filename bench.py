@@ -298,8 +298,10 @@ def make_serving_clouds(n_clouds: int, seed: int):
     return out
 
 
-def run_served(args, dev, pair_rate_gps: float, policy: int = 0, clouds_np=None, precision: int = 0):
-    """Continuous-batching run: Poisson arrivals at `load` x the measured pair
+def run_served(args, dev, pair_rate_gps: float, policy: int = 0, clouds_np=None, precision: int = 0,
+               load: float | None = None):
+    """Continuous-batching run: Poisson arrivals at `load` (default
+    --serve-load) x the measured pair
     rate, requests of Q log-uniform in [1,024, 4,194,304] against random
     resident clouds; kinds QUERY 70%, OFFSET 10%, UNION / DIFFERENCE 10%,
     TRACE_STEP 10%; every request at `precision` (0 FP32 with the tensor
@@ -330,7 +332,8 @@ def run_served(args, dev, pair_rate_gps: float, policy: int = 0, clouds_np=None,
         pairs = q * ns[ca] + (q * ns[cb] if kind in (S.SDF_REQ_UNION, S.SDF_REQ_DIFFERENCE) else 0)
         reqs.append(dict(kind=kind, q=q, ca=ca, cb=cb, off=off, pairs=pairs, offset=0.05 if 0.7 <= u < 0.8 else 0.0))
     mean_pairs = float(np.mean([r["pairs"] for r in reqs]))
-    rate = args.serve_load * pair_rate_gps * 1e9 / mean_pairs          # requests per second
+    load = args.serve_load if load is None else load
+    rate = load * pair_rate_gps * 1e9 / mean_pairs          # requests per second
     arrivals = np.cumsum(rng.exponential(1.0 / rate, size=len(reqs)))
     srv = S.Server(mem_budget_bytes=16 << 30, max_inflight=8, n_streams=args.serve_streams, policy=policy,
                    starve_ms=2000, split_gpairs=SERVE_SPLIT_GPAIRS, express_gpairs=args.serve_express)
@@ -383,7 +386,7 @@ def run_served(args, dev, pair_rate_gps: float, policy: int = 0, clouds_np=None,
             "worst_slowdown": [{"pairs": float(reqs[i]["pairs"]), "latency_ms": float(lat[i]),
                                 "queue_ms": float(queue[i]), "service_ms": float(service[i]),
                                 "chunks": int(stats[i]["chunks"])} for i in np.argsort(-slow)[:3]],
-            "offered_load": args.serve_load, "arrival_rate_per_s": rate, "mean_pairs_per_request": mean_pairs,
+            "offered_load": load, "arrival_rate_per_s": rate, "mean_pairs_per_request": mean_pairs,
             "clouds": len(clouds), "points_total": int(sum(ns)), "outputs_finite": finite,
             "server": {"max_inflight": 8, "n_streams": args.serve_streams, "mem_budget_bytes": 16 << 30,
                        "express_pairs": args.serve_express * 1e9,
@@ -392,7 +395,7 @@ def run_served(args, dev, pair_rate_gps: float, policy: int = 0, clouds_np=None,
                        "requests_split": sum(1 for st in stats if st["chunks"] > 1)},
             "workload": f"{len(clouds)} resident clouds N~logU[2048,500000] (sphere/torus/superquadric/ellipsoid), "
                         f"{len(reqs)} requests Q~logU[1024,4194304], Poisson arrivals at "
-                        f"{args.serve_load} x measured capacity; "
+                        f"{load} x measured capacity; "
                         f"{'FP32 (tensor engine)' if precision == 0 else 'F16X2 packed-half weights, FP32 sums'}"}
 
 
@@ -807,7 +810,7 @@ def compact_summary(line: dict) -> dict:
             out["radius"]["large_cloud_queries_s"] = r(rd["large_cloud"]["queries_per_s"])
             if rd["large_cloud"].get("roofline"):
                 out["radius"]["large_cloud_issue_frac"] = r(rd["large_cloud"]["roofline"]["frac"], 3)
-    for k in ("served", "served_fifo", "served_f16x2"):
+    for k in ("served", "served_high", "served_fifo", "served_f16x2"):
         if k in line:
             out[k] = {"gpairs_s": r(line[k]["value"]), "p50_ms": r(line[k]["p50_ms"]), "p99_ms": r(line[k]["p99_ms"]),
                       "slowdown_p99": r(line[k].get("slowdown_p99"), 3)}
@@ -817,9 +820,11 @@ def compact_summary(line: dict) -> dict:
 
 
 def workload_config(q: int, world: int) -> dict:
-    """The workload both arms run (the main arm adds how it runs it)."""
+    """The workload both arms run, the same dict in both lines (how the main
+    arm runs it goes under its own "run" key)."""
     return {"workload": WORKLOAD, "N": N_POINTS, "Q": q, "C": 64, "lambda": "global",
-            "parallelism": f"replicas{world}" if world > 1 else "single"}
+            "parallelism": f"replicas{world}" if world > 1 else "single",
+            "l2": "inputs larger than L2 (queries 201 MB, phi 67 MB); not flushed"}
 
 
 def run_reference(args, rank, world):
@@ -963,8 +968,8 @@ def run_ours(args, rank, world, local):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": elapsed_s / args.steps * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": dict(workload_config(q, world), precision="fp32", engine="auto (tensor cores for every tile)",
-                       l2="inputs larger than L2 (queries 201 MB, phi 67 MB); not flushed"),
+        "config": workload_config(q, world),
+        "run": {"precision": "fp32", "engine": "auto (tensor cores for every tile)"},
         "queries_per_s": world * q * args.steps / elapsed_s,
         "e2e": {"value": world * pairs_per_step * args.steps / e2e_s / 1e9, "unit": UNIT,
                 "h2d_bytes_per_step": q * 12, "d2h_bytes_per_step": q * 4},
@@ -990,6 +995,10 @@ def run_ours(args, rank, world, local):
         variants = set(args.serve_variants.split(","))
         if "fp32" in variants:
             line["served"] = run_served(args, dev, value, policy=1, clouds_np=clouds_np)
+        if "high" in variants:
+            # the same requests and arrivals, offered at the higher load
+            line["served_high"] = run_served(args, dev, value, policy=1, clouds_np=clouds_np,
+                                             load=args.serve_load_high)
         if "fifo" in variants:
             line["served_fifo"] = run_served(args, dev, value, policy=0, clouds_np=clouds_np)
         if "f16x2" in variants:
@@ -1015,9 +1024,11 @@ def main():
                     help="requests of at most this many Gpairs run on high-priority streams (0: one priority)")
     ap.add_argument("--no-extra-legs", action="store_true", help="omit the gradient and tracing legs")
     ap.add_argument("--serve-clouds", type=int, default=32)
-    ap.add_argument("--serve-variants", default="fp32,fifo,f16x2",
-                    help="served runs: fp32 (smallest-first), fifo, f16x2 (comma-separated)")
+    ap.add_argument("--serve-variants", default="fp32,high,fifo,f16x2",
+                    help="served runs: fp32 (smallest-first), high (the same at --serve-load-high), fifo, "
+                         "f16x2 (comma-separated)")
     ap.add_argument("--serve-load", type=float, default=0.7, help="offered load as a fraction of capacity")
+    ap.add_argument("--serve-load-high", type=float, default=0.9, help="offered load of the 'high' served run")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -204,6 +204,42 @@ __global__ void __launch_bounds__(kThreads) k_prepass(const float4* __restrict__
 // tiles a warp visits differ from warp to warp.
 // --------------------------------------------------------------------------
 constexpr int kPrunedThreads = kConsumerWarps * 32;
+#ifndef PTSDF_PRE_UNROLL
+#define PTSDF_PRE_UNROLL 1   // 0: the sphere walks and tile scans one load at a time
+#endif
+
+// One sphere's tile of the prepass array (points first .. first + cnt - 1),
+// for the lane's queries, with k_prepass's arithmetic.  A full tile's loop
+// has a fixed trip count, so its loads can be issued ahead of the arithmetic.
+template <bool ARGMAX>
+__device__ __forceinline__ void pruned_scan_tile(const float4* __restrict__ pre, int64_t first, int cnt,
+                                                 const float (&xs)[kQueriesPerThread][3],
+                                                 float (&hi)[kQueriesPerThread], float (&lo)[kQueriesPerThread],
+                                                 int32_t (&far)[kQueriesPerThread]) {
+    auto point = [&](int j) {
+        const float4 r = __ldg(pre + first + j);
+#pragma unroll
+        for (int k = 0; k < kQueriesPerThread; ++k) {
+            const float v = fmaf(xs[k][0], r.x, fmaf(xs[k][1], r.y, fmaf(xs[k][2], r.z, r.w)));
+            if (ARGMAX) {
+                if (v > hi[k] || (v == hi[k] && (int32_t)(first + j) < far[k])) {
+                    hi[k] = v;
+                    far[k] = (int32_t)(first + j);
+                }
+            } else {
+                hi[k] = fmaxf(hi[k], v);
+            }
+            lo[k] = fminf(lo[k], v);
+        }
+    };
+    if (PTSDF_PRE_UNROLL && cnt == kSphereTile) {
+#pragma unroll 8
+        for (int j = 0; j < kSphereTile; ++j) point(j);
+    } else {
+#pragma unroll 1
+        for (int j = 0; j < cnt; ++j) point(j);
+    }
+}
 
 template <bool ARGMAX>
 __global__ void __launch_bounds__(kPrunedThreads) k_prepass_pruned(const float4* __restrict__ pre,
@@ -229,8 +265,10 @@ __global__ void __launch_bounds__(kPrunedThreads) k_prepass_pruned(const float4*
     }
     // bounds from the spheres; every lane also notes the spheres that gave its
     // first query's bounds
-    int64_t t_far = 0, t_near = 0;
-    for (int64_t t = 0; t < nsph; ++t) {
+    int32_t t_far = 0, t_near = 0;
+    const int32_t ns = (int32_t)nsph;
+#pragma unroll 4
+    for (int32_t t = 0; t < ns; ++t) {
         const float4 s = __ldg(spheres + t);
 #pragma unroll
         for (int k = 0; k < kQueriesPerThread; ++k) {
@@ -249,31 +287,16 @@ __global__ void __launch_bounds__(kPrunedThreads) k_prepass_pruned(const float4*
     // (its queries are neighbours), and take the farthest and nearest of their
     // points (less a rounding margin) as the bounds.  Only the thresholds of the scan below change; every
     // extreme still comes from the same arithmetic.
-    int64_t seeds[4] = {__shfl_sync(0xffffffffu, t_far, 0), __shfl_sync(0xffffffffu, t_near, 0),
-                        __shfl_sync(0xffffffffu, t_far, 31), __shfl_sync(0xffffffffu, t_near, 31)};
+    const int32_t seeds[4] = {__shfl_sync(0xffffffffu, t_far, 0), __shfl_sync(0xffffffffu, t_near, 0),
+                              __shfl_sync(0xffffffffu, t_far, 31), __shfl_sync(0xffffffffu, t_near, 31)};
     for (int seed = 0; seed < 4; ++seed) {
         const int64_t t = seeds[seed];
         bool dup = false;
         for (int o = 0; o < seed; ++o) dup = dup || seeds[o] == t;
         if (dup) continue;
         const int64_t first = t * kSphereTile;
-        const int cnt = (int)(n - first < kSphereTile ? n - first : kSphereTile);
-        for (int j = 0; j < cnt; ++j) {
-            const float4 r = __ldg(pre + first + j);
-#pragma unroll
-            for (int k = 0; k < kQueriesPerThread; ++k) {
-                const float v = fmaf(xs[k][0], r.x, fmaf(xs[k][1], r.y, fmaf(xs[k][2], r.z, r.w)));
-                if (ARGMAX) {
-                    if (v > hi[k] || (v == hi[k] && (int32_t)(first + j) < far[k])) {
-                        hi[k] = v;
-                        far[k] = (int32_t)(first + j);
-                    }
-                } else {
-                    hi[k] = fmaxf(hi[k], v);
-                }
-                lo[k] = fminf(lo[k], v);
-            }
-        }
+        pruned_scan_tile<ARGMAX>(pre, first, (int)(n - first < kSphereTile ? n - first : kSphereTile), xs, hi, lo,
+                                 far);
     }
 #pragma unroll
     for (int k = 0; k < kQueriesPerThread; ++k) {
@@ -283,34 +306,30 @@ __global__ void __launch_bounds__(kPrunedThreads) k_prepass_pruned(const float4*
         lbmax[k] = fmaxf(lbmax[k], sqrtf(fmaxf(hi[k] + xx[k], 0.f)) - margin);
         ubmin[k] = fminf(ubmin[k], sqrtf(fmaxf(lo[k] + xx[k], 0.f)) + margin);
     }
-    // exact scan of the tiles that may hold an extreme
-    for (int64_t t = 0; t < nsph; ++t) {
-        const float4 s = __ldg(spheres + t);
-        bool need = false;
+    // exact scan of the tiles that may hold an extreme: the spheres are
+    // tested four at a time (their loads and roots issued together), then
+    // the tiles any lane needs are scanned in order
+    constexpr int kTest = PTSDF_PRE_UNROLL ? 4 : 1;
+    for (int32_t t0 = 0; t0 < ns; t0 += kTest) {
+        bool need[kTest];
 #pragma unroll
-        for (int k = 0; k < kQueriesPerThread; ++k) {
-            const float dx = xs[k][0] - s.x, dy = xs[k][1] - s.y, dz = xs[k][2] - s.z;
-            const float dc = sqrt_mufu(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
-            need = need || (dc + s.w >= lbmax[k]) || (dc - s.w <= ubmin[k]);
-        }
-        if (!__any_sync(0xffffffffu, need)) continue;
-        const int64_t first = t * kSphereTile;
-        const int cnt = (int)(n - first < kSphereTile ? n - first : kSphereTile);
-        for (int j = 0; j < cnt; ++j) {
-            const float4 r = __ldg(pre + first + j);
+        for (int u = 0; u < kTest; ++u) {
+            const int32_t t = t0 + u < ns ? t0 + u : ns - 1;
+            const float4 s = __ldg(spheres + t);
+            need[u] = false;
 #pragma unroll
             for (int k = 0; k < kQueriesPerThread; ++k) {
-                const float v = fmaf(xs[k][0], r.x, fmaf(xs[k][1], r.y, fmaf(xs[k][2], r.z, r.w)));
-                if (ARGMAX) {
-                    if (v > hi[k] || (v == hi[k] && (int32_t)(first + j) < far[k])) {
-                        hi[k] = v;
-                        far[k] = (int32_t)(first + j);
-                    }
-                } else {
-                    hi[k] = fmaxf(hi[k], v);
-                }
-                lo[k] = fminf(lo[k], v);
+                const float dx = xs[k][0] - s.x, dy = xs[k][1] - s.y, dz = xs[k][2] - s.z;
+                const float dc = sqrt_mufu(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+                need[u] = need[u] || (dc + s.w >= lbmax[k]) || (dc - s.w <= ubmin[k]);
             }
+        }
+#pragma unroll
+        for (int u = 0; u < kTest; ++u) {
+            if (t0 + u >= ns || !__any_sync(0xffffffffu, need[u])) continue;
+            const int64_t first = (int64_t)(t0 + u) * kSphereTile;
+            pruned_scan_tile<ARGMAX>(pre, first, (int)(n - first < kSphereTile ? n - first : kSphereTile), xs,
+                                     hi, lo, far);
         }
     }
 #pragma unroll

@@ -144,3 +144,19 @@ def test_radius_roofline_needs_a_capture_of_the_current_source(tmp_path, monkeyp
     assert r["frac"] == pytest.approx(600.0 / (4 * 148 * 2.032)) and r["traffic"] == 1.0e9
     path.write_text(json.dumps({"kernel_sha": "0" * 16, "warp_instructions_per_call": 6.0e10}))
     assert bench.radius_issue_roofline(0.1, 148, 2032.0) is None
+
+
+def test_both_arms_print_the_same_config(monkeypatch, capsys):
+    """The main arm and the reference (oracle) arm describe one workload with
+    the same dict (the main arm puts how it runs it under its own key): the
+    reference arm's printed line, with its timed oracle samples stubbed."""
+    class Args:
+        warmup, steps = 3, 2
+    monkeypatch.setattr(bench, "_timed_oracle_sample", lambda *a, **k: (2048, 0.05))
+    bench.run_reference(Args(), 0, 1)
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert line["impl"] == "reference"
+    assert line["config"] == bench.workload_config(bench.GRID_RES ** 3, 1)
+    c = line["config"]
+    assert c["Q"] == bench.GRID_RES ** 3 and c["N"] == bench.N_POINTS
+    assert "l2" in c and "engine" not in c and "precision" not in c
