@@ -36,24 +36,53 @@ struct Extremes {
 };
 
 template <bool ARGMAX>
+__device__ __forceinline__ void scan_point(float4 r, int64_t j, float xs0, float xs1, float xs2, Extremes& e) {
+    const float v = fmaf(xs0, r.x, fmaf(xs1, r.y, fmaf(xs2, r.z, r.w)));
+    if (ARGMAX) {
+        if (v > e.hi || (v == e.hi && (int32_t)j < e.far)) {
+            e.hi = v;
+            e.far = (int32_t)j;
+        }
+    } else {
+        e.hi = fmaxf(e.hi, v);
+    }
+    e.lo = fminf(e.lo, v);
+}
+
+template <bool ARGMAX>
 __device__ __forceinline__ void scan_tile(const float4* __restrict__ pre, int64_t n, int64_t t, int lane, float xs0,
                                           float xs1, float xs2, Extremes& e) {
     const int64_t first = t * kSphereTile;
+    if (PTSDF_PRE_UNROLL && first + kSphereTile <= n) {   // a full tile: both loads before the arithmetic
+        const float4 r0 = __ldg(pre + first + lane), r1 = __ldg(pre + first + 32 + lane);
+        scan_point<ARGMAX>(r0, first + lane, xs0, xs1, xs2, e);
+        scan_point<ARGMAX>(r1, first + 32 + lane, xs0, xs1, xs2, e);
+        return;
+    }
 #pragma unroll
     for (int h = 0; h < kSphereTile; h += 32) {
         const int64_t j = first + h + lane;
         if (j >= n) break;
-        const float4 r = __ldg(pre + j);
-        const float v = fmaf(xs0, r.x, fmaf(xs1, r.y, fmaf(xs2, r.z, r.w)));
-        if (ARGMAX) {
-            if (v > e.hi || (v == e.hi && (int32_t)j < e.far)) {
-                e.hi = v;
-                e.far = (int32_t)j;
-            }
-        } else {
-            e.hi = fmaxf(e.hi, v);
-        }
-        e.lo = fminf(e.lo, v);
+        scan_point<ARGMAX>(__ldg(pre + j), j, xs0, xs1, xs2, e);
+    }
+}
+
+// Two tiles, all four loads issued before the arithmetic (the extremes and
+// the lowest farthest index do not depend on the order of the points).
+template <bool ARGMAX>
+__device__ __forceinline__ void scan_tile_pair(const float4* __restrict__ pre, int64_t n, int64_t t, int64_t u,
+                                               int lane, float xs0, float xs1, float xs2, Extremes& e) {
+    const int64_t ft = t * kSphereTile, fu = u * kSphereTile;
+    if (ft + kSphereTile <= n && fu + kSphereTile <= n) {
+        const float4 r0 = __ldg(pre + ft + lane), r1 = __ldg(pre + ft + 32 + lane);
+        const float4 r2 = __ldg(pre + fu + lane), r3 = __ldg(pre + fu + 32 + lane);
+        scan_point<ARGMAX>(r0, ft + lane, xs0, xs1, xs2, e);
+        scan_point<ARGMAX>(r1, ft + 32 + lane, xs0, xs1, xs2, e);
+        scan_point<ARGMAX>(r2, fu + lane, xs0, xs1, xs2, e);
+        scan_point<ARGMAX>(r3, fu + 32 + lane, xs0, xs1, xs2, e);
+    } else {
+        scan_tile<ARGMAX>(pre, n, t, lane, xs0, xs1, xs2, e);
+        scan_tile<ARGMAX>(pre, n, u, lane, xs0, xs1, xs2, e);
     }
 }
 
@@ -87,6 +116,7 @@ __global__ void __launch_bounds__(kWarpPreThreads) k_prepass_warp(const float4* 
         // 1. bounds from the spheres, with the spheres that gave them
         float lb = -INFINITY, ub = INFINITY;
         int64_t tf = 0, tn = 0;
+#pragma unroll 4
         for (int64_t t = lane; t < nsph; t += 32) {
             const float4 s = __ldg(spheres + t);
             const float dx = xs0 - s.x, dy = xs1 - s.y, dz = xs2 - s.z;
@@ -138,7 +168,13 @@ __global__ void __launch_bounds__(kWarpPreThreads) k_prepass_warp(const float4* 
             while (m) {
                 const int b = __ffs(m) - 1;
                 m &= m - 1;
-                scan_tile<ARGMAX>(pre, n, t0 + b, lane, xs0, xs1, xs2, e);
+                if (PTSDF_PRE_UNROLL && m) {
+                    const int b2 = __ffs(m) - 1;
+                    m &= m - 1;
+                    scan_tile_pair<ARGMAX>(pre, n, t0 + b, t0 + b2, lane, xs0, xs1, xs2, e);
+                } else {
+                    scan_tile<ARGMAX>(pre, n, t0 + b, lane, xs0, xs1, xs2, e);
+                }
             }
         }
         warp_reduce<ARGMAX>(e);
