@@ -102,10 +102,11 @@ def pair_ceiling(rates, fp32_per_pair):
 # Newton steps (8 of its FP32 operations, as .f32x2 pairs) and the rest of
 # its arithmetic as .f32x2.  Direct: a, b -> rho (MUFU sqrt), the tube
 # distance (MUFU sqrt), the weight's exp2; flat curvature form: one half-angle
-# step (sqrt + rcp); curved: two.  The probe does not time these mixes whole,
-# so their cost is the sum of the single-operation costs (the mixes it does
-# time equal those sums).
-TC_FORM_COST = {"direct": ((2, 0, 1), 17), "flat": ((1, 1, 1), 19), "curved": ((2, 2, 1), 23)}
+# step (sqrt + rcp); curved: two square roots and, with the two steps over a
+# common denominator, one reciprocal (26 FP32 operations).  The probe does
+# not time these mixes whole, so their cost is the sum of the single-operation
+# costs (the mixes it does time equal those sums).
+TC_FORM_COST = {"direct": ((2, 0, 1), 17), "flat": ((1, 1, 1), 19), "curved": ((2, 1, 1), 26)}
 
 
 def mix_cost(rates, form):

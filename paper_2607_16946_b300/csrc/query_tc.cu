@@ -97,6 +97,9 @@ constexpr uint32_t kBTileBytes = 2 * kTcSubB;         // K = 32
 #ifndef PTSDF_TC_ACC2
 #define PTSDF_TC_ACC2 1     // the packed epilogues add into .f32x2 sums kept across batches and tiles (0: into W, S per batch)
 #endif
+#ifndef PTSDF_TC_ONE_RCP
+#define PTSDF_TC_ONE_RCP 1  // general curvature-form pairs: one reciprocal instead of two (0: the record formula's two)
+#endif
 #ifndef PTSDF_TC_STAGES
 #define PTSDF_TC_STAGES 8
 #endif
@@ -327,20 +330,42 @@ __device__ __forceinline__ void tile_pairs_kappa2(const float (&v)[kVals], float
         const f32x2 h = f2_pack(v[8 + i], v[9 + i]), m0 = f2_pack(v[24 + i], v[25 + i]);
         const f32x2 nkM = f2_pack(v[40 + i], v[41 + i]), z2 = f2_pack(v[48 + i], v[49 + i]);
         const f32x2 hh = f2_mul(h, h);
-        f32x2 ap;
-        if (FORM == kFormFlat) {
-            ap = f2_mul(m0, f2_pack(0.5f, 0.5f));
-        } else {
+        f32x2 g;
+        if (FORM != kFormFlat && PTSDF_TC_ONE_RCP) {
+            // The general formula with one reciprocal: with D1 = 1 + sqrt(1 + k m),
+            // a' = m / D1 and Nn = N' D1^2 = kM (m^2 + h^2 D1^2) + 2 zeta m D1 (kM the
+            // record's -kappa_max), 1 + kM N' = (D1^2 + kM Nn) / D1^2, so
+            // g = N' / (1 + sqrt(1 + kM N')) = Nn / (D1 (D1 + sqrt(D1^2 + kM Nn))).
+            // D1 >= 1 keeps the denominator >= 1, and the clamp of the second
+            // root's argument at 0 is the same as the general formula's.
             const f32x2 yy = f2_pack(v[16 + i], v[17 + i]), k = f2_pack(v[32 + i], v[33 + i]);
             const f32x2 m = f2_fma(k, f2_sub(yy, hh), m0);
             const f32x2 t1 = f2_fma(k, m, ONE);
-            const f32x2 den1 = f2_add(ONE, f2_pack(sqrt_mufu(fmaxf(f2_lo(t1), 0.f)), sqrt_mufu(fmaxf(f2_hi(t1), 0.f))));
-            ap = f2_mul(m, f2_pack(rcp_mufu(f2_lo(den1)), rcp_mufu(f2_hi(den1))));
+            const f32x2 D1 = f2_add(ONE, f2_pack(sqrt_mufu(fmaxf(f2_lo(t1), 0.f)), sqrt_mufu(fmaxf(f2_hi(t1), 0.f))));
+            const f32x2 D1sq = f2_mul(D1, D1);
+            const f32x2 Nn = f2_fma(nkM, f2_fma(m, m, f2_mul(hh, D1sq)), f2_mul(z2, f2_mul(m, D1)));
+            const f32x2 u = f2_fma(nkM, Nn, D1sq);
+            const f32x2 den = f2_mul(D1, f2_add(D1, f2_pack(sqrt_mufu(fmaxf(f2_lo(u), 0.f)),
+                                                            sqrt_mufu(fmaxf(f2_hi(u), 0.f)))));
+            g = f2_mul(Nn, f2_pack(rcp_mufu(f2_lo(den)), rcp_mufu(f2_hi(den))));
+        } else {
+            f32x2 ap;
+            if (FORM == kFormFlat) {
+                ap = f2_mul(m0, f2_pack(0.5f, 0.5f));
+            } else {
+                const f32x2 yy = f2_pack(v[16 + i], v[17 + i]), k = f2_pack(v[32 + i], v[33 + i]);
+                const f32x2 m = f2_fma(k, f2_sub(yy, hh), m0);
+                const f32x2 t1 = f2_fma(k, m, ONE);
+                const f32x2 den1 =
+                    f2_add(ONE, f2_pack(sqrt_mufu(fmaxf(f2_lo(t1), 0.f)), sqrt_mufu(fmaxf(f2_hi(t1), 0.f))));
+                ap = f2_mul(m, f2_pack(rcp_mufu(f2_lo(den1)), rcp_mufu(f2_hi(den1))));
+            }
+            const f32x2 Np = f2_fma(nkM, f2_fma(ap, ap, hh), f2_mul(z2, ap));
+            const f32x2 t2 = f2_fma(nkM, Np, ONE);
+            const f32x2 den2 =
+                f2_add(ONE, f2_pack(sqrt_mufu(fmaxf(f2_lo(t2), 0.f)), sqrt_mufu(fmaxf(f2_hi(t2), 0.f))));
+            g = f2_mul(Np, f2_pack(rcp_mufu(f2_lo(den2)), rcp_mufu(f2_hi(den2))));
         }
-        const f32x2 Np = f2_fma(nkM, f2_fma(ap, ap, hh), f2_mul(z2, ap));
-        const f32x2 t2 = f2_fma(nkM, Np, ONE);
-        const f32x2 den2 = f2_add(ONE, f2_pack(sqrt_mufu(fmaxf(f2_lo(t2), 0.f)), sqrt_mufu(fmaxf(f2_hi(t2), 0.f))));
-        const f32x2 g = f2_mul(Np, f2_pack(rcp_mufu(f2_lo(den2)), rcp_mufu(f2_hi(den2))));
         // |d^2|: the products may round a zero distance slightly negative
         const f32x2 d = sqrt2_newton(fabsf(v[i]), fabsf(v[i + 1]));
         const f32x2 arg = f2_fma(NLs, d, A0v);

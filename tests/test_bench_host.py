@@ -17,10 +17,10 @@ RATES = {"sqrt": 16.0, "rsqrt": 16.0, "ex2": 32.0, "fma": 124.1, "rcp": 16.0,
 
 def test_single_form_ceiling():
     """Every tensor-core form takes d on the FMA pipe: direct 2 sqrt + 1 exp2,
-    flat 1 sqrt + 1 rcp + 1 exp2, curved 2 sqrt + 2 rcp + 1 exp2, from the
+    flat 1 sqrt + 1 rcp + 1 exp2, curved 2 sqrt + 1 rcp + 1 exp2, from the
     single-operation rates."""
     expect = {"direct": 2 / 16.0 + 1 / 32.0, "flat": 1 / 16.0 + 1 / 16.0 + 1 / 32.0,
-              "curved": 2 / 16.0 + 2 / 16.0 + 1 / 32.0}
+              "curved": 2 / 16.0 + 1 / 16.0 + 1 / 32.0}
     for form in ("direct", "flat", "curved"):
         best, mufu, fma = bench.tc_pair_ceiling(RATES, {form: 1000})
         assert mufu == pytest.approx(1.0 / expect[form])
@@ -37,7 +37,7 @@ def test_mixed_forms_share_the_clocks():
     unchanged when every count doubles, lower with more curved points."""
     counts = {"direct": 97904, "curved": 2096}
     _, mufu, _ = bench.tc_pair_ceiling(RATES, counts)
-    curved = 1.0 / (4 / 16.0 + 1 / 32.0)
+    curved = 1.0 / (3 / 16.0 + 1 / 32.0)
     assert curved < mufu < 6.4
     assert mufu == pytest.approx(100000 / (97904 / 6.4 + 2096 / curved))
     assert bench.tc_pair_ceiling(RATES, {k: 2 * v for k, v in counts.items()})[1] == pytest.approx(mufu)
@@ -47,7 +47,7 @@ def test_mixed_forms_share_the_clocks():
 def test_unmeasured_mix_falls_back_to_single_operations():
     single = {k: v for k, v in RATES.items() if not k.startswith("pair_")}
     assert bench.mix_cost(single, "direct") == pytest.approx(2 / 16.0 + 1 / 32.0)
-    assert bench.mix_cost(single, "curved") == pytest.approx(2 / 16.0 + 2 / 16.0 + 1 / 32.0)
+    assert bench.mix_cost(single, "curved") == pytest.approx(2 / 16.0 + 1 / 16.0 + 1 / 32.0)
     # with the measured rates the mixes are additive: the single-operation sums
     # equal the mixes the probe times whole
     assert 1 / bench.single_op_cost(single, (3, 0, 1)) == pytest.approx(RATES["pair_direct"], rel=1e-3)
