@@ -1,8 +1,9 @@
 """Accuracy of the FP32 sums on a cloud of 2^21 = 2,097,152 points.
 
-Every query's W and S are sums over two million weights, accumulated per
-32-point tile, per point chunk and in the fixed-order merge of the chunks'
-partials, all in FP32.  Against the FP64 oracle on 512 queries (half of them
+Every query's W and S are sums over two million weights, all in FP32:
+accumulated per epilogue lane in two running halves (tensor-core engine) or
+per 32-point tile (FP32 units), per point chunk, and in the fixed-order merge
+of the chunks' partials.  Against the FP64 oracle on 512 queries (half of them
 near the surface), on both engines and with explicit point chunks (the merge
 of 64 partials): the FP32 bar (1e-4 x AABB diagonal) holds, so the merge needs
 no FP64.  The measured errors are printed (pytest -s).
