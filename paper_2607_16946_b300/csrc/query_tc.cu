@@ -50,8 +50,8 @@
 // rho = sqrt(a^2 + b^2), D = sqrt((rho - R)^2 + h^2), g = sT D - sT r (three
 // square roots with d).  Curvature form: the two half-angle steps of the
 // record formula (kappa_min = 0 tiles skip the first, which is then exact
-// without a root), again three roots and two reciprocals with d, or two and
-// one.  Then w = exp2(-L (d - d_min)), W += w, S += w g.  The packed
+// without a root; the other tiles take the two steps over one denominator),
+// three roots and one reciprocal with d, or two and one.  Then w = exp2(-L (d - d_min)), W += w, S += w g.  The packed
 // epilogues keep W and S as .f32x2 running sums (one per point parity of a
 // step) for the lane's whole share of the tiles and add the two halves once
 // at the end: on the dense grid this saves the four scalar adds per batch
@@ -320,7 +320,8 @@ __device__ __forceinline__ void tile_pairs_direct2(const float (&v)[kVals], floa
 // FP32 arithmetic as .f32x2 (the MUFU roots and reciprocals stay scalar) and
 // d on the FMA pipe as in the direct form, so that a flat pair costs the
 // special-function unit 1 sqrt + 1 rcp + 1 exp2 (20 cycles per 32 pairs
-// instead of 28) and a curved one 2 sqrt + 2 rcp + 1 exp2 (36 instead of 44).
+// instead of 28) and a curved one, with its two half-angle steps over one
+// denominator, 2 sqrt + 1 rcp + 1 exp2 (28 instead of 44).
 template <int FORM>
 __device__ __forceinline__ void tile_pairs_kappa2(const float (&v)[kVals], float Ls, float A0, f32x2& tw, f32x2& ts) {
     const f32x2 NLs = f2_pack(-Ls, -Ls), A0v = f2_pack(A0, A0), ONE = f2_pack(1.f, 1.f);
