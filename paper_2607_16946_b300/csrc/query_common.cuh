@@ -205,7 +205,7 @@ __global__ void __launch_bounds__(kThreads) k_prepass(const float4* __restrict__
 // --------------------------------------------------------------------------
 constexpr int kPrunedThreads = kConsumerWarps * 32;
 #ifndef PTSDF_PRE_UNROLL
-#define PTSDF_PRE_UNROLL 1   // 0: the sphere walks and tile scans one load at a time
+#define PTSDF_PRE_UNROLL 1   // 0: spheres tested one at a time, tiles scanned at a variable trip count
 #endif
 
 // One sphere's tile of the prepass array (points first .. first + cnt - 1),
