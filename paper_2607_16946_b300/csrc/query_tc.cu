@@ -100,6 +100,9 @@ constexpr uint32_t kBTileBytes = 2 * kTcSubB;         // K = 32
 #ifndef PTSDF_TC_ONE_RCP
 #define PTSDF_TC_ONE_RCP 1  // general curvature-form pairs: one reciprocal instead of two (0: the record formula's two)
 #endif
+#ifndef PTSDF_TC_FLAT_LD
+#define PTSDF_TC_FLAT_LD 1  // flat tiles load only the five quantities their formula reads (0: all seven)
+#endif
 #ifndef PTSDF_TC_STAGES
 #define PTSDF_TC_STAGES 8
 #endif
@@ -607,11 +610,23 @@ __global__ void __maxnreg__(96) k_fwd_tc(TcArgs ta, int32_t* status) {
                 const int cg = half * kGroupsPerWarp + gb;   // column group: 8 points x 7 quantities
                 float v[kVals];
                 const uint32_t ta_addr = lane_addr + (uint32_t)b * kBufCols + (uint32_t)(cg * kVals);
-                tc::tmem_ld16(ta_addr, v, 0);
-                tc::tmem_ld16(ta_addr + 16, v, 16);
-                tc::tmem_ld16(ta_addr + 32, v, 32);
-                tc::tmem_ld8(ta_addr + 48, v, 48);
-                tc::tmem_wait_ld_values(v);
+                if constexpr (FORMS == kFormFlat && PTSDF_TC_FLAT_LD) {
+                    // the flat formula reads d^2, h, m0, -kmax s and 2 zeta
+                    // (quantities 0, 1, 3, 5, 6): |y|^2 and |kmin| s stay in TMEM
+                    tc::tmem_ld16(ta_addr, v, 0);
+                    tc::tmem_ld8(ta_addr + 24, v, 24);
+                    tc::tmem_ld16(ta_addr + 40, v, 40);
+                    tc::tmem_wait_ld();
+#pragma unroll
+                    for (int i = 0; i < kVals; ++i)
+                        if (i < 16 || (i >= 24 && i < 32) || i >= 40) asm volatile("" : "+f"(v[i]));
+                } else {
+                    tc::tmem_ld16(ta_addr, v, 0);
+                    tc::tmem_ld16(ta_addr + 16, v, 16);
+                    tc::tmem_ld16(ta_addr + 32, v, 32);
+                    tc::tmem_ld8(ta_addr + 48, v, 48);
+                    tc::tmem_wait_ld_values(v);
+                }
                 if (gb == kGroupsPerWarp - 1) {   // the accumulator is read: the next MMA may overwrite it
                     tc::fence_before_sync();
                     __syncwarp();
